@@ -1,0 +1,270 @@
+"""Benchmark: candidates evaluated per second and time-to-optimal reduction of the
+exhaustive Kron-based search (Algorithm 1) on the 1,000-bus synthetic feeder.
+
+One step = one full reduction through the C ABI: load flow of both scenarios,
+renumbering/LCA/path impedances, the search to 50 % reduction (or until no
+candidate is feasible), and the result export, on inputs already resident in
+HBM (``okr_reduce_device``).  ``e2e`` repeats the measurement through
+``okr_reduce`` from pinned host buffers, with the result read back.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank reduces its own replica of the workload (the search of
+one feeder is one sequential chain of merges; replicas scale weakly).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "candidates evaluated/s & time-to-optimal reduction, 1000-node feeder vs FP64"
+WORKLOAD = "feeder1000"
+FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (non-tensor) rate; see the design doc
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _workload_config(f, run):
+    return {"workload": f"{WORKLOAD}: {f.n_bus} buses ({f.n_phase_nodes} phase nodes), 12.47 kV, "
+                        f"{f.n_scen} loading scenarios, target {int(run['target'] * 100)}% reduction, "
+                        f"margin {run['margin']} p.u.",
+            "n_bus": f.n_bus, "n_phase_nodes": f.n_phase_nodes, "scenarios": f.n_scen,
+            "target_reduction": run["target"], "margin_pu": run["margin"], "seed": f.meta["seed"]}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.out = open(os.devnull, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                data, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                data, _ = self.proc.communicate()
+            self.lines = [l for l in data.splitlines() if l.strip()]
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            c = [x.strip() for x in line.split(",")]
+            try:
+                sm.append(float(c[1]))
+                smax.append(float(c[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, c[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(f, run, max_seconds=30.0):
+    """The CPU oracle (delta mode, FP64, OpenMP over candidates) on the same
+    feeder: the full reduction when it fits the time budget."""
+    from oracle import oracle as O
+    vhat, ihat = O.operating_points(f)
+    merges = O.max_merges_for(f.n_bus, run["target"])
+    t0 = time.perf_counter()
+    res = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
+    dt = time.perf_counter() - t0
+    return {"value": res["candidates"] / dt, "unit": "candidates/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"full {WORKLOAD} reduction ({res['n_iter']} merges, {res['candidates']} candidates) "
+                      f"in {dt:.2f} s, delta mode", "seconds": dt, "merges": int(res["n_iter"])}
+
+
+def run_reference(args, rank, world):
+    import feedergen as fg
+    from oracle import oracle as O
+    if rank != 0:
+        return
+    f, run = fg.preset(WORKLOAD)
+    vhat, ihat = O.operating_points(f)
+    merges = O.max_merges_for(f.n_bus, run["target"])
+    # one step = the first `sample` merges of the reduction (the costliest part:
+    # the candidate count falls as the feeder shrinks), sized to finish in seconds
+    sample = min(merges, 100)
+    for _ in range(args.warmup):
+        O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=sample)
+    times, cands = [], 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=sample)
+        times.append(time.perf_counter() - t0)
+        cands += r["candidates"]
+    total = sum(times)
+    value = cands / total
+    line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": _workload_config(f, run) | {"step": f"first {sample} merges by the CPU oracle"},
+            "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"first {sample} merges of {WORKLOAD} per step, delta mode"},
+            "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import feedergen as fg
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    f, run = fg.preset(WORKLOAD)
+    stream = torch.cuda.current_stream()
+    ctx = K.Context(local, stream.cuda_stream)
+    p = K.default_params(margin=run["margin"], target_reduction=run["target"])
+
+    dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f.parent, f.phases, f.z_line, f.s_load)]
+    dfeed = K.device_feeder(f.n_bus, f.n_scen, *[t.data_ptr() for t in dev], f.v_slack)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(max(args.warmup, 3)):
+        ctx.reduce_device(dfeed, p)
+    summ = ctx.summary()
+    cand_per_step = summ["candidates"]
+    launches_per_step = summ["launches"]
+
+    # ---- device-resident timed region
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))                      # evict L2 between steps (outside the events)
+            starts[i].record(stream)
+            ctx.reduce_device(dfeed, p)
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if dist:
+        dist.barrier()
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cand_per_step * args.steps / (ms / 1e3)
+
+    # ---- end to end: pinned host inputs through okr_reduce, result read back
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (f.parent, f.phases, f.z_line, f.s_load)]
+
+    import types
+    host_feeder = types.SimpleNamespace(parent=pinned[0].numpy(), phases=pinned[1].numpy(), z_line=pinned[2].numpy(),
+                                        s_load=pinned[3].numpy(), v_slack=f.v_slack)
+
+    h2d = sum(t.numel() * t.element_size() for t in pinned)
+    e2e_steps = max(1, min(args.steps, 50))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.reduce(host_feeder, p)
+        sup = ctx.assignment()
+        dec = ctx.decisions()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    d2h = sup.nbytes + sum(v.nbytes for v in dec.values())
+    e2e = {"value": cand_per_step / e2e_s, "unit": "candidates/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "time_to_optimal_s": e2e_s}
+
+    # ---- roofline of the dominant kernel (candidate sweep), CUDA events around
+    # every sweep launch on the library stream, one profiled step
+    pp = K.default_params(margin=run["margin"], target_reduction=run["target"], profile=1)
+    ctx.reduce_device(dfeed, pp)
+    ps = ctx.summary()
+    achieved = ps["sweep_flops"] / (ps["sweep_ms"] / 1e3) / 1e12 if ps["sweep_ms"] > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_sweep",
+                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+                "avg_launch_us": 1e3 * ps["sweep_ms"] / max(1, ps["sweep_launches"]),
+                "launches": ps["sweep_launches"], "flops_per_launch": ps["sweep_flops"] / max(1, ps["sweep_launches"]),
+                "share_of_step": ps["sweep_ms"] / (ms / args.steps)}
+
+    if rank == 0:
+        cb = cpu_baseline(f, run) if world == 1 else None
+        line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": _workload_config(f, run) | {
+                    "l2": "flushed between steps (256 MB write outside the timed events)",
+                    "parallelism": f"replicas x{world}", "time_to_optimal_ms": ms / args.steps,
+                    "candidates_per_step": cand_per_step, "merges": summ["n_iter"],
+                    "stop_reason": summ["stop_reason"], "wall_s": t_wall},
+                "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+                "roofline": roofline}
+        if cb:
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = _args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

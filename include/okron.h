@@ -1,0 +1,163 @@
+/*
+ * okron.h -- C ABI of libokron: exhaustive Kron-based reduction of unbalanced
+ * three-phase radial distribution feeders on a GB300 (sm_103a) GPU.
+ *
+ * The method is Algorithm 1 ("Exhaustive Network Reduction") of Sec. IV of
+ * "Optimal Kron-based reduction of three-phase distribution feeders"
+ * (arXiv 2510.19608).  Starting from every bus being its own super-node, each
+ * iteration evaluates every feasible assignment of one super-node's cluster to
+ * an adjacent super-node (Sec. II-C rules: connectivity, phase availability,
+ * uniqueness), solves the network with the aggregated injections -- which gives
+ * the Kron-reduced super-node voltages of Sec. II-B -- scores the per-phase
+ * voltage-magnitude error against the full network (MICE / SMICE, Sec. III),
+ * rejects candidates whose error exceeds the margin, and commits the argmin.
+ *
+ * Conventions shared by every call
+ *   - Buses are numbered 0..n_bus-1 by the caller; bus 0 is the substation
+ *     (slack, fixed voltage) and parent[i] < i for i >= 1.  phases[i] is a bit
+ *     mask (a = 1, b = 2, c = 4), non-empty, a subset of phases[parent[i]].
+ *   - Complex numbers are two doubles (re, im).  Per-unit throughout.
+ *   - Three-phase arrays are padded: x[..][bus][3][2]; entries of absent phases
+ *     are ignored on input and written as 0 on output.
+ *   - Every call returns an okr_status; no call aborts or throws.  On error the
+ *     context keeps a message (okr_last_error) and the previous results are
+ *     invalid.
+ *   - A context owns one CUDA stream and its device memory; it is not thread
+ *     safe.  Calls that run GPU work return after that work has finished.
+ *   - Input arrays are caller-owned and only read during the call.  Output
+ *     buffers are caller-owned and sized as documented per call.
+ *
+ * Readings of the paper taken by the library (where the text leaves a choice):
+ *   the slack bus keeps its voltage and is never reduced (it may absorb a
+ *   neighbour); a candidate moves the whole cluster of r into s and every member
+ *   takes the super-node's voltage; the error is per phase,
+ *   e = | |Vhat| - |V^c| |; MICE is the largest error in a cluster and SMICE
+ *   sums it over clusters and scenarios; ties: every feasible candidate whose
+ *   score is within tie_tol of the minimum is tied and the smallest (r, s) pair
+ *   of caller bus ids wins; the scenario injections are Ihat = Y Vhat.
+ */
+#ifndef OKRON_H
+#define OKRON_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum okr_status {
+    OKR_OK = 0,
+    OKR_EINVAL = 1,     /* bad argument: null pointer, size, tree or phase rule broken */
+    OKR_ENOMEM = 2,     /* host or device allocation failed */
+    OKR_ECUDA = 3,      /* a CUDA runtime call failed (message in okr_last_error) */
+    OKR_EPF = 4,        /* load flow did not converge */
+    OKR_ETIMEOUT = 5,   /* a device-side wait gave up after its spin limit */
+    OKR_ENOTREADY = 6,  /* no result is available yet */
+    OKR_ESINGULAR = 7,  /* a line impedance block is singular */
+    OKR_EINTERNAL = 8   /* internal bound exceeded (should not happen) */
+} okr_status;
+
+typedef struct okr_ctx okr_ctx;
+
+/* A feeder (Sec. II-A network model).  Which memory the pointers refer to is
+ * stated by each entry point. */
+typedef struct okr_feeder {
+    int32_t n_bus;              /* 2 .. 32768 */
+    int32_t n_scen;             /* scenarios L, 1 .. 4 */
+    const int32_t *parent;      /* [n_bus]; parent[0] = -1 */
+    const uint8_t *phases;      /* [n_bus] */
+    const double *z_line;       /* [n_bus][3][3][2] series impedance of line parent(i) -> i
+                                   (row 0 unused); the block on phases[i] must be invertible */
+    const double *s_load;       /* [n_scen][n_bus][3][2] constant-power load per phase
+                                   (consumption positive) */
+    double v_slack[3][2];       /* slack voltage per phase */
+} okr_feeder;
+
+/* Search parameters (Algorithm 1 inputs and the stop rule). */
+typedef struct okr_params {
+    double margin;              /* voltage-error bound E_bar (eq. v_abs), p.u., > 0 */
+    double target_reduction;    /* stop after ceil(target * n_bus) merges (capped at
+                                   n_bus - 1); 1.0 = run until no candidate is feasible */
+    double tie_tol;             /* tie band tau on the score, >= 0 (default 1e-9) */
+    int32_t objective;          /* 0 = SMICE (Algorithm 1); other values are rejected */
+    int32_t precision;          /* 0 = FP64 throughout */
+    int32_t record_iters;       /* keep every candidate's score for the first K iterations */
+    int32_t max_merges;         /* >= 0 overrides the target; -1 = use target_reduction */
+    int32_t profile;            /* 1 = time every candidate-sweep launch with CUDA events and
+                                   count its arithmetic (slower: no graph replay) */
+    int32_t reserved;           /* must be 0 */
+    int64_t max_spins;          /* limit for device-side waits (0 = default) */
+} okr_params;
+
+typedef struct okr_summary {
+    int32_t n_bus, n_scen;
+    int32_t n_iter;             /* merges committed */
+    int32_t stop_reason;        /* 0 target reached, 1 no feasible candidate */
+    int32_t pf_sweeps;          /* load-flow sweeps (largest over scenarios; 0 if given) */
+    int32_t n_kept;             /* super-nodes left */
+    int64_t candidates;         /* candidates evaluated over the run */
+    double smice;               /* SMICE of the final reduction */
+    double max_error;           /* largest per-phase magnitude error of the final reduction */
+    int64_t launches;           /* kernels launched by the last call */
+    /* filled when params.profile = 1 (zero otherwise): */
+    int64_t sweep_launches;     /* candidate-sweep launches that evaluated candidates */
+    double sweep_ms;            /* their summed duration (CUDA events on the library stream) */
+    double sweep_flops;         /* their algorithmic floating-point operations */
+} okr_summary;
+
+/* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
+ * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, max_spins 0. */
+void okr_default_params(okr_params *p);
+
+/* Creates a context on CUDA device `device`.  stream: a cudaStream_t to run
+ * on, or NULL for a stream owned by the context.  *ctx is library-owned until
+ * okr_destroy.  Device memory is allocated lazily by the first reduction and
+ * grown when a larger feeder arrives. */
+okr_status okr_create(okr_ctx **ctx, int device, void *stream);
+okr_status okr_destroy(okr_ctx *ctx);
+const char *okr_status_str(okr_status s);
+const char *okr_last_error(const okr_ctx *ctx);
+
+/* Full path (Sec. III operating points, then Algorithm 1): load flow of every
+ * scenario by backward/forward sweep, Ihat = Y Vhat, then the search.  Feeder
+ * arrays in HOST memory (copied to the device inside the call). */
+okr_status okr_reduce(okr_ctx *ctx, const okr_feeder *f, const okr_params *p);
+
+/* Same as okr_reduce with the feeder arrays (parent, phases, z_line, s_load)
+ * already in DEVICE memory of the context's device; v_slack is read from *f. */
+okr_status okr_reduce_device(okr_ctx *ctx, const okr_feeder *f, const okr_params *p);
+
+/* Algorithm 1 with a caller-supplied scenario library (its inputs Vhat, Ihat
+ * with Y Vhat = Ihat), HOST memory, [n_scen][n_bus][3][2] each; s_load unused. */
+okr_status okr_reduce_ops(okr_ctx *ctx, const okr_feeder *f, const double *vhat,
+                          const double *ihat, const okr_params *p);
+
+/* Load flow only (HOST feeder).  vhat_out: [n_scen][n_bus][3][2], ihat_out
+ * (may be NULL): Y Vhat, same layout; *sweeps (may be NULL): sweeps used. */
+okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, double *ihat_out,
+                          int32_t *sweeps);
+
+/* ---- results of the last reduction (host buffers, caller-owned) ---- */
+okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out);
+/* Decision sequence, one entry per merge, in caller bus ids: s (absorbing
+ * super-node), r (absorbed), SMICE after the merge, largest error after the
+ * merge, distance of the next score above the tie band, candidates evaluated.
+ * cap = buffer length; any pointer may be NULL. */
+okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_t *r, double *smice,
+                             double *max_error, double *gap, int32_t *ncand);
+/* super_of[n_bus]: the super-node (caller id) each bus is assigned to. */
+okr_status okr_get_assignment(const okr_ctx *ctx, int32_t *super_of);
+/* vhat, vred: [n_scen][n_bus][3][2]; vred[i] is the reduced-network voltage of
+ * bus i (its super-node's).  Either pointer may be NULL. */
+okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred);
+/* Scores of every candidate of iteration `iter` < record_iters (SMICE the
+ * candidate would give; +inf if it breaks the margin), in no particular order.
+ * cap = buffer length (2*n_bus suffices); *count = candidates of that iteration. */
+okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32_t *s, int32_t *r,
+                            double *smice, int32_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OKRON_H */

@@ -201,7 +201,7 @@ int orc_pf(int n, const int *parent, const unsigned char *ph, const double *z,
                         if (ph[i] >> q & 1u) drop += zat(z, i, p, q) * J[i * 3 + q];
                     cplx vn = Vl[parent[i] * 3 + p] - drop;
                     double d = mag(vn - Vl[i * 3 + p]);
-                    if (d > dmax) dmax = d;
+                    if (!(d <= dmax)) dmax = d;        /* a NaN keeps the sweep from converging */
                     Vl[i * 3 + p] = vn;
                 }
             }

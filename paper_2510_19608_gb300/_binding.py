@@ -1,0 +1,238 @@
+"""ctypes binding of libokron (include/okron.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy/torch
+arrays to the C structs and back.  Importing it does not build anything: call
+``paper_2510_19608_gb300.build.build()`` first.  When the library is missing the
+import of :func:`lib` raises -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, EPF, ETIMEOUT, ENOTREADY, ESINGULAR, EINTERNAL = range(9)
+
+
+class OkrError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"okron status {status}: {msg}")
+        self.status = status
+
+
+class Feeder(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_scen", C.c_int32),
+                ("parent", C.c_void_p), ("phases", C.c_void_p), ("z_line", C.c_void_p), ("s_load", C.c_void_p),
+                ("v_slack", (C.c_double * 2) * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("margin", C.c_double), ("target_reduction", C.c_double), ("tie_tol", C.c_double),
+                ("objective", C.c_int32), ("precision", C.c_int32), ("record_iters", C.c_int32),
+                ("max_merges", C.c_int32), ("profile", C.c_int32), ("reserved", C.c_int32),
+                ("max_spins", C.c_int64)]
+
+
+class Summary(C.Structure):
+    _fields_ = [("n_bus", C.c_int32), ("n_scen", C.c_int32), ("n_iter", C.c_int32), ("stop_reason", C.c_int32),
+                ("pf_sweeps", C.c_int32), ("n_kept", C.c_int32), ("candidates", C.c_int64),
+                ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
+                ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double), ("sweep_flops", C.c_double)]
+
+
+EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
+           "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
+           "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libokron.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = lib_path()
+            if not os.path.exists(path):
+                raise OSError(f"{path} is missing: build it with paper_2510_19608_gb300.build.build()")
+            L = C.CDLL(path)
+            P, I32 = C.c_void_p, C.c_int32
+            L.okr_default_params.argtypes = [C.POINTER(Params)]
+            L.okr_default_params.restype = None
+            L.okr_create.argtypes = [C.POINTER(P), C.c_int, P]
+            L.okr_destroy.argtypes = [P]
+            L.okr_status_str.argtypes = [C.c_int]
+            L.okr_status_str.restype = C.c_char_p
+            L.okr_last_error.argtypes = [P]
+            L.okr_last_error.restype = C.c_char_p
+            for fn in ("okr_reduce", "okr_reduce_device"):
+                getattr(L, fn).argtypes = [P, C.POINTER(Feeder), C.POINTER(Params)]
+            L.okr_reduce_ops.argtypes = [P, C.POINTER(Feeder), P, P, C.POINTER(Params)]
+            L.okr_power_flow.argtypes = [P, C.POINTER(Feeder), P, P, P]
+            L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
+            L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
+            L.okr_get_assignment.argtypes = [P, P]
+            L.okr_get_voltages.argtypes = [P, P, P]
+            L.okr_get_recorded.argtypes = [P, I32, I32, P, P, P, P]
+            for fn in EXPORTS:
+                if fn not in ("okr_default_params", "okr_status_str", "okr_last_error"):
+                    getattr(L, fn).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def default_params(**over) -> Params:
+    p = Params()
+    lib().okr_default_params(C.byref(p))
+    for k, v in over.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+class HostFeeder:
+    """Keeps contiguous host copies alive while a call uses their pointers."""
+
+    def __init__(self, feeder):
+        self.parent = np.ascontiguousarray(feeder.parent, dtype=np.int32)
+        self.phases = np.ascontiguousarray(feeder.phases, dtype=np.uint8)
+        self.z_line = np.ascontiguousarray(feeder.z_line, dtype=np.float64)
+        s = getattr(feeder, "s_load", None)
+        self.s_load = None if s is None else np.ascontiguousarray(s, dtype=np.float64)
+        self.v_slack = np.ascontiguousarray(feeder.v_slack, dtype=np.float64).reshape(3, 2)
+        self.n_scen = int(self.s_load.shape[0]) if self.s_load is not None else int(getattr(feeder, "n_scen"))
+        self.c = Feeder()
+        self.c.n_bus = self.parent.shape[0]
+        self.c.n_scen = self.n_scen
+        self.c.parent = _ptr(self.parent).value
+        self.c.phases = _ptr(self.phases).value
+        self.c.z_line = _ptr(self.z_line).value
+        self.c.s_load = None if self.s_load is None else _ptr(self.s_load).value
+        for p in range(3):
+            self.c.v_slack[p][0] = self.v_slack[p, 0]
+            self.c.v_slack[p][1] = self.v_slack[p, 1]
+
+
+def device_feeder(n_bus: int, n_scen: int, parent_ptr: int, phases_ptr: int, z_ptr: int, s_ptr: int,
+                  v_slack) -> Feeder:
+    """okr_feeder whose arrays are device pointers (e.g. torch tensor data_ptr())."""
+    f = Feeder()
+    f.n_bus, f.n_scen = int(n_bus), int(n_scen)
+    f.parent, f.phases, f.z_line, f.s_load = int(parent_ptr), int(phases_ptr), int(z_ptr), int(s_ptr)
+    vs = np.asarray(v_slack, dtype=np.float64).reshape(3, 2)
+    for p in range(3):
+        f.v_slack[p][0], f.v_slack[p][1] = vs[p, 0], vs[p, 1]
+    return f
+
+
+class Context:
+    """One okr_ctx: a CUDA stream and the device workspace."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        self._h = C.c_void_p()
+        self._check(lib().okr_create(C.byref(self._h), int(device), C.c_void_p(stream) if stream else None))
+        self.n_bus = 0
+        self.n_scen = 0
+
+    def close(self):
+        if self._h:
+            lib().okr_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, status: int):
+        if status != OK:
+            h = getattr(self, "_h", None)
+            msg = lib().okr_last_error(h).decode() if h else lib().okr_status_str(status).decode()
+            raise OkrError(status, msg or lib().okr_status_str(status).decode())
+
+    # ---- entry points
+    def reduce(self, feeder, params: Params):
+        hf = HostFeeder(feeder)
+        self._check(lib().okr_reduce(self._h, C.byref(hf.c), C.byref(params)))
+        self.n_bus, self.n_scen = hf.c.n_bus, hf.c.n_scen
+
+    def reduce_device(self, dfeeder: Feeder, params: Params):
+        self._check(lib().okr_reduce_device(self._h, C.byref(dfeeder), C.byref(params)))
+        self.n_bus, self.n_scen = dfeeder.n_bus, dfeeder.n_scen
+
+    def reduce_ops(self, feeder, vhat: np.ndarray, ihat: np.ndarray, params: Params):
+        hf = HostFeeder(feeder)
+        vh = np.ascontiguousarray(np.stack([vhat.real, vhat.imag], -1) if np.iscomplexobj(vhat) else vhat, dtype=np.float64)
+        ih = np.ascontiguousarray(np.stack([ihat.real, ihat.imag], -1) if np.iscomplexobj(ihat) else ihat, dtype=np.float64)
+        hf.c.n_scen = vh.shape[0]
+        self._check(lib().okr_reduce_ops(self._h, C.byref(hf.c), _ptr(vh), _ptr(ih), C.byref(params)))
+        self.n_bus, self.n_scen = hf.c.n_bus, hf.c.n_scen
+
+    def power_flow(self, feeder):
+        hf = HostFeeder(feeder)
+        n, L = hf.c.n_bus, hf.c.n_scen
+        v = np.zeros((L, n, 3, 2))
+        i = np.zeros((L, n, 3, 2))
+        sw = C.c_int32()
+        self._check(lib().okr_power_flow(self._h, C.byref(hf.c), _ptr(v), _ptr(i), C.byref(sw)))
+        return v[..., 0] + 1j * v[..., 1], i[..., 0] + 1j * i[..., 1], int(sw.value)
+
+    # ---- results
+    def summary(self) -> dict:
+        s = Summary()
+        self._check(lib().okr_get_summary(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in Summary._fields_}
+
+    def decisions(self) -> dict:
+        t = self.summary()["n_iter"]
+        cap = max(t, 1)
+        s = np.zeros(cap, np.int32)
+        r = np.zeros(cap, np.int32)
+        sm = np.zeros(cap)
+        me = np.zeros(cap)
+        gap = np.zeros(cap)
+        nc = np.zeros(cap, np.int32)
+        self._check(lib().okr_get_decisions(self._h, cap, _ptr(s), _ptr(r), _ptr(sm), _ptr(me), _ptr(gap), _ptr(nc)))
+        return dict(s=s[:t], r=r[:t], score=sm[:t], maxerr=me[:t], gap=gap[:t], ncand=nc[:t])
+
+    def assignment(self) -> np.ndarray:
+        out = np.zeros(self.n_bus, np.int32)
+        self._check(lib().okr_get_assignment(self._h, _ptr(out)))
+        return out
+
+    def voltages(self):
+        v = np.zeros((self.n_scen, self.n_bus, 3, 2))
+        w = np.zeros((self.n_scen, self.n_bus, 3, 2))
+        self._check(lib().okr_get_voltages(self._h, _ptr(v), _ptr(w)))
+        return v[..., 0] + 1j * v[..., 1], w[..., 0] + 1j * w[..., 1]
+
+    def recorded(self, it: int) -> dict:
+        cap = 2 * self.n_bus
+        s = np.zeros(cap, np.int32)
+        r = np.zeros(cap, np.int32)
+        sc = np.zeros(cap)
+        cnt = C.c_int32()
+        self._check(lib().okr_get_recorded(self._h, int(it), cap, _ptr(s), _ptr(r), _ptr(sc), C.byref(cnt)))
+        c = min(cnt.value, cap)
+        return dict(s=s[:c], r=r[:c], score=sc[:c])

@@ -1,0 +1,674 @@
+// okr_capi.cu -- the C ABI declared in include/okron.h: context, device
+// workspace, and the host orchestration of the per-feeder setup kernels and the
+// per-iteration search kernels (one CUDA graph per iteration, replayed).
+#include "okron.h"
+#include "okr_internal.cuh"
+#include "okr_kernels.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace okr;
+
+namespace {
+
+constexpr int kIterBatch = 32;          // graph replays between host checks of the stop flag
+constexpr double kPfTol = 1e-13;
+constexpr int kPfMaxIter = 200;
+
+}  // namespace
+
+struct okr_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+
+    // capacity of the workspace
+    int cap_n = 0, cap_L = 0, cap_rec = 0;
+    std::vector<void *> allocs;
+
+    // inputs copied from the host
+    int *parent_in = nullptr;
+    uint8_t *ph_in = nullptr;
+    double *z_in = nullptr, *s_in = nullptr, *vh_in = nullptr, *ih_in = nullptr;
+    // topology scratch
+    int *dep = nullptr, *anc = nullptr, *anc2 = nullptr, *d2 = nullptr, *size = nullptr, *ccount = nullptr;
+    int *coff_c = nullptr, *child_c = nullptr;
+    uint16_t *rmq = nullptr;
+    double2 *J = nullptr;
+    int *pf_iters = nullptr, *err_dev = nullptr;
+    // outputs
+    int *super_out = nullptr;
+    double *vred_out = nullptr, *vhat_out = nullptr;
+
+    Topo T{};
+    State S{};
+    Search X{};
+    Ctrl *C = nullptr;
+    Ctrl *C_host = nullptr;     // pinned
+
+    // cached graph of one iteration
+    cudaGraphExec_t graph = nullptr;
+    int graph_n = -1, graph_L = -1;
+
+    // counters of the last call
+    int64_t launches = 0;
+    double sweep_ms = 0.0;
+    int64_t sweep_launches = 0;
+
+    // last result
+    bool have_result = false;
+    int n = 0, L = 0, rec_iters = 0, pf_sweeps = 0;
+    Ctrl last{};
+};
+
+namespace {
+
+okr_status fail(okr_ctx *c, okr_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? OKR_ENOMEM : OKR_ECUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+    } while (0)
+
+void free_all(okr_ctx *ctx) {
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->graph_n = ctx->graph_L = -1;
+    for (void *p : ctx->allocs) cudaFree(p);
+    ctx->allocs.clear();
+    ctx->cap_n = ctx->cap_L = ctx->cap_rec = 0;
+}
+
+template <typename T>
+cudaError_t dalloc(okr_ctx *ctx, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) { ctx->allocs.push_back(q); *p = (T *)q; }
+    return e;
+}
+
+int log2_ceil(int n) {
+    int j = 0;
+    while ((1 << j) < n) ++j;
+    return j;
+}
+
+// Largest number of chunks one iteration can need: every candidate covers at
+// most n_bus positions, and there are at most 2 n_bus candidate slots.
+size_t max_chunks_for(int n) { return (size_t)2 * n * (size_t)((n + kChunk - 1) / kChunk); }
+
+okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
+    if (n <= ctx->cap_n && L <= ctx->cap_L && rec <= ctx->cap_rec) return OKR_OK;
+    free_all(ctx);
+    const size_t N = n, NL3 = (size_t)3 * L * n;
+    const int LOG = log2_ceil(n) + 1;
+    const size_t MC = max_chunks_for(n);
+    CK(dalloc(ctx, &ctx->parent_in, N));
+    CK(dalloc(ctx, &ctx->ph_in, N));
+    CK(dalloc(ctx, &ctx->z_in, N * 18));
+    CK(dalloc(ctx, &ctx->s_in, (size_t)L * N * 6));
+    CK(dalloc(ctx, &ctx->vh_in, (size_t)L * N * 6));
+    CK(dalloc(ctx, &ctx->ih_in, (size_t)L * N * 6));
+    CK(dalloc(ctx, &ctx->dep, N));
+    CK(dalloc(ctx, &ctx->anc, N));
+    CK(dalloc(ctx, &ctx->anc2, N));
+    CK(dalloc(ctx, &ctx->d2, N));
+    CK(dalloc(ctx, &ctx->size, N));
+    CK(dalloc(ctx, &ctx->ccount, N + 2));
+    CK(dalloc(ctx, &ctx->coff_c, N + 1));
+    CK(dalloc(ctx, &ctx->child_c, N));
+    CK(dalloc(ctx, &ctx->rmq, (size_t)LOG * N));
+    CK(dalloc(ctx, &ctx->J, NL3));
+    CK(dalloc(ctx, &ctx->pf_iters, (size_t)L));
+    CK(dalloc(ctx, &ctx->err_dev, 1));
+    CK(dalloc(ctx, &ctx->super_out, N));
+    CK(dalloc(ctx, &ctx->vred_out, (size_t)L * N * 6));
+    CK(dalloc(ctx, &ctx->vhat_out, (size_t)L * N * 6));
+
+    Topo &T = ctx->T;
+    CK(dalloc(ctx, &T.maxd, 1));
+    CK(dalloc(ctx, &T.parent, N));
+    CK(dalloc(ctx, &T.orig, N));
+    CK(dalloc(ctx, &T.pre, N));
+    CK(dalloc(ctx, &T.sz, N));
+    CK(dalloc(ctx, &T.depth, N));
+    CK(dalloc(ctx, &T.child_off, N + 1));
+    CK(dalloc(ctx, &T.child, N));
+    CK(dalloc(ctx, &T.level_off, N + 2));
+    CK(dalloc(ctx, &T.level_bus, N));
+    CK(dalloc(ctx, &T.ph, N));
+    CK(dalloc(ctx, &T.lca, N * N));
+    CK(dalloc(ctx, &T.zl, N * 9));
+    CK(dalloc(ctx, &T.yl, N * 9));
+    CK(dalloc(ctx, &T.zc, N * 9));
+    CK(dalloc(ctx, &T.vhat, NL3));
+    CK(dalloc(ctx, &T.ihat, NL3));
+    CK(dalloc(ctx, &T.amag, NL3));
+    CK(dalloc(ctx, &T.vslack, 3));
+
+    State &S = ctx->S;
+    CK(dalloc(ctx, &S.label, N));
+    CK(dalloc(ctx, &S.top, N));
+    CK(dalloc(ctx, &S.vcur, NL3));
+    CK(dalloc(ctx, &S.icur, NL3));
+    CK(dalloc(ctx, &S.hi, NL3));
+    CK(dalloc(ctx, &S.lo, NL3));
+    CK(dalloc(ctx, &S.mice, (size_t)L * N));
+
+    Search &X = ctx->X;
+    CK(dalloc(ctx, &X.cand, 2 * N));
+    CK(dalloc(ctx, &X.nchunk, 2 * N));
+    CK(dalloc(ctx, &X.base, 2 * N + 1));
+    CK(dalloc(ctx, &X.chunk_cand, MC));
+    CK(dalloc(ctx, &X.partial, MC));
+    CK(dalloc(ctx, &X.score, 2 * N));
+    CK(dalloc(ctx, &X.feas, 2 * N));
+    X.max_chunks = (int)MC;
+    CK(dalloc(ctx, &X.dec_s, N));
+    CK(dalloc(ctx, &X.dec_r, N));
+    CK(dalloc(ctx, &X.dec_score, N));
+    CK(dalloc(ctx, &X.dec_maxerr, N));
+    CK(dalloc(ctx, &X.dec_gap, N));
+    CK(dalloc(ctx, &X.dec_ncand, N));
+    const size_t R = rec > 0 ? (size_t)rec : 1;
+    CK(dalloc(ctx, &X.rec_s, R * 2 * N));
+    CK(dalloc(ctx, &X.rec_r, R * 2 * N));
+    CK(dalloc(ctx, &X.rec_score, R * 2 * N));
+    CK(dalloc(ctx, &X.rec_count, R));
+    CK(dalloc(ctx, &ctx->C, 1));
+
+    ctx->cap_n = n;
+    ctx->cap_L = L;
+    ctx->cap_rec = rec;
+    return OKR_OK;
+}
+
+}  // namespace
+
+namespace {
+
+int blocks_for(size_t work, int threads, int cap) {
+    size_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > (size_t)cap) b = cap;
+    return (int)b;
+}
+
+okr_status check_feeder_shape(okr_ctx *ctx, const okr_feeder *f) {
+    if (!f) return fail(ctx, OKR_EINVAL, "feeder is NULL");
+    if (f->n_bus < 2 || f->n_bus > kMaxBus) return fail(ctx, OKR_EINVAL, "n_bus=%d outside [2, %d]", f->n_bus, kMaxBus);
+    if (f->n_scen < 1 || f->n_scen > kMaxScen) return fail(ctx, OKR_EINVAL, "n_scen=%d outside [1, %d]", f->n_scen, kMaxScen);
+    if (!f->parent || !f->phases || !f->z_line) return fail(ctx, OKR_EINVAL, "feeder array is NULL");
+    return OKR_OK;
+}
+
+okr_status check_params(okr_ctx *ctx, const okr_params *p) {
+    if (!p) return fail(ctx, OKR_EINVAL, "params is NULL");
+    if (!(p->margin > 0.0) || !std::isfinite(p->margin)) return fail(ctx, OKR_EINVAL, "margin must be positive");
+    if (!(p->tie_tol >= 0.0) || !std::isfinite(p->tie_tol)) return fail(ctx, OKR_EINVAL, "tie_tol must be >= 0");
+    if (p->max_merges < 0 && !(p->target_reduction >= 0.0 && p->target_reduction <= 1.0))
+        return fail(ctx, OKR_EINVAL, "target_reduction outside [0, 1]");
+    if (p->objective != 0) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
+    if (p->precision != 0) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
+    if (p->record_iters < 0) return fail(ctx, OKR_EINVAL, "record_iters < 0");
+    if (p->reserved != 0) return fail(ctx, OKR_EINVAL, "reserved must be 0");
+    return OKR_OK;
+}
+
+int merges_for(int n, const okr_params *p) {
+    long m;
+    if (p->max_merges >= 0) m = p->max_merges;
+    else m = (long)std::ceil(p->target_reduction * n - 1e-12);
+    if (m > n - 1) m = n - 1;
+    if (m < 0) m = 0;
+    return (int)m;
+}
+
+okr_status read_setup_errors(okr_ctx *ctx);
+
+// Per-feeder setup on the device: topology, LCA table, lines, path impedances.
+okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
+    cudaStream_t st = ctx->stream;
+    Topo &T = ctx->T;
+    T.n = n;
+    T.L = L;
+    double2 vs[3];
+    for (int p = 0; p < 3; ++p) vs[p] = make_double2(vslack[2 * p], vslack[2 * p + 1]);
+    CK(cudaMemcpyAsync(T.vslack, vs, sizeof vs, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
+    k_topology<<<1, 1024, 0, st>>>(n, ctx->parent_in, ctx->ph_in, T, ctx->dep, ctx->anc, ctx->anc2, ctx->d2,
+                                   ctx->size, ctx->ccount, ctx->coff_c, ctx->child_c, ctx->err_dev);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    // the later setup kernels index with the renumbering: stop here on an invalid tree
+    okr_status s = read_setup_errors(ctx);
+    if (s != OKR_OK) return s;
+    k_child_offsets<<<1, 1024, 0, st>>>(n, T, ctx->coff_c, ctx->child_c);
+    const int LOG = log2_ceil(n) + 1;
+    for (int j = 0; j < LOG; ++j) k_rmq_level<<<blocks_for(n, 256, 1 << 20), 256, 0, st>>>(n, j, T.depth, ctx->rmq);
+    k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, T.parent, T.sz, T.depth, ctx->rmq, T.lca);
+    k_lines<<<1, 1024, 0, st>>>(n, T, ctx->z_in, ctx->err_dev);
+    ctx->launches += 3 + LOG;
+    CK(cudaGetLastError());
+    return read_setup_errors(ctx);
+}
+
+okr_status read_setup_errors(okr_ctx *ctx) {
+    int e = 0;
+    CK(cudaMemcpyAsync(ctx->C_host, ctx->err_dev, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    std::memcpy(&e, ctx->C_host, sizeof e);
+    if (e == 1) return fail(ctx, OKR_EINVAL, "invalid feeder: parent[0] must be -1, parent[i] < i, phases non-empty and within the parent's");
+    if (e == 2) return fail(ctx, OKR_ESINGULAR, "singular line impedance block");
+    if (e == 3) return fail(ctx, OKR_EPF, "load flow did not converge in %d sweeps", kPfMaxIter);
+    if (e) return fail(ctx, OKR_EINTERNAL, "device error %d", e);
+    return OKR_OK;
+}
+
+okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
+    cudaStream_t st = ctx->stream;
+    Topo &T = ctx->T;
+    k_power_flow<<<L, 1024, 0, st>>>(n, L, T, ctx->s_in, kPfTol, kPfMaxIter, ctx->J, ctx->pf_iters, ctx->err_dev);
+    k_line_currents<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
+    k_injections<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
+    ctx->launches += 3;
+    CK(cudaGetLastError());
+    return OKR_OK;
+}
+
+constexpr int kKernelsPerIter = 5;
+
+// The five kernels of one iteration; with events, the sweep is bracketed.
+void launch_iteration(okr_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->T.n;
+    const int nb = blocks_for(n, 256, ctx->num_sms * 8);
+    k_setup<<<nb, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
+    k_scan<<<1, 1024, 0, st>>>(ctx->T, ctx->X, ctx->C);
+    if (e0) cudaEventRecord(e0, st);
+    k_sweep<<<ctx->num_sms * 8, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
+    if (e1) cudaEventRecord(e1, st);
+    k_select<<<1, 1024, 0, st>>>(ctx->T, ctx->X, ctx->C);
+    k_commit<<<nb, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
+}
+
+okr_status build_graph(okr_ctx *ctx) {
+    const int n = ctx->T.n, L = ctx->T.L;
+    if (ctx->graph && ctx->graph_n == n && ctx->graph_L == L) return OKR_OK;
+    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    cudaStream_t st = ctx->stream;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    launch_iteration(ctx, nullptr, nullptr);
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (e != cudaSuccess) return fail(ctx, OKR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&ctx->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { ctx->graph = nullptr; return fail(ctx, OKR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
+    ctx->graph_n = n;
+    ctx->graph_L = L;
+    return OKR_OK;
+}
+
+// Initial state, then iterations until the stop flag is raised.  Normal mode
+// replays the captured iteration graph in batches and reads the stop flag after
+// each batch; profile mode launches the kernels directly with an event pair
+// around every sweep.
+okr_status run_search(okr_ctx *ctx, const okr_params *p) {
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->T.n, L = ctx->T.L;
+    Search &X = ctx->X;
+    X.rec_iters = p->record_iters;
+    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->S);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    const int mm = merges_for(n, p);
+    Ctrl c{};
+    c.max_merges = mm;
+    c.done = (mm == 0);
+    c.margin = p->margin;
+    c.tau = p->tie_tol;
+    c.profile = p->profile ? 1 : 0;
+    CK(cudaMemcpyAsync(ctx->C, &c, sizeof c, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
+    if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
+    // the graph bakes in the Search struct (rec_iters): rebuild when it changes
+    if (ctx->graph && ctx->rec_iters != p->record_iters) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->rec_iters = p->record_iters;
+    ctx->sweep_ms = 0.0;
+    ctx->sweep_launches = 0;
+    std::vector<cudaEvent_t> ev;
+    if (p->profile) {
+        ev.resize(2 * kIterBatch);
+        for (auto &e : ev) CK(cudaEventCreate(&e));
+    } else {
+        okr_status s = build_graph(ctx);
+        if (s != OKR_OK) return s;
+    }
+    int launched = 0, swept = 0;
+    okr_status status = OKR_OK;
+    while (true) {
+        int batch = mm + 1 - launched;          // one extra pass observes the stop
+        if (batch > kIterBatch) batch = kIterBatch;
+        if (batch < 1) batch = 1;
+        for (int b = 0; b < batch; ++b) {
+            if (p->profile) launch_iteration(ctx, ev[2 * b], ev[2 * b + 1]);
+            else if (cudaGraphLaunch(ctx->graph, st) != cudaSuccess) { status = fail(ctx, OKR_ECUDA, "graph launch failed"); break; }
+        }
+        if (status != OKR_OK) break;
+        ctx->launches += (int64_t)batch * kKernelsPerIter;
+        launched += batch;
+        if (cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) { status = fail(ctx, OKR_ECUDA, "%s", cudaGetErrorString(cudaGetLastError())); break; }
+        if (p->profile) {
+            // sweeps that found work come first in the batch
+            const int ran = ctx->C_host->sweeps_run - swept;
+            for (int b = 0; b < ran && b < batch; ++b) {
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, ev[2 * b], ev[2 * b + 1]);
+                ctx->sweep_ms += ms;
+            }
+            ctx->sweep_launches += ran;
+            swept = ctx->C_host->sweeps_run;
+        }
+        if (ctx->C_host->done || ctx->C_host->err) break;
+        if (launched > mm + 1) { status = fail(ctx, OKR_EINTERNAL, "search did not stop after %d iterations", launched); break; }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (status != OKR_OK) return status;
+    k_final_maxerr<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, X, ctx->C);
+    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, ctx->vred_out,
+                                                                                ctx->super_out, ctx->vhat_out);
+    ctx->launches += 2;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->last = *ctx->C_host;
+    if (ctx->last.err == 4) return fail(ctx, OKR_EINTERNAL, "chunk buffer too small");
+    if (ctx->last.err) return fail(ctx, OKR_EINTERNAL, "device error %d", ctx->last.err);
+    return OKR_OK;
+}
+
+enum class Src { Host, Device, Ops };
+
+okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, const double *ihat,
+                       const okr_params *p, Src src) {
+    if (!ctx) return OKR_EINVAL;
+    ctx->have_result = false;
+    ctx->launches = 0;
+    okr_status s = check_feeder_shape(ctx, f);
+    if (s != OKR_OK) return s;
+    s = check_params(ctx, p);
+    if (s != OKR_OK) return s;
+    if (src != Src::Ops && !f->s_load) return fail(ctx, OKR_EINVAL, "s_load is NULL");
+    if (src == Src::Ops && (!vhat || !ihat)) return fail(ctx, OKR_EINVAL, "vhat/ihat is NULL");
+    const int n = f->n_bus, L = f->n_scen;
+    CK(cudaSetDevice(ctx->device));
+    s = ensure_workspace(ctx, n, L, p->record_iters);
+    if (s != OKR_OK) return s;
+    cudaStream_t st = ctx->stream;
+    const cudaMemcpyKind kind = (src == Src::Device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(ctx->parent_in, f->parent, sizeof(int) * n, kind, st));
+    CK(cudaMemcpyAsync(ctx->ph_in, f->phases, n, kind, st));
+    CK(cudaMemcpyAsync(ctx->z_in, f->z_line, sizeof(double) * 18 * n, kind, st));
+    if (src == Src::Ops) {
+        CK(cudaMemcpyAsync(ctx->vh_in, vhat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->ih_in, ihat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(ctx->s_in, f->s_load, sizeof(double) * 6 * L * n, kind, st));
+    }
+    s = build_topology(ctx, n, L, &f->v_slack[0][0]);
+    if (s != OKR_OK) return s;
+    if (src == Src::Ops) {
+        k_import_ops<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->vh_in, ctx->ih_in);
+        ctx->launches += 1;
+        CK(cudaGetLastError());
+        ctx->pf_sweeps = 0;
+    } else {
+        s = run_power_flow(ctx, n, L);
+        if (s != OKR_OK) return s;
+    }
+    s = read_setup_errors(ctx);
+    if (s != OKR_OK) return s;
+    if (src != Src::Ops) {
+        int it[kMaxScen];
+        CK(cudaMemcpy(it, ctx->pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
+        int w = 0;
+        for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
+        ctx->pf_sweeps = w;
+    }
+    s = run_search(ctx, p);
+    if (s != OKR_OK) return s;
+    ctx->n = n;
+    ctx->L = L;
+    ctx->have_result = true;
+    return OKR_OK;
+}
+
+}  // namespace
+
+// ======================================================================= C ABI
+extern "C" {
+
+void okr_default_params(okr_params *p) {
+    if (!p) return;
+    p->margin = 0.005;
+    p->target_reduction = 1.0;
+    p->tie_tol = 1e-9;
+    p->objective = 0;
+    p->precision = 0;
+    p->record_iters = 0;
+    p->max_merges = -1;
+    p->profile = 0;
+    p->reserved = 0;
+    p->max_spins = 0;
+}
+
+const char *okr_status_str(okr_status s) {
+    switch (s) {
+    case OKR_OK: return "ok";
+    case OKR_EINVAL: return "invalid argument";
+    case OKR_ENOMEM: return "out of memory";
+    case OKR_ECUDA: return "CUDA error";
+    case OKR_EPF: return "load flow did not converge";
+    case OKR_ETIMEOUT: return "device wait timed out";
+    case OKR_ENOTREADY: return "no result";
+    case OKR_ESINGULAR: return "singular line impedance";
+    case OKR_EINTERNAL: return "internal error";
+    }
+    return "unknown status";
+}
+
+const char *okr_last_error(const okr_ctx *ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+okr_status okr_create(okr_ctx **out, int device, void *stream) {
+    if (!out) return OKR_EINVAL;
+    *out = nullptr;
+    okr_ctx *ctx = new (std::nothrow) okr_ctx();
+    if (!ctx) return OKR_ENOMEM;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        delete ctx;
+        return e != cudaSuccess ? OKR_ECUDA : OKR_EINVAL;
+    }
+    ctx->device = device;
+    if ((e = cudaSetDevice(device)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) {
+        delete ctx;
+        return OKR_ECUDA;
+    }
+    if (stream) {
+        ctx->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return OKR_ECUDA; }
+        ctx->own_stream = true;
+    }
+    if (cudaMallocHost((void **)&ctx->C_host, sizeof(Ctrl)) != cudaSuccess) {
+        if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+        delete ctx;
+        return OKR_ENOMEM;
+    }
+    *out = ctx;
+    return OKR_OK;
+}
+
+okr_status okr_destroy(okr_ctx *ctx) {
+    if (!ctx) return OKR_EINVAL;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    if (ctx->C_host) cudaFreeHost(ctx->C_host);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return OKR_OK;
+}
+
+okr_status okr_reduce(okr_ctx *ctx, const okr_feeder *f, const okr_params *p) {
+    return reduce_impl(ctx, f, nullptr, nullptr, p, Src::Host);
+}
+
+okr_status okr_reduce_device(okr_ctx *ctx, const okr_feeder *f, const okr_params *p) {
+    return reduce_impl(ctx, f, nullptr, nullptr, p, Src::Device);
+}
+
+okr_status okr_reduce_ops(okr_ctx *ctx, const okr_feeder *f, const double *vhat, const double *ihat,
+                          const okr_params *p) {
+    return reduce_impl(ctx, f, vhat, ihat, p, Src::Ops);
+}
+
+okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, double *ihat_out, int32_t *sweeps) {
+    if (!ctx) return OKR_EINVAL;
+    ctx->have_result = false;
+    okr_status s = check_feeder_shape(ctx, f);
+    if (s != OKR_OK) return s;
+    if (!f->s_load || !vhat_out) return fail(ctx, OKR_EINVAL, "s_load or vhat_out is NULL");
+    const int n = f->n_bus, L = f->n_scen;
+    CK(cudaSetDevice(ctx->device));
+    s = ensure_workspace(ctx, n, L, ctx->cap_rec);
+    if (s != OKR_OK) return s;
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->parent_in, f->parent, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->ph_in, f->phases, n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->z_in, f->z_line, sizeof(double) * 18 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->s_in, f->s_load, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+    s = build_topology(ctx, n, L, &f->v_slack[0][0]);
+    if (s != OKR_OK) return s;
+    s = run_power_flow(ctx, n, L);
+    if (s != OKR_OK) return s;
+    s = read_setup_errors(ctx);
+    if (s != OKR_OK) return s;
+    // export: reuse k_export with the initial state (each bus its own super-node)
+    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->S);
+    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, nullptr, nullptr,
+                                                                                ctx->vhat_out);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(vhat_out, ctx->vhat_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
+    if (ihat_out) {
+        // S.icur == Ihat after the initial state; export it through vred's slot
+        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, State{ctx->S.label, ctx->S.top, ctx->S.icur, ctx->S.icur, ctx->S.hi, ctx->S.lo, ctx->S.mice},
+                                                                                    ctx->vred_out, nullptr, nullptr);
+        CK(cudaMemcpyAsync(ihat_out, ctx->vred_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (sweeps) {
+        int it[kMaxScen];
+        CK(cudaMemcpy(it, ctx->pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
+        int w = 0;
+        for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
+        *sweeps = w;
+    }
+    return OKR_OK;
+}
+
+okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
+    if (!ctx || !out) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    const Ctrl &c = ctx->last;
+    out->n_bus = ctx->n;
+    out->n_scen = ctx->L;
+    out->n_iter = c.t;
+    out->stop_reason = c.stop_reason;
+    out->pf_sweeps = ctx->pf_sweeps;
+    out->n_kept = ctx->n - c.t;
+    out->candidates = c.candidates;
+    out->smice = c.s_cur;
+    double me = 0.0;
+    if (c.t > 0) cudaMemcpy(&me, ctx->X.dec_maxerr + (c.t - 1), sizeof me, cudaMemcpyDeviceToHost);
+    out->max_error = me;
+    out->launches = ctx->launches;
+    out->sweep_launches = ctx->sweep_launches;
+    out->sweep_ms = ctx->sweep_ms;
+    out->sweep_flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
+    return OKR_OK;
+}
+
+okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_t *r, double *smice,
+                             double *max_error, double *gap, int32_t *ncand) {
+    if (!ctx || cap < 0) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    const int t = ctx->last.t < cap ? ctx->last.t : cap;
+    if (t == 0) return OKR_OK;
+    const Search &X = ctx->X;
+    if (s && cudaMemcpy(s, X.dec_s, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (r && cudaMemcpy(r, X.dec_r, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (smice && cudaMemcpy(smice, X.dec_score, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (max_error && cudaMemcpy(max_error, X.dec_maxerr, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (gap && cudaMemcpy(gap, X.dec_gap, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (ncand && cudaMemcpy(ncand, X.dec_ncand, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    return OKR_OK;
+}
+
+okr_status okr_get_assignment(const okr_ctx *ctx, int32_t *super_of) {
+    if (!ctx || !super_of) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    if (cudaMemcpy(super_of, ctx->super_out, sizeof(int) * ctx->n, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    return OKR_OK;
+}
+
+okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred) {
+    if (!ctx) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    const size_t bytes = sizeof(double) * 6 * ctx->L * ctx->n;
+    if (vhat && cudaMemcpy(vhat, ctx->vhat_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (vred && cudaMemcpy(vred, ctx->vred_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    return OKR_OK;
+}
+
+okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32_t *s, int32_t *r, double *smice,
+                            int32_t *count) {
+    if (!ctx || !count || cap < 0) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    if (iter < 0 || iter >= ctx->rec_iters) return OKR_EINVAL;
+    int c = 0;
+    if (cudaMemcpy(&c, ctx->X.rec_count + iter, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    *count = c;
+    const int k = c < cap ? c : cap;
+    const size_t off = (size_t)iter * 2 * ctx->n;
+    if (k > 0) {
+        if (s && cudaMemcpy(s, ctx->X.rec_s + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (r && cudaMemcpy(r, ctx->X.rec_r + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (smice && cudaMemcpy(smice, ctx->X.rec_score + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    }
+    return OKR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,33 @@
+// okr_kernels.cuh -- kernel declarations shared between translation units.
+#pragma once
+
+#include "okr_internal.cuh"
+
+namespace okr {
+
+// okr_setup.cu
+__global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict__ parent_in, const uint8_t *__restrict__ ph_in,
+                           Topo T, int *dep, int *anc, int *anc2, int *d2, int *size, int *ccount,
+                           int *coff_c, int *child_c, int *err);
+__global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c);
+__global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_t *st);
+__global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
+                           const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca);
+__global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__restrict__ z_in, int *err);
+__global__ void __launch_bounds__(1024) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol, int max_iter,
+                             double2 *J, int *iters, int *err);
+__global__ void k_line_currents(int n, int L, Topo T, double2 *J);
+__global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J);
+__global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);
+__global__ void k_state_init(int n, int L, Topo T, State S);
+
+// okr_search.cu
+__global__ void k_setup(Topo T, State S, Search X, Ctrl *C);
+__global__ void __launch_bounds__(1024) k_scan(Topo T, Search X, Ctrl *C);
+__global__ void __launch_bounds__(256) k_sweep(Topo T, State S, Search X, Ctrl *C);
+__global__ void __launch_bounds__(1024) k_select(Topo T, Search X, Ctrl *C);
+__global__ void k_commit(Topo T, State S, Search X, Ctrl *C);
+__global__ void k_final_maxerr(Topo T, State S, Search X, const Ctrl *C);
+__global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);
+
+}  // namespace okr

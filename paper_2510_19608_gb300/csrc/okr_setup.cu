@@ -1,0 +1,402 @@
+// okr_setup.cu -- once-per-feeder work on the device: validation, preorder
+// renumbering, lowest-common-ancestor table, path impedances, the
+// backward/forward-sweep load flow that produces the scenario library
+// (Sec. III: operating points of the full network), the injections
+// Ihat = Y Vhat (Sec. II-A), and the initial reduction state of Algorithm 1
+// (every bus its own super-node, I = Ihat).
+#include "okr_internal.cuh"
+#include "okr_kernels.cuh"
+
+namespace okr {
+
+// ---------------------------------------------------------------- small dense helpers
+// Inverse of the sub-block of a 3x3 complex matrix on phase mask m (Gauss-Jordan
+// with partial pivoting); entries outside the sub-block are zero.  Returns false
+// if the sub-block is singular.
+__device__ bool inv3_sub(const double2 *a, unsigned m, double2 *out) {
+    int idx[3], k = 0;
+    for (int p = 0; p < 3; ++p)
+        if (m >> p & 1u) idx[k++] = p;
+    double2 w[3][6];
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < 2 * k; ++j)
+            w[i][j] = (j < k) ? a[idx[i] * 3 + idx[j]] : make_double2(j - k == i ? 1.0 : 0.0, 0.0);
+    for (int c = 0; c < k; ++c) {
+        int piv = c;
+        double best = cmag(w[c][c]);
+        for (int i = c + 1; i < k; ++i) {
+            double v = cmag(w[i][c]);
+            if (v > best) { best = v; piv = i; }
+        }
+        if (best == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j < 2 * k; ++j) { double2 t = w[c][j]; w[c][j] = w[piv][j]; w[piv][j] = t; }
+        double2 d = w[c][c];
+        for (int j = 0; j < 2 * k; ++j) w[c][j] = cdiv(w[c][j], d);
+        for (int i = 0; i < k; ++i) {
+            if (i == c) continue;
+            double2 f = w[i][c];
+            for (int j = 0; j < 2 * k; ++j) w[i][j] = csub(w[i][j], cmul(f, w[c][j]));
+        }
+    }
+    for (int q = 0; q < 9; ++q) out[q] = make_double2(0.0, 0.0);
+    for (int i = 0; i < k; ++i)
+        for (int j = 0; j < k; ++j) out[idx[i] * 3 + idx[j]] = w[i][k + j];
+    return true;
+}
+
+__device__ __forceinline__ void block_barrier() { __syncthreads(); }
+
+// ---------------------------------------------------------------- topology (one CTA)
+// Input in caller numbering.  Scratch arrays (caller numbering): dep, anc/anc2,
+// d2, size, ccount.  Writes the Topo arrays in preorder numbering.
+__global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict__ parent_in, const uint8_t *__restrict__ ph_in,
+                           Topo T, int *dep, int *anc, int *anc2, int *d2, int *size, int *ccount,
+                           int *coff_c, int *child_c, int *err) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_bad, s_maxd;
+    if (tid == 0) { s_bad = 0; s_maxd = 0; }
+    block_barrier();
+    // 1. validation
+    for (int i = tid; i < n; i += nt) {
+        int p = parent_in[i];
+        unsigned m = ph_in[i];
+        bool ok = (m != 0u) && (m <= 7u);
+        if (i == 0) ok = ok && (p == -1);
+        else ok = ok && (p >= 0) && (p < i) && ((m & ph_in[p]) == m);
+        if (!ok) atomicExch(&s_bad, 1);
+    }
+    block_barrier();
+    if (s_bad) { if (tid == 0) atomicExch(err, 1); return; }
+    // 2. depth by pointer jumping (caller numbering)
+    for (int i = tid; i < n; i += nt) { anc[i] = (i == 0) ? 0 : parent_in[i]; dep[i] = (i == 0) ? 0 : 1; }
+    block_barrier();
+    int *a0 = anc, *a1 = anc2, *d0 = dep, *d1 = d2;
+    for (int step = 1; step < 2 * n; step <<= 1) {
+        for (int i = tid; i < n; i += nt) { d1[i] = d0[i] + d0[a0[i]]; a1[i] = a0[a0[i]]; }
+        block_barrier();
+        int *t = a0; a0 = a1; a1 = t;
+        t = d0; d0 = d1; d1 = t;
+    }
+    if (d0 != dep) {
+        for (int i = tid; i < n; i += nt) dep[i] = d0[i];
+        block_barrier();
+    }
+    for (int i = tid; i < n; i += nt) atomicMax(&s_maxd, dep[i]);
+    block_barrier();
+    const int maxd = s_maxd;
+    // 3. level lists (caller ids, stable order inside a level is irrelevant)
+    for (int i = tid; i < maxd + 2; i += nt) T.level_off[i] = 0;
+    for (int i = tid; i < n; i += nt) { size[i] = 1; ccount[i] = 0; }
+    block_barrier();
+    for (int i = tid; i < n; i += nt) atomicAdd(&T.level_off[dep[i] + 1], 1);
+    block_barrier();
+    if (tid == 0) {
+        for (int d = 0; d <= maxd; ++d) T.level_off[d + 1] += T.level_off[d];
+    }
+    block_barrier();
+    // children counts
+    for (int i = tid + 1; i < n; i += nt) atomicAdd(&ccount[parent_in[i]], 1);
+    block_barrier();
+    // 4. subtree sizes, deepest level first (integer atomics: order-independent)
+    for (int d = maxd; d >= 1; --d) {
+        for (int i = tid; i < n; i += nt)
+            if (dep[i] == d) atomicAdd(&size[parent_in[i]], size[i]);
+        block_barrier();
+    }
+    // 5. children CSR in caller numbering, each list sorted by caller id
+    if (tid == 0) {
+        int acc = 0;
+        for (int i = 0; i < n; ++i) { coff_c[i] = acc; acc += ccount[i]; }
+        coff_c[n] = acc;
+    }
+    block_barrier();
+    for (int i = tid; i < n; i += nt) ccount[i] = 0;
+    block_barrier();
+    for (int i = tid + 1; i < n; i += nt) {
+        int p = parent_in[i];
+        int slot = atomicAdd(&ccount[p], 1);
+        child_c[coff_c[p] + slot] = i;
+    }
+    block_barrier();
+    for (int p = tid; p < n; p += nt) {
+        int b = coff_c[p], e = coff_c[p + 1];
+        for (int x = b + 1; x < e; ++x) {           // insertion sort (degrees are small)
+            int v = child_c[x], y = x - 1;
+            while (y >= b && child_c[y] > v) { child_c[y + 1] = child_c[y]; --y; }
+            child_c[y + 1] = v;
+        }
+    }
+    block_barrier();
+    // 6. preorder positions, top-down
+    if (tid == 0) T.pre[0] = 0;
+    block_barrier();
+    for (int d = 0; d < maxd; ++d) {
+        for (int i = tid; i < n; i += nt) {
+            if (dep[i] != d) continue;
+            int pos = T.pre[i] + 1;
+            for (int x = coff_c[i]; x < coff_c[i + 1]; ++x) {
+                int c = child_c[x];
+                T.pre[c] = pos;
+                pos += size[c];
+            }
+        }
+        block_barrier();
+    }
+    // 7. preorder-indexed copies; child lists become preorder ids
+    for (int i = tid; i < n; i += nt) {
+        int v = T.pre[i];
+        T.orig[v] = i;
+        T.parent[v] = (i == 0) ? -1 : T.pre[parent_in[i]];
+        T.sz[v] = size[i];
+        T.depth[v] = dep[i];
+        T.ph[v] = ph_in[i];
+    }
+    block_barrier();
+    for (int x = tid; x < n - 1; x += nt) child_c[x] = T.pre[child_c[x]];
+    for (int i = tid; i < n; i += nt) ccount[i] = 0;
+    block_barrier();
+    for (int i = tid; i < n; i += nt) {
+        int d = dep[i];
+        int slot = atomicAdd(&ccount[d], 1);
+        T.level_bus[T.level_off[d] + slot] = T.pre[i];
+    }
+    if (tid == 0) *T.maxd = maxd;
+}
+
+// Children CSR indexed by preorder id (one CTA).  The children of preorder
+// node v are those of caller bus orig[v], already converted to preorder ids
+// and increasing.
+__global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c) {
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int v = 0; v < n; ++v) {
+            int i = T.orig[v];
+            T.child_off[v] = acc;
+            acc += coff_c[i + 1] - coff_c[i];
+        }
+        T.child_off[n] = acc;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < n; v += blockDim.x) {
+        int i = T.orig[v];
+        int b = coff_c[i], e = coff_c[i + 1];
+        int o = T.child_off[v];
+        for (int x = b; x < e; ++x) T.child[o + (x - b)] = child_c[x];
+    }
+}
+
+// Sparse table of the minimum-depth bus over preorder windows: st[j*n + v] is the
+// index of the shallowest bus in [v, v + 2^j).
+__global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_t *st) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n) return;
+    if (j == 0) { st[v] = (uint16_t)v; return; }
+    int h = 1 << (j - 1);
+    int a = st[(size_t)(j - 1) * n + v];
+    int w = v + h;
+    if (w + h <= n) {
+        int b = st[(size_t)(j - 1) * n + w];
+        if (depth[b] < depth[a]) a = b;
+    }
+    st[(size_t)j * n + v] = (uint16_t)a;
+}
+
+// LCA[u][v] for all pairs (preorder ids).  For u < v: if v lies in u's subtree
+// the answer is u; otherwise it is the parent of the shallowest bus in (u, v].
+__global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
+                           const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca) {
+    size_t tot = (size_t)n * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        int u = (int)(e / n), v = (int)(e % n);
+        int lo = u < v ? u : v, hi = u < v ? v : u;
+        int res;
+        if (lo == hi || hi < lo + sz[lo]) {
+            res = lo;
+        } else {
+            int len = hi - lo;                       // window (lo, hi]
+            int j = 31 - __clz(len);
+            int a = st[(size_t)j * n + lo + 1];
+            int b = st[(size_t)j * n + hi - (1 << j) + 1];
+            int m = depth[b] < depth[a] ? b : a;
+            res = parent[m];
+        }
+        lca[e] = (uint16_t)res;
+    }
+}
+
+// Line data in preorder: zl, yl (inverse on the bus phases); path impedance by
+// levels (parents first).  One CTA.
+__global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__restrict__ z_in, int *err) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int v = tid; v < n; v += nt) {
+        int i = T.orig[v];
+        double2 z[9];
+        for (int q = 0; q < 9; ++q) {
+            z[q] = (v == 0) ? make_double2(0.0, 0.0) : make_double2(z_in[((size_t)i * 9 + q) * 2], z_in[((size_t)i * 9 + q) * 2 + 1]);
+            T.zl[(size_t)v * 9 + q] = z[q];
+        }
+        double2 y[9];
+        if (v == 0) {
+            for (int q = 0; q < 9; ++q) y[q] = make_double2(0.0, 0.0);
+        } else if (!inv3_sub(z, T.ph[v], y)) {
+            atomicExch(err, 2);
+            for (int q = 0; q < 9; ++q) y[q] = make_double2(0.0, 0.0);
+        }
+        for (int q = 0; q < 9; ++q) T.yl[(size_t)v * 9 + q] = y[q];
+    }
+    __syncthreads();
+    for (int q = tid; q < 9; q += nt) T.zc[q] = make_double2(0.0, 0.0);
+    __syncthreads();
+    const int maxd = *T.maxd;
+    for (int d = 1; d <= maxd; ++d) {
+        for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+            int v = T.level_bus[x], p = T.parent[v];
+            for (int q = 0; q < 9; ++q) T.zc[(size_t)v * 9 + q] = cadd(T.zc[(size_t)p * 9 + q], T.zl[(size_t)v * 9 + q]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- load flow
+// Backward/forward sweep, one CTA per scenario.  Constant-power wye loads:
+// current drawn at (k,p) is conj(S/V).  Backward: J_k = load(k) + sum of the
+// children's J (children in preorder order).  Forward: V_k = V_parent - z_k J_k.
+// Stops when max |dV| < tol; otherwise reports failure.
+__global__ void __launch_bounds__(1024) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol, int max_iter,
+                             double2 *J, int *iters, int *err) {
+    const int l = blockIdx.x;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double2 *V = T.vhat;
+    double2 *Jl = J + (size_t)l * 3 * n;
+    __shared__ double s_red[32];
+    __shared__ int s_conv;
+    for (int v = tid; v < n; v += nt)
+        for (int p = 0; p < 3; ++p)
+            V[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
+    __syncthreads();
+    const int maxd = *T.maxd;
+    int it;
+    bool conv = false;
+    for (it = 1; it <= max_iter; ++it) {
+        for (int d = maxd; d >= 1; --d) {
+            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                int v = T.level_bus[x], i = T.orig[v];
+                for (int p = 0; p < 3; ++p) {
+                    double2 j = make_double2(0.0, 0.0);
+                    if (T.ph[v] >> p & 1u) {
+                        double2 s = make_double2(s_in[(((size_t)l * n + i) * 3 + p) * 2], s_in[(((size_t)l * n + i) * 3 + p) * 2 + 1]);
+                        j = cconj(cdiv(s, V[sidx(l, p, v, n)]));
+                    }
+                    for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Jl[(size_t)p * n + T.child[c]]);
+                    Jl[(size_t)p * n + v] = j;
+                }
+            }
+            __syncthreads();
+        }
+        double dmax = 0.0;
+        for (int d = 1; d <= maxd; ++d) {
+            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                int v = T.level_bus[x], par = T.parent[v];
+                for (int p = 0; p < 3; ++p) {
+                    if (!(T.ph[v] >> p & 1u)) continue;
+                    double2 drop = make_double2(0.0, 0.0);
+                    for (int q = 0; q < 3; ++q)
+                        if (T.ph[v] >> q & 1u) drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], Jl[(size_t)q * n + v]));
+                    double2 vn = csub(V[sidx(l, p, par, n)], drop);
+                    double dd = cmag(csub(vn, V[sidx(l, p, v, n)]));
+                    if (!isfinite(dd)) dd = INFINITY;          // a diverging sweep never converges
+                    dmax = fmax(dmax, dd);
+                    V[sidx(l, p, v, n)] = vn;
+                }
+            }
+            __syncthreads();
+        }
+        // block max of dmax
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if ((tid & 31) == 0) s_red[tid >> 5] = dmax;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, s_red[w]);
+            s_conv = (m < tol);
+        }
+        __syncthreads();
+        if (s_conv) { conv = true; break; }
+    }
+    if (tid == 0) {
+        iters[l] = conv ? it : -1;
+        if (!conv) atomicExch(err, 3);
+    }
+}
+
+// Ihat = Y Vhat line by line: line current J_k = y_k (V_parent - V_k) on the
+// phases of k; injection I_k = sum of children's J - J_k.  Also |Vhat|.
+__global__ void k_line_currents(int n, int L, Topo T, double2 *J) {
+    size_t tot = (size_t)L * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        int l = (int)(e / n), v = (int)(e % n);
+        for (int p = 0; p < 3; ++p) {
+            double2 j = make_double2(0.0, 0.0);
+            if (v > 0 && (T.ph[v] >> p & 1u)) {
+                int par = T.parent[v];
+                for (int q = 0; q < 3; ++q)
+                    if (T.ph[v] >> q & 1u)
+                        j = cadd(j, cmul(T.yl[(size_t)v * 9 + p * 3 + q], csub(T.vhat[sidx(l, q, par, n)], T.vhat[sidx(l, q, v, n)])));
+            }
+            J[sidx(l, p, v, n)] = j;
+            double2 vv = T.vhat[sidx(l, p, v, n)];
+            T.amag[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? cmag(vv) : 0.0;
+        }
+    }
+}
+
+__global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J) {
+    size_t tot = (size_t)L * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        int l = (int)(e / n), v = (int)(e % n);
+        for (int p = 0; p < 3; ++p) {
+            double2 s = make_double2(0.0, 0.0);
+            for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) s = cadd(s, J[sidx(l, p, T.child[c], n)]);
+            T.ihat[sidx(l, p, v, n)] = csub(s, J[sidx(l, p, v, n)]);
+        }
+    }
+}
+
+// Caller-supplied scenario library (host layout [L][n][3][2], caller numbering).
+__global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih) {
+    size_t tot = (size_t)L * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        int l = (int)(e / n), v = (int)(e % n);
+        int i = T.orig[v];
+        for (int p = 0; p < 3; ++p) {
+            size_t src = (((size_t)l * n + i) * 3 + p) * 2;
+            bool on = T.ph[v] >> p & 1u;
+            double2 vv = on ? make_double2(vh[src], vh[src + 1]) : make_double2(0.0, 0.0);
+            T.vhat[sidx(l, p, v, n)] = vv;
+            T.ihat[sidx(l, p, v, n)] = on ? make_double2(ih[src], ih[src + 1]) : make_double2(0.0, 0.0);
+            T.amag[sidx(l, p, v, n)] = on ? cmag(vv) : 0.0;
+        }
+    }
+}
+
+// Initial state of Algorithm 1: every bus is its own super-node, I = Ihat,
+// V = Vhat, cluster extremes = |Vhat|, MICE = 0.
+__global__ void k_state_init(int n, int L, Topo T, State S) {
+    size_t tot = (size_t)L * n;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+        int l = (int)(e / n), v = (int)(e % n);
+        if (l == 0) { S.label[v] = v; S.top[v] = v; }
+        S.mice[(size_t)l * n + v] = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            size_t q = sidx(l, p, v, n);
+            bool on = T.ph[v] >> p & 1u;
+            S.vcur[q] = T.vhat[q];
+            S.icur[q] = T.ihat[q];
+            S.hi[q] = on ? T.amag[q] : -INFINITY;
+            S.lo[q] = on ? T.amag[q] : INFINITY;
+        }
+    }
+}
+
+}  // namespace okr
