@@ -83,8 +83,7 @@ typedef struct okr_params {
     int32_t precision;          /* 0 = FP64 throughout */
     int32_t record_iters;       /* keep every candidate's score for the first K iterations */
     int32_t max_merges;         /* >= 0 overrides the target; -1 = use target_reduction */
-    int32_t profile;            /* 1 = time every candidate-sweep launch with CUDA events and
-                                   count its arithmetic (slower: no graph replay) */
+    int32_t profile;            /* 1 = count the search's arithmetic and time its sweep phase */
     int32_t reserved;           /* must be 0 */
     int64_t max_spins;          /* limit for device-side waits (0 = default) */
 } okr_params;
@@ -99,10 +98,12 @@ typedef struct okr_summary {
     double smice;               /* SMICE of the final reduction */
     double max_error;           /* largest per-phase magnitude error of the final reduction */
     int64_t launches;           /* kernels launched by the last call */
+    double search_ms;           /* duration of the search kernel (CUDA events on the
+                                   library stream; the search runs as one persistent launch) */
+    int64_t sweeps;             /* candidate sweeps run (one per iteration) */
     /* filled when params.profile = 1 (zero otherwise): */
-    int64_t sweep_launches;     /* candidate-sweep launches that evaluated candidates */
-    double sweep_ms;            /* their summed duration (CUDA events on the library stream) */
-    double sweep_flops;         /* their algorithmic floating-point operations */
+    double sweep_ms;            /* time inside the sweep phase (device timer of CTA 0) */
+    double flops;               /* algorithmic floating-point operations of the search */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,

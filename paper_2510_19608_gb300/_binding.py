@@ -44,7 +44,7 @@ class Summary(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_scen", C.c_int32), ("n_iter", C.c_int32), ("stop_reason", C.c_int32),
                 ("pf_sweeps", C.c_int32), ("n_kept", C.c_int32), ("candidates", C.c_int64),
                 ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
-                ("sweep_launches", C.c_int64), ("sweep_ms", C.c_double), ("sweep_flops", C.c_double)]
+                ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double)]
 
 
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",

@@ -1,6 +1,6 @@
 // okr_capi.cu -- the C ABI declared in include/okron.h: context, device
 // workspace, and the host orchestration of the per-feeder setup kernels and the
-// per-iteration search kernels (one CUDA graph per iteration, replayed).
+// persistent search kernel (one cooperative launch per reduction).
 #include "okron.h"
 #include "okr_internal.cuh"
 #include "okr_kernels.cuh"
@@ -17,7 +17,7 @@ using namespace okr;
 
 namespace {
 
-constexpr int kIterBatch = 32;          // graph replays between host checks of the stop flag
+constexpr long long kDefaultSpins = 4000000;   // bounded device waits: well under a second
 constexpr double kPfTol = 1e-13;
 constexpr int kPfMaxIter = 200;
 
@@ -44,6 +44,11 @@ struct okr_ctx {
     uint16_t *rmq = nullptr;
     double2 *J = nullptr;
     int *pf_iters = nullptr, *err_dev = nullptr;
+    GridBar *gb = nullptr;
+    int grid = 0;                       // CTAs of the persistent search kernel
+    std::vector<void *> work_allocs;    // chunk map and partial sums (grown on demand)
+    int cap_chunks = 0;
+    int sum_sz = 0, max_depth = 0;      // of the current feeder
     // outputs
     int *super_out = nullptr;
     double *vred_out = nullptr, *vhat_out = nullptr;
@@ -54,14 +59,10 @@ struct okr_ctx {
     Ctrl *C = nullptr;
     Ctrl *C_host = nullptr;     // pinned
 
-    // cached graph of one iteration
-    cudaGraphExec_t graph = nullptr;
-    int graph_n = -1, graph_L = -1;
 
     // counters of the last call
     int64_t launches = 0;
-    double sweep_ms = 0.0;
-    int64_t sweep_launches = 0;
+    double search_ms = 0.0;
 
     // last result
     bool have_result = false;
@@ -90,10 +91,11 @@ okr_status fail(okr_ctx *c, okr_status s, const char *fmt, ...) {
     } while (0)
 
 void free_all(okr_ctx *ctx) {
-    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
-    ctx->graph_n = ctx->graph_L = -1;
     for (void *p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
+    for (void *p : ctx->work_allocs) cudaFree(p);
+    ctx->work_allocs.clear();
+    ctx->cap_chunks = 0;
     ctx->cap_n = ctx->cap_L = ctx->cap_rec = 0;
 }
 
@@ -111,16 +113,13 @@ int log2_ceil(int n) {
     return j;
 }
 
-// Largest number of chunks one iteration can need: every candidate covers at
-// most n_bus positions, and there are at most 2 n_bus candidate slots.
-size_t max_chunks_for(int n) { return (size_t)2 * n * (size_t)((n + kChunk - 1) / kChunk); }
+
 
 okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     if (n <= ctx->cap_n && L <= ctx->cap_L && rec <= ctx->cap_rec) return OKR_OK;
     free_all(ctx);
     const size_t N = n, NL3 = (size_t)3 * L * n;
     const int LOG = log2_ceil(n) + 1;
-    const size_t MC = max_chunks_for(n);
     CK(dalloc(ctx, &ctx->parent_in, N));
     CK(dalloc(ctx, &ctx->ph_in, N));
     CK(dalloc(ctx, &ctx->z_in, N * 18));
@@ -144,7 +143,7 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &ctx->vhat_out, (size_t)L * N * 6));
 
     Topo &T = ctx->T;
-    CK(dalloc(ctx, &T.maxd, 1));
+    CK(dalloc(ctx, &T.maxd, 2));
     CK(dalloc(ctx, &T.parent, N));
     CK(dalloc(ctx, &T.orig, N));
     CK(dalloc(ctx, &T.pre, N));
@@ -167,6 +166,9 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     State &S = ctx->S;
     CK(dalloc(ctx, &S.label, N));
     CK(dalloc(ctx, &S.top, N));
+    CK(dalloc(ctx, &S.sn_list[0], N));
+    CK(dalloc(ctx, &S.sn_list[1], N));
+    CK(dalloc(ctx, &S.sn_rank, N + 1));
     CK(dalloc(ctx, &S.vcur, NL3));
     CK(dalloc(ctx, &S.icur, NL3));
     CK(dalloc(ctx, &S.hi, NL3));
@@ -175,13 +177,16 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
 
     Search &X = ctx->X;
     CK(dalloc(ctx, &X.cand, 2 * N));
-    CK(dalloc(ctx, &X.nchunk, 2 * N));
+    CK(dalloc(ctx, &X.slot, 2 * N));
     CK(dalloc(ctx, &X.base, 2 * N + 1));
-    CK(dalloc(ctx, &X.chunk_cand, MC));
-    CK(dalloc(ctx, &X.partial, MC));
+    CK(dalloc(ctx, &X.arrive, 2 * N));
+    CK(dalloc(ctx, &X.block_tot, (size_t)ctx->num_sms));
     CK(dalloc(ctx, &X.score, 2 * N));
     CK(dalloc(ctx, &X.feas, 2 * N));
-    X.max_chunks = (int)MC;
+    CK(dalloc(ctx, &ctx->gb, 1));
+    X.chunk_first = nullptr;
+    X.partial = nullptr;
+    X.max_chunks = 0;
     CK(dalloc(ctx, &X.dec_s, N));
     CK(dalloc(ctx, &X.dec_r, N));
     CK(dalloc(ctx, &X.dec_score, N));
@@ -268,7 +273,13 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     k_lines<<<1, 1024, 0, st>>>(n, T, ctx->z_in, ctx->err_dev);
     ctx->launches += 3 + LOG;
     CK(cudaGetLastError());
-    return read_setup_errors(ctx);
+    s = read_setup_errors(ctx);
+    if (s != OKR_OK) return s;
+    int stats[2] = {0, 0};
+    CK(cudaMemcpy(stats, T.maxd, sizeof stats, cudaMemcpyDeviceToHost));
+    ctx->max_depth = stats[0];
+    ctx->sum_sz = stats[1];
+    return OKR_OK;
 }
 
 okr_status read_setup_errors(okr_ctx *ctx) {
@@ -294,44 +305,34 @@ okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
     return OKR_OK;
 }
 
-constexpr int kKernelsPerIter = 5;
-
-// The five kernels of one iteration; with events, the sweep is bracketed.
-void launch_iteration(okr_ctx *ctx, cudaEvent_t e0, cudaEvent_t e1) {
-    cudaStream_t st = ctx->stream;
-    const int n = ctx->T.n;
-    const int nb = blocks_for(n, 256, ctx->num_sms * 8);
-    k_setup<<<nb, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
-    k_scan<<<1, 1024, 0, st>>>(ctx->T, ctx->X, ctx->C);
-    if (e0) cudaEventRecord(e0, st);
-    k_sweep<<<ctx->num_sms * 8, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
-    if (e1) cudaEventRecord(e1, st);
-    k_select<<<1, 1024, 0, st>>>(ctx->T, ctx->X, ctx->C);
-    k_commit<<<nb, 256, 0, st>>>(ctx->T, ctx->S, ctx->X, ctx->C);
-}
-
-okr_status build_graph(okr_ctx *ctx) {
-    const int n = ctx->T.n, L = ctx->T.L;
-    if (ctx->graph && ctx->graph_n == n && ctx->graph_L == L) return OKR_OK;
-    if (ctx->graph) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
-    cudaStream_t st = ctx->stream;
-    cudaGraph_t g = nullptr;
-    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    launch_iteration(ctx, nullptr, nullptr);
-    cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (e != cudaSuccess) return fail(ctx, OKR_ECUDA, "graph capture: %s", cudaGetErrorString(e));
-    e = cudaGraphInstantiate(&ctx->graph, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) { ctx->graph = nullptr; return fail(ctx, OKR_ECUDA, "graph instantiate: %s", cudaGetErrorString(e)); }
-    ctx->graph_n = n;
-    ctx->graph_L = L;
+// Chunk map and partial sums for up to `chunks` chunks of one sweep.
+okr_status ensure_work(okr_ctx *ctx, long long chunks) {
+    if (chunks <= ctx->cap_chunks) return OKR_OK;
+    if (chunks > (long long)INT32_MAX / 2) return fail(ctx, OKR_EINVAL, "feeder too large for the search buffers");
+    for (void *p : ctx->work_allocs) cudaFree(p);
+    ctx->work_allocs.clear();
+    ctx->cap_chunks = 0;
+    void *a = nullptr, *b = nullptr;
+    cudaError_t e = cudaMalloc(&a, sizeof(int) * (size_t)chunks);
+    if (e == cudaSuccess) e = cudaMalloc(&b, sizeof(double2) * ((size_t)chunks + 2 * (size_t)ctx->cap_n));
+    if (e != cudaSuccess) {
+        if (a) cudaFree(a);
+        return fail(ctx, OKR_ENOMEM, "search buffers: %s", cudaGetErrorString(e));
+    }
+    ctx->work_allocs.push_back(a);
+    ctx->work_allocs.push_back(b);
+    ctx->X.chunk_first = (int *)a;
+    ctx->X.partial = (double2 *)b;
+    ctx->X.max_chunks = (int)chunks;
+    ctx->cap_chunks = (int)chunks;
     return OKR_OK;
 }
 
-// Initial state, then iterations until the stop flag is raised.  Normal mode
-// replays the captured iteration graph in batches and reads the stop flag after
-// each batch; profile mode launches the kernels directly with an event pair
-// around every sweep.
+int positions_per_chunk(int L) { return 32 / (4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4))); }
+
+// Initial state, then the persistent search kernel.  The kernel stops by itself
+// (target reached or nothing feasible); if one sweep needs more work buffer than
+// allocated it saves its state and exits, and is relaunched with a larger one.
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     cudaStream_t st = ctx->stream;
     const int n = ctx->T.n, L = ctx->T.L;
@@ -347,53 +348,55 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     c.margin = p->margin;
     c.tau = p->tie_tol;
     c.profile = p->profile ? 1 : 0;
+    c.n_super = n;
+    c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
     CK(cudaMemcpyAsync(ctx->C, &c, sizeof c, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
+    CK(cudaMemsetAsync(X.arrive, 0, sizeof(int) * 2 * n, st));
+    CK(cudaMemsetAsync(ctx->gb, 0, sizeof(GridBar), st));
     if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
-    // the graph bakes in the Search struct (rec_iters): rebuild when it changes
-    if (ctx->graph && ctx->rec_iters != p->record_iters) { cudaGraphExecDestroy(ctx->graph); ctx->graph = nullptr; }
     ctx->rec_iters = p->record_iters;
-    ctx->sweep_ms = 0.0;
-    ctx->sweep_launches = 0;
-    std::vector<cudaEvent_t> ev;
-    if (p->profile) {
-        ev.resize(2 * kIterBatch);
-        for (auto &e : ev) CK(cudaEventCreate(&e));
-    } else {
-        okr_status s = build_graph(ctx);
-        if (s != OKR_OK) return s;
-    }
-    int launched = 0, swept = 0;
-    okr_status status = OKR_OK;
-    while (true) {
-        int batch = mm + 1 - launched;          // one extra pass observes the stop
-        if (batch > kIterBatch) batch = kIterBatch;
-        if (batch < 1) batch = 1;
-        for (int b = 0; b < batch; ++b) {
-            if (p->profile) launch_iteration(ctx, ev[2 * b], ev[2 * b + 1]);
-            else if (cudaGraphLaunch(ctx->graph, st) != cudaSuccess) { status = fail(ctx, OKR_ECUDA, "graph launch failed"); break; }
+    ctx->search_ms = 0.0;
+    // first sweep: every bus is a super-node; candidate (p -> w) and (w -> p)
+    // cover subtree(w) and one extra position, so 2 * sum(sz) + 2 n bounds it
+    const int ppc = positions_per_chunk(L);
+    long long want = (2LL * ctx->sum_sz + 2LL * n + ppc - 1) / ppc + 1;
+    okr_status s = ensure_work(ctx, want);
+    if (s != OKR_OK) return s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int attempt = 0; attempt < 16 && !c.done; ++attempt) {
+        void *args[] = {&ctx->T, &ctx->S, &ctx->X, &ctx->C, &ctx->gb};
+        cudaEventRecord(e0, st);
+        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_search, dim3(ctx->grid), dim3(512), args, 0, st);
+        cudaEventRecord(e1, st);
+        ctx->launches += 1;
+        if (e != cudaSuccess) { s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e)); break; }
+        e = cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = fail(ctx, OKR_ECUDA, "search: %s", cudaGetErrorString(e)); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ctx->search_ms += ms;
+        c = *ctx->C_host;
+        if (c.err == 7) {                       // grow the work buffers and continue
+            want = 2LL * ((c.total_pos + ppc - 1) / ppc + 1);
+            s = ensure_work(ctx, want);
+            if (s != OKR_OK) break;
+            int zero = 0;
+            CK(cudaMemcpyAsync(&ctx->C->err, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
+            c.done = 0;
+            continue;
         }
-        if (status != OKR_OK) break;
-        ctx->launches += (int64_t)batch * kKernelsPerIter;
-        launched += batch;
-        if (cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-            cudaStreamSynchronize(st) != cudaSuccess) { status = fail(ctx, OKR_ECUDA, "%s", cudaGetErrorString(cudaGetLastError())); break; }
-        if (p->profile) {
-            // sweeps that found work come first in the batch
-            const int ran = ctx->C_host->sweeps_run - swept;
-            for (int b = 0; b < ran && b < batch; ++b) {
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, ev[2 * b], ev[2 * b + 1]);
-                ctx->sweep_ms += ms;
-            }
-            ctx->sweep_launches += ran;
-            swept = ctx->C_host->sweeps_run;
-        }
-        if (ctx->C_host->done || ctx->C_host->err) break;
-        if (launched > mm + 1) { status = fail(ctx, OKR_EINTERNAL, "search did not stop after %d iterations", launched); break; }
+        break;
     }
-    for (auto &e : ev) cudaEventDestroy(e);
-    if (status != OKR_OK) return status;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != OKR_OK) return s;
+    if (c.err == 6) return fail(ctx, OKR_ETIMEOUT, "a grid barrier of the search gave up after %lld polls", c.max_spins);
+    if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
+    if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
     k_final_maxerr<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, X, ctx->C);
     k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, ctx->vred_out,
                                                                                 ctx->super_out, ctx->vhat_out);
@@ -402,8 +405,6 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     CK(cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     ctx->last = *ctx->C_host;
-    if (ctx->last.err == 4) return fail(ctx, OKR_EINTERNAL, "chunk buffer too small");
-    if (ctx->last.err) return fail(ctx, OKR_EINTERNAL, "device error %d", ctx->last.err);
     return OKR_OK;
 }
 
@@ -516,6 +517,13 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
         delete ctx;
         return OKR_ECUDA;
     }
+    int coop = 0, per_sm = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, 512, 0) != cudaSuccess || per_sm < 1) {
+        delete ctx;
+        return OKR_ECUDA;
+    }
+    ctx->grid = ctx->num_sms;               // one CTA per SM: all co-resident
     if (stream) {
         ctx->stream = (cudaStream_t)stream;
     } else {
@@ -584,8 +592,10 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     CK(cudaMemcpyAsync(vhat_out, ctx->vhat_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
     if (ihat_out) {
         // S.icur == Ihat after the initial state; export it through vred's slot
-        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, State{ctx->S.label, ctx->S.top, ctx->S.icur, ctx->S.icur, ctx->S.hi, ctx->S.lo, ctx->S.mice},
-                                                                                    ctx->vred_out, nullptr, nullptr);
+        State si = ctx->S;
+        si.vcur = ctx->S.icur;                  // export the injections through the voltage slot
+        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, si, ctx->vred_out,
+                                                                                    nullptr, nullptr);
         CK(cudaMemcpyAsync(ihat_out, ctx->vred_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
@@ -615,9 +625,10 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     if (c.t > 0) cudaMemcpy(&me, ctx->X.dec_maxerr + (c.t - 1), sizeof me, cudaMemcpyDeviceToHost);
     out->max_error = me;
     out->launches = ctx->launches;
-    out->sweep_launches = ctx->sweep_launches;
-    out->sweep_ms = ctx->sweep_ms;
-    out->sweep_flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
+    out->search_ms = ctx->search_ms;
+    out->sweeps = ctx->last.iters;
+    out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
+    out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
     return OKR_OK;
 }
 

@@ -41,7 +41,7 @@ __host__ __device__ __forceinline__ size_t sidx(int l, int p, int k, int n) { re
 // Static description of one feeder (preorder numbering), built once per call.
 struct Topo {
     int n, L;
-    int *maxd;          // [1] deepest level (written on the device)
+    int *maxd;          // [2] deepest level, sum of subtree sizes (written on the device)
     int *parent;        // [n], parent[0] = -1
     int *orig;          // [n] preorder -> caller id
     int *pre;           // [n] caller id -> preorder
@@ -62,20 +62,27 @@ struct Topo {
     double2 *vslack;    // [3]
 };
 
-// Candidate slot 2*w + d for the quotient edge above cluster w (d = 0: w's
-// cluster joins its parent cluster x; d = 1: x's cluster joins w).
+// One candidate (s, r) of the current iteration, in a compact list.  Its work
+// positions are the super-nodes of the two affected preorder ranges, listed in
+// the compact super-node order (s side first, then r side), plus one position
+// for the merged cluster of s when s is the common ancestor (its voltage does
+// not move, only its cluster grows).
 struct Cand {
-    int s, r, a;        // super-nodes and their lowest common ancestor
-    int dir;            // 0: s above r, 1: r above s
-    int lo_s, len_s;    // buses whose path to s leaves the s-r path below a
-    int lo_r, len_r;    // same on the r side
+    int s, r, a;        // super-nodes and their lowest common ancestor (preorder ids)
+    int dir;            // 0: s's cluster above r's, 1: r's above s's
+    int js, ns;         // s side: super-node list range [js, js + ns)
+    int jr, nr;         // r side
+    int fixed;          // 1: extra position for the merged cluster of s (s == a)
+    int pad;
     unsigned long long key;   // (caller r, caller s) for the tie rule
 };
 
-// Reduction state (super-node quantities live at the super-node's index).
+// Reduction state (super-node quantities live at the super-node's bus index).
 struct State {
     int *label;         // [n] super-node of each bus
     int *top;           // [n] topmost bus of each cluster
+    int *sn_list[2];    // [n] super-nodes in increasing preorder id after t merges: buffer t & 1
+    int *sn_rank;       // [n+1] number of super-nodes with a smaller preorder id
     double2 *vcur;      // [L*3*n] super-node voltages for the current injections
     double2 *icur;      // [L*3*n] aggregated injections
     double *hi, *lo;    // [L*3*n] max / min of |vhat| over the cluster (per phase)
@@ -87,28 +94,37 @@ struct Ctrl {
     int max_merges;
     int done;               // 1 once the search has stopped
     int stop_reason;        // 0 target reached, 1 no feasible candidate
+    int n_cand;             // candidates of the current iteration
+    int total_pos;          // work positions of the current iteration
     int total_chunks;
-    int win;                // winning slot of the last iteration
-    int commit;             // 1 between a selection and its commit
-    int n_valid;            // candidates of the last iteration
+    int n_super;            // super-nodes left
     int err;                // device-side error code (0 = none)
+    int profile;            // 1: count arithmetic and time the sweep phase
+    int iters;              // sweeps run
+    int pad;
     double margin;          // voltage-error bound (p.u.)
     double tau;             // tie band
     double s_cur;           // SMICE of the current state
-    double win_d;           // score change of the winner
-    double gap;             // distance of the next score above the tie band
     long long candidates;   // candidates evaluated over the run
-    int profile;            // 1: the sweep counts its arithmetic
-    int sweeps_run;         // sweep launches that found work (profile mode)
-    double sweep_flops;     // algorithmic flops of those sweeps (profile mode)
+    long long max_spins;    // limit of a device-side wait
+    double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
+    unsigned long long sweep_ns;   // time in the sweep phase (profile mode, device timer)
+};
+
+// Grid-wide barrier of the persistent search kernel.
+struct GridBar {
+    unsigned int count;
+    unsigned int gen;
 };
 
 struct Search {
-    Cand *cand;             // [2n]
-    int *nchunk;            // [2n]
-    int *base;              // [2n+1]
-    int *chunk_cand;        // [max_chunks]
-    double2 *partial;       // [max_chunks] (sum of score changes, max new MICE)
+    Cand *cand;             // [2n] compact candidate list
+    Cand *slot;             // [2n] candidates by super-node slot (s < 0: none)
+    int *base;              // [2n+1] first work position of each candidate
+    int *arrive;            // [2n] pieces written so far (reset by the last writer)
+    int2 *block_tot;        // [grid] per-CTA (candidates, positions)
+    int *chunk_first;       // [max_chunks] candidate holding the first position of a chunk
+    double2 *partial;       // [max_chunks + 2n] (sum of score changes, max new MICE), slot g + c
     double *score;          // [2n] score change D(c)
     int *feas;              // [2n]
     int max_chunks;

@@ -21,12 +21,8 @@ __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J
 __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);
 __global__ void k_state_init(int n, int L, Topo T, State S);
 
-// okr_search.cu
-__global__ void k_setup(Topo T, State S, Search X, Ctrl *C);
-__global__ void __launch_bounds__(1024) k_scan(Topo T, Search X, Ctrl *C);
-__global__ void __launch_bounds__(256) k_sweep(Topo T, State S, Search X, Ctrl *C);
-__global__ void __launch_bounds__(1024) k_select(Topo T, Search X, Ctrl *C);
-__global__ void k_commit(Topo T, State S, Search X, Ctrl *C);
+// okr_persist.cu
+__global__ void __launch_bounds__(512, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb);
 __global__ void k_final_maxerr(Topo T, State S, Search X, const Ctrl *C);
 __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);
 

@@ -161,7 +161,14 @@ __global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict_
         int slot = atomicAdd(&ccount[d], 1);
         T.level_bus[T.level_off[d] + slot] = T.pre[i];
     }
-    if (tid == 0) *T.maxd = maxd;
+    __shared__ int s_sum;
+    if (tid == 0) s_sum = 0;
+    __syncthreads();
+    int part = 0;
+    for (int i = tid; i < n; i += nt) part += size[i];
+    atomicAdd(&s_sum, part);
+    __syncthreads();
+    if (tid == 0) { T.maxd[0] = maxd; T.maxd[1] = s_sum; }
 }
 
 // Children CSR indexed by preorder id (one CTA).  The children of preorder
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__r
     __syncthreads();
     for (int q = tid; q < 9; q += nt) T.zc[q] = make_double2(0.0, 0.0);
     __syncthreads();
-    const int maxd = *T.maxd;
+    const int maxd = T.maxd[0];
     for (int d = 1; d <= maxd; ++d) {
         for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
             int v = T.level_bus[x], p = T.parent[v];
@@ -275,7 +282,7 @@ __global__ void __launch_bounds__(1024) k_power_flow(int n, int L, Topo T, const
         for (int p = 0; p < 3; ++p)
             V[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
     __syncthreads();
-    const int maxd = *T.maxd;
+    const int maxd = T.maxd[0];
     int it;
     bool conv = false;
     for (it = 1; it <= max_iter; ++it) {
@@ -386,7 +393,13 @@ __global__ void k_state_init(int n, int L, Topo T, State S) {
     size_t tot = (size_t)L * n;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
         int l = (int)(e / n), v = (int)(e % n);
-        if (l == 0) { S.label[v] = v; S.top[v] = v; }
+        if (l == 0) {
+            S.label[v] = v;
+            S.top[v] = v;
+            S.sn_list[0][v] = v;
+            S.sn_rank[v] = v;
+            if (v == n - 1) S.sn_rank[n] = n;
+        }
         S.mice[(size_t)l * n + v] = 0.0;
         for (int p = 0; p < 3; ++p) {
             size_t q = sidx(l, p, v, n);
