@@ -80,7 +80,10 @@ typedef struct okr_params {
                                    n_bus - 1); 1.0 = run until no candidate is feasible */
     double tie_tol;             /* tie band tau on the score, >= 0 (default 1e-9) */
     int32_t objective;          /* 0 = SMICE (Algorithm 1); other values are rejected */
-    int32_t precision;          /* 0 = FP64 throughout */
+    int32_t precision;          /* 0 = every candidate scored in FP64;
+                                   1 = FP32 screen with a rigorous error bound, FP64 rescoring of
+                                   the candidates the bound cannot separate, FP64 merges.  Both
+                                   select the same candidate as an all-FP64 search. */
     int32_t record_iters;       /* keep every candidate's score for the first K iterations */
     int32_t max_merges;         /* >= 0 overrides the target; -1 = use target_reduction */
     int32_t profile;            /* 1 = count the search's arithmetic and time its sweep phase */
@@ -104,6 +107,10 @@ typedef struct okr_summary {
     /* filled when params.profile = 1 (zero otherwise): */
     double sweep_ms;            /* time inside the sweep phase (device timer of CTA 0) */
     double flops;               /* algorithmic floating-point operations of the search */
+    int32_t rechecks;           /* precision 1: iterations that rescored candidates in FP64 */
+    int32_t recheck_cands;      /* precision 1: candidates rescored in FP64 over the run */
+    double phase_ms[8];         /* profile mode: time of CTA 0 in selection, FP64 recheck, merge,
+                                   candidate setup, barrier, compaction, barrier, sweep */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
@@ -153,9 +160,12 @@ okr_status okr_get_assignment(const okr_ctx *ctx, int32_t *super_of);
 okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred);
 /* Scores of every candidate of iteration `iter` < record_iters (SMICE the
  * candidate would give; +inf if it breaks the margin), in no particular order.
- * cap = buffer length (2*n_bus suffices); *count = candidates of that iteration. */
+ * With precision 1 these are the FP32 screen values and bound[i] bounds their
+ * distance to the FP64 values (0 with precision 0).  cap = buffer length
+ * (2*n_bus suffices); *count = candidates of that iteration.  s, r, smice,
+ * bound may be NULL. */
 okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32_t *s, int32_t *r,
-                            double *smice, int32_t *count);
+                            double *smice, double *bound, int32_t *count);
 
 #ifdef __cplusplus
 }

@@ -44,7 +44,8 @@ class Summary(C.Structure):
     _fields_ = [("n_bus", C.c_int32), ("n_scen", C.c_int32), ("n_iter", C.c_int32), ("stop_reason", C.c_int32),
                 ("pf_sweeps", C.c_int32), ("n_kept", C.c_int32), ("candidates", C.c_int64),
                 ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
-                ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double)]
+                ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double),
+                ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 8)]
 
 
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
@@ -82,7 +83,7 @@ def lib():
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
             L.okr_get_voltages.argtypes = [P, P, P]
-            L.okr_get_recorded.argtypes = [P, I32, I32, P, P, P, P]
+            L.okr_get_recorded.argtypes = [P, I32, I32, P, P, P, P, P]
             for fn in EXPORTS:
                 if fn not in ("okr_default_params", "okr_status_str", "okr_last_error"):
                     getattr(L, fn).restype = C.c_int
@@ -202,7 +203,9 @@ class Context:
     def summary(self) -> dict:
         s = Summary()
         self._check(lib().okr_get_summary(self._h, C.byref(s)))
-        return {k: getattr(s, k) for k, _ in Summary._fields_}
+        out = {k: getattr(s, k) for k, _ in Summary._fields_}
+        out["phase_ms"] = list(s.phase_ms)
+        return out
 
     def decisions(self) -> dict:
         t = self.summary()["n_iter"]
@@ -232,7 +235,8 @@ class Context:
         s = np.zeros(cap, np.int32)
         r = np.zeros(cap, np.int32)
         sc = np.zeros(cap)
+        bd = np.zeros(cap)
         cnt = C.c_int32()
-        self._check(lib().okr_get_recorded(self._h, int(it), cap, _ptr(s), _ptr(r), _ptr(sc), C.byref(cnt)))
+        self._check(lib().okr_get_recorded(self._h, int(it), cap, _ptr(s), _ptr(r), _ptr(sc), _ptr(bd), C.byref(cnt)))
         c = min(cnt.value, cap)
-        return dict(s=s[:c], r=r[:c], score=sc[:c])
+        return dict(s=s[:c], r=r[:c], score=sc[:c], bound=bd[:c])

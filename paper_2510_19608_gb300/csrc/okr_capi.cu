@@ -158,6 +158,8 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &T.zl, N * 9));
     CK(dalloc(ctx, &T.yl, N * 9));
     CK(dalloc(ctx, &T.zc, N * 9));
+    CK(dalloc(ctx, &T.zh, N * 9));
+    CK(dalloc(ctx, &T.zlo, N * 9));
     CK(dalloc(ctx, &T.vhat, NL3));
     CK(dalloc(ctx, &T.ihat, NL3));
     CK(dalloc(ctx, &T.amag, NL3));
@@ -174,6 +176,12 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &S.hi, NL3));
     CK(dalloc(ctx, &S.lo, NL3));
     CK(dalloc(ctx, &S.mice, (size_t)L * N));
+    CK(dalloc(ctx, &S.mcur, NL3));
+    CK(dalloc(ctx, &S.v32, NL3));
+    CK(dalloc(ctx, &S.hr32, NL3));
+    CK(dalloc(ctx, &S.lr32, NL3));
+    CK(dalloc(ctx, &S.mice32, (size_t)L * N));
+    CK(dalloc(ctx, &S.icur32, NL3));
 
     Search &X = ctx->X;
     CK(dalloc(ctx, &X.cand, 2 * N));
@@ -183,6 +191,8 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &X.block_tot, (size_t)ctx->num_sms));
     CK(dalloc(ctx, &X.score, 2 * N));
     CK(dalloc(ctx, &X.feas, 2 * N));
+    CK(dalloc(ctx, &X.scr, 2 * N));
+    CK(dalloc(ctx, &X.wsum, (size_t)ctx->num_sms * (512 / 32)));
     CK(dalloc(ctx, &ctx->gb, 1));
     X.chunk_first = nullptr;
     X.partial = nullptr;
@@ -197,6 +207,7 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &X.rec_s, R * 2 * N));
     CK(dalloc(ctx, &X.rec_r, R * 2 * N));
     CK(dalloc(ctx, &X.rec_score, R * 2 * N));
+    CK(dalloc(ctx, &X.rec_bound, R * 2 * N));
     CK(dalloc(ctx, &X.rec_count, R));
     CK(dalloc(ctx, &ctx->C, 1));
 
@@ -232,7 +243,7 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
     if (p->max_merges < 0 && !(p->target_reduction >= 0.0 && p->target_reduction <= 1.0))
         return fail(ctx, OKR_EINVAL, "target_reduction outside [0, 1]");
     if (p->objective != 0) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
-    if (p->precision != 0) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
+    if (p->precision != 0 && p->precision != 1) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
     if (p->record_iters < 0) return fail(ctx, OKR_EINVAL, "record_iters < 0");
     if (p->reserved != 0) return fail(ctx, OKR_EINVAL, "reserved must be 0");
     return OKR_OK;
@@ -349,6 +360,7 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     c.tau = p->tie_tol;
     c.profile = p->profile ? 1 : 0;
     c.n_super = n;
+    c.precision = p->precision;
     c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
     CK(cudaMemcpyAsync(ctx->C, &c, sizeof c, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
@@ -367,9 +379,9 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     for (int attempt = 0; attempt < 16 && !c.done; ++attempt) {
-        void *args[] = {&ctx->T, &ctx->S, &ctx->X, &ctx->C, &ctx->gb};
+        CK(cudaMemsetAsync(ctx->gb, 0, sizeof(GridBar), st));
         cudaEventRecord(e0, st);
-        cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_search, dim3(ctx->grid), dim3(512), args, 0, st);
+        cudaError_t e = launch_search(p->precision, ctx->grid, ctx->T, ctx->S, ctx->X, ctx->C, ctx->gb, st);
         cudaEventRecord(e1, st);
         ctx->launches += 1;
         if (e != cudaSuccess) { s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e)); break; }
@@ -397,10 +409,9 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     if (c.err == 6) return fail(ctx, OKR_ETIMEOUT, "a grid barrier of the search gave up after %lld polls", c.max_spins);
     if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
     if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
-    k_final_maxerr<<<blocks_for(n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, X, ctx->C);
     k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, ctx->vred_out,
                                                                                 ctx->super_out, ctx->vhat_out);
-    ctx->launches += 2;
+    ctx->launches += 1;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -519,7 +530,7 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
     }
     int coop = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_search, 512, 0) != cudaSuccess || per_sm < 1) {
+        (per_sm = search_blocks_per_sm()) < 1) {
         delete ctx;
         return OKR_ECUDA;
     }
@@ -629,6 +640,9 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->sweeps = ctx->last.iters;
     out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
     out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
+    out->rechecks = ctx->last.rechecks;
+    out->recheck_cands = ctx->last.recheck_cands;
+    for (int i = 0; i < 8; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;
     return OKR_OK;
 }
 
@@ -665,7 +679,7 @@ okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred) {
 }
 
 okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32_t *s, int32_t *r, double *smice,
-                            int32_t *count) {
+                            double *bound, int32_t *count) {
     if (!ctx || !count || cap < 0) return OKR_EINVAL;
     if (!ctx->have_result) return OKR_ENOTREADY;
     if (iter < 0 || iter >= ctx->rec_iters) return OKR_EINVAL;
@@ -678,6 +692,7 @@ okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32
         if (s && cudaMemcpy(s, ctx->X.rec_s + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
         if (r && cudaMemcpy(r, ctx->X.rec_r + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
         if (smice && cudaMemcpy(smice, ctx->X.rec_score + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (bound && cudaMemcpy(bound, ctx->X.rec_bound + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     }
     return OKR_OK;
 }

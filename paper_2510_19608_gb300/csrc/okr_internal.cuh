@@ -56,6 +56,7 @@ struct Topo {
     double2 *zl;        // [n*9] line impedance parent(k)->k, row-major 3x3
     double2 *yl;        // [n*9] line admittance on the phases of k
     double2 *zc;        // [n*9] path impedance root->k
+    float2 *zh, *zlo;   // [n*9] zc split into two floats: zc ~ zh + zlo
     double2 *vhat;      // [L*3*n] scenario voltages
     double2 *ihat;      // [L*3*n] scenario injections, Y vhat
     double *amag;       // [L*3*n] |vhat|
@@ -87,6 +88,12 @@ struct State {
     double2 *icur;      // [L*3*n] aggregated injections
     double *hi, *lo;    // [L*3*n] max / min of |vhat| over the cluster (per phase)
     double *mice;       // [L*n] current MICE of each cluster
+    double *mcur;       // [L*3*n] |vcur|
+    // single-precision copies for the screening sweep
+    float2 *v32;        // [L*3*n] vcur
+    float *hr32, *lr32; // [L*3*n] hi - |vcur|, lo - |vcur| (differences taken in FP64)
+    float *mice32;      // [L*n]
+    float2 *icur32;     // [L*3*n]
 };
 
 struct Ctrl {
@@ -101,7 +108,9 @@ struct Ctrl {
     int err;                // device-side error code (0 = none)
     int profile;            // 1: count arithmetic and time the sweep phase
     int iters;              // sweeps run
-    int pad;
+    int precision;          // 0 FP64 sweep, 1 FP32 screen + FP64 recheck
+    int rechecks;           // iterations that needed an FP64 recheck
+    int recheck_cands;      // candidates rechecked in FP64 over the run
     double margin;          // voltage-error bound (p.u.)
     double tau;             // tie band
     double s_cur;           // SMICE of the current state
@@ -109,12 +118,14 @@ struct Ctrl {
     long long max_spins;    // limit of a device-side wait
     double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
     unsigned long long sweep_ns;   // time in the sweep phase (profile mode, device timer)
+    unsigned long long phase_ns[8];   // profile mode, CTA 0: select, recheck, commit, setup,
+                                      // barrier 1, phase 2, barrier 2, sweep + barrier 3
 };
 
 // Grid-wide barrier of the persistent search kernel.
 struct GridBar {
-    unsigned int count;
-    unsigned int gen;
+    unsigned int count;     // arrivals since launch; barrier k completes at k * grid
+    unsigned int pad;
 };
 
 struct Search {
@@ -125,8 +136,10 @@ struct Search {
     int2 *block_tot;        // [grid] per-CTA (candidates, positions)
     int *chunk_first;       // [max_chunks] candidate holding the first position of a chunk
     double2 *partial;       // [max_chunks + 2n] (sum of score changes, max new MICE), slot g + c
-    double *score;          // [2n] score change D(c)
+    double *score;          // [2n] score change D(c) (FP64 sweep, or FP64 recheck of R)
     int *feas;              // [2n]
+    float4 *scr;            // [2n] screen: (D32, bound of D, max new MICE, bound of it)
+    double *wsum;           // [grid*warps] per-warp FP64 score change of the committed merge
     int max_chunks;
     // per-iteration record
     int *dec_s, *dec_r;     // caller ids
@@ -135,6 +148,7 @@ struct Search {
     int rec_iters;
     int *rec_s, *rec_r;     // [rec_iters][2n]
     double *rec_score;
+    double *rec_bound;      // [rec_iters][2n] bound of the recorded score (0 for FP64)
     int *rec_count;
 };
 

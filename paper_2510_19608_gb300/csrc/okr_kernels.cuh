@@ -22,8 +22,8 @@ __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh
 __global__ void k_state_init(int n, int L, Topo T, State S);
 
 // okr_persist.cu
-__global__ void __launch_bounds__(512, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb);
-__global__ void k_final_maxerr(Topo T, State S, Search X, const Ctrl *C);
+cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st);
+int search_blocks_per_sm();     // CTAs of the search kernel that fit one SM (0 on error)
 __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);
 
 }  // namespace okr

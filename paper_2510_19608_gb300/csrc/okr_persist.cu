@@ -1,10 +1,11 @@
 // okr_persist.cu -- the exhaustive search (Algorithm 1, Sec. IV) as one
 // persistent cooperative kernel, one CTA per SM, three grid barriers per
-// iteration:
+// iteration (four when an FP64 recheck is needed):
 //
 //   phase 1  select + commit of the last sweep (argmin with the tie band, then
 //            the merge), fused with the candidate setup of the next sweep
-//   phase 2  candidate compaction, work positions, chunk map, super-node list
+//   phase 2  candidate compaction, work positions, chunk map, super-node list,
+//            bookkeeping of the merge
 //   phase 3  sweep: the score change of every candidate
 //
 // Candidate evaluation.  The paper evaluates a candidate (s, r) by moving the
@@ -37,6 +38,17 @@
 // warp scan, then the pieces of a candidate in chunk order), so results do not
 // depend on timing.
 //
+// Precision.  precision 0 scores every candidate in FP64.  precision 1 screens
+// every candidate in FP32 with a rigorous bound B(c) on the distance between the
+// screened score and the FP64 one (and a bound on the screened largest MICE), then
+//   U = min over surely feasible candidates of D32(c) + B(c),
+//   R = { c not surely infeasible : D32(c) - B(c) <= U + tau }.
+// The FP64 minimum and every candidate of its tie band lie in R.  When R holds
+// one surely feasible candidate, it is the FP64 winner; otherwise R is scored
+// again in FP64 and the selection runs on those scores.  The merge itself is
+// always applied in FP64, so the state carried between iterations is FP64 in
+// both modes and the FP32 copies are refreshed from it.
+//
 // Memory written by other CTAs during the kernel is read with L2-coherent loads
 // (ld.global.cg); the static feeder description with ordinary loads.
 #include "okr_internal.cuh"
@@ -50,6 +62,8 @@ constexpr int kThreads = 512;
 __device__ __forceinline__ int ldi(const int *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldd(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ double2 ldz(const double2 *p) { return __ldcg(p); }
+__device__ __forceinline__ float ldf(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ldf2(const float2 *p) { return __ldcg(p); }
 __device__ __forceinline__ Cand ldcand(const Cand *p) {
     Cand c;
     const int4 *q = reinterpret_cast<const int4 *>(p);
@@ -63,37 +77,44 @@ __device__ __forceinline__ Cand ldcand(const Cand *p) {
 static_assert(sizeof(Cand) == 48, "Cand layout");
 
 // ---------------------------------------------------------------- grid barrier
-// Sense by generation: thread 0 of each CTA arrives on the counter; the last
-// arrival resets it and bumps the generation; the others wait for the bump.
-// Every wait is bounded: after max_spins polls the CTA records err = 6 and the
-// kernel unwinds (all CTAs leave at their next barrier or error check).
-__device__ bool grid_barrier(GridBar *gb, Ctrl *C, unsigned nblocks) {
+// The arrival counter only grows: barrier number k (counted per CTA) completes
+// when it reaches k * gridDim.x.  Thread 0 of each CTA publishes the CTA's
+// writes (fence, then the arrival) and polls with acquire loads.  Every wait is
+// bounded: after max_spins polls the CTA records err = 6 and the kernel unwinds
+// (each CTA leaves at its next barrier, whose wait also ends on the error flag).
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ bool grid_barrier(GridBar *gb, Ctrl *C, unsigned nblocks, unsigned &epoch) {
     __shared__ int s_ok;
     __syncthreads();
+    epoch += 1;
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &gb->gen;
-        const unsigned my = *gen;
+        const unsigned target = epoch * nblocks;
         __threadfence();
-        const unsigned arrived = atomicAdd(&gb->count, 1u);
+        atomicAdd(&gb->count, 1u);
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            atomicExch(&gb->count, 0u);
-            __threadfence();
-            atomicAdd(&gb->gen, 1u);
-        } else {
-            long long spins = 0;
-            const long long lim = C->max_spins;
-            while (*gen == my) {
-                if (++spins > lim || *(volatile int *)&C->err) { ok = 0; break; }
-                __nanosleep(32);
-            }
-            if (!ok) atomicCAS(&C->err, 0, 6);
+        long long spins = 0;
+        const long long lim = C->max_spins;
+        while (ld_acquire(&gb->count) < target) {
+            if (++spins > lim || *(volatile int *)&C->err) { ok = 0; break; }
+            __nanosleep(20);
         }
+        if (!ok) atomicCAS(&C->err, 0, 6);
         __threadfence();
         s_ok = ok;
     }
     __syncthreads();
     return s_ok;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 // ---------------------------------------------------------------- small helpers
@@ -172,21 +193,22 @@ __device__ int2 block_scan2(int2 v, int2 *smem, int2 *tot) {
     return make_int2(smem[wid].x + inc.x - v.x, smem[wid].y + inc.y - v.y);
 }
 
+
 // ---------------------------------------------------------------- one work item
-// Scenario l, phase p of the cluster of super-node k for candidate cd: the
-// cluster's new voltage on that phase and its largest member error
-// max(hi - |V|, |V| - lo) (merged extremes when the cluster is s's).  k < 0
+// Scenario l, phase p of the cluster of super-node k for candidate cd.  k < 0
 // stands for s's cluster when s is the common ancestor (no voltage change).
-struct ItemOut {
-    double e;
-    double2 v;
-    bool on;
+struct Item64 {
+    double e;       // largest member error max(hi - |V|, |V| - lo), merged extremes for s
+    double m;       // |V|
+    double2 v;      // new voltage
+    bool on;        // phase present
 };
 
-__device__ __forceinline__ ItemOut eval_item(const Topo &T, const State &S, int n, const Cand &cd, int k, bool sside,
-                                             int l, int p, const double2 *Ir, unsigned phr) {
-    ItemOut o;
+__device__ __forceinline__ Item64 eval_item64(const Topo &T, const State &S, int n, const Cand &cd, int k, bool sside,
+                                              int l, int p, const double2 *Ir, unsigned phr) {
+    Item64 o;
     o.e = 0.0;
+    o.m = 0.0;
     o.v = make_double2(0.0, 0.0);
     o.on = false;
     const int kk = k < 0 ? cd.s : k;
@@ -211,24 +233,329 @@ __device__ __forceinline__ ItemOut eval_item(const Topo &T, const State &S, int 
         lo = fmin(lo, ldd(S.lo + sidx(l, p, cd.r, n)));
     }
     o.e = fmax(h - mag, mag - lo);
+    o.m = mag;
     o.v = v;
     o.on = true;
     return o;
 }
 
-__device__ __forceinline__ double item_flops(const Topo &T, const Cand &cd, int k, unsigned phr) {
-    // per (scenario, phase): per phase of r a complex subtraction and a complex
-    // multiply-add; the voltage update, |V|, two differences, two maxima
-    return k < 0 ? 8.0 : 10.0 * __popc(phr) + 10.0;
+// Single-precision screen of the same item with a bound b on |e32 - e64|.
+// With u = 2^-24 and S = sum_q |G_pq| |I_q| (1-norms of the complex numbers):
+//   G from the split path impedances: relative error <= 3u; I rounded: u;
+//   products and sums: <= 4u S, so |dV32 - dV| <= 8u S;
+//   delta = |V + dV| - |V| = (2 Re(conj V dV) + |dV|^2) / (|V + dV| + |V|):
+//     numerator error <= u (23 |V|_1 + 3 |V|_1 + 11 |V|_1 + 11 S) S,
+//     denominator relative error <= 4u, division u;
+//   e = max(hr - delta, delta - lr) with hr, lr rounded from FP64 differences.
+// The constants below round these up (40 for the numerator, 8 |delta|) and the
+// whole bound carries a factor 1.5 and an additive 4e-15 for the FP64 path's own
+// rounding.  Merged extremes of s and r add the rounding of the shift
+// |V_r| - |V_s| and of the shifted extremes.
+struct Item32 {
+    float e, b;
+};
+
+constexpr float kU = 5.9604645e-08f;    // 2^-24
+
+__device__ __forceinline__ Item32 eval_item32(const Topo &T, const State &S, int n, const Cand &cd, int k, bool sside,
+                                              int l, int p, const float2 *Ir, unsigned phr, float &flops) {
+    Item32 o;
+    o.e = 0.0f;
+    o.b = 0.0f;
+    const int kk = k < 0 ? cd.s : k;
+    if (!(T.ph[kk] >> p & 1u)) return o;
+    const size_t ik = sidx(l, p, kk, n);
+    float hr = ldf(S.hr32 + ik), lr = ldf(S.lr32 + ik);
+    float bx = 0.0f;
+    if (kk == cd.s && (T.ph[cd.r] >> p & 1u)) {
+        const size_t ir = sidx(l, p, cd.r, n);
+        const float dr = (float)(ldd(S.mcur + ir) - ldd(S.mcur + ik));
+        const float hrr = ldf(S.hr32 + ir) + dr, lrr = ldf(S.lr32 + ir) + dr;
+        hr = fmaxf(hr, hrr);
+        lr = fminf(lr, lrr);
+        bx = 2.0f * kU * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
+    }
+    float delta = 0.0f, bd = 0.0f;
+    if (k >= 0) {
+        const float2 v = ldf2(S.v32 + ik);
+        const int y = T.lca[(size_t)(sside ? cd.s : cd.r) * n + k];
+        const float2 *zhy = T.zh + (size_t)y * 9 + p * 3, *zly = T.zlo + (size_t)y * 9 + p * 3;
+        const float2 *zha = T.zh + (size_t)cd.a * 9 + p * 3, *zla = T.zlo + (size_t)cd.a * 9 + p * 3;
+        float2 dv = make_float2(0.0f, 0.0f);
+        float sdv = 0.0f;
+        for (int q = 0; q < 3; ++q) {
+            if (!(phr >> q & 1u)) continue;
+            float gx = (zhy[q].x - zha[q].x) + (zly[q].x - zla[q].x);
+            float gy = (zhy[q].y - zha[q].y) + (zly[q].y - zla[q].y);
+            if (!sside) { gx = -gx; gy = -gy; }
+            dv.x = fmaf(gx, Ir[q].x, fmaf(-gy, Ir[q].y, dv.x));
+            dv.y = fmaf(gx, Ir[q].y, fmaf(gy, Ir[q].x, dv.y));
+            sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(Ir[q].x) + fabsf(Ir[q].y), sdv);
+        }
+        const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
+        const float wx = v.x + dv.x, wy = v.y + dv.y;
+        const float mv = sqrtf(v.x * v.x + v.y * v.y);
+        const float den = sqrtf(wx * wx + wy * wy) + mv;
+        delta = num / den;
+        const float v1 = fabsf(v.x) + fabsf(v.y);
+        bd = kU * (40.0f * (v1 + sdv) * sdv / den + 8.0f * fabsf(delta));
+        flops += 10.0f * __popc(phr) + 14.0f;
+    }
+    o.e = fmaxf(hr - delta, delta - lr);
+    o.b = 1.5f * (kU * (fabsf(hr) + fabsf(lr) + fabsf(o.e)) + bd) + bx + 4e-15f;
+    return o;
+}
+
+// ---------------------------------------------------------------- chunk scoring
+// One warp scores PPW consecutive positions.  Per lane: `ci` the candidate slot
+// its position belongs to (used for the partial-sum slot g + ci, the arrival
+// counter and the outputs), `cd` the candidate, `q` the position inside the
+// candidate, `first` the candidate's first chunk, `np` its chunk count.  Lanes of
+// a position reduce over phases (xor 1, 2), then over scenarios (xor 4, 8); the
+// lanes of a candidate reduce with a segmented scan in lane order; the last lane
+// of a segment stores the piece and the writer of the last piece sums the
+// pieces in order.
+__device__ __forceinline__ void seg_scan_setup(bool active, int ci, int lane, unsigned &heads, int &seg_start,
+                                               bool &last) {
+    const int cseg = active ? ci : -1 - lane;
+    const int prev = __shfl_up_sync(0xffffffffu, cseg, 1);
+    const bool head = (lane == 0) || (prev != cseg);
+    heads = __ballot_sync(0xffffffffu, head);
+    seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+    last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+}
+
+__device__ void score64_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
+                              bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
+                              double margin, double *out_score, int *out_feas, bool prof, double &flops) {
+    const int lane = threadIdx.x & 31, sub = lane % SP, l = sub >> 2, p = sub & 3;
+    int k = cd.r;
+    bool sside = false;
+    if (active) k = position_bus(list, cd, q, sside);
+    const bool valid = active && k != cd.r;
+    Item64 o;
+    o.e = 0.0;
+    o.on = false;
+    if (valid && l < L && p < 3) {
+        double2 Ir[3];
+        for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldz(S.icur + sidx(l, qq, cd.r, n));
+        o = eval_item64(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r]);
+        if (prof && o.on) flops += (k < 0) ? 8.0 : 10.0 * __popc(T.ph[cd.r]) + 10.0;
+    }
+    double m = o.e;
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    double dl = 0.0, ml = 0.0;
+    if (valid && p == 0 && l < L) {
+        const int kk = k < 0 ? cd.s : k;
+        dl = m - ldd(S.mice + (size_t)l * n + kk);
+        if (kk == cd.s) dl -= ldd(S.mice + (size_t)l * n + cd.r);
+        ml = m;
+    }
+    for (int o2 = 4; o2 < SP; o2 <<= 1) {
+        dl += __shfl_xor_sync(0xffffffffu, dl, o2);
+        ml = fmax(ml, __shfl_xor_sync(0xffffffffu, ml, o2));
+    }
+    if (sub != 0) { dl = 0.0; ml = 0.0; }
+    unsigned heads;
+    int seg_start;
+    bool last;
+    seg_scan_setup(active, ci, lane, heads, seg_start, last);
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, dl, o2);
+        const double z = __shfl_up_sync(0xffffffffu, ml, o2);
+        if (lane - o2 >= seg_start) { dl += y; ml = fmax(ml, z); }
+    }
+    if (active && last) {
+        X.partial[g + ci] = make_double2(dl, ml);
+        __threadfence();
+        if (atomicAdd(X.arrive + ci, 1) == np - 1) {
+            __threadfence();
+            double sum = 0.0, mx = 0.0;
+            for (int j = 0; j < np; ++j) {
+                const double2 pj = ldz(X.partial + first + ci + j);
+                sum += pj.x;
+                mx = fmax(mx, pj.y);
+            }
+            out_score[ci] = sum;
+            out_feas[ci] = (mx <= margin);
+            X.arrive[ci] = 0;
+        }
+    }
+}
+
+// FP32 screen of a chunk (precision 1).  Pieces hold (D32, bound, max MICE,
+// bound of the max); the final bound adds 32u sum |piece| for the rounding of
+// the FP32 sums.
+__device__ void score32_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
+                              bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
+                              bool prof, double &flops) {
+    const int lane = threadIdx.x & 31, sub = lane % SP, l = sub >> 2, p = sub & 3;
+    int k = cd.r;
+    bool sside = false;
+    if (active) k = position_bus(list, cd, q, sside);
+    const bool valid = active && k != cd.r;
+    Item32 o;
+    o.e = 0.0f;
+    o.b = 0.0f;
+    float fl = 0.0f;
+    if (valid && l < L && p < 3) {
+        float2 Ir[3];
+        for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldf2(S.icur32 + sidx(l, qq, cd.r, n));
+        o = eval_item32(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r], fl);
+    }
+    if (prof) flops += fl;
+    float m = o.e, bm = o.b;
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 1));
+    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
+    float dl = 0.0f, bl = 0.0f, ad = 0.0f, ml = 0.0f, bml = 0.0f;
+    if (valid && p == 0 && l < L) {
+        const int kk = k < 0 ? cd.s : k;
+        const float mo = ldf(S.mice32 + (size_t)l * n + kk);
+        const float mr = (kk == cd.s) ? ldf(S.mice32 + (size_t)l * n + cd.r) : 0.0f;
+        dl = (m - mo) - mr;
+        bl = bm + 2.0f * kU * (fabsf(mo) + fabsf(mr) + fabsf(m));
+        ad = fabsf(dl);
+        ml = m;
+        bml = bm;
+    }
+    for (int o2 = 4; o2 < SP; o2 <<= 1) {
+        dl += __shfl_xor_sync(0xffffffffu, dl, o2);
+        bl += __shfl_xor_sync(0xffffffffu, bl, o2);
+        ad += __shfl_xor_sync(0xffffffffu, ad, o2);
+        ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o2));
+        bml = fmaxf(bml, __shfl_xor_sync(0xffffffffu, bml, o2));
+    }
+    if (sub != 0) { dl = bl = ad = ml = bml = 0.0f; }
+    unsigned heads;
+    int seg_start;
+    bool last;
+    seg_scan_setup(active, ci, lane, heads, seg_start, last);
+    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+        const float y1 = __shfl_up_sync(0xffffffffu, dl, o2);
+        const float y2 = __shfl_up_sync(0xffffffffu, bl, o2);
+        const float y3 = __shfl_up_sync(0xffffffffu, ad, o2);
+        const float y4 = __shfl_up_sync(0xffffffffu, ml, o2);
+        const float y5 = __shfl_up_sync(0xffffffffu, bml, o2);
+        if (lane - o2 >= seg_start) { dl += y1; bl += y2; ad += y3; ml = fmaxf(ml, y4); bml = fmaxf(bml, y5); }
+    }
+    if (active && last) {
+        float4 *pf = reinterpret_cast<float4 *>(X.partial);
+        pf[g + ci] = make_float4(dl, bl + 32.0f * kU * ad, ml, bml);
+        __threadfence();
+        if (atomicAdd(X.arrive + ci, 1) == np - 1) {
+            __threadfence();
+            float sum = 0.0f, bsum = 0.0f, asum = 0.0f, mx = 0.0f, bmx = 0.0f;
+            for (int j = 0; j < np; ++j) {
+                const float4 pj = __ldcg(pf + first + ci + j);
+                sum += pj.x;
+                bsum += pj.y;
+                asum += fabsf(pj.x);
+                mx = fmaxf(mx, pj.z);
+                bmx = fmaxf(bmx, pj.w);
+            }
+            X.scr[ci] = make_float4(sum, 1.001f * (bsum + 32.0f * kU * asum), mx, bmx);
+            X.arrive[ci] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- selection
+// Exact selection over m entries with FP64 scores (entry i is candidate
+// map ? map[i] : i): minimum over feasible entries, tie band [min, min + tau],
+// smallest (r, s) inside it.  Identical in every CTA.
+struct Sel {
+    int w;          // winning candidate (-1: nothing feasible)
+    double gap;     // distance of the next score above the tie band
+};
+
+__device__ Sel select_exact(const Search &X, int m, const int *map, const double *score, const int *feas, double tau,
+                            double *smd, unsigned long long *smu, int *smi) {
+    const int tid = threadIdx.x;
+    double best = INFINITY;
+    for (int i = tid; i < m; i += kThreads)
+        if (ldi(feas + i)) best = fmin(best, ldd(score + i));
+    best = block_reduce(best, MinD(), smd);
+    Sel out;
+    out.w = -1;
+    out.gap = INFINITY;
+    if (best == INFINITY) return out;
+    const double edge = best + tau;
+    unsigned long long key = ~0ull;
+    double gap = INFINITY;
+    for (int i = tid; i < m; i += kThreads) {
+        if (!ldi(feas + i)) continue;
+        const double d = ldd(score + i);
+        if (d <= edge) {
+            const unsigned long long k = ldcand(X.cand + (map ? map[i] : i)).key;
+            if (k < key) key = k;
+        } else {
+            gap = fmin(gap, d - edge);
+        }
+    }
+    key = block_reduce(key, MinU(), smu);
+    gap = block_reduce(gap, MinD(), smd);
+    int w = 0x7fffffff;
+    for (int i = tid; i < m; i += kThreads)
+        if (ldi(feas + i) && ldd(score + i) <= edge && ldcand(X.cand + (map ? map[i] : i)).key == key) w = min(w, i);
+    w = block_reduce(w, MinI(), smi);
+    out.w = (w < m) ? (map ? map[w] : w) : -2;
+    out.gap = gap;
+    return out;
+}
+
+constexpr int kRmax = 1024;     // candidates an FP64 recheck can hold in shared memory
+
+// Screen selection (precision 1): U, then R in candidate order into s_R.
+// Returns the size of R (may exceed kRmax; then s_R is incomplete) and the
+// screen margin below the band: the smallest D32 - B - (U + tau) over the
+// candidates left out of R.
+__device__ int screen_select(const Search &X, int nc, double margin, double tau, int *s_R, int2 *sm2, double *smd,
+                             double &gap) {
+    const int tid = threadIdx.x;
+    double U = INFINITY;
+    for (int c = tid; c < nc; c += kThreads) {
+        const float4 q = __ldcg(X.scr + c);
+        if ((double)q.z + (double)q.w <= margin) U = fmin(U, (double)q.x + (double)q.y);
+    }
+    U = block_reduce(U, MinD(), smd);
+    const double edge = U + tau;
+    int nR = 0;
+    double g = INFINITY;
+    for (int c0 = 0; c0 < nc; c0 += kThreads) {
+        const int c = c0 + tid;
+        int flag = 0;
+        if (c < nc) {
+            const float4 q = __ldcg(X.scr + c);
+            const bool maybe = (double)q.z - (double)q.w <= margin;
+            if (maybe) {
+                const double lo = (double)q.x - (double)q.y;
+                if (lo <= edge) flag = 1;
+                else g = fmin(g, lo - edge);
+            }
+        }
+        int2 tot;
+        const int2 ex = block_scan2(make_int2(flag, 0), sm2, &tot);
+        if (flag && nR + ex.x < kRmax) s_R[nR + ex.x] = c;
+        nR += tot.x;
+    }
+    gap = block_reduce(g, MinD(), smd);
+    __syncthreads();
+    return nR;
 }
 
 // ---------------------------------------------------------------- the kernel
+template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb) {
     __shared__ double smd[32];
     __shared__ unsigned long long smu[32];
     __shared__ int smi[32];
     __shared__ int2 sm2[33];
     __shared__ int2 s_pref, s_tot;
+    __shared__ int s_R[kRmax];
+    __shared__ int s_Rbase[kRmax + 1];
     const int n = T.n, L = T.L;
     const int Lp = L <= 1 ? 1 : (L <= 2 ? 2 : 4);
     const int SP = 4 * Lp, PPW = 32 / SP;
@@ -240,139 +567,217 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
     const int max_merges = C->max_merges;
     const bool prof = C->profile != 0;
     const bool lead = (blockIdx.x == 0 && tid == 0);
+    unsigned epoch = 0;
     int t = C->t, ns = C->n_super;
-    double s_cur = C->s_cur;
+    double s_cur = C->s_cur;               // SMICE of the committed state
     bool have = false;                     // a sweep's scores wait for selection
     int nc = 0, P = 0, nchunks = 0;        // current candidate list
     int2 my_ex = make_int2(0, 0);          // this thread's offsets inside its CTA
     double flops = 0.0;
+    int nw_commit = 0;                     // warps that held items of the last commit
     if (t >= max_merges || C->done) return;
 
     for (;;) {
         // ============================================================ phase 1
+        s_cur = ldd(&C->s_cur);                // updated by one thread in the last phase 2
+        unsigned long long tp = (prof && lead) ? gtimer() : 0;
+        auto stamp = [&](int i) {
+            if (prof && lead) { const unsigned long long now = gtimer(); C->phase_ns[i] += now - tp; tp = now; }
+        };
         const int told = t;
         const int *list_old = S.sn_list[told & 1];
-        bool committed = false;
+        bool committed = false, finishing = false;
         int r0 = -1, s0 = -1, dir0 = 0, jr0 = 0;
         if (have) {
-            // ---- selection (identical in every CTA)
-            double best = INFINITY;
-            for (int c = tid; c < nc; c += kThreads)
-                if (ldi(X.feas + c)) best = fmin(best, ldd(X.score + c));
-            best = block_reduce(best, MinD(), smd);
-            const bool rec = lead && t < X.rec_iters;
-            if (best == INFINITY) {
+            Sel sel;
+            bool full64 = (PREC == 0);
+            if (PREC == 1) {
+                double sgap = INFINITY;
+                const int nR = screen_select(X, nc, margin, tau, s_R, sm2, smd, sgap);
+                stamp(0);
                 if (blockIdx.x == 0 && t < X.rec_iters) {
                     for (int c = tid; c < nc; c += kThreads) {
-                        const Cand cd = ldcand(X.cand + c);
-                        X.rec_s[(size_t)t * 2 * n + c] = T.orig[cd.s];
-                        X.rec_r[(size_t)t * 2 * n + c] = T.orig[cd.r];
-                        X.rec_score[(size_t)t * 2 * n + c] = INFINITY;
+                        const Cand cc = ldcand(X.cand + c);
+                        const float4 q = __ldcg(X.scr + c);
+                        const bool out = (double)q.z - (double)q.w > margin;
+                        X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
+                        X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
+                        X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : s_cur + (double)q.x;
+                        X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
                     }
                 }
-                if (lead) {
-                    if (t < X.rec_iters) X.rec_count[t] = nc;
-                    C->done = 1; C->stop_reason = 1; C->t = t; C->s_cur = s_cur; C->n_super = ns;
-                }
-                break;
-            }
-            const double edge = best + tau;
-            unsigned long long key = ~0ull;
-            double gap = INFINITY;
-            for (int c = tid; c < nc; c += kThreads) {
-                if (!ldi(X.feas + c)) continue;
-                const double d = ldd(X.score + c);
-                if (d <= edge) {
-                    const unsigned long long k = ldcand(X.cand + c).key;
-                    if (k < key) key = k;
+                if (nR == 0) {
+                    sel.w = -1;
+                } else if (nR == 1 && [&] { const float4 q = __ldcg(X.scr + s_R[0]);
+                                            return (double)q.z + (double)q.w <= margin; }()) {
+                    sel.w = s_R[0];
+                    sel.gap = sgap;
+                } else if (nR <= kRmax) {
+                    // FP64 recheck of R: positions of R back to back
+                    for (int i0 = 0; i0 < nR; i0 += kThreads) {
+                        const int i = i0 + tid;
+                        const int cnt = i < nR ? cand_positions(ldcand(X.cand + s_R[i])) : 0;
+                        int2 tot;
+                        const int2 ex = block_scan2(make_int2(cnt, 0), sm2, &tot);
+                        const int off = (i0 == 0) ? 0 : s_Rbase[i0];
+                        __syncthreads();
+                        if (i < nR) s_Rbase[i] = off + ex.x;
+                        if (tid == 0) s_Rbase[min(i0 + kThreads, nR)] = off + tot.x;
+                        __syncthreads();
+                    }
+                    const int PR = s_Rbase[nR];
+                    const int rchunks = (PR + PPW - 1) / PPW;
+                    const int *list = S.sn_list[t & 1];
+                    for (int g = warp; g < rchunks; g += nwarps) {
+                        const int q = g * PPW + lane / SP;
+                        const bool active = q < PR;
+                        int lo = 0, hi = nR - 1;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (s_Rbase[mid] <= q) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        const Cand cd = ldcand(X.cand + s_R[lo]);
+                        const int b0 = s_Rbase[lo], cnt = s_Rbase[lo + 1] - b0;
+                        const int first = b0 / PPW, np = (b0 + cnt - 1) / PPW - first + 1;
+                        score64_chunk(T, S, X, n, L, SP, g, active, lo, cd, q - b0, first, np, list, margin,
+                                      X.score, X.feas, false, flops);
+                    }
+                    if (lead) { C->rechecks += 1; C->recheck_cands += nR; }
+                    if (!grid_barrier(gb, C, G, epoch)) return;
+                    sel = select_exact(X, nR, s_R, X.score, X.feas, tau, smd, smu, smi);
+                    stamp(1);
                 } else {
-                    gap = fmin(gap, d - edge);
+                    full64 = true;                      // R too large: rescore everything in FP64
+                    if (lead) { C->rechecks += 1; C->recheck_cands += nc; }
+                }
+                if (full64) {
+                    const int *list = S.sn_list[t & 1];
+                    for (int g = warp; g < nchunks; g += nwarps) {
+                        const int c0 = ldi(X.chunk_first + g);
+                        const int q = g * PPW + lane / SP;
+                        const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;
+                        int off = 0;
+                        for (int j = 1; j < 32; ++j) off += (__shfl_sync(0xffffffffu, cb, j) <= q);
+                        const int cbase = __shfl_sync(0xffffffffu, cb, off);
+                        const int c = c0 + off;
+                        const bool active = q < P;
+                        Cand cd;
+                        cd.r = -1;
+                        int first = 0, np = 1;
+                        if (active) {
+                            cd = ldcand(X.cand + c);
+                            first = cbase / PPW;
+                            np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
+                        }
+                        score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin,
+                                      X.score, X.feas, false, flops);
+                    }
+                    if (!grid_barrier(gb, C, G, epoch)) return;
                 }
             }
-            key = block_reduce(key, MinU(), smu);
-            gap = block_reduce(gap, MinD(), smd);
-            int w = 0x7fffffff;
-            for (int c = tid; c < nc; c += kThreads)
-                if (ldi(X.feas + c) && ldd(X.score + c) <= edge && ldcand(X.cand + c).key == key) w = min(w, c);
-            w = block_reduce(w, MinI(), smi);
-            if (w >= nc) {                              // unreachable: the minimum lies in the band
+            if (full64) {
+                if (PREC == 0 && blockIdx.x == 0 && t < X.rec_iters) {
+                    for (int c = tid; c < nc; c += kThreads) {
+                        const Cand cc = ldcand(X.cand + c);
+                        X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
+                        X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
+                        X.rec_score[(size_t)t * 2 * n + c] = ldi(X.feas + c) ? s_cur + ldd(X.score + c) : INFINITY;
+                        X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
+                    }
+                }
+                sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi);
+                stamp(PREC == 0 ? 0 : 1);
+            }
+            if (lead && t < X.rec_iters) X.rec_count[t] = nc;
+            if (sel.w == -2) {                          // unreachable: the minimum lies in the band
                 if (lead) { C->err = 5; C->done = 1; }
                 break;
             }
-            const Cand cd = ldcand(X.cand + w);
-            const double dw = ldd(X.score + w);
-            if (blockIdx.x == 0 && t < X.rec_iters) {
-                for (int c = tid; c < nc; c += kThreads) {
-                    const Cand cc = ldcand(X.cand + c);
-                    X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
-                    X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
-                    X.rec_score[(size_t)t * 2 * n + c] = ldi(X.feas + c) ? s_cur + ldd(X.score + c) : INFINITY;
-                }
+            if (sel.w < 0) {                            // nothing feasible
+                if (lead) { C->done = 1; C->stop_reason = 1; C->t = t; C->s_cur = s_cur; C->n_super = ns; }
+                break;
             }
-            // ---- commit: r's cluster joins s
+
+            // ---- commit in FP64: r's cluster joins s
+            const Cand cd = ldcand(X.cand + sel.w);
             const unsigned phr = T.ph[cd.r];
             for (int i = gt; i < n; i += gs)
                 if (ldi(S.label + i) == cd.r) S.label[i] = cd.s;
             const int nitems = cand_positions(cd) * SP;
+            double acc = 0.0;
             for (int i0 = warp * 32; i0 < nitems; i0 += nwarps * 32) {
                 const int item = i0 + lane;
                 const int q = item / SP, sub = item % SP, l = sub >> 2, p = sub & 3;
                 bool sside = false;
                 const int k = item < nitems ? position_bus(list_old, cd, q, sside) : cd.r;
                 const bool live = item < nitems && l < L && p < 3 && k != cd.r;
-                ItemOut o;
-                o.e = 0.0; o.on = false;
+                const int kk = k < 0 ? cd.s : k;
+                Item64 o;
+                o.e = 0.0;
+                o.on = false;
                 if (live) {
                     double2 Ir[3];
                     for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldz(S.icur + sidx(l, qq, cd.r, n));
-                    o = eval_item(T, S, n, cd, k, sside, l, p, Ir, phr);
+                    o = eval_item64(T, S, n, cd, k, sside, l, p, Ir, phr);
                 }
                 double m = o.e;
                 m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
                 m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
-                if (live) {
-                    const int kk = k < 0 ? cd.s : k;
-                    if (o.on) {
-                        S.vcur[sidx(l, p, kk, n)] = o.v;
-                        if (kk == cd.s) {
-                            S.hi[sidx(l, p, kk, n)] = fmax(ldd(S.hi + sidx(l, p, kk, n)), ldd(S.hi + sidx(l, p, cd.r, n)));
-                            S.lo[sidx(l, p, kk, n)] = fmin(ldd(S.lo + sidx(l, p, kk, n)), ldd(S.lo + sidx(l, p, cd.r, n)));
-                        }
+                if (live && o.on) {
+                    const size_t ik = sidx(l, p, kk, n);
+                    double h = ldd(S.hi + ik), lo = ldd(S.lo + ik);
+                    if (kk == cd.s) {
+                        h = fmax(h, ldd(S.hi + sidx(l, p, cd.r, n)));
+                        lo = fmin(lo, ldd(S.lo + sidx(l, p, cd.r, n)));
+                        S.hi[ik] = h;
+                        S.lo[ik] = lo;
                     }
-                    if (p == 0) S.mice[(size_t)l * n + kk] = m;
+                    S.vcur[ik] = o.v;
+                    S.mcur[ik] = o.m;
+                    S.v32[ik] = make_float2((float)o.v.x, (float)o.v.y);
+                    S.hr32[ik] = (float)(h - o.m);
+                    S.lr32[ik] = (float)(lo - o.m);
+                }
+                if (live && p == 0) {
+                    const double mold = ldd(S.mice + (size_t)l * n + kk);
+                    double d = m - mold;
+                    if (kk == cd.s) d -= ldd(S.mice + (size_t)l * n + cd.r);
+                    acc += d;
+                    S.mice[(size_t)l * n + kk] = m;
+                    S.mice32[(size_t)l * n + kk] = (float)m;
                 }
             }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
+            nw_commit = min(nwarps, (nitems + 31) / 32);
+            if (lane == 0 && warp < nw_commit) X.wsum[warp] = acc;
             if (lead) {
-                for (int l = 0; l < L; ++l) {
+                for (int l = 0; l < L; ++l)
                     for (int q = 0; q < 3; ++q)
-                        if (phr >> q & 1u)
-                            S.icur[sidx(l, q, cd.s, n)] = cadd(ldz(S.icur + sidx(l, q, cd.s, n)), ldz(S.icur + sidx(l, q, cd.r, n)));
-                    S.mice[(size_t)l * n + cd.r] = 0.0;
-                }
+                        if (phr >> q & 1u) {
+                            const size_t is = sidx(l, q, cd.s, n);
+                            const double2 ni = cadd(ldz(S.icur + is), ldz(S.icur + sidx(l, q, cd.r, n)));
+                            S.icur[is] = ni;
+                            S.icur32[is] = make_float2((float)ni.x, (float)ni.y);
+                        }
                 if (cd.dir == 1) S.top[cd.s] = ldi(S.top + cd.r);
                 X.dec_s[t] = T.orig[cd.s];
                 X.dec_r[t] = T.orig[cd.r];
-                X.dec_score[t] = s_cur + dw;
-                X.dec_gap[t] = gap;
+                X.dec_gap[t] = sel.gap;
                 X.dec_ncand[t] = nc;
-                if (rec) X.rec_count[t] = nc;
             }
+            stamp(2);
             committed = true;
             r0 = cd.r; s0 = cd.s; dir0 = cd.dir;
             jr0 = ldi(S.sn_rank + r0);
             t += 1;
-            s_cur += dw;
             ns -= 1;
-            if (lead) { C->t = t; C->s_cur = s_cur; C->n_super = ns; }
-            if (t >= max_merges) {
-                if (lead) { C->done = 1; C->stop_reason = 0; }
-                break;
-            }
+            finishing = (t >= max_merges);
         }
 
         // ---- candidate setup for the next sweep (reads adjusted for the merge
         // committed above: label r -> s, rank drops past r, s's top)
-        {
+        if (!finishing) {
             int2 mine = make_int2(0, 0);
             const int j = gt;
             Cand c0, c1;
@@ -417,31 +822,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             my_ex = block_scan2(mine, sm2, &tot);
             if (tid == 0) X.block_tot[blockIdx.x] = tot;
         }
-        if (!grid_barrier(gb, C, G)) return;
+        stamp(3);
+        if (!grid_barrier(gb, C, G, epoch)) return;
+        stamp(4);
 
         // ============================================================ phase 2
-        if (tid < 32) {
-            int2 acc = make_int2(0, 0), all = make_int2(0, 0);
-            for (int b = lane; b < (int)G; b += 32) {
-                const int2 v = __ldcg(X.block_tot + b);
-                if (b < (int)blockIdx.x) { acc.x += v.x; acc.y += v.y; }
-                all.x += v.x;
-                all.y += v.y;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-                all.x += __shfl_xor_sync(0xffffffffu, all.x, o);
-                all.y += __shfl_xor_sync(0xffffffffu, all.y, o);
-            }
-            if (lane == 0) { s_pref = acc; s_tot = all; }
-        }
-        __syncthreads();
-        const int2 pref = s_pref, tot = s_tot;
-        nc = tot.x;
-        P = tot.y;
-        nchunks = (P + PPW - 1) / PPW;
         if (committed) {
+            // exact score change of the merge, in warp order (CTA 0, warp 0)
+            if (blockIdx.x == 0 && tid < 32) {
+                double d = 0.0;
+                for (int w2 = lane; w2 < nw_commit; w2 += 32) d += ldd(X.wsum + w2);
+                for (int o2 = 16; o2 > 0; o2 >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o2);
+                if (lane == 0) {
+                    s_cur += d;
+                    X.dec_score[told] = s_cur;
+                    for (int l = 0; l < L; ++l) {
+                        S.mice[(size_t)l * n + r0] = 0.0;
+                        S.mice32[(size_t)l * n + r0] = 0.0f;
+                    }
+                    C->t = t;
+                    C->s_cur = s_cur;
+                    C->n_super = ns;
+                }
+            }
             // super-node list after the merge (other buffer), ranks, largest MICE
             int *list_new = S.sn_list[t & 1];
             double m = 0.0;
@@ -455,6 +858,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             if (tid == 0 && m > 0.0)
                 atomicMax((unsigned long long *)&X.dec_maxerr[told], (unsigned long long)__double_as_longlong(m));
         }
+        if (finishing) {
+            if (lead) { C->done = 1; C->stop_reason = 0; }
+            break;
+        }
+        if (tid < 32) {
+            int2 acc = make_int2(0, 0), all = make_int2(0, 0);
+            for (int b = lane; b < (int)G; b += 32) {
+                const int2 v = __ldcg(X.block_tot + b);
+                if (b < (int)blockIdx.x) { acc.x += v.x; acc.y += v.y; }
+                all.x += v.x;
+                all.y += v.y;
+            }
+            for (int o2 = 16; o2 > 0; o2 >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o2);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o2);
+                all.x += __shfl_xor_sync(0xffffffffu, all.x, o2);
+                all.y += __shfl_xor_sync(0xffffffffu, all.y, o2);
+            }
+            if (lane == 0) { s_pref = acc; s_tot = all; }
+        }
+        __syncthreads();
+        const int2 pref = s_pref, tot = s_tot;
+        nc = tot.x;
+        P = tot.y;
+        nchunks = (P + PPW - 1) / PPW;
         if (nc == 0) {                                  // no candidate at all: nothing is feasible
             if (lead) { C->done = 1; C->stop_reason = 1; C->t = t; C->s_cur = s_cur; C->n_super = ns; }
             break;
@@ -483,94 +911,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             C->candidates += nc;
             C->iters += 1;
         }
-        if (!grid_barrier(gb, C, G)) return;
+        stamp(5);
+        if (!grid_barrier(gb, C, G, epoch)) return;
+        stamp(6);
 
         // ============================================================ phase 3
         {
             const int *list_new = S.sn_list[t & 1];
             unsigned long long t_start = 0;
             if (prof && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
-            const int sub = lane % SP, l = sub >> 2, p = sub & 3;
             for (int g = warp; g < nchunks; g += nwarps) {
                 const int c0 = ldi(X.chunk_first + g);
                 const int q = g * PPW + lane / SP;
-                const bool active = q < P;
                 const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
                 int off = 0;
                 for (int j = 1; j < 32; ++j) off += (__shfl_sync(0xffffffffu, cb, j) <= q);
                 const int cbase = __shfl_sync(0xffffffffu, cb, off);
                 const int c = c0 + off;
+                const bool active = q < P;
                 Cand cd;
                 cd.r = -1;
-                int k = -1;
-                bool sside = false;
+                int first = 0, np = 1;
                 if (active) {
                     cd = ldcand(X.cand + c);
-                    k = position_bus(list_new, cd, q - cbase, sside);
+                    first = cbase / PPW;
+                    np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
                 }
-                const bool valid = active && k != cd.r;
-                const bool live = valid && l < L && p < 3;
-                ItemOut o;
-                o.e = 0.0;
-                o.on = false;
-                if (live) {
-                    double2 Ir[3];
-                    for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldz(S.icur + sidx(l, qq, cd.r, n));
-                    o = eval_item(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r]);
-                    if (prof && o.on) flops += item_flops(T, cd, k, T.ph[cd.r]);
-                }
-                double m = o.e;
-                m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
-                m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
-                double dl = 0.0, ml = 0.0;
-                if (valid && p == 0 && l < L) {
-                    const int kk = k < 0 ? cd.s : k;
-                    dl = m - ldd(S.mice + (size_t)l * n + kk);
-                    if (kk == cd.s) dl -= ldd(S.mice + (size_t)l * n + cd.r);
-                    ml = m;
-                }
-                for (int o2 = 4; o2 < SP; o2 <<= 1) {
-                    dl += __shfl_xor_sync(0xffffffffu, dl, o2);
-                    ml = fmax(ml, __shfl_xor_sync(0xffffffffu, ml, o2));
-                }
-                if (sub != 0) { dl = 0.0; ml = 0.0; }
-                // segmented inclusive scan over the lanes of one candidate
-                const int cseg = active ? c : -1 - lane;
-                const int prev = __shfl_up_sync(0xffffffffu, cseg, 1);
-                const bool head = (lane == 0) || (prev != cseg);
-                const unsigned heads = __ballot_sync(0xffffffffu, head);
-                const int seg_start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
-                for (int o2 = 1; o2 < 32; o2 <<= 1) {
-                    const double y = __shfl_up_sync(0xffffffffu, dl, o2);
-                    const double z = __shfl_up_sync(0xffffffffu, ml, o2);
-                    if (lane - o2 >= seg_start) { dl += y; ml = fmax(ml, z); }
-                }
-                const bool last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
-                if (active && last) {
-                    const int first = cbase / PPW;
-                    const int np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
-                    X.partial[g + c] = make_double2(dl, ml);
-                    __threadfence();
-                    if (atomicAdd(X.arrive + c, 1) == np - 1) {
-                        __threadfence();
-                        double sum = 0.0, mx = 0.0;
-                        for (int j = 0; j < np; ++j) {
-                            const double2 pj = ldz(X.partial + first + c + j);
-                            sum += pj.x;
-                            mx = fmax(mx, pj.y);
-                        }
-                        X.score[c] = sum;
-                        X.feas[c] = (mx <= margin);
-                        X.arrive[c] = 0;
-                    }
-                }
+                if (PREC == 0)
+                    score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, margin,
+                                  X.score, X.feas, prof, flops);
+                else
+                    score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops);
             }
-            if (!grid_barrier(gb, C, G)) return;
+            if (!grid_barrier(gb, C, G, epoch)) return;
             if (prof && lead) {
                 unsigned long long t_end;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
                 C->sweep_ns += t_end - t_start;
             }
+            stamp(7);
         }
         have = true;
     }
@@ -580,18 +959,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
     }
 }
 
-// Largest MICE of the final state into the record of the last merge (the
-// search records every earlier merge itself).
-__global__ void k_final_maxerr(Topo T, State S, Search X, const Ctrl *C) {
-    const int n = T.n, L = T.L, t = C->t;
-    if (t < 1) return;
-    double m = 0.0;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-        if (S.label[k] == k)
-            for (int l = 0; l < L; ++l) m = fmax(m, S.mice[(size_t)l * n + k]);
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0)
-        atomicMax((unsigned long long *)&X.dec_maxerr[t - 1], (unsigned long long)__double_as_longlong(m));
+// Host entry points for the search kernel (kept in this translation unit with
+// the template instantiations).
+cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st) {
+    void *args[] = {&T, &S, &X, &C, &gb};
+    const void *fn = precision == 1 ? (const void *)k_search<1> : (const void *)k_search<0>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
+}
+
+int search_blocks_per_sm() {
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_search<0>, kThreads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<1>, kThreads, 0) != cudaSuccess) return 0;
+    return a < b ? a : b;
 }
 
 // Results in caller numbering: super-node of each bus, reduced-network voltage

@@ -263,6 +263,13 @@ __global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__r
         }
         __syncthreads();
     }
+    // single-precision split of the path impedances: zc ~ zh + zl
+    for (int e = tid; e < 9 * n; e += nt) {
+        const double2 z = T.zc[e];
+        const float2 h = make_float2((float)z.x, (float)z.y);
+        T.zh[e] = h;
+        T.zlo[e] = make_float2((float)(z.x - (double)h.x), (float)(z.y - (double)h.y));
+    }
 }
 
 // ---------------------------------------------------------------- load flow
@@ -401,6 +408,7 @@ __global__ void k_state_init(int n, int L, Topo T, State S) {
             if (v == n - 1) S.sn_rank[n] = n;
         }
         S.mice[(size_t)l * n + v] = 0.0;
+        S.mice32[(size_t)l * n + v] = 0.0f;
         for (int p = 0; p < 3; ++p) {
             size_t q = sidx(l, p, v, n);
             bool on = T.ph[v] >> p & 1u;
@@ -408,6 +416,11 @@ __global__ void k_state_init(int n, int L, Topo T, State S) {
             S.icur[q] = T.ihat[q];
             S.hi[q] = on ? T.amag[q] : -INFINITY;
             S.lo[q] = on ? T.amag[q] : INFINITY;
+            S.mcur[q] = T.amag[q];
+            S.v32[q] = make_float2((float)T.vhat[q].x, (float)T.vhat[q].y);
+            S.hr32[q] = 0.0f;
+            S.lr32[q] = 0.0f;
+            S.icur32[q] = make_float2((float)T.ihat[q].x, (float)T.ihat[q].y);
         }
     }
 }

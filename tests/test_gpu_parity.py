@@ -86,14 +86,40 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", CASES, ids=[f"n{c[0]}-s{c[1]}-L{c[5]}" for c in CASES])
-def test_search_matches_oracle(ctx, case):
+def test_search_matches_oracle(ctx, case, precision):
     n, seed, kv, mode, load, L, margin, target = case
     f = fg.make_feeder(n, seed, kv_ll=kv, phase_mode=mode, load=load, n_scen=L)
     merges = O.max_merges_for(n, target)
     res, vhat_o = oracle_run(f, margin, merges)
-    ctx.reduce(f, params(margin=margin, target_reduction=target))
+    ctx.reduce(f, params(margin=margin, target_reduction=target, precision=precision))
     assert_same_run(ctx, res, vhat_o)
+
+
+def test_screen_bounds_cover_the_fp64_scores(ctx):
+    """Precision 1: every screened score lies within its bound of the oracle's
+    FP64 score (the argument that makes the mixed-precision selection exact)."""
+    for f in (fg.preset("feeder40")[0], fg.make_feeder(300, 23, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0))):
+        K = 8
+        res, _ = oracle_run(f, 0.005, f.n_bus, record=K)
+        ctx.reduce(f, params(margin=0.005, record_iters=K, precision=1))
+        worst = 0.0
+        for t in range(min(K, res["n_iter"])):
+            go = {(int(s), int(r)): v for s, r, v in zip(res["recorded"][t]["s"], res["recorded"][t]["r"],
+                                                         res["recorded"][t]["score"])}
+            rg = ctx.recorded(t)
+            assert len(rg["s"]) == len(go)
+            for s, r, v, b in zip(rg["s"], rg["r"], rg["score"], rg["bound"]):
+                o = go[(int(s), int(r))]
+                if math.isinf(v):
+                    assert math.isinf(o)        # screened out only when surely infeasible
+                    continue
+                if math.isinf(o):
+                    continue                    # screen kept an infeasible candidate: allowed
+                assert abs(v - o) <= b, (t, s, r, v, o, b)
+                worst = max(worst, abs(v - o) / b if b > 0 else 0.0)
+        assert worst < 1.0
 
 
 def test_every_candidate_score_matches_oracle(ctx):
@@ -167,11 +193,12 @@ EDGE = {
 }
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", sorted(EDGE))
-def test_edge_feeders_match_oracle(ctx, name):
+def test_edge_feeders_match_oracle(ctx, name, precision):
     f = EDGE[name]
     res, vhat_o = oracle_run(f, 0.01, f.n_bus)
-    ctx.reduce(f, params(margin=0.01))
+    ctx.reduce(f, params(margin=0.01, precision=precision))
     if name == "unloaded":
         # every candidate scores exactly 0: all tied, the smallest (r, s) wins each time
         assert np.all(res["score"] == 0.0)
@@ -266,11 +293,18 @@ def _check_properties(ctx, f, margin):
     assert abs(s["max_error"] - e.max()) <= 1e-12
 
 
-def test_feeder1000_full_run_matches_oracle(ctx):
+@pytest.fixture(scope="module")
+def feeder1000_oracle():
     f, run = fg.preset("feeder1000")
     merges = O.max_merges_for(f.n_bus, run["target"])
     res, vhat_o = oracle_run(f, run["margin"], merges)
-    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"]))
+    return f, run, res, vhat_o
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_feeder1000_full_run_matches_oracle(ctx, feeder1000_oracle, precision):
+    f, run, res, vhat_o = feeder1000_oracle
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=precision))
     assert_same_run(ctx, res, vhat_o)
     _check_properties(ctx, f, run["margin"])
 
@@ -280,9 +314,14 @@ def test_large_feeders_prefix_and_properties(ctx, name):
     f, run = fg.preset(name)
     K = 12
     res, vhat_o = oracle_run(f, run["margin"], K)
-    ctx.reduce(f, params(margin=run["margin"], max_merges=K))
-    assert_same_run(ctx, res, vhat_o)
-    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"]))
+    for precision in (0, 1):
+        ctx.reduce(f, params(margin=run["margin"], max_merges=K, precision=precision))
+        assert_same_run(ctx, res, vhat_o)
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=1))
+    full1 = ctx.decisions()
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=0))
+    full0 = ctx.decisions()
+    assert np.array_equal(full0["s"], full1["s"]) and np.array_equal(full0["r"], full1["r"])
     s = ctx.summary()
     assert s["n_iter"] == O.max_merges_for(f.n_bus, run["target"]) or s["stop_reason"] == 1
     _check_properties(ctx, f, run["margin"])
