@@ -258,8 +258,9 @@ def run_ours(args, rank, world, local):
                 "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1,
                 "flops_per_launch": ps["flops"], "sweeps_per_launch": ps["sweeps"],
                 "sweep_phase_share": ps["sweep_ms"] / ps["search_ms"] if ps["search_ms"] > 0 else None,
-                "phase_ms": dict(zip(["select", "recheck", "merge", "setup", "barrier1", "compact", "barrier2",
-                                      "sweep+barrier3"], [round(x, 3) for x in ps["phase_ms"]])),
+                "phase_ms": dict(zip(["select", "recheck", "merge", "setup", "barrier1", "chunkmap", "barrier2",
+                                      "sweep+barrier3", "merge_sum", "list_update", "offsets", "compaction"],
+                                     [round(x, 3) for x in ps["phase_ms"][:12]])),
                 "share_of_step": search_ms / (ms / args.steps)}
 
     if rank == 0:

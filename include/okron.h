@@ -109,8 +109,9 @@ typedef struct okr_summary {
     double flops;               /* algorithmic floating-point operations of the search */
     int32_t rechecks;           /* precision 1: iterations that rescored candidates in FP64 */
     int32_t recheck_cands;      /* precision 1: candidates rescored in FP64 over the run */
-    double phase_ms[8];         /* profile mode: time of CTA 0 in selection, FP64 recheck, merge,
-                                   candidate setup, barrier, compaction, barrier, sweep */
+    double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration (selection,
+                                   FP64 recheck, merge, candidate setup, barrier, merge bookkeeping,
+                                   list update, offsets, compaction, chunk map, barrier, sweep) */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,

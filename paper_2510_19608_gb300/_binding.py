@@ -45,7 +45,7 @@ class Summary(C.Structure):
                 ("pf_sweeps", C.c_int32), ("n_kept", C.c_int32), ("candidates", C.c_int64),
                 ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
                 ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double),
-                ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 8)]
+                ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 16)]
 
 
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",

@@ -186,6 +186,7 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     Search &X = ctx->X;
     CK(dalloc(ctx, &X.cand, 2 * N));
     CK(dalloc(ctx, &X.slot, 2 * N));
+    CK(dalloc(ctx, &X.ckey, 2 * N));
     CK(dalloc(ctx, &X.base, 2 * N + 1));
     CK(dalloc(ctx, &X.arrive, 2 * N));
     CK(dalloc(ctx, &X.block_tot, (size_t)ctx->num_sms));
@@ -642,7 +643,7 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
-    for (int i = 0; i < 8; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;
+    for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;
     return OKR_OK;
 }
 

@@ -118,8 +118,7 @@ struct Ctrl {
     long long max_spins;    // limit of a device-side wait
     double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
     unsigned long long sweep_ns;   // time in the sweep phase (profile mode, device timer)
-    unsigned long long phase_ns[8];   // profile mode, CTA 0: select, recheck, commit, setup,
-                                      // barrier 1, phase 2, barrier 2, sweep + barrier 3
+    unsigned long long phase_ns[16];  // profile mode, CTA 0: time per step of an iteration
 };
 
 // Grid-wide barrier of the persistent search kernel.
@@ -130,6 +129,7 @@ struct GridBar {
 
 struct Search {
     Cand *cand;             // [2n] compact candidate list
+    unsigned long long *ckey;   // [2n] tie key of each compact candidate
     Cand *slot;             // [2n] candidates by super-node slot (s < 0: none)
     int *base;              // [2n+1] first work position of each candidate
     int *arrive;            // [2n] pieces written so far (reset by the last writer)

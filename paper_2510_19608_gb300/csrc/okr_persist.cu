@@ -315,6 +315,19 @@ __device__ __forceinline__ Item32 eval_item32(const Topo &T, const State &S, int
 // lanes of a candidate reduce with a segmented scan in lane order; the last lane
 // of a segment stores the piece and the writer of the last piece sums the
 // pieces in order.
+// Lane `lane` holds the first position cb of candidate c0 + lane (candidates in
+// increasing order, c0 owning the chunk's first position q0).  Returns, for a
+// lane at position q0 + u, the offset of its candidate from c0: one ballot per
+// position of the chunk.
+__device__ __forceinline__ int chunk_offset(int cb, int q0, int ppw, int u) {
+    int off = 0;
+    for (int v = 0; v < ppw; ++v) {
+        const int c = __popc(__ballot_sync(0xffffffffu, cb <= q0 + v)) - 1;
+        if (v == u) off = c;
+    }
+    return off;
+}
+
 __device__ __forceinline__ void seg_scan_setup(bool active, int ci, int lane, unsigned &heads, int &seg_start,
                                                bool &last) {
     const int cseg = active ? ci : -1 - lane;
@@ -366,20 +379,40 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
         const double z = __shfl_up_sync(0xffffffffu, ml, o2);
         if (lane - o2 >= seg_start) { dl += y; ml = fmax(ml, z); }
     }
+    bool fin = false;
     if (active && last) {
-        X.partial[g + ci] = make_double2(dl, ml);
-        __threadfence();
-        if (atomicAdd(X.arrive + ci, 1) == np - 1) {
+        if (np == 1) {                      // the whole candidate lies in this chunk
+            out_score[ci] = dl;
+            out_feas[ci] = (ml <= margin);
+        } else {
+            X.partial[g + ci] = make_double2(dl, ml);
             __threadfence();
-            double sum = 0.0, mx = 0.0;
-            for (int j = 0; j < np; ++j) {
-                const double2 pj = ldz(X.partial + first + ci + j);
-                sum += pj.x;
-                mx = fmax(mx, pj.y);
-            }
-            out_score[ci] = sum;
-            out_feas[ci] = (mx <= margin);
-            X.arrive[ci] = 0;
+            fin = atomicAdd(X.arrive + ci, 1) == np - 1;
+        }
+    }
+    // the warp that stored a candidate's last piece sums all its pieces: lane j
+    // takes pieces j, j + 32, ...; then a fixed butterfly
+    unsigned finm = __ballot_sync(0xffffffffu, fin);
+    if (finm) __threadfence();
+    while (finm) {
+        const int src = __ffs(finm) - 1;
+        finm &= finm - 1;
+        const int fci = __shfl_sync(0xffffffffu, ci, src), ff = __shfl_sync(0xffffffffu, first, src);
+        const int fnp = __shfl_sync(0xffffffffu, np, src);
+        double sum = 0.0, mx = 0.0;
+        for (int j = lane; j < fnp; j += 32) {
+            const double2 pj = ldz(X.partial + ff + fci + j);
+            sum += pj.x;
+            mx = fmax(mx, pj.y);
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+        }
+        if (lane == 0) {
+            out_score[fci] = sum;
+            out_feas[fci] = (mx <= margin);
+            X.arrive[fci] = 0;
         }
     }
 }
@@ -441,28 +474,65 @@ __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, in
         const float y5 = __shfl_up_sync(0xffffffffu, bml, o2);
         if (lane - o2 >= seg_start) { dl += y1; bl += y2; ad += y3; ml = fmaxf(ml, y4); bml = fmaxf(bml, y5); }
     }
+    float4 *pf = reinterpret_cast<float4 *>(X.partial);
+    bool fin = false;
     if (active && last) {
-        float4 *pf = reinterpret_cast<float4 *>(X.partial);
-        pf[g + ci] = make_float4(dl, bl + 32.0f * kU * ad, ml, bml);
-        __threadfence();
-        if (atomicAdd(X.arrive + ci, 1) == np - 1) {
+        const float pb = bl + 32.0f * kU * ad;
+        if (np == 1) {                      // the whole candidate lies in this chunk
+            X.scr[ci] = make_float4(dl, 1.001f * (pb + 38.0f * kU * fabsf(dl)), ml, bml);
+        } else {
+            pf[g + ci] = make_float4(dl, pb, ml, bml);
             __threadfence();
-            float sum = 0.0f, bsum = 0.0f, asum = 0.0f, mx = 0.0f, bmx = 0.0f;
-            for (int j = 0; j < np; ++j) {
-                const float4 pj = __ldcg(pf + first + ci + j);
-                sum += pj.x;
-                bsum += pj.y;
-                asum += fabsf(pj.x);
-                mx = fmaxf(mx, pj.z);
-                bmx = fmaxf(bmx, pj.w);
-            }
-            X.scr[ci] = make_float4(sum, 1.001f * (bsum + 32.0f * kU * asum), mx, bmx);
-            X.arrive[ci] = 0;
+            fin = atomicAdd(X.arrive + ci, 1) == np - 1;
+        }
+    }
+    unsigned finm = __ballot_sync(0xffffffffu, fin);
+    if (finm) __threadfence();
+    while (finm) {
+        const int src = __ffs(finm) - 1;
+        finm &= finm - 1;
+        const int fci = __shfl_sync(0xffffffffu, ci, src), ff = __shfl_sync(0xffffffffu, first, src);
+        const int fnp = __shfl_sync(0xffffffffu, np, src);
+        float sum = 0.0f, bsum = 0.0f, asum = 0.0f, mx = 0.0f, bmx = 0.0f;
+        for (int j = lane; j < fnp; j += 32) {
+            const float4 pj = __ldcg(pf + ff + fci + j);
+            sum += pj.x;
+            bsum += pj.y;
+            asum += fabsf(pj.x);
+            mx = fmaxf(mx, pj.z);
+            bmx = fmaxf(bmx, pj.w);
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o2);
+            bsum += __shfl_xor_sync(0xffffffffu, bsum, o2);
+            asum += __shfl_xor_sync(0xffffffffu, asum, o2);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+            bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o2));
+        }
+        if (lane == 0) {
+            // rounding of the piece sums: at most ceil(np / 32) + 5 additions deep
+            const float depth = (float)((fnp + 31) / 32 + 5);
+            X.scr[fci] = make_float4(sum, 1.001f * (bsum + (depth + 32.0f) * kU * asum), mx, bmx);
+            X.arrive[fci] = 0;
         }
     }
 }
 
 // ---------------------------------------------------------------- selection
+// Doubles compared through order-preserving 64-bit keys, so that the minimum,
+// band and gap searches run on the integer pipe (FP64 comparisons issue on the
+// slow FP64 pipe of this GPU).
+__device__ __forceinline__ unsigned long long dkey(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dval(unsigned long long k) {
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+struct MinF { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
+struct MaxU { __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; } };
+
 // Exact selection over m entries with FP64 scores (entry i is candidate
 // map ? map[i] : i): minimum over feasible entries, tie band [min, min + tau],
 // smallest (r, s) inside it.  Identical in every CTA.
@@ -472,88 +542,149 @@ struct Sel {
 };
 
 __device__ Sel select_exact(const Search &X, int m, const int *map, const double *score, const int *feas, double tau,
-                            double *smd, unsigned long long *smu, int *smi) {
+                            double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc) {
     const int tid = threadIdx.x;
-    double best = INFINITY;
+    unsigned long long bk = ~0ull;
     for (int i = tid; i < m; i += kThreads)
-        if (ldi(feas + i)) best = fmin(best, ldd(score + i));
-    best = block_reduce(best, MinD(), smd);
+        if (ldi(feas + i)) bk = min(bk, dkey(ldd(score + i)));
+    bk = block_reduce(bk, MinU(), smu);
     Sel out;
     out.w = -1;
     out.gap = INFINITY;
-    if (best == INFINITY) return out;
-    const double edge = best + tau;
-    unsigned long long key = ~0ull;
-    double gap = INFINITY;
+    if (bk == ~0ull || dval(bk) == INFINITY) return out;
+    const double edge = dval(bk) + tau;
+    const unsigned long long ek = dkey(edge);
+    unsigned long long key = ~0ull, gk = ~0ull;
     for (int i = tid; i < m; i += kThreads) {
         if (!ldi(feas + i)) continue;
-        const double d = ldd(score + i);
-        if (d <= edge) {
-            const unsigned long long k = ldcand(X.cand + (map ? map[i] : i)).key;
-            if (k < key) key = k;
-        } else {
-            gap = fmin(gap, d - edge);
+        const unsigned long long k = dkey(ldd(score + i));
+        if (k <= ek) {
+            const unsigned long long t = __ldcg(X.ckey + (map ? map[i] : i));
+            if (t < key) key = t;
+        } else if (k < gk) {
+            gk = k;
         }
     }
     key = block_reduce(key, MinU(), smu);
-    gap = block_reduce(gap, MinD(), smd);
+    gk = block_reduce(gk, MinU(), smu);
     int w = 0x7fffffff;
-    for (int i = tid; i < m; i += kThreads)
-        if (ldi(feas + i) && ldd(score + i) <= edge && ldcand(X.cand + (map ? map[i] : i)).key == key) w = min(w, i);
-    w = block_reduce(w, MinI(), smi);
-    out.w = (w < m) ? (map ? map[w] : w) : -2;
-    out.gap = gap;
+    if (ksure < key) {              // a candidate known to be in the band has the smallest key
+        for (int c = tid; c < nc; c += kThreads)
+            if (__ldcg(X.ckey + c) == ksure) w = min(w, c);
+        w = block_reduce(w, MinI(), smi);
+        out.w = (w < nc) ? w : -2;
+    } else {
+        for (int i = tid; i < m; i += kThreads)
+            if (ldi(feas + i) && dkey(ldd(score + i)) <= ek && __ldcg(X.ckey + (map ? map[i] : i)) == key) w = min(w, i);
+        w = block_reduce(w, MinI(), smi);
+        out.w = (w < m) ? (map ? map[w] : w) : -2;
+    }
+    out.gap = (gk == ~0ull) ? INFINITY : dval(gk) - edge;
     return out;
 }
 
 constexpr int kRmax = 1024;     // candidates an FP64 recheck can hold in shared memory
 
-// Screen selection (precision 1): U, then R in candidate order into s_R.
-// Returns the size of R (may exceed kRmax; then s_R is incomplete) and the
-// screen margin below the band: the smallest D32 - B - (U + tau) over the
-// candidates left out of R.
-__device__ int screen_select(const Search &X, int nc, double margin, double tau, int *s_R, int2 *sm2, double *smd,
-                             double &gap) {
+// Screen selection (precision 1), in FP32 with directed rounding so that every
+// test holds for the real intervals [D32 - B, D32 + B] and [M32 - Bm, M32 + Bm]
+// that contain each candidate's FP64 score and largest MICE.  With
+//   m_lo = min over maybe-feasible lower ends, m_hi = min over surely feasible
+//   upper ends (the FP64 minimum m lies in [m_lo, m_hi]),
+// a candidate is surely in the FP64 tie band when it is surely feasible and its
+// upper end is <= m_lo + tau, surely out when it may be infeasible only by
+// margin or its lower end is > m_hi + tau, and uncertain otherwise.  The winner
+// is the smallest key of the band.  If no uncertain candidate has a key below the
+// smallest surely-in key, that candidate wins.  Otherwise R = (candidates whose
+// lower end is <= m_hi: they may hold the minimum) + (uncertain candidates with
+// a smaller key) is rescored in FP64; the winner is then the smallest key among
+// the surely-in candidates and the members of R inside the exact band.
+__device__ __forceinline__ bool surely_feasible(float4 q, float margin_lo) { return __fadd_ru(q.z, q.w) <= margin_lo; }
+
+struct Screen {
+    int nR;                     // size of R (0 when no recheck is needed)
+    int win;                    // winner when no recheck is needed (-1 otherwise / none)
+    unsigned long long ksure;   // smallest surely-in key (~0 if none)
+    bool any;                   // some candidate may be feasible
+    double gap;                 // screen distance from the band edge to the next candidate
+};
+
+__device__ Screen screen_select(const Search &X, int nc, double margin, double tau, int *s_R, int2 *sm2, float *smf,
+                                unsigned long long *smu, int *smi) {
     const int tid = threadIdx.x;
-    double U = INFINITY;
+    const float margin_lo = __double2float_rd(margin), margin_hi = __double2float_ru(margin);
+    const float tau_lo = __double2float_rd(tau), tau_hi = __double2float_ru(tau);
+    float mhi = INFINITY, mlo = INFINITY;
     for (int c = tid; c < nc; c += kThreads) {
         const float4 q = __ldcg(X.scr + c);
-        if ((double)q.z + (double)q.w <= margin) U = fmin(U, (double)q.x + (double)q.y);
+        if (__fsub_rd(q.z, q.w) <= margin_hi) mlo = fminf(mlo, __fsub_rd(q.x, q.y));
+        if (surely_feasible(q, margin_lo)) mhi = fminf(mhi, __fadd_ru(q.x, q.y));
     }
-    U = block_reduce(U, MinD(), smd);
-    const double edge = U + tau;
-    int nR = 0;
-    double g = INFINITY;
+    mlo = block_reduce(mlo, MinF(), smf);
+    mhi = block_reduce(mhi, MinF(), smf);
+    Screen out;
+    out.nR = 0;
+    out.win = -1;
+    out.ksure = ~0ull;
+    out.any = mlo < INFINITY;
+    out.gap = INFINITY;
+    if (!out.any) return out;
+    const float edge_in = __fadd_rd(mlo, tau_lo), edge_out = __fadd_ru(mhi, tau_hi);
+    unsigned long long ks = ~0ull;
+    float g = INFINITY;
+    for (int c = tid; c < nc; c += kThreads) {
+        const float4 q = __ldcg(X.scr + c);
+        const bool maybe = __fsub_rd(q.z, q.w) <= margin_hi;
+        if (!maybe) continue;
+        const float lo = __fsub_rd(q.x, q.y), hi = __fadd_ru(q.x, q.y);
+        if (surely_feasible(q, margin_lo) && hi <= edge_in) ks = min(ks, __ldcg(X.ckey + c));
+        if (lo > edge_out) g = fminf(g, lo - edge_out);
+    }
+    ks = block_reduce(ks, MinU(), smu);
+    out.ksure = ks;
+    out.gap = (double)block_reduce(g, MinF(), smf);
+    // R: possible minimizers and uncertain candidates with a key below ks
+    int nR = 0, need = 0;
     for (int c0 = 0; c0 < nc; c0 += kThreads) {
         const int c = c0 + tid;
-        int flag = 0;
+        int flag = 0, unc = 0;
         if (c < nc) {
             const float4 q = __ldcg(X.scr + c);
-            const bool maybe = (double)q.z - (double)q.w <= margin;
-            if (maybe) {
-                const double lo = (double)q.x - (double)q.y;
-                if (lo <= edge) flag = 1;
-                else g = fmin(g, lo - edge);
+            if (__fsub_rd(q.z, q.w) <= margin_hi) {
+                const float lo = __fsub_rd(q.x, q.y), hi = __fadd_ru(q.x, q.y);
+                const bool in_sure = surely_feasible(q, margin_lo) && hi <= edge_in;
+                const bool out_sure = lo > edge_out;
+                if (!in_sure && !out_sure && __ldcg(X.ckey + c) < ks) unc = 1;
+                if (unc || lo <= mhi) flag = 1;
             }
         }
         int2 tot;
-        const int2 ex = block_scan2(make_int2(flag, 0), sm2, &tot);
+        const int2 ex = block_scan2(make_int2(flag, unc), sm2, &tot);
         if (flag && nR + ex.x < kRmax) s_R[nR + ex.x] = c;
         nR += tot.x;
+        need += tot.y;
     }
-    gap = block_reduce(g, MinD(), smd);
+    if (need == 0) {
+        int w = 0x7fffffff;
+        for (int c = tid; c < nc; c += kThreads)
+            if (__ldcg(X.ckey + c) == ks) w = min(w, c);
+        w = block_reduce(w, MinI(), smi);
+        out.win = (w < nc) ? w : -2;
+        return out;
+    }
+    out.nR = nR;
     __syncthreads();
-    return nR;
+    return out;
 }
 
 // ---------------------------------------------------------------- the kernel
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb) {
     __shared__ double smd[32];
+    __shared__ float smf[32];
     __shared__ unsigned long long smu[32];
     __shared__ int smi[32];
     __shared__ int2 sm2[33];
-    __shared__ int2 s_pref, s_tot;
+    __shared__ int2 s_pref, s_tot, s_mine;
     __shared__ int s_R[kRmax];
     __shared__ int s_Rbase[kRmax + 1];
     const int n = T.n, L = T.L;
@@ -592,26 +723,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             Sel sel;
             bool full64 = (PREC == 0);
             if (PREC == 1) {
-                double sgap = INFINITY;
-                const int nR = screen_select(X, nc, margin, tau, s_R, sm2, smd, sgap);
+                const Screen sc = screen_select(X, nc, margin, tau, s_R, sm2, smf, smu, smi);
+                const int nR = sc.nR;
                 stamp(0);
                 if (blockIdx.x == 0 && t < X.rec_iters) {
                     for (int c = tid; c < nc; c += kThreads) {
                         const Cand cc = ldcand(X.cand + c);
                         const float4 q = __ldcg(X.scr + c);
-                        const bool out = (double)q.z - (double)q.w > margin;
+                        const bool out = __fsub_rd(q.z, q.w) > __double2float_ru(margin);
                         X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
                         X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
                         X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : s_cur + (double)q.x;
                         X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
                     }
                 }
-                if (nR == 0) {
+                if (!sc.any) {
                     sel.w = -1;
-                } else if (nR == 1 && [&] { const float4 q = __ldcg(X.scr + s_R[0]);
-                                            return (double)q.z + (double)q.w <= margin; }()) {
-                    sel.w = s_R[0];
-                    sel.gap = sgap;
+                } else if (nR == 0) {
+                    sel.w = sc.win;
+                    sel.gap = sc.gap;
                 } else if (nR <= kRmax) {
                     // FP64 recheck of R: positions of R back to back
                     for (int i0 = 0; i0 < nR; i0 += kThreads) {
@@ -645,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                     }
                     if (lead) { C->rechecks += 1; C->recheck_cands += nR; }
                     if (!grid_barrier(gb, C, G, epoch)) return;
-                    sel = select_exact(X, nR, s_R, X.score, X.feas, tau, smd, smu, smi);
+                    sel = select_exact(X, nR, s_R, X.score, X.feas, tau, smd, smu, smi, sc.ksure, nc);
                     stamp(1);
                 } else {
                     full64 = true;                      // R too large: rescore everything in FP64
@@ -656,9 +786,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                     for (int g = warp; g < nchunks; g += nwarps) {
                         const int c0 = ldi(X.chunk_first + g);
                         const int q = g * PPW + lane / SP;
-                        const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;
-                        int off = 0;
-                        for (int j = 1; j < 32; ++j) off += (__shfl_sync(0xffffffffu, cb, j) <= q);
+                        const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
+                        const int off = chunk_offset(cb, g * PPW, PPW, lane / SP);
                         const int cbase = __shfl_sync(0xffffffffu, cb, off);
                         const int c = c0 + off;
                         const bool active = q < P;
@@ -686,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                         X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
                     }
                 }
-                sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi);
+                sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
                 stamp(PREC == 0 ? 0 : 1);
             }
             if (lead && t < X.rec_iters) X.rec_count[t] = nc;
@@ -820,7 +949,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             }
             int2 tot;
             my_ex = block_scan2(mine, sm2, &tot);
-            if (tid == 0) X.block_tot[blockIdx.x] = tot;
+            if (tid == 0) { X.block_tot[blockIdx.x] = tot; s_mine = tot; }
         }
         stamp(3);
         if (!grid_barrier(gb, C, G, epoch)) return;
@@ -845,18 +974,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                     C->n_super = ns;
                 }
             }
+            stamp(8);
             // super-node list after the merge (other buffer), ranks, largest MICE
             int *list_new = S.sn_list[t & 1];
-            double m = 0.0;
+            unsigned long long m = 0;          // MICE >= 0: bit patterns order like the values
             for (int j = gt; j < ns; j += gs) {
                 const int k = ldi(list_old + j + (j >= jr0 ? 1 : 0));
                 list_new[j] = k;
-                for (int l = 0; l < L; ++l) m = fmax(m, ldd(S.mice + (size_t)l * n + k));
+                for (int l = 0; l < L; ++l)
+                    m = max(m, (unsigned long long)__double_as_longlong(ldd(S.mice + (size_t)l * n + k)));
             }
             for (int b = r0 + 1 + gt; b <= n; b += gs) S.sn_rank[b] = ldi(S.sn_rank + b) - 1;
-            m = block_reduce(m, MaxD(), smd);
-            if (tid == 0 && m > 0.0)
-                atomicMax((unsigned long long *)&X.dec_maxerr[told], (unsigned long long)__double_as_longlong(m));
+            m = block_reduce(m, MaxU(), smu);
+            if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
+            stamp(9);
         }
         if (finishing) {
             if (lead) { C->done = 1; C->stop_reason = 0; }
@@ -879,6 +1010,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             if (lane == 0) { s_pref = acc; s_tot = all; }
         }
         __syncthreads();
+        stamp(10);
         const int2 pref = s_pref, tot = s_tot;
         nc = tot.x;
         P = tot.y;
@@ -891,17 +1023,39 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             if (lead) { C->err = 7; C->total_pos = P; C->t = t; C->s_cur = s_cur; C->n_super = ns; }
             break;
         }
-        if (gt >= 1 && gt < ns) {
-            int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y;
-            for (int d = 0; d < 2; ++d) {
-                const Cand c = X.slot[2 * gt + d];
-                if (c.s < 0) continue;
-                const int cnt = cand_positions(c);
-                X.cand[ci] = c;
-                X.base[ci] = pos;
-                for (int g = (pos + PPW - 1) / PPW; g * PPW < pos + cnt; ++g) X.chunk_first[g] = ci;
-                ++ci;
-                pos += cnt;
+        {
+            // this CTA's candidates into the compact list; their first positions
+            // also into shared memory for the chunk map below
+            int *s_lbase = s_Rbase;
+            if (gt >= 1 && gt < ns) {
+                int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
+                for (int d = 0; d < 2; ++d) {
+                    const Cand c = X.slot[2 * gt + d];
+                    if (c.s < 0) continue;
+                    X.cand[ci] = c;
+                    X.ckey[ci] = c.key;
+                    X.base[ci] = pos;
+                    s_lbase[li] = pos;
+                    ++ci;
+                    ++li;
+                    pos += cand_positions(c);
+                }
+            }
+            __syncthreads();
+            stamp(11);
+            // chunk map: every chunk that starts inside this CTA's positions gets the
+            // candidate holding its first position (binary search in shared memory)
+            const int2 mt = s_mine;
+            const int p0 = pref.y, p1 = pref.y + mt.y;
+            for (int g = (p0 + PPW - 1) / PPW + tid; g * PPW < p1; g += kThreads) {
+                const int q = g * PPW;
+                int lo = 0, hi = mt.x - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_lbase[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                X.chunk_first[g] = pref.x + lo;
             }
         }
         if (lead) {
@@ -924,8 +1078,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 const int c0 = ldi(X.chunk_first + g);
                 const int q = g * PPW + lane / SP;
                 const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
-                int off = 0;
-                for (int j = 1; j < 32; ++j) off += (__shfl_sync(0xffffffffu, cb, j) <= q);
+                const int off = chunk_offset(cb, g * PPW, PPW, lane / SP);
                 const int cbase = __shfl_sync(0xffffffffu, cb, off);
                 const int c = c0 + off;
                 const bool active = q < P;
