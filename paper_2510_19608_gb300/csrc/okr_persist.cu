@@ -130,8 +130,9 @@ __device__ __forceinline__ int child_toward(const Topo &T, int a, int v) {
     return T.child[lo];
 }
 
+// Tie key: (caller r, caller s) lexicographic; caller ids are < 2^15.
 __device__ __forceinline__ unsigned long long tie_key(const Topo &T, int s, int r) {
-    return ((unsigned long long)(unsigned)T.orig[r] << 32) | (unsigned)T.orig[s];
+    return ((unsigned long long)(unsigned)T.orig[r] << 15) | (unsigned)T.orig[s];
 }
 
 __device__ __forceinline__ int cand_positions(const Cand &c) { return c.ns + c.nr + c.fixed; }
@@ -831,11 +832,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             // ---- commit in FP64: r's cluster joins s
             const Cand cd = ldcand(X.cand + sel.w);
             const unsigned phr = T.ph[cd.r];
-            for (int i = gt; i < n; i += gs)
+            // the merge runs on the last warps of the grid, the candidate setup
+            // below on the first threads, so that the two overlap
+            const int rgt = gs - 1 - gt, cwarp = nwarps - 1 - warp;
+            for (int i = rgt; i < n; i += gs)
                 if (ldi(S.label + i) == cd.r) S.label[i] = cd.s;
             const int nitems = cand_positions(cd) * SP;
             double acc = 0.0;
-            for (int i0 = warp * 32; i0 < nitems; i0 += nwarps * 32) {
+            for (int i0 = cwarp * 32; i0 < nitems; i0 += nwarps * 32) {
                 const int item = i0 + lane;
                 const int q = item / SP, sub = item % SP, l = sub >> 2, p = sub & 3;
                 bool sside = false;
@@ -879,8 +883,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             }
             for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o2);
             nw_commit = min(nwarps, (nitems + 31) / 32);
-            if (lane == 0 && warp < nw_commit) X.wsum[warp] = acc;
-            if (lead) {
+            if (lane == 0 && cwarp < nw_commit) X.wsum[cwarp] = acc;
+            if (rgt == 0) {
                 for (int l = 0; l < L; ++l)
                     for (int q = 0; q < 3; ++q)
                         if (phr >> q & 1u) {
