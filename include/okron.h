@@ -146,6 +146,39 @@ okr_status okr_reduce_ops(okr_ctx *ctx, const okr_feeder *f, const double *vhat,
 okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, double *ihat_out,
                           int32_t *sweeps);
 
+/* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
+#define OKR_STATIC_MAX_BUS 4096
+
+/* The load flow of okr_power_flow for callers that cannot allocate device
+ * memory: code inside a host framework whose allocator owns the GPU's memory
+ * (a cudaMalloc there fails or escapes its accounting), and loops that cannot
+ * take the device-wide synchronisation of cudaMalloc/cudaFree.  The paper has
+ * no counterpart: this is an interface variant, not a step of the method.
+ *
+ * Needs no context and allocates nothing: no cudaMalloc, cudaFree or
+ * allocating library routine.  Its scratch is one static device array of
+ * 5,396,480 bytes (sized for OKR_STATIC_MAX_BUS buses and 4 scenarios) that
+ * every GPU which loads the library holds until the process exits.  Runs on the CURRENT device and on `stream` (a cudaStream_t,
+ * NULL = the default stream); returns after the stream has finished the work.
+ *
+ * f: feeder arrays (parent, phases, z_line, s_load) in DEVICE memory of the
+ * current device, caller-owned, read only; v_slack is read from *f.
+ * vhat_out (required), ihat_out (may be NULL): DEVICE buffers
+ * [n_scen][n_bus][3][2], caller-owned, written (0 on absent phases);
+ * *sweeps (HOST, may be NULL): sweeps of the slowest scenario.
+ * Errors: OKR_EINVAL for NULL arrays, n_bus outside [2, OKR_STATIC_MAX_BUS],
+ * n_scen outside [1, 4] or an invalid tree; OKR_ESINGULAR, OKR_EPF as
+ * okr_power_flow; OKR_ECUDA for a CUDA failure.  No message string is kept.
+ *
+ * The first call on a device also looks up the device address of the static
+ * array (once per device, with that device current): make that first call
+ * before any stream capture.  Every call shares the one array, which keeps
+ * the previous call's contents; calls that overlap on the GPU (other streams,
+ * other host threads on the same device) race on it and must be serialised
+ * by the caller. */
+okr_status okr_power_flow_static(const okr_feeder *f, double *vhat_out, double *ihat_out,
+                                 int32_t *sweeps, void *stream);
+
 /* ---- results of the last reduction (host buffers, caller-owned) ---- */
 okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out);
 /* Decision sequence, one entry per merge, in caller bus ids: s (absorbing

@@ -6,7 +6,7 @@ with the same entry points.  The algorithm is Algorithm 1 of arXiv 2510.19608
 (Sec. IV), with the Kron reduction of Sec. II-B and the error model of Sec. III.
 """
 from ._binding import (Context, Feeder, OkrError, Params, Summary, default_params,  # noqa: F401
-                       device_feeder, lib, lib_path)
+                       device_feeder, lib, lib_path, power_flow_static)
 
 __all__ = ["Context", "Feeder", "OkrError", "Params", "Summary", "default_params", "device_feeder",
-           "lib", "lib_path"]
+           "lib", "lib_path", "power_flow_static"]

@@ -50,7 +50,8 @@ class Summary(C.Structure):
 
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
-           "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded")
+           "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
+           "okr_power_flow_static")
 
 
 def lib_path() -> str:
@@ -79,6 +80,7 @@ def lib():
                 getattr(L, fn).argtypes = [P, C.POINTER(Feeder), C.POINTER(Params)]
             L.okr_reduce_ops.argtypes = [P, C.POINTER(Feeder), P, P, C.POINTER(Params)]
             L.okr_power_flow.argtypes = [P, C.POINTER(Feeder), P, P, P]
+            L.okr_power_flow_static.argtypes = [C.POINTER(Feeder), P, P, P, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -138,6 +140,22 @@ def device_feeder(n_bus: int, n_scen: int, parent_ptr: int, phases_ptr: int, z_p
     for p in range(3):
         f.v_slack[p][0], f.v_slack[p][1] = vs[p, 0], vs[p, 1]
     return f
+
+
+def power_flow_static(dfeeder: Feeder, vhat_ptr: int, ihat_ptr: int | None = None, stream: int | None = None) -> int:
+    """okr_power_flow_static: load flow into caller device buffers, no device allocation.
+
+    dfeeder from device_feeder(); vhat_ptr / ihat_ptr: device addresses of
+    [n_scen][n_bus][3][2] float64 buffers.  Returns the sweeps used; raises
+    OkrError on a non-OK status.
+    """
+    sw = C.c_int32()
+    st = lib().okr_power_flow_static(C.byref(dfeeder), C.c_void_p(int(vhat_ptr)),
+                                     C.c_void_p(int(ihat_ptr)) if ihat_ptr else None, C.byref(sw),
+                                     C.c_void_p(int(stream)) if stream else None)
+    if st != OK:
+        raise OkrError(st, lib().okr_status_str(st).decode())
+    return int(sw.value)
 
 
 class Context:
