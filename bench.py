@@ -27,8 +27,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "candidates evaluated/s & time-to-optimal reduction, 1000-node feeder vs FP64"
 WORKLOAD = "feeder1000"
-FP64_PEAK_TFLOPS = 1.25     # GB300 nominal FP64 (non-tensor) rate; see the design doc
+# FP32 ALU peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
+# (the search's counted arithmetic is its FP32 candidate screen)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes of one k_search launch on this workload from the ncu capture in
+# profiles/k_search_feeder1000.md, valid only for the kernel source it was taken on
+NCU_TRAFFIC = {"bytes": 1013248 + 155392, "source": "paper_2510_19608_gb300/csrc/okr_persist.cu",
+               "sha256_prefix": "8f22566c0aeeacf8", "summary": "profiles/k_search_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def _ncu_traffic():
+    """Per-launch DRAM bytes from the committed ncu capture, or None when the
+    kernel source has changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, NCU_TRAFFIC["source"]), "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return NCU_TRAFFIC["bytes"] if h.startswith(NCU_TRAFFIC["sha256_prefix"]) else None
 
 
 def _args():
@@ -252,9 +270,9 @@ def run_ours(args, rank, world, local):
     ps = ctx.summary()
     search_ms = summ_last["search_ms"]
     achieved = ps["flops"] / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_search",
-                "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _ncu_traffic(), "kernel": "k_search",
+                "peak_source": "derived FP32 ALU rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                 "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1,
                 "flops_per_launch": ps["flops"], "sweeps_per_launch": ps["sweeps"],
                 "sweep_phase_share": ps["sweep_ms"] / ps["search_ms"] if ps["search_ms"] > 0 else None,
