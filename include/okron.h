@@ -112,6 +112,7 @@ typedef struct okr_summary {
     double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration (selection,
                                    FP64 recheck, merge, candidate setup, barrier, merge bookkeeping,
                                    list update, offsets, compaction, chunk map, barrier, sweep) */
+    double kron_ms;             /* device time of the last okr_kron since the reduction (0 if none) */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
@@ -145,6 +146,27 @@ okr_status okr_reduce_ops(okr_ctx *ctx, const okr_feeder *f, const double *vhat,
  * (may be NULL): Y Vhat, same layout; *sweeps (may be NULL): sweeps used. */
 okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, double *ihat_out,
                           int32_t *sweeps);
+
+/* Y_Kron (Sec. II-B, eqs. (Y-partitioned) and (Y_kron)): the Kron-reduced
+ * admittance matrix Y_KK - Y_KR Y_RR^-1 Y_RK of the feeder of the last
+ * okr_reduce* / okr_power_flow call onto a kept bus set, over the kept
+ * phase-nodes, the slack bus included.
+ *
+ * kept: HOST [n_bus] flags in caller numbering (bus 0 must be kept), or NULL
+ *   for the super-nodes of the last reduction (the network the search chose).
+ * *k_phi (required): number of kept phase-nodes.  Pass y_out = phase_node =
+ *   NULL to query it alone.
+ * y_out (HOST, may be NULL): [k_phi][k_phi][2] complex, row-major, rows and
+ *   columns in phase_node order; needs cap >= k_phi.
+ * phase_node (HOST, may be NULL): [k_phi], caller bus * 3 + phase, ordered by
+ *   bus then phase.
+ * Computed in FP64 on the device: one small dense elimination per connected
+ * component of reduced buses.  Errors: OKR_ENOTREADY without a feeder (or
+ * without a reduction when kept is NULL); OKR_EINVAL if bus 0 is not kept,
+ * cap < k_phi, or a reduced component borders more than 1024 kept
+ * phase-nodes; OKR_ESINGULAR for a singular block. */
+okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_out,
+                    int32_t *phase_node, int32_t *k_phi);
 
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096

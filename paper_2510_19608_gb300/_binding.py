@@ -45,13 +45,14 @@ class Summary(C.Structure):
                 ("pf_sweeps", C.c_int32), ("n_kept", C.c_int32), ("candidates", C.c_int64),
                 ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
                 ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double),
-                ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 16)]
+                ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 16),
+                ("kron_ms", C.c_double)]
 
 
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
-           "okr_power_flow_static")
+           "okr_power_flow_static", "okr_kron")
 
 
 def lib_path() -> str:
@@ -81,6 +82,7 @@ def lib():
             L.okr_reduce_ops.argtypes = [P, C.POINTER(Feeder), P, P, C.POINTER(Params)]
             L.okr_power_flow.argtypes = [P, C.POINTER(Feeder), P, P, P]
             L.okr_power_flow_static.argtypes = [C.POINTER(Feeder), P, P, P, P]
+            L.okr_kron.argtypes = [P, P, I32, P, P, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -216,6 +218,20 @@ class Context:
         sw = C.c_int32()
         self._check(lib().okr_power_flow(self._h, C.byref(hf.c), _ptr(v), _ptr(i), C.byref(sw)))
         return v[..., 0] + 1j * v[..., 1], i[..., 0] + 1j * i[..., 1], int(sw.value)
+
+    def kron(self, kept=None):
+        """Y_Kron onto `kept` (caller-order flags; None = the last reduction's
+        super-nodes).  Returns (Y complex [k, k], phase_node int32 [k])."""
+        kp = None
+        if kept is not None:
+            kp = np.ascontiguousarray(kept, dtype=np.uint8)
+        k = C.c_int32()
+        self._check(lib().okr_kron(self._h, _ptr(kp) if kp is not None else None, 0, None, None, C.byref(k)))
+        K = int(k.value)
+        y = np.zeros((K, K, 2))
+        pn = np.zeros(K, np.int32)
+        self._check(lib().okr_kron(self._h, _ptr(kp) if kp is not None else None, K, _ptr(y), _ptr(pn), C.byref(k)))
+        return y[..., 0] + 1j * y[..., 1], pn
 
     # ---- results
     def summary(self) -> dict:

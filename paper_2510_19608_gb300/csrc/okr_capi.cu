@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 using namespace okr;
@@ -64,7 +65,17 @@ struct okr_ctx {
     int64_t launches = 0;
     double search_ms = 0.0;
 
+    // Y_Kron work (allocated on the first okr_kron call)
+    KronWork kw{};
+    int cap_kron_n = 0;
+    std::vector<void *> kron_allocs;
+    double2 *ykr = nullptr, *kbig = nullptr;
+    uint8_t *kron_kept = nullptr;
+    size_t cap_ykr = 0, cap_kbig = 0;
+    double kron_ms = 0.0;
+
     // last result
+    bool have_topo = false;     // T describes the feeder of the last call
     bool have_result = false;
     int n = 0, L = 0, rec_iters = 0, pf_sweeps = 0;
     Ctrl last{};
@@ -90,7 +101,18 @@ okr_status fail(okr_ctx *c, okr_status s, const char *fmt, ...) {
                         #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
     } while (0)
 
+void free_kron(okr_ctx *ctx) {
+    for (void *p : ctx->kron_allocs) cudaFree(p);
+    ctx->kron_allocs.clear();
+    ctx->cap_kron_n = 0;
+    if (ctx->ykr) cudaFree(ctx->ykr);
+    if (ctx->kbig) cudaFree(ctx->kbig);
+    ctx->ykr = ctx->kbig = nullptr;
+    ctx->cap_ykr = ctx->cap_kbig = 0;
+}
+
 void free_all(okr_ctx *ctx) {
+    free_kron(ctx);
     for (void *p : ctx->allocs) cudaFree(p);
     ctx->allocs.clear();
     for (void *p : ctx->work_allocs) cudaFree(p);
@@ -291,6 +313,7 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     CK(cudaMemcpy(stats, T.maxd, sizeof stats, cudaMemcpyDeviceToHost));
     ctx->max_depth = stats[0];
     ctx->sum_sz = stats[1];
+    ctx->have_topo = true;
     return OKR_OK;
 }
 
@@ -426,7 +449,9 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
                        const okr_params *p, Src src) {
     if (!ctx) return OKR_EINVAL;
     ctx->have_result = false;
+    ctx->have_topo = false;
     ctx->launches = 0;
+    ctx->kron_ms = 0.0;
     okr_status s = check_feeder_shape(ctx, f);
     if (s != OKR_OK) return s;
     s = check_params(ctx, p);
@@ -578,6 +603,7 @@ okr_status okr_reduce_ops(okr_ctx *ctx, const okr_feeder *f, const double *vhat,
 okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, double *ihat_out, int32_t *sweeps) {
     if (!ctx) return OKR_EINVAL;
     ctx->have_result = false;
+    ctx->have_topo = false;
     okr_status s = check_feeder_shape(ctx, f);
     if (s != OKR_OK) return s;
     if (!f->s_load || !vhat_out) return fail(ctx, OKR_EINVAL, "s_load or vhat_out is NULL");
@@ -621,6 +647,113 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     return OKR_OK;
 }
 
+okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_out, int32_t *phase_node,
+                    int32_t *k_phi) {
+    if (!ctx || !k_phi) return OKR_EINVAL;
+    if (!ctx->have_topo) return fail(ctx, OKR_ENOTREADY, "no feeder: run a reduction or a load flow first");
+    if (!kept && !ctx->have_result) return fail(ctx, OKR_ENOTREADY, "no reduction result to take the kept set from");
+    if ((y_out || phase_node) && cap < 0) return fail(ctx, OKR_EINVAL, "cap < 0");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->T.n;
+    if (ctx->cap_kron_n < n) {
+        for (void *q : ctx->kron_allocs) cudaFree(q);
+        ctx->kron_allocs.clear();
+        ctx->cap_kron_n = 0;
+        KronWork &W = ctx->kw;
+        auto take = [&](auto **ptr, size_t count) -> cudaError_t {
+            void *q = nullptr;
+            cudaError_t e = cudaMalloc(&q, sizeof(**ptr) * (count ? count : 1));
+            if (e == cudaSuccess) { ctx->kron_allocs.push_back(q); *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q); }
+            return e;
+        };
+        const size_t N = n;
+        CK(take(&W.keptp, N));
+        CK(take(&W.g, N));
+        CK(take(&W.key, N));
+        CK(take(&W.cnt, N));
+        CK(take(&W.dsum, N));
+        CK(take(&W.fill, N));
+        CK(take(&W.goff, N));
+        CK(take(&W.ports, N));
+        CK(take(&W.out_off, N + 1));
+        CK(take(&W.pn, 3 * N));
+        CK(take(&W.gkey, N));
+        CK(take(&W.gp, N));
+        CK(take(&W.gd, N));
+        CK(take(&W.gport, N + 1));
+        CK(take(&W.grow, N + 1));
+        CK(take(&W.rows, 3 * N));
+        CK(take(&W.gbig, N));
+        CK(take(&W.hdr, 1));
+        CK(take(&ctx->kron_kept, N));
+        ctx->cap_kron_n = n;
+    }
+    KronWork &W = ctx->kw;
+    uint8_t *kept_dev = nullptr;
+    if (kept) {
+        kept_dev = ctx->kron_kept;
+        CK(cudaMemcpyAsync(kept_dev, kept, n, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(W.hdr, 0, sizeof(KronHdr), st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, st));
+    k_kron_groups<<<1, 1024, 0, st>>>(ctx->T, kept ? nullptr : ctx->S.label, kept_dev, W);
+    CK(cudaGetLastError());
+    KronHdr h{};
+    CK(cudaMemcpyAsync(&h, W.hdr, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    okr_status s = OKR_OK;
+    if (h.err == 1) s = fail(ctx, OKR_EINVAL, "the slack bus (bus 0) must be kept");
+    else if (h.max_d > kKronMaxGroup)
+        s = fail(ctx, OKR_EINVAL, "a reduced component has %d boundary phase-nodes (at most %d)", h.max_d, kKronMaxGroup);
+    if (s != OKR_OK || (!y_out && !phase_node)) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        *k_phi = h.k_phi;
+        return s;
+    }
+    *k_phi = h.k_phi;
+    if (cap < h.k_phi) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(ctx, OKR_EINVAL, "cap %d < k_phi %d", cap, h.k_phi);
+    }
+    const size_t K = h.k_phi, need_y = K * K, need_big = (size_t)h.big_total;
+    if (need_y > ctx->cap_ykr) {
+        if (ctx->ykr) cudaFree(ctx->ykr);
+        ctx->ykr = nullptr;
+        ctx->cap_ykr = 0;
+        CK(cudaMalloc(&ctx->ykr, sizeof(double2) * need_y));
+        ctx->cap_ykr = need_y;
+    }
+    if (need_big > ctx->cap_kbig) {
+        if (ctx->kbig) cudaFree(ctx->kbig);
+        ctx->kbig = nullptr;
+        ctx->cap_kbig = 0;
+        CK(cudaMalloc(&ctx->kbig, sizeof(double2) * need_big));
+        ctx->cap_kbig = need_big;
+    }
+    CK(cudaMemsetAsync(ctx->ykr, 0, sizeof(double2) * need_y, st));
+    CK(launch_kron_solve(h.n_groups, ctx->T, W, ctx->kbig, ctx->ykr, (int)K, st));
+    if (K > 0) k_kron_diag<<<blocks_for(K * 32, 256, ctx->num_sms * 8), 256, 0, st>>>(W, ctx->ykr, (int)K);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(e1, st));
+    CK(cudaMemcpyAsync(&h, W.hdr, sizeof h, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ctx->kron_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (h.err == 2) return fail(ctx, OKR_ESINGULAR, "singular port impedance block in the Kron reduction");
+    if (y_out) CK(cudaMemcpy(y_out, ctx->ykr, sizeof(double2) * need_y, cudaMemcpyDeviceToHost));
+    if (phase_node) CK(cudaMemcpy(phase_node, W.pn, sizeof(int) * K, cudaMemcpyDeviceToHost));
+    return OKR_OK;
+}
+
 okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     if (!ctx || !out) return OKR_EINVAL;
     if (!ctx->have_result) return OKR_ENOTREADY;
@@ -641,6 +774,7 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->sweeps = ctx->last.iters;
     out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
     out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
+    out->kron_ms = ctx->kron_ms;
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
     for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;

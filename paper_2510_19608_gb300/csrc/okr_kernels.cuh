@@ -21,6 +21,32 @@ __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J
 __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);
 __global__ void k_state_init(int n, int L, Topo T, State S);
 
+// okr_kron.cu
+constexpr int kKronShared = 64;     // groups up to this many phase-nodes are inverted in shared memory
+constexpr int kKronMaxGroup = 1024; // larger groups are refused (dense inverse per group)
+struct KronHdr {
+    int n_groups, k_phi, max_d, err;
+    long long big_total;            // double2 elements of global scratch for large groups
+};
+// Work arrays of the Y_Kron build (preorder ids unless noted).
+struct KronWork {
+    uint8_t *keptp;                 // [n] kept flag
+    int *g;                         // [n] component top of a reduced bus
+    int *key;                       // [n] group key of a kept non-root bus
+    int *cnt, *dsum, *fill, *goff;  // [n] per key: ports, phase-nodes, fill counter, port offset
+    int *ports;                     // [n] ports grouped by key
+    int *out_off;                   // [n+1] output row offset per CALLER bus id
+    int *pn;                        // [3n] output row -> caller bus * 3 + phase
+    int *gkey, *gp, *gd;            // [n] per group: key, reference bus p, phase-nodes d
+    int *gport, *grow;              // [n+1] per group: first port, first row
+    int *rows;                      // [3n] per group rows: preorder bus * 4 + phase
+    long long *gbig;                // [n] per group offset into the global scratch
+    KronHdr *hdr;
+};
+__global__ void __launch_bounds__(1024) k_kron_groups(Topo T, const int *label, const uint8_t *kept_in, KronWork W);
+__global__ void k_kron_diag(KronWork W, double2 *Y, int K);
+cudaError_t launch_kron_solve(int n_groups, Topo T, KronWork W, double2 *big, double2 *Y, int K, cudaStream_t st);
+
 // okr_persist.cu
 cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st);
 int search_blocks_per_sm();     // CTAs of the search kernel that fit one SM (0 on error)
