@@ -79,7 +79,9 @@ typedef struct okr_params {
     double target_reduction;    /* stop after ceil(target * n_bus) merges (capped at
                                    n_bus - 1); 1.0 = run until no candidate is feasible */
     double tie_tol;             /* tie band tau on the score, >= 0 (default 1e-9) */
-    int32_t objective;          /* 0 = SMICE (Algorithm 1); other values are rejected */
+    int32_t objective;          /* 0 = SMICE (Algorithm 1); 1 = the largest per-phase error of the
+                                   candidate network (the iteration objective of Sec. IV), with
+                                   precision 0 only; other values are rejected */
     int32_t precision;          /* 0 = every candidate scored in FP64;
                                    1 = FP32 screen with a rigorous error bound, FP64 rescoring of
                                    the candidates the bound cannot separate, FP64 merges.  Both

@@ -216,6 +216,8 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     CK(dalloc(ctx, &X.feas, 2 * N));
     CK(dalloc(ctx, &X.scr, 2 * N));
     CK(dalloc(ctx, &X.wsum, (size_t)ctx->num_sms * (512 / 32)));
+    CK(dalloc(ctx, &X.mrank, N));
+    CK(dalloc(ctx, &X.bmax, N / 32 + 2));
     CK(dalloc(ctx, &ctx->gb, 1));
     X.chunk_first = nullptr;
     X.partial = nullptr;
@@ -265,7 +267,9 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
     if (!(p->tie_tol >= 0.0) || !std::isfinite(p->tie_tol)) return fail(ctx, OKR_EINVAL, "tie_tol must be >= 0");
     if (p->max_merges < 0 && !(p->target_reduction >= 0.0 && p->target_reduction <= 1.0))
         return fail(ctx, OKR_EINVAL, "target_reduction outside [0, 1]");
-    if (p->objective != 0) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
+    if (p->objective != 0 && p->objective != 1) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
+    if (p->objective == 1 && p->precision != 0)
+        return fail(ctx, OKR_EINVAL, "objective 1 (largest error) runs with precision 0 only");
     if (p->precision != 0 && p->precision != 1) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
     if (p->record_iters < 0) return fail(ctx, OKR_EINVAL, "record_iters < 0");
     if (p->reserved != 0) return fail(ctx, OKR_EINVAL, "reserved must be 0");
@@ -385,10 +389,13 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     c.profile = p->profile ? 1 : 0;
     c.n_super = n;
     c.precision = p->precision;
+    c.objective = p->objective;
     c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
     CK(cudaMemcpyAsync(ctx->C, &c, sizeof c, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
     CK(cudaMemsetAsync(X.arrive, 0, sizeof(int) * 2 * n, st));
+    CK(cudaMemsetAsync(X.mrank, 0, sizeof(double) * n, st));           // every MICE starts at 0
+    CK(cudaMemsetAsync(X.bmax, 0, sizeof(double) * (n / 32 + 2), st));
     CK(cudaMemsetAsync(ctx->gb, 0, sizeof(GridBar), st));
     if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
     ctx->rec_iters = p->record_iters;

@@ -111,6 +111,8 @@ struct Ctrl {
     int precision;          // 0 FP64 sweep, 1 FP32 screen + FP64 recheck
     int rechecks;           // iterations that needed an FP64 recheck
     int recheck_cands;      // candidates rechecked in FP64 over the run
+    int objective;          // 0 SMICE (Algorithm 1), 1 largest error of the candidate network
+    int pad_obj;
     double margin;          // voltage-error bound (p.u.)
     double tau;             // tie band
     double s_cur;           // SMICE of the current state
@@ -140,6 +142,8 @@ struct Search {
     int *feas;              // [2n]
     float4 *scr;            // [2n] screen: (D32, bound of D, max new MICE, bound of it)
     double *wsum;           // [grid*warps] per-warp FP64 score change of the committed merge
+    double *mrank;          // [n] objective 1: largest MICE over scenarios, by super-node rank
+    double *bmax;           // [n/32+1] objective 1: max of mrank over each block of 32 ranks
     int max_chunks;
     // per-iteration record
     int *dec_s, *dec_r;     // caller ids

@@ -339,9 +339,36 @@ __device__ __forceinline__ void seg_scan_setup(bool active, int ci, int lane, un
     last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
 }
 
+// Objective 1: the largest MICE among the clusters a candidate leaves unchanged,
+// i.e. over the super-node ranks outside [js, js+ns), [jr, jr+nr) and, when s is
+// the common ancestor, s's own rank.  Whole blocks of 32 ranks come from bmax,
+// the (at most five) partly excluded blocks rank by rank.  Warp-cooperative; the
+// result is returned to every lane.
+__device__ __forceinline__ double unaffected_max(const Search &X, int nsn, int js, int ns, int jr, int nr, int jfix) {
+    const int lane = threadIdx.x & 31;
+    double u = 0.0;
+    const int nb = (nsn + 31) >> 5;
+    for (int b = lane; b < nb; b += 32) {
+        const int lo = b << 5, hi = min(nsn, lo + 32);
+        const bool touch = (js < hi && js + ns > lo && ns > 0) || (jr < hi && jr + nr > lo && nr > 0) ||
+                           (jfix >= lo && jfix < hi);
+        if (!touch) {
+            u = fmax(u, ldd(X.bmax + b));
+        } else {
+            for (int j = lo; j < hi; ++j) {
+                const bool ex = (j >= js && j < js + ns) || (j >= jr && j < jr + nr) || j == jfix;
+                if (!ex) u = fmax(u, ldd(X.mrank + j));
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+    return u;
+}
+
 __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
-                              double margin, double *out_score, int *out_feas, bool prof, double &flops) {
+                              double margin, double *out_score, int *out_feas, bool prof, double &flops,
+                              bool obj1 = false, int nsn = 0) {
     const int lane = threadIdx.x & 31, sub = lane % SP, l = sub >> 2, p = sub & 3;
     int k = cd.r;
     bool sside = false;
@@ -380,11 +407,15 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
         const double z = __shfl_up_sync(0xffffffffu, ml, o2);
         if (lane - o2 >= seg_start) { dl += y; ml = fmax(ml, z); }
     }
-    bool fin = false;
+    bool fin = false, direct = false;
     if (active && last) {
         if (np == 1) {                      // the whole candidate lies in this chunk
-            out_score[ci] = dl;
-            out_feas[ci] = (ml <= margin);
+            if (obj1) {
+                direct = true;
+            } else {
+                out_score[ci] = dl;
+                out_feas[ci] = (ml <= margin);
+            }
         } else {
             X.partial[g + ci] = make_double2(dl, ml);
             __threadfence();
@@ -410,10 +441,34 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
             sum += __shfl_xor_sync(0xffffffffu, sum, o2);
             mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
         }
+        if (obj1) {
+            const int js = __shfl_sync(0xffffffffu, cd.js, src), nsr = __shfl_sync(0xffffffffu, cd.ns, src);
+            const int jr = __shfl_sync(0xffffffffu, cd.jr, src), nr = __shfl_sync(0xffffffffu, cd.nr, src);
+            const int fx = __shfl_sync(0xffffffffu, cd.fixed, src), s = __shfl_sync(0xffffffffu, cd.s, src);
+            const int jf = fx ? ldi(S.sn_rank + s) : -1;
+            sum = fmax(mx, unaffected_max(X, nsn, js, nsr, jr, nr, jf));
+        }
         if (lane == 0) {
             out_score[fci] = sum;
             out_feas[fci] = (mx <= margin);
             X.arrive[fci] = 0;
+        }
+    }
+    // objective 1, single-chunk candidates: largest error over the whole network
+    unsigned dm = __ballot_sync(0xffffffffu, direct);
+    while (dm) {
+        const int src = __ffs(dm) - 1;
+        dm &= dm - 1;
+        const int fci = __shfl_sync(0xffffffffu, ci, src);
+        const double fml = __shfl_sync(0xffffffffu, ml, src);
+        const int js = __shfl_sync(0xffffffffu, cd.js, src), nsr = __shfl_sync(0xffffffffu, cd.ns, src);
+        const int jr = __shfl_sync(0xffffffffu, cd.jr, src), nr = __shfl_sync(0xffffffffu, cd.nr, src);
+        const int fx = __shfl_sync(0xffffffffu, cd.fixed, src), s = __shfl_sync(0xffffffffu, cd.s, src);
+        const int jf = fx ? ldi(S.sn_rank + s) : -1;
+        const double u = unaffected_max(X, nsn, js, nsr, jr, nr, jf);
+        if (lane == 0) {
+            out_score[fci] = fmax(fml, u);
+            out_feas[fci] = (fml <= margin);
         }
     }
 }
@@ -698,6 +753,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
     const double margin = C->margin, tau = C->tau;
     const int max_merges = C->max_merges;
     const bool prof = C->profile != 0;
+    const bool obj1 = (PREC == 0) && C->objective == 1;
     const bool lead = (blockIdx.x == 0 && tid == 0);
     unsigned epoch = 0;
     int t = C->t, ns = C->n_super;
@@ -812,7 +868,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                         const Cand cc = ldcand(X.cand + c);
                         X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
                         X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
-                        X.rec_score[(size_t)t * 2 * n + c] = ldi(X.feas + c) ? s_cur + ldd(X.score + c) : INFINITY;
+                        X.rec_score[(size_t)t * 2 * n + c] =
+                            ldi(X.feas + c) ? (obj1 ? 0.0 : s_cur) + ldd(X.score + c) : INFINITY;
                         X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
                     }
                 }
@@ -898,6 +955,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 X.dec_r[t] = T.orig[cd.r];
                 X.dec_gap[t] = sel.gap;
                 X.dec_ncand[t] = nc;
+                if (obj1) X.dec_score[t] = ldd(X.score + sel.w);    // largest error of the chosen network
             }
             stamp(2);
             committed = true;
@@ -968,7 +1026,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 for (int o2 = 16; o2 > 0; o2 >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o2);
                 if (lane == 0) {
                     s_cur += d;
-                    X.dec_score[told] = s_cur;
+                    if (!obj1) X.dec_score[told] = s_cur;
                     for (int l = 0; l < L; ++l) {
                         S.mice[(size_t)l * n + r0] = 0.0;
                         S.mice32[(size_t)l * n + r0] = 0.0f;
@@ -982,11 +1040,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             // super-node list after the merge (other buffer), ranks, largest MICE
             int *list_new = S.sn_list[t & 1];
             unsigned long long m = 0;          // MICE >= 0: bit patterns order like the values
-            for (int j = gt; j < ns; j += gs) {
-                const int k = ldi(list_old + j + (j >= jr0 ? 1 : 0));
-                list_new[j] = k;
-                for (int l = 0; l < L; ++l)
-                    m = max(m, (unsigned long long)__double_as_longlong(ldd(S.mice + (size_t)l * n + k)));
+            for (int j0 = gt - lane; j0 < ns; j0 += gs) {     // warp-uniform trip count
+                const int j = j0 + lane;
+                double mr = 0.0;
+                if (j < ns) {
+                    const int k = ldi(list_old + j + (j >= jr0 ? 1 : 0));
+                    list_new[j] = k;
+                    for (int l = 0; l < L; ++l) mr = fmax(mr, ldd(S.mice + (size_t)l * n + k));
+                    m = max(m, (unsigned long long)__double_as_longlong(mr));
+                    if (obj1) X.mrank[j] = mr;
+                }
+                if (obj1) {                                   // 32 consecutive ranks per warp
+                    for (int o2 = 16; o2 > 0; o2 >>= 1) mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o2));
+                    if (lane == 0) X.bmax[j0 >> 5] = mr;
+                }
             }
             for (int b = r0 + 1 + gt; b <= n; b += gs) S.sn_rank[b] = ldi(S.sn_rank + b) - 1;
             m = block_reduce(m, MaxU(), smu);
@@ -1096,7 +1163,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 }
                 if (PREC == 0)
                     score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, margin,
-                                  X.score, X.feas, prof, flops);
+                                  X.score, X.feas, prof, flops, obj1, ns);
                 else
                     score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops);
             }

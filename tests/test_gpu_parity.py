@@ -141,6 +141,44 @@ def test_every_candidate_score_matches_oracle(ctx):
                     assert abs(v - w) <= S_TOL, (t, key, v, w)
 
 
+# ----------------------------------------------------------------------------- objective 1
+OBJ1_FEEDERS = {
+    "feeder40": lambda: fg.preset("feeder40")[0],
+    "feeder1000_300": lambda: fg.preset("feeder1000", n_bus=300)[0],
+    "mixed200": lambda: fg.make_feeder(200, 21, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(OBJ1_FEEDERS))
+def test_max_error_objective_matches_oracle(ctx, name):
+    """objective = 1: each candidate is scored by the largest per-phase error of
+    its network (the iteration objective of Sec. IV); decisions and every
+    recorded score must match the oracle's."""
+    f = OBJ1_FEEDERS[name]()
+    K = 4
+    vhat, ihat = O.operating_points(f)
+    merges = f.n_bus - 1 if name == "feeder40" else f.n_bus // 2
+    res = O.reduce(f, vhat, ihat, margin=0.005, max_merges=merges, objective=1, record_iters=K)
+    ctx.reduce(f, params(margin=0.005, max_merges=merges, objective=1, precision=0, record_iters=K))
+    assert_same_run(ctx, res, vhat)
+    for t in range(min(K, res["n_iter"])):
+        rec_o, rec_g = res["recorded"][t], ctx.recorded(t)
+        go = {(int(s), int(r)): v for s, r, v in zip(rec_o["s"], rec_o["r"], rec_o["score"])}
+        gg = {(int(s), int(r)): v for s, r, v in zip(rec_g["s"], rec_g["r"], rec_g["score"])}
+        assert set(go) == set(gg)
+        for key, v in go.items():
+            w = gg[key]
+            assert (math.isinf(v) and math.isinf(w)) or abs(v - w) <= S_TOL, (t, key, v, w)
+
+
+def test_max_error_objective_needs_fp64(ctx):
+    import paper_2510_19608_gb300 as K
+    f, _ = fg.preset("feeder40")
+    with pytest.raises(K.OkrError) as e:
+        ctx.reduce(f, params(objective=1, precision=1))
+    assert e.value.status == 1
+
+
 def test_reduce_ops_with_oracle_operating_points(ctx):
     f, run = fg.preset("feeder40")
     vhat, ihat = O.operating_points(f)
