@@ -306,10 +306,10 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     if (s != OKR_OK) return s;
     k_child_offsets<<<1, 1024, 0, st>>>(n, T, ctx->coff_c, ctx->child_c);
     const int LOG = log2_ceil(n) + 1;
-    for (int j = 0; j < LOG; ++j) k_rmq_level<<<blocks_for(n, 256, 1 << 20), 256, 0, st>>>(n, j, T.depth, ctx->rmq);
+    k_rmq_all<<<1, 1024, 0, st>>>(n, LOG, T.depth, ctx->rmq);
     k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, T.parent, T.sz, T.depth, ctx->rmq, T.lca);
-    k_lines<<<1, 1024, 0, st>>>(n, T, ctx->z_in, ctx->err_dev);
-    ctx->launches += 3 + LOG;
+    CK(launch_lines(n, T, ctx->z_in, ctx->err_dev, ctx->num_sms, st));
+    ctx->launches += 5;
     CK(cudaGetLastError());
     s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
@@ -329,6 +329,7 @@ okr_status read_setup_errors(okr_ctx *ctx) {
     if (e == 1) return fail(ctx, OKR_EINVAL, "invalid feeder: parent[0] must be -1, parent[i] < i, phases non-empty and within the parent's");
     if (e == 2) return fail(ctx, OKR_ESINGULAR, "singular line impedance block");
     if (e == 3) return fail(ctx, OKR_EPF, "load flow did not converge in %d sweeps", kPfMaxIter);
+    if (e == 6) return fail(ctx, OKR_ETIMEOUT, "a grid barrier of the load flow gave up");
     if (e) return fail(ctx, OKR_EINTERNAL, "device error %d", e);
     return OKR_OK;
 }
@@ -336,7 +337,9 @@ okr_status read_setup_errors(okr_ctx *ctx) {
 okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
     cudaStream_t st = ctx->stream;
     Topo &T = ctx->T;
-    k_power_flow<<<L, 1024, 0, st>>>(n, L, T, ctx->s_in, kPfTol, kPfMaxIter, ctx->J, ctx->pf_iters, ctx->err_dev);
+    // the load flow's work buffers alias T.ihat and T.amag, which the next two kernels fill
+    CK(launch_power_flow(n, L, T, ctx->s_in, kPfTol, kPfMaxIter, ctx->J, T.ihat, T.amag, ctx->pf_iters,
+                         ctx->err_dev, ctx->num_sms, st));
     k_line_currents<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
     k_injections<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
     ctx->launches += 3;

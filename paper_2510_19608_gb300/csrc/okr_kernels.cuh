@@ -11,11 +11,16 @@ __global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict_
                            int *coff_c, int *child_c, int *err);
 __global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c);
 __global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_t *st);
+__global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__restrict__ depth, uint16_t *st);
 __global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
                            const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca);
-__global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__restrict__ z_in, int *err);
-__global__ void __launch_bounds__(1024) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol, int max_iter,
-                             double2 *J, int *iters, int *err);
+// line inverses (grid) and path impedances (one CTA)
+cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st);
+// load flow of every scenario (cooperative launch).  J: [L*3n] line currents,
+// W: [L*3n] work (its contents are overwritten), red: [3L+1] doubles of
+// reduction slots and barrier counter (cleared by the launch), iters: [L].
+cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double tol, int max_iter, double2 *J,
+                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st);
 __global__ void k_line_currents(int n, int L, Topo T, double2 *J);
 __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J);
 __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);

@@ -175,15 +175,39 @@ __global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict_
 // node v are those of caller bus orig[v], already converted to preorder ids
 // and increasing.
 __global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c) {
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int v = 0; v < n; ++v) {
-            int i = T.orig[v];
-            T.child_off[v] = acc;
-            acc += coff_c[i + 1] - coff_c[i];
+    // exclusive scan of the child counts in preorder, 1024 buses per pass
+    __shared__ int s_w[32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int v = base + tid;
+        int c = 0;
+        if (v < n) { const int i = T.orig[v]; c = coff_c[i + 1] - coff_c[i]; }
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        T.child_off[n] = acc;
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? s_w[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_w[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        if (v < n) T.child_off[v] = carry + (warp > 0 ? s_w[warp - 1] : 0) + x - c;
+        __syncthreads();
+        if (tid == 0) s_carry = carry + s_w[nw - 1];
+        __syncthreads();
     }
+    if (tid == 0) T.child_off[n] = s_carry;
     __syncthreads();
     for (int v = threadIdx.x; v < n; v += blockDim.x) {
         int i = T.orig[v];
@@ -207,6 +231,25 @@ __global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_
         if (depth[b] < depth[a]) a = b;
     }
     st[(size_t)j * n + v] = (uint16_t)a;
+}
+
+// All levels of the sparse table in one CTA (levels 0 .. nlev-1).
+__global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__restrict__ depth, uint16_t *st) {
+    for (int v = threadIdx.x; v < n; v += blockDim.x) st[v] = (uint16_t)v;
+    __syncthreads();
+    for (int j = 1; j < nlev; ++j) {
+        const int h = 1 << (j - 1);
+        for (int v = threadIdx.x; v < n; v += blockDim.x) {
+            int a = st[(size_t)(j - 1) * n + v];
+            const int w = v + h;
+            if (w + h <= n) {
+                const int b = st[(size_t)(j - 1) * n + w];
+                if (depth[b] < depth[a]) a = b;
+            }
+            st[(size_t)j * n + v] = (uint16_t)a;
+        }
+        __syncthreads();
+    }
 }
 
 // LCA[u][v] for all pairs (preorder ids).  For u < v: if v lies in u's subtree
@@ -234,10 +277,11 @@ __global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__r
 
 // Line data in preorder: zl, yl (inverse on the bus phases); path impedance by
 // levels (parents first).  One CTA.
-__global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__restrict__ z_in, int *err) {
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int v = tid; v < n; v += nt) {
-        int i = T.orig[v];
+// Line data: copies of the impedances and their inverses on the line's phases,
+// one thread per bus over the whole grid.
+__global__ void k_line_inverses(int n, Topo T, const double *__restrict__ z_in, int *err) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        const int i = T.orig[v];
         double2 z[9];
         for (int q = 0; q < 9; ++q) {
             z[q] = (v == 0) ? make_double2(0.0, 0.0) : make_double2(z_in[((size_t)i * 9 + q) * 2], z_in[((size_t)i * 9 + q) * 2 + 1]);
@@ -252,7 +296,12 @@ __global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__r
         }
         for (int q = 0; q < 9; ++q) T.yl[(size_t)v * 9 + q] = y[q];
     }
-    __syncthreads();
+}
+
+// Path impedances root -> k level by level (one CTA), then their split into
+// two floats for the screening sweep.
+__global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
+    const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = tid; q < 9; q += nt) T.zc[q] = make_double2(0.0, 0.0);
     __syncthreads();
     const int maxd = T.maxd[0];
@@ -272,76 +321,214 @@ __global__ void __launch_bounds__(1024) k_lines(int n, Topo T, const double *__r
     }
 }
 
+cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
+    int blocks = (n + 255) / 256;
+    if (blocks > num_sms * 8) blocks = num_sms * 8;
+    k_line_inverses<<<blocks, 256, 0, st>>>(n, T, z_in, err);
+    k_path_impedance<<<1, 1024, 0, st>>>(n, T);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- load flow
-// Backward/forward sweep, one CTA per scenario.  Constant-power wye loads:
-// current drawn at (k,p) is conj(S/V).  Backward: J_k = load(k) + sum of the
+// Backward/forward sweep for every scenario.  Constant-power wye loads: the
+// current drawn at (k,p) is conj(S/V).  Backward: J_k = load(k) + the sum of the
 // children's J (children in preorder order).  Forward: V_k = V_parent - z_k J_k.
-// Stops when max |dV| < tol; otherwise reports failure.
-__global__ void __launch_bounds__(1024) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol, int max_iter,
-                             double2 *J, int *iters, int *err) {
-    const int l = blockIdx.x;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    double2 *V = T.vhat;
-    double2 *Jl = J + (size_t)l * 3 * n;
-    __shared__ double s_red[32];
-    __shared__ int s_conv;
-    for (int v = tid; v < n; v += nt)
-        for (int p = 0; p < 3; ++p)
-            V[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
+// A scenario stops when max |dV| < tol; one that has not stopped after max_iter
+// sweeps is a failure.
+//
+// FP64 division, the 3x3 products and the magnitudes dominate the arithmetic,
+// and GB300's FP64 rate per SM is low, so these run over the whole cooperative
+// grid; only the level-by-level sums (additions) run one CTA per (scenario,
+// phase), staged in shared memory.  Five grid barriers per sweep:
+//   S1 load currents I1 = conj(S / V)          (grid)
+//   S2 line currents J = I1 + sum children J  (CTA per (l, p), deepest level first)
+//   S3 drops D = z J                            (grid)
+//   S4 new voltages Vn = Vn_parent - D          (CTA per (l, p), top down)
+//   S5 |Vn - V|, V = Vn, per-scenario maximum   (grid)
+// I1, D and Vn share one buffer W (D overwrites I1, Vn overwrites D in place).
+// The arithmetic is the same, operation for operation, as a one-thread-per-bus
+// sweep.
+constexpr int kPfShared = 2048;     // buses whose (l, p) slice is staged in shared memory
+constexpr long long kPfSpins = 4000000;
+
+__device__ __forceinline__ unsigned pf_ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier on a monotonic counter; bounded: returns false (and sets
+// err = 6) when the wait gives up or another CTA already gave up.
+__device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsigned &epoch) {
+    __shared__ int s_ok;
     __syncthreads();
+    epoch += 1;
+    if (threadIdx.x == 0) {
+        const unsigned target = epoch * nblocks;
+        __threadfence();
+        atomicAdd(count, 1u);
+        int ok = 1;
+        long long spins = 0;
+        while (pf_ld_acquire(count) < target) {
+            if (++spins > kPfSpins || *(volatile int *)err == 6) { ok = 0; break; }
+            __nanosleep(20);
+        }
+        if (!ok) atomicExch(err, 6);
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok;
+}
+
+__global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol,
+                                                    int max_iter, double2 *J, double2 *W, double *red, unsigned *bar,
+                                                    int *iters, int *err) {
+    extern __shared__ double2 pf_sm[];
+    __shared__ int s_live[kMaxScen];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const unsigned G = gridDim.x;
+    const int gt = blockIdx.x * nt + tid, gs = (int)G * nt;
+    const size_t N3 = (size_t)3 * n;
+    const size_t tot = (size_t)L * N3;
     const int maxd = T.maxd[0];
+    unsigned epoch = 0;
+    for (size_t e = gt; e < tot; e += gs) {
+        const int v = (int)(e % n), p = (int)((e / n) % 3);
+        T.vhat[e] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
+    }
+    if (tid < kMaxScen) s_live[tid] = tid < L;
+    const bool line_cta = blockIdx.x < (unsigned)(3 * L);
+    const int ll = blockIdx.x / 3, lp = blockIdx.x % 3;      // (scenario, phase) of a level CTA
+    double2 *const loc = n <= kPfShared ? pf_sm : nullptr;
+    bool conv_all = false;
     int it;
-    bool conv = false;
     for (it = 1; it <= max_iter; ++it) {
-        for (int d = maxd; d >= 1; --d) {
-            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
-                int v = T.level_bus[x], i = T.orig[v];
-                for (int p = 0; p < 3; ++p) {
-                    double2 j = make_double2(0.0, 0.0);
-                    if (T.ph[v] >> p & 1u) {
-                        double2 s = make_double2(s_in[(((size_t)l * n + i) * 3 + p) * 2], s_in[(((size_t)l * n + i) * 3 + p) * 2 + 1]);
-                        j = cconj(cdiv(s, V[sidx(l, p, v, n)]));
-                    }
-                    for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Jl[(size_t)p * n + T.child[c]]);
-                    Jl[(size_t)p * n + v] = j;
-                }
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (gt == 0) for (int l = 0; l < L; ++l) red[((it + 1) % 3) * L + l] = 0.0;
+        // S1: load currents
+        for (size_t e = gt; e < tot; e += gs) {
+            const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
+            if (!s_live[l]) continue;
+            double2 j = make_double2(0.0, 0.0);
+            if (T.ph[v] >> p & 1u) {
+                const size_t o = (((size_t)l * n + T.orig[v]) * 3 + p) * 2;
+                const double2 sv = make_double2(__ldg(s_in + o), __ldg(s_in + o + 1));
+                j = cconj(cdiv(sv, T.vhat[e]));
+            }
+            W[e] = j;
+        }
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        // S2: line currents, deepest level first
+        if (line_cta && s_live[ll]) {
+            const size_t off = ((size_t)ll * 3 + lp) * n;
+            double2 *Jx = loc ? loc : J + off;
+            if (loc) {
+                for (int v = tid; v < n; v += nt) loc[v] = W[off + v];
+            } else {
+                for (int v = tid; v < n; v += nt) Jx[v] = W[off + v];
             }
             __syncthreads();
-        }
-        double dmax = 0.0;
-        for (int d = 1; d <= maxd; ++d) {
-            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
-                int v = T.level_bus[x], par = T.parent[v];
-                for (int p = 0; p < 3; ++p) {
-                    if (!(T.ph[v] >> p & 1u)) continue;
-                    double2 drop = make_double2(0.0, 0.0);
-                    for (int q = 0; q < 3; ++q)
-                        if (T.ph[v] >> q & 1u) drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], Jl[(size_t)q * n + v]));
-                    double2 vn = csub(V[sidx(l, p, par, n)], drop);
-                    double dd = cmag(csub(vn, V[sidx(l, p, v, n)]));
-                    if (!isfinite(dd)) dd = INFINITY;          // a diverging sweep never converges
-                    dmax = fmax(dmax, dd);
-                    V[sidx(l, p, v, n)] = vn;
+            for (int d = maxd; d >= 1; --d) {
+                for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                    const int v = T.level_bus[x];
+                    double2 j = Jx[v];
+                    for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Jx[T.child[c]]);
+                    Jx[v] = j;
                 }
+                __syncthreads();
             }
+            if (loc)
+                for (int v = tid; v < n; v += nt) J[off + v] = loc[v];
+        }
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        // S3: drops z J on the phases of each line (root excluded)
+        for (size_t e = gt; e < tot; e += gs) {
+            const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
+            if (!s_live[l]) continue;
+            const unsigned ph = T.ph[v];
+            double2 drop = make_double2(0.0, 0.0);
+            if (v > 0 && (ph >> p & 1u))
+                for (int q = 0; q < 3; ++q)
+                    if (ph >> q & 1u)
+                        drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], J[(size_t)l * N3 + (size_t)q * n + v]));
+            W[e] = drop;
+        }
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        // S4: new voltages, top down (Vn overwrites D)
+        if (line_cta && s_live[ll]) {
+            const size_t off = ((size_t)ll * 3 + lp) * n;
+            double2 *Vx = loc ? loc : W + off;
+            if (loc)
+                for (int v = tid; v < n; v += nt) loc[v] = W[off + v];
             __syncthreads();
+            if (tid == 0) Vx[0] = T.vhat[off];
+            __syncthreads();
+            for (int d = 1; d <= maxd; ++d) {
+                for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                    const int v = T.level_bus[x];
+                    Vx[v] = csub(Vx[T.parent[v]], Vx[v]);
+                }
+                __syncthreads();
+            }
+            if (loc)
+                for (int v = tid; v < n; v += nt) W[off + v] = loc[v];
         }
-        // block max of dmax
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if ((tid & 31) == 0) s_red[tid >> 5] = dmax;
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        // S5: change of the voltages, per-scenario maximum
+        double mx[kMaxScen] = {0.0, 0.0, 0.0, 0.0};
+        for (size_t e = gt; e < tot; e += gs) {
+            const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
+            if (!s_live[l] || v == 0 || !(T.ph[v] >> p & 1u)) continue;
+            const double2 vn = W[e];
+            double dd = cmag(csub(vn, T.vhat[e]));
+            if (!isfinite(dd)) dd = INFINITY;               // a diverging sweep never converges
+            T.vhat[e] = vn;
+            for (int l2 = 0; l2 < kMaxScen; ++l2)
+                if (l2 == l) mx[l2] = fmax(mx[l2], dd);
+        }
+        for (int l = 0; l < L; ++l) {
+            double m = mx[0];
+            if (l == 1) m = mx[1];
+            if (l == 2) m = mx[2];
+            if (l == 3) m = mx[3];
+            for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((tid & 31) == 0 && m > 0.0)
+                atomicMax((unsigned long long *)&red[(it % 3) * L + l], (unsigned long long)__double_as_longlong(m));
+        }
+        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        conv_all = true;
         __syncthreads();
-        if (tid == 0) {
-            double m = 0.0;
-            for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, s_red[w]);
-            s_conv = (m < tol);
+        if (tid < L && s_live[tid]) {
+            const double m = __longlong_as_double((long long)__ldcg((const unsigned long long *)&red[(it % 3) * L + tid]));
+            if (m < tol) {
+                s_live[tid] = 0;
+                if (blockIdx.x == 0) iters[tid] = it;
+            }
         }
         __syncthreads();
-        if (s_conv) { conv = true; break; }
+        for (int l = 0; l < L; ++l) conv_all = conv_all && !s_live[l];
+        if (conv_all) break;
     }
-    if (tid == 0) {
-        iters[l] = conv ? it : -1;
-        if (!conv) atomicExch(err, 3);
+    if (blockIdx.x == 0 && tid < L && s_live[tid]) {
+        iters[tid] = -1;
+        atomicExch(err, 3);
     }
+}
+
+// Blocks of the cooperative load flow: enough for the grid-wide stages, at
+// least one per (scenario, phase), at most one per SM.
+cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double tol, int max_iter, double2 *J,
+                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st) {
+    int G = (int)(((size_t)3 * L * n + 127) / 128);
+    if (G < 3 * L) G = 3 * L;
+    if (G > num_sms) G = num_sms;
+    const size_t smem = n <= kPfShared ? sizeof(double2) * (size_t)n : 0;
+    unsigned *bar = reinterpret_cast<unsigned *>(red + 3 * L);
+    cudaError_t e = cudaMemsetAsync(red, 0, sizeof(double) * (3 * L + 1), st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&n, &L, &T, &s_in, &tol, &max_iter, &J, &W, &red, &bar, &iters, &err};
+    return cudaLaunchCooperativeKernel((const void *)k_power_flow, dim3(G), dim3(256), args, smem, st);
 }
 
 // Ihat = Y Vhat line by line: line current J_k = y_k (V_parent - V_k) on the

@@ -180,6 +180,7 @@ okr_status read_err(const int *err_dev, cudaStream_t st) {
     if (e == 1) return OKR_EINVAL;
     if (e == 2) return OKR_ESINGULAR;
     if (e == 3) return OKR_EPF;
+    if (e == 6) return OKR_ETIMEOUT;
     return e ? OKR_EINTERNAL : OKR_OK;
 }
 
@@ -220,8 +221,11 @@ extern "C" okr_status okr_power_flow_static(const okr_feeder *f, double *vhat_ou
     s = read_err(w.err, st);
     if (s != OKR_OK) return s;
     k_child_offsets<<<1, 1024, 0, st>>>(n, T, w.coff_c, w.child_c);
-    k_lines<<<1, 1024, 0, st>>>(n, T, f->z_line, w.err);
-    k_power_flow<<<L, 1024, 0, st>>>(n, L, T, f->s_load, kPfTol, kPfMaxIter, w.J, w.sweeps, w.err);
+    if (launch_lines(n, T, f->z_line, w.err, slot.num_sms, st) != cudaSuccess) return OKR_ECUDA;
+    // the load flow's work buffers alias T.ihat and T.amag, which the next two kernels fill
+    if (launch_power_flow(n, L, T, f->s_load, kPfTol, kPfMaxIter, w.J, T.ihat, T.amag, w.sweeps, w.err,
+                          slot.num_sms, st) != cudaSuccess)
+        return OKR_ECUDA;
     k_line_currents<<<grid_for((size_t)L * n, slot.num_sms), 256, 0, st>>>(n, L, T, w.J);
     k_injections<<<grid_for((size_t)L * n, slot.num_sms), 256, 0, st>>>(n, L, T, w.J);
     k_export_static<<<grid_for((size_t)L * n, slot.num_sms), 256, 0, st>>>(T, vhat_out, ihat_out);
