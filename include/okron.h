@@ -170,6 +170,50 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
 okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_out,
                     int32_t *phase_node, int32_t *k_phi);
 
+/* ---- many feeders in one launch ----------------------------------------
+ * Result of one feeder of okr_reduce_batch. */
+typedef struct okr_batch_item {
+    int32_t status;             /* okr_status of this feeder */
+    int32_t n_iter;             /* merges committed */
+    int32_t stop_reason;        /* 0 target reached, 1 no feasible candidate */
+    int32_t n_kept;             /* super-nodes left */
+    int64_t candidates;         /* candidates evaluated */
+    double smice;               /* SMICE of the final reduction */
+    double max_error;           /* largest per-phase error of the final reduction */
+} okr_batch_item;
+
+typedef struct okr_batch_stats {
+    double setup_ms;            /* device time of the setup of every feeder (load flows included) */
+    double search_ms;           /* device time of the batched search launch(es) */
+    int64_t candidates;         /* over all feeders */
+    int32_t config;             /* CTA shape: 0/1/2 = 512/256/128 threads, 1/2/4 CTAs per SM */
+    int32_t ctas;               /* CTAs of the batched search launch */
+    int32_t fallbacks;          /* feeders re-run alone because their work buffer was too small */
+    int32_t reserved;
+} okr_batch_stats;
+
+/* Algorithm 1 for many independent feeders (Sec. IV; the candidates of one
+ * feeder are independent, and so are feeders): one batched setup of every
+ * feeder (load flows included), then ONE persistent launch in which each CTA
+ * takes the next feeder from a queue ordered largest-first and runs that
+ * feeder's whole search alone.  Each feeder's result is the one okr_reduce
+ * gives for it alone.
+ *
+ * feeders: [n_feeders] HOST feeders.  params: [n_params] with n_params = 1
+ * (shared) or n_feeders; record_iters must be 0.  items: [n_feeders] HOST,
+ * written.  super_of (HOST, may be NULL): the assignments, concatenated in
+ * feeder order (sum of n_bus entries).  stats (HOST, may be NULL).
+ * Returns a non-OK status only for bad arguments or a CUDA failure of the
+ * batch; each feeder's own outcome is in items[f].status. */
+okr_status okr_reduce_batch(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                            int32_t n_params, okr_batch_item *items, int32_t *super_of, okr_batch_stats *stats);
+
+/* Times the batched search with each CTA shape on this batch (two runs each),
+ * keeps the fastest for later okr_reduce_batch calls on this context, and
+ * returns it in *config (search_ms: [3] times in ms, may be NULL). */
+okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                              int32_t n_params, int32_t *config, double *search_ms);
+
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096
 

@@ -49,10 +49,20 @@ class Summary(C.Structure):
                 ("kron_ms", C.c_double)]
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_iter", C.c_int32), ("stop_reason", C.c_int32), ("n_kept", C.c_int32),
+                ("candidates", C.c_int64), ("smice", C.c_double), ("max_error", C.c_double)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("setup_ms", C.c_double), ("search_ms", C.c_double), ("candidates", C.c_int64),
+                ("config", C.c_int32), ("ctas", C.c_int32), ("fallbacks", C.c_int32), ("reserved", C.c_int32)]
+
+
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
-           "okr_power_flow_static", "okr_kron")
+           "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune")
 
 
 def lib_path() -> str:
@@ -83,6 +93,8 @@ def lib():
             L.okr_power_flow.argtypes = [P, C.POINTER(Feeder), P, P, P]
             L.okr_power_flow_static.argtypes = [C.POINTER(Feeder), P, P, P, P]
             L.okr_kron.argtypes = [P, P, I32, P, P, P]
+            L.okr_reduce_batch.argtypes = [P, I32, P, P, I32, P, P, P]
+            L.okr_batch_autotune.argtypes = [P, I32, P, P, I32, P, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -218,6 +230,43 @@ class Context:
         sw = C.c_int32()
         self._check(lib().okr_power_flow(self._h, C.byref(hf.c), _ptr(v), _ptr(i), C.byref(sw)))
         return v[..., 0] + 1j * v[..., 1], i[..., 0] + 1j * i[..., 1], int(sw.value)
+
+    @staticmethod
+    def _batch_args(feeders, params):
+        hfs = [HostFeeder(f) for f in feeders]
+        arr = (Feeder * len(hfs))(*[h.c for h in hfs])
+        plist = params if isinstance(params, (list, tuple)) else [params]
+        parr = (Params * len(plist))(*plist)
+        return hfs, arr, parr, len(plist)
+
+    def reduce_batch(self, feeders, params, want_assignment=True):
+        """okr_reduce_batch: many feeders in one launch.  params: one Params or
+        one per feeder.  Returns (items, assignments or None, stats) with items
+        and stats as dicts and one int32 array per feeder."""
+        hfs, arr, parr, npar = self._batch_args(feeders, params)
+        nf = len(hfs)
+        items = (BatchItem * nf)()
+        st = BatchStats()
+        tot = sum(h.c.n_bus for h in hfs)
+        sup = np.zeros(tot, np.int32) if want_assignment else None
+        self._check(lib().okr_reduce_batch(self._h, nf, arr, parr, npar, items,
+                                           _ptr(sup) if sup is not None else None, C.byref(st)))
+        out = [{k: getattr(it, k) for k, _ in BatchItem._fields_} for it in items]
+        parts = None
+        if sup is not None:
+            parts, o = [], 0
+            for h in hfs:
+                parts.append(sup[o:o + h.c.n_bus].copy())
+                o += h.c.n_bus
+        return out, parts, {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
+    def batch_autotune(self, feeders, params):
+        """okr_batch_autotune: returns (best config, search ms per config)."""
+        hfs, arr, parr, npar = self._batch_args(feeders, params)
+        cfg = C.c_int32()
+        ms = (C.c_double * 3)()
+        self._check(lib().okr_batch_autotune(self._h, len(hfs), arr, parr, npar, C.byref(cfg), ms))
+        return int(cfg.value), list(ms)
 
     def kron(self, kept=None):
         """Y_Kron onto `kept` (caller-order flags; None = the last reduction's

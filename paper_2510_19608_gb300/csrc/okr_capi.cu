@@ -4,7 +4,9 @@
 #include "okron.h"
 #include "okr_internal.cuh"
 #include "okr_kernels.cuh"
+#include "okr_layout.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -33,33 +35,14 @@ struct okr_ctx {
 
     // capacity of the workspace
     int cap_n = 0, cap_L = 0, cap_rec = 0;
-    std::vector<void *> allocs;
 
-    // inputs copied from the host
-    int *parent_in = nullptr;
-    uint8_t *ph_in = nullptr;
-    double *z_in = nullptr, *s_in = nullptr, *vh_in = nullptr, *ih_in = nullptr;
-    // topology scratch
-    int *dep = nullptr, *anc = nullptr, *anc2 = nullptr, *d2 = nullptr, *size = nullptr, *ccount = nullptr;
-    int *coff_c = nullptr, *child_c = nullptr;
-    uint16_t *rmq = nullptr;
-    double2 *J = nullptr;
-    int *pf_iters = nullptr, *err_dev = nullptr;
-    GridBar *gb = nullptr;
+    FeederBufs fb;                      // device buffers of the current feeder (one allocation)
+    void *arena = nullptr;
     int grid = 0;                       // CTAs of the persistent search kernel
     std::vector<void *> work_allocs;    // chunk map and partial sums (grown on demand)
     int cap_chunks = 0;
     int sum_sz = 0, max_depth = 0;      // of the current feeder
-    // outputs
-    int *super_out = nullptr;
-    double *vred_out = nullptr, *vhat_out = nullptr;
-
-    Topo T{};
-    State S{};
-    Search X{};
-    Ctrl *C = nullptr;
-    Ctrl *C_host = nullptr;     // pinned
-
+    Ctrl *C_host = nullptr;             // pinned
 
     // counters of the last call
     int64_t launches = 0;
@@ -73,6 +56,13 @@ struct okr_ctx {
     uint8_t *kron_kept = nullptr;
     size_t cap_ykr = 0, cap_kbig = 0;
     double kron_ms = 0.0;
+
+    // multi-feeder batch (grown on demand)
+    void *batch_arena = nullptr;
+    size_t batch_cap = 0;
+    unsigned char *batch_host = nullptr;    // pinned staging
+    size_t batch_host_cap = 0;
+    int batch_config = 1;                   // CTA shape of the batched search (autotuned)
 
     // last result
     bool have_topo = false;     // T describes the feeder of the last call
@@ -111,22 +101,23 @@ void free_kron(okr_ctx *ctx) {
     ctx->cap_ykr = ctx->cap_kbig = 0;
 }
 
+void free_batch(okr_ctx *ctx) {
+    if (ctx->batch_arena) cudaFree(ctx->batch_arena);
+    ctx->batch_arena = nullptr;
+    ctx->batch_cap = 0;
+    if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+    ctx->batch_host = nullptr;
+    ctx->batch_host_cap = 0;
+}
+
 void free_all(okr_ctx *ctx) {
     free_kron(ctx);
-    for (void *p : ctx->allocs) cudaFree(p);
-    ctx->allocs.clear();
+    if (ctx->arena) cudaFree(ctx->arena);
+    ctx->arena = nullptr;
     for (void *p : ctx->work_allocs) cudaFree(p);
     ctx->work_allocs.clear();
     ctx->cap_chunks = 0;
     ctx->cap_n = ctx->cap_L = ctx->cap_rec = 0;
-}
-
-template <typename T>
-cudaError_t dalloc(okr_ctx *ctx, T **p, size_t count) {
-    void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
-    if (e == cudaSuccess) { ctx->allocs.push_back(q); *p = (T *)q; }
-    return e;
 }
 
 int log2_ceil(int n) {
@@ -140,102 +131,15 @@ int log2_ceil(int n) {
 okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     if (n <= ctx->cap_n && L <= ctx->cap_L && rec <= ctx->cap_rec) return OKR_OK;
     free_all(ctx);
-    const size_t N = n, NL3 = (size_t)3 * L * n;
-    const int LOG = log2_ceil(n) + 1;
-    CK(dalloc(ctx, &ctx->parent_in, N));
-    CK(dalloc(ctx, &ctx->ph_in, N));
-    CK(dalloc(ctx, &ctx->z_in, N * 18));
-    CK(dalloc(ctx, &ctx->s_in, (size_t)L * N * 6));
-    CK(dalloc(ctx, &ctx->vh_in, (size_t)L * N * 6));
-    CK(dalloc(ctx, &ctx->ih_in, (size_t)L * N * 6));
-    CK(dalloc(ctx, &ctx->dep, N));
-    CK(dalloc(ctx, &ctx->anc, N));
-    CK(dalloc(ctx, &ctx->anc2, N));
-    CK(dalloc(ctx, &ctx->d2, N));
-    CK(dalloc(ctx, &ctx->size, N));
-    CK(dalloc(ctx, &ctx->ccount, N + 2));
-    CK(dalloc(ctx, &ctx->coff_c, N + 1));
-    CK(dalloc(ctx, &ctx->child_c, N));
-    CK(dalloc(ctx, &ctx->rmq, (size_t)LOG * N));
-    CK(dalloc(ctx, &ctx->J, NL3));
-    CK(dalloc(ctx, &ctx->pf_iters, (size_t)L));
-    CK(dalloc(ctx, &ctx->err_dev, 1));
-    CK(dalloc(ctx, &ctx->super_out, N));
-    CK(dalloc(ctx, &ctx->vred_out, (size_t)L * N * 6));
-    CK(dalloc(ctx, &ctx->vhat_out, (size_t)L * N * 6));
-
-    Topo &T = ctx->T;
-    CK(dalloc(ctx, &T.maxd, 2));
-    CK(dalloc(ctx, &T.parent, N));
-    CK(dalloc(ctx, &T.orig, N));
-    CK(dalloc(ctx, &T.pre, N));
-    CK(dalloc(ctx, &T.sz, N));
-    CK(dalloc(ctx, &T.depth, N));
-    CK(dalloc(ctx, &T.child_off, N + 1));
-    CK(dalloc(ctx, &T.child, N));
-    CK(dalloc(ctx, &T.level_off, N + 2));
-    CK(dalloc(ctx, &T.level_bus, N));
-    CK(dalloc(ctx, &T.ph, N));
-    CK(dalloc(ctx, &T.lca, N * N));
-    CK(dalloc(ctx, &T.zl, N * 9));
-    CK(dalloc(ctx, &T.yl, N * 9));
-    CK(dalloc(ctx, &T.zc, N * 9));
-    CK(dalloc(ctx, &T.zh, N * 9));
-    CK(dalloc(ctx, &T.zlo, N * 9));
-    CK(dalloc(ctx, &T.vhat, NL3));
-    CK(dalloc(ctx, &T.ihat, NL3));
-    CK(dalloc(ctx, &T.amag, NL3));
-    CK(dalloc(ctx, &T.vslack, 3));
-
-    State &S = ctx->S;
-    CK(dalloc(ctx, &S.label, N));
-    CK(dalloc(ctx, &S.top, N));
-    CK(dalloc(ctx, &S.sn_list[0], N));
-    CK(dalloc(ctx, &S.sn_list[1], N));
-    CK(dalloc(ctx, &S.sn_rank, N + 1));
-    CK(dalloc(ctx, &S.vcur, NL3));
-    CK(dalloc(ctx, &S.icur, NL3));
-    CK(dalloc(ctx, &S.hi, NL3));
-    CK(dalloc(ctx, &S.lo, NL3));
-    CK(dalloc(ctx, &S.mice, (size_t)L * N));
-    CK(dalloc(ctx, &S.mcur, NL3));
-    CK(dalloc(ctx, &S.v32, NL3));
-    CK(dalloc(ctx, &S.hr32, NL3));
-    CK(dalloc(ctx, &S.lr32, NL3));
-    CK(dalloc(ctx, &S.mice32, (size_t)L * N));
-    CK(dalloc(ctx, &S.icur32, NL3));
-
-    Search &X = ctx->X;
-    CK(dalloc(ctx, &X.cand, 2 * N));
-    CK(dalloc(ctx, &X.slot, 2 * N));
-    CK(dalloc(ctx, &X.ckey, 2 * N));
-    CK(dalloc(ctx, &X.base, 2 * N + 1));
-    CK(dalloc(ctx, &X.arrive, 2 * N));
-    CK(dalloc(ctx, &X.block_tot, (size_t)ctx->num_sms));
-    CK(dalloc(ctx, &X.score, 2 * N));
-    CK(dalloc(ctx, &X.feas, 2 * N));
-    CK(dalloc(ctx, &X.scr, 2 * N));
-    CK(dalloc(ctx, &X.wsum, (size_t)ctx->num_sms * (512 / 32)));
-    CK(dalloc(ctx, &X.mrank, N));
-    CK(dalloc(ctx, &X.bmax, N / 32 + 2));
-    CK(dalloc(ctx, &ctx->gb, 1));
-    X.chunk_first = nullptr;
-    X.partial = nullptr;
-    X.max_chunks = 0;
-    CK(dalloc(ctx, &X.dec_s, N));
-    CK(dalloc(ctx, &X.dec_r, N));
-    CK(dalloc(ctx, &X.dec_score, N));
-    CK(dalloc(ctx, &X.dec_maxerr, N));
-    CK(dalloc(ctx, &X.dec_gap, N));
-    CK(dalloc(ctx, &X.dec_ncand, N));
-    const size_t R = rec > 0 ? (size_t)rec : 1;
-    CK(dalloc(ctx, &X.rec_s, R * 2 * N));
-    CK(dalloc(ctx, &X.rec_r, R * 2 * N));
-    CK(dalloc(ctx, &X.rec_score, R * 2 * N));
-    CK(dalloc(ctx, &X.rec_bound, R * 2 * N));
-    CK(dalloc(ctx, &X.rec_count, R));
-    CK(dalloc(ctx, &ctx->C, 1));
-
+    Carver m;
+    FeederBufs f;
+    layout_feeder(m, n, L, rec, ctx->num_sms, 0, f);
+    void *p = nullptr;
+    CK(cudaMalloc(&p, m.used));
+    ctx->arena = p;
+    Carver c;
+    c.base = static_cast<unsigned char *>(p);
+    layout_feeder(c, n, L, rec, ctx->num_sms, 0, ctx->fb);
     ctx->cap_n = n;
     ctx->cap_L = L;
     ctx->cap_rec = rec;
@@ -290,25 +194,25 @@ okr_status read_setup_errors(okr_ctx *ctx);
 // Per-feeder setup on the device: topology, LCA table, lines, path impedances.
 okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     cudaStream_t st = ctx->stream;
-    Topo &T = ctx->T;
+    Topo &T = ctx->fb.T;
     T.n = n;
     T.L = L;
     double2 vs[3];
     for (int p = 0; p < 3; ++p) vs[p] = make_double2(vslack[2 * p], vslack[2 * p + 1]);
     CK(cudaMemcpyAsync(T.vslack, vs, sizeof vs, cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(ctx->err_dev, 0, sizeof(int), st));
-    k_topology<<<1, 1024, 0, st>>>(n, ctx->parent_in, ctx->ph_in, T, ctx->dep, ctx->anc, ctx->anc2, ctx->d2,
-                                   ctx->size, ctx->ccount, ctx->coff_c, ctx->child_c, ctx->err_dev);
+    CK(cudaMemsetAsync(ctx->fb.err_dev, 0, sizeof(int), st));
+    k_topology<<<1, 1024, 0, st>>>(n, ctx->fb.parent_in, ctx->fb.ph_in, T, ctx->fb.dep, ctx->fb.anc, ctx->fb.anc2, ctx->fb.d2,
+                                   ctx->fb.size, ctx->fb.ccount, ctx->fb.coff_c, ctx->fb.child_c, ctx->fb.err_dev);
     ctx->launches += 1;
     CK(cudaGetLastError());
     // the later setup kernels index with the renumbering: stop here on an invalid tree
     okr_status s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
-    k_child_offsets<<<1, 1024, 0, st>>>(n, T, ctx->coff_c, ctx->child_c);
+    k_child_offsets<<<1, 1024, 0, st>>>(n, T, ctx->fb.coff_c, ctx->fb.child_c);
     const int LOG = log2_ceil(n) + 1;
-    k_rmq_all<<<1, 1024, 0, st>>>(n, LOG, T.depth, ctx->rmq);
-    k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, T.parent, T.sz, T.depth, ctx->rmq, T.lca);
-    CK(launch_lines(n, T, ctx->z_in, ctx->err_dev, ctx->num_sms, st));
+    k_rmq_all<<<1, 1024, 0, st>>>(n, LOG, T.depth, ctx->fb.rmq);
+    k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, T.parent, T.sz, T.depth, ctx->fb.rmq, T.lca);
+    CK(launch_lines(n, T, ctx->fb.z_in, ctx->fb.err_dev, ctx->num_sms, st));
     ctx->launches += 5;
     CK(cudaGetLastError());
     s = read_setup_errors(ctx);
@@ -323,7 +227,7 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
 
 okr_status read_setup_errors(okr_ctx *ctx) {
     int e = 0;
-    CK(cudaMemcpyAsync(ctx->C_host, ctx->err_dev, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->C_host, ctx->fb.err_dev, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     std::memcpy(&e, ctx->C_host, sizeof e);
     if (e == 1) return fail(ctx, OKR_EINVAL, "invalid feeder: parent[0] must be -1, parent[i] < i, phases non-empty and within the parent's");
@@ -336,12 +240,12 @@ okr_status read_setup_errors(okr_ctx *ctx) {
 
 okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
     cudaStream_t st = ctx->stream;
-    Topo &T = ctx->T;
+    Topo &T = ctx->fb.T;
     // the load flow's work buffers alias T.ihat and T.amag, which the next two kernels fill
-    CK(launch_power_flow(n, L, T, ctx->s_in, kPfTol, kPfMaxIter, ctx->J, T.ihat, T.amag, ctx->pf_iters,
-                         ctx->err_dev, ctx->num_sms, st));
-    k_line_currents<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
-    k_injections<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->J);
+    CK(launch_power_flow(n, L, T, ctx->fb.s_in, kPfTol, kPfMaxIter, ctx->fb.J, T.ihat, T.amag, ctx->fb.pf_iters,
+                         ctx->fb.err_dev, ctx->num_sms, st));
+    k_line_currents<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->fb.J);
+    k_injections<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->fb.J);
     ctx->launches += 3;
     CK(cudaGetLastError());
     return OKR_OK;
@@ -363,9 +267,9 @@ okr_status ensure_work(okr_ctx *ctx, long long chunks) {
     }
     ctx->work_allocs.push_back(a);
     ctx->work_allocs.push_back(b);
-    ctx->X.chunk_first = (int *)a;
-    ctx->X.partial = (double2 *)b;
-    ctx->X.max_chunks = (int)chunks;
+    ctx->fb.X.chunk_first = (int *)a;
+    ctx->fb.X.partial = (double2 *)b;
+    ctx->fb.X.max_chunks = (int)chunks;
     ctx->cap_chunks = (int)chunks;
     return OKR_OK;
 }
@@ -377,10 +281,10 @@ int positions_per_chunk(int L) { return 32 / (4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4)
 // allocated it saves its state and exits, and is relaunched with a larger one.
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     cudaStream_t st = ctx->stream;
-    const int n = ctx->T.n, L = ctx->T.L;
-    Search &X = ctx->X;
+    const int n = ctx->fb.T.n, L = ctx->fb.T.L;
+    Search &X = ctx->fb.X;
     X.rec_iters = p->record_iters;
-    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->S);
+    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.S);
     ctx->launches += 1;
     CK(cudaGetLastError());
     const int mm = merges_for(n, p);
@@ -394,12 +298,12 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     c.precision = p->precision;
     c.objective = p->objective;
     c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
-    CK(cudaMemcpyAsync(ctx->C, &c, sizeof c, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->fb.C, &c, sizeof c, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
     CK(cudaMemsetAsync(X.arrive, 0, sizeof(int) * 2 * n, st));
     CK(cudaMemsetAsync(X.mrank, 0, sizeof(double) * n, st));           // every MICE starts at 0
     CK(cudaMemsetAsync(X.bmax, 0, sizeof(double) * (n / 32 + 2), st));
-    CK(cudaMemsetAsync(ctx->gb, 0, sizeof(GridBar), st));
+    CK(cudaMemsetAsync(ctx->fb.gb, 0, sizeof(GridBar), st));
     if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
     ctx->rec_iters = p->record_iters;
     ctx->search_ms = 0.0;
@@ -413,13 +317,13 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     for (int attempt = 0; attempt < 16 && !c.done; ++attempt) {
-        CK(cudaMemsetAsync(ctx->gb, 0, sizeof(GridBar), st));
+        CK(cudaMemsetAsync(ctx->fb.gb, 0, sizeof(GridBar), st));
         cudaEventRecord(e0, st);
-        cudaError_t e = launch_search(p->precision, ctx->grid, ctx->T, ctx->S, ctx->X, ctx->C, ctx->gb, st);
+        cudaError_t e = launch_search(p->precision, ctx->grid, ctx->fb.T, ctx->fb.S, ctx->fb.X, ctx->fb.C, ctx->fb.gb, st);
         cudaEventRecord(e1, st);
         ctx->launches += 1;
         if (e != cudaSuccess) { s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e)); break; }
-        e = cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        e = cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) { s = fail(ctx, OKR_ECUDA, "search: %s", cudaGetErrorString(e)); break; }
         float ms = 0.f;
@@ -431,7 +335,7 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
             s = ensure_work(ctx, want);
             if (s != OKR_OK) break;
             int zero = 0;
-            CK(cudaMemcpyAsync(&ctx->C->err, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(&ctx->fb.C->err, &zero, sizeof zero, cudaMemcpyHostToDevice, st));
             c.done = 0;
             continue;
         }
@@ -443,11 +347,11 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     if (c.err == 6) return fail(ctx, OKR_ETIMEOUT, "a grid barrier of the search gave up after %lld polls", c.max_spins);
     if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
     if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
-    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, ctx->vred_out,
-                                                                                ctx->super_out, ctx->vhat_out);
+    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, ctx->fb.vred_out,
+                                                                                ctx->fb.super_out, ctx->fb.vhat_out);
     ctx->launches += 1;
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->C_host, ctx->C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     ctx->last = *ctx->C_host;
     return OKR_OK;
@@ -474,19 +378,19 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
     if (s != OKR_OK) return s;
     cudaStream_t st = ctx->stream;
     const cudaMemcpyKind kind = (src == Src::Device) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    CK(cudaMemcpyAsync(ctx->parent_in, f->parent, sizeof(int) * n, kind, st));
-    CK(cudaMemcpyAsync(ctx->ph_in, f->phases, n, kind, st));
-    CK(cudaMemcpyAsync(ctx->z_in, f->z_line, sizeof(double) * 18 * n, kind, st));
+    CK(cudaMemcpyAsync(ctx->fb.parent_in, f->parent, sizeof(int) * n, kind, st));
+    CK(cudaMemcpyAsync(ctx->fb.ph_in, f->phases, n, kind, st));
+    CK(cudaMemcpyAsync(ctx->fb.z_in, f->z_line, sizeof(double) * 18 * n, kind, st));
     if (src == Src::Ops) {
-        CK(cudaMemcpyAsync(ctx->vh_in, vhat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
-        CK(cudaMemcpyAsync(ctx->ih_in, ihat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->fb.vh_in, vhat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ctx->fb.ih_in, ihat, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
     } else {
-        CK(cudaMemcpyAsync(ctx->s_in, f->s_load, sizeof(double) * 6 * L * n, kind, st));
+        CK(cudaMemcpyAsync(ctx->fb.s_in, f->s_load, sizeof(double) * 6 * L * n, kind, st));
     }
     s = build_topology(ctx, n, L, &f->v_slack[0][0]);
     if (s != OKR_OK) return s;
     if (src == Src::Ops) {
-        k_import_ops<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->vh_in, ctx->ih_in);
+        k_import_ops<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.vh_in, ctx->fb.ih_in);
         ctx->launches += 1;
         CK(cudaGetLastError());
         ctx->pf_sweeps = 0;
@@ -498,7 +402,7 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
     if (s != OKR_OK) return s;
     if (src != Src::Ops) {
         int it[kMaxScen];
-        CK(cudaMemcpy(it, ctx->pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(it, ctx->fb.pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
         int w = 0;
         for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
         ctx->pf_sweeps = w;
@@ -591,6 +495,7 @@ okr_status okr_destroy(okr_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
+    free_batch(ctx);
     if (ctx->C_host) cudaFreeHost(ctx->C_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -622,10 +527,10 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     s = ensure_workspace(ctx, n, L, ctx->cap_rec);
     if (s != OKR_OK) return s;
     cudaStream_t st = ctx->stream;
-    CK(cudaMemcpyAsync(ctx->parent_in, f->parent, sizeof(int) * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->ph_in, f->phases, n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->z_in, f->z_line, sizeof(double) * 18 * n, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(ctx->s_in, f->s_load, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->fb.parent_in, f->parent, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->fb.ph_in, f->phases, n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->fb.z_in, f->z_line, sizeof(double) * 18 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->fb.s_in, f->s_load, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
     s = build_topology(ctx, n, L, &f->v_slack[0][0]);
     if (s != OKR_OK) return s;
     s = run_power_flow(ctx, n, L);
@@ -633,23 +538,23 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
     // export: reuse k_export with the initial state (each bus its own super-node)
-    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->T, ctx->S);
-    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, ctx->S, nullptr, nullptr,
-                                                                                ctx->vhat_out);
+    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.S);
+    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, nullptr, nullptr,
+                                                                                ctx->fb.vhat_out);
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(vhat_out, ctx->vhat_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(vhat_out, ctx->fb.vhat_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
     if (ihat_out) {
         // S.icur == Ihat after the initial state; export it through vred's slot
-        State si = ctx->S;
-        si.vcur = ctx->S.icur;                  // export the injections through the voltage slot
-        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->T, si, ctx->vred_out,
+        State si = ctx->fb.S;
+        si.vcur = ctx->fb.S.icur;                  // export the injections through the voltage slot
+        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, si, ctx->fb.vred_out,
                                                                                     nullptr, nullptr);
-        CK(cudaMemcpyAsync(ihat_out, ctx->vred_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(ihat_out, ctx->fb.vred_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
     }
     CK(cudaStreamSynchronize(st));
     if (sweeps) {
         int it[kMaxScen];
-        CK(cudaMemcpy(it, ctx->pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(it, ctx->fb.pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
         int w = 0;
         for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
         *sweeps = w;
@@ -665,7 +570,7 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
     if ((y_out || phase_node) && cap < 0) return fail(ctx, OKR_EINVAL, "cap < 0");
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    const int n = ctx->T.n;
+    const int n = ctx->fb.T.n;
     if (ctx->cap_kron_n < n) {
         for (void *q : ctx->kron_allocs) cudaFree(q);
         ctx->kron_allocs.clear();
@@ -710,7 +615,7 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventRecord(e0, st));
-    k_kron_groups<<<1, 1024, 0, st>>>(ctx->T, kept ? nullptr : ctx->S.label, kept_dev, W);
+    k_kron_groups<<<1, 1024, 0, st>>>(ctx->fb.T, kept ? nullptr : ctx->fb.S.label, kept_dev, W);
     CK(cudaGetLastError());
     KronHdr h{};
     CK(cudaMemcpyAsync(&h, W.hdr, sizeof h, cudaMemcpyDeviceToHost, st));
@@ -747,7 +652,7 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
         ctx->cap_kbig = need_big;
     }
     CK(cudaMemsetAsync(ctx->ykr, 0, sizeof(double2) * need_y, st));
-    CK(launch_kron_solve(h.n_groups, ctx->T, W, ctx->kbig, ctx->ykr, (int)K, st));
+    CK(launch_kron_solve(h.n_groups, ctx->fb.T, W, ctx->kbig, ctx->ykr, (int)K, st));
     if (K > 0) k_kron_diag<<<blocks_for(K * 32, 256, ctx->num_sms * 8), 256, 0, st>>>(W, ctx->ykr, (int)K);
     CK(cudaGetLastError());
     CK(cudaEventRecord(e1, st));
@@ -764,6 +669,356 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
     return OKR_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------- many feeders
+namespace {
+
+// Host check of the tree rules (the batched setup does not stop between kernels).
+bool valid_tree(const okr_feeder *f) {
+    const int n = f->n_bus;
+    if (f->parent[0] != -1 || f->phases[0] == 0 || f->phases[0] > 7) return false;
+    for (int i = 1; i < n; ++i) {
+        const int p = f->parent[i];
+        const unsigned m = f->phases[i];
+        if (p < 0 || p >= i || m == 0 || m > 7 || (m & f->phases[p]) != m) return false;
+    }
+    return true;
+}
+
+okr_status batch_status_of_setup(int e) {
+    switch (e) {
+    case 0: return OKR_OK;
+    case 1: return OKR_EINVAL;
+    case 2: return OKR_ESINGULAR;
+    case 3: return OKR_EPF;
+    case 6: return OKR_ETIMEOUT;
+    default: return OKR_EINTERNAL;
+    }
+}
+
+}  // namespace
+
+static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *feeders, const okr_params *params,
+                                    int32_t n_params, okr_batch_item *items, int32_t *super_of,
+                                    okr_batch_stats *stats, int config) {
+    if (!ctx) return OKR_EINVAL;
+    if (nf < 1 || !feeders || !params || !items) return fail(ctx, OKR_EINVAL, "batch: bad arguments");
+    if (n_params != 1 && n_params != nf) return fail(ctx, OKR_EINVAL, "batch: n_params must be 1 or n_feeders");
+    if (config < 0 || config > 2) return fail(ctx, OKR_EINVAL, "batch: config %d", config);
+    ctx->have_result = false;
+    ctx->have_topo = false;
+    std::vector<long long> sum_sz(nf);
+    std::vector<int> merges(nf);
+    int maxL = 1;
+    long long max_nn = 1, tot_n = 0;
+    for (int f = 0; f < nf; ++f) {
+        const okr_feeder *F = &feeders[f];
+        const okr_params *P = &params[n_params == 1 ? 0 : f];
+        okr_status st = check_feeder_shape(ctx, F);
+        if (st == OKR_OK) st = check_params(ctx, P);
+        if (st != OKR_OK) return fail(ctx, st, "batch feeder %d: %s", f, ctx->err.c_str());
+        if (!F->s_load) return fail(ctx, OKR_EINVAL, "batch feeder %d: s_load is NULL", f);
+        if (P->record_iters != 0) return fail(ctx, OKR_EINVAL, "batch feeder %d: record_iters must be 0", f);
+        if (!valid_tree(F)) return fail(ctx, OKR_EINVAL, "batch feeder %d: invalid tree or phases", f);
+        const int n = F->n_bus;
+        std::vector<int> dep(n, 0);
+        long long ss = 0;
+        for (int i = 0; i < n; ++i) {
+            if (i > 0) dep[i] = dep[F->parent[i]] + 1;
+            ss += dep[i] + 1;
+        }
+        sum_sz[f] = ss;
+        merges[f] = merges_for(n, P);
+        maxL = std::max(maxL, (int)F->n_scen);
+        max_nn = std::max(max_nn, (long long)n * n);
+        tot_n += n;
+    }
+    // ---- layout: [staged block: descriptors, controls, order, queues, flags, inputs] [per-feeder buffers] [outputs]
+    Carver m;                                   // staged block (mirrors the pinned host buffer)
+    BatchSetup *bs_d = nullptr;
+    BatchFeeder *bf_d = nullptr;
+    Ctrl *ctrl_d = nullptr;
+    int *order_d = nullptr, *queue_d = nullptr, *err_d = nullptr;
+    double *maxerr_d = nullptr;
+    m.take(bs_d, nf);
+    m.take(bf_d, nf);
+    m.take(ctrl_d, nf);
+    m.take(order_d, nf);
+    m.take(queue_d, 2);
+    m.take(err_d, nf);
+    m.take(maxerr_d, nf);
+    std::vector<size_t> in_off(nf);
+    for (int f = 0; f < nf; ++f) {
+        const size_t n = feeders[f].n_bus, L = feeders[f].n_scen;
+        in_off[f] = m.used;
+        int *a; uint8_t *b; double *c, *d; double2 *e;
+        m.take(a, n);
+        m.take(b, n);
+        m.take(c, 18 * n);
+        m.take(d, 6 * L * n);
+        m.take(e, 3);
+    }
+    const size_t staged = m.used;
+    std::vector<size_t> fb_off(nf);
+    Carver w;
+    w.used = staged;
+    std::vector<FeederBufs> fbs(nf);
+    for (int f = 0; f < nf; ++f) {
+        const int n = feeders[f].n_bus, L = feeders[f].n_scen;
+        const int ppc = positions_per_chunk(L);
+        const long long chunks = 2LL * ((2LL * sum_sz[f] + 2LL * n + ppc - 1) / ppc + 1);
+        fb_off[f] = w.used;
+        layout_feeder(w, n, L, 0, 1, chunks, fbs[f]);
+    }
+    int *super_all_d = nullptr;
+    const size_t super_off = w.used;
+    w.take(super_all_d, (size_t)tot_n);
+    const size_t total = w.used;
+    if (total > ctx->batch_cap) {
+        if (ctx->batch_arena) cudaFree(ctx->batch_arena);
+        ctx->batch_arena = nullptr;
+        ctx->batch_cap = 0;
+        CK(cudaMalloc(&ctx->batch_arena, total));
+        ctx->batch_cap = total;
+    }
+    const size_t host_need = std::max(staged, (size_t)tot_n * sizeof(int));
+    if (host_need > ctx->batch_host_cap) {
+        if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+        ctx->batch_host = nullptr;
+        ctx->batch_host_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->batch_host, host_need));
+        ctx->batch_host_cap = host_need;
+    }
+    unsigned char *base = static_cast<unsigned char *>(ctx->batch_arena);
+    unsigned char *hb = ctx->batch_host;
+    super_all_d = reinterpret_cast<int *>(base + super_off);      // the measuring pass left it null
+    std::memset(hb, 0, staged);
+    // device pointers of the staged block
+    Carver md;
+    md.base = base;
+    md.take(bs_d, nf);
+    md.take(bf_d, nf);
+    md.take(ctrl_d, nf);
+    md.take(order_d, nf);
+    md.take(queue_d, 2);
+    md.take(err_d, nf);
+    md.take(maxerr_d, nf);
+    Carver mh;                                  // the same offsets in the host buffer
+    mh.base = hb;
+    BatchSetup *bs_h; BatchFeeder *bf_h; Ctrl *ctrl_h; int *order_h, *queue_h, *err_h; double *maxerr_h;
+    mh.take(bs_h, nf);
+    mh.take(bf_h, nf);
+    mh.take(ctrl_h, nf);
+    mh.take(order_h, nf);
+    mh.take(queue_h, 2);
+    mh.take(err_h, nf);
+    mh.take(maxerr_h, nf);
+    // per feeder: buffers, inputs, descriptors, controls
+    size_t soff = 0;
+    std::vector<size_t> super_pos(nf);
+    for (int f = 0; f < nf; ++f) {
+        const okr_feeder *F = &feeders[f];
+        const okr_params *P = &params[n_params == 1 ? 0 : f];
+        const int n = F->n_bus, L = F->n_scen;
+        Carver c;
+        c.base = base + fb_off[f];
+        FeederBufs &B = fbs[f];
+        layout_feeder(c, n, L, 0, 1, B.X.max_chunks, B);
+        // inputs live in the staged block
+        Carver ci;
+        ci.base = base + in_off[f];
+        Carver chh;
+        chh.base = hb + in_off[f];
+        int *pd, *ph_; uint8_t *phd, *phh; double *zd, *zh_, *sd, *sh_; double2 *vd, *vh_;
+        ci.take(pd, n); ci.take(phd, n); ci.take(zd, 18 * (size_t)n); ci.take(sd, 6 * (size_t)L * n); ci.take(vd, 3);
+        chh.take(ph_, n); chh.take(phh, n); chh.take(zh_, 18 * (size_t)n); chh.take(sh_, 6 * (size_t)L * n); chh.take(vh_, 3);
+        std::memcpy(ph_, F->parent, sizeof(int) * n);
+        std::memcpy(phh, F->phases, n);
+        std::memcpy(zh_, F->z_line, sizeof(double) * 18 * n);
+        std::memcpy(sh_, F->s_load, sizeof(double) * 6 * L * n);
+        for (int p = 0; p < 3; ++p) vh_[p] = make_double2(F->v_slack[p][0], F->v_slack[p][1]);
+        B.T.vslack = vd;
+        B.C = ctrl_d + f;
+        B.err_dev = err_d + f;
+        super_pos[f] = soff;
+        B.super_out = super_all_d + soff;
+        soff += n;
+        BatchSetup &S = bs_h[f];
+        S.n = n;
+        S.L = L;
+        S.nlev = log2_ceil(n) + 1;
+        S.parent_in = pd;
+        S.ph_in = phd;
+        S.z_in = zd;
+        S.s_in = sd;
+        S.T = B.T;
+        S.S = B.S;
+        S.dep = B.dep; S.anc = B.anc; S.anc2 = B.anc2; S.d2 = B.d2; S.size = B.size; S.ccount = B.ccount;
+        S.coff_c = B.coff_c; S.child_c = B.child_c;
+        S.rmq = B.rmq;
+        S.J = B.J;
+        S.pf_iters = B.pf_iters;
+        S.err = B.err_dev;
+        S.dec_maxerr = B.X.dec_maxerr;
+        S.mrank = B.X.mrank;
+        S.bmax = B.X.bmax;
+        S.arrive = B.X.arrive;
+        BatchFeeder &D = bf_h[f];
+        D.T = B.T;
+        D.S = B.S;
+        D.X = B.X;
+        D.X.rec_iters = 0;
+        D.C = B.C;
+        D.setup_err = B.err_dev;
+        D.super_out = B.super_out;
+        D.max_err = maxerr_d + f;
+        Ctrl &cc = ctrl_h[f];
+        cc.max_merges = merges[f];
+        cc.done = (merges[f] == 0);
+        cc.margin = P->margin;
+        cc.tau = P->tie_tol;
+        cc.profile = 0;
+        cc.n_super = n;
+        cc.precision = P->precision;
+        cc.objective = P->objective;
+        cc.max_spins = P->max_spins > 0 ? P->max_spins : kDefaultSpins;
+    }
+    // largest expected work first, FP64 feeders in their own list
+    std::vector<int> ord[2];
+    for (int f = 0; f < nf; ++f) ord[params[n_params == 1 ? 0 : f].precision].push_back(f);
+    for (int g = 0; g < 2; ++g)
+        std::stable_sort(ord[g].begin(), ord[g].end(), [&](int a, int b) {
+            return (double)feeders[a].n_bus * merges[a] > (double)feeders[b].n_bus * merges[b];
+        });
+    int k = 0;
+    for (int g = 0; g < 2; ++g)
+        for (int f : ord[g]) order_h[k++] = f;
+    cudaStream_t st = ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventCreate(&e2));
+    CK(cudaMemcpyAsync(base, hb, staged, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecord(e0, st));
+    CK(launch_batch_setup(nf, maxL, max_nn, bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
+    CK(cudaEventRecord(e1, st));
+    int ctas = 0;
+    for (int g = 0, first = 0; g < 2; first += (int)ord[g].size(), ++g) {
+        const int cnt = (int)ord[g].size();
+        if (cnt == 0) continue;
+        const int per_sm = search_batch_blocks_per_sm(g, config);
+        if (per_sm < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
+        const int grid = std::min(cnt, ctx->num_sms * per_sm);
+        ctas = std::max(ctas, grid);
+        CK(launch_search_batch(g, config, grid, bf_d, order_d + first, cnt, queue_d + g, st));
+    }
+    CK(cudaEventRecord(e2, st));
+    // results: controls, setup errors and largest errors (one copy), assignments
+    const size_t res_off = (size_t)((unsigned char *)ctrl_d - base);
+    const size_t res_len = (size_t)((unsigned char *)(maxerr_d + nf) - (unsigned char *)ctrl_d);
+    CK(cudaMemcpyAsync(hb + res_off, base + res_off, res_len, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float ms_setup = 0.f, ms_search = 0.f;
+    cudaEventElapsedTime(&ms_setup, e0, e1);
+    cudaEventElapsedTime(&ms_search, e1, e2);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    std::vector<Ctrl> ctrl(ctrl_h, ctrl_h + nf);
+    std::vector<int> serr(err_h, err_h + nf);
+    std::vector<double> maxerr(maxerr_h, maxerr_h + nf);
+    if (super_of) {
+        CK(cudaMemcpyAsync(hb, base + super_off, sizeof(int) * (size_t)tot_n, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::memcpy(super_of, hb, sizeof(int) * (size_t)tot_n);
+    }
+    int64_t cand_total = 0;
+    int fallbacks = 0;
+    for (int f = 0; f < nf; ++f) {
+        okr_batch_item &it = items[f];
+        std::memset(&it, 0, sizeof it);
+        const Ctrl &c = ctrl[f];
+        if (serr[f]) { it.status = batch_status_of_setup(serr[f]); continue; }
+        if (c.err == 7) {                       // work buffers too small: run this feeder alone
+            ++fallbacks;
+            const okr_params *P = &params[n_params == 1 ? 0 : f];
+            okr_status s2 = reduce_impl(ctx, &feeders[f], nullptr, nullptr, P, Src::Host);
+            it.status = s2;
+            if (s2 != OKR_OK) continue;
+            const Ctrl &l = ctx->last;
+            it.n_iter = l.t;
+            it.stop_reason = l.stop_reason;
+            it.n_kept = feeders[f].n_bus - l.t;
+            it.candidates = l.candidates;
+            it.smice = l.s_cur;
+            double me = 0.0;
+            if (l.t > 0) CK(cudaMemcpy(&me, ctx->fb.X.dec_maxerr + (l.t - 1), sizeof me, cudaMemcpyDeviceToHost));
+            it.max_error = me;
+            if (super_of) CK(cudaMemcpy(super_of + super_pos[f], ctx->fb.super_out, sizeof(int) * feeders[f].n_bus,
+                                        cudaMemcpyDeviceToHost));
+            cand_total += l.candidates;
+            continue;
+        }
+        if (c.err == 6) { it.status = OKR_ETIMEOUT; continue; }
+        if (c.err || !c.done) { it.status = OKR_EINTERNAL; continue; }
+        it.status = OKR_OK;
+        it.n_iter = c.t;
+        it.stop_reason = c.stop_reason;
+        it.n_kept = feeders[f].n_bus - c.t;
+        it.candidates = c.candidates;
+        it.smice = c.s_cur;
+        it.max_error = maxerr[f];
+        cand_total += c.candidates;
+    }
+    if (stats) {
+        stats->setup_ms = ms_setup;
+        stats->search_ms = ms_search;
+        stats->candidates = cand_total;
+        stats->config = config;
+        stats->ctas = ctas;
+        stats->fallbacks = fallbacks;
+        stats->reserved = 0;
+    }
+    return OKR_OK;
+}
+
+extern "C" {
+
+okr_status okr_reduce_batch(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                            int32_t n_params, okr_batch_item *items, int32_t *super_of, okr_batch_stats *stats) {
+    if (!ctx) return OKR_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    return reduce_batch_impl(ctx, n_feeders, feeders, params, n_params, items, super_of, stats, ctx->batch_config);
+}
+
+okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                              int32_t n_params, int32_t *config, double *search_ms) {
+    if (!ctx) return OKR_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    std::vector<okr_batch_item> items(n_feeders > 0 ? n_feeders : 1);
+    double best = 1e300;
+    int best_c = ctx->batch_config;
+    for (int c = 0; c < 3; ++c) {
+        okr_batch_stats st{};
+        double t = 1e300;
+        for (int rep = 0; rep < 2; ++rep) {     // the first run warms the buffers
+            okr_status s = reduce_batch_impl(ctx, n_feeders, feeders, params, n_params, items.data(), nullptr, &st, c);
+            if (s != OKR_OK) return s;
+            t = std::min(t, st.search_ms);
+        }
+        if (search_ms) search_ms[c] = t;
+        if (t < best) { best = t; best_c = c; }
+    }
+    ctx->batch_config = best_c;
+    if (config) *config = best_c;
+    return OKR_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     if (!ctx || !out) return OKR_EINVAL;
     if (!ctx->have_result) return OKR_ENOTREADY;
@@ -777,7 +1032,7 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->candidates = c.candidates;
     out->smice = c.s_cur;
     double me = 0.0;
-    if (c.t > 0) cudaMemcpy(&me, ctx->X.dec_maxerr + (c.t - 1), sizeof me, cudaMemcpyDeviceToHost);
+    if (c.t > 0) cudaMemcpy(&me, ctx->fb.X.dec_maxerr + (c.t - 1), sizeof me, cudaMemcpyDeviceToHost);
     out->max_error = me;
     out->launches = ctx->launches;
     out->search_ms = ctx->search_ms;
@@ -797,7 +1052,7 @@ okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_
     if (!ctx->have_result) return OKR_ENOTREADY;
     const int t = ctx->last.t < cap ? ctx->last.t : cap;
     if (t == 0) return OKR_OK;
-    const Search &X = ctx->X;
+    const Search &X = ctx->fb.X;
     if (s && cudaMemcpy(s, X.dec_s, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (r && cudaMemcpy(r, X.dec_r, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (smice && cudaMemcpy(smice, X.dec_score, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
@@ -810,7 +1065,7 @@ okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_
 okr_status okr_get_assignment(const okr_ctx *ctx, int32_t *super_of) {
     if (!ctx || !super_of) return OKR_EINVAL;
     if (!ctx->have_result) return OKR_ENOTREADY;
-    if (cudaMemcpy(super_of, ctx->super_out, sizeof(int) * ctx->n, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (cudaMemcpy(super_of, ctx->fb.super_out, sizeof(int) * ctx->n, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     return OKR_OK;
 }
 
@@ -818,8 +1073,8 @@ okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred) {
     if (!ctx) return OKR_EINVAL;
     if (!ctx->have_result) return OKR_ENOTREADY;
     const size_t bytes = sizeof(double) * 6 * ctx->L * ctx->n;
-    if (vhat && cudaMemcpy(vhat, ctx->vhat_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
-    if (vred && cudaMemcpy(vred, ctx->vred_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (vhat && cudaMemcpy(vhat, ctx->fb.vhat_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (vred && cudaMemcpy(vred, ctx->fb.vred_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     return OKR_OK;
 }
 
@@ -829,15 +1084,15 @@ okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32
     if (!ctx->have_result) return OKR_ENOTREADY;
     if (iter < 0 || iter >= ctx->rec_iters) return OKR_EINVAL;
     int c = 0;
-    if (cudaMemcpy(&c, ctx->X.rec_count + iter, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    if (cudaMemcpy(&c, ctx->fb.X.rec_count + iter, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     *count = c;
     const int k = c < cap ? c : cap;
     const size_t off = (size_t)iter * 2 * ctx->n;
     if (k > 0) {
-        if (s && cudaMemcpy(s, ctx->X.rec_s + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
-        if (r && cudaMemcpy(r, ctx->X.rec_r + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
-        if (smice && cudaMemcpy(smice, ctx->X.rec_score + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
-        if (bound && cudaMemcpy(bound, ctx->X.rec_bound + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (s && cudaMemcpy(s, ctx->fb.X.rec_s + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (r && cudaMemcpy(r, ctx->fb.X.rec_r + off, sizeof(int) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (smice && cudaMemcpy(smice, ctx->fb.X.rec_score + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+        if (bound && cudaMemcpy(bound, ctx->fb.X.rec_bound + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     }
     return OKR_OK;
 }

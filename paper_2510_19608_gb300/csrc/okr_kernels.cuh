@@ -26,6 +26,26 @@ __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J
 __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);
 __global__ void k_state_init(int n, int L, Topo T, State S);
 
+// Per-feeder setup descriptor of a batch (every pointer into that feeder's buffers).
+struct BatchSetup {
+    int n, L, nlev;
+    const int *parent_in;
+    const uint8_t *ph_in;
+    const double *z_in, *s_in;
+    Topo T;
+    State S;
+    int *dep, *anc, *anc2, *d2, *size, *ccount, *coff_c, *child_c;
+    uint16_t *rmq;
+    double2 *J;
+    int *pf_iters;
+    int *err;                   // setup error of this feeder (0 = none)
+    double *dec_maxerr, *mrank, *bmax;
+    int *arrive;
+};
+// Setup of many feeders in four launches (CTA per feeder, per feeder x scenario).
+cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchSetup *bs, double tol, int max_iter,
+                               int num_sms, cudaStream_t st);
+
 // okr_kron.cu
 constexpr int kKronShared = 64;     // groups up to this many phase-nodes are inverted in shared memory
 constexpr int kKronMaxGroup = 1024; // larger groups are refused (dense inverse per group)
@@ -53,6 +73,21 @@ __global__ void k_kron_diag(KronWork W, double2 *Y, int K);
 cudaError_t launch_kron_solve(int n_groups, Topo T, KronWork W, double2 *big, double2 *Y, int K, cudaStream_t st);
 
 // okr_persist.cu
+// One feeder of a batched search launch.
+struct BatchFeeder {
+    Topo T;
+    State S;
+    Search X;
+    Ctrl *C;
+    int *setup_err;             // nonzero: the setup failed, the search is skipped
+    int *super_out;             // [n] assignment in caller numbering
+    double *max_err;            // largest per-phase error of the final network
+};
+// Batched search: configs 0/1/2 = 512/256/128 threads per CTA (1/2/4 CTAs per SM).
+cudaError_t launch_search_batch(int precision, int config, int grid, const BatchFeeder *fd, const int *order, int nf,
+                                int *queue, cudaStream_t st);
+int search_batch_threads(int config);
+int search_batch_blocks_per_sm(int precision, int config);
 cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st);
 int search_blocks_per_sm();     // CTAs of the search kernel that fit one SM (0 on error)
 __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);

@@ -111,6 +111,18 @@ __device__ bool grid_barrier(GridBar *gb, Ctrl *C, unsigned nblocks, unsigned &e
     return s_ok;
 }
 
+// Barrier of the CTAs that share one feeder: the whole grid (G > 1), or one
+// CTA (G == 1), where a fence and __syncthreads suffice.
+__device__ __forceinline__ bool team_barrier(GridBar *gb, Ctrl *C, unsigned G, unsigned &epoch) {
+    if (G == 1) {
+        __threadfence();
+        __syncthreads();
+        epoch += 1;
+        return true;
+    }
+    return grid_barrier(gb, C, G, epoch);
+}
+
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -601,7 +613,7 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
                             double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc) {
     const int tid = threadIdx.x;
     unsigned long long bk = ~0ull;
-    for (int i = tid; i < m; i += kThreads)
+    for (int i = tid; i < m; i += (int)blockDim.x)
         if (ldi(feas + i)) bk = min(bk, dkey(ldd(score + i)));
     bk = block_reduce(bk, MinU(), smu);
     Sel out;
@@ -611,7 +623,7 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
     const double edge = dval(bk) + tau;
     const unsigned long long ek = dkey(edge);
     unsigned long long key = ~0ull, gk = ~0ull;
-    for (int i = tid; i < m; i += kThreads) {
+    for (int i = tid; i < m; i += (int)blockDim.x) {
         if (!ldi(feas + i)) continue;
         const unsigned long long k = dkey(ldd(score + i));
         if (k <= ek) {
@@ -625,12 +637,12 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
     gk = block_reduce(gk, MinU(), smu);
     int w = 0x7fffffff;
     if (ksure < key) {              // a candidate known to be in the band has the smallest key
-        for (int c = tid; c < nc; c += kThreads)
+        for (int c = tid; c < nc; c += (int)blockDim.x)
             if (__ldcg(X.ckey + c) == ksure) w = min(w, c);
         w = block_reduce(w, MinI(), smi);
         out.w = (w < nc) ? w : -2;
     } else {
-        for (int i = tid; i < m; i += kThreads)
+        for (int i = tid; i < m; i += (int)blockDim.x)
             if (ldi(feas + i) && dkey(ldd(score + i)) <= ek && __ldcg(X.ckey + (map ? map[i] : i)) == key) w = min(w, i);
         w = block_reduce(w, MinI(), smi);
         out.w = (w < m) ? (map ? map[w] : w) : -2;
@@ -670,7 +682,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     const float margin_lo = __double2float_rd(margin), margin_hi = __double2float_ru(margin);
     const float tau_lo = __double2float_rd(tau), tau_hi = __double2float_ru(tau);
     float mhi = INFINITY, mlo = INFINITY;
-    for (int c = tid; c < nc; c += kThreads) {
+    for (int c = tid; c < nc; c += (int)blockDim.x) {
         const float4 q = __ldcg(X.scr + c);
         if (__fsub_rd(q.z, q.w) <= margin_hi) mlo = fminf(mlo, __fsub_rd(q.x, q.y));
         if (surely_feasible(q, margin_lo)) mhi = fminf(mhi, __fadd_ru(q.x, q.y));
@@ -687,7 +699,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     const float edge_in = __fadd_rd(mlo, tau_lo), edge_out = __fadd_ru(mhi, tau_hi);
     unsigned long long ks = ~0ull;
     float g = INFINITY;
-    for (int c = tid; c < nc; c += kThreads) {
+    for (int c = tid; c < nc; c += (int)blockDim.x) {
         const float4 q = __ldcg(X.scr + c);
         const bool maybe = __fsub_rd(q.z, q.w) <= margin_hi;
         if (!maybe) continue;
@@ -700,7 +712,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     out.gap = (double)block_reduce(g, MinF(), smf);
     // R: possible minimizers and uncertain candidates with a key below ks
     int nR = 0, need = 0;
-    for (int c0 = 0; c0 < nc; c0 += kThreads) {
+    for (int c0 = 0; c0 < nc; c0 += (int)blockDim.x) {
         const int c = c0 + tid;
         int flag = 0, unc = 0;
         if (c < nc) {
@@ -721,7 +733,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     }
     if (need == 0) {
         int w = 0x7fffffff;
-        for (int c = tid; c < nc; c += kThreads)
+        for (int c = tid; c < nc; c += (int)blockDim.x)
             if (__ldcg(X.ckey + c) == ks) w = min(w, c);
         w = block_reduce(w, MinI(), smi);
         out.win = (w < nc) ? w : -2;
@@ -733,8 +745,10 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
 }
 
 // ---------------------------------------------------------------- the kernel
+// One feeder's search on a team of G CTAs (rank = this CTA's index in the team).
 template <int PREC>
-__global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb) {
+__device__ __forceinline__ void search_run(const Topo &T, const State &S, const Search &X, Ctrl *C, GridBar *gb,
+                                           int rank, unsigned G) {
     __shared__ double smd[32];
     __shared__ float smf[32];
     __shared__ unsigned long long smu[32];
@@ -746,15 +760,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
     const int n = T.n, L = T.L;
     const int Lp = L <= 1 ? 1 : (L <= 2 ? 2 : 4);
     const int SP = 4 * Lp, PPW = 32 / SP;
-    const unsigned G = gridDim.x;
+    const int nt = blockDim.x;
     const int tid = threadIdx.x, lane = tid & 31;
-    const int gt = blockIdx.x * kThreads + tid, gs = (int)G * kThreads;
+    const int gt = rank * nt + tid, gs = (int)G * nt;
     const int warp = gt >> 5, nwarps = gs >> 5;
     const double margin = C->margin, tau = C->tau;
     const int max_merges = C->max_merges;
     const bool prof = C->profile != 0;
     const bool obj1 = (PREC == 0) && C->objective == 1;
-    const bool lead = (blockIdx.x == 0 && tid == 0);
+    const bool lead = (rank == 0 && tid == 0);
     unsigned epoch = 0;
     int t = C->t, ns = C->n_super;
     double s_cur = C->s_cur;               // SMICE of the committed state
@@ -783,8 +797,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 const Screen sc = screen_select(X, nc, margin, tau, s_R, sm2, smf, smu, smi);
                 const int nR = sc.nR;
                 stamp(0);
-                if (blockIdx.x == 0 && t < X.rec_iters) {
-                    for (int c = tid; c < nc; c += kThreads) {
+                if (rank == 0 && t < X.rec_iters) {
+                    for (int c = tid; c < nc; c += nt) {
                         const Cand cc = ldcand(X.cand + c);
                         const float4 q = __ldcg(X.scr + c);
                         const bool out = __fsub_rd(q.z, q.w) > __double2float_ru(margin);
@@ -801,7 +815,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                     sel.gap = sc.gap;
                 } else if (nR <= kRmax) {
                     // FP64 recheck of R: positions of R back to back
-                    for (int i0 = 0; i0 < nR; i0 += kThreads) {
+                    for (int i0 = 0; i0 < nR; i0 += nt) {
                         const int i = i0 + tid;
                         const int cnt = i < nR ? cand_positions(ldcand(X.cand + s_R[i])) : 0;
                         int2 tot;
@@ -809,7 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                         const int off = (i0 == 0) ? 0 : s_Rbase[i0];
                         __syncthreads();
                         if (i < nR) s_Rbase[i] = off + ex.x;
-                        if (tid == 0) s_Rbase[min(i0 + kThreads, nR)] = off + tot.x;
+                        if (tid == 0) s_Rbase[min(i0 + nt, nR)] = off + tot.x;
                         __syncthreads();
                     }
                     const int PR = s_Rbase[nR];
@@ -831,7 +845,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                                       X.score, X.feas, false, flops);
                     }
                     if (lead) { C->rechecks += 1; C->recheck_cands += nR; }
-                    if (!grid_barrier(gb, C, G, epoch)) return;
+                    if (!team_barrier(gb, C, G, epoch)) return;
                     sel = select_exact(X, nR, s_R, X.score, X.feas, tau, smd, smu, smi, sc.ksure, nc);
                     stamp(1);
                 } else {
@@ -859,12 +873,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                         score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin,
                                       X.score, X.feas, false, flops);
                     }
-                    if (!grid_barrier(gb, C, G, epoch)) return;
+                    if (!team_barrier(gb, C, G, epoch)) return;
                 }
             }
             if (full64) {
-                if (PREC == 0 && blockIdx.x == 0 && t < X.rec_iters) {
-                    for (int c = tid; c < nc; c += kThreads) {
+                if (PREC == 0 && rank == 0 && t < X.rec_iters) {
+                    for (int c = tid; c < nc; c += nt) {
                         const Cand cc = ldcand(X.cand + c);
                         X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
                         X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
@@ -970,11 +984,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
         // committed above: label r -> s, rank drops past r, s's top)
         if (!finishing) {
             int2 mine = make_int2(0, 0);
-            const int j = gt;
+            // each thread owns `per` consecutive super-node slots (one on a full grid)
+            const int per = (ns + gs - 1) / gs, jb = gt * per, je = min(ns, jb + per);
+            for (int j = jb; j < je; ++j) {
             Cand c0, c1;
             c0.s = -1;
             c1.s = -1;
-            if (j >= 1 && j < ns) {
+            if (j >= 1) {
                 const int w = ldi(list_old + j + (committed && j >= jr0 ? 1 : 0));
                 const int tw = (committed && w == s0 && dir0 == 1) ? ldi(S.top + r0) : ldi(S.top + w);
                 int x = ldi(S.label + T.parent[tw]);
@@ -1005,22 +1021,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                     mine.y += cand_positions(c1);
                 }
             }
-            if (j < ns) {
-                X.slot[2 * j] = c0;
-                X.slot[2 * j + 1] = c1;
+            X.slot[2 * j] = c0;
+            X.slot[2 * j + 1] = c1;
             }
             int2 tot;
             my_ex = block_scan2(mine, sm2, &tot);
-            if (tid == 0) { X.block_tot[blockIdx.x] = tot; s_mine = tot; }
+            if (tid == 0) { X.block_tot[rank] = tot; s_mine = tot; }
         }
         stamp(3);
-        if (!grid_barrier(gb, C, G, epoch)) return;
+        if (!team_barrier(gb, C, G, epoch)) return;
         stamp(4);
 
         // ============================================================ phase 2
         if (committed) {
             // exact score change of the merge, in warp order (CTA 0, warp 0)
-            if (blockIdx.x == 0 && tid < 32) {
+            if (rank == 0 && tid < 32) {
                 double d = 0.0;
                 for (int w2 = lane; w2 < nw_commit; w2 += 32) d += ldd(X.wsum + w2);
                 for (int o2 = 16; o2 > 0; o2 >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o2);
@@ -1068,7 +1083,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             int2 acc = make_int2(0, 0), all = make_int2(0, 0);
             for (int b = lane; b < (int)G; b += 32) {
                 const int2 v = __ldcg(X.block_tot + b);
-                if (b < (int)blockIdx.x) { acc.x += v.x; acc.y += v.y; }
+                if (b < (int)rank) { acc.x += v.x; acc.y += v.y; }
                 all.x += v.x;
                 all.y += v.y;
             }
@@ -1098,32 +1113,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             // this CTA's candidates into the compact list; their first positions
             // also into shared memory for the chunk map below
             int *s_lbase = s_Rbase;
-            if (gt >= 1 && gt < ns) {
+            const bool in_smem = s_mine.x <= kRmax;     // this CTA's candidate bases fit shared memory
+            {
+                const int per = (ns + gs - 1) / gs, jb = max(1, gt * per), je = min(ns, gt * per + per);
                 int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
-                for (int d = 0; d < 2; ++d) {
-                    const Cand c = X.slot[2 * gt + d];
-                    if (c.s < 0) continue;
-                    X.cand[ci] = c;
-                    X.ckey[ci] = c.key;
-                    X.base[ci] = pos;
-                    s_lbase[li] = pos;
-                    ++ci;
-                    ++li;
-                    pos += cand_positions(c);
-                }
+                for (int j = jb; j < je; ++j)
+                    for (int d = 0; d < 2; ++d) {
+                        const Cand c = X.slot[2 * j + d];
+                        if (c.s < 0) continue;
+                        X.cand[ci] = c;
+                        X.ckey[ci] = c.key;
+                        X.base[ci] = pos;
+                        if (in_smem) s_lbase[li] = pos;
+                        ++ci;
+                        ++li;
+                        pos += cand_positions(c);
+                    }
             }
+            if (!in_smem) __threadfence();
             __syncthreads();
             stamp(11);
             // chunk map: every chunk that starts inside this CTA's positions gets the
             // candidate holding its first position (binary search in shared memory)
             const int2 mt = s_mine;
             const int p0 = pref.y, p1 = pref.y + mt.y;
-            for (int g = (p0 + PPW - 1) / PPW + tid; g * PPW < p1; g += kThreads) {
+            for (int g = (p0 + PPW - 1) / PPW + tid; g * PPW < p1; g += nt) {
                 const int q = g * PPW;
                 int lo = 0, hi = mt.x - 1;
                 while (lo < hi) {
                     const int mid = (lo + hi + 1) >> 1;
-                    if (s_lbase[mid] <= q) lo = mid;
+                    const int bm = in_smem ? s_lbase[mid] : ldi(X.base + pref.x + mid);
+                    if (bm <= q) lo = mid;
                     else hi = mid - 1;
                 }
                 X.chunk_first[g] = pref.x + lo;
@@ -1137,7 +1157,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
             C->iters += 1;
         }
         stamp(5);
-        if (!grid_barrier(gb, C, G, epoch)) return;
+        if (!team_barrier(gb, C, G, epoch)) return;
         stamp(6);
 
         // ============================================================ phase 3
@@ -1167,7 +1187,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
                 else
                     score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops);
             }
-            if (!grid_barrier(gb, C, G, epoch)) return;
+            if (!team_barrier(gb, C, G, epoch)) return;
             if (prof && lead) {
                 unsigned long long t_end;
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
@@ -1180,6 +1200,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search 
     if (prof) {
         for (int o2 = 16; o2 > 0; o2 >>= 1) flops += __shfl_xor_sync(0xffffffffu, flops, o2);
         if (lane == 0 && flops > 0.0) atomicAdd(&C->sweep_flops, flops);
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb) {
+    search_run<PREC>(T, S, X, C, gb, blockIdx.x, gridDim.x);
+}
+
+// Many feeders in one launch: every CTA takes the next feeder from the queue
+// (feeders listed largest first) and runs its whole search alone, then writes
+// the feeder's assignment in caller numbering.
+template <int PREC, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_search_batch(const BatchFeeder *fd, const int *order, int nf, int *queue) {
+    __shared__ Topo sT;
+    __shared__ State sS;
+    __shared__ Search sX;
+    __shared__ int s_f;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_f = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = s_f;
+        if (q >= nf) return;
+        const int f = order[q];
+        if (threadIdx.x == 0) {
+            sT = fd[f].T;
+            sS = fd[f].S;
+            sX = fd[f].X;
+        }
+        __syncthreads();
+        Ctrl *C = fd[f].C;
+        const bool ok = ldi(fd[f].setup_err) == 0;
+        if (ok) search_run<PREC>(sT, sS, sX, C, nullptr, 0, 1);
+        __threadfence();
+        __syncthreads();
+        for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[ldi(sS.label + sT.pre[i])] : -1;
+        if (threadIdx.x == 0) {
+            const int t = ok ? ldi(&C->t) : 0;
+            *fd[f].max_err = t > 0 ? ldd(sX.dec_maxerr + t - 1) : 0.0;
+        }
     }
 }
 
@@ -1196,6 +1256,29 @@ int search_blocks_per_sm() {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_search<0>, kThreads, 0) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_search<1>, kThreads, 0) != cudaSuccess) return 0;
     return a < b ? a : b;
+}
+
+cudaError_t launch_search_batch(int precision, int config, int grid, const BatchFeeder *fd, const int *order, int nf,
+                                int *queue, cudaStream_t st) {
+    void *args[] = {&fd, &order, &nf, &queue};
+    const void *fn = nullptr;
+    int nt = 512;
+    if (config == 0) { fn = precision == 1 ? (const void *)k_search_batch<1, 512, 1> : (const void *)k_search_batch<0, 512, 1>; nt = 512; }
+    else if (config == 1) { fn = precision == 1 ? (const void *)k_search_batch<1, 256, 2> : (const void *)k_search_batch<0, 256, 2>; nt = 256; }
+    else { fn = precision == 1 ? (const void *)k_search_batch<1, 128, 4> : (const void *)k_search_batch<0, 128, 4>; nt = 128; }
+    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, 0, st);
+}
+
+int search_batch_threads(int config) { return config == 0 ? 512 : (config == 1 ? 256 : 128); }
+
+int search_batch_blocks_per_sm(int precision, int config) {
+    int a = 0;
+    const void *fn;
+    if (config == 0) fn = precision == 1 ? (const void *)k_search_batch<1, 512, 1> : (const void *)k_search_batch<0, 512, 1>;
+    else if (config == 1) fn = precision == 1 ? (const void *)k_search_batch<1, 256, 2> : (const void *)k_search_batch<0, 256, 2>;
+    else fn = precision == 1 ? (const void *)k_search_batch<1, 128, 4> : (const void *)k_search_batch<0, 128, 4>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, search_batch_threads(config), 0) != cudaSuccess) return 0;
+    return a;
 }
 
 // Results in caller numbering: super-node of each bus, reduced-network voltage

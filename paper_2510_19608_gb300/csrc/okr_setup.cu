@@ -50,7 +50,7 @@ __device__ __forceinline__ void block_barrier() { __syncthreads(); }
 // ---------------------------------------------------------------- topology (one CTA)
 // Input in caller numbering.  Scratch arrays (caller numbering): dep, anc/anc2,
 // d2, size, ccount.  Writes the Topo arrays in preorder numbering.
-__global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict__ parent_in, const uint8_t *__restrict__ ph_in,
+__device__ void dev_topology(int n, const int *__restrict__ parent_in, const uint8_t *__restrict__ ph_in,
                            Topo T, int *dep, int *anc, int *anc2, int *d2, int *size, int *ccount,
                            int *coff_c, int *child_c, int *err) {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -171,10 +171,16 @@ __global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict_
     if (tid == 0) { T.maxd[0] = maxd; T.maxd[1] = s_sum; }
 }
 
+__global__ void __launch_bounds__(1024) k_topology(int n, const int *__restrict__ parent_in, const uint8_t *__restrict__ ph_in,
+                           Topo T, int *dep, int *anc, int *anc2, int *d2, int *size, int *ccount,
+                           int *coff_c, int *child_c, int *err) {
+    dev_topology(n, parent_in, ph_in, T, dep, anc, anc2, d2, size, ccount, coff_c, child_c, err);
+}
+
 // Children CSR indexed by preorder id (one CTA).  The children of preorder
 // node v are those of caller bus orig[v], already converted to preorder ids
 // and increasing.
-__global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c) {
+__device__ void dev_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c) {
     // exclusive scan of the child counts in preorder, 1024 buses per pass
     __shared__ int s_w[32];
     __shared__ int s_carry;
@@ -217,6 +223,10 @@ __global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int
     }
 }
 
+__global__ void __launch_bounds__(1024) k_child_offsets(int n, Topo T, const int *__restrict__ coff_c, const int *__restrict__ child_c) {
+    dev_child_offsets(n, T, coff_c, child_c);
+}
+
 // Sparse table of the minimum-depth bus over preorder windows: st[j*n + v] is the
 // index of the shallowest bus in [v, v + 2^j).
 __global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_t *st) {
@@ -234,7 +244,7 @@ __global__ void k_rmq_level(int n, int j, const int *__restrict__ depth, uint16_
 }
 
 // All levels of the sparse table in one CTA (levels 0 .. nlev-1).
-__global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__restrict__ depth, uint16_t *st) {
+__device__ void dev_rmq_all(int n, int nlev, const int *__restrict__ depth, uint16_t *st) {
     for (int v = threadIdx.x; v < n; v += blockDim.x) st[v] = (uint16_t)v;
     __syncthreads();
     for (int j = 1; j < nlev; ++j) {
@@ -252,12 +262,17 @@ __global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__
     }
 }
 
+__global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__restrict__ depth, uint16_t *st) {
+    dev_rmq_all(n, nlev, depth, st);
+}
+
 // LCA[u][v] for all pairs (preorder ids).  For u < v: if v lies in u's subtree
 // the answer is u; otherwise it is the parent of the shallowest bus in (u, v].
-__global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
-                           const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca) {
+__device__ void dev_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
+                             const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca,
+                             size_t first, size_t stride) {
     size_t tot = (size_t)n * n;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = first; e < tot; e += stride) {
         int u = (int)(e / n), v = (int)(e % n);
         int lo = u < v ? u : v, hi = u < v ? v : u;
         int res;
@@ -275,12 +290,17 @@ __global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__r
     }
 }
 
+__global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
+                           const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca) {
+    dev_lca_fill(n, parent, sz, depth, st, lca, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
 // Line data in preorder: zl, yl (inverse on the bus phases); path impedance by
 // levels (parents first).  One CTA.
 // Line data: copies of the impedances and their inverses on the line's phases,
 // one thread per bus over the whole grid.
-__global__ void k_line_inverses(int n, Topo T, const double *__restrict__ z_in, int *err) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+__device__ void dev_line_inverses(int n, Topo T, const double *__restrict__ z_in, int *err, int first, int stride) {
+    for (int v = first; v < n; v += stride) {
         const int i = T.orig[v];
         double2 z[9];
         for (int q = 0; q < 9; ++q) {
@@ -298,9 +318,13 @@ __global__ void k_line_inverses(int n, Topo T, const double *__restrict__ z_in, 
     }
 }
 
+__global__ void k_line_inverses(int n, Topo T, const double *__restrict__ z_in, int *err) {
+    dev_line_inverses(n, T, z_in, err, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x);
+}
+
 // Path impedances root -> k level by level (one CTA), then their split into
 // two floats for the screening sweep.
-__global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
+__device__ void dev_path_impedance(int n, Topo T) {
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int q = tid; q < 9; q += nt) T.zc[q] = make_double2(0.0, 0.0);
     __syncthreads();
@@ -319,6 +343,10 @@ __global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
         T.zh[e] = h;
         T.zlo[e] = make_float2((float)(z.x - (double)h.x), (float)(z.y - (double)h.y));
     }
+}
+
+__global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
+    dev_path_impedance(n, T);
 }
 
 cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
@@ -533,9 +561,9 @@ cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double t
 
 // Ihat = Y Vhat line by line: line current J_k = y_k (V_parent - V_k) on the
 // phases of k; injection I_k = sum of children's J - J_k.  Also |Vhat|.
-__global__ void k_line_currents(int n, int L, Topo T, double2 *J) {
+__device__ void dev_line_currents(int n, int L, Topo T, double2 *J, size_t first, size_t stride) {
     size_t tot = (size_t)L * n;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = first; e < tot; e += stride) {
         int l = (int)(e / n), v = (int)(e % n);
         for (int p = 0; p < 3; ++p) {
             double2 j = make_double2(0.0, 0.0);
@@ -552,9 +580,13 @@ __global__ void k_line_currents(int n, int L, Topo T, double2 *J) {
     }
 }
 
-__global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J) {
+__global__ void k_line_currents(int n, int L, Topo T, double2 *J) {
+    dev_line_currents(n, L, T, J, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+__device__ void dev_injections(int n, int L, Topo T, const double2 *__restrict__ J, size_t first, size_t stride) {
     size_t tot = (size_t)L * n;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = first; e < tot; e += stride) {
         int l = (int)(e / n), v = (int)(e % n);
         for (int p = 0; p < 3; ++p) {
             double2 s = make_double2(0.0, 0.0);
@@ -562,6 +594,10 @@ __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J
             T.ihat[sidx(l, p, v, n)] = csub(s, J[sidx(l, p, v, n)]);
         }
     }
+}
+
+__global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J) {
+    dev_injections(n, L, T, J, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
 }
 
 // Caller-supplied scenario library (host layout [L][n][3][2], caller numbering).
@@ -583,9 +619,9 @@ __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh
 
 // Initial state of Algorithm 1: every bus is its own super-node, I = Ihat,
 // V = Vhat, cluster extremes = |Vhat|, MICE = 0.
-__global__ void k_state_init(int n, int L, Topo T, State S) {
+__device__ void dev_state_init(int n, int L, Topo T, State S, size_t first, size_t stride) {
     size_t tot = (size_t)L * n;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = first; e < tot; e += stride) {
         int l = (int)(e / n), v = (int)(e % n);
         if (l == 0) {
             S.label[v] = v;
@@ -610,6 +646,153 @@ __global__ void k_state_init(int n, int L, Topo T, State S) {
             S.icur32[q] = make_float2((float)T.ihat[q].x, (float)T.ihat[q].y);
         }
     }
+}
+
+__global__ void k_state_init(int n, int L, Topo T, State S) {
+    dev_state_init(n, L, T, S, (size_t)blockIdx.x * blockDim.x + threadIdx.x, (size_t)gridDim.x * blockDim.x);
+}
+
+}  // namespace okr
+
+namespace okr {
+
+// ---------------------------------------------------------------- many feeders
+// Load flow of one scenario by one CTA (the batch runs many such CTAs side by
+// side, which spreads the FP64 arithmetic over the SMs): the same sweep,
+// operation for operation, as k_power_flow.
+__device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__restrict__ s_in, double tol,
+                                   int max_iter, double2 *J, int *iters, int *err) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double2 *V = T.vhat;
+    double2 *Jl = J + (size_t)l * 3 * n;
+    __shared__ double s_red[32];
+    __shared__ int s_conv;
+    for (int v = tid; v < n; v += nt)
+        for (int p = 0; p < 3; ++p)
+            V[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
+    __syncthreads();
+    const int maxd = T.maxd[0];
+    int it;
+    bool conv = false;
+    for (it = 1; it <= max_iter; ++it) {
+        for (int d = maxd; d >= 1; --d) {
+            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                const int v = T.level_bus[x], i = T.orig[v];
+                for (int p = 0; p < 3; ++p) {
+                    double2 j = make_double2(0.0, 0.0);
+                    if (T.ph[v] >> p & 1u) {
+                        const size_t o = (((size_t)l * n + i) * 3 + p) * 2;
+                        j = cconj(cdiv(make_double2(s_in[o], s_in[o + 1]), V[sidx(l, p, v, n)]));
+                    }
+                    for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Jl[(size_t)p * n + T.child[c]]);
+                    Jl[(size_t)p * n + v] = j;
+                }
+            }
+            __syncthreads();
+        }
+        double dmax = 0.0;
+        for (int d = 1; d <= maxd; ++d) {
+            for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+                const int v = T.level_bus[x], par = T.parent[v];
+                for (int p = 0; p < 3; ++p) {
+                    if (!(T.ph[v] >> p & 1u)) continue;
+                    double2 drop = make_double2(0.0, 0.0);
+                    for (int q = 0; q < 3; ++q)
+                        if (T.ph[v] >> q & 1u) drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], Jl[(size_t)q * n + v]));
+                    const double2 vn = csub(V[sidx(l, p, par, n)], drop);
+                    double dd = cmag(csub(vn, V[sidx(l, p, v, n)]));
+                    if (!isfinite(dd)) dd = INFINITY;
+                    dmax = fmax(dmax, dd);
+                    V[sidx(l, p, v, n)] = vn;
+                }
+            }
+            __syncthreads();
+        }
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        if ((tid & 31) == 0) s_red[tid >> 5] = dmax;
+        __syncthreads();
+        if (tid == 0) {
+            double m = 0.0;
+            for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, s_red[w]);
+            s_conv = (m < tol);
+        }
+        __syncthreads();
+        if (s_conv) { conv = true; break; }
+    }
+    if (tid == 0) {
+        iters[l] = conv ? it : -1;
+        if (!conv) atomicExch(err, 3);
+    }
+}
+
+// Per feeder, one CTA: validation and renumbering, children, sparse table,
+// line inverses, path impedances.
+__global__ void __launch_bounds__(1024) k_batch_prep(const BatchSetup *bs) {
+    __shared__ BatchSetup b;
+    if (threadIdx.x == 0) b = bs[blockIdx.x];
+    __syncthreads();
+    dev_topology(b.n, b.parent_in, b.ph_in, b.T, b.dep, b.anc, b.anc2, b.d2, b.size, b.ccount, b.coff_c, b.child_c,
+                 b.err);
+    __syncthreads();
+    if (*(volatile int *)b.err) return;
+    dev_child_offsets(b.n, b.T, b.coff_c, b.child_c);
+    __syncthreads();
+    dev_rmq_all(b.n, b.nlev, b.T.depth, b.rmq);
+    dev_line_inverses(b.n, b.T, b.z_in, b.err, threadIdx.x, blockDim.x);
+    __syncthreads();
+    dev_path_impedance(b.n, b.T);
+}
+
+// LCA tables: blockIdx.y = feeder.
+__global__ void k_batch_lca(const BatchSetup *bs) {
+    const BatchSetup &b = bs[blockIdx.y];
+    if (*(volatile int *)b.err == 1) return;
+    dev_lca_fill(b.n, b.T.parent, b.T.sz, b.T.depth, b.rmq, b.T.lca, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (size_t)gridDim.x * blockDim.x);
+}
+
+// Load flow: blockIdx.y = feeder, blockIdx.x = scenario.
+__global__ void __launch_bounds__(1024) k_batch_pf(const BatchSetup *bs, double tol, int max_iter) {
+    __shared__ BatchSetup b;
+    if (threadIdx.x == 0) b = bs[blockIdx.y];
+    __syncthreads();
+    if ((int)blockIdx.x >= b.L || *(volatile int *)b.err == 1) return;
+    dev_power_flow_cta(b.n, blockIdx.x, b.T, b.s_in, tol, max_iter, b.J, b.pf_iters, b.err);
+}
+
+// Per feeder, one CTA: Ihat = Y Vhat, |Vhat|, the initial search state and the
+// zeroed per-run counters of the search.
+__global__ void __launch_bounds__(1024) k_batch_finish(const BatchSetup *bs) {
+    __shared__ BatchSetup b;
+    if (threadIdx.x == 0) b = bs[blockIdx.x];
+    __syncthreads();
+    if (*(volatile int *)b.err) return;
+    const size_t first = threadIdx.x, stride = blockDim.x;
+    dev_line_currents(b.n, b.L, b.T, b.J, first, stride);
+    __syncthreads();
+    dev_injections(b.n, b.L, b.T, b.J, first, stride);
+    __syncthreads();
+    dev_state_init(b.n, b.L, b.T, b.S, first, stride);
+    for (int i = threadIdx.x; i < b.n; i += blockDim.x) {
+        b.dec_maxerr[i] = 0.0;
+        b.mrank[i] = 0.0;
+        b.arrive[2 * i] = 0;
+        b.arrive[2 * i + 1] = 0;
+    }
+    for (int i = threadIdx.x; i < b.n / 32 + 2; i += blockDim.x) b.bmax[i] = 0.0;
+}
+
+cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchSetup *bs, double tol, int max_iter,
+                               int num_sms, cudaStream_t st) {
+    if (nf <= 0) return cudaSuccess;
+    k_batch_prep<<<nf, 1024, 0, st>>>(bs);
+    long long bx = (max_nn + 255) / 256;
+    if (bx > num_sms * 2) bx = num_sms * 2;
+    if (bx < 1) bx = 1;
+    k_batch_lca<<<dim3((unsigned)bx, nf), 256, 0, st>>>(bs);
+    k_batch_pf<<<dim3(max_L, nf), 1024, 0, st>>>(bs, tol, max_iter);
+    k_batch_finish<<<nf, 1024, 0, st>>>(bs);
+    return cudaGetLastError();
 }
 
 }  // namespace okr
