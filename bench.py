@@ -55,6 +55,7 @@ def _args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-feeder batch measurement")
     return ap.parse_args()
 
 
@@ -167,6 +168,40 @@ def run_reference(args, rank, world):
                              "sample": f"first {sample} merges of {WORKLOAD} per step, delta mode"},
             "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def batch_line(K, ctx, reps=3):
+    """Many-feeder workload: 256 seeded feeders, n ~ U[200, 2000], targets in
+    {50, 70, 90} %, margin 0.005, reduced by okr_reduce_batch (one persistent
+    launch), mixed precision and plain FP64.  Inputs (about 1 GB of device
+    buffers) exceed L2, so no flush is needed between repetitions."""
+    import feedergen as fg
+    batch = fg.batch_presets(256)
+    feeders = [f for f, _ in batch]
+    out = {"workload": "256 feeders, n ~ U[200, 2000] buses (sum %d), targets {50, 70, 90} %%, margin 0.005 p.u., "
+                       "2 scenarios" % sum(f.n_bus for f in feeders)}
+    for prec, key in ((1, "mixed"), (0, "fp64")):
+        plist = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=prec) for _, r in batch]
+        if prec == 1:
+            cfg, ms = ctx.batch_autotune(feeders, plist)
+            out["autotune"] = {"config": cfg, "search_ms_by_config": [round(x, 3) for x in ms],
+                               "configs": ["1 CTA per feeder", "2 CTAs", "4 CTAs", "8 CTAs"]}
+        ctx.reduce_batch(feeders, plist, want_assignment=False)          # warm-up
+        walls, dev_ms, st = [], [], None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            items, _, st = ctx.reduce_batch(feeders, plist, want_assignment=True)
+            walls.append(time.perf_counter() - t0)
+            dev_ms.append(st["setup_ms"] + st["search_ms"])
+        bad = sum(1 for it in items if it["status"] != 0)
+        wall = statistics.median(walls)
+        dms = statistics.median(dev_ms)
+        out[key] = {"feeders_per_s": len(feeders) / (dms / 1e3), "candidates_per_s": st["candidates"] / (dms / 1e3),
+                    "device_ms": dms, "setup_ms": st["setup_ms"], "search_ms": st["search_ms"],
+                    "e2e_feeders_per_s": len(feeders) / wall, "e2e_ms": 1e3 * wall,
+                    "candidates": st["candidates"], "ctas": st["ctas"], "fallbacks": st["fallbacks"],
+                    "failed_feeders": bad}
+    return out
 
 
 def run_ours(args, rank, world, local):
@@ -285,6 +320,7 @@ def run_ours(args, rank, world, local):
                                      [round(x, 3) for x in ps["phase_ms"][:12]])),
                 "share_of_step": search_ms / (ms / args.steps)}
 
+    batch = batch_line(K, ctx) if not args.no_batch else None
     if rank == 0:
         cb = cpu_baseline(f, run) if world == 1 else None
         line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
@@ -297,7 +333,8 @@ def run_ours(args, rank, world, local):
                     "l2": "flushed between steps (256 MB write outside the timed events)",
                     "parallelism": f"replicas x{world}", "time_to_optimal_ms": ms / args.steps,
                     "candidates_per_step": cand_per_step, "merges": summ["n_iter"],
-                    "stop_reason": summ["stop_reason"], "wall_s": t_wall, "y_kron": kron},
+                    "stop_reason": summ["stop_reason"], "wall_s": t_wall, "y_kron": kron,
+                    "batch": batch},
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline}
         if cb:

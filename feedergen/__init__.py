@@ -83,17 +83,30 @@ def _mask(ps) -> int:
     return m
 
 
-def _chain_shares(parent: np.ndarray, elig: np.ndarray, q: float, w: float) -> tuple[float, float]:
+def _levels(parent: np.ndarray) -> list[np.ndarray]:
+    """Bus indices grouped by depth (root excluded), parents before children."""
+    n = parent.shape[0]
+    depth = np.zeros(n, dtype=np.int64)
+    for i in range(1, n):
+        depth[i] = depth[parent[i]] + 1
+    return [np.nonzero(depth == d)[0] for d in range(1, int(depth.max()) + 1)] if n > 1 else []
+
+
+def _chain_shares(parent: np.ndarray, elig: np.ndarray, q: float, w: float, levels=None) -> tuple[float, float]:
     """Exact expected (three-phase, two-phase) shares of the lateral drop chain."""
     n = parent.shape[0]
+    if levels is None:
+        levels = _levels(parent)
     pr = np.zeros((n, 3))
     pr[0, 0] = 1.0
-    for i in range(1, n):
-        a3, a2, a1 = pr[parent[i]]
-        qq = q if elig[i] else 0.0
-        pr[i, 0] = a3 * (1.0 - qq)
-        pr[i, 1] = a3 * qq * w + a2 * (1.0 - qq)
-        pr[i, 2] = a3 * qq * (1.0 - w) + a2 * qq + a1
+    qv = np.where(elig, q, 0.0)
+    for idx in levels:                         # element-wise the same arithmetic as a bus-by-bus loop
+        par = parent[idx]
+        a3, a2, a1 = pr[par, 0], pr[par, 1], pr[par, 2]
+        qq = qv[idx]
+        pr[idx, 0] = a3 * (1.0 - qq)
+        pr[idx, 1] = a3 * qq * w + a2 * (1.0 - qq)
+        pr[idx, 2] = a3 * qq * (1.0 - w) + a2 * qq + a1
     m = pr.mean(axis=0)
     return float(m[0]), float(m[1])
 
@@ -101,10 +114,11 @@ def _chain_shares(parent: np.ndarray, elig: np.ndarray, q: float, w: float) -> t
 def _fit_phase_chain(parent: np.ndarray, elig: np.ndarray, mix) -> tuple[float, float]:
     """Fit (q, w) so that the expected three- and two-phase shares match ``mix``."""
     f3, f2 = float(mix[0]), float(mix[1])
+    levels = _levels(parent)
     lo, hi = 0.0, 1.0
     for _ in range(50):                       # three-phase share falls with q
         q = 0.5 * (lo + hi)
-        if _chain_shares(parent, elig, q, 0.5)[0] > f3:
+        if _chain_shares(parent, elig, q, 0.5, levels)[0] > f3:
             lo = q
         else:
             hi = q
@@ -112,7 +126,7 @@ def _fit_phase_chain(parent: np.ndarray, elig: np.ndarray, mix) -> tuple[float, 
     lo, hi = 0.0, 1.0
     for _ in range(50):                       # two-phase share rises with w
         w = 0.5 * (lo + hi)
-        if _chain_shares(parent, elig, q, w)[1] < f2:
+        if _chain_shares(parent, elig, q, w, levels)[1] < f2:
             lo = w
         else:
             hi = w

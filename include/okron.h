@@ -186,7 +186,7 @@ typedef struct okr_batch_stats {
     double setup_ms;            /* device time of the setup of every feeder (load flows included) */
     double search_ms;           /* device time of the batched search launch(es) */
     int64_t candidates;         /* over all feeders */
-    int32_t config;             /* CTA shape: 0/1/2 = 512/256/128 threads, 1/2/4 CTAs per SM */
+    int32_t config;             /* team shape: 0/1/2/3 = 1/2/4/8 CTAs (512 threads each) per feeder */
     int32_t ctas;               /* CTAs of the batched search launch */
     int32_t fallbacks;          /* feeders re-run alone because their work buffer was too small */
     int32_t reserved;
@@ -194,9 +194,10 @@ typedef struct okr_batch_stats {
 
 /* Algorithm 1 for many independent feeders (Sec. IV; the candidates of one
  * feeder are independent, and so are feeders): one batched setup of every
- * feeder (load flows included), then ONE persistent launch in which each CTA
- * takes the next feeder from a queue ordered largest-first and runs that
- * feeder's whole search alone.  Each feeder's result is the one okr_reduce
+ * feeder (load flows included), then ONE persistent cooperative launch in
+ * which each team of CTAs takes the next feeder from a queue ordered
+ * largest-first and runs that feeder's whole search (teams of 1, 2, 4 or 8
+ * CTAs, chosen by okr_batch_autotune; default 2).  Each feeder's result is the one okr_reduce
  * gives for it alone.
  *
  * feeders: [n_feeders] HOST feeders.  params: [n_params] with n_params = 1
@@ -208,11 +209,15 @@ typedef struct okr_batch_stats {
 okr_status okr_reduce_batch(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
                             int32_t n_params, okr_batch_item *items, int32_t *super_of, okr_batch_stats *stats);
 
-/* Times the batched search with each CTA shape on this batch (two runs each),
- * keeps the fastest for later okr_reduce_batch calls on this context, and
- * returns it in *config (search_ms: [3] times in ms, may be NULL). */
+/* Times the batched search with each team shape on this batch (two runs
+ * each), keeps the fastest for later okr_reduce_batch calls on this context,
+ * and returns it in *config (search_ms: [4] times in ms, may be NULL). */
 okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
                               int32_t n_params, int32_t *config, double *search_ms);
+
+/* Sets the team shape of later okr_reduce_batch calls on this context
+ * (0/1/2/3 = 1/2/4/8 CTAs per feeder); OKR_EINVAL outside that range. */
+okr_status okr_set_batch_config(okr_ctx *ctx, int32_t config);
 
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096

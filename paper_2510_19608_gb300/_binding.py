@@ -62,7 +62,8 @@ class BatchStats(C.Structure):
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
-           "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune")
+           "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
+           "okr_set_batch_config")
 
 
 def lib_path() -> str:
@@ -95,6 +96,7 @@ def lib():
             L.okr_kron.argtypes = [P, P, I32, P, P, P]
             L.okr_reduce_batch.argtypes = [P, I32, P, P, I32, P, P, P]
             L.okr_batch_autotune.argtypes = [P, I32, P, P, I32, P, P]
+            L.okr_set_batch_config.argtypes = [P, I32]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -260,11 +262,15 @@ class Context:
                 o += h.c.n_bus
         return out, parts, {k: getattr(st, k) for k, _ in BatchStats._fields_}
 
+    def set_batch_config(self, config: int):
+        """okr_set_batch_config: team shape 0/1/2/3 = 1/2/4/8 CTAs per feeder."""
+        self._check(lib().okr_set_batch_config(self._h, int(config)))
+
     def batch_autotune(self, feeders, params):
         """okr_batch_autotune: returns (best config, search ms per config)."""
         hfs, arr, parr, npar = self._batch_args(feeders, params)
         cfg = C.c_int32()
-        ms = (C.c_double * 3)()
+        ms = (C.c_double * 4)()
         self._check(lib().okr_batch_autotune(self._h, len(hfs), arr, parr, npar, C.byref(cfg), ms))
         return int(cfg.value), list(ms)
 

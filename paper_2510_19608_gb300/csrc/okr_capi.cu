@@ -62,7 +62,7 @@ struct okr_ctx {
     size_t batch_cap = 0;
     unsigned char *batch_host = nullptr;    // pinned staging
     size_t batch_host_cap = 0;
-    int batch_config = 1;                   // CTA shape of the batched search (autotuned)
+    int batch_config = 1;                   // team shape of the batched search: 2 CTAs per feeder (autotuned)
 
     // last result
     bool have_topo = false;     // T describes the feeder of the last call
@@ -705,7 +705,11 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     if (!ctx) return OKR_EINVAL;
     if (nf < 1 || !feeders || !params || !items) return fail(ctx, OKR_EINVAL, "batch: bad arguments");
     if (n_params != 1 && n_params != nf) return fail(ctx, OKR_EINVAL, "batch: n_params must be 1 or n_feeders");
-    if (config < 0 || config > 2) return fail(ctx, OKR_EINVAL, "batch: config %d", config);
+    if (config < 0 || config > 3) return fail(ctx, OKR_EINVAL, "batch: config %d", config);
+    const int team = 1 << config;                       // CTAs per feeder: 1, 2, 4, 8
+    int per_sm[2] = {search_batch_blocks_per_sm(0), search_batch_blocks_per_sm(1)};
+    if (per_sm[0] < 1 || per_sm[1] < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
+    const int max_teams = std::max(1, ctx->num_sms * std::max(per_sm[0], per_sm[1]) / team);
     ctx->have_result = false;
     ctx->have_topo = false;
     std::vector<long long> sum_sz(nf);
@@ -741,6 +745,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     Ctrl *ctrl_d = nullptr;
     int *order_d = nullptr, *queue_d = nullptr, *err_d = nullptr;
     double *maxerr_d = nullptr;
+    BatchTeam *teams_d = nullptr;
     m.take(bs_d, nf);
     m.take(bf_d, nf);
     m.take(ctrl_d, nf);
@@ -748,6 +753,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     m.take(queue_d, 2);
     m.take(err_d, nf);
     m.take(maxerr_d, nf);
+    m.take(teams_d, 2 * (size_t)max_teams);
     std::vector<size_t> in_off(nf);
     for (int f = 0; f < nf; ++f) {
         const size_t n = feeders[f].n_bus, L = feeders[f].n_scen;
@@ -769,7 +775,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         const int ppc = positions_per_chunk(L);
         const long long chunks = 2LL * ((2LL * sum_sz[f] + 2LL * n + ppc - 1) / ppc + 1);
         fb_off[f] = w.used;
-        layout_feeder(w, n, L, 0, 1, chunks, fbs[f]);
+        layout_feeder(w, n, L, 0, 8, chunks, fbs[f]);          // per-CTA sums for teams of up to 8
     }
     int *super_all_d = nullptr;
     const size_t super_off = w.used;
@@ -804,6 +810,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     md.take(queue_d, 2);
     md.take(err_d, nf);
     md.take(maxerr_d, nf);
+    md.take(teams_d, 2 * (size_t)max_teams);
     Carver mh;                                  // the same offsets in the host buffer
     mh.base = hb;
     BatchSetup *bs_h; BatchFeeder *bf_h; Ctrl *ctrl_h; int *order_h, *queue_h, *err_h; double *maxerr_h;
@@ -814,6 +821,12 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     mh.take(queue_h, 2);
     mh.take(err_h, nf);
     mh.take(maxerr_h, nf);
+    BatchTeam *teams_h;
+    mh.take(teams_h, 2 * (size_t)max_teams);
+    for (int i = 0; i < 2 * max_teams; ++i) {
+        teams_h[i].ctrl.max_spins = params[0].max_spins > 0 ? params[0].max_spins : kDefaultSpins;
+        teams_h[i].slot = 0;
+    }
     // per feeder: buffers, inputs, descriptors, controls
     size_t soff = 0;
     std::vector<size_t> super_pos(nf);
@@ -824,7 +837,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         Carver c;
         c.base = base + fb_off[f];
         FeederBufs &B = fbs[f];
-        layout_feeder(c, n, L, 0, 1, B.X.max_chunks, B);
+        layout_feeder(c, n, L, 0, 8, B.X.max_chunks, B);
         // inputs live in the staged block
         Carver ci;
         ci.base = base + in_off[f];
@@ -907,11 +920,11 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     for (int g = 0, first = 0; g < 2; first += (int)ord[g].size(), ++g) {
         const int cnt = (int)ord[g].size();
         if (cnt == 0) continue;
-        const int per_sm = search_batch_blocks_per_sm(g, config);
-        if (per_sm < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
-        const int grid = std::min(cnt, ctx->num_sms * per_sm);
+        const int nteams = std::min(cnt, ctx->num_sms * per_sm[g] / team);
+        if (nteams < 1) return fail(ctx, OKR_EINVAL, "batched search: team of %d CTAs does not fit", team);
+        const int grid = nteams * team;
         ctas = std::max(ctas, grid);
-        CK(launch_search_batch(g, config, grid, bf_d, order_d + first, cnt, queue_d + g, st));
+        CK(launch_search_batch(g, team, grid, bf_d, order_d + first, cnt, queue_d + g, teams_d + g * max_teams, st));
     }
     CK(cudaEventRecord(e2, st));
     // results: controls, setup errors and largest errors (one copy), assignments
@@ -992,6 +1005,13 @@ okr_status okr_reduce_batch(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *f
     return reduce_batch_impl(ctx, n_feeders, feeders, params, n_params, items, super_of, stats, ctx->batch_config);
 }
 
+okr_status okr_set_batch_config(okr_ctx *ctx, int32_t config) {
+    if (!ctx) return OKR_EINVAL;
+    if (config < 0 || config > 3) return fail(ctx, OKR_EINVAL, "batch config %d outside [0, 3]", config);
+    ctx->batch_config = config;
+    return OKR_OK;
+}
+
 okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
                               int32_t n_params, int32_t *config, double *search_ms) {
     if (!ctx) return OKR_EINVAL;
@@ -999,7 +1019,7 @@ okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder 
     std::vector<okr_batch_item> items(n_feeders > 0 ? n_feeders : 1);
     double best = 1e300;
     int best_c = ctx->batch_config;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 4; ++c) {
         okr_batch_stats st{};
         double t = 1e300;
         for (int rep = 0; rep < 2; ++rep) {     // the first run warms the buffers

@@ -83,11 +83,19 @@ struct BatchFeeder {
     int *super_out;             // [n] assignment in caller numbering
     double *max_err;            // largest per-phase error of the final network
 };
-// Batched search: configs 0/1/2 = 512/256/128 threads per CTA (1/2/4 CTAs per SM).
-cudaError_t launch_search_batch(int precision, int config, int grid, const BatchFeeder *fd, const int *order, int nf,
-                                int *queue, cudaStream_t st);
-int search_batch_threads(int config);
-int search_batch_blocks_per_sm(int precision, int config);
+// Per-team state of a batched search: the team's barrier, its control block
+// (spin limit, error flag) and the queue slot its leader fetched.
+struct BatchTeam {
+    GridBar bar;
+    Ctrl ctrl;
+    int slot;
+    int pad;
+};
+// Batched search with teams of `team` CTAs (cooperative launch of `grid` CTAs,
+// a multiple of `team`).
+cudaError_t launch_search_batch(int precision, int team, int grid, const BatchFeeder *fd, const int *order, int nf,
+                                int *queue, BatchTeam *teams, cudaStream_t st);
+int search_batch_blocks_per_sm(int precision);
 cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st);
 int search_blocks_per_sm();     // CTAs of the search kernel that fit one SM (0 on error)
 __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);

@@ -613,7 +613,7 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
                             double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc) {
     const int tid = threadIdx.x;
     unsigned long long bk = ~0ull;
-    for (int i = tid; i < m; i += (int)blockDim.x)
+    for (int i = tid; i < m; i += kThreads)
         if (ldi(feas + i)) bk = min(bk, dkey(ldd(score + i)));
     bk = block_reduce(bk, MinU(), smu);
     Sel out;
@@ -623,7 +623,7 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
     const double edge = dval(bk) + tau;
     const unsigned long long ek = dkey(edge);
     unsigned long long key = ~0ull, gk = ~0ull;
-    for (int i = tid; i < m; i += (int)blockDim.x) {
+    for (int i = tid; i < m; i += kThreads) {
         if (!ldi(feas + i)) continue;
         const unsigned long long k = dkey(ldd(score + i));
         if (k <= ek) {
@@ -637,12 +637,12 @@ __device__ Sel select_exact(const Search &X, int m, const int *map, const double
     gk = block_reduce(gk, MinU(), smu);
     int w = 0x7fffffff;
     if (ksure < key) {              // a candidate known to be in the band has the smallest key
-        for (int c = tid; c < nc; c += (int)blockDim.x)
+        for (int c = tid; c < nc; c += kThreads)
             if (__ldcg(X.ckey + c) == ksure) w = min(w, c);
         w = block_reduce(w, MinI(), smi);
         out.w = (w < nc) ? w : -2;
     } else {
-        for (int i = tid; i < m; i += (int)blockDim.x)
+        for (int i = tid; i < m; i += kThreads)
             if (ldi(feas + i) && dkey(ldd(score + i)) <= ek && __ldcg(X.ckey + (map ? map[i] : i)) == key) w = min(w, i);
         w = block_reduce(w, MinI(), smi);
         out.w = (w < m) ? (map ? map[w] : w) : -2;
@@ -682,7 +682,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     const float margin_lo = __double2float_rd(margin), margin_hi = __double2float_ru(margin);
     const float tau_lo = __double2float_rd(tau), tau_hi = __double2float_ru(tau);
     float mhi = INFINITY, mlo = INFINITY;
-    for (int c = tid; c < nc; c += (int)blockDim.x) {
+    for (int c = tid; c < nc; c += kThreads) {
         const float4 q = __ldcg(X.scr + c);
         if (__fsub_rd(q.z, q.w) <= margin_hi) mlo = fminf(mlo, __fsub_rd(q.x, q.y));
         if (surely_feasible(q, margin_lo)) mhi = fminf(mhi, __fadd_ru(q.x, q.y));
@@ -699,7 +699,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     const float edge_in = __fadd_rd(mlo, tau_lo), edge_out = __fadd_ru(mhi, tau_hi);
     unsigned long long ks = ~0ull;
     float g = INFINITY;
-    for (int c = tid; c < nc; c += (int)blockDim.x) {
+    for (int c = tid; c < nc; c += kThreads) {
         const float4 q = __ldcg(X.scr + c);
         const bool maybe = __fsub_rd(q.z, q.w) <= margin_hi;
         if (!maybe) continue;
@@ -712,7 +712,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     out.gap = (double)block_reduce(g, MinF(), smf);
     // R: possible minimizers and uncertain candidates with a key below ks
     int nR = 0, need = 0;
-    for (int c0 = 0; c0 < nc; c0 += (int)blockDim.x) {
+    for (int c0 = 0; c0 < nc; c0 += kThreads) {
         const int c = c0 + tid;
         int flag = 0, unc = 0;
         if (c < nc) {
@@ -733,7 +733,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     }
     if (need == 0) {
         int w = 0x7fffffff;
-        for (int c = tid; c < nc; c += (int)blockDim.x)
+        for (int c = tid; c < nc; c += kThreads)
             if (__ldcg(X.ckey + c) == ks) w = min(w, c);
         w = block_reduce(w, MinI(), smi);
         out.win = (w < nc) ? w : -2;
@@ -748,7 +748,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
 // One feeder's search on a team of G CTAs (rank = this CTA's index in the team).
 template <int PREC>
 __device__ __forceinline__ void search_run(const Topo &T, const State &S, const Search &X, Ctrl *C, GridBar *gb,
-                                           int rank, unsigned G) {
+                                           int rank, unsigned G, unsigned &epoch) {
     __shared__ double smd[32];
     __shared__ float smf[32];
     __shared__ unsigned long long smu[32];
@@ -760,7 +760,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
     const int n = T.n, L = T.L;
     const int Lp = L <= 1 ? 1 : (L <= 2 ? 2 : 4);
     const int SP = 4 * Lp, PPW = 32 / SP;
-    const int nt = blockDim.x;
+    constexpr int nt = kThreads;           // every search kernel runs 512-thread CTAs
     const int tid = threadIdx.x, lane = tid & 31;
     const int gt = rank * nt + tid, gs = (int)G * nt;
     const int warp = gt >> 5, nwarps = gs >> 5;
@@ -769,7 +769,6 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
     const bool prof = C->profile != 0;
     const bool obj1 = (PREC == 0) && C->objective == 1;
     const bool lead = (rank == 0 && tid == 0);
-    unsigned epoch = 0;
     int t = C->t, ns = C->n_super;
     double s_cur = C->s_cur;               // SMICE of the committed state
     bool have = false;                     // a sweep's scores wait for selection
@@ -1114,7 +1113,22 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             // also into shared memory for the chunk map below
             int *s_lbase = s_Rbase;
             const bool in_smem = s_mine.x <= kRmax;     // this CTA's candidate bases fit shared memory
-            {
+            if (gs >= ns) {                             // one slot per thread (a full grid)
+                if (gt >= 1 && gt < ns) {
+                    int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
+                    for (int d = 0; d < 2; ++d) {
+                        const Cand c = X.slot[2 * gt + d];
+                        if (c.s < 0) continue;
+                        X.cand[ci] = c;
+                        X.ckey[ci] = c.key;
+                        X.base[ci] = pos;
+                        if (in_smem) s_lbase[li] = pos;
+                        ++ci;
+                        ++li;
+                        pos += cand_positions(c);
+                    }
+                }
+            } else {
                 const int per = (ns + gs - 1) / gs, jb = max(1, gt * per), je = min(ns, gt * per + per);
                 int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
                 for (int j = jb; j < je; ++j)
@@ -1140,11 +1154,18 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             for (int g = (p0 + PPW - 1) / PPW + tid; g * PPW < p1; g += nt) {
                 const int q = g * PPW;
                 int lo = 0, hi = mt.x - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    const int bm = in_smem ? s_lbase[mid] : ldi(X.base + pref.x + mid);
-                    if (bm <= q) lo = mid;
-                    else hi = mid - 1;
+                if (in_smem) {
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (s_lbase[mid] <= q) lo = mid;
+                        else hi = mid - 1;
+                    }
+                } else {
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (ldi(X.base + pref.x + mid) <= q) lo = mid;
+                        else hi = mid - 1;
+                    }
                 }
                 X.chunk_first[g] = pref.x + lo;
             }
@@ -1205,23 +1226,31 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
 
 template <int PREC>
 __global__ void __launch_bounds__(kThreads, 1) k_search(Topo T, State S, Search X, Ctrl *C, GridBar *gb) {
-    search_run<PREC>(T, S, X, C, gb, blockIdx.x, gridDim.x);
+    unsigned epoch = 0;
+    search_run<PREC>(T, S, X, C, gb, blockIdx.x, gridDim.x, epoch);
 }
 
-// Many feeders in one launch: every CTA takes the next feeder from the queue
-// (feeders listed largest first) and runs its whole search alone, then writes
-// the feeder's assignment in caller numbering.
-template <int PREC, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_search_batch(const BatchFeeder *fd, const int *order, int nf, int *queue) {
+// Many feeders in one launch.  The grid is split into teams of k CTAs; each
+// team takes the next feeder from the queue (feeders listed largest first),
+// runs that feeder's whole search with team-wide barriers (a plain CTA barrier
+// when k = 1), then writes the feeder's assignment in caller numbering.  All
+// CTAs are co-resident (cooperative launch), and every wait is bounded.
+template <int PREC>
+__global__ void __launch_bounds__(kThreads, 1) k_search_batch(const BatchFeeder *fd, const int *order, int nf,
+                                                              int *queue, BatchTeam *teams, int k) {
     __shared__ Topo sT;
     __shared__ State sS;
     __shared__ Search sX;
-    __shared__ int s_f;
+    __shared__ int s_q;
+    const int team = blockIdx.x / k, rank = blockIdx.x % k;
+    BatchTeam *tm = teams + team;
+    unsigned epoch = 0;
     for (;;) {
+        if (rank == 0 && threadIdx.x == 0) tm->slot = atomicAdd(queue, 1);
+        if (!team_barrier(&tm->bar, &tm->ctrl, k, epoch)) return;
+        if (threadIdx.x == 0) s_q = *(volatile int *)&tm->slot;
         __syncthreads();
-        if (threadIdx.x == 0) s_f = atomicAdd(queue, 1);
-        __syncthreads();
-        const int q = s_f;
+        const int q = s_q;
         if (q >= nf) return;
         const int f = order[q];
         if (threadIdx.x == 0) {
@@ -1232,14 +1261,15 @@ __global__ void __launch_bounds__(NT, MINB) k_search_batch(const BatchFeeder *fd
         __syncthreads();
         Ctrl *C = fd[f].C;
         const bool ok = ldi(fd[f].setup_err) == 0;
-        if (ok) search_run<PREC>(sT, sS, sX, C, nullptr, 0, 1);
-        __threadfence();
-        __syncthreads();
-        for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[ldi(sS.label + sT.pre[i])] : -1;
-        if (threadIdx.x == 0) {
+        if (ok) search_run<PREC>(sT, sS, sX, C, &tm->bar, rank, k, epoch);
+        if (!team_barrier(&tm->bar, &tm->ctrl, k, epoch)) return;
+        for (int i = rank * kThreads + threadIdx.x; i < sT.n; i += k * kThreads)
+            fd[f].super_out[i] = ok ? sT.orig[ldi(sS.label + sT.pre[i])] : -1;
+        if (rank == 0 && threadIdx.x == 0) {
             const int t = ok ? ldi(&C->t) : 0;
             *fd[f].max_err = t > 0 ? ldd(sX.dec_maxerr + t - 1) : 0.0;
         }
+        if (!team_barrier(&tm->bar, &tm->ctrl, k, epoch)) return;     // the slot is read by all before reuse
     }
 }
 
@@ -1258,26 +1288,17 @@ int search_blocks_per_sm() {
     return a < b ? a : b;
 }
 
-cudaError_t launch_search_batch(int precision, int config, int grid, const BatchFeeder *fd, const int *order, int nf,
-                                int *queue, cudaStream_t st) {
-    void *args[] = {&fd, &order, &nf, &queue};
-    const void *fn = nullptr;
-    int nt = 512;
-    if (config == 0) { fn = precision == 1 ? (const void *)k_search_batch<1, 512, 1> : (const void *)k_search_batch<0, 512, 1>; nt = 512; }
-    else if (config == 1) { fn = precision == 1 ? (const void *)k_search_batch<1, 256, 2> : (const void *)k_search_batch<0, 256, 2>; nt = 256; }
-    else { fn = precision == 1 ? (const void *)k_search_batch<1, 128, 4> : (const void *)k_search_batch<0, 128, 4>; nt = 128; }
-    return cudaLaunchKernel(fn, dim3(grid), dim3(nt), args, 0, st);
+cudaError_t launch_search_batch(int precision, int team, int grid, const BatchFeeder *fd, const int *order, int nf,
+                                int *queue, BatchTeam *teams, cudaStream_t st) {
+    void *args[] = {&fd, &order, &nf, &queue, &teams, &team};
+    const void *fn = precision == 1 ? (const void *)k_search_batch<1> : (const void *)k_search_batch<0>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
 }
 
-int search_batch_threads(int config) { return config == 0 ? 512 : (config == 1 ? 256 : 128); }
-
-int search_batch_blocks_per_sm(int precision, int config) {
+int search_batch_blocks_per_sm(int precision) {
     int a = 0;
-    const void *fn;
-    if (config == 0) fn = precision == 1 ? (const void *)k_search_batch<1, 512, 1> : (const void *)k_search_batch<0, 512, 1>;
-    else if (config == 1) fn = precision == 1 ? (const void *)k_search_batch<1, 256, 2> : (const void *)k_search_batch<0, 256, 2>;
-    else fn = precision == 1 ? (const void *)k_search_batch<1, 128, 4> : (const void *)k_search_batch<0, 128, 4>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, search_batch_threads(config), 0) != cudaSuccess) return 0;
+    const void *fn = precision == 1 ? (const void *)k_search_batch<1> : (const void *)k_search_batch<0>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fn, kThreads, 0) != cudaSuccess) return 0;
     return a;
 }
 

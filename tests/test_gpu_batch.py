@@ -117,8 +117,20 @@ def test_autotune_picks_a_shape_and_keeps_results(ctx):
     plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1) for _, r in batch]
     ref, ref_parts, _ = ctx.reduce_batch(feeders, plist)
     cfg, ms = ctx.batch_autotune(feeders, plist)
-    assert cfg in (0, 1, 2) and all(m > 0 and math.isfinite(m) for m in ms)
+    assert cfg in (0, 1, 2, 3) and all(m > 0 and math.isfinite(m) for m in ms)
     items, parts, stats = ctx.reduce_batch(feeders, plist)
     assert stats["config"] == cfg
     for a, b, pa, pb in zip(ref, items, ref_parts, parts):
+        assert abs(a.pop("smice") - b.pop("smice")) <= S_TOL      # summation order follows the team size
         assert a == b and np.array_equal(pa, pb)
+
+
+@pytest.mark.parametrize("config", [0, 1, 2, 3])
+def test_every_team_shape_matches_single_runs(ctx, config):
+    batch = _batch(6, 40, 500, seed=41 + config)
+    feeders = [f for f, _ in batch]
+    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1) for _, r in batch]
+    ctx.set_batch_config(config)
+    items, parts, stats = ctx.reduce_batch(feeders, plist)
+    assert stats["config"] == config and stats["ctas"] % (1 << config) == 0
+    _check_against_single(ctx, feeders, plist, items, parts)
