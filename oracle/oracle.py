@@ -13,6 +13,9 @@ Functions (each names the passage it follows):
   zbus            Z = Y_LL^{-1}
   kron            Y_Kron, the Schur complement onto the kept buses (Sec. II-B)
   reduce          Algorithm 1 (Sec. IV), literal or delta mode
+  kron_graph      bus adjacency of Y_Kron: a 3x3 block with a nonzero entry (Sec. V)
+  maximal_cliques maximal cliques of that graph (Bron-Kerbosch with pivoting)
+  radialize       critical nodes of every maximal clique (Sec. V)
 """
 from __future__ import annotations
 
@@ -228,3 +231,86 @@ def max_merges_for(n_bus: int, target: float) -> int:
     """Target reduction -> number of merges: ceil(target * n), at most n - 1."""
     import math
     return min(n_bus - 1, int(math.ceil(target * n_bus - 1e-12)))
+
+
+# ----------------------------------------------------------------------------- Sec. V
+def kron_graph(feeder, kept: np.ndarray, tol: float = 0.0) -> tuple[np.ndarray, dict]:
+    """Kept buses and their adjacency in the Kron-reduced network: buses i != j are
+    connected when the 3x3 block of Y_Kron between them has an entry with
+    |y| > tol (Sec. V extends the single-phase nonzero test to blocks)."""
+    Yk, kidx = kron(feeder, kept)
+    bus = kidx // 3
+    buses = np.unique(bus)
+    adj = {int(b): set() for b in buses}
+    for a in range(len(kidx)):
+        for c in range(len(kidx)):
+            if bus[a] != bus[c] and abs(Yk[a, c]) > tol:
+                adj[int(bus[a])].add(int(bus[c]))
+    return buses, adj
+
+
+def maximal_cliques(adj: dict) -> list[set]:
+    """Every maximal clique of an undirected graph (Bron-Kerbosch with pivoting)."""
+    out = []
+
+    def bk(r, p, x):
+        if not p and not x:
+            out.append(set(r))
+            return
+        u = max(p | x, key=lambda v: len(adj[v] & p))
+        for v in list(p - adj[u]):
+            bk(r | {v}, p & adj[v], x & adj[v])
+            p = p - {v}
+            x = x | {v}
+
+    bk(set(), set(adj), set())
+    return out
+
+
+def radialize(feeder, kept: np.ndarray) -> np.ndarray:
+    """Critical nodes (Sec. V): for every maximal clique of the Kron-reduced graph,
+    take the sub-tree of the original feeder that spans the clique's buses and
+    mark its buses of degree >= 3 (within that sub-tree) that are not kept.
+    Returns a flag per bus; kept + critical buses make the reduced network radial."""
+    parent = np.asarray(feeder.parent)
+    n = parent.shape[0]
+    _, adj = kron_graph(feeder, kept)
+    crit = np.zeros(n, dtype=np.uint8)
+    for clique in maximal_cliques(adj):
+        if len(clique) < 3:
+            continue
+        # spanning sub-tree: the union of the tree paths between the clique's buses
+        nodes, edges = set(), set()
+        cl = sorted(clique)
+        for a in cl:
+            for b in cl:
+                if a >= b:
+                    continue
+                pa, pb = [a], [b]
+                while pa[-1] != 0:
+                    pa.append(int(parent[pa[-1]]))
+                while pb[-1] != 0:
+                    pb.append(int(parent[pb[-1]]))
+                common = set(pa) & set(pb)
+                path = [v for v in pa if v not in common] + [v for v in pb if v not in common]
+                # lowest common ancestor: the deepest common bus
+                depth = {}
+                for v in common:
+                    d, w = 0, v
+                    while w != 0:
+                        w = int(parent[w])
+                        d += 1
+                    depth[v] = d
+                lca = max(common, key=lambda v: depth[v])
+                for v in path:
+                    nodes.add(v)
+                    edges.add((v, int(parent[v])))
+                nodes.add(lca)
+        deg = {v: 0 for v in nodes}
+        for (c, p_) in edges:
+            deg[c] += 1
+            deg[p_] += 1
+        for v, d in deg.items():
+            if d >= 3 and not kept[v]:
+                crit[v] = 1
+    return crit

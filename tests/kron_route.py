@@ -181,3 +181,25 @@ def connected_partitions(feeder):
                 for i in mem:
                     sup[i] = k
             yield sup
+
+
+def kron_kept_voltages(feeder, Ypad, kept_bus, iagg):
+    """Voltages of the kept buses of the Kron-reduced network on `kept_bus` for
+    injections `iagg` ([L, 3n], zero on eliminated buses), slack fixed."""
+    n = feeder.n_bus
+    pres = present(feeder)
+    kept_rows = np.repeat(np.asarray(kept_bus, bool), 3)
+    Yk = kron_pinv(Ypad, kept_rows)
+    K = np.where(kept_rows)[0]
+    v0 = feeder.v_slack[:, 0] + 1j * feeder.v_slack[:, 1]
+    unk = [a for a, k in enumerate(K) if k >= 3 and pres[k]]
+    fix = [a for a, k in enumerate(K) if k < 3]
+    out = np.zeros((iagg.shape[0], 3 * n), dtype=np.complex128)
+    for l in range(iagg.shape[0]):
+        A = Yk[np.ix_(unk, unk)]
+        b = iagg[l, K[unk]] - Yk[np.ix_(unk, fix)] @ v0
+        x = np.linalg.solve(A, b)
+        out[l, 0:3] = v0
+        for a, v in zip(unk, x):
+            out[l, K[a]] = v
+    return out

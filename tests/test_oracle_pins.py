@@ -455,3 +455,86 @@ def test_golden_feeder40_decision_sequence():
         assert (res["s"][t], res["r"][t]) == (int(row[1]), int(row[2]))
         assert abs(res["score"][t] - float(row[3])) <= 1e-11
         assert abs(res["maxerr"][t] - float(row[4])) <= 1e-12
+
+
+# ----------------------------------------------------------------------------- Sec. V radialization
+def _is_tree(buses, adj):
+    edges = sum(len(v) for v in adj.values()) // 2
+    if edges != len(buses) - 1:
+        return False
+    seen, stack = {int(buses[0])}, [int(buses[0])]
+    while stack:
+        u = stack.pop()
+        for w in adj[u]:
+            if w not in seen:
+                seen.add(w)
+                stack.append(w)
+    return len(seen) == len(buses)
+
+
+def _star_feeder(children):
+    parent = [-1, 0] + [1] * children
+    return _simple_feeder(parent, [7] * len(parent))
+
+
+def _simple_feeder(parent, phases):
+    n = len(parent)
+    z = np.zeros((n, 3, 3, 2))
+    s = np.zeros((2, n, 3, 2))
+    rng = np.random.default_rng(n)
+    for i in range(1, n):
+        for a in range(3):
+            for b in range(3):
+                if phases[i] >> a & 1 and phases[i] >> b & 1:
+                    z[i, a, b] = (0.004 + 0.001 * rng.random(), 0.008) if a == b else (0.001, 0.003)
+    vs = np.array([[1.0, 0.0], [-0.5, -math.sqrt(3) / 2], [-0.5, math.sqrt(3) / 2]])
+    return fg.Feeder(parent=np.array(parent, np.int32), phases=np.array(phases, np.uint8), z_line=z, s_load=s,
+                     v_slack=vs, meta={})
+
+
+def test_radialize_star_marks_the_hub_and_a_chain_needs_nothing():
+    f = _star_feeder(3)                               # 0 - 1 - {2, 3, 4}
+    kept = np.array([1, 0, 1, 1, 1], np.uint8)        # Kron graph: the 4-clique {0, 2, 3, 4}
+    assert list(O.radialize(f, kept)) == [0, 1, 0, 0, 0]
+    chain = _simple_feeder([-1, 0, 1, 2, 3, 4], [7] * 6)
+    assert not O.radialize(chain, np.array([1, 0, 1, 0, 0, 1], np.uint8)).any()
+    # two children kept under a reduced bus only: a 3-clique with the parent side
+    assert list(O.radialize(_star_feeder(2), np.array([1, 0, 1, 1], np.uint8))) == [0, 1, 0, 0]
+
+
+@pytest.mark.parametrize("seed,frac", [(1, 0.3), (2, 0.5), (3, 0.7)])
+def test_radialized_network_is_radial_and_minimal(seed, frac):
+    f, _ = fg.preset("feeder1000", n_bus=120, seed=seed)
+    kept = (np.random.default_rng(seed).random(f.n_bus) < frac).astype(np.uint8)
+    kept[0] = 1
+    crit = O.radialize(f, kept)
+    rad = np.maximum(kept, crit)
+    buses, adj = O.kron_graph(f, rad)
+    assert _is_tree(buses, adj)
+    if not crit.any():
+        assert _is_tree(*O.kron_graph(f, kept))
+    for c in np.nonzero(crit)[0][:6]:                 # each critical bus is needed
+        less = rad.copy()
+        less[c] = 0
+        assert not _is_tree(*O.kron_graph(f, less))
+
+
+def test_radialization_keeps_super_node_voltages():
+    """Sec. V: critical buses added without injections leave the super-node
+    voltages of the Kron-reduced network unchanged."""
+    f, run = fg.preset("feeder1000", n_bus=150)
+    vhat, ihat = O.operating_points(f)
+    res = O.reduce(f, vhat, ihat, margin=0.005, max_merges=90)
+    sup = res["super_of"]
+    kept = (sup == np.arange(f.n_bus)).astype(np.uint8)
+    crit = O.radialize(f, kept)
+    assert crit.any()
+    iagg = np.zeros((ihat.shape[0], 3 * f.n_bus), dtype=np.complex128)
+    for l in range(ihat.shape[0]):
+        for i in range(f.n_bus):
+            iagg[l, 3 * sup[i]:3 * sup[i] + 3] += ihat[l, i]
+    Ypad = KR.padded_y(f)
+    v1 = KR.kron_kept_voltages(f, Ypad, kept, iagg)
+    v2 = KR.kron_kept_voltages(f, Ypad, np.maximum(kept, crit), iagg)
+    rows = np.repeat(kept.astype(bool), 3) & KR.present(f)
+    assert np.abs(v1[:, rows] - v2[:, rows]).max() <= 1e-12
