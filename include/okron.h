@@ -219,6 +219,19 @@ okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder 
  * (0/1/2/3 = 1/2/4/8 CTAs per feeder); OKR_EINVAL outside that range. */
 okr_status okr_set_batch_config(okr_ctx *ctx, int32_t config);
 
+/* Three-phase radialization (Sec. V): the critical buses that make the
+ * Kron-reduced network radial.  For every maximal clique of Y_Kron's bus
+ * graph (one per connected component of reduced buses and its boundary),
+ * the reduced buses of degree >= 3 in the sub-tree spanning the clique.  The
+ * radial network keeps kept + critical buses (okr_kron with that set gives
+ * its Y_Kron); with no injection moved to the critical buses, the super-node
+ * voltages are those of the unradialized network.
+ *
+ * kept: HOST [n_bus] flags (bus 0 kept) or NULL for the last reduction's
+ * super-nodes.  critical: HOST [n_bus] flags, written (caller numbering).
+ * *n_critical (may be NULL): their number.  Errors as okr_kron. */
+okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, int32_t *n_critical);
+
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096
 

@@ -63,7 +63,7 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
            "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
-           "okr_set_batch_config")
+           "okr_set_batch_config", "okr_radialize")
 
 
 def lib_path() -> str:
@@ -97,6 +97,7 @@ def lib():
             L.okr_reduce_batch.argtypes = [P, I32, P, P, I32, P, P, P]
             L.okr_batch_autotune.argtypes = [P, I32, P, P, I32, P, P]
             L.okr_set_batch_config.argtypes = [P, I32]
+            L.okr_radialize.argtypes = [P, P, P, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -273,6 +274,17 @@ class Context:
         ms = (C.c_double * 4)()
         self._check(lib().okr_batch_autotune(self._h, len(hfs), arr, parr, npar, C.byref(cfg), ms))
         return int(cfg.value), list(ms)
+
+    def radialize(self, kept=None):
+        """okr_radialize: critical-bus flags (caller order) of `kept` (None = the
+        last reduction's super-nodes)."""
+        n = int(self.summary()["n_bus"]) if kept is None else len(kept)
+        kp = None if kept is None else np.ascontiguousarray(kept, dtype=np.uint8)
+        out = np.zeros(n, np.uint8)
+        cnt = C.c_int32()
+        self._check(lib().okr_radialize(self._h, _ptr(kp) if kp is not None else None, _ptr(out), C.byref(cnt)))
+        assert int(cnt.value) == int(out.sum())
+        return out
 
     def kron(self, kept=None):
         """Y_Kron onto `kept` (caller-order flags; None = the last reduction's

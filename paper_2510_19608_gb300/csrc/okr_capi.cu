@@ -53,7 +53,8 @@ struct okr_ctx {
     int cap_kron_n = 0;
     std::vector<void *> kron_allocs;
     double2 *ykr = nullptr, *kbig = nullptr;
-    uint8_t *kron_kept = nullptr;
+    uint8_t *kron_kept = nullptr, *kron_crit = nullptr;
+    int *kron_count = nullptr;
     size_t cap_ykr = 0, cap_kbig = 0;
     double kron_ms = 0.0;
 
@@ -418,6 +419,49 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
 }  // namespace
 
 // ======================================================================= C ABI
+namespace {
+
+okr_status ensure_kron_work(okr_ctx *ctx, int n) {
+    if (ctx->cap_kron_n < n) {
+        for (void *q : ctx->kron_allocs) cudaFree(q);
+        ctx->kron_allocs.clear();
+        ctx->cap_kron_n = 0;
+        KronWork &W = ctx->kw;
+        auto take = [&](auto **ptr, size_t count) -> cudaError_t {
+            void *q = nullptr;
+            cudaError_t e = cudaMalloc(&q, sizeof(**ptr) * (count ? count : 1));
+            if (e == cudaSuccess) { ctx->kron_allocs.push_back(q); *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q); }
+            return e;
+        };
+        const size_t N = n;
+        CK(take(&W.keptp, N));
+        CK(take(&W.g, N));
+        CK(take(&W.key, N));
+        CK(take(&W.cnt, N));
+        CK(take(&W.dsum, N));
+        CK(take(&W.fill, N));
+        CK(take(&W.goff, N));
+        CK(take(&W.ports, N));
+        CK(take(&W.out_off, N + 1));
+        CK(take(&W.pn, 3 * N));
+        CK(take(&W.gkey, N));
+        CK(take(&W.gp, N));
+        CK(take(&W.gd, N));
+        CK(take(&W.gport, N + 1));
+        CK(take(&W.grow, N + 1));
+        CK(take(&W.rows, 3 * N));
+        CK(take(&W.gbig, N));
+        CK(take(&W.hdr, 1));
+        CK(take(&ctx->kron_kept, N));
+        CK(take(&ctx->kron_crit, N));
+        CK(take(&ctx->kron_count, 1));
+        ctx->cap_kron_n = n;
+    }
+    return OKR_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void okr_default_params(okr_params *p) {
@@ -562,6 +606,28 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     return OKR_OK;
 }
 
+okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, int32_t *n_critical) {
+    if (!ctx || !critical) return OKR_EINVAL;
+    if (!ctx->have_topo) return fail(ctx, OKR_ENOTREADY, "no feeder: run a reduction or a load flow first");
+    if (!kept && !ctx->have_result) return fail(ctx, OKR_ENOTREADY, "no reduction result to take the kept set from");
+    if (kept && !kept[0]) return fail(ctx, OKR_EINVAL, "the slack bus (bus 0) must be kept");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->fb.T.n;
+    okr_status ks = ensure_kron_work(ctx, n);
+    if (ks != OKR_OK) return ks;
+    if (kept) CK(cudaMemcpyAsync(ctx->kron_kept, kept, n, cudaMemcpyHostToDevice, st));
+    k_radial_critical<<<1, 1024, 0, st>>>(ctx->fb.T, kept ? nullptr : ctx->fb.S.label, kept ? ctx->kron_kept : nullptr,
+                                          ctx->kw, ctx->kron_crit, ctx->kron_count);
+    CK(cudaGetLastError());
+    int cnt = 0;
+    CK(cudaMemcpyAsync(critical, ctx->kron_crit, n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&cnt, ctx->kron_count, sizeof cnt, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (n_critical) *n_critical = cnt;
+    return OKR_OK;
+}
+
 okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_out, int32_t *phase_node,
                     int32_t *k_phi) {
     if (!ctx || !k_phi) return OKR_EINVAL;
@@ -571,39 +637,8 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
     CK(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n;
-    if (ctx->cap_kron_n < n) {
-        for (void *q : ctx->kron_allocs) cudaFree(q);
-        ctx->kron_allocs.clear();
-        ctx->cap_kron_n = 0;
-        KronWork &W = ctx->kw;
-        auto take = [&](auto **ptr, size_t count) -> cudaError_t {
-            void *q = nullptr;
-            cudaError_t e = cudaMalloc(&q, sizeof(**ptr) * (count ? count : 1));
-            if (e == cudaSuccess) { ctx->kron_allocs.push_back(q); *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q); }
-            return e;
-        };
-        const size_t N = n;
-        CK(take(&W.keptp, N));
-        CK(take(&W.g, N));
-        CK(take(&W.key, N));
-        CK(take(&W.cnt, N));
-        CK(take(&W.dsum, N));
-        CK(take(&W.fill, N));
-        CK(take(&W.goff, N));
-        CK(take(&W.ports, N));
-        CK(take(&W.out_off, N + 1));
-        CK(take(&W.pn, 3 * N));
-        CK(take(&W.gkey, N));
-        CK(take(&W.gp, N));
-        CK(take(&W.gd, N));
-        CK(take(&W.gport, N + 1));
-        CK(take(&W.grow, N + 1));
-        CK(take(&W.rows, 3 * N));
-        CK(take(&W.gbig, N));
-        CK(take(&W.hdr, 1));
-        CK(take(&ctx->kron_kept, N));
-        ctx->cap_kron_n = n;
-    }
+    okr_status ks = ensure_kron_work(ctx, n);
+    if (ks != OKR_OK) return ks;
     KronWork &W = ctx->kw;
     uint8_t *kept_dev = nullptr;
     if (kept) {

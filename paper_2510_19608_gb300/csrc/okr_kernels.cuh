@@ -70,6 +70,8 @@ struct KronWork {
 };
 __global__ void __launch_bounds__(1024) k_kron_groups(Topo T, const int *label, const uint8_t *kept_in, KronWork W);
 __global__ void k_kron_diag(KronWork W, double2 *Y, int K);
+__global__ void __launch_bounds__(1024) k_radial_critical(Topo T, const int *label, const uint8_t *kept_in, KronWork W,
+                                                          uint8_t *crit, int *count);
 cudaError_t launch_kron_solve(int n_groups, Topo T, KronWork W, double2 *big, double2 *Y, int K, cudaStream_t st);
 
 // okr_persist.cu

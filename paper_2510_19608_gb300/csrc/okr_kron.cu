@@ -364,6 +364,42 @@ __global__ void k_kron_diag(KronWork W, double2 *Y, int K) {
     }
 }
 
+// Radialization (Sec. V): in the tree, the buses of a reduced component and
+// its boundary span a sub-tree; a reduced bus is critical when it has degree
+// >= 3 in that sub-tree, i.e. when two or more of its children lead to the
+// boundary (a kept child, or a reduced child with a kept bus below it in the
+// component) -- its parent edge always leads to the boundary bus above the
+// component.  One CTA, deepest level first.  crit: [n] flags, caller order.
+__global__ void __launch_bounds__(1024) k_radial_critical(Topo T, const int *label, const uint8_t *kept_in, KronWork W,
+                                                          uint8_t *crit, int *count) {
+    const int n = T.n, tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_cnt;
+    if (tid == 0) s_cnt = 0;
+    for (int v = tid; v < n; v += nt) {
+        W.keptp[v] = kept_in ? (kept_in[T.orig[v]] != 0) : (label[v] == v);
+        W.fill[v] = 0;                              // reused: "a kept bus lies below, inside the component"
+    }
+    __syncthreads();
+    const int maxd = T.maxd[0];
+    for (int d = maxd; d >= 0; --d) {
+        for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+            const int v = T.level_bus[x];
+            int c2 = 0;
+            if (!W.keptp[v])
+                for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) {
+                    const int ch = T.child[c];
+                    if (W.keptp[ch] || W.fill[ch]) ++c2;
+                }
+            W.fill[v] = c2 > 0;
+            const int cr = (!W.keptp[v] && c2 >= 2) ? 1 : 0;
+            crit[T.orig[v]] = (uint8_t)cr;
+            if (cr) atomicAdd(&s_cnt, 1);
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *count = s_cnt;
+}
+
 cudaError_t launch_kron_solve(int n_groups, Topo T, KronWork W, double2 *big, double2 *Y, int K, cudaStream_t st) {
     const size_t smem = sizeof(double2) * ((size_t)kKronShared * kKronShared + kKronShared) + sizeof(int) * kKronShared;
     cudaError_t e = cudaFuncSetAttribute(k_kron_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

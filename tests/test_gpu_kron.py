@@ -129,3 +129,60 @@ def test_kron_needs_a_feeder():
         with pytest.raises(K.OkrError) as e:
             c.kron()
         assert e.value.status == 6
+
+
+# ----------------------------------------------------------------------------- Sec. V radialization
+def _bus_graph(Y, pn, tol=0.0):
+    bus = pn // 3
+    buses = np.unique(bus)
+    adj = {int(b): set() for b in buses}
+    rows, cols = np.nonzero(np.abs(Y) > tol)
+    for a, c in zip(rows, cols):
+        if bus[a] != bus[c]:
+            adj[int(bus[a])].add(int(bus[c]))
+    return buses, adj
+
+
+def _is_tree(buses, adj):
+    if sum(len(v) for v in adj.values()) // 2 != len(buses) - 1:
+        return False
+    seen, stack = {int(buses[0])}, [int(buses[0])]
+    while stack:
+        u = stack.pop()
+        for w in adj[u]:
+            if w not in seen:
+                seen.add(w)
+                stack.append(w)
+    return len(seen) == len(buses)
+
+
+@pytest.mark.parametrize("name,n", [("feeder40", None), ("feeder1000", None), ("feeder2200", 600)])
+def test_radialization_of_the_chosen_network(ctx, name, n):
+    import paper_2510_19608_gb300 as K
+    f, run = fg.preset(name, **({"n_bus": n} if n else {}))
+    ctx.reduce(f, K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1))
+    kept = (ctx.assignment() == np.arange(f.n_bus)).astype(np.uint8)
+    crit = ctx.radialize()
+    assert np.array_equal(crit, O.radialize(f, kept))
+    Yr, pr = ctx.kron(np.maximum(kept, crit))
+    assert _is_tree(*_bus_graph(Yr, pr))
+
+
+@pytest.mark.parametrize("frac", [0.2, 0.5, 0.8])
+def test_radialization_of_random_kept_sets(ctx, frac):
+    f, _ = fg.preset("feeder1000", n_bus=300)
+    ctx.power_flow(f)
+    kept = (np.random.default_rng(int(100 * frac)).random(f.n_bus) < frac).astype(np.uint8)
+    kept[0] = 1
+    crit = ctx.radialize(kept)
+    assert np.array_equal(crit, O.radialize(f, kept))
+    Yr, pr = ctx.kron(np.maximum(kept, crit))
+    assert _is_tree(*_bus_graph(Yr, pr))
+
+
+def test_radialization_of_a_hub(ctx):
+    f = _hub(5)
+    ctx.power_flow(f)
+    kept = np.ones(f.n_bus, np.uint8)
+    kept[1] = 0
+    assert list(ctx.radialize(kept)) == [0, 1] + [0] * 5
