@@ -232,6 +232,47 @@ okr_status okr_set_batch_config(okr_ctx *ctx, int32_t config);
  * *n_critical (may be NULL): their number.  Errors as okr_kron. */
 okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, int32_t *n_critical);
 
+/* ---- learned candidate scorer -----------------------------------------
+ * A small network (three hidden layers of 128 ReLU units; weights kept in
+ * FP32, used as bfloat16 in every product with FP32 accumulation) that
+ * predicts a candidate's score change from local features.  It is trained on
+ * the scores the exhaustive search itself produces (record_iters, precision 0)
+ * and is used to rank candidates; the exhaustive search remains the reference
+ * that measures how often the ranking misses the optimum.  It is an addition
+ * to the method, which has no learned part.
+ *
+ * Features of candidate (s, r), OKR_SCORER_FEATURES floats: log10 of the path
+ * impedance between r and the common ancestor a, same for s; log10 of the
+ * injections of r and of s (sum over scenarios and phases of |re| + |im|);
+ * phase counts of r and s / 3; current MICE of r and of s / margin; direction
+ * (1: the cluster above joins the one below); log10(1 + affected clusters);
+ * voltage spread (max hi - lo) of r and of s / margin. */
+#define OKR_SCORER_FEATURES 12
+
+/* Features of every candidate of recorded iteration `iter` of the last
+ * reduction (same order as okr_get_recorded).  features: HOST [cap][12]. */
+okr_status okr_get_recorded_features(const okr_ctx *ctx, int32_t iter, int32_t cap, float *features,
+                                     int32_t *count);
+
+/* (Re)creates the scorer for n_features (1..16) inputs with parameters theta
+ * (HOST, okr_scorer_params order; NULL = zeros) and clears the Adam state.
+ * Parameter order: W1 (n_features x 128, row-major), b1 (128), W2 (128 x 128),
+ * b2, W3 (128 x 128), b3, w4 (128), b4 (1). */
+okr_status okr_scorer_init(okr_ctx *ctx, int32_t n_features, const float *theta);
+/* Current parameters (theta may be NULL to query *n_params). */
+okr_status okr_scorer_params(okr_ctx *ctx, float *theta, int32_t *n_params);
+/* Gradient of the mean squared error (1/n) sum (y_i - t_i)^2 at the current
+ * parameters over n samples x (HOST [n][n_features]), t (HOST [n]); grad:
+ * HOST [n_params] (may be NULL); *loss (may be NULL). */
+okr_status okr_scorer_gradient(okr_ctx *ctx, const float *x, const float *t, int32_t n, float *grad, double *loss);
+/* Adam (lr, beta 0.9 / 0.999) over `epochs` passes of consecutive minibatches
+ * of `batch` samples (the caller shuffles); epoch_loss: HOST [epochs], the
+ * mean squared error over each pass (may be NULL). */
+okr_status okr_scorer_train(okr_ctx *ctx, const float *x, const float *t, int64_t n, int32_t batch, int32_t epochs,
+                            float lr, double *epoch_loss);
+/* Predictions y (HOST [n]) for x (HOST [n][n_features]). */
+okr_status okr_scorer_predict(okr_ctx *ctx, const float *x, int64_t n, float *y);
+
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096
 

@@ -63,7 +63,8 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
            "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
-           "okr_set_batch_config", "okr_radialize")
+           "okr_set_batch_config", "okr_radialize", "okr_get_recorded_features", "okr_scorer_init",
+           "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict")
 
 
 def lib_path() -> str:
@@ -98,6 +99,12 @@ def lib():
             L.okr_batch_autotune.argtypes = [P, I32, P, P, I32, P, P]
             L.okr_set_batch_config.argtypes = [P, I32]
             L.okr_radialize.argtypes = [P, P, P, P]
+            L.okr_get_recorded_features.argtypes = [P, I32, I32, P, P]
+            L.okr_scorer_init.argtypes = [P, I32, P]
+            L.okr_scorer_params.argtypes = [P, P, P]
+            L.okr_scorer_gradient.argtypes = [P, P, P, I32, P, P]
+            L.okr_scorer_train.argtypes = [P, P, P, C.c_int64, I32, I32, C.c_float, P]
+            L.okr_scorer_predict.argtypes = [P, P, C.c_int64, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -285,6 +292,47 @@ class Context:
         self._check(lib().okr_radialize(self._h, _ptr(kp) if kp is not None else None, _ptr(out), C.byref(cnt)))
         assert int(cnt.value) == int(out.sum())
         return out
+
+    # ---- learned scorer
+    def recorded_features(self, it: int) -> np.ndarray:
+        cnt = C.c_int32()
+        self._check(lib().okr_get_recorded_features(self._h, it, 0, None, C.byref(cnt)))
+        out = np.zeros((int(cnt.value), 12), np.float32)
+        self._check(lib().okr_get_recorded_features(self._h, it, out.shape[0], _ptr(out), C.byref(cnt)))
+        return out
+
+    def scorer_init(self, n_features: int, theta=None):
+        th = None if theta is None else np.ascontiguousarray(theta, dtype=np.float32)
+        self._check(lib().okr_scorer_init(self._h, int(n_features), _ptr(th) if th is not None else None))
+
+    def scorer_params(self) -> np.ndarray:
+        k = C.c_int32()
+        self._check(lib().okr_scorer_params(self._h, None, C.byref(k)))
+        out = np.zeros(int(k.value), np.float32)
+        self._check(lib().okr_scorer_params(self._h, _ptr(out), C.byref(k)))
+        return out
+
+    def scorer_gradient(self, x, t):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        g = np.zeros(self.scorer_params().size, np.float32)
+        loss = C.c_double()
+        self._check(lib().okr_scorer_gradient(self._h, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(g), C.byref(loss)))
+        return g, float(loss.value)
+
+    def scorer_train(self, x, t, batch: int, epochs: int, lr: float) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        el = np.zeros(max(epochs, 1))
+        self._check(lib().okr_scorer_train(self._h, _ptr(x), _ptr(t), int(x.shape[0]), int(batch), int(epochs),
+                                           float(lr), _ptr(el)))
+        return el[:epochs]
+
+    def scorer_predict(self, x) -> np.ndarray:
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros(x.shape[0], np.float32)
+        self._check(lib().okr_scorer_predict(self._h, _ptr(x), int(x.shape[0]), _ptr(y)))
+        return y
 
     def kron(self, kept=None):
         """Y_Kron onto `kept` (caller-order flags; None = the last reduction's

@@ -65,6 +65,14 @@ struct okr_ctx {
     size_t batch_host_cap = 0;
     int batch_config = 1;                   // team shape of the batched search: 2 CTAs per feeder (autotuned)
 
+    // learned scorer
+    MlpBufs mb;
+    MlpWork mw;
+    std::vector<void *> mlp_allocs, mlp_work_allocs, mlp_data_allocs;
+    float *mlp_x = nullptr, *mlp_t = nullptr;    // device copies of a data set
+    long long mlp_data_cap = 0;
+    int mlp_step = 0;
+
     // last result
     bool have_topo = false;     // T describes the feeder of the last call
     bool have_result = false;
@@ -109,6 +117,21 @@ void free_batch(okr_ctx *ctx) {
     if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
     ctx->batch_host = nullptr;
     ctx->batch_host_cap = 0;
+}
+
+void free_list(std::vector<void *> &v) {
+    for (void *p : v) cudaFree(p);
+    v.clear();
+}
+
+void free_mlp(okr_ctx *ctx) {
+    free_list(ctx->mlp_allocs);
+    free_list(ctx->mlp_work_allocs);
+    free_list(ctx->mlp_data_allocs);
+    ctx->mb = MlpBufs{};
+    ctx->mw = MlpWork{};
+    ctx->mlp_data_cap = 0;
+    ctx->mlp_x = ctx->mlp_t = nullptr;
 }
 
 void free_all(okr_ctx *ctx) {
@@ -540,6 +563,7 @@ okr_status okr_destroy(okr_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream);
     free_all(ctx);
     free_batch(ctx);
+    free_mlp(ctx);
     if (ctx->C_host) cudaFreeHost(ctx->C_host);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1133,6 +1157,22 @@ okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred) {
     return OKR_OK;
 }
 
+okr_status okr_get_recorded_features(const okr_ctx *ctx, int32_t iter, int32_t cap, float *features, int32_t *count) {
+    if (!ctx || !count || cap < 0) return OKR_EINVAL;
+    if (!ctx->have_result) return OKR_ENOTREADY;
+    if (iter < 0 || iter >= ctx->rec_iters) return OKR_EINVAL;
+    int c = 0;
+    if (cudaMemcpy(&c, ctx->fb.X.rec_count + iter, sizeof c, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    *count = c;
+    const int k = c < cap ? c : cap;
+    const size_t off = (size_t)iter * 2 * ctx->n * kScorerFeatures;
+    if (k > 0 && features &&
+        cudaMemcpy(features, ctx->fb.X.rec_feat + off, sizeof(float) * k * kScorerFeatures, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+        return OKR_ECUDA;
+    return OKR_OK;
+}
+
 okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32_t *s, int32_t *r, double *smice,
                             double *bound, int32_t *count) {
     if (!ctx || !count || cap < 0) return OKR_EINVAL;
@@ -1149,6 +1189,165 @@ okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32
         if (smice && cudaMemcpy(smice, ctx->fb.X.rec_score + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
         if (bound && cudaMemcpy(bound, ctx->fb.X.rec_bound + off, sizeof(double) * k, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     }
+    return OKR_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- learned scorer
+namespace {
+
+template <typename T>
+cudaError_t grab(std::vector<void *> &list, T **p, size_t count) {
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    if (e == cudaSuccess) { list.push_back(q); *p = static_cast<T *>(q); }
+    return e;
+}
+
+okr_status mlp_ensure_work(okr_ctx *ctx, int N) {
+    if (N <= ctx->mw.cap) return OKR_OK;
+    free_list(ctx->mlp_work_allocs);
+    ctx->mw = MlpWork{};
+    MlpWork &w = ctx->mw;
+    const size_t NH = (size_t)N * kMlpHidden;
+    CK(grab(ctx->mlp_work_allocs, &w.h1, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.h2, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.h3, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.d1, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.d2, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.d3, NH));
+    CK(grab(ctx->mlp_work_allocs, &w.y, (size_t)N));
+    CK(grab(ctx->mlp_work_allocs, &w.dy, (size_t)N));
+    CK(grab(ctx->mlp_work_allocs, &w.part, (size_t)mlp_segments(N) * (kMlpHidden + 1) * kMlpHidden));
+    w.cap = N;
+    return OKR_OK;
+}
+
+okr_status mlp_upload(okr_ctx *ctx, const float *x, const float *t, long long N) {
+    const int F = ctx->mb.F;
+    if (N > ctx->mlp_data_cap) {
+        free_list(ctx->mlp_data_allocs);
+        ctx->mlp_data_cap = 0;
+        CK(grab(ctx->mlp_data_allocs, &ctx->mlp_x, (size_t)N * F));
+        CK(grab(ctx->mlp_data_allocs, &ctx->mlp_t, (size_t)N));
+        ctx->mlp_data_cap = N;
+    }
+    CK(cudaMemcpyAsync(ctx->mlp_x, x, sizeof(float) * (size_t)N * F, cudaMemcpyHostToDevice, ctx->stream));
+    if (t) CK(cudaMemcpyAsync(ctx->mlp_t, t, sizeof(float) * (size_t)N, cudaMemcpyHostToDevice, ctx->stream));
+    return OKR_OK;
+}
+
+okr_status mlp_batch_loss(okr_ctx *ctx, const float *y, const float *t, int N, double *sum) {
+    const int nseg = mlp_segments(N);
+    CK(mlp_sqerr(y, t, N, ctx->mw.part, ctx->stream));
+    std::vector<float> part(nseg);
+    CK(cudaMemcpyAsync(part.data(), ctx->mw.part, sizeof(float) * nseg, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double acc = 0.0;
+    for (float v : part) acc += v;
+    *sum = acc;
+    return OKR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+okr_status okr_scorer_init(okr_ctx *ctx, int32_t n_features, const float *theta) {
+    if (!ctx) return OKR_EINVAL;
+    if (n_features < 1 || n_features > kMlpMaxF) return fail(ctx, OKR_EINVAL, "n_features %d outside [1, %d]", n_features, kMlpMaxF);
+    CK(cudaSetDevice(ctx->device));
+    free_mlp(ctx);
+    MlpBufs &b = ctx->mb;
+    b.F = n_features;
+    const int P = mlp_param_count(n_features);
+    CK(grab(ctx->mlp_allocs, &b.theta, (size_t)P));
+    CK(grab(ctx->mlp_allocs, &b.grad, (size_t)P));
+    CK(grab(ctx->mlp_allocs, &b.m, (size_t)P));
+    CK(grab(ctx->mlp_allocs, &b.v, (size_t)P));
+    CK(grab(ctx->mlp_allocs, &b.w1, (size_t)kMlpMaxF * kMlpHidden));
+    CK(grab(ctx->mlp_allocs, &b.w2, (size_t)kMlpHidden * kMlpHidden));
+    CK(grab(ctx->mlp_allocs, &b.w3, (size_t)kMlpHidden * kMlpHidden));
+    CK(grab(ctx->mlp_allocs, &b.w4, (size_t)kMlpHidden));
+    cudaStream_t st = ctx->stream;
+    if (theta) CK(cudaMemcpyAsync(b.theta, theta, sizeof(float) * P, cudaMemcpyHostToDevice, st));
+    else CK(cudaMemsetAsync(b.theta, 0, sizeof(float) * P, st));
+    CK(cudaMemsetAsync(b.m, 0, sizeof(float) * P, st));
+    CK(cudaMemsetAsync(b.v, 0, sizeof(float) * P, st));
+    CK(cudaMemsetAsync(b.grad, 0, sizeof(float) * P, st));
+    CK(mlp_sync_bf16(b, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->mlp_step = 0;
+    return OKR_OK;
+}
+
+okr_status okr_scorer_params(okr_ctx *ctx, float *theta, int32_t *n_params) {
+    if (!ctx || !n_params) return OKR_EINVAL;
+    if (!ctx->mb.theta) return fail(ctx, OKR_ENOTREADY, "scorer not initialised");
+    const int P = mlp_param_count(ctx->mb.F);
+    *n_params = P;
+    if (theta) CK(cudaMemcpy(theta, ctx->mb.theta, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    return OKR_OK;
+}
+
+okr_status okr_scorer_gradient(okr_ctx *ctx, const float *x, const float *t, int32_t n, float *grad, double *loss) {
+    if (!ctx || !x || !t || n < 1) return OKR_EINVAL;
+    if (!ctx->mb.theta) return fail(ctx, OKR_ENOTREADY, "scorer not initialised");
+    CK(cudaSetDevice(ctx->device));
+    okr_status s = mlp_ensure_work(ctx, n);
+    if (s == OKR_OK) s = mlp_upload(ctx, x, t, n);
+    if (s != OKR_OK) return s;
+    CK(mlp_gradient(ctx->mb, ctx->mw, ctx->mlp_x, ctx->mlp_t, n, ctx->num_sms, ctx->stream));
+    double sum = 0.0;
+    s = mlp_batch_loss(ctx, ctx->mw.y, ctx->mlp_t, n, &sum);
+    if (s != OKR_OK) return s;
+    if (loss) *loss = sum / n;
+    const int P = mlp_param_count(ctx->mb.F);
+    if (grad) CK(cudaMemcpy(grad, ctx->mb.grad, sizeof(float) * P, cudaMemcpyDeviceToHost));
+    return OKR_OK;
+}
+
+okr_status okr_scorer_train(okr_ctx *ctx, const float *x, const float *t, int64_t n, int32_t batch, int32_t epochs,
+                            float lr, double *epoch_loss) {
+    if (!ctx || !x || !t || n < 1 || batch < 1 || epochs < 0 || !(lr > 0.0f)) return OKR_EINVAL;
+    if (!ctx->mb.theta) return fail(ctx, OKR_ENOTREADY, "scorer not initialised");
+    CK(cudaSetDevice(ctx->device));
+    const int B = (int)std::min<int64_t>(batch, n);
+    okr_status s = mlp_ensure_work(ctx, B);
+    if (s == OKR_OK) s = mlp_upload(ctx, x, t, n);
+    if (s != OKR_OK) return s;
+    const int F = ctx->mb.F;
+    for (int e = 0; e < epochs; ++e) {
+        double sum = 0.0;
+        for (int64_t b0 = 0; b0 < n; b0 += B) {
+            const int nb = (int)std::min<int64_t>(B, n - b0);
+            const float *xb = ctx->mlp_x + (size_t)b0 * F;
+            const float *tb = ctx->mlp_t + b0;
+            CK(mlp_gradient(ctx->mb, ctx->mw, xb, tb, nb, ctx->num_sms, ctx->stream));
+            double bs = 0.0;
+            s = mlp_batch_loss(ctx, ctx->mw.y, tb, nb, &bs);
+            if (s != OKR_OK) return s;
+            sum += bs;
+            CK(mlp_adam(ctx->mb, lr, ++ctx->mlp_step, ctx->stream));
+        }
+        if (epoch_loss) epoch_loss[e] = sum / (double)n;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return OKR_OK;
+}
+
+okr_status okr_scorer_predict(okr_ctx *ctx, const float *x, int64_t n, float *y) {
+    if (!ctx || !x || !y || n < 1) return OKR_EINVAL;
+    if (!ctx->mb.theta) return fail(ctx, OKR_ENOTREADY, "scorer not initialised");
+    if (n > INT32_MAX) return fail(ctx, OKR_EINVAL, "too many samples");
+    CK(cudaSetDevice(ctx->device));
+    okr_status s = mlp_upload(ctx, x, nullptr, n);
+    if (s != OKR_OK) return s;
+    float *yd = ctx->mlp_t;                     // the targets' buffer holds the predictions
+    CK(mlp_forward(ctx->mb, ctx->mlp_x, (int)n, nullptr, nullptr, nullptr, yd, ctx->num_sms, ctx->stream));
+    CK(cudaMemcpyAsync(y, yd, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     return OKR_OK;
 }
 

@@ -18,6 +18,7 @@ namespace okr {
 constexpr int kChunk = 32;          // candidate positions per warp work item
 constexpr int kMaxScen = 4;         // scenarios held in registers by the sweep
 constexpr int kMaxBus = 32768;      // LCA table uses 16-bit entries
+constexpr int kScorerFeatures = 12; // features of one candidate for the learned scorer
 
 // ---------------------------------------------------------------- complex helpers
 __host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
@@ -153,6 +154,7 @@ struct Search {
     int *rec_s, *rec_r;     // [rec_iters][2n]
     double *rec_score;
     double *rec_bound;      // [rec_iters][2n] bound of the recorded score (0 for FP64)
+    float *rec_feat;        // [rec_iters][2n][kScorerFeatures] scorer features of the recorded candidates
     int *rec_count;
 };
 

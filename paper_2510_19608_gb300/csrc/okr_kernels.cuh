@@ -3,6 +3,8 @@
 
 #include "okr_internal.cuh"
 
+#include <cuda_bf16.h>
+
 namespace okr {
 
 // okr_setup.cu
@@ -73,6 +75,30 @@ __global__ void k_kron_diag(KronWork W, double2 *Y, int K);
 __global__ void __launch_bounds__(1024) k_radial_critical(Topo T, const int *label, const uint8_t *kept_in, KronWork W,
                                                           uint8_t *crit, int *count);
 cudaError_t launch_kron_solve(int n_groups, Topo T, KronWork W, double2 *big, double2 *Y, int K, cudaStream_t st);
+
+// okr_mlp.cu -- the learned candidate scorer
+constexpr int kMlpHidden = 128;     // units per hidden layer
+constexpr int kMlpMaxF = 16;        // longest feature vector
+struct MlpBufs {
+    int F = 0;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;   // FP32 [P]
+    __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w3 = nullptr, *w4 = nullptr;  // bf16 copies
+};
+struct MlpWork {
+    int cap = 0;                    // samples the buffers hold
+    float *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *d1 = nullptr, *d2 = nullptr, *d3 = nullptr;  // [cap][H]
+    float *y = nullptr, *dy = nullptr;                                   // [cap]
+    float *part = nullptr;                                               // [segments][(H+1) x H]
+};
+int mlp_param_count(int F);
+int mlp_segments(int N);
+cudaError_t mlp_sync_bf16(const MlpBufs &b, cudaStream_t st);
+cudaError_t mlp_forward(const MlpBufs &b, const float *x, int N, float *h1, float *h2, float *h3, float *y, int num_sms,
+                        cudaStream_t st);
+cudaError_t mlp_gradient(const MlpBufs &b, const MlpWork &w, const float *x, const float *t, int N, int num_sms,
+                         cudaStream_t st);
+cudaError_t mlp_adam(const MlpBufs &b, float lr, int step, cudaStream_t st);
+cudaError_t mlp_sqerr(const float *y, const float *t, int N, float *part, cudaStream_t st);
 
 // okr_persist.cu
 // One feeder of a batched search launch.

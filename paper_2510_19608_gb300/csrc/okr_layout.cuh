@@ -147,6 +147,7 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(X.rec_score, R * 2 * N);
     c.take(X.rec_bound, R * 2 * N);
     c.take(X.rec_count, R);
+    c.take(X.rec_feat, R * 2 * N * kScorerFeatures);
     c.take(f.C, 1);
     if (chunks > 0) {
         c.take(X.chunk_first, (size_t)chunks);

@@ -744,6 +744,56 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     return out;
 }
 
+// ---------------------------------------------------------------- scorer features
+// Local features of candidate (s, r) on the current state, for the learned
+// scorer: how far r's injection moves (path impedance between r and the
+// common ancestor, and between s and it), how much is moved (injections of r
+// and s), phase counts, the current MICE and voltage spread of both clusters
+// relative to the margin, the direction and the number of affected clusters.
+__device__ void cand_features(const Topo &T, const State &S, int n, int L, const Cand &c, double margin, float *f) {
+    auto zdist = [&](int u) {
+        double acc = 0.0;
+        for (int q = 0; q < 9; ++q) {
+            const double2 d = csub(ldz(T.zc + (size_t)u * 9 + q), ldz(T.zc + (size_t)c.a * 9 + q));
+            acc += fabs(d.x) + fabs(d.y);
+        }
+        return acc;
+    };
+    auto inj = [&](int u) {
+        double acc = 0.0;
+        for (int l = 0; l < L; ++l)
+            for (int p = 0; p < 3; ++p) {
+                const double2 i = ldz(S.icur + sidx(l, p, u, n));
+                acc += fabs(i.x) + fabs(i.y);
+            }
+        return acc;
+    };
+    auto mice = [&](int u) {
+        double m = 0.0;
+        for (int l = 0; l < L; ++l) m = fmax(m, ldd(S.mice + (size_t)l * n + u));
+        return m;
+    };
+    auto spread = [&](int u) {
+        double m = 0.0;
+        for (int l = 0; l < L; ++l)
+            for (int p = 0; p < 3; ++p)
+                if (T.ph[u] >> p & 1u) m = fmax(m, ldd(S.hi + sidx(l, p, u, n)) - ldd(S.lo + sidx(l, p, u, n)));
+        return m;
+    };
+    f[0] = (float)log10(1e-9 + zdist(c.r));
+    f[1] = (float)log10(1e-9 + zdist(c.s));
+    f[2] = (float)log10(1e-9 + inj(c.r));
+    f[3] = (float)log10(1e-9 + inj(c.s));
+    f[4] = (float)__popc(T.ph[c.r]) / 3.0f;
+    f[5] = (float)__popc(T.ph[c.s]) / 3.0f;
+    f[6] = (float)(mice(c.r) / margin);
+    f[7] = (float)(mice(c.s) / margin);
+    f[8] = (float)c.dir;
+    f[9] = (float)log10(1.0 + c.ns + c.nr);
+    f[10] = (float)(spread(c.r) / margin);
+    f[11] = (float)(spread(c.s) / margin);
+}
+
 // ---------------------------------------------------------------- the kernel
 // One feeder's search on a team of G CTAs (rank = this CTA's index in the team).
 template <int PREC>
@@ -805,6 +855,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
                         X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : s_cur + (double)q.x;
                         X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
+                        cand_features(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
                     }
                 }
                 if (!sc.any) {
@@ -884,6 +935,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         X.rec_score[(size_t)t * 2 * n + c] =
                             ldi(X.feas + c) ? (obj1 ? 0.0 : s_cur) + ldd(X.score + c) : INFINITY;
                         X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
+                        cand_features(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
                     }
                 }
                 sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);

@@ -1,0 +1,107 @@
+"""Training data and evaluation for the learned candidate scorer.
+
+The network, its training (forward, backward, Adam) and its inference run in
+libokron.so (okr_scorer_*); this module only gathers data through the C ABI,
+shapes the targets and counts how often the ranking misses the optimum.
+
+Data: an exhaustive search with ``record_iters`` (precision 0) keeps, for its
+first iterations, every candidate's exact score and features.  The target of a
+candidate is its distance to that iteration's best score, in units of the
+margin, on a log scale: ``log10(1e-6 + (score - best) / margin)``, clipped to
+[-6, 2]; infeasible candidates get 2.  Ranking candidates by the prediction
+then puts the likely optimum first.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import _binding as B
+
+T_LO, T_HI = -6.0, 2.0
+
+
+def targets(scores: np.ndarray, margin: float) -> np.ndarray:
+    s = np.asarray(scores, np.float64)
+    feas = np.isfinite(s)
+    out = np.full(s.shape, T_HI, np.float64)
+    if feas.any():
+        best = s[feas].min()
+        out[feas] = np.clip(np.log10(1e-6 + (s[feas] - best) / margin), T_LO, T_HI)
+    return out.astype(np.float32)
+
+
+def winner(s_ids: np.ndarray, r_ids: np.ndarray, scores: np.ndarray, tau: float = 1e-9) -> int:
+    """Index of the candidate Algorithm 1 commits: the smallest (r, s) inside the
+    tie band [m, m + tau] of the feasible scores (-1 if none is feasible)."""
+    feas = np.isfinite(scores)
+    if not feas.any():
+        return -1
+    m = scores[feas].min()
+    band = np.nonzero(feas & (scores <= m + tau))[0]
+    return int(min(band, key=lambda i: (int(r_ids[i]), int(s_ids[i]))))
+
+
+def collect(ctx: "B.Context", runs, record_iters: int):
+    """Run each (feeder, params) with recording and return (X, T, groups): the
+    features, targets and, per recorded iteration, (start, stop, winner) rows."""
+    xs, ts, groups = [], [], []
+    o = 0
+    for f, p in runs:
+        q = B.default_params(margin=p.margin, target_reduction=p.target_reduction, max_merges=p.max_merges,
+                             tie_tol=p.tie_tol, precision=0, record_iters=record_iters)
+        ctx.reduce(f, q)
+        n_it = min(record_iters, ctx.summary()["n_iter"])
+        for it in range(n_it):
+            rec = ctx.recorded(it)
+            feat = ctx.recorded_features(it)
+            k = feat.shape[0]
+            xs.append(feat)
+            ts.append(targets(rec["score"], p.margin))
+            groups.append((o, o + k, winner(rec["s"], rec["r"], rec["score"], p.tie_tol)))
+            o += k
+    X = np.concatenate(xs) if xs else np.zeros((0, 12), np.float32)
+    T = np.concatenate(ts) if ts else np.zeros(0, np.float32)
+    return X, T, groups
+
+
+def init_params(n_features: int, seed: int) -> np.ndarray:
+    """He-normal weights, zero biases, in the okr_scorer_params order."""
+    rng = np.random.default_rng(seed)
+    H = 128
+    parts = [rng.normal(0.0, math.sqrt(2.0 / n_features), (n_features, H)), np.zeros(H),
+             rng.normal(0.0, math.sqrt(2.0 / H), (H, H)), np.zeros(H),
+             rng.normal(0.0, math.sqrt(2.0 / H), (H, H)), np.zeros(H),
+             rng.normal(0.0, math.sqrt(1.0 / H), H), np.zeros(1)]
+    return np.concatenate([a.ravel() for a in parts]).astype(np.float32)
+
+
+def train(ctx: "B.Context", X: np.ndarray, T: np.ndarray, *, epochs: int = 20, batch: int = 4096, lr: float = 1e-3,
+          seed: int = 0) -> np.ndarray:
+    """Initialise and train the scorer on the GPU; returns the loss per epoch."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(X.shape[0])
+    ctx.scorer_init(X.shape[1], init_params(X.shape[1], seed))
+    return ctx.scorer_train(X[perm], T[perm], batch=batch, epochs=epochs, lr=lr)
+
+
+def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256)) -> dict:
+    """For each recorded iteration with a feasible candidate, whether the
+    committed candidate is among the top-k predictions, for each k; also the
+    mean fraction of candidates a top-k evaluation would score."""
+    pred = ctx.scorer_predict(X) if X.shape[0] else np.zeros(0, np.float32)
+    out = {}
+    rows = [(a, b, w) for a, b, w in groups if w >= 0]
+    for k in ks:
+        miss, frac = 0, 0.0
+        for a, b, w in rows:
+            order = np.argsort(pred[a:b], kind="stable")
+            if w not in set(order[:k].tolist()):
+                miss += 1
+            frac += min(k, b - a) / (b - a)
+        out[k] = {"miss_rate": miss / max(1, len(rows)), "evaluated_fraction": frac / max(1, len(rows)),
+                  "iterations": len(rows)}
+    pct = [float(np.searchsorted(np.sort(pred[a:b]), pred[a + w], side="left")) / (b - a) for a, b, w in rows]
+    out["winner_rank_percentile"] = float(np.mean(pct)) if pct else float("nan")
+    return out

@@ -1,0 +1,102 @@
+"""The learned candidate scorer through the C ABI: forward and gradient of
+the CUDA kernels against the FP64 CPU oracle (oracle/mlp.py, evaluated at the
+same bfloat16-rounded weights the kernels use), training, recorded features,
+and the ranking it learns from exhaustive-search scores."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import feedergen as fg
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+F = 12
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import build
+    build.build()
+    c = K.Context(0)
+    yield c
+    c.close()
+
+
+def _bf16_weights(theta, F):
+    """The kernels multiply with bfloat16 copies of the weight matrices (biases stay FP32)."""
+    th = theta.astype(np.float32).copy()
+    W1, b1, W2, b2, W3, b3, w4, b4 = M.unpack(th, F)
+    for a in (W1, W2, W3, w4):
+        a[...] = M.bf16_round(a)
+    return th.astype(np.float64)
+
+
+def _problem(seed, N):
+    from paper_2510_19608_gb300 import scorer
+    rng = np.random.default_rng(seed)
+    theta = scorer.init_params(F, seed)
+    x = rng.normal(0.0, 1.0, (N, F)).astype(np.float32)
+    t = rng.normal(0.0, 1.0, N).astype(np.float32)
+    return theta, x, t
+
+
+def test_forward_matches_oracle(ctx):
+    theta, x, _ = _problem(1, 257)
+    ctx.scorer_init(F, theta)
+    y = ctx.scorer_predict(x)
+    y_ref, _ = M.forward(_bf16_weights(theta, F), x.astype(np.float64))
+    assert np.abs(y - y_ref).max() <= 1e-4 * max(1.0, np.abs(y_ref).max())
+
+
+@pytest.mark.parametrize("N", [1, 33, 4100])
+def test_gradient_matches_oracle(ctx, N):
+    theta, x, t = _problem(2 + N, N)
+    ctx.scorer_init(F, theta)
+    g, loss = ctx.scorer_gradient(x, t)
+    th = _bf16_weights(theta, F)
+    g_ref = M.grad(th, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - M.loss(th, x.astype(np.float64), t.astype(np.float64))) <= 1e-4 * max(1.0, loss)
+    assert np.abs(g - g_ref).max() <= 2e-4 * max(1e-3, np.abs(g_ref).max())
+
+
+def test_training_fits_a_smooth_function(ctx):
+    from paper_2510_19608_gb300 import scorer
+    rng = np.random.default_rng(5)
+    x = rng.uniform(-1.0, 1.0, (20000, F)).astype(np.float32)
+    t = (np.sin(2 * x[:, 0]) + x[:, 1] * x[:, 2] + 0.5 * np.abs(x[:, 3])).astype(np.float32)
+    loss = scorer.train(ctx, x, t, epochs=15, batch=1024, lr=2e-3, seed=5)
+    assert loss[-1] < 0.05 * np.var(t) and loss[-1] < loss[0]
+    y = ctx.scorer_predict(x[:2000])
+    assert np.mean((y - t[:2000]) ** 2) < 0.05 * np.var(t)
+
+
+def test_recorded_features(ctx):
+    import paper_2510_19608_gb300 as K
+    f, run = fg.preset("feeder40")
+    ctx.reduce(f, K.default_params(margin=run["margin"], precision=0, record_iters=3))
+    for it in range(3):
+        rec = ctx.recorded(it)
+        feat = ctx.recorded_features(it)
+        assert feat.shape == (rec["s"].size, 12) and np.isfinite(feat).all()
+        pc = np.array([bin(int(v)).count("1") for v in f.phases]) / 3.0
+        assert np.allclose(feat[:, 4], pc[rec["r"]]) and np.allclose(feat[:, 5], pc[rec["s"]])
+        assert set(np.unique(feat[:, 8])) <= {0.0, 1.0}
+        if it == 0:
+            assert np.all(feat[:, 6] == 0) and np.all(feat[:, 7] == 0)      # every MICE starts at 0
+
+
+def test_learned_ranking_beats_chance_on_held_out_feeders(ctx):
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import scorer
+    train_runs = [(fg.make_feeder(300, 10000 + k, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0)),
+                   K.default_params(margin=0.005, target_reduction=0.5)) for k in range(4)]
+    test_runs = [(fg.make_feeder(300, 20000, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0)),
+                  K.default_params(margin=0.005, target_reduction=0.5))]
+    X, T, _ = scorer.collect(ctx, train_runs, record_iters=40)
+    scorer.train(ctx, X, T, epochs=10, batch=2048, lr=1e-3, seed=0)
+    Xt, _, groups = scorer.collect(ctx, test_runs, record_iters=40)
+    q = scorer.miss_rate(ctx, Xt, groups, ks=(64,))
+    assert q["winner_rank_percentile"] < 0.25               # chance: 0.5
