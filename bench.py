@@ -56,6 +56,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-feeder batch measurement")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-scorer training and evaluation")
     return ap.parse_args()
 
 
@@ -204,6 +205,42 @@ def batch_line(K, ctx, reps=3):
     return out
 
 
+def learned_line(K, ctx, n_train=64, record=64):
+    """Learned scorer: trained on the GPU on the exhaustive-search scores of the
+    first `record` iterations of 64 seeded feeders (500-2,000 buses, the
+    45/15/40 % phase mix, lognormal loads), then ranked against the exhaustive
+    search on the first iterations of the 3,100-bus stand-in: how often the
+    committed candidate falls outside the top-k predictions."""
+    import numpy as np
+    import feedergen as fg
+    from paper_2510_19608_gb300 import scorer
+    runs = []
+    for k in range(n_train):
+        n = int(np.random.default_rng(10000 + k).integers(500, 2001))
+        f = fg.make_feeder(n, 10000 + k, phase_mode=(0.45, 0.15, 0.4), load=("lognormal", 15.0, 1.0),
+                           pf_range=(0.85, 0.99))
+        runs.append((f, K.default_params(margin=0.005, target_reduction=0.8, max_merges=record)))
+    t0 = time.perf_counter()
+    X, T, _ = scorer.collect(ctx, runs, record)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    loss = scorer.train(ctx, X, T, epochs=8, batch=8192, lr=1e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    f3, run3 = fg.preset("feeder3100")
+    Xt, Tt, groups = scorer.collect(ctx, [(f3, K.default_params(margin=run3["margin"], target_reduction=run3["target"],
+                                                                max_merges=record))], record)
+    t0 = time.perf_counter()
+    q = scorer.miss_rate(ctx, Xt, groups, ks=(16, 64, 256), T=Tt, margin=run3["margin"])
+    t_eval = time.perf_counter() - t0
+    return {"train_feeders": n_train, "iterations_per_feeder": record, "samples": int(X.shape[0]),
+            "epochs": len(loss), "loss_first_last": [float(loss[0]), float(loss[-1])],
+            "collect_s": t_collect, "train_s": t_train, "train_samples_per_s": len(loss) * X.shape[0] / t_train,
+            "eval": {"workload": "feeder3100, first %d iterations" % record, "candidates": int(Xt.shape[0]),
+                     "predict_and_rank_s": t_eval,
+                     "top_k": {str(k): v for k, v in q.items() if isinstance(k, int)},
+                     "winner_rank_percentile": q["winner_rank_percentile"]}}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -321,6 +358,7 @@ def run_ours(args, rank, world, local):
                 "share_of_step": search_ms / (ms / args.steps)}
 
     batch = batch_line(K, ctx) if not args.no_batch else None
+    learned = learned_line(K, ctx) if not args.no_learned else None
     if rank == 0:
         cb = cpu_baseline(f, run) if world == 1 else None
         line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
@@ -334,7 +372,7 @@ def run_ours(args, rank, world, local):
                     "parallelism": f"replicas x{world}", "time_to_optimal_ms": ms / args.steps,
                     "candidates_per_step": cand_per_step, "merges": summ["n_iter"],
                     "stop_reason": summ["stop_reason"], "wall_s": t_wall, "y_kron": kron,
-                    "batch": batch},
+                    "batch": batch, "learned_scorer": learned},
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline}
         if cb:

@@ -246,8 +246,10 @@ okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, i
  * injections of r and of s (sum over scenarios and phases of |re| + |im|);
  * phase counts of r and s / 3; current MICE of r and of s / margin; direction
  * (1: the cluster above joins the one below); log10(1 + affected clusters);
- * voltage spread (max hi - lo) of r and of s / margin. */
-#define OKR_SCORER_FEATURES 12
+ * voltage spread (max hi - lo) of r and of s / margin; the merged cluster's
+ * error at s's present voltage magnitude / margin, and that error less the
+ * MICE of r and s / margin. */
+#define OKR_SCORER_FEATURES 14
 
 /* Features of every candidate of recorded iteration `iter` of the last
  * reduction (same order as okr_get_recorded).  features: HOST [cap][12]. */

@@ -297,7 +297,7 @@ class Context:
     def recorded_features(self, it: int) -> np.ndarray:
         cnt = C.c_int32()
         self._check(lib().okr_get_recorded_features(self._h, it, 0, None, C.byref(cnt)))
-        out = np.zeros((int(cnt.value), 12), np.float32)
+        out = np.zeros((int(cnt.value), 14), np.float32)
         self._check(lib().okr_get_recorded_features(self._h, it, out.shape[0], _ptr(out), C.byref(cnt)))
         return out
 

@@ -18,7 +18,7 @@ namespace okr {
 constexpr int kChunk = 32;          // candidate positions per warp work item
 constexpr int kMaxScen = 4;         // scenarios held in registers by the sweep
 constexpr int kMaxBus = 32768;      // LCA table uses 16-bit entries
-constexpr int kScorerFeatures = 12; // features of one candidate for the learned scorer
+constexpr int kScorerFeatures = 14; // features of one candidate for the learned scorer
 
 // ---------------------------------------------------------------- complex helpers
 __host__ __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }

@@ -792,6 +792,19 @@ __device__ void cand_features(const Topo &T, const State &S, int n, int L, const
     f[9] = (float)log10(1.0 + c.ns + c.nr);
     f[10] = (float)(spread(c.r) / margin);
     f[11] = (float)(spread(c.s) / margin);
+    // the merged cluster's error before any voltage moves: r's members (and
+    // s's) measured against s's present voltage magnitude
+    double em = 0.0;
+    for (int l = 0; l < L; ++l)
+        for (int p = 0; p < 3; ++p) {
+            if (!(T.ph[c.s] >> p & 1u)) continue;
+            const double ms = ldd(S.mcur + sidx(l, p, c.s, n));
+            em = fmax(em, fmax(ldd(S.hi + sidx(l, p, c.s, n)) - ms, ms - ldd(S.lo + sidx(l, p, c.s, n))));
+            if (T.ph[c.r] >> p & 1u)
+                em = fmax(em, fmax(ldd(S.hi + sidx(l, p, c.r, n)) - ms, ms - ldd(S.lo + sidx(l, p, c.r, n))));
+        }
+    f[12] = (float)(em / margin);
+    f[13] = (float)((em - mice(c.r) - mice(c.s)) / margin);
 }
 
 // ---------------------------------------------------------------- the kernel

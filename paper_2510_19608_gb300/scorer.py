@@ -61,7 +61,7 @@ def collect(ctx: "B.Context", runs, record_iters: int):
             ts.append(targets(rec["score"], p.margin))
             groups.append((o, o + k, winner(rec["s"], rec["r"], rec["score"], p.tie_tol)))
             o += k
-    X = np.concatenate(xs) if xs else np.zeros((0, 12), np.float32)
+    X = np.concatenate(xs) if xs else np.zeros((0, 14), np.float32)
     T = np.concatenate(ts) if ts else np.zeros(0, np.float32)
     return X, T, groups
 
@@ -86,22 +86,38 @@ def train(ctx: "B.Context", X: np.ndarray, T: np.ndarray, *, epochs: int = 20, b
     return ctx.scorer_train(X[perm], T[perm], batch=batch, epochs=epochs, lr=lr)
 
 
-def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256)) -> dict:
-    """For each recorded iteration with a feasible candidate, whether the
-    committed candidate is among the top-k predictions, for each k; also the
-    mean fraction of candidates a top-k evaluation would score."""
+def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256), T=None, margin=0.005,
+              tau=1e-9) -> dict:
+    """For each recorded iteration with a feasible candidate and each k: whether
+    the committed candidate is among the top-k predictions (miss_rate); with the
+    targets T, also whether the top-k holds any candidate of optimal score
+    (optimum_missed: none within the tie band) and the regret, the best exact
+    score among the top-k above the optimum, in margins; and the mean fraction
+    of candidates a top-k evaluation would score."""
     pred = ctx.scorer_predict(X) if X.shape[0] else np.zeros(0, np.float32)
     out = {}
     rows = [(a, b, w) for a, b, w in groups if w >= 0]
+    band = math.log10(1e-6 + tau / margin)
     for k in ks:
-        miss, frac = 0, 0.0
+        miss, opt_miss, frac, regrets = 0, 0, 0.0, []
         for a, b, w in rows:
             order = np.argsort(pred[a:b], kind="stable")
-            if w not in set(order[:k].tolist()):
+            top = order[:k]
+            if w not in set(top.tolist()):
                 miss += 1
+            if T is not None:
+                tbest = float(T[a:b][top].min())
+                if tbest > band + 1e-6:
+                    opt_miss += 1
+                regrets.append(max(0.0, 10.0 ** tbest - 1e-6))
             frac += min(k, b - a) / (b - a)
-        out[k] = {"miss_rate": miss / max(1, len(rows)), "evaluated_fraction": frac / max(1, len(rows)),
-                  "iterations": len(rows)}
+        d = {"miss_rate": miss / max(1, len(rows)), "evaluated_fraction": frac / max(1, len(rows)),
+             "iterations": len(rows)}
+        if T is not None:
+            d["optimum_missed"] = opt_miss / max(1, len(rows))
+            d["regret_margins_median"] = float(np.median(regrets)) if regrets else 0.0
+            d["regret_margins_max"] = float(np.max(regrets)) if regrets else 0.0
+        out[k] = d
     pct = [float(np.searchsorted(np.sort(pred[a:b]), pred[a + w], side="left")) / (b - a) for a, b, w in rows]
     out["winner_rank_percentile"] = float(np.mean(pct)) if pct else float("nan")
     return out

@@ -80,7 +80,7 @@ def test_recorded_features(ctx):
     for it in range(3):
         rec = ctx.recorded(it)
         feat = ctx.recorded_features(it)
-        assert feat.shape == (rec["s"].size, 12) and np.isfinite(feat).all()
+        assert feat.shape == (rec["s"].size, 14) and np.isfinite(feat).all()
         pc = np.array([bin(int(v)).count("1") for v in f.phases]) / 3.0
         assert np.allclose(feat[:, 4], pc[rec["r"]]) and np.allclose(feat[:, 5], pc[rec["s"]])
         assert set(np.unique(feat[:, 8])) <= {0.0, 1.0}
