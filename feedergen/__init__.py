@@ -45,7 +45,7 @@ import math
 
 import numpy as np
 
-__all__ = ["Feeder", "make_feeder", "preset", "batch_presets", "PRESETS"]
+__all__ = ["Feeder", "make_feeder", "preset", "batch_presets", "PRESETS", "daily_profiles", "with_loads"]
 
 
 @dataclasses.dataclass
@@ -302,3 +302,23 @@ def batch_presets(count: int = 256, first_seed: int = 0, n_lo: int = 200, n_hi: 
                         pf_range=(0.9, 0.98))
         out.append((f, dict(target=target, margin=0.005)))
     return out
+
+
+def daily_profiles(feeder: Feeder, hours: int = 24, seed: int = 0, noise: float = 0.15) -> np.ndarray:
+    """Synthetic hourly loads for robustness studies: the feeder's heavy
+    scenario scaled per hour by a daily shape (night trough, evening peak) and,
+    per bus, by a random shift of that shape and a lognormal factor, so that
+    buses do not move in lockstep.  Returns s_load [hours, n, 3, 2]."""
+    rng = np.random.default_rng(seed)
+    n = feeder.n_bus
+    shift = rng.uniform(-2.0, 2.0, n)                     # hours
+    h = np.arange(hours)[:, None] + shift[None, :]
+    shape = 0.55 + 0.30 * np.sin(2 * math.pi * (h - 10.0) / 24.0) + 0.15 * np.exp(-((h % 24 - 19.0) ** 2) / 8.0)
+    fac = shape * rng.lognormal(0.0, noise, (hours, n))
+    return feeder.s_load[0][None, :, :, :] * fac[:, :, None, None]
+
+
+def with_loads(feeder: Feeder, s_load: np.ndarray) -> Feeder:
+    """The same network with other per-scenario loads ([L, n, 3, 2])."""
+    return Feeder(parent=feeder.parent, phases=feeder.phases, z_line=feeder.z_line,
+                  s_load=np.ascontiguousarray(s_load, dtype=np.float64), v_slack=feeder.v_slack, meta=dict(feeder.meta))

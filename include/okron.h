@@ -275,6 +275,19 @@ okr_status okr_scorer_train(okr_ctx *ctx, const float *x, const float *t, int64_
 /* Predictions y (HOST [n]) for x (HOST [n][n_features]). */
 okr_status okr_scorer_predict(okr_ctx *ctx, const float *x, int64_t n, float *y);
 
+/* The reduced network of a given assignment, evaluated on the feeder's own
+ * scenarios (HOST feeder; its load flows are solved first): super-nodes take
+ * the aggregated injections of their members, the network is solved with the
+ * slack fixed, every bus takes its super-node's voltage (Algorithm 1's
+ * voltage model), and max_error[l] (HOST [n_scen]) receives the largest
+ * per-phase magnitude error against the full network.  Used to test a
+ * reduction on operating points other than the ones it was built from.
+ * super_of: HOST [n_bus] caller ids; every super_of[i] must be a super-node
+ * (super_of[super_of[i]] == super_of[i]) and super_of[0] == 0.
+ * vred (HOST [n_scen][n_bus][3][2], may be NULL): the reduced voltages.
+ * Invalidates the last reduction's results. */
+okr_status okr_evaluate(okr_ctx *ctx, const okr_feeder *f, const int32_t *super_of, double *max_error, double *vred);
+
 /* Largest feeder okr_power_flow_static accepts (buses; scenarios up to 4). */
 #define OKR_STATIC_MAX_BUS 4096
 

@@ -16,6 +16,8 @@ Functions (each names the passage it follows):
   kron_graph      bus adjacency of Y_Kron: a 3x3 block with a nonzero entry (Sec. V)
   maximal_cliques maximal cliques of that graph (Bron-Kerbosch with pivoting)
   radialize       critical nodes of every maximal clique (Sec. V)
+  evaluate        the reduced network of a given assignment on a feeder's own
+                  scenarios (Algorithm 1's voltage model, eq. i_agg)
 """
 from __future__ import annotations
 
@@ -314,3 +316,21 @@ def radialize(feeder, kept: np.ndarray) -> np.ndarray:
             if d >= 3 and not kept[v]:
                 crit[v] = 1
     return crit
+
+
+def evaluate(feeder, super_of: np.ndarray):
+    """Largest per-phase magnitude error per scenario, and the reduced voltages,
+    of assignment super_of on the feeder's scenarios: aggregated injections at
+    the super-nodes, the tree solved with the slack fixed, every bus at its
+    super-node's voltage."""
+    vhat, ihat = operating_points(feeder)
+    n = feeder.n_bus
+    sup = np.asarray(super_of)
+    iagg = np.zeros_like(ihat)
+    for i in range(n):
+        iagg[:, sup[i], :] += ihat[:, i, :]
+    V = tree_solve(feeder, iagg)
+    pres = np.array([[(int(feeder.phases[i]) >> p) & 1 for p in range(3)] for i in range(n)], bool)
+    vred = np.where(pres[None], V[:, sup, :], 0.0)
+    err = np.array([np.abs(np.abs(vhat[l][pres]) - np.abs(vred[l][pres])).max() for l in range(vhat.shape[0])])
+    return err, vred

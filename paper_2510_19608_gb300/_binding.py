@@ -64,7 +64,8 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
            "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
            "okr_set_batch_config", "okr_radialize", "okr_get_recorded_features", "okr_scorer_init",
-           "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict")
+           "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict",
+           "okr_evaluate")
 
 
 def lib_path() -> str:
@@ -100,6 +101,7 @@ def lib():
             L.okr_set_batch_config.argtypes = [P, I32]
             L.okr_radialize.argtypes = [P, P, P, P]
             L.okr_get_recorded_features.argtypes = [P, I32, I32, P, P]
+            L.okr_evaluate.argtypes = [P, C.POINTER(Feeder), P, P, P]
             L.okr_scorer_init.argtypes = [P, I32, P]
             L.okr_scorer_params.argtypes = [P, P, P]
             L.okr_scorer_gradient.argtypes = [P, P, P, I32, P, P]
@@ -292,6 +294,16 @@ class Context:
         self._check(lib().okr_radialize(self._h, _ptr(kp) if kp is not None else None, _ptr(out), C.byref(cnt)))
         assert int(cnt.value) == int(out.sum())
         return out
+
+    def evaluate(self, feeder, super_of):
+        """okr_evaluate: (max error per scenario, reduced voltages [L, n, 3] complex)."""
+        hf = HostFeeder(feeder)
+        sup = np.ascontiguousarray(super_of, dtype=np.int32)
+        L, n = hf.c.n_scen, hf.c.n_bus
+        err = np.zeros(L)
+        v = np.zeros((L, n, 3, 2))
+        self._check(lib().okr_evaluate(self._h, C.byref(hf.c), _ptr(sup), _ptr(err), _ptr(v)))
+        return err, v[..., 0] + 1j * v[..., 1]
 
     # ---- learned scorer
     def recorded_features(self, it: int) -> np.ndarray:

@@ -630,6 +630,56 @@ okr_status okr_power_flow(okr_ctx *ctx, const okr_feeder *f, double *vhat_out, d
     return OKR_OK;
 }
 
+okr_status okr_evaluate(okr_ctx *ctx, const okr_feeder *f, const int32_t *super_of, double *max_error, double *vred) {
+    if (!ctx) return OKR_EINVAL;
+    ctx->have_result = false;
+    ctx->have_topo = false;
+    okr_status s = check_feeder_shape(ctx, f);
+    if (s != OKR_OK) return s;
+    if (!f->s_load || !super_of || !max_error) return fail(ctx, OKR_EINVAL, "s_load, super_of or max_error is NULL");
+    const int n = f->n_bus, L = f->n_scen;
+    if (super_of[0] != 0) return fail(ctx, OKR_EINVAL, "the slack bus must be its own super-node");
+    std::vector<int> moff(n + 1, 0), mem(n);
+    for (int i = 0; i < n; ++i) {
+        const int k = super_of[i];
+        if (k < 0 || k >= n || super_of[k] != k) return fail(ctx, OKR_EINVAL, "super_of[%d] = %d is not a super-node", i, k);
+        moff[k + 1] += 1;
+    }
+    for (int i = 0; i < n; ++i) moff[i + 1] += moff[i];
+    {
+        std::vector<int> fill(moff.begin(), moff.end() - 1);
+        for (int i = 0; i < n; ++i) mem[fill[super_of[i]]++] = i;      // members in increasing caller id
+    }
+    CK(cudaSetDevice(ctx->device));
+    s = ensure_workspace(ctx, n, L, ctx->cap_rec);
+    if (s != OKR_OK) return s;
+    cudaStream_t st = ctx->stream;
+    FeederBufs &B = ctx->fb;
+    CK(cudaMemcpyAsync(B.parent_in, f->parent, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.ph_in, f->phases, n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.z_in, f->z_line, sizeof(double) * 18 * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(B.s_in, f->s_load, sizeof(double) * 6 * L * n, cudaMemcpyHostToDevice, st));
+    s = build_topology(ctx, n, L, &f->v_slack[0][0]);
+    if (s != OKR_OK) return s;
+    s = run_power_flow(ctx, n, L);
+    if (s != OKR_OK) return s;
+    s = read_setup_errors(ctx);
+    if (s != OKR_OK) return s;
+    // the member lists go into buffers this call does not otherwise use
+    // (super_out [n], base [2n+1], dec_s [n], score [2n >= 4])
+    int *sup_d = B.super_out, *moff_d = B.X.base, *mem_d = B.X.dec_s;
+    CK(cudaMemcpyAsync(sup_d, super_of, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(moff_d, moff.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(mem_d, mem.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    double *err_d = B.X.score;
+    k_eval_reduced<<<L, 1024, 0, st>>>(B.T, sup_d, moff_d, mem_d, B.J, B.S.vcur, vred ? B.vred_out : nullptr, err_d);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(max_error, err_d, sizeof(double) * L, cudaMemcpyDeviceToHost, st));
+    if (vred) CK(cudaMemcpyAsync(vred, B.vred_out, sizeof(double) * 6 * L * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return OKR_OK;
+}
+
 okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, int32_t *n_critical) {
     if (!ctx || !critical) return OKR_EINVAL;
     if (!ctx->have_topo) return fail(ctx, OKR_ENOTREADY, "no feeder: run a reduction or a load flow first");

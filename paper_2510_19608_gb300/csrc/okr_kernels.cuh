@@ -48,6 +48,11 @@ struct BatchSetup {
 cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchSetup *bs, double tol, int max_iter,
                                int num_sms, cudaStream_t st);
 
+// The reduced network of a caller assignment (one CTA per scenario).
+__global__ void __launch_bounds__(1024) k_eval_reduced(Topo T, const int *__restrict__ sup, const int *__restrict__ moff,
+                                                      const int *__restrict__ mem, double2 *W, double2 *V, double *vred,
+                                                      double *err);
+
 // okr_kron.cu
 constexpr int kKronShared = 64;     // groups up to this many phase-nodes are inverted in shared memory
 constexpr int kKronMaxGroup = 1024; // larger groups are refused (dense inverse per group)

@@ -796,3 +796,90 @@ cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchS
 }
 
 }  // namespace okr
+
+namespace okr {
+
+// ---------------------------------------------------------------- a given reduced network
+// The reduced network of a caller assignment, for the scenarios of T (Algorithm 1's
+// solve with the aggregated injections, eq. i_agg): every super-node takes the
+// injections of its members (members listed per super-node in increasing caller
+// id, so the sums are deterministic), the tree is solved with those injections
+// and the slack fixed, every bus takes its super-node's voltage, and the largest
+// per-phase magnitude error against Vhat is reported.  One CTA per scenario.
+//   moff/mem: members of each super-node (caller ids), CSR over caller ids.
+//   sup: [n] super-node of each bus (caller ids).  W: [L*3n] work (injections, then
+//   line currents), V: [L*3n] work (voltages).  vred: [L][n][3][2] (may be null).
+__global__ void __launch_bounds__(1024) k_eval_reduced(Topo T, const int *__restrict__ sup, const int *__restrict__ moff,
+                                                      const int *__restrict__ mem, double2 *W, double2 *V, double *vred,
+                                                      double *err) {
+    const int n = T.n, l = blockIdx.x, tid = threadIdx.x, nt = blockDim.x;
+    double2 *Wl = W + (size_t)l * 3 * n, *Vl = V + (size_t)l * 3 * n;
+    __shared__ double s_red[32];
+    // aggregated injections at the super-nodes (preorder), zero elsewhere
+    for (int e = tid; e < 3 * n; e += nt) {
+        const int p = e / n, v = e % n, i = T.orig[v];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int x = moff[i]; x < moff[i + 1]; ++x) {
+            const int u = T.pre[mem[x]];
+            if (T.ph[u] >> p & 1u) acc = cadd(acc, T.ihat[sidx(l, p, u, n)]);
+        }
+        Wl[e] = acc;
+    }
+    __syncthreads();
+    // line currents J_v = -I_v + sum of the children's J, deepest level first
+    const int maxd = T.maxd[0];
+    for (int d = maxd; d >= 1; --d) {
+        for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+            const int v = T.level_bus[x];
+            for (int p = 0; p < 3; ++p) {
+                double2 j = make_double2(-Wl[(size_t)p * n + v].x, -Wl[(size_t)p * n + v].y);
+                for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Wl[(size_t)p * n + T.child[c]]);
+                Wl[(size_t)p * n + v] = j;
+            }
+        }
+        __syncthreads();
+    }
+    // voltages, top down: V_v = V_parent - z_v J_v on the phases of v
+    for (int e = tid; e < 3; e += nt) Vl[(size_t)e * n] = (T.ph[0] >> e & 1u) ? T.vslack[e] : make_double2(0.0, 0.0);
+    __syncthreads();
+    for (int d = 1; d <= maxd; ++d) {
+        for (int x = T.level_off[d] + tid; x < T.level_off[d + 1]; x += nt) {
+            const int v = T.level_bus[x], par = T.parent[v];
+            for (int p = 0; p < 3; ++p) {
+                double2 vv = make_double2(0.0, 0.0);
+                if (T.ph[v] >> p & 1u) {
+                    double2 drop = make_double2(0.0, 0.0);
+                    for (int q = 0; q < 3; ++q)
+                        if (T.ph[v] >> q & 1u) drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], Wl[(size_t)q * n + v]));
+                    vv = csub(Vl[(size_t)p * n + par], drop);
+                }
+                Vl[(size_t)p * n + v] = vv;
+            }
+        }
+        __syncthreads();
+    }
+    // every bus at its super-node's voltage; largest magnitude error
+    double m = 0.0;
+    for (int e = tid; e < 3 * n; e += nt) {
+        const int p = e / n, i = e % n;
+        const int v = T.pre[i], s = T.pre[sup[i]];
+        const bool on = T.ph[v] >> p & 1u;
+        const double2 vr = on ? Vl[(size_t)p * n + s] : make_double2(0.0, 0.0);
+        if (on) m = fmax(m, fabs(T.amag[sidx(l, p, v, n)] - cmag(vr)));
+        if (vred) {
+            const size_t o = (((size_t)l * n + i) * 3 + p) * 2;
+            vred[o] = vr.x;
+            vred[o + 1] = vr.y;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = m;
+    __syncthreads();
+    if (tid == 0) {
+        double r = 0.0;
+        for (int w = 0; w < (nt + 31) / 32; ++w) r = fmax(r, s_red[w]);
+        err[l] = r;
+    }
+}
+
+}  // namespace okr

@@ -538,3 +538,22 @@ def test_radialization_keeps_super_node_voltages():
     v2 = KR.kron_kept_voltages(f, Ypad, np.maximum(kept, crit), iagg)
     rows = np.repeat(kept.astype(bool), 3) & KR.present(f)
     assert np.abs(v1[:, rows] - v2[:, rows]).max() <= 1e-12
+
+
+# ----------------------------------------------------------------------------- evaluation of a given network
+def test_evaluate_identity_assignment_is_exact():
+    f, _ = fg.preset("feeder40")
+    err, vred = O.evaluate(f, np.arange(f.n_bus))
+    vhat, _ = O.operating_points(f)
+    assert err.max() <= 1e-12 and np.abs(vred - vhat).max() <= 1e-12
+
+
+def test_evaluate_reproduces_the_search_result():
+    """Algorithm 1's own voltages and largest error for its final network equal
+    the evaluation of that network by a separate route (tree solve)."""
+    f, run = fg.preset("feeder1000", n_bus=120)
+    vhat, ihat = O.operating_points(f)
+    res = O.reduce(f, vhat, ihat, margin=0.005, max_merges=60)
+    err, vred = O.evaluate(f, res["super_of"])
+    assert abs(err.max() - res["maxerr"][-1]) <= 1e-12
+    assert np.abs(vred - res["v_red"]).max() <= 1e-12
