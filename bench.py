@@ -241,6 +241,29 @@ def learned_line(K, ctx, n_train=64, record=64):
                      "winner_rank_percentile": q["winner_rank_percentile"]}}
 
 
+def sweeps_line(K, ctx):
+    """Margin sweep (eight margins of the 1,000-bus stand-in in one batched
+    launch, run until infeasible, with radialization) and the robustness of its
+    0.005 p.u. reduction over 24 synthetic hours (library: heaviest and lightest
+    hour)."""
+    import feedergen as fg
+    from paper_2510_19608_gb300 import sweeps
+    f, run = fg.preset(WORKLOAD)
+    margins = [0.0005, 0.001, 0.002, 0.003, 0.005, 0.0075, 0.01, 0.015]
+    t0 = time.perf_counter()
+    rows, st = sweeps.margin_sweep(ctx, f, margins)
+    t_sweep = time.perf_counter() - t0
+    hours = fg.daily_profiles(f, hours=24, seed=0)
+    t0 = time.perf_counter()
+    rob = sweeps.profile_robustness(ctx, f, hours, margin=run["margin"], target=1.0)
+    t_rob = time.perf_counter() - t0
+    return {"margin_sweep": {"rows": [{k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items()}
+                                      for r in rows],
+                             "wall_s": t_sweep, "search_ms": st["search_ms"], "setup_ms": st["setup_ms"]},
+            "robustness": {"hours": 24, "wall_s": t_rob, **{k: v for k, v in rob.items() if k != "max_error_by_hour"},
+                           "max_error_by_hour": [round(e, 6) for e in rob["max_error_by_hour"]]}}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -359,6 +382,7 @@ def run_ours(args, rank, world, local):
 
     batch = batch_line(K, ctx) if not args.no_batch else None
     learned = learned_line(K, ctx) if not args.no_learned else None
+    studies = sweeps_line(K, ctx) if not args.no_batch else None
     if rank == 0:
         cb = cpu_baseline(f, run) if world == 1 else None
         line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
@@ -372,7 +396,7 @@ def run_ours(args, rank, world, local):
                     "parallelism": f"replicas x{world}", "time_to_optimal_ms": ms / args.steps,
                     "candidates_per_step": cand_per_step, "merges": summ["n_iter"],
                     "stop_reason": summ["stop_reason"], "wall_s": t_wall, "y_kron": kron,
-                    "batch": batch, "learned_scorer": learned},
+                    "batch": batch, "learned_scorer": learned, "studies": studies},
                 "clocks": clk.summary(), "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
                 "roofline": roofline}
         if cb:
