@@ -67,6 +67,23 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest value of x over all ranks (the job's time is its slowest
+    replica's); the identity on a single process."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_step: float, steps: int, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_step units per step for `steps` steps, timed by the slowest."""
+    return world * units_per_step * steps / (slowest_ms / 1e3)
+
+
 def _workload_config(f, run):
     return {"workload": f"{WORKLOAD}: {f.n_bus} buses ({f.n_phase_nodes} phase nodes), 12.47 kV, "
                         f"{f.n_scen} loading scenarios, target {int(run['target'] * 100)}% reduction, "
@@ -315,11 +332,8 @@ def run_ours(args, rank, world, local):
         dist.barrier()
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     summ_last = ctx.summary()                          # the last timed step
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cand_per_step * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, dist, "cuda")
+    value = replica_value(cand_per_step, args.steps, world, ms)
 
     # ---- the all-FP64 search on the same workload (comparison row)
     for _ in range(3):
