@@ -610,46 +610,7 @@ struct Sel {
 };
 
 __device__ Sel select_exact(const Search &X, int m, const int *map, const double *score, const int *feas, double tau,
-                            double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc) {
-    const int tid = threadIdx.x;
-    unsigned long long bk = ~0ull;
-    for (int i = tid; i < m; i += kThreads)
-        if (ldi(feas + i)) bk = min(bk, dkey(ldd(score + i)));
-    bk = block_reduce(bk, MinU(), smu);
-    Sel out;
-    out.w = -1;
-    out.gap = INFINITY;
-    if (bk == ~0ull || dval(bk) == INFINITY) return out;
-    const double edge = dval(bk) + tau;
-    const unsigned long long ek = dkey(edge);
-    unsigned long long key = ~0ull, gk = ~0ull;
-    for (int i = tid; i < m; i += kThreads) {
-        if (!ldi(feas + i)) continue;
-        const unsigned long long k = dkey(ldd(score + i));
-        if (k <= ek) {
-            const unsigned long long t = __ldcg(X.ckey + (map ? map[i] : i));
-            if (t < key) key = t;
-        } else if (k < gk) {
-            gk = k;
-        }
-    }
-    key = block_reduce(key, MinU(), smu);
-    gk = block_reduce(gk, MinU(), smu);
-    int w = 0x7fffffff;
-    if (ksure < key) {              // a candidate known to be in the band has the smallest key
-        for (int c = tid; c < nc; c += kThreads)
-            if (__ldcg(X.ckey + c) == ksure) w = min(w, c);
-        w = block_reduce(w, MinI(), smi);
-        out.w = (w < nc) ? w : -2;
-    } else {
-        for (int i = tid; i < m; i += kThreads)
-            if (ldi(feas + i) && dkey(ldd(score + i)) <= ek && __ldcg(X.ckey + (map ? map[i] : i)) == key) w = min(w, i);
-        w = block_reduce(w, MinI(), smi);
-        out.w = (w < m) ? (map ? map[w] : w) : -2;
-    }
-    out.gap = (gk == ~0ull) ? INFINITY : dval(gk) - edge;
-    return out;
-}
+                            double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc);
 
 constexpr int kRmax = 1024;     // candidates an FP64 recheck can hold in shared memory
 
@@ -676,6 +637,96 @@ struct Screen {
     double gap;                 // screen distance from the band edge to the next candidate
 };
 
+// Block-wide minima of two floats with one pair of barriers.
+__device__ __forceinline__ void block_min2f(float &a, float &b) {
+    __shared__ float2 sm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fminf(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fminf(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    __syncthreads();
+    if (lane == 0) sm[wid] = make_float2(a, b);
+    __syncthreads();
+    a = sm[0].x;
+    b = sm[0].y;
+    for (int w = 1; w < nw; ++w) {
+        a = fminf(a, sm[w].x);
+        b = fminf(b, sm[w].y);
+    }
+}
+
+// Block-wide minima of two 64-bit keys and a float with one pair of barriers.
+__device__ __forceinline__ void block_min_uuf(unsigned long long &a, unsigned long long &b, float &c) {
+    struct R3 {
+        unsigned long long a, b;
+        float c;
+    };
+    __shared__ R3 sm[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        a = min(a, (unsigned long long)__shfl_xor_sync(0xffffffffu, a, o));
+        b = min(b, (unsigned long long)__shfl_xor_sync(0xffffffffu, b, o));
+        c = fminf(c, __shfl_xor_sync(0xffffffffu, c, o));
+    }
+    __syncthreads();
+    if (lane == 0) sm[wid] = R3{a, b, c};
+    __syncthreads();
+    a = sm[0].a;
+    b = sm[0].b;
+    c = sm[0].c;
+    for (int w = 1; w < nw; ++w) {
+        a = min(a, sm[w].a);
+        b = min(b, sm[w].b);
+        c = fminf(c, sm[w].c);
+    }
+}
+
+__device__ Sel select_exact(const Search &X, int m, const int *map, const double *score, const int *feas, double tau,
+                            double *smd, unsigned long long *smu, int *smi, unsigned long long ksure, int nc) {
+    const int tid = threadIdx.x;
+    unsigned long long bk = ~0ull;
+    for (int i = tid; i < m; i += kThreads)
+        if (ldi(feas + i)) bk = min(bk, dkey(ldd(score + i)));
+    bk = block_reduce(bk, MinU(), smu);
+    Sel out;
+    out.w = -1;
+    out.gap = INFINITY;
+    if (bk == ~0ull || dval(bk) == INFINITY) return out;
+    const double edge = dval(bk) + tau;
+    const unsigned long long ek = dkey(edge);
+    // one pass: the band's smallest key packed with its index, and the
+    // smallest score above the band
+    unsigned long long kp = ~0ull, gk = ~0ull;
+    float unused = INFINITY;
+    for (int i = tid; i < m; i += kThreads) {
+        if (!ldi(feas + i)) continue;
+        const unsigned long long k = dkey(ldd(score + i));
+        if (k <= ek) {
+            const unsigned long long t = __ldcg(X.ckey + (map ? map[i] : i));
+            kp = min(kp, (t << 32) | (unsigned)i);
+        } else if (k < gk) {
+            gk = k;
+        }
+    }
+    block_min_uuf(kp, gk, unused);
+    const unsigned long long key = (kp == ~0ull) ? ~0ull : (kp >> 32);
+    if (ksure < key) {              // a candidate known to be in the band has the smallest key
+        int w = 0x7fffffff;
+        for (int c = tid; c < nc; c += kThreads)
+            if (__ldcg(X.ckey + c) == ksure) w = min(w, c);
+        w = block_reduce(w, MinI(), smi);
+        out.w = (w < nc) ? w : -2;
+    } else if (kp == ~0ull) {
+        out.w = -2;
+    } else {
+        const int w = (int)(kp & 0xffffffffu);
+        out.w = map ? map[w] : w;
+    }
+    out.gap = (gk == ~0ull) ? INFINITY : dval(gk) - edge;
+    return out;
+}
+
 __device__ Screen screen_select(const Search &X, int nc, double margin, double tau, int *s_R, int2 *sm2, float *smf,
                                 unsigned long long *smu, int *smi) {
     const int tid = threadIdx.x;
@@ -687,8 +738,7 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
         if (__fsub_rd(q.z, q.w) <= margin_hi) mlo = fminf(mlo, __fsub_rd(q.x, q.y));
         if (surely_feasible(q, margin_lo)) mhi = fminf(mhi, __fadd_ru(q.x, q.y));
     }
-    mlo = block_reduce(mlo, MinF(), smf);
-    mhi = block_reduce(mhi, MinF(), smf);
+    block_min2f(mlo, mhi);
     Screen out;
     out.nR = 0;
     out.win = -1;
@@ -697,47 +747,49 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
     out.gap = INFINITY;
     if (!out.any) return out;
     const float edge_in = __fadd_rd(mlo, tau_lo), edge_out = __fadd_ru(mhi, tau_hi);
-    unsigned long long ks = ~0ull;
+    // one pass: the smallest surely-in key (packed with its candidate index), the
+    // smallest key of an uncertain candidate, and the gap above the band
+    unsigned long long kp = ~0ull, ku = ~0ull;
     float g = INFINITY;
     for (int c = tid; c < nc; c += kThreads) {
         const float4 q = __ldcg(X.scr + c);
         const bool maybe = __fsub_rd(q.z, q.w) <= margin_hi;
         if (!maybe) continue;
         const float lo = __fsub_rd(q.x, q.y), hi = __fadd_ru(q.x, q.y);
-        if (surely_feasible(q, margin_lo) && hi <= edge_in) ks = min(ks, __ldcg(X.ckey + c));
-        if (lo > edge_out) g = fminf(g, lo - edge_out);
+        const bool in_sure = surely_feasible(q, margin_lo) && hi <= edge_in;
+        const bool out_sure = lo > edge_out;
+        const unsigned long long key = __ldcg(X.ckey + c);
+        if (in_sure) kp = min(kp, (key << 32) | (unsigned)c);
+        else if (!out_sure) ku = min(ku, key);
+        if (out_sure) g = fminf(g, lo - edge_out);
     }
-    ks = block_reduce(ks, MinU(), smu);
+    block_min_uuf(kp, ku, g);
+    const unsigned long long ks = (kp == ~0ull) ? ~0ull : (kp >> 32);
     out.ksure = ks;
-    out.gap = (double)block_reduce(g, MinF(), smf);
+    out.gap = (double)g;
+    if (!(ku < ks)) {                   // no uncertain candidate can take the band's smallest key
+        out.win = (kp == ~0ull) ? -2 : (int)(kp & 0xffffffffu);
+        return out;
+    }
     // R: possible minimizers and uncertain candidates with a key below ks
-    int nR = 0, need = 0;
+    int nR = 0;
     for (int c0 = 0; c0 < nc; c0 += kThreads) {
         const int c = c0 + tid;
-        int flag = 0, unc = 0;
+        int flag = 0;
         if (c < nc) {
             const float4 q = __ldcg(X.scr + c);
             if (__fsub_rd(q.z, q.w) <= margin_hi) {
                 const float lo = __fsub_rd(q.x, q.y), hi = __fadd_ru(q.x, q.y);
                 const bool in_sure = surely_feasible(q, margin_lo) && hi <= edge_in;
                 const bool out_sure = lo > edge_out;
-                if (!in_sure && !out_sure && __ldcg(X.ckey + c) < ks) unc = 1;
+                const bool unc = !in_sure && !out_sure && __ldcg(X.ckey + c) < ks;
                 if (unc || lo <= mhi) flag = 1;
             }
         }
         int2 tot;
-        const int2 ex = block_scan2(make_int2(flag, unc), sm2, &tot);
+        const int2 ex = block_scan2(make_int2(flag, 0), sm2, &tot);
         if (flag && nR + ex.x < kRmax) s_R[nR + ex.x] = c;
         nR += tot.x;
-        need += tot.y;
-    }
-    if (need == 0) {
-        int w = 0x7fffffff;
-        for (int c = tid; c < nc; c += kThreads)
-            if (__ldcg(X.ckey + c) == ks) w = min(w, c);
-        w = block_reduce(w, MinI(), smi);
-        out.win = (w < nc) ? w : -2;
-        return out;
     }
     out.nR = nR;
     __syncthreads();
