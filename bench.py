@@ -392,7 +392,10 @@ def run_ours(args, rank, world, local):
                 "phase_ms": dict(zip(["select", "recheck", "merge", "setup", "barrier1", "chunkmap", "barrier2",
                                       "sweep+barrier3", "merge_sum", "list_update", "offsets", "compaction"],
                                      [round(x, 3) for x in ps["phase_ms"][:12]])),
-                "share_of_step": search_ms / (ms / args.steps)}
+                "share_of_step": search_ms / (ms / args.steps),
+                "sweep_warps": {"mean_us": 1e3 * ps["phase_ms"][12] / max(1e-9, 1e6 * ps["phase_ms"][13]),
+                                "max_us": 1e3 * ps["phase_ms"][14], "warp_sweeps": int(round(1e6 * ps["phase_ms"][13])),
+                                "chunks": int(round(1e6 * ps["phase_ms"][15]))}}
 
     batch = batch_line(K, ctx) if not args.no_batch else None
     learned = learned_line(K, ctx) if not args.no_learned else None

@@ -1301,9 +1301,12 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         // ============================================================ phase 3
         {
             const int *list_new = S.sn_list[t & 1];
-            unsigned long long t_start = 0;
+            unsigned long long t_start = 0, w_start = 0;
             if (prof && lead) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+            if (prof) w_start = gtimer();
+            int my_chunks = 0;
             for (int g = warp; g < nchunks; g += nwarps) {
+                ++my_chunks;
                 const int c0 = ldi(X.chunk_first + g);
                 const int q = g * PPW + lane / SP;
                 const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
@@ -1324,6 +1327,13 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                                   X.score, X.feas, prof, flops, obj1, ns);
                 else
                     score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops);
+            }
+            if (prof && lane == 0 && my_chunks > 0) {      // per-warp sweep time: sum, count, largest
+                const unsigned long long d = gtimer() - w_start;
+                atomicAdd(&C->phase_ns[12], d);
+                atomicAdd(&C->phase_ns[13], 1ull);
+                atomicMax(&C->phase_ns[14], d);
+                atomicAdd(&C->phase_ns[15], (unsigned long long)my_chunks);
             }
             if (!team_barrier(gb, C, G, epoch)) return;
             if (prof && lead) {
