@@ -29,14 +29,15 @@
 // max(hi - m, m - lo); the MICE is the largest of these over phases.
 //
 // Work layout.  The (candidate, affected super-node) pairs of an iteration form
-// one dense position space, candidates back to back.  Each position spreads over
-// a group of SP = 4 * Lp lanes, one lane per (scenario, phase) (Lp = scenarios
-// rounded up to a power of two; the fourth phase lane idles): on this GPU the
-// FP64 pipe issues a warp instruction every few dozen cycles, so a lane's FP64
-// chain sets the latency and short chains matter more than idle lanes.
-// Per-candidate sums are reduced in a fixed order (group shuffles, a segmented
-// warp scan, then the pieces of a candidate in chunk order), so results do not
-// depend on timing.
+// one dense position space, candidates back to back.  A sweep gives each
+// position four lanes, one per phase (the fourth idles), and each lane takes the
+// scenarios in turn, so a warp holds eight positions: on a 1,000-bus feeder an
+// iteration's positions then fit in about one warp each, and the sweep's time is
+// one warp's chain of dependent loads rather than two.  (The merge's items use
+// one lane per (scenario, phase): 4 * Lp lanes, Lp = scenarios rounded up to a
+// power of two.)  Per-candidate sums are reduced in a fixed order (phase
+// shuffles, scenarios in order, a segmented warp scan, then the pieces of a
+// candidate in chunk order), so results do not depend on timing.
 //
 // Precision.  precision 0 scores every candidate in FP64.  precision 1 screens
 // every candidate in FP32 with a rigorous bound B(c) on the distance between the
@@ -381,35 +382,35 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
                               double margin, double *out_score, int *out_feas, bool prof, double &flops,
                               bool obj1 = false, int nsn = 0) {
-    const int lane = threadIdx.x & 31, sub = lane % SP, l = sub >> 2, p = sub & 3;
+    // one lane per phase (SP == 4), the scenarios in turn inside the lane
+    const int lane = threadIdx.x & 31, p = lane & 3;
     int k = cd.r;
     bool sside = false;
     if (active) k = position_bus(list, cd, q, sside);
     const bool valid = active && k != cd.r;
-    Item64 o;
-    o.e = 0.0;
-    o.on = false;
-    if (valid && l < L && p < 3) {
-        double2 Ir[3];
-        for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldz(S.icur + sidx(l, qq, cd.r, n));
-        o = eval_item64(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r]);
-        if (prof && o.on) flops += (k < 0) ? 8.0 : 10.0 * __popc(T.ph[cd.r]) + 10.0;
-    }
-    double m = o.e;
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    const int kk = k < 0 ? cd.s : k;
     double dl = 0.0, ml = 0.0;
-    if (valid && p == 0 && l < L) {
-        const int kk = k < 0 ? cd.s : k;
-        dl = m - ldd(S.mice + (size_t)l * n + kk);
-        if (kk == cd.s) dl -= ldd(S.mice + (size_t)l * n + cd.r);
-        ml = m;
+    for (int l = 0; l < L; ++l) {
+        Item64 o;
+        o.e = 0.0;
+        o.on = false;
+        if (valid && p < 3) {
+            double2 Ir[3];
+            for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldz(S.icur + sidx(l, qq, cd.r, n));
+            o = eval_item64(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r]);
+            if (prof && o.on) flops += (k < 0) ? 8.0 : 10.0 * __popc(T.ph[cd.r]) + 10.0;
+        }
+        double m = o.e;
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        if (valid && p == 0) {
+            double d = m - ldd(S.mice + (size_t)l * n + kk);
+            if (kk == cd.s) d -= ldd(S.mice + (size_t)l * n + cd.r);
+            dl += d;
+            ml = fmax(ml, m);
+        }
     }
-    for (int o2 = 4; o2 < SP; o2 <<= 1) {
-        dl += __shfl_xor_sync(0xffffffffu, dl, o2);
-        ml = fmax(ml, __shfl_xor_sync(0xffffffffu, ml, o2));
-    }
-    if (sub != 0) { dl = 0.0; ml = 0.0; }
+    if (p != 0) { dl = 0.0; ml = 0.0; }
     unsigned heads;
     int seg_start;
     bool last;
@@ -491,45 +492,43 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
 __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
                               bool prof, double &flops) {
-    const int lane = threadIdx.x & 31, sub = lane % SP, l = sub >> 2, p = sub & 3;
+    // one lane per phase (SP == 4), the scenarios in turn inside the lane
+    const int lane = threadIdx.x & 31, p = lane & 3;
     int k = cd.r;
     bool sside = false;
     if (active) k = position_bus(list, cd, q, sside);
     const bool valid = active && k != cd.r;
-    Item32 o;
-    o.e = 0.0f;
-    o.b = 0.0f;
+    const int kk = k < 0 ? cd.s : k;
+    const unsigned phr = T.ph[cd.r];
     float fl = 0.0f;
-    if (valid && l < L && p < 3) {
-        float2 Ir[3];
-        for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldf2(S.icur32 + sidx(l, qq, cd.r, n));
-        o = eval_item32(T, S, n, cd, k, sside, l, p, Ir, T.ph[cd.r], fl);
+    float dl = 0.0f, bl = 0.0f, ad = 0.0f, ml = 0.0f, bml = 0.0f;
+    for (int l = 0; l < L; ++l) {
+        Item32 o;
+        o.e = 0.0f;
+        o.b = 0.0f;
+        if (valid && p < 3) {
+            float2 Ir[3];
+            for (int qq = 0; qq < 3; ++qq) Ir[qq] = ldf2(S.icur32 + sidx(l, qq, cd.r, n));
+            o = eval_item32(T, S, n, cd, k, sside, l, p, Ir, phr, fl);
+        }
+        float m = o.e, bm = o.b;
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+        bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 1));
+        bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
+        if (valid && p == 0) {
+            const float mo = ldf(S.mice32 + (size_t)l * n + kk);
+            const float mr = (kk == cd.s) ? ldf(S.mice32 + (size_t)l * n + cd.r) : 0.0f;
+            const float d = (m - mo) - mr;
+            dl += d;
+            bl += bm + 2.0f * kU * (fabsf(mo) + fabsf(mr) + fabsf(m));
+            ad += fabsf(d);
+            ml = fmaxf(ml, m);
+            bml = fmaxf(bml, bm);
+        }
     }
     if (prof) flops += fl;
-    float m = o.e, bm = o.b;
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 1));
-    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
-    float dl = 0.0f, bl = 0.0f, ad = 0.0f, ml = 0.0f, bml = 0.0f;
-    if (valid && p == 0 && l < L) {
-        const int kk = k < 0 ? cd.s : k;
-        const float mo = ldf(S.mice32 + (size_t)l * n + kk);
-        const float mr = (kk == cd.s) ? ldf(S.mice32 + (size_t)l * n + cd.r) : 0.0f;
-        dl = (m - mo) - mr;
-        bl = bm + 2.0f * kU * (fabsf(mo) + fabsf(mr) + fabsf(m));
-        ad = fabsf(dl);
-        ml = m;
-        bml = bm;
-    }
-    for (int o2 = 4; o2 < SP; o2 <<= 1) {
-        dl += __shfl_xor_sync(0xffffffffu, dl, o2);
-        bl += __shfl_xor_sync(0xffffffffu, bl, o2);
-        ad += __shfl_xor_sync(0xffffffffu, ad, o2);
-        ml = fmaxf(ml, __shfl_xor_sync(0xffffffffu, ml, o2));
-        bml = fmaxf(bml, __shfl_xor_sync(0xffffffffu, bml, o2));
-    }
-    if (sub != 0) { dl = bl = ad = ml = bml = 0.0f; }
+    if (p != 0) { dl = bl = ad = ml = bml = 0.0f; }
     unsigned heads;
     int seg_start;
     bool last;
@@ -874,7 +873,8 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
     __shared__ int s_Rbase[kRmax + 1];
     const int n = T.n, L = T.L;
     const int Lp = L <= 1 ? 1 : (L <= 2 ? 2 : 4);
-    const int SP = 4 * Lp, PPW = 32 / SP;
+    const int SPC = 4 * Lp;                    // lanes per position of the merge's items
+    constexpr int SP = 4, PPW = 8;             // sweeps: one lane per phase, 8 positions per warp
     constexpr int nt = kThreads;           // every search kernel runs 512-thread CTAs
     const int tid = threadIdx.x, lane = tid & 31;
     const int gt = rank * nt + tid, gs = (int)G * nt;
@@ -1024,11 +1024,11 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             const int rgt = gs - 1 - gt, cwarp = nwarps - 1 - warp;
             for (int i = rgt; i < n; i += gs)
                 if (ldi(S.label + i) == cd.r) S.label[i] = cd.s;
-            const int nitems = cand_positions(cd) * SP;
+            const int nitems = cand_positions(cd) * SPC;
             double acc = 0.0;
             for (int i0 = cwarp * 32; i0 < nitems; i0 += nwarps * 32) {
                 const int item = i0 + lane;
-                const int q = item / SP, sub = item % SP, l = sub >> 2, p = sub & 3;
+                const int q = item / SPC, sub = item % SPC, l = sub >> 2, p = sub & 3;
                 bool sside = false;
                 const int k = item < nitems ? position_bus(list_old, cd, q, sside) : cd.r;
                 const bool live = item < nitems && l < L && p < 3 && k != cd.r;
