@@ -1150,8 +1150,11 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
 
         // ============================================================ phase 2
         if (committed) {
-            // exact score change of the merge, in warp order (CTA 0, warp 0)
-            if (rank == 0 && tid < 32) {
+            // The merge's bookkeeping runs on the grid's last warps, so that it
+            // overlaps the compaction and chunk map on the first CTAs.
+            // Exact score change of the merge, in warp order (the last warp);
+            // its lane 0 is the only writer of C->s_cur in this phase.
+            if (rank == (int)G - 1 && tid >= nt - 32) {
                 double d = 0.0;
                 for (int w2 = lane; w2 < nw_commit; w2 += 32) d += ldd(X.wsum + w2);
                 for (int o2 = 16; o2 > 0; o2 >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o2);
@@ -1171,7 +1174,8 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             // super-node list after the merge (other buffer), ranks, largest MICE
             int *list_new = S.sn_list[t & 1];
             unsigned long long m = 0;          // MICE >= 0: bit patterns order like the values
-            for (int j0 = gt - lane; j0 < ns; j0 += gs) {     // warp-uniform trip count
+            const int rwarp = nwarps - 1 - warp;
+            for (int j0 = rwarp * 32; j0 < ns; j0 += gs) {    // warp-uniform trip count
                 const int j = j0 + lane;
                 double mr = 0.0;
                 if (j < ns) {
@@ -1186,7 +1190,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                     if (lane == 0) X.bmax[j0 >> 5] = mr;
                 }
             }
-            for (int b = r0 + 1 + gt; b <= n; b += gs) S.sn_rank[b] = ldi(S.sn_rank + b) - 1;
+            for (int b = r0 + 1 + (gs - 1 - gt); b <= n; b += gs) S.sn_rank[b] = ldi(S.sn_rank + b) - 1;
             m = block_reduce(m, MaxU(), smu);
             if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
             stamp(9);
@@ -1217,12 +1221,13 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         nc = tot.x;
         P = tot.y;
         nchunks = (P + PPW - 1) / PPW;
+        // (C->s_cur already holds this iteration's value: the merge's sum wrote it)
         if (nc == 0) {                                  // no candidate at all: nothing is feasible
-            if (lead) { C->done = 1; C->stop_reason = 1; C->t = t; C->s_cur = s_cur; C->n_super = ns; }
+            if (lead) { C->done = 1; C->stop_reason = 1; C->t = t; C->n_super = ns; }
             break;
         }
         if (nchunks > X.max_chunks) {                   // grow the work buffers and relaunch
-            if (lead) { C->err = 7; C->total_pos = P; C->t = t; C->s_cur = s_cur; C->n_super = ns; }
+            if (lead) { C->err = 7; C->total_pos = P; C->t = t; C->n_super = ns; }
             break;
         }
         {
