@@ -83,6 +83,7 @@ struct Cand {
 struct State {
     int *label;         // [n] super-node of each bus
     int *top;           // [n] topmost bus of each cluster
+    int *ptop;          // [n] parent bus of that topmost bus (-1 for the slack's cluster)
     int *sn_list[2];    // [n] super-nodes in increasing preorder id after t merges: buffer t & 1
     int *sn_rank;       // [n+1] number of super-nodes with a smaller preorder id
     double2 *vcur;      // [L*3*n] super-node voltages for the current injections

@@ -106,6 +106,7 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     State &S = f.S;
     c.take(S.label, N);
     c.take(S.top, N);
+    c.take(S.ptop, N);
     c.take(S.sn_list[0], N);
     c.take(S.sn_list[1], N);
     c.take(S.sn_rank, N + 1);

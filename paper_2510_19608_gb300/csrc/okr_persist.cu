@@ -1080,7 +1080,10 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                             S.icur[is] = ni;
                             S.icur32[is] = make_float2((float)ni.x, (float)ni.y);
                         }
-                if (cd.dir == 1) S.top[cd.s] = ldi(S.top + cd.r);
+                if (cd.dir == 1) {
+                    S.top[cd.s] = ldi(S.top + cd.r);
+                    S.ptop[cd.s] = ldi(S.ptop + cd.r);
+                }
                 X.dec_s[t] = T.orig[cd.s];
                 X.dec_r[t] = T.orig[cd.r];
                 X.dec_gap[t] = sel.gap;
@@ -1108,11 +1111,16 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             c1.s = -1;
             if (j >= 1) {
                 const int w = ldi(list_old + j + (committed && j >= jr0 ? 1 : 0));
-                const int tw = (committed && w == s0 && dir0 == 1) ? ldi(S.top + r0) : ldi(S.top + w);
-                int x = ldi(S.label + T.parent[tw]);
+                const bool moved = committed && w == s0 && dir0 == 1;     // s took r's top this merge
+                const int tw = moved ? ldi(S.top + r0) : ldi(S.top + w);
+                const int pw_bus = moved ? ldi(S.ptop + r0) : ldi(S.ptop + w);
+                int x = ldi(S.label + pw_bus);
                 if (committed && x == r0) x = s0;
-                const int a = T.lca[(size_t)x * n + w];
-                const int cw = child_toward(T, a, w);
+                // when x's own bus is the parent of w's top, x is the common ancestor
+                // and w's branch starts at its top: no table lookup or search
+                const bool direct = (x == pw_bus);
+                const int a = direct ? x : (int)T.lca[(size_t)x * n + w];
+                const int cw = direct ? tw : child_toward(T, a, w);
                 auto rank = [&](int b) { return ldi(S.sn_rank + b) - ((committed && b > r0) ? 1 : 0); };
                 const int jw = rank(cw), nw = rank(cw + T.sz[cw]) - jw;
                 int jx = 0, nx = 0;
@@ -1175,7 +1183,9 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             int *list_new = S.sn_list[t & 1];
             unsigned long long m = 0;          // MICE >= 0: bit patterns order like the values
             const int rwarp = nwarps - 1 - warp;
-            for (int j0 = rwarp * 32; j0 < ns; j0 += gs) {    // warp-uniform trip count
+            // CTAs whose (reversed) warps hold no list entry skip the loop and its reduction
+            const bool has_list = (nwarps - (rank + 1) * (nt / 32)) * 32 < ns;
+            for (int j0 = rwarp * 32; has_list && j0 < ns; j0 += gs) {    // warp-uniform trip count
                 const int j = j0 + lane;
                 double mr = 0.0;
                 if (j < ns) {
@@ -1191,8 +1201,10 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 }
             }
             for (int b = r0 + 1 + (gs - 1 - gt); b <= n; b += gs) S.sn_rank[b] = ldi(S.sn_rank + b) - 1;
-            m = block_reduce(m, MaxU(), smu);
-            if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
+            if (has_list) {
+                m = block_reduce(m, MaxU(), smu);
+                if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
+            }
             stamp(9);
         }
         if (finishing) {

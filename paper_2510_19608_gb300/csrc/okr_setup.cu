@@ -626,6 +626,7 @@ __device__ void dev_state_init(int n, int L, Topo T, State S, size_t first, size
         if (l == 0) {
             S.label[v] = v;
             S.top[v] = v;
+            S.ptop[v] = T.parent[v];
             S.sn_list[0][v] = v;
             S.sn_rank[v] = v;
             if (v == n - 1) S.sn_rank[n] = n;
