@@ -152,9 +152,30 @@ def cpu_baseline(f, run, max_seconds=30.0):
     t0 = time.perf_counter()
     res = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
     dt = time.perf_counter() - t0
-    return {"value": res["candidates"] / dt, "unit": "candidates/s", "cores": O.num_threads(), "kind": "oracle",
+    cores = O.num_threads()
+    # the same oracle on one thread (first 50 merges), and its literal mode
+    # (a full network solve per candidate) on the 40-bus case
+    O.set_threads(1)
+    try:
+        t1 = time.perf_counter()
+        r1 = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=min(merges, 50))
+        d1 = time.perf_counter() - t1
+        import feedergen as fg
+        f40, run40 = fg.preset("feeder40")
+        v40, i40 = O.operating_points(f40)
+        t2 = time.perf_counter()
+        r40 = O.reduce(f40, v40, i40, margin=run40["margin"], max_merges=f40.n_bus - 1, mode="literal")
+        d2 = time.perf_counter() - t2
+    finally:
+        O.set_threads(cores)
+    return {"value": res["candidates"] / dt, "unit": "candidates/s", "cores": cores, "kind": "oracle",
             "sample": f"full {WORKLOAD} reduction ({res['n_iter']} merges, {res['candidates']} candidates) "
-                      f"in {dt:.2f} s, delta mode", "seconds": dt, "merges": int(res["n_iter"])}
+                      f"in {dt:.2f} s, delta mode", "seconds": dt, "merges": int(res["n_iter"]),
+            "one_thread": {"value": r1["candidates"] / d1, "unit": "candidates/s", "cores": 1,
+                           "sample": f"first {r1['n_iter']} merges of {WORKLOAD}, delta mode", "seconds": d1},
+            "literal_feeder40": {"value": r40["candidates"] / d2, "unit": "candidates/s", "cores": 1,
+                                 "sample": f"feeder40 until infeasible ({r40['n_iter']} merges), literal mode",
+                                 "seconds": d2}}
 
 
 def run_reference(args, rank, world):
