@@ -328,6 +328,11 @@ def _check_properties(ctx, f, margin):
     smice = sum(float(e[l][sup == k].max()) for l in range(e.shape[0]) for k in np.unique(sup))
     s = ctx.summary()
     assert abs(s["smice"] - smice) <= 1e-10
+    # the chosen network evaluated by the oracle (load flow, aggregated
+    # injections, tree solve): the same voltages and the same largest error
+    err_o, vred_o = O.evaluate(f, sup)
+    assert np.abs(vr - vred_o).max() <= V_TOL
+    assert abs(float(err_o.max()) - s["max_error"]) <= 1e-11
     assert abs(s["max_error"] - e.max()) <= 1e-12
 
 
