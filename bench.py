@@ -32,8 +32,8 @@ WORKLOAD = "feeder1000"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes of one k_search launch on this workload from the ncu capture in
 # profiles/k_search_feeder1000.md, valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"bytes": 1096960 + 131072, "source": "paper_2510_19608_gb300/csrc/okr_persist.cu",
-               "sha256_prefix": "954098d3a9b39e9e", "summary": "profiles/k_search_feeder1000.md"}
+NCU_TRAFFIC = {"bytes": 1037824 + 114432, "source": "paper_2510_19608_gb300/csrc/okr_persist.cu",
+               "sha256_prefix": "31fd03f65db8da77", "summary": "profiles/k_search_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
