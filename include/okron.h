@@ -80,8 +80,8 @@ typedef struct okr_params {
                                    n_bus - 1); 1.0 = run until no candidate is feasible */
     double tie_tol;             /* tie band tau on the score, >= 0 (default 1e-9) */
     int32_t objective;          /* 0 = SMICE (Algorithm 1); 1 = the largest per-phase error of the
-                                   candidate network (the iteration objective of Sec. IV), with
-                                   precision 0 only; other values are rejected */
+                                   candidate network (the iteration objective of Sec. IV); other
+                                   values are rejected */
     int32_t precision;          /* 0 = every candidate scored in FP64;
                                    1 = FP32 screen with a rigorous error bound, FP64 rescoring of
                                    the candidates the bound cannot separate, FP64 merges.  Both
@@ -324,8 +324,9 @@ okr_status okr_power_flow_static(const okr_feeder *f, double *vhat_out, double *
 /* ---- results of the last reduction (host buffers, caller-owned) ---- */
 okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out);
 /* Decision sequence, one entry per merge, in caller bus ids: s (absorbing
- * super-node), r (absorbed), SMICE after the merge, largest error after the
- * merge, distance of the next score above the tie band, candidates evaluated.
+ * super-node), r (absorbed), the objective after the merge (SMICE, or the
+ * largest error with objective 1), largest error after the merge, distance
+ * of the next score above the tie band, candidates evaluated.
  * cap = buffer length; any pointer may be NULL. */
 okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_t *r, double *smice,
                              double *max_error, double *gap, int32_t *ncand);

@@ -196,8 +196,6 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
     if (p->max_merges < 0 && !(p->target_reduction >= 0.0 && p->target_reduction <= 1.0))
         return fail(ctx, OKR_EINVAL, "target_reduction outside [0, 1]");
     if (p->objective != 0 && p->objective != 1) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
-    if (p->objective == 1 && p->precision != 0)
-        return fail(ctx, OKR_EINVAL, "objective 1 (largest error) runs with precision 0 only");
     if (p->precision != 0 && p->precision != 1) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
     if (p->record_iters < 0) return fail(ctx, OKR_EINVAL, "record_iters < 0");
     if (p->reserved != 0) return fail(ctx, OKR_EINVAL, "reserved must be 0");
@@ -1184,7 +1182,9 @@ okr_status okr_get_decisions(const okr_ctx *ctx, int32_t cap, int32_t *s, int32_
     const Search &X = ctx->fb.X;
     if (s && cudaMemcpy(s, X.dec_s, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (r && cudaMemcpy(r, X.dec_r, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
-    if (smice && cudaMemcpy(smice, X.dec_score, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    // objective 1 scores a network by its largest error, which is max_error
+    const double *score = ctx->last.objective == 1 ? X.dec_maxerr : X.dec_score;
+    if (smice && cudaMemcpy(smice, score, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (max_error && cudaMemcpy(max_error, X.dec_maxerr, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (gap && cudaMemcpy(gap, X.dec_gap, sizeof(double) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (ncand && cudaMemcpy(ncand, X.dec_ncand, sizeof(int) * t, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;

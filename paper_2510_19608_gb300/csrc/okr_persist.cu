@@ -489,9 +489,18 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
 // FP32 screen of a chunk (precision 1).  Pieces hold (D32, bound, max MICE,
 // bound of the max); the final bound adds 32u sum |piece| for the rounding of
 // the FP32 sums.
+// Objective 1 in the screen: the absolute score max(largest new MICE, largest
+// unaffected MICE) as an interval [hi - y, hi + y] that contains
+// [max(ml - bml, U), max(ml + bml, U)] (U exact, rounded outward to FP32).
+__device__ __forceinline__ float4 obj1_screen(float ml, float bml, double U) {
+    const float ulo = __double2float_rd(U), uhi = __double2float_ru(U);
+    const float lo = fmaxf(__fsub_rd(ml, bml), ulo), hi = fmaxf(__fadd_ru(ml, bml), uhi);
+    return make_float4(hi, __fsub_ru(hi, lo), ml, bml);
+}
+
 __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
-                              bool prof, double &flops) {
+                              bool prof, double &flops, bool obj1 = false, int nsn = 0) {
     // one lane per phase (SP == 4), the scenarios in turn inside the lane
     const int lane = threadIdx.x & 31, p = lane & 3;
     int k = cd.r;
@@ -542,11 +551,12 @@ __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, in
         if (lane - o2 >= seg_start) { dl += y1; bl += y2; ad += y3; ml = fmaxf(ml, y4); bml = fmaxf(bml, y5); }
     }
     float4 *pf = reinterpret_cast<float4 *>(X.partial);
-    bool fin = false;
+    bool fin = false, direct = false;
     if (active && last) {
         const float pb = bl + 32.0f * kU * ad;
         if (np == 1) {                      // the whole candidate lies in this chunk
-            X.scr[ci] = make_float4(dl, 1.001f * (pb + 38.0f * kU * fabsf(dl)), ml, bml);
+            if (obj1) direct = true;
+            else X.scr[ci] = make_float4(dl, 1.001f * (pb + 38.0f * kU * fabsf(dl)), ml, bml);
         } else {
             pf[g + ci] = make_float4(dl, pb, ml, bml);
             __threadfence();
@@ -576,12 +586,33 @@ __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, in
             mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
             bmx = fmaxf(bmx, __shfl_xor_sync(0xffffffffu, bmx, o2));
         }
+        double U = 0.0;
+        if (obj1) {
+            const int js = __shfl_sync(0xffffffffu, cd.js, src), nsr = __shfl_sync(0xffffffffu, cd.ns, src);
+            const int jr = __shfl_sync(0xffffffffu, cd.jr, src), nr = __shfl_sync(0xffffffffu, cd.nr, src);
+            const int fx = __shfl_sync(0xffffffffu, cd.fixed, src), s = __shfl_sync(0xffffffffu, cd.s, src);
+            U = unaffected_max(X, nsn, js, nsr, jr, nr, fx ? ldi(S.sn_rank + s) : -1);
+        }
         if (lane == 0) {
             // rounding of the piece sums: at most ceil(np / 32) + 5 additions deep
             const float depth = (float)((fnp + 31) / 32 + 5);
-            X.scr[fci] = make_float4(sum, 1.001f * (bsum + (depth + 32.0f) * kU * asum), mx, bmx);
+            X.scr[fci] = obj1 ? obj1_screen(mx, bmx, U)
+                              : make_float4(sum, 1.001f * (bsum + (depth + 32.0f) * kU * asum), mx, bmx);
             X.arrive[fci] = 0;
         }
+    }
+    // objective 1, single-chunk candidates
+    unsigned dm = __ballot_sync(0xffffffffu, direct);
+    while (dm) {
+        const int src = __ffs(dm) - 1;
+        dm &= dm - 1;
+        const int fci = __shfl_sync(0xffffffffu, ci, src);
+        const float fml = __shfl_sync(0xffffffffu, ml, src), fbml = __shfl_sync(0xffffffffu, bml, src);
+        const int js = __shfl_sync(0xffffffffu, cd.js, src), nsr = __shfl_sync(0xffffffffu, cd.ns, src);
+        const int jr = __shfl_sync(0xffffffffu, cd.jr, src), nr = __shfl_sync(0xffffffffu, cd.nr, src);
+        const int fx = __shfl_sync(0xffffffffu, cd.fixed, src), s = __shfl_sync(0xffffffffu, cd.s, src);
+        const double U = unaffected_max(X, nsn, js, nsr, jr, nr, fx ? ldi(S.sn_rank + s) : -1);
+        if (lane == 0) X.scr[fci] = obj1_screen(fml, fbml, U);
     }
 }
 
@@ -882,7 +913,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
     const double margin = C->margin, tau = C->tau;
     const int max_merges = C->max_merges;
     const bool prof = C->profile != 0;
-    const bool obj1 = (PREC == 0) && C->objective == 1;
+    const bool obj1 = C->objective == 1;
     const bool lead = (rank == 0 && tid == 0);
     int t = C->t, ns = C->n_super;
     double s_cur = C->s_cur;               // SMICE of the committed state
@@ -918,7 +949,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         const bool out = __fsub_rd(q.z, q.w) > __double2float_ru(margin);
                         X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
                         X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
-                        X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : s_cur + (double)q.x;
+                        X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : (obj1 ? 0.0 : s_cur) + (double)q.x;
                         X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
                         cand_features(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
                     }
@@ -957,7 +988,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         const int b0 = s_Rbase[lo], cnt = s_Rbase[lo + 1] - b0;
                         const int first = b0 / PPW, np = (b0 + cnt - 1) / PPW - first + 1;
                         score64_chunk(T, S, X, n, L, SP, g, active, lo, cd, q - b0, first, np, list, margin,
-                                      X.score, X.feas, false, flops);
+                                      X.score, X.feas, false, flops, obj1, ns);
                     }
                     if (lead) { C->rechecks += 1; C->recheck_cands += nR; }
                     if (!team_barrier(gb, C, G, epoch)) return;
@@ -986,7 +1017,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                             np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
                         }
                         score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin,
-                                      X.score, X.feas, false, flops);
+                                      X.score, X.feas, false, flops, obj1, ns);
                     }
                     if (!team_barrier(gb, C, G, epoch)) return;
                 }
@@ -1088,7 +1119,6 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 X.dec_r[t] = T.orig[cd.r];
                 X.dec_gap[t] = sel.gap;
                 X.dec_ncand[t] = nc;
-                if (obj1) X.dec_score[t] = ldd(X.score + sel.w);    // largest error of the chosen network
             }
             stamp(2);
             committed = true;
@@ -1343,7 +1373,8 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                     score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, margin,
                                   X.score, X.feas, prof, flops, obj1, ns);
                 else
-                    score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops);
+                    score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops,
+                                  obj1, ns);
             }
             if (prof && lane == 0 && my_chunks > 0) {      // per-warp sweep time: sum, count, largest
                 const unsigned long long d = gtimer() - w_start;
