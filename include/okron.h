@@ -89,7 +89,12 @@ typedef struct okr_params {
     int32_t record_iters;       /* keep every candidate's score for the first K iterations */
     int32_t max_merges;         /* >= 0 overrides the target; -1 = use target_reduction */
     int32_t profile;            /* 1 = count the search's arithmetic and time its sweep phase */
-    int32_t reserved;           /* must be 0 */
+    int32_t scorer_topk;        /* 0 = exhaustive; k > 0 = evaluate exactly only the k candidates the
+                                   learned scorer ranks best in each iteration (okr_scorer_init with
+                                   OKR_SCORER_FEATURES inputs first).  An iteration whose k candidates
+                                   are all infeasible is re-evaluated exhaustively.  The committed
+                                   candidate is always exactly evaluated; it may differ from the
+                                   exhaustive choice. */
     int64_t max_spins;          /* limit for device-side waits (0 = default) */
 } okr_params;
 
@@ -115,10 +120,14 @@ typedef struct okr_summary {
                                    FP64 recheck, merge, candidate setup, barrier, merge bookkeeping,
                                    list update, offsets, compaction, chunk map, barrier, sweep) */
     double kron_ms;             /* device time of the last okr_kron since the reduction (0 if none) */
+    int32_t scorer_fallbacks;   /* learned pruning: iterations re-evaluated exhaustively because the
+                                   scorer's k candidates were all infeasible */
+    int32_t pad;
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
- * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, max_spins 0. */
+ * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, scorer_topk 0,
+ * max_spins 0. */
 void okr_default_params(okr_params *p);
 
 /* Creates a context on CUDA device `device`.  stream: a cudaStream_t to run

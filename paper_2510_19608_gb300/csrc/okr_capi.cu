@@ -198,7 +198,9 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
     if (p->objective != 0 && p->objective != 1) return fail(ctx, OKR_EINVAL, "objective %d not supported", p->objective);
     if (p->precision != 0 && p->precision != 1) return fail(ctx, OKR_EINVAL, "precision %d not supported", p->precision);
     if (p->record_iters < 0) return fail(ctx, OKR_EINVAL, "record_iters < 0");
-    if (p->reserved != 0) return fail(ctx, OKR_EINVAL, "reserved must be 0");
+    if (p->scorer_topk < 0) return fail(ctx, OKR_EINVAL, "scorer_topk < 0");
+    if (p->scorer_topk > 0 && (!ctx || ctx->mb.F != kScorerFeatures))
+        return fail(ctx, OKR_EINVAL, "scorer_topk needs a scorer with %d features (okr_scorer_init)", kScorerFeatures);
     return OKR_OK;
 }
 
@@ -306,6 +308,14 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
     Search &X = ctx->fb.X;
     X.rec_iters = p->record_iters;
+    X.topk = p->scorer_topk;
+    if (X.topk > 0) {
+        X.mlp_theta = ctx->mb.theta;
+        X.mlp_w1 = reinterpret_cast<const uint16_t *>(ctx->mb.w1);
+        X.mlp_w2 = reinterpret_cast<const uint16_t *>(ctx->mb.w2);
+        X.mlp_w3 = reinterpret_cast<const uint16_t *>(ctx->mb.w3);
+        X.mlp_w4 = reinterpret_cast<const uint16_t *>(ctx->mb.w4);
+    }
     k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.S);
     ctx->launches += 1;
     CK(cudaGetLastError());
@@ -495,7 +505,7 @@ void okr_default_params(okr_params *p) {
     p->record_iters = 0;
     p->max_merges = -1;
     p->profile = 0;
-    p->reserved = 0;
+    p->scorer_topk = 0;
     p->max_spins = 0;
 }
 
@@ -831,6 +841,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         if (st != OKR_OK) return fail(ctx, st, "batch feeder %d: %s", f, ctx->err.c_str());
         if (!F->s_load) return fail(ctx, OKR_EINVAL, "batch feeder %d: s_load is NULL", f);
         if (P->record_iters != 0) return fail(ctx, OKR_EINVAL, "batch feeder %d: record_iters must be 0", f);
+        if (P->scorer_topk != 0) return fail(ctx, OKR_EINVAL, "batch feeder %d: scorer_topk must be 0", f);
         if (!valid_tree(F)) return fail(ctx, OKR_EINVAL, "batch feeder %d: invalid tree or phases", f);
         const int n = F->n_bus;
         std::vector<int> dep(n, 0);
@@ -1167,6 +1178,8 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
     out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
     out->kron_ms = ctx->kron_ms;
+    out->scorer_fallbacks = c.scorer_fallbacks;
+    out->pad = 0;
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
     for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;

@@ -114,7 +114,7 @@ struct Ctrl {
     int rechecks;           // iterations that needed an FP64 recheck
     int recheck_cands;      // candidates rechecked in FP64 over the run
     int objective;          // 0 SMICE (Algorithm 1), 1 largest error of the candidate network
-    int pad_obj;
+    int scorer_fallbacks;   // learned pruning: iterations re-evaluated exhaustively
     double margin;          // voltage-error bound (p.u.)
     double tau;             // tie band
     double s_cur;           // SMICE of the current state
@@ -156,6 +156,12 @@ struct Search {
     double *rec_score;
     double *rec_bound;      // [rec_iters][2n] bound of the recorded score (0 for FP64)
     float *rec_feat;        // [rec_iters][2n][kScorerFeatures] scorer features of the recorded candidates
+    // learned pruning (topk > 0): the scorer's parameters (FP32 biases in mlp_theta,
+    // bfloat16 bit patterns of the weight matrices) and a prediction per candidate slot
+    int topk;
+    const float *mlp_theta;
+    const uint16_t *mlp_w1, *mlp_w2, *mlp_w3, *mlp_w4;
+    float *pred;            // [2n]
     int *rec_count;
 };
 

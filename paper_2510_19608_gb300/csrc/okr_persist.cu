@@ -352,6 +352,121 @@ __device__ __forceinline__ void seg_scan_setup(bool active, int ci, int lane, un
     last = (lane == 31) || ((heads >> (lane + 1)) & 1u);
 }
 
+// ---------------------------------------------------------------- learned pruning
+// The scorer's weights in shared memory (bfloat16 bit patterns; biases FP32).
+constexpr int kMlpH = 128;
+struct MlpSmem {
+    uint16_t w2[kMlpH * kMlpH], w3[kMlpH * kMlpH], w1[kScorerFeatures * kMlpH], w4[kMlpH];
+    float b1[kMlpH], b2[kMlpH], b3[kMlpH], b4;
+    float feat[kThreads / 32][16];          // per-warp feature scratch
+};
+
+__device__ __forceinline__ float bf16f(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
+
+// Order-preserving key of a float (smaller key = smaller value).
+__device__ __forceinline__ unsigned fkey(float x) {
+    const unsigned u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ void mlp_load_smem(const Search &X, MlpSmem *W) {
+    const int F = kScorerFeatures;
+    const float *th = X.mlp_theta;
+    const int o_b1 = F * kMlpH, o_b2 = o_b1 + kMlpH + kMlpH * kMlpH, o_b3 = o_b2 + kMlpH + kMlpH * kMlpH;
+    const int o_b4 = o_b3 + kMlpH + kMlpH;
+    for (int e = threadIdx.x; e < kMlpH * kMlpH; e += blockDim.x) {
+        W->w2[e] = X.mlp_w2[e];
+        W->w3[e] = X.mlp_w3[e];
+    }
+    for (int e = threadIdx.x; e < F * kMlpH; e += blockDim.x) W->w1[e] = X.mlp_w1[e];
+    for (int e = threadIdx.x; e < kMlpH; e += blockDim.x) {
+        W->w4[e] = X.mlp_w4[e];
+        W->b1[e] = th[o_b1 + e];
+        W->b2[e] = th[o_b2 + e];
+        W->b3[e] = th[o_b3 + e];
+    }
+    if (threadIdx.x == 0) W->b4 = th[o_b4];
+}
+
+// One candidate's prediction by one warp (the same products, in the same order,
+// as the training kernels' forward pass).  f: the warp's feature scratch.
+__device__ float mlp_predict_warp(const MlpSmem *W, const float *f) {
+    const int lane = threadIdx.x & 31;
+    float h[4], g[4];
+    for (int m = 0; m < 4; ++m) {
+        const int j = lane + 32 * m;
+        float z = W->b1[j];
+        for (int k = 0; k < kScorerFeatures; ++k) z = fmaf(f[k], bf16f(W->w1[k * kMlpH + j]), z);
+        h[m] = fmaxf(z, 0.0f);
+    }
+    for (int layer = 0; layer < 2; ++layer) {
+        const uint16_t *w = layer == 0 ? W->w2 : W->w3;
+        const float *bias = layer == 0 ? W->b2 : W->b3;
+        for (int m = 0; m < 4; ++m) g[m] = bias[lane + 32 * m];
+        for (int ms = 0; ms < 4; ++ms)
+            for (int sl = 0; sl < 32; ++sl) {
+                const float hk = __shfl_sync(0xffffffffu, h[ms], sl);
+                const int k = ms * 32 + sl;
+                for (int m = 0; m < 4; ++m) g[m] = fmaf(hk, bf16f(w[k * kMlpH + lane + 32 * m]), g[m]);
+            }
+        for (int m = 0; m < 4; ++m) h[m] = fmaxf(g[m], 0.0f);
+    }
+    float acc = h[0] * bf16f(W->w4[lane]) + h[1] * bf16f(W->w4[lane + 32]) + h[2] * bf16f(W->w4[lane + 64]) +
+                h[3] * bf16f(W->w4[lane + 96]);
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return acc + W->b4;
+}
+
+// Key of the k-th smallest prediction over the candidate slots (radix select,
+// four 8-bit digits; every CTA computes it).  Returns ~0u when k >= nc.
+__device__ unsigned topk_threshold(const Search &X, int nslots, int k, int nc) {
+    if (k >= nc) return ~0u;
+    __shared__ unsigned hist[256];
+    __shared__ unsigned s_prefix, s_need;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) { s_prefix = 0u; s_need = (unsigned)k; }
+    unsigned mask = 0u;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 24 - 8 * pass;
+        for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0u;
+        __syncthreads();
+        const unsigned prefix = s_prefix;
+        for (int i = tid; i < nslots; i += blockDim.x) {
+            const unsigned key = fkey(__ldcg(X.pred + i));
+            if ((key & mask) == prefix) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        if (tid < 32) {                             // the digit holding the need-th key
+            unsigned c[8], tot = 0u;
+            for (int q = 0; q < 8; ++q) { c[q] = hist[lane * 8 + q]; tot += c[q]; }
+            unsigned incl = tot;
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned excl = incl - tot, need = s_need;
+            const bool mine = excl < need && need <= incl;
+            if (mine) {
+                unsigned cum = excl;
+                int b = 0;
+                for (int q = 0; q < 8; ++q) {
+                    if (cum + c[q] >= need) { b = q; break; }
+                    cum += c[q];
+                }
+                s_prefix = prefix | ((unsigned)(lane * 8 + b) << shift);
+                s_need = need - cum;
+            }
+        }
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    return s_prefix;
+}
+
+__device__ __forceinline__ bool slot_selected(const Search &X, const Cand &c, unsigned theta) {
+    return theta == ~0u || fkey(__ldcg(X.pred + c.pad)) <= theta;
+}
+
 // Objective 1: the largest MICE among the clusters a candidate leaves unchanged,
 // i.e. over the super-node ranks outside [js, js+ns), [jr, jr+nr) and, when s is
 // the common ancestor, s's own rank.  Whole blocks of 32 ranks come from bmax,
@@ -381,13 +496,14 @@ __device__ __forceinline__ double unaffected_max(const Search &X, int nsn, int j
 __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
                               double margin, double *out_score, int *out_feas, bool prof, double &flops,
-                              bool obj1 = false, int nsn = 0) {
+                              bool obj1 = false, int nsn = 0, unsigned theta = ~0u) {
     // one lane per phase (SP == 4), the scenarios in turn inside the lane
     const int lane = threadIdx.x & 31, p = lane & 3;
+    const bool chosen = !active || slot_selected(X, cd, theta);    // learned pruning
     int k = cd.r;
     bool sside = false;
-    if (active) k = position_bus(list, cd, q, sside);
-    const bool valid = active && k != cd.r;
+    if (active && chosen) k = position_bus(list, cd, q, sside);
+    const bool valid = active && chosen && k != cd.r;
     const int kk = k < 0 ? cd.s : k;
     double dl = 0.0, ml = 0.0;
     for (int l = 0; l < L; ++l) {
@@ -422,7 +538,10 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
     }
     bool fin = false, direct = false;
     if (active && last) {
-        if (np == 1) {                      // the whole candidate lies in this chunk
+        if (!chosen) {                      // pruned: never the winner (the same value from every chunk)
+            out_score[ci] = INFINITY;
+            out_feas[ci] = 0;
+        } else if (np == 1) {               // the whole candidate lies in this chunk
             if (obj1) {
                 direct = true;
             } else {
@@ -500,15 +619,16 @@ __device__ __forceinline__ float4 obj1_screen(float ml, float bml, double U) {
 
 __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
-                              bool prof, double &flops, bool obj1 = false, int nsn = 0) {
+                              bool prof, double &flops, bool obj1 = false, int nsn = 0, unsigned theta = ~0u) {
     // one lane per phase (SP == 4), the scenarios in turn inside the lane
     const int lane = threadIdx.x & 31, p = lane & 3;
+    const bool chosen = !active || slot_selected(X, cd, theta);    // learned pruning
     int k = cd.r;
     bool sside = false;
-    if (active) k = position_bus(list, cd, q, sside);
-    const bool valid = active && k != cd.r;
+    if (active && chosen) k = position_bus(list, cd, q, sside);
+    const bool valid = active && chosen && k != cd.r;
     const int kk = k < 0 ? cd.s : k;
-    const unsigned phr = T.ph[cd.r];
+    const unsigned phr = active ? T.ph[cd.r] : 0u;
     float fl = 0.0f;
     float dl = 0.0f, bl = 0.0f, ad = 0.0f, ml = 0.0f, bml = 0.0f;
     for (int l = 0; l < L; ++l) {
@@ -554,7 +674,9 @@ __device__ void score32_chunk(const Topo &T, const State &S, const Search &X, in
     bool fin = false, direct = false;
     if (active && last) {
         const float pb = bl + 32.0f * kU * ad;
-        if (np == 1) {                      // the whole candidate lies in this chunk
+        if (!chosen) {                      // pruned: surely infeasible for the selection
+            X.scr[ci] = make_float4(0.0f, 0.0f, INFINITY, 0.0f);
+        } else if (np == 1) {               // the whole candidate lies in this chunk
             if (obj1) direct = true;
             else X.scr[ci] = make_float4(dl, 1.001f * (pb + 38.0f * kU * fabsf(dl)), ml, bml);
         } else {
@@ -922,7 +1044,14 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
     int2 my_ex = make_int2(0, 0);          // this thread's offsets inside its CTA
     double flops = 0.0;
     int nw_commit = 0;                     // warps that held items of the last commit
+    unsigned theta = ~0u;                  // learned pruning: key of the k-th best prediction (~0: none)
     if (t >= max_merges || C->done) return;
+    extern __shared__ unsigned char dyn_smem[];
+    MlpSmem *MW = X.topk > 0 ? reinterpret_cast<MlpSmem *>(dyn_smem) : nullptr;
+    if (MW) {
+        mlp_load_smem(X, MW);
+        __syncthreads();
+    }
 
     for (;;) {
         // ============================================================ phase 1
@@ -1017,7 +1146,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                             np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
                         }
                         score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin,
-                                      X.score, X.feas, false, flops, obj1, ns);
+                                      X.score, X.feas, false, flops, obj1, ns, theta);
                     }
                     if (!team_barrier(gb, C, G, epoch)) return;
                 }
@@ -1036,6 +1165,32 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 }
                 sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
                 stamp(PREC == 0 ? 0 : 1);
+            }
+            if (theta != ~0u && sel.w < 0) {
+                // learned pruning left no feasible candidate: evaluate them all in FP64
+                const int *list = S.sn_list[t & 1];
+                for (int g = warp; g < nchunks; g += nwarps) {
+                    const int c0 = ldi(X.chunk_first + g);
+                    const int q = g * PPW + lane / SP;
+                    const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
+                    const int off = chunk_offset(cb, g * PPW, PPW, lane / SP);
+                    const int cbase = __shfl_sync(0xffffffffu, cb, off);
+                    const int c = c0 + off;
+                    const bool active = q < P;
+                    Cand cd;
+                    cd.r = -1;
+                    int first = 0, np = 1;
+                    if (active) {
+                        cd = ldcand(X.cand + c);
+                        first = cbase / PPW;
+                        np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
+                    }
+                    score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin, X.score,
+                                  X.feas, false, flops, obj1, ns, ~0u);
+                }
+                if (!team_barrier(gb, C, G, epoch)) return;
+                sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
+                if (lead) C->scorer_fallbacks += 1;
             }
             if (lead && t < X.rec_iters) X.rec_count[t] = nc;
             if (sel.w == -2) {                          // unreachable: the minimum lies in the band
@@ -1281,8 +1436,9 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 if (gt >= 1 && gt < ns) {
                     int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
                     for (int d = 0; d < 2; ++d) {
-                        const Cand c = X.slot[2 * gt + d];
+                        Cand c = X.slot[2 * gt + d];
                         if (c.s < 0) continue;
+                        c.pad = 2 * gt + d;                 // the candidate's slot (its prediction)
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;
@@ -1297,8 +1453,9 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 int ci = pref.x + my_ex.x, pos = pref.y + my_ex.y, li = my_ex.x;
                 for (int j = jb; j < je; ++j)
                     for (int d = 0; d < 2; ++d) {
-                        const Cand c = X.slot[2 * j + d];
+                        Cand c = X.slot[2 * j + d];
                         if (c.s < 0) continue;
+                        c.pad = 2 * j + d;
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;
@@ -1334,6 +1491,23 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 X.chunk_first[g] = pref.x + lo;
             }
         }
+        if (MW) {
+            // the scorer's prediction for every candidate slot (slots are readable
+            // since barrier 1), warps of the CTAs that compact taking the last slots
+            const int nsl = 2 * ns, wl = tid >> 5;
+            const int mw = (warp + nwarps - min(32, nwarps)) % nwarps;
+            for (int sl = mw; sl < nsl; sl += nwarps) {
+                const Cand c = ldcand(X.slot + sl);
+                float y = INFINITY;
+                if (c.s >= 0) {
+                    if (lane == 0) cand_features(T, S, n, L, c, margin, MW->feat[wl]);
+                    __syncwarp();
+                    y = mlp_predict_warp(MW, MW->feat[wl]);
+                    __syncwarp();
+                }
+                if (lane == 0) X.pred[sl] = y;
+            }
+        }
         if (lead) {
             X.base[nc] = P;
             C->n_cand = nc;
@@ -1346,6 +1520,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         stamp(6);
 
         // ============================================================ phase 3
+        theta = MW ? topk_threshold(X, 2 * ns, X.topk, nc) : ~0u;
         {
             const int *list_new = S.sn_list[t & 1];
             unsigned long long t_start = 0, w_start = 0;
@@ -1371,10 +1546,10 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 }
                 if (PREC == 0)
                     score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, margin,
-                                  X.score, X.feas, prof, flops, obj1, ns);
+                                  X.score, X.feas, prof, flops, obj1, ns, theta);
                 else
                     score32_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list_new, prof, flops,
-                                  obj1, ns);
+                                  obj1, ns, theta);
             }
             if (prof && lane == 0 && my_chunks > 0) {      // per-warp sweep time: sum, count, largest
                 const unsigned long long d = gtimer() - w_start;
@@ -1453,7 +1628,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_search_batch(const BatchFeeder 
 cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st) {
     void *args[] = {&T, &S, &X, &C, &gb};
     const void *fn = precision == 1 ? (const void *)k_search<1> : (const void *)k_search<0>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, 0, st);
+    const size_t smem = X.topk > 0 ? sizeof(MlpSmem) : 0;    // the scorer's weights for learned pruning
+    if (smem) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, st);
 }
 
 int search_blocks_per_sm() {

@@ -100,3 +100,63 @@ def test_learned_ranking_beats_chance_on_held_out_feeders(ctx):
     Xt, _, groups = scorer.collect(ctx, test_runs, record_iters=40)
     q = scorer.miss_rate(ctx, Xt, groups, ks=(64,))
     assert q["winner_rank_percentile"] < 0.25               # chance: 0.5
+
+
+# ----------------------------------------------------------------------------- learned pruning in the search
+def _props_of_network(ctx, f, margin):
+    """A pruned run's network: the reported voltages are the oracle's evaluation
+    of its assignment, its largest error is within the margin and equals the
+    reported one, and the reported SMICE is recomputed from those voltages."""
+    from oracle import oracle as O
+    sup = ctx.assignment()
+    err_o, vred_o = O.evaluate(f, sup)
+    _, vr = ctx.voltages()
+    s = ctx.summary()
+    assert np.abs(vr - vred_o).max() <= 1e-9
+    assert err_o.max() <= margin + 1e-12 and abs(err_o.max() - s["max_error"]) <= 1e-11
+    vh, _ = ctx.voltages()
+    pres = np.array([[(int(f.phases[i]) >> p) & 1 for p in range(3)] for i in range(f.n_bus)], bool)
+    e = np.where(pres[None], np.abs(np.abs(vh) - np.abs(vr)), 0.0)
+    smice = sum(float(e[l][sup == k].max()) for l in range(e.shape[0]) for k in np.unique(sup))
+    assert abs(s["smice"] - smice) <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_pruning_with_k_above_the_candidate_count_is_exhaustive(ctx, precision):
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import scorer
+    f, run = fg.preset("feeder1000", n_bus=300)
+    ctx.scorer_init(14, scorer.init_params(14, 3))            # any weights: every candidate is kept
+    p = dict(margin=run["margin"], target_reduction=0.5, precision=precision)
+    ctx.reduce(f, K.default_params(**p))
+    ref = ctx.decisions()
+    ctx.reduce(f, K.default_params(scorer_topk=100000, **p))
+    got = ctx.decisions()
+    assert np.array_equal(got["s"], ref["s"]) and np.array_equal(got["r"], ref["r"])
+    assert np.abs(got["score"] - ref["score"]).max() <= 1e-12
+
+
+@pytest.mark.parametrize("precision,topk", [(1, 16), (0, 16), (1, 1)])
+def test_pruned_search_yields_a_valid_network(ctx, precision, topk):
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import scorer
+    runs = [(fg.make_feeder(250, 10000 + k, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0)),
+             K.default_params(margin=0.005, target_reduction=0.5)) for k in range(3)]
+    X, T, _ = scorer.collect(ctx, runs, record_iters=30)
+    scorer.train(ctx, X, T, epochs=6, batch=2048, lr=1e-3, seed=1)
+    f, run = fg.preset("feeder1000", n_bus=300)
+    ctx.reduce(f, K.default_params(margin=run["margin"], target_reduction=0.5, precision=precision, scorer_topk=topk))
+    s = ctx.summary()
+    assert s["n_iter"] == 150 or s["stop_reason"] == 1
+    _props_of_network(ctx, f, run["margin"])
+    dec = ctx.decisions()
+    assert np.all(dec["maxerr"] <= run["margin"] + 1e-12)
+
+
+def test_pruning_needs_a_scorer_of_the_right_width(ctx):
+    import paper_2510_19608_gb300 as K
+    f, _ = fg.preset("feeder40")
+    ctx.scorer_init(12)
+    with pytest.raises(K.OkrError) as e:
+        ctx.reduce(f, K.default_params(scorer_topk=8))
+    assert e.value.status == 1
