@@ -270,13 +270,33 @@ def learned_line(K, ctx, n_train=64, record=64):
     t0 = time.perf_counter()
     q = scorer.miss_rate(ctx, Xt, groups, ks=(16, 64, 256), T=Tt, margin=run3["margin"])
     t_eval = time.perf_counter() - t0
+    # the search with learned pruning against the exhaustive search, full runs
+    pruned = {}
+    for name in ("feeder3100", "feeder2200", WORKLOAD):
+        fx, rx = fg.preset(name)
+        rows = {}
+        for k in (0, 64, 16):
+            px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=1, scorer_topk=k)
+            ctx.reduce(fx, px)                                        # warm-up
+            times = []
+            for _ in range(3):
+                t0 = time.perf_counter()
+                ctx.reduce(fx, px)
+                times.append(time.perf_counter() - t0)
+            sm = ctx.summary()
+            rows["exhaustive" if k == 0 else f"top{k}"] = {
+                "ms": 1e3 * statistics.median(times), "search_ms": sm["search_ms"], "merges": sm["n_iter"],
+                "stop_reason": sm["stop_reason"], "smice": sm["smice"], "max_error": sm["max_error"],
+                "fallbacks": sm["scorer_fallbacks"]}
+        pruned[name] = rows
     return {"train_feeders": n_train, "iterations_per_feeder": record, "samples": int(X.shape[0]),
             "epochs": len(loss), "loss_first_last": [float(loss[0]), float(loss[-1])],
             "collect_s": t_collect, "train_s": t_train, "train_samples_per_s": len(loss) * X.shape[0] / t_train,
             "eval": {"workload": "feeder3100, first %d iterations" % record, "candidates": int(Xt.shape[0]),
                      "predict_and_rank_s": t_eval,
                      "top_k": {str(k): v for k, v in q.items() if isinstance(k, int)},
-                     "winner_rank_percentile": q["winner_rank_percentile"]}}
+                     "winner_rank_percentile": q["winner_rank_percentile"]},
+            "pruned_search": pruned}
 
 
 def sweeps_line(K, ctx):
