@@ -95,8 +95,27 @@ typedef struct okr_params {
                                    are all infeasible is re-evaluated exhaustively.  The committed
                                    candidate is always exactly evaluated; it may differ from the
                                    exhaustive choice. */
-    int64_t max_spins;          /* limit for device-side waits (0 = default) */
+    int32_t engine;             /* how the candidates are scored (all give the same decisions):
+                                   OKR_ENGINE_AUTO (0): incremental when objective = 0, precision = 0
+                                     and scorer_topk = 0, otherwise the sweep;
+                                   OKR_ENGINE_SWEEP (1): every iteration evaluates every candidate
+                                     afresh (one persistent launch over all SMs; precision 0 or 1);
+                                   OKR_ENGINE_INCREMENTAL (2): every candidate's FP64 score is carried
+                                     from one iteration to the next and only the terms whose inputs
+                                     the last merge changed are evaluated again (exact: the score is a
+                                     fixed-point sum of FP64 terms); one CTA per feeder.  Needs
+                                     objective 0, precision 0 and scorer_topk 0 (else OKR_EINVAL);
+                                     record_iters records scores but not scorer features;
+                                   OKR_ENGINE_VERIFY (3): as 2, and after every merge every candidate
+                                     is also evaluated afresh and compared bit for bit with its
+                                     carried score (okr_summary.inc_mismatches; for tests). */
+    int64_t max_spins;          /* limit for device-side waits (0 = default; the sweep engine) */
 } okr_params;
+
+#define OKR_ENGINE_AUTO 0
+#define OKR_ENGINE_SWEEP 1
+#define OKR_ENGINE_INCREMENTAL 2
+#define OKR_ENGINE_VERIFY 3
 
 typedef struct okr_summary {
     int32_t n_bus, n_scen;
@@ -116,18 +135,25 @@ typedef struct okr_summary {
     double flops;               /* algorithmic floating-point operations of the search */
     int32_t rechecks;           /* precision 1: iterations that rescored candidates in FP64 */
     int32_t recheck_cands;      /* precision 1: candidates rescored in FP64 over the run */
-    double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration (selection,
-                                   FP64 recheck, merge, candidate setup, barrier, merge bookkeeping,
-                                   list update, offsets, compaction, chunk map, barrier, sweep) */
+    double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration.  Sweep engine:
+                                   selection, FP64 recheck, merge, candidate setup, barrier, merge
+                                   bookkeeping, list update, offsets, compaction, chunk map, barrier,
+                                   sweep.  Incremental engine: selection, changed set, terms before
+                                   the merge, merge, rebuilt candidates, terms after the merge */
     double kron_ms;             /* device time of the last okr_kron since the reduction (0 if none) */
     int32_t scorer_fallbacks;   /* learned pruning: iterations re-evaluated exhaustively because the
                                    scorer's k candidates were all infeasible */
+    int32_t inc_mismatches;     /* OKR_ENGINE_VERIFY: carried scores that differed from a fresh
+                                   evaluation, summed over the merges (0 when correct) */
+    int32_t engine;             /* engine that ran: OKR_ENGINE_SWEEP or OKR_ENGINE_INCREMENTAL */
     int32_t pad;
+    int64_t terms;              /* incremental engine: (candidate, cluster) terms evaluated over the
+                                   run, the initial evaluation included (profile mode; 0 otherwise) */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
  * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, scorer_topk 0,
- * max_spins 0. */
+ * engine OKR_ENGINE_AUTO, max_spins 0. */
 void okr_default_params(okr_params *p);
 
 /* Creates a context on CUDA device `device`.  stream: a cudaStream_t to run

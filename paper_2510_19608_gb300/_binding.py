@@ -37,7 +37,7 @@ class Params(C.Structure):
     _fields_ = [("margin", C.c_double), ("target_reduction", C.c_double), ("tie_tol", C.c_double),
                 ("objective", C.c_int32), ("precision", C.c_int32), ("record_iters", C.c_int32),
                 ("max_merges", C.c_int32), ("profile", C.c_int32), ("scorer_topk", C.c_int32),
-                ("max_spins", C.c_int64)]
+                ("engine", C.c_int32), ("max_spins", C.c_int64)]
 
 
 class Summary(C.Structure):
@@ -46,7 +46,8 @@ class Summary(C.Structure):
                 ("smice", C.c_double), ("max_error", C.c_double), ("launches", C.c_int64),
                 ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double),
                 ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 16),
-                ("kron_ms", C.c_double), ("scorer_fallbacks", C.c_int32), ("pad", C.c_int32)]
+                ("kron_ms", C.c_double), ("scorer_fallbacks", C.c_int32), ("inc_mismatches", C.c_int32),
+                ("engine", C.c_int32), ("pad", C.c_int32), ("terms", C.c_int64)]
 
 
 class BatchItem(C.Structure):

@@ -47,6 +47,7 @@ struct okr_ctx {
     // counters of the last call
     int64_t launches = 0;
     double search_ms = 0.0;
+    int last_engine = 0;                // OKR_ENGINE_SWEEP or OKR_ENGINE_INCREMENTAL
 
     // Y_Kron work (allocated on the first okr_kron call)
     KronWork kw{};
@@ -201,7 +202,19 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
     if (p->scorer_topk < 0) return fail(ctx, OKR_EINVAL, "scorer_topk < 0");
     if (p->scorer_topk > 0 && (!ctx || ctx->mb.F != kScorerFeatures))
         return fail(ctx, OKR_EINVAL, "scorer_topk needs a scorer with %d features (okr_scorer_init)", kScorerFeatures);
+    if (p->engine < OKR_ENGINE_AUTO || p->engine > OKR_ENGINE_VERIFY)
+        return fail(ctx, OKR_EINVAL, "engine %d not supported", p->engine);
+    if (p->engine >= OKR_ENGINE_INCREMENTAL && (p->objective != 0 || p->precision != 0 || p->scorer_topk != 0))
+        return fail(ctx, OKR_EINVAL, "the incremental engine needs objective 0, precision 0 and scorer_topk 0");
     return OKR_OK;
+}
+
+// The engine a valid parameter set runs: OKR_ENGINE_SWEEP or OKR_ENGINE_INCREMENTAL.
+int resolve_engine(const okr_params *p) {
+    if (p->engine == OKR_ENGINE_SWEEP) return OKR_ENGINE_SWEEP;
+    if (p->engine >= OKR_ENGINE_INCREMENTAL) return OKR_ENGINE_INCREMENTAL;
+    return (p->objective == 0 && p->precision == 0 && p->scorer_topk == 0) ? OKR_ENGINE_INCREMENTAL
+                                                                          : OKR_ENGINE_SWEEP;
 }
 
 int merges_for(int n, const okr_params *p) {
@@ -303,7 +316,11 @@ int positions_per_chunk(int L) { return 32 / (4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4)
 // Initial state, then the persistent search kernel.  The kernel stops by itself
 // (target reached or nothing feasible); if one sweep needs more work buffer than
 // allocated it saves its state and exits, and is relaunched with a larger one.
+okr_status run_search_inc(okr_ctx *ctx, const okr_params *p);
+
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
+    ctx->last_engine = resolve_engine(p);
+    if (ctx->last_engine == OKR_ENGINE_INCREMENTAL) return run_search_inc(ctx, p);
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
     Search &X = ctx->fb.X;
@@ -377,6 +394,72 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     cudaEventDestroy(e1);
     if (s != OKR_OK) return s;
     if (c.err == 6) return fail(ctx, OKR_ETIMEOUT, "a grid barrier of the search gave up after %lld polls", c.max_spins);
+    if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
+    if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
+    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, ctx->fb.vred_out,
+                                                                                ctx->fb.super_out, ctx->fb.vhat_out);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    ctx->last = *ctx->C_host;
+    return OKR_OK;
+}
+
+// Initial state, then one CTA runs the whole search with carried scores
+// (okr_incr.cu); then the export.
+okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
+    cudaStream_t st = ctx->stream;
+    const int n = ctx->fb.T.n, L = ctx->fb.T.L;
+    Search &X = ctx->fb.X;
+    X.rec_iters = p->record_iters;
+    X.topk = 0;
+    k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.S);
+    ctx->launches += 1;
+    CK(cudaGetLastError());
+    const int mm = merges_for(n, p);
+    Ctrl c{};
+    c.max_merges = mm;
+    c.done = (mm == 0);
+    c.margin = p->margin;
+    c.tau = p->tie_tol;
+    c.profile = p->profile ? 1 : 0;
+    c.n_super = n;
+    c.precision = 0;
+    c.objective = 0;
+    c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
+    CK(cudaMemcpyAsync(ctx->fb.C, &c, sizeof c, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(X.dec_maxerr, 0, sizeof(double) * n, st));
+    if (p->record_iters > 0) {
+        CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
+        CK(cudaMemsetAsync(X.rec_feat, 0, sizeof(float) * (size_t)p->record_iters * 2 * n * kScorerFeatures, st));
+    }
+    ctx->rec_iters = p->record_iters;
+    ctx->search_ms = 0.0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    cudaEventRecord(e0, st);
+    cudaError_t e = launch_search_inc(ctx->fb.T, ctx->fb.S, X, ctx->fb.I, ctx->fb.C,
+                                      p->engine == OKR_ENGINE_VERIFY ? 1 : 0, st);
+    cudaEventRecord(e1, st);
+    ctx->launches += 1;
+    okr_status s = OKR_OK;
+    if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e));
+    if (s == OKR_OK) {
+        e = cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "search: %s", cudaGetErrorString(e));
+    }
+    if (s == OKR_OK) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ctx->search_ms = ms;
+        c = *ctx->C_host;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != OKR_OK) return s;
     if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
     if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
     k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, ctx->fb.vred_out,
@@ -506,6 +589,7 @@ void okr_default_params(okr_params *p) {
     p->max_merges = -1;
     p->profile = 0;
     p->scorer_topk = 0;
+    p->engine = OKR_ENGINE_AUTO;
     p->max_spins = 0;
 }
 
@@ -1000,6 +1084,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         D.S = B.S;
         D.X = B.X;
         D.X.rec_iters = 0;
+        D.I = B.I;
         D.C = B.C;
         D.setup_err = B.err_dev;
         D.super_out = B.super_out;
@@ -1015,15 +1100,18 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         cc.objective = P->objective;
         cc.max_spins = P->max_spins > 0 ? P->max_spins : kDefaultSpins;
     }
-    // largest expected work first, FP64 feeders in their own list
-    std::vector<int> ord[2];
-    for (int f = 0; f < nf; ++f) ord[params[n_params == 1 ? 0 : f].precision].push_back(f);
-    for (int g = 0; g < 2; ++g)
+    // largest expected work first; lists: sweep FP64, sweep mixed precision, incremental
+    std::vector<int> ord[3];
+    for (int f = 0; f < nf; ++f) {
+        const okr_params *P = &params[n_params == 1 ? 0 : f];
+        ord[resolve_engine(P) == OKR_ENGINE_INCREMENTAL ? 2 : P->precision].push_back(f);
+    }
+    for (int g = 0; g < 3; ++g)
         std::stable_sort(ord[g].begin(), ord[g].end(), [&](int a, int b) {
             return (double)feeders[a].n_bus * merges[a] > (double)feeders[b].n_bus * merges[b];
         });
     int k = 0;
-    for (int g = 0; g < 2; ++g)
+    for (int g = 0; g < 3; ++g)
         for (int f : ord[g]) order_h[k++] = f;
     cudaStream_t st = ctx->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1035,9 +1123,14 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     CK(launch_batch_setup(nf, maxL, max_nn, bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
     CK(cudaEventRecord(e1, st));
     int ctas = 0;
-    for (int g = 0, first = 0; g < 2; first += (int)ord[g].size(), ++g) {
+    for (int g = 0, first = 0; g < 3; first += (int)ord[g].size(), ++g) {
         const int cnt = (int)ord[g].size();
         if (cnt == 0) continue;
+        if (g == 2) {                           // one CTA per feeder
+            ctas = std::max(ctas, cnt);
+            CK(launch_search_inc_batch(bf_d, order_d + first, cnt, st));
+            continue;
+        }
         const int nteams = std::min(cnt, ctx->num_sms * per_sm[g] / team);
         if (nteams < 1) return fail(ctx, OKR_EINVAL, "batched search: team of %d CTAs does not fit", team);
         const int grid = nteams * team;
@@ -1176,10 +1269,13 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->search_ms = ctx->search_ms;
     out->sweeps = ctx->last.iters;
     out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
-    out->flops = ctx->last.profile ? ctx->last.sweep_flops : 0.0;
+    out->flops = (ctx->last.profile && ctx->last_engine == OKR_ENGINE_SWEEP) ? ctx->last.sweep_flops : 0.0;
     out->kron_ms = ctx->kron_ms;
     out->scorer_fallbacks = c.scorer_fallbacks;
+    out->inc_mismatches = c.inc_mismatch;
+    out->engine = ctx->last_engine;
     out->pad = 0;
+    out->terms = (ctx->last_engine == OKR_ENGINE_INCREMENTAL && c.profile) ? (int64_t)c.sweep_flops : 0;
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
     for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;

@@ -119,6 +119,8 @@ struct Ctrl {
     double tau;             // tie band
     double s_cur;           // SMICE of the current state
     long long candidates;   // candidates evaluated over the run
+    int inc_mismatch;       // incremental search, verification mode: slots whose carried score differs
+    int pad2;
     long long max_spins;    // limit of a device-side wait
     double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
     unsigned long long sweep_ns;   // time in the sweep phase (profile mode, device timer)
@@ -130,6 +132,31 @@ struct GridBar {
     unsigned int count;     // arrivals since launch; barrier k completes at k * grid
     unsigned int pad;
 };
+
+// Incremental search (okr_incr.cu).  One work entry: the (candidate, cluster)
+// terms of one candidate slot that an iteration evaluates, as ranges of
+// super-node ranks.
+constexpr int kIncMaxSeg = 7;
+struct IncWork {
+    int slot;           // candidate slot 2 w + d (w = the lower super-node of the quotient edge)
+    int mode;           // 0: terms of changed clusters, ranks before the merge; 1: every term, ranks after
+    int nseg;
+    int pad;
+    int2 seg[kIncMaxSeg];   // rank ranges [x, y)
+};
+
+// Per-feeder buffers of the incremental search.
+struct Inc {
+    unsigned long long *acc;    // [2n][2] D(c) of each candidate slot, fixed point (low, high word)
+    int *viol;                  // [2n] (cluster, scenario) terms above the margin; kIncDead: no candidate
+    int *qpar;                  // [n] super-node holding the parent of the cluster's top (-1: slack's cluster)
+    int *fpair;                 // [n] slot pairs whose candidates are rebuilt after the merge
+    IncWork *work;              // [2n] work entries of one iteration
+    double *cbuf;               // [n * 10 L] the merge's new voltages, magnitudes and MICE
+    unsigned long long *vacc;   // [2n][2] verification: every term re-evaluated (engine 3)
+    int *vviol;                 // [2n]
+};
+constexpr int kIncDead = 1 << 30;
 
 struct Search {
     Cand *cand;             // [2n] compact candidate list

@@ -111,6 +111,7 @@ struct BatchFeeder {
     Topo T;
     State S;
     Search X;
+    Inc I;
     Ctrl *C;
     int *setup_err;             // nonzero: the setup failed, the search is skipped
     int *super_out;             // [n] assignment in caller numbering
@@ -132,5 +133,12 @@ int search_batch_blocks_per_sm(int precision);
 cudaError_t launch_search(int precision, int grid, Topo T, State S, Search X, Ctrl *C, GridBar *gb, cudaStream_t st);
 int search_blocks_per_sm();     // CTAs of the search kernel that fit one SM (0 on error)
 __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, double *vhat_out);
+
+// okr_incr.cu -- the search with scores carried across iterations: one CTA per
+// feeder (verify = 1: every merge also re-evaluates every candidate and counts
+// mismatches of the carried scores in C->inc_mismatch).
+cudaError_t launch_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st);
+// Many feeders: one CTA each, in the order given.
+cudaError_t launch_search_inc_batch(const BatchFeeder *fd, const int *order, int nf, cudaStream_t st);
 
 }  // namespace okr

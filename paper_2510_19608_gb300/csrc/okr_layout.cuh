@@ -26,6 +26,7 @@ struct FeederBufs {
     Topo T{};
     State S{};
     Search X{};
+    Inc I{};
     Ctrl *C = nullptr;
 };
 
@@ -154,6 +155,15 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     X.mlp_theta = nullptr;
     X.mlp_w1 = X.mlp_w2 = X.mlp_w3 = X.mlp_w4 = nullptr;
     c.take(f.C, 1);
+    Inc &I = f.I;
+    c.take(I.acc, 4 * N);
+    c.take(I.viol, 2 * N);
+    c.take(I.qpar, N);
+    c.take(I.fpair, N);
+    c.take(I.work, 2 * N);
+    c.take(I.cbuf, N * 10 * (size_t)L);
+    c.take(I.vacc, 4 * N);
+    c.take(I.vviol, 2 * N);
     if (chunks > 0) {
         c.take(X.chunk_first, (size_t)chunks);
         c.take(X.partial, (size_t)chunks + 2 * N);

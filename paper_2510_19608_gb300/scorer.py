@@ -50,7 +50,7 @@ def collect(ctx: "B.Context", runs, record_iters: int):
     o = 0
     for f, p in runs:
         q = B.default_params(margin=p.margin, target_reduction=p.target_reduction, max_merges=p.max_merges,
-                             tie_tol=p.tie_tol, precision=0, record_iters=record_iters)
+                             tie_tol=p.tie_tol, precision=0, record_iters=record_iters, engine=1)
         ctx.reduce(f, q)
         n_it = min(record_iters, ctx.summary()["n_iter"])
         for it in range(n_it):

@@ -39,6 +39,14 @@ def params(**kw):
     return K.default_params(**kw)
 
 
+# The three ways of scoring candidates; each must reproduce the oracle's decisions.
+ENGINES = {
+    "sweep-fp64": dict(engine=1, precision=0),
+    "sweep-mixed": dict(engine=1, precision=1),
+    "incremental": dict(engine=2, precision=0),
+}
+
+
 def oracle_run(f, margin, merges, record=0, mode="delta"):
     merges = min(merges, f.n_bus - 1)            # the library caps merges the same way
     vhat, ihat = O.operating_points(f)
@@ -86,14 +94,14 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("case", CASES, ids=[f"n{c[0]}-s{c[1]}-L{c[5]}" for c in CASES])
-def test_search_matches_oracle(ctx, case, precision):
+def test_search_matches_oracle(ctx, case, engine):
     n, seed, kv, mode, load, L, margin, target = case
     f = fg.make_feeder(n, seed, kv_ll=kv, phase_mode=mode, load=load, n_scen=L)
     merges = O.max_merges_for(n, target)
     res, vhat_o = oracle_run(f, margin, merges)
-    ctx.reduce(f, params(margin=margin, target_reduction=target, precision=precision))
+    ctx.reduce(f, params(margin=margin, target_reduction=target, **ENGINES[engine]))
     assert_same_run(ctx, res, vhat_o)
 
 
@@ -122,11 +130,12 @@ def test_screen_bounds_cover_the_fp64_scores(ctx):
         assert worst < 1.0
 
 
-def test_every_candidate_score_matches_oracle(ctx):
+@pytest.mark.parametrize("engine", ["sweep-fp64", "incremental"])
+def test_every_candidate_score_matches_oracle(ctx, engine):
     for f in (fg.preset("feeder40")[0], fg.make_feeder(200, 21, phase_mode=(0.7, 0.1, 0.2), load=("uniform", 100.0))):
         K = 6
         res, _ = oracle_run(f, 0.005, f.n_bus, record=K)
-        ctx.reduce(f, params(margin=0.005, record_iters=K))
+        ctx.reduce(f, params(margin=0.005, record_iters=K, **ENGINES[engine]))
         for t in range(min(K, res["n_iter"])):
             rec_o = res["recorded"][t]
             rec_g = ctx.recorded(t)
@@ -232,12 +241,12 @@ EDGE = {
 }
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("engine", sorted(ENGINES))
 @pytest.mark.parametrize("name", sorted(EDGE))
-def test_edge_feeders_match_oracle(ctx, name, precision):
+def test_edge_feeders_match_oracle(ctx, name, engine):
     f = EDGE[name]
     res, vhat_o = oracle_run(f, 0.01, f.n_bus)
-    ctx.reduce(f, params(margin=0.01, precision=precision))
+    ctx.reduce(f, params(margin=0.01, **ENGINES[engine]))
     if name == "unloaded":
         # every candidate scores exactly 0: all tied, the smallest (r, s) wins each time
         assert np.all(res["score"] == 0.0)
@@ -345,10 +354,10 @@ def feeder1000_oracle():
     return f, run, res, vhat_o
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_feeder1000_full_run_matches_oracle(ctx, feeder1000_oracle, precision):
+@pytest.mark.parametrize("engine", sorted(ENGINES))
+def test_feeder1000_full_run_matches_oracle(ctx, feeder1000_oracle, engine):
     f, run, res, vhat_o = feeder1000_oracle
-    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=precision))
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], **ENGINES[engine]))
     assert_same_run(ctx, res, vhat_o)
     _check_properties(ctx, f, run["margin"])
 
@@ -358,12 +367,12 @@ def test_large_feeders_prefix_and_properties(ctx, name):
     f, run = fg.preset(name)
     K = 12
     res, vhat_o = oracle_run(f, run["margin"], K)
-    for precision in (0, 1):
-        ctx.reduce(f, params(margin=run["margin"], max_merges=K, precision=precision))
+    for engine in sorted(ENGINES):
+        ctx.reduce(f, params(margin=run["margin"], max_merges=K, **ENGINES[engine]))
         assert_same_run(ctx, res, vhat_o)
-    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=1))
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], **ENGINES["sweep-mixed"]))
     full1 = ctx.decisions()
-    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], precision=0))
+    ctx.reduce(f, params(margin=run["margin"], target_reduction=run["target"], **ENGINES["incremental"]))
     full0 = ctx.decisions()
     assert np.array_equal(full0["s"], full1["s"]) and np.array_equal(full0["r"], full1["r"])
     s = ctx.summary()

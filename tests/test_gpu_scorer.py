@@ -76,7 +76,7 @@ def test_training_fits_a_smooth_function(ctx):
 def test_recorded_features(ctx):
     import paper_2510_19608_gb300 as K
     f, run = fg.preset("feeder40")
-    ctx.reduce(f, K.default_params(margin=run["margin"], precision=0, record_iters=3))
+    ctx.reduce(f, K.default_params(margin=run["margin"], precision=0, record_iters=3, engine=1))
     for it in range(3):
         rec = ctx.recorded(it)
         feat = ctx.recorded_features(it)
