@@ -96,15 +96,17 @@ typedef struct okr_params {
                                    candidate is always exactly evaluated; it may differ from the
                                    exhaustive choice. */
     int32_t engine;             /* how the candidates are scored (all give the same decisions):
-                                   OKR_ENGINE_AUTO (0): incremental when objective = 0, precision = 0
-                                     and scorer_topk = 0, otherwise the sweep;
+                                   OKR_ENGINE_AUTO (0): incremental when objective = 0 and
+                                     scorer_topk = 0, otherwise the sweep;
                                    OKR_ENGINE_SWEEP (1): every iteration evaluates every candidate
-                                     afresh (one persistent launch over all SMs; precision 0 or 1);
-                                   OKR_ENGINE_INCREMENTAL (2): every candidate's FP64 score is carried
+                                     afresh (one persistent launch over all SMs);
+                                   OKR_ENGINE_INCREMENTAL (2): every candidate's score is carried
                                      from one iteration to the next and only the terms whose inputs
-                                     the last merge changed are evaluated again (exact: the score is a
-                                     fixed-point sum of FP64 terms); one CTA per feeder.  Needs
-                                     objective 0, precision 0 and scorer_topk 0 (else OKR_EINVAL);
+                                     the last merge changed are evaluated again (exact: a carried
+                                     score is a fixed-point sum of its terms; precision 0 carries FP64
+                                     terms, precision 1 FP32 terms with a carried error bound and an
+                                     FP64 rescoring where the bound cannot decide); one CTA per feeder.
+                                     Needs objective 0 and scorer_topk 0 (else OKR_EINVAL);
                                      record_iters records scores but not scorer features;
                                    OKR_ENGINE_VERIFY (3): as 2, and after every merge every candidate
                                      is also evaluated afresh and compared bit for bit with its

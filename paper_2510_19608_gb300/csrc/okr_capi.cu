@@ -204,8 +204,8 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
         return fail(ctx, OKR_EINVAL, "scorer_topk needs a scorer with %d features (okr_scorer_init)", kScorerFeatures);
     if (p->engine < OKR_ENGINE_AUTO || p->engine > OKR_ENGINE_VERIFY)
         return fail(ctx, OKR_EINVAL, "engine %d not supported", p->engine);
-    if (p->engine >= OKR_ENGINE_INCREMENTAL && (p->objective != 0 || p->precision != 0 || p->scorer_topk != 0))
-        return fail(ctx, OKR_EINVAL, "the incremental engine needs objective 0, precision 0 and scorer_topk 0");
+    if (p->engine >= OKR_ENGINE_INCREMENTAL && (p->objective != 0 || p->scorer_topk != 0))
+        return fail(ctx, OKR_EINVAL, "the incremental engine needs objective 0 and scorer_topk 0");
     return OKR_OK;
 }
 
@@ -213,8 +213,7 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
 int resolve_engine(const okr_params *p) {
     if (p->engine == OKR_ENGINE_SWEEP) return OKR_ENGINE_SWEEP;
     if (p->engine >= OKR_ENGINE_INCREMENTAL) return OKR_ENGINE_INCREMENTAL;
-    return (p->objective == 0 && p->precision == 0 && p->scorer_topk == 0) ? OKR_ENGINE_INCREMENTAL
-                                                                          : OKR_ENGINE_SWEEP;
+    return (p->objective == 0 && p->scorer_topk == 0) ? OKR_ENGINE_INCREMENTAL : OKR_ENGINE_SWEEP;
 }
 
 int merges_for(int n, const okr_params *p) {
@@ -425,7 +424,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     c.tau = p->tie_tol;
     c.profile = p->profile ? 1 : 0;
     c.n_super = n;
-    c.precision = 0;
+    c.precision = p->precision;
     c.objective = 0;
     c.max_spins = p->max_spins > 0 ? p->max_spins : kDefaultSpins;
     CK(cudaMemcpyAsync(ctx->fb.C, &c, sizeof c, cudaMemcpyHostToDevice, st));
@@ -440,7 +439,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     cudaEventRecord(e0, st);
-    cudaError_t e = launch_search_inc(ctx->fb.T, ctx->fb.S, X, ctx->fb.I, ctx->fb.C,
+    cudaError_t e = launch_search_inc(p->precision, ctx->fb.T, ctx->fb.S, X, ctx->fb.I, ctx->fb.C,
                                       p->engine == OKR_ENGINE_VERIFY ? 1 : 0, st);
     cudaEventRecord(e1, st);
     ctx->launches += 1;
@@ -1100,18 +1099,19 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         cc.objective = P->objective;
         cc.max_spins = P->max_spins > 0 ? P->max_spins : kDefaultSpins;
     }
-    // largest expected work first; lists: sweep FP64, sweep mixed precision, incremental
-    std::vector<int> ord[3];
+    // largest expected work first; lists: sweep FP64, sweep mixed precision,
+    // incremental FP64, incremental mixed precision
+    std::vector<int> ord[4];
     for (int f = 0; f < nf; ++f) {
         const okr_params *P = &params[n_params == 1 ? 0 : f];
-        ord[resolve_engine(P) == OKR_ENGINE_INCREMENTAL ? 2 : P->precision].push_back(f);
+        ord[(resolve_engine(P) == OKR_ENGINE_INCREMENTAL ? 2 : 0) + P->precision].push_back(f);
     }
-    for (int g = 0; g < 3; ++g)
+    for (int g = 0; g < 4; ++g)
         std::stable_sort(ord[g].begin(), ord[g].end(), [&](int a, int b) {
             return (double)feeders[a].n_bus * merges[a] > (double)feeders[b].n_bus * merges[b];
         });
     int k = 0;
-    for (int g = 0; g < 3; ++g)
+    for (int g = 0; g < 4; ++g)
         for (int f : ord[g]) order_h[k++] = f;
     cudaStream_t st = ctx->stream;
     cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
@@ -1123,12 +1123,12 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     CK(launch_batch_setup(nf, maxL, max_nn, bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
     CK(cudaEventRecord(e1, st));
     int ctas = 0;
-    for (int g = 0, first = 0; g < 3; first += (int)ord[g].size(), ++g) {
+    for (int g = 0, first = 0; g < 4; first += (int)ord[g].size(), ++g) {
         const int cnt = (int)ord[g].size();
         if (cnt == 0) continue;
-        if (g == 2) {                           // one CTA per feeder
+        if (g >= 2) {                           // one CTA per feeder
             ctas = std::max(ctas, cnt);
-            CK(launch_search_inc_batch(bf_d, order_d + first, cnt, st));
+            CK(launch_search_inc_batch(g - 2, bf_d, order_d + first, cnt, st));
             continue;
         }
         const int nteams = std::min(cnt, ctx->num_sms * per_sm[g] / team);

@@ -21,22 +21,30 @@
 // On a 1,000-bus feeder that is about 0.2 % of the terms a full sweep
 // evaluates.
 //
-// Exactness.  D(c) is held as a 128-bit fixed-point integer (units of 2^-100
-// p.u.).  A term is computed in FP64 and converted by a fixed function of its
-// bits; integer addition is associative, so removing a term's old value and
-// adding its new one gives exactly the sum a fresh evaluation of every term
-// gives, in any order.  The old value is recomputed from the unchanged inputs
-// by the same compiled function (term(), not inlined), so it is bit-identical
-// to the value added earlier.  Feasibility is carried the same way: the count of
-// (cluster, scenario) terms whose new MICE exceeds the margin.  Engine 3 checks
-// both against a full re-evaluation after every merge.
+// Exactness.  Carried sums are 128-bit fixed-point integers (units of 2^-100
+// p.u.).  A term is converted by a fixed function of its bits; integer
+// addition is associative, so removing a term's old value and adding its new
+// one gives exactly the sum a fresh evaluation of every term gives, in any
+// order.  The old value is recomputed from the unchanged inputs by the same
+// compiled function (group_term*, not inlined), so it is bit-identical to the
+// value added earlier.  Counts of terms above the margin are carried the same
+// way.  Engine 3 checks the carried values against a fresh evaluation after
+// every merge.
 //
-// Selection compares the fixed-point D(c) exactly: the minimum m over feasible
-// candidates, the tie band D <= m + tau, and the smallest (r, s) key in it.
+// Precision 0 carries FP64 terms and selects on them exactly: the minimum m
+// over feasible candidates, the tie band D <= m + tau, the smallest (r, s) key
+// in it.  Precision 1 (GB300's FP64 rate is a small fraction of its FP32 rate)
+// carries FP32 terms of the same quantities with the rigorous per-term bound
+// of okr_persist.cu, summed into a bound B(c) >= |D32 - D64|, and counts of
+// terms surely / possibly above the margin.  The selection of okr_persist.cu's
+// screen then decides the FP64 winner, or names the few candidates whose FP64
+// score it needs; those are evaluated in FP64 from scratch.  Merges are always
+// applied in FP64.
 //
 // Execution.  One CTA runs one feeder's whole search; its steps are separated
-// by __syncthreads only (no grid barrier, no device-side wait).  A batch runs
-// one CTA per feeder.
+// by __syncthreads only (no grid barrier, no device-side wait).  A term is
+// evaluated by a group of lanes, one per (scenario, phase).  A batch runs one
+// CTA per feeder.
 #include "okr_internal.cuh"
 #include "okr_kernels.cuh"
 
@@ -48,6 +56,9 @@ typedef unsigned __int128 u128;
 
 constexpr int kFxShift = 100;               // fixed point: value * 2^100
 constexpr u128 kSignBit = (u128)1 << 127;
+constexpr u128 kNone = ~(u128)0;
+constexpr float kU32 = 5.9604645e-08f;      // 2^-24
+constexpr int kTE = 512;                    // work entries per tile
 
 __device__ __forceinline__ unsigned long long gtimer_inc() {
     unsigned long long t;
@@ -90,6 +101,7 @@ __device__ __forceinline__ void st128(unsigned long long *p, u128 v) {
 }
 // signed order as unsigned order
 __device__ __forceinline__ u128 okey(u128 v) { return v ^ kSignBit; }
+__device__ __forceinline__ u128 umin(u128 a, u128 b) { return a < b ? a : b; }
 
 __device__ __forceinline__ u128 shfl_xor_u128(u128 v, int o) {
     const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
@@ -107,28 +119,47 @@ __device__ __forceinline__ void sadd128(unsigned long long *lo, unsigned long lo
 }
 
 // ---------------------------------------------------------------- block primitives
-template <int NT>
-__device__ __forceinline__ int block_sum_int(int v, int *sm) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sm[wid] = v;
-    __syncthreads();
-    int t = 0;
-    for (int w = 0; w < NT / 32; ++w) t += sm[w];
-    return t;
+// Every reduction: warps reduce with shuffles, warp 0 reduces the warps'
+// partials and publishes the result; two barriers.
+struct Red {
+    u128 a, b, c;
+    int i;
+};
+
+__device__ __forceinline__ Red red_op(Red x, Red y) {
+    Red r;
+    r.a = umin(x.a, y.a);
+    r.b = umin(x.b, y.b);
+    r.c = umin(x.c, y.c);
+    r.i = x.i + y.i;
+    return r;
+}
+__device__ __forceinline__ Red red_shfl(Red x, int o) {
+    Red r;
+    r.a = shfl_xor_u128(x.a, o);
+    r.b = shfl_xor_u128(x.b, o);
+    r.c = shfl_xor_u128(x.c, o);
+    r.i = __shfl_xor_sync(0xffffffffu, x.i, o);
+    return r;
 }
 
+// Three 128-bit minima and one int sum over the block.
 template <int NT>
-__device__ __forceinline__ double block_max_d(double v, double *sm) {
+__device__ __forceinline__ Red block_red(Red v, Red *sm) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) v = red_op(v, red_shfl(v, o));
     if (lane == 0) sm[wid] = v;
     __syncthreads();
-    double t = sm[0];
-    for (int w = 1; w < NT / 32; ++w) t = fmax(t, sm[w]);
-    return t;
+    if (wid == 0) {
+        Red x;
+        x.a = x.b = x.c = kNone;
+        x.i = 0;
+        if (lane < NT / 32) x = sm[lane];
+        for (int o = 16; o > 0; o >>= 1) x = red_op(x, red_shfl(x, o));
+        if (lane == 0) sm[32] = x;
+    }
+    __syncthreads();
+    return sm[32];
 }
 
 // Exclusive prefix sum of one int per thread; *total = the block's sum.
@@ -140,45 +171,21 @@ __device__ __forceinline__ int block_excl_scan(int v, int *total, int *sm) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    __syncthreads();
     if (lane == 31) sm[wid] = x;
     __syncthreads();
-    int before = 0, tot = 0;
-    for (int w = 0; w < NT / 32; ++w) {
-        const int s = sm[w];
-        if (w < wid) before += s;
-        tot += s;
-    }
-    *total = tot;
-    return before + x - v;
-}
-
-// Block minima of two 128-bit keys and one 64-bit key at once.
-struct Min3 {
-    u128 a, b;
-    unsigned long long c;
-};
-template <int NT>
-__device__ __forceinline__ void block_min3(u128 &a, u128 &b, unsigned long long &c, Min3 *sm) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        const u128 ya = shfl_xor_u128(a, o), yb = shfl_xor_u128(b, o);
-        const unsigned long long yc = __shfl_xor_sync(0xffffffffu, c, o);
-        a = ya < a ? ya : a;
-        b = yb < b ? yb : b;
-        c = yc < c ? yc : c;
+    if (wid == 0) {
+        int y = lane < NT / 32 ? sm[lane] : 0;
+        const int y0 = y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < NT / 32) sm[lane] = y - y0;      // exclusive offsets of the warps
+        if (lane == 31) sm[32] = y;                 // total
     }
     __syncthreads();
-    if (lane == 0) sm[wid] = Min3{a, b, c};
-    __syncthreads();
-    a = sm[0].a;
-    b = sm[0].b;
-    c = sm[0].c;
-    for (int w = 1; w < NT / 32; ++w) {
-        a = sm[w].a < a ? sm[w].a : a;
-        b = sm[w].b < b ? sm[w].b : b;
-        c = sm[w].c < c ? sm[w].c : c;
-    }
+    *total = sm[32];
+    return sm[wid] + x - v;
 }
 
 // ---------------------------------------------------------------- geometry
@@ -230,59 +237,158 @@ __device__ int slot_geometry(const Topo &T, const State &S, int n, int w, Cand &
     return x;
 }
 
-// ---------------------------------------------------------------- one term
-// Term of position k (a super-node, k != c.r) of candidate c over every
-// scenario: fx = sum over l of fixed(new MICE - MICE_k [- MICE_r if k = s]),
-// nv = scenarios whose new MICE exceeds the margin.  With out != nullptr it
-// also writes the new voltage and magnitude per (l, p) and the new MICE per l
-// (the merge of the winner).  Not inlined: every evaluation of a term runs the
-// same instructions, so equal inputs give bit-equal terms.
-__device__ __noinline__ void term(const Topo &T, const State &S, int n, int L, const Cand &c, int k, double margin,
-                                  u128 *fx_out, int *nv_out, double *out) {
-    const bool fixed = (k == c.s) && c.fixed;
-    const bool sside = (k >= c.js && k < c.js + c.ns);
-    const unsigned phk = T.ph[k], phr = T.ph[c.r];
-    const int y = fixed ? 0 : (int)T.lca[(size_t)(sside ? c.s : c.r) * n + k];
-    const double2 *zy = T.zc + (size_t)y * 9, *za = T.zc + (size_t)c.a * 9;
-    u128 fx = 0;
-    int nv = 0;
-    for (int l = 0; l < L; ++l) {
-        double2 Ir[3];
-        for (int q = 0; q < 3; ++q) Ir[q] = S.icur[sidx(l, q, c.r, n)];
-        double m = 0.0;
-        for (int p = 0; p < 3; ++p) {
-            if (!(phk >> p & 1u)) continue;
-            double2 v = S.vcur[sidx(l, p, k, n)];
-            if (!fixed) {
-                double2 dv = make_double2(0.0, 0.0);
-                for (int q = 0; q < 3; ++q) {
-                    if (!(phr >> q & 1u)) continue;
-                    const double2 g = sside ? csub(zy[p * 3 + q], za[p * 3 + q]) : csub(za[p * 3 + q], zy[p * 3 + q]);
-                    dv = cadd(dv, cmul(g, Ir[q]));
-                }
-                v = cadd(v, dv);
+// ---------------------------------------------------------------- term groups
+// A term (candidate c, position k) is evaluated by a group of G = 4 Lp lanes
+// (Lp = scenarios rounded up to a power of two): lane gl takes scenario
+// l = gl / 4 and phase p = gl % 4 (p = 3 idles).  Every lane of the warp calls
+// the group function (it shuffles); `valid` is false for lanes whose group has
+// no term.  The results are the group's sums over its scenarios (every lane
+// holds them).  The functions are not inlined, so that every evaluation of a
+// term runs the same instructions and equal inputs give bit-equal results.
+
+// FP64 term.  d = sum over l of fixed(new MICE - MICE_k [- MICE_r]); nv = scenarios
+// whose new MICE exceeds the margin.  out != nullptr: the new voltage and
+// magnitude per (l, p) and the new MICE per l (the merge).
+__device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, int L, int G, const Cand &c, int k,
+                                          bool valid, int gl, double margin, double *out, u128 *d_out, int *nv_out) {
+    const int l = gl >> 2, p = gl & 3;
+    const bool lv = valid && l < L;
+    const bool on = lv && p < 3 && (T.ph[k] >> p & 1u);
+    double e = 0.0;
+    if (on) {
+        const bool fixed = (k == c.s) && c.fixed;
+        const bool sside = (k >= c.js && k < c.js + c.ns);
+        const size_t ik = sidx(l, p, k, n);
+        double2 v = S.vcur[ik];
+        if (!fixed) {
+            const unsigned phr = T.ph[c.r];
+            const int y = T.lca[(size_t)(sside ? c.s : c.r) * n + k];
+            const double2 *zy = T.zc + (size_t)y * 9 + p * 3, *za = T.zc + (size_t)c.a * 9 + p * 3;
+            double2 dv = make_double2(0.0, 0.0);
+            for (int q = 0; q < 3; ++q) {
+                if (!(phr >> q & 1u)) continue;
+                const double2 g = sside ? csub(zy[q], za[q]) : csub(za[q], zy[q]);
+                dv = cadd(dv, cmul(g, S.icur[sidx(l, q, c.r, n)]));
             }
-            const double mag = cmag(v);
-            double h = S.hi[sidx(l, p, k, n)], lo = S.lo[sidx(l, p, k, n)];
-            if (k == c.s) {
-                h = fmax(h, S.hi[sidx(l, p, c.r, n)]);
-                lo = fmin(lo, S.lo[sidx(l, p, c.r, n)]);
-            }
-            m = fmax(m, fmax(h - mag, mag - lo));
-            if (out) {
-                out[(l * 3 + p) * 3 + 0] = v.x;
-                out[(l * 3 + p) * 3 + 1] = v.y;
-                out[(l * 3 + p) * 3 + 2] = mag;
-            }
+            v = cadd(v, dv);
         }
-        double d = m - S.mice[(size_t)l * n + k];
-        if (k == c.s) d -= S.mice[(size_t)l * n + c.r];
-        fx += to_fx(d);
-        nv += (m > margin) ? 1 : 0;
+        const double mag = cmag(v);
+        double h = S.hi[ik], lo = S.lo[ik];
+        if (k == c.s) {
+            const size_t ir = sidx(l, p, c.r, n);
+            h = fmax(h, S.hi[ir]);
+            lo = fmin(lo, S.lo[ir]);
+        }
+        e = fmax(h - mag, mag - lo);
+        if (out) {
+            out[(l * 3 + p) * 3 + 0] = v.x;
+            out[(l * 3 + p) * 3 + 1] = v.y;
+            out[(l * 3 + p) * 3 + 2] = mag;
+        }
+    }
+    double m = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    u128 d = 0;
+    int nv = 0;
+    if (lv && p == 0) {
+        double dd = m - S.mice[(size_t)l * n + k];
+        if (k == c.s) dd -= S.mice[(size_t)l * n + c.r];
+        d = to_fx(dd);
+        nv = (m > margin) ? 1 : 0;
         if (out) out[9 * L + l] = m;
     }
-    *fx_out = fx;
+    for (int o = 4; o < G; o <<= 1) {
+        d += shfl_xor_u128(d, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    }
+    *d_out = d;
     *nv_out = nv;
+}
+
+// FP32 term with a rigorous bound (the screen of okr_persist.cu, per item
+// e = max(hr - delta, delta - lr) relative to the cluster's present magnitude).
+// d = sum over l of fixed(D32 term); b = sum over l of a fixed-point bound on
+// |fixed(D32 term) - fixed(D64 term)|; n_sure = scenarios whose new MICE is
+// surely above the margin; n_maybe = scenarios where it may be.
+__device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, int L, int G, const Cand &c, int k,
+                                          bool valid, int gl, float margin_lo, float margin_hi, u128 *d_out,
+                                          u128 *b_out, int *ns_out, int *nm_out) {
+    const int l = gl >> 2, p = gl & 3;
+    const bool lv = valid && l < L;
+    const bool on = lv && p < 3 && (T.ph[k] >> p & 1u);
+    float e = 0.0f, b = 0.0f;
+    if (on) {
+        const bool fixed = (k == c.s) && c.fixed;
+        const bool sside = (k >= c.js && k < c.js + c.ns);
+        const size_t ik = sidx(l, p, k, n);
+        float hr = S.hr32[ik], lr = S.lr32[ik];
+        float bx = 0.0f;
+        if (k == c.s && (T.ph[c.r] >> p & 1u)) {
+            const size_t ir = sidx(l, p, c.r, n);
+            const float dr = (float)(S.mcur[ir] - S.mcur[ik]);
+            const float hrr = S.hr32[ir] + dr, lrr = S.lr32[ir] + dr;
+            hr = fmaxf(hr, hrr);
+            lr = fminf(lr, lrr);
+            bx = 2.0f * kU32 * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
+        }
+        float delta = 0.0f, bd = 0.0f;
+        if (!fixed) {
+            const unsigned phr = T.ph[c.r];
+            const float2 v = S.v32[ik];
+            const int y = T.lca[(size_t)(sside ? c.s : c.r) * n + k];
+            const float2 *zhy = T.zh + (size_t)y * 9 + p * 3, *zly = T.zlo + (size_t)y * 9 + p * 3;
+            const float2 *zha = T.zh + (size_t)c.a * 9 + p * 3, *zla = T.zlo + (size_t)c.a * 9 + p * 3;
+            float2 dv = make_float2(0.0f, 0.0f);
+            float sdv = 0.0f;
+            for (int q = 0; q < 3; ++q) {
+                if (!(phr >> q & 1u)) continue;
+                const float2 iq = S.icur32[sidx(l, q, c.r, n)];
+                float gx = (zhy[q].x - zha[q].x) + (zly[q].x - zla[q].x);
+                float gy = (zhy[q].y - zha[q].y) + (zly[q].y - zla[q].y);
+                if (!sside) { gx = -gx; gy = -gy; }
+                dv.x = fmaf(gx, iq.x, fmaf(-gy, iq.y, dv.x));
+                dv.y = fmaf(gx, iq.y, fmaf(gy, iq.x, dv.y));
+                sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(iq.x) + fabsf(iq.y), sdv);
+            }
+            const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
+            const float wx = v.x + dv.x, wy = v.y + dv.y;
+            const float mv = sqrtf(v.x * v.x + v.y * v.y);
+            const float den = sqrtf(wx * wx + wy * wy) + mv;
+            delta = num / den;
+            const float v1 = fabsf(v.x) + fabsf(v.y);
+            bd = kU32 * (40.0f * (v1 + sdv) * sdv / den + 8.0f * fabsf(delta));
+        }
+        e = fmaxf(hr - delta, delta - lr);
+        b = 1.5f * (kU32 * (fabsf(hr) + fabsf(lr) + fabsf(e)) + bd) + bx + 4e-15f;
+    }
+    float m = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    float bm = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, 1));
+    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
+    u128 d = 0, bb = 0;
+    int ns = 0, nm = 0;
+    if (lv && p == 0) {
+        const float mo = S.mice32[(size_t)l * n + k];
+        const float mr = (k == c.s) ? S.mice32[(size_t)l * n + c.r] : 0.0f;
+        const float dd = (m - mo) - mr;
+        // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
+        // factor 1.001 covers the rounding of the bound's own arithmetic
+        const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(mo) + fabsf(mr) + fabsf(m)));
+        d = to_fx((double)dd);
+        bb = to_fx((double)bl) + 3;      // + the truncations of both terms to fixed point
+        ns = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
+        nm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
+    }
+    for (int o = 4; o < G; o <<= 1) {
+        d += shfl_xor_u128(d, o);
+        bb += shfl_xor_u128(bb, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        nm += __shfl_xor_sync(0xffffffffu, nm, o);
+    }
+    *d_out = d;
+    *b_out = bb;
+    *ns_out = ns;
+    *nm_out = nm;
 }
 
 // ---------------------------------------------------------------- the changed set of a merge
@@ -297,8 +403,24 @@ struct Win {
 
 __device__ __forceinline__ bool in_range(int b, int lo, int hi) { return b >= lo && b < hi; }
 
+// Whether candidate c (not next to s* or r*) has a term that reads an input
+// the merge h changes: a position in the moved ranges or at s*, r*; its fixed
+// s when that cluster changed; its s term when r's MICE changed.
+__device__ __forceinline__ bool touched(const Cand &c, const Win &h) {
+    auto in_cr = [&](int b) { return in_range(b, c.js, c.js + c.ns) || in_range(b, c.jr, c.jr + c.nr); };
+    auto in_w = [&](int b) { return in_range(b, h.w1lo, h.w1hi) || in_range(b, h.w2lo, h.w2hi); };
+    const int clo[2] = {c.js, c.jr}, chi[2] = {c.js + c.ns, c.jr + c.nr};
+    const int wlo[2] = {h.w1lo, h.w2lo}, whi[2] = {h.w1hi, h.w2hi};
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+            if (max(clo[i], wlo[j]) < min(chi[i], whi[j])) return true;
+    if (in_cr(h.s) || in_cr(h.r)) return true;
+    if (c.fixed && (in_w(c.s) || c.s == h.s || c.s == h.r)) return true;
+    return in_w(c.r) || c.r == h.s || c.r == h.r;
+}
+
 // Rank ranges of the terms of candidate c that read an input the merge h
-// changes (c is not next to s* or r*).  Returns their number (0: c unchanged).
+// changes (c is not next to s* or r*).  Returns their number.
 __device__ int changed_segments(const Cand &c, const Win &h, const int *sn_rank, int2 *seg) {
     int k = 0;
     const int clo[2] = {c.js, c.jr}, chi[2] = {c.js + c.ns, c.jr + c.nr};
@@ -355,84 +477,166 @@ __device__ __forceinline__ void write_entry(IncWork *w, int slot, int mode, int 
 }
 
 // ---------------------------------------------------------------- evaluation of work entries
-struct EvalSmem {
-    unsigned long long lo[1024], hi[1024];
-    int nv[1024];
-    int off[1025];
+enum Pass {
+    kOld = 0,       // carried terms on the state before the merge: subtracted
+    kNew = 1,       // carried terms on the state after it: added (mode 0) or set (mode 1)
+    kFresh = 2,     // carried precision, every term of the entries, into vacc / vviol
+    kF64 = 3        // FP64, every term of the entries, into vacc / vviol
 };
 
-// Evaluates the terms of entries [e0, e1) of I.work and applies them to the
-// accumulators (acc, viol): sub = subtract (terms before the merge); entries
-// of mode 1 are set (every term), the others added.  Mode-0 entries take
-// positions from list_old and skip r* after the merge; mode-1 entries from
-// list_new.  Returns the number of terms evaluated (thread 0's count is exact).
+struct EvalSmem {
+    unsigned long long dlo[kTE], dhi[kTE], blo[kTE], bhi[kTE];
+    int n1[kTE], n2[kTE];
+    int off[kTE + 1];
+};
+
+// The merge's own evaluation (FP64, state before the merge): new voltage,
+// magnitude and MICE of each of its positions into the scratch.
+struct Commit {
+    const Win *h;
+    Cand wc;
+    const int *list;        // super-nodes before the merge
+};
+
 template <int NT>
-__device__ long long eval_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L,
-                                  double margin, int e0, int e1, bool sub, int rstar, const int *list_old,
-                                  const int *list_new, unsigned long long *acc, int *viol, EvalSmem *E, int *smi) {
-    const int tid = threadIdx.x;
+__device__ __forceinline__ void commit_groups(const Topo &T, const State &S, const Inc &I, int n, int L, int G,
+                                              double margin, const Commit &cm) {
+    const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
+    const Win &h = *cm.h;
+    const int n1 = h.q1hi - h.q1lo, n2 = h.q2hi - h.q2lo;
+    for (int r0 = 0; r0 < h.npos; r0 += NG) {
+        const int q = r0 + (NG - 1 - gi);               // the last warps first: the entries start at the first
+        bool valid = q < h.npos;
+        int k = cm.wc.s;
+        if (valid) {
+            k = q < n1 ? cm.list[h.q1lo + q] : (q < n1 + n2 ? cm.list[h.q2lo + q - n1] : cm.wc.s);
+            if (k == cm.wc.r) { valid = false; k = cm.wc.s; }
+        }
+        u128 d;
+        int nv;
+        group_term64(T, S, n, L, G, cm.wc, k, valid, gl, margin, valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d,
+                     &nv);
+    }
+}
+
+// Evaluates the terms of work entries [e0, e1) (tiles of kTE entries) and applies
+// them per the pass.  Mode-0 entries take positions from list_pre (and skip r*
+// after the merge), mode-1 entries from list_post; kFresh / kF64 use list_pre.
+// With cm != nullptr the merge's own evaluation runs alongside.  Returns the
+// number of terms evaluated.
+template <int NT, int PREC>
+__device__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
+                                 double margin, float mlo, float mhi, int e0, int e1, int pass, const int *list_pre,
+                                 const int *list_post, int rstar, const Commit *cm, EvalSmem &E, int *sscan) {
+    const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
     long long terms = 0;
-    for (int t0 = e0; t0 < e1; t0 += NT) {
-        const int e = t0 + tid;
+    bool commit_done = (cm == nullptr);
+    for (int t0 = e0; t0 < e1; t0 += kTE) {
+        const int ne = min(kTE, e1 - t0);
         int cnt = 0;
-        if (e < e1) {
-            const IncWork &w = I.work[e];
+        if (tid < ne) {
+            const IncWork &w = I.work[t0 + tid];
             for (int i = 0; i < w.nseg; ++i) cnt += w.seg[i].y - w.seg[i].x;
         }
         int tot = 0;
-        const int off = block_excl_scan<NT>(cnt, &tot, smi);
-        E->off[tid] = off;
-        if (tid == NT - 1) E->off[NT] = tot;
-        E->lo[tid] = 0ull;
-        E->hi[tid] = 0ull;
-        E->nv[tid] = 0;
+        const int off = block_excl_scan<NT>(cnt, &tot, sscan);
+        if (tid < kTE) E.off[tid] = off;
+        for (int i = tid; i < kTE; i += NT) {
+            E.dlo[i] = E.dhi[i] = E.blo[i] = E.bhi[i] = 0ull;
+            E.n1[i] = E.n2[i] = 0;
+        }
         terms += tot;
-        const int ne = min(NT, e1 - t0);
         __syncthreads();
-        for (int q = tid; q < tot; q += NT) {
-            int lo = 0, hi = ne - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (E->off[mid] <= q) lo = mid;
-                else hi = mid - 1;
+        if (!commit_done) {
+            commit_groups<NT>(T, S, I, n, L, G, margin, *cm);
+            commit_done = true;
+        }
+        for (int r0 = 0; r0 < tot; r0 += NG) {
+            const int q = r0 + gi;
+            bool valid = q < tot;
+            int ei = 0, k = 0;
+            Cand c = X.slot[0];
+            if (valid) {
+                int lo = 0, hi = ne - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (E.off[mid] <= q) lo = mid;
+                    else hi = mid - 1;
+                }
+                ei = lo;
+                const IncWork &w = I.work[t0 + ei];
+                int rem = q - E.off[ei], j = 0;
+                for (int i = 0; i < w.nseg; ++i) {
+                    const int len = w.seg[i].y - w.seg[i].x;
+                    if (rem < len) { j = w.seg[i].x + rem; break; }
+                    rem -= len;
+                }
+                k = ((pass == kNew && w.mode == 1) ? list_post : list_pre)[j];
+                c = X.slot[w.slot];
+                if (k == c.r || (pass == kNew && w.mode == 0 && k == rstar)) valid = false;
             }
-            const IncWork &w = I.work[t0 + lo];
-            int rem = q - E->off[lo], j = -1;
-            for (int i = 0; i < w.nseg; ++i) {
-                const int len = w.seg[i].y - w.seg[i].x;
-                if (rem < len) { j = w.seg[i].x + rem; break; }
-                rem -= len;
+            if (PREC == 0 || pass == kF64) {
+                u128 d;
+                int nv;
+                group_term64(T, S, n, L, G, c, k, valid, gl, margin, nullptr, &d, &nv);
+                if (valid && gl == 0) {
+                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
+                    if (nv) atomicAdd(&E.n1[ei], nv);
+                }
+            } else {
+                u128 d, b;
+                int ns, nm;
+                group_term32(T, S, n, L, G, c, k, valid, gl, mlo, mhi, &d, &b, &ns, &nm);
+                if (valid && gl == 0) {
+                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
+                    sadd128(&E.blo[ei], &E.bhi[ei], b);
+                    if (ns) atomicAdd(&E.n1[ei], ns);
+                    if (nm) atomicAdd(&E.n2[ei], nm);
+                }
             }
-            if (j < 0) continue;
-            const int k = (w.mode == 0 ? list_old : list_new)[j];
-            const Cand &c = X.slot[w.slot];
-            if (k == c.r || (!sub && w.mode == 0 && k == rstar)) continue;
-            u128 fx;
-            int nv;
-            term(T, S, n, L, c, k, margin, &fx, &nv, nullptr);
-            if (sub) { fx = (u128)0 - fx; nv = -nv; }
-            sadd128(&E->lo[lo], &E->hi[lo], fx);
-            if (nv) atomicAdd(&E->nv[lo], nv);
         }
         __syncthreads();
-        if (e < e1) {
-            const IncWork &w = I.work[e];
-            const u128 add = ((u128)E->hi[tid] << 64) | (u128)E->lo[tid];
-            unsigned long long *a = acc + 2 * (size_t)w.slot;
-            if (w.mode == 1 && !sub) {
-                st128(a, add);
-                viol[w.slot] = E->nv[tid];
+        if (tid < ne) {
+            const IncWork &w = I.work[t0 + tid];
+            const int sl = w.slot;
+            const u128 d = ((u128)E.dhi[tid] << 64) | (u128)E.dlo[tid];
+            const u128 b = ((u128)E.bhi[tid] << 64) | (u128)E.blo[tid];
+            unsigned long long *a = I.acc + 2 * (size_t)sl, *bp = I.bnd + 2 * (size_t)sl;
+            if (pass == kOld) {
+                st128(a, ld128(a) - d);
+                I.viol[sl] -= E.n1[tid];
+                if (PREC == 1) {
+                    st128(bp, ld128(bp) - b);
+                    I.vmay[sl] -= E.n2[tid];
+                }
+            } else if (pass == kNew) {
+                if (w.mode == 1) {
+                    st128(a, d);
+                    I.viol[sl] = E.n1[tid];
+                    if (PREC == 1) {
+                        st128(bp, b);
+                        I.vmay[sl] = E.n2[tid];
+                    }
+                } else {
+                    st128(a, ld128(a) + d);
+                    I.viol[sl] += E.n1[tid];
+                    if (PREC == 1) {
+                        st128(bp, ld128(bp) + b);
+                        I.vmay[sl] += E.n2[tid];
+                    }
+                }
             } else {
-                st128(a, ld128(a) + add);
-                viol[w.slot] += E->nv[tid];
+                st128(I.vacc + 2 * (size_t)sl, d);
+                I.vviol[sl] = E.n1[tid];
             }
         }
         __syncthreads();
     }
+    if (!commit_done) commit_groups<NT>(T, S, I, n, L, G, margin, *cm);
     return terms;
 }
 
-// Slot pairs w handled by this thread: [w_b, w_e), consecutive.
+// Slot pairs w handled by this thread: [wb, we), consecutive.
 template <int NT>
 __device__ __forceinline__ void my_pairs(int n, int &wb, int &we) {
     const int per = (n + NT - 1) / NT;
@@ -441,11 +645,11 @@ __device__ __forceinline__ void my_pairs(int n, int &wb, int &we) {
 }
 
 // Rebuilds the slot pairs listed in fp[0, nf) from the current clusters and
-// appends a full work entry for each valid candidate at I.work[base...).
-// Returns the number of entries appended.
+// writes a full work entry for each valid candidate at I.work[base...).
+// Returns the number of entries written.
 template <int NT>
 __device__ int rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
-                             int base, int *smi) {
+                             int base, int *sscan) {
     int added = 0;
     for (int i0 = 0; i0 < nf; i0 += NT) {
         const int i = i0 + threadIdx.x;
@@ -457,15 +661,16 @@ __device__ int rebuild_pairs(const Topo &T, const State &S, const Search &X, con
             I.qpar[w] = slot_geometry(T, S, n, w, c[0], c[1]);
             for (int d = 0; d < 2; ++d) {
                 X.slot[2 * w + d] = c[d];
-                if (c[d].s >= 0) ++cnt;
-                else {
+                if (c[d].s >= 0) {
+                    ++cnt;
+                } else {
                     I.viol[2 * w + d] = kIncDead;
                     st128(I.acc + 4 * (size_t)w + 2 * d, 0);
                 }
             }
         }
         int tot = 0;
-        int off = block_excl_scan<NT>(cnt, &tot, smi);
+        int off = block_excl_scan<NT>(cnt, &tot, sscan);
         if (i < nf) {
             const int w = fp[i];
             for (int d = 0; d < 2; ++d) {
@@ -484,16 +689,34 @@ __device__ int rebuild_pairs(const Topo &T, const State &S, const Search &X, con
 }  // namespace
 
 // ---------------------------------------------------------------- the search
+// Largest MICE over the clusters (dead slots hold 0), for the decision record.
 template <int NT>
+__device__ double max_mice(const State &S, int n, int L, Red *sred) {
+    u128 m = kNone;
+    for (int w = threadIdx.x; w < n; w += NT)
+        for (int l = 0; l < L; ++l)
+            m = umin(m, ~(u128)(unsigned long long)__double_as_longlong(S.mice[(size_t)l * n + w]));
+    Red v;
+    v.a = m;
+    v.b = v.c = kNone;
+    v.i = 0;
+    v = block_red<NT>(v, sred);
+    return v.a == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~v.a);
+}
+
+template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify) {
+    static_assert(NT >= kTE && NT <= 1024, "thread count");
     __shared__ __align__(16) EvalSmem E;
-    __shared__ __align__(16) Min3 sm3[NT / 32];
-    __shared__ int smi[NT / 32];
-    __shared__ double smd[NT / 32];
+    __shared__ __align__(16) Red sred[33];
+    __shared__ int sscan[33];
     __shared__ Win h;
     __shared__ unsigned long long s_sfx[2];     // SMICE of the committed state, fixed point
+    __shared__ unsigned long long s_dsum[2];    // the last merge's change of it
     const int n = T.n, L = T.L, tid = threadIdx.x;
+    const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
     const double margin = C->margin;
+    const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
     const int max_merges = C->max_merges;
     const bool prof = C->profile != 0;
     const u128 tau_fx = to_fx(C->tau);
@@ -505,15 +728,17 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         if (prof && tid == 0) { const unsigned long long now = gtimer_inc(); C->phase_ns[i] += now - tp; tp = now; }
     };
     long long terms = 0;
+    int rechecks = 0, recheck_cands = 0;
+    bool maxerr_done = true;                // dec_maxerr of the last merge written
 
     // ---- every slot pair from the initial clusters (all singletons), every term
     for (int w = tid; w < n; w += NT) I.fpair[w] = w;
     __syncthreads();
     {
-        const int ne = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, n, 0, smi);
+        const int ne = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, n, 0, sscan);
         __syncthreads();
-        terms += eval_entries<NT>(T, S, X, I, n, L, margin, 0, ne, false, -1, S.sn_list[0], S.sn_list[0], I.acc,
-                                  I.viol, &E, smi);
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kNew, S.sn_list[0], S.sn_list[0],
+                                       -1, nullptr, E, sscan);
     }
     if (prof && tid == 0) tp = gtimer_inc();
 
@@ -525,69 +750,168 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         const int *list_old = S.sn_list[t & 1];
         int *list_new = S.sn_list[(t + 1) & 1];
         // ============================================================ selection
-        u128 best = ~(u128)0, dummy = ~(u128)0;
-        unsigned long long dmy = ~0ull;
-        int nvalid = 0;
+        // pass A: precision 0: minimum over feasible; precision 1: smallest lower
+        // end over possibly feasible (m_lo), smallest upper end over surely
+        // feasible (m_hi); the largest MICE of the last merge; candidates.
+        Red ra;
+        ra.a = ra.b = ra.c = kNone;
+        ra.i = 0;
         for (int c = tid; c < 2 * n; c += NT) {
+            if ((c & 1) == 0 && t > 0)
+                for (int l = 0; l < L; ++l)
+                    ra.c = umin(ra.c, ~(u128)(unsigned long long)__double_as_longlong(S.mice[(size_t)l * n + (c >> 1)]));
             const int v = I.viol[c];
             if (v >= kIncDead) continue;
-            ++nvalid;
-            if (v == 0) {
-                const u128 k = okey(ld128(I.acc + 2 * (size_t)c));
-                best = k < best ? k : best;
+            ++ra.i;
+            if (v != 0) continue;
+            const u128 d = ld128(I.acc + 2 * (size_t)c);
+            if (PREC == 0) {
+                ra.a = umin(ra.a, okey(d));
+            } else {
+                const u128 b = ld128(I.bnd + 2 * (size_t)c);
+                ra.a = umin(ra.a, okey(d - b));
+                if (I.vmay[c] == 0) ra.b = umin(ra.b, okey(d + b));
             }
         }
-        nvalid = block_sum_int<NT>(nvalid, smi);
-        block_min3<NT>(best, dummy, dmy, sm3);
+        ra = block_red<NT>(ra, sred);
+        const int nvalid = ra.i;
         if (tid == 0) {
             C->candidates += nvalid;
             C->iters += 1;
             X.dec_ncand[t] = nvalid;
+            if (t > 0)
+                X.dec_maxerr[t - 1] = ra.c == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~ra.c);
         }
         const double s_cur = fx_to_d(ld128(s_sfx));
         if (t < X.rec_iters) {
-            // every candidate's SMICE (+inf when infeasible), compacted in slot order
+            // every candidate's SMICE (+inf when (surely) infeasible), compacted in slot order
             int base = 0;
             for (int c0 = 0; c0 < 2 * n; c0 += NT) {
                 const int c = c0 + tid;
                 const int v = c < 2 * n ? I.viol[c] : kIncDead;
                 const int f = v < kIncDead ? 1 : 0;
                 int tot = 0;
-                const int o = block_excl_scan<NT>(f, &tot, smi) + base;
+                const int o = block_excl_scan<NT>(f, &tot, sscan) + base;
                 if (f) {
                     const Cand &cc = X.slot[c];
                     const size_t at = (size_t)t * 2 * n + o;
                     X.rec_s[at] = T.orig[cc.s];
                     X.rec_r[at] = T.orig[cc.r];
                     X.rec_score[at] = v == 0 ? s_cur + fx_to_d(ld128(I.acc + 2 * (size_t)c)) : INFINITY;
-                    X.rec_bound[at] = 0.0;
+                    X.rec_bound[at] = (PREC == 1 && v == 0) ? fx_to_d(ld128(I.bnd + 2 * (size_t)c)) * (1.0 + 1e-12) : 0.0;
                 }
                 base += tot;
             }
             if (tid == 0) X.rec_count[t] = nvalid;
         }
-        if (best == ~(u128)0) {                          // nothing feasible
+        if (ra.a == kNone) {                             // nothing (possibly) feasible
+            if (tid == 0) { C->done = 1; C->stop_reason = 1; }
+            maxerr_done = true;
+            break;
+        }
+        // pass B
+        int ws = -1;
+        double gap = INFINITY;
+        if (PREC == 0) {
+            const u128 edge = (ra.a ^ kSignBit) + tau_fx, ek = okey(edge);
+            Red rb;
+            rb.a = rb.b = rb.c = kNone;
+            rb.i = 0;
+            for (int c = tid; c < 2 * n; c += NT) {
+                if (I.viol[c] != 0) continue;
+                const u128 k = okey(ld128(I.acc + 2 * (size_t)c));
+                if (k <= ek) rb.a = umin(rb.a, ((u128)X.slot[c].key << 32) | (u128)(unsigned)c);
+                else rb.b = umin(rb.b, k);
+            }
+            rb = block_red<NT>(rb, sred);
+            ws = (int)(unsigned)(rb.a & 0xffffffffu);
+            if (rb.b != kNone) gap = fx_to_d((rb.b ^ kSignBit) - edge);
+        } else {
+            const bool has_hi = ra.b != kNone;
+            const u128 ein = okey((ra.a ^ kSignBit) + tau_fx);
+            const u128 eout = has_hi ? okey((ra.b ^ kSignBit) + tau_fx) : kNone;
+            Red rb;
+            rb.a = rb.b = rb.c = kNone;
+            rb.i = 0;
+            for (int c = tid; c < 2 * n; c += NT) {
+                if (I.viol[c] != 0) continue;
+                const u128 d = ld128(I.acc + 2 * (size_t)c), b = ld128(I.bnd + 2 * (size_t)c);
+                const u128 lo = okey(d - b), hi = okey(d + b);
+                const bool in_sure = I.vmay[c] == 0 && hi <= ein;
+                const bool out_sure = has_hi && lo > eout;
+                const u128 key = (u128)X.slot[c].key;
+                if (in_sure) rb.a = umin(rb.a, (key << 32) | (u128)(unsigned)c);
+                else if (!out_sure) rb.b = umin(rb.b, key);
+                if (out_sure) rb.c = umin(rb.c, lo);
+            }
+            rb = block_red<NT>(rb, sred);
+            const u128 ks = rb.a == kNone ? kNone : (rb.a >> 32);
+            if (!(rb.b < ks)) {                          // no uncertain candidate can take the band's smallest key
+                ws = (int)(unsigned)(rb.a & 0xffffffffu);
+                if (rb.c != kNone) gap = fx_to_d((rb.c ^ kSignBit) - (eout ^ kSignBit));
+            } else {
+                // FP64 rescoring of R: the possible minimizers and the uncertain
+                // candidates with a key below the smallest surely-in key
+                int nR = 0;
+                for (int c0 = 0; c0 < 2 * n; c0 += NT) {
+                    const int c = c0 + tid;
+                    int f = 0;
+                    if (c < 2 * n && I.viol[c] == 0) {
+                        const u128 d = ld128(I.acc + 2 * (size_t)c), b = ld128(I.bnd + 2 * (size_t)c);
+                        const u128 lo = okey(d - b), hi = okey(d + b);
+                        const bool in_sure = I.vmay[c] == 0 && hi <= ein;
+                        const bool out_sure = has_hi && lo > eout;
+                        const bool unc = !in_sure && !out_sure && (u128)X.slot[c].key < ks;
+                        if (unc || !has_hi || lo <= okey(ra.b ^ kSignBit)) f = 1;
+                    }
+                    int tot = 0;
+                    const int o = block_excl_scan<NT>(f, &tot, sscan) + nR;
+                    if (f) {
+                        I.rlist[o] = c;
+                        int2 seg[kIncMaxSeg];
+                        const int k = full_segments(X.slot[c], S.sn_rank, seg);
+                        write_entry(I.work + o, c, 1, k, seg);
+                    }
+                    nR += tot;
+                }
+                __syncthreads();
+                terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, nR, kF64, list_old, list_old,
+                                               -1, nullptr, E, sscan);
+                // exact selection over R, with the surely-in candidate of key ks
+                Red rc;
+                rc.a = rc.b = rc.c = kNone;
+                rc.i = 0;
+                for (int i = tid; i < nR; i += NT) {
+                    const int c = I.rlist[i];
+                    if (I.vviol[c] == 0) rc.a = umin(rc.a, okey(ld128(I.vacc + 2 * (size_t)c)));
+                }
+                rc = block_red<NT>(rc, sred);
+                Red rd;
+                rd.a = rd.b = rd.c = kNone;
+                rd.i = 0;
+                if (rc.a != kNone) {
+                    const u128 edge = (rc.a ^ kSignBit) + tau_fx, ek = okey(edge);
+                    for (int i = tid; i < nR; i += NT) {
+                        const int c = I.rlist[i];
+                        if (I.vviol[c] != 0) continue;
+                        const u128 k = okey(ld128(I.vacc + 2 * (size_t)c));
+                        if (k <= ek) rd.a = umin(rd.a, ((u128)X.slot[c].key << 32) | (u128)(unsigned)c);
+                        else rd.b = umin(rd.b, k);
+                    }
+                    rd = block_red<NT>(rd, sred);
+                    if (rd.b != kNone) gap = fx_to_d((rd.b ^ kSignBit) - edge);
+                }
+                const u128 best = umin(rd.a, rb.a);
+                ws = best == kNone ? -1 : (int)(unsigned)(best & 0xffffffffu);
+                ++rechecks;
+                recheck_cands += nR;
+            }
+        }
+        if (ws < 0) {                                    // FP64 rescoring found nothing feasible
             if (tid == 0) { C->done = 1; C->stop_reason = 1; }
             break;
         }
-        const u128 m = best ^ kSignBit;
-        const u128 edge = m + tau_fx;
-        const u128 ek = okey(edge);
-        // band: smallest (r, s) key with its slot; gap: smallest score above the band
-        u128 kp = ~(u128)0, gk = ~(u128)0;
-        for (int c = tid; c < 2 * n; c += NT) {
-            if (I.viol[c] != 0) continue;
-            const u128 k = okey(ld128(I.acc + 2 * (size_t)c));
-            if (k <= ek) {
-                const u128 key = ((u128)X.slot[c].key << 32) | (u128)(unsigned)c;
-                kp = key < kp ? key : kp;
-            } else {
-                gk = k < gk ? k : gk;
-            }
-        }
-        block_min3<NT>(kp, gk, dmy, sm3);
         stamp(0);
-        const int ws = (int)(unsigned)(kp & 0xffffffffu);
         // ============================================================ the merge's changed set
         if (tid == 0) {
             const Cand w = X.slot[ws];
@@ -603,7 +927,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             h.npos = (h.q1hi - h.q1lo) + (h.q2hi - h.q2lo) + w.fixed;
             X.dec_s[t] = T.orig[w.s];
             X.dec_r[t] = T.orig[w.r];
-            X.dec_gap[t] = (gk == ~(u128)0) ? INFINITY : fx_to_d((gk ^ kSignBit) - edge);
+            X.dec_gap[t] = gap;
+            s_dsum[0] = 0ull;
+            s_dsum[1] = 0ull;
         }
         __syncthreads();
         const Win hw = h;
@@ -617,47 +943,41 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             if (w == hw.s || qp == hw.r || qp == hw.s) { ++nf_mine; continue; }
             for (int d = 0; d < 2; ++d) {
                 const Cand &c = X.slot[2 * w + d];
-                if (c.s < 0) continue;
-                int2 seg[kIncMaxSeg];
-                if (changed_segments(c, hw, S.sn_rank, seg) > 0) ++np_mine;
+                if (c.s >= 0 && touched(c, hw)) ++np_mine;
             }
         }
         int nf_tot = 0, np_tot = 0;
-        int fo = block_excl_scan<NT>(nf_mine, &nf_tot, smi);
-        int po = block_excl_scan<NT>(np_mine, &np_tot, smi);
-        for (int w = wb; w < we; ++w) {
+        int fo = block_excl_scan<NT>(nf_mine, &nf_tot, sscan);
+        int po = block_excl_scan<NT>(np_mine, &np_tot, sscan);
+        for (int w = wb; w < we && (nf_mine | np_mine); ++w) {
             if (w == hw.r) continue;
             const int qp = I.qpar[w];
             if (w == hw.s || qp == hw.r || qp == hw.s) { I.fpair[fo++] = w; continue; }
             for (int d = 0; d < 2; ++d) {
                 const Cand &c = X.slot[2 * w + d];
-                if (c.s < 0) continue;
+                if (c.s < 0 || !touched(c, hw)) continue;
                 int2 seg[kIncMaxSeg];
                 const int k = changed_segments(c, hw, S.sn_rank, seg);
-                if (k > 0) write_entry(I.work + po++, 2 * w + d, 0, k, seg);
+                write_entry(I.work + po++, 2 * w + d, 0, k, seg);
             }
         }
         __syncthreads();
         stamp(1);
-        // ============================================================ terms before the merge
-        // the merge's own new values (state before the merge) into the scratch
+        // ============================================================ terms before the merge, and the merge's own values
         {
-            const Cand wc = X.slot[ws];
-            const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
-            for (int j = tid; j < hw.npos; j += NT) {
-                const int k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : wc.s);
-                if (k == wc.r) continue;
-                u128 fx;
-                int nv;
-                term(T, S, n, L, wc, k, margin, &fx, &nv, I.cbuf + (size_t)j * 10 * L);
-            }
+            Commit cm;
+            cm.h = &h;
+            cm.wc = X.slot[ws];
+            cm.list = list_old;
+            terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot, kOld, list_old, list_new,
+                                           hw.r, &cm, E, sscan);
         }
-        terms += eval_entries<NT>(T, S, X, I, n, L, margin, 0, np_tot, true, hw.r, list_old, list_new, I.acc, I.viol,
-                                  &E, smi);
+        __syncthreads();
         stamp(2);
-        // ============================================================ the merge (FP64)
+        // ============================================================ the merge (FP64, then the FP32 copies)
         {
             const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
+            u128 dsum = 0;
             for (int j = tid; j < hw.npos; j += NT) {
                 const bool fx = j >= n1 + n2;
                 const int k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : hw.s);
@@ -668,19 +988,35 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     for (int p = 0; p < 3; ++p) {
                         if (!(phk >> p & 1u)) continue;
                         const size_t ik = sidx(l, p, k, n);
+                        double mc = S.mcur[ik];
                         if (!fx) {
-                            S.vcur[ik] = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
-                            S.mcur[ik] = cb[(l * 3 + p) * 3 + 2];
+                            const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
+                            mc = cb[(l * 3 + p) * 3 + 2];
+                            S.vcur[ik] = v;
+                            S.mcur[ik] = mc;
+                            S.v32[ik] = make_float2((float)v.x, (float)v.y);
                         }
+                        double hh = S.hi[ik], ll = S.lo[ik];
                         if (k == hw.s) {
                             const size_t ir = sidx(l, p, hw.r, n);
-                            S.hi[ik] = fmax(S.hi[ik], S.hi[ir]);
-                            S.lo[ik] = fmin(S.lo[ik], S.lo[ir]);
+                            hh = fmax(hh, S.hi[ir]);
+                            ll = fmin(ll, S.lo[ir]);
+                            S.hi[ik] = hh;
+                            S.lo[ik] = ll;
                         }
+                        S.hr32[ik] = (float)(hh - mc);
+                        S.lr32[ik] = (float)(ll - mc);
                     }
-                    S.mice[(size_t)l * n + k] = cb[9 * L + l];
+                    // the merge's exact score change: its FP64 terms in fixed point
+                    const double m = cb[9 * L + l];
+                    double dd = m - S.mice[(size_t)l * n + k];
+                    if (k == hw.s) dd -= S.mice[(size_t)l * n + hw.r];
+                    dsum += to_fx(dd);
+                    S.mice[(size_t)l * n + k] = m;
+                    S.mice32[(size_t)l * n + k] = (float)m;
                 }
             }
+            if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
             // r's members join s; ranks past r drop by one; the new super-node list
             for (int b = hw.rtop + tid; b < hw.rtop_end; b += NT)
                 if (S.label[b] == hw.r) S.label[b] = hw.s;
@@ -692,17 +1028,15 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     for (int q = 0; q < 3; ++q)
                         if (phr >> q & 1u) {
                             const size_t is = sidx(l, q, hw.s, n), ir = sidx(l, q, hw.r, n);
-                            S.icur[is] = cadd(S.icur[is], S.icur[ir]);
+                            const double2 ni = cadd(S.icur[is], S.icur[ir]);
+                            S.icur[is] = ni;
+                            S.icur32[is] = make_float2((float)ni.x, (float)ni.y);
                         }
-                    S.mice[(size_t)l * n + hw.r] = 0.0;
                 }
                 if (hw.dir == 1) {
                     S.top[hw.s] = S.top[hw.r];
                     S.ptop[hw.s] = S.ptop[hw.r];
                 }
-                const u128 sfx = ld128(s_sfx) + ld128(I.acc + 2 * (size_t)ws);
-                st128(s_sfx, sfx);
-                X.dec_score[t] = fx_to_d(sfx);
                 I.qpar[hw.r] = -1;
             }
             if (tid < 2) {
@@ -713,33 +1047,33 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         __syncthreads();
         ns -= 1;
         stamp(3);
-        // ---- largest MICE of the reduced network
-        {
-            double mx = 0.0;
-            for (int j = tid; j < ns; j += NT) {
-                const int k = list_new[j];
-                for (int l = 0; l < L; ++l) mx = fmax(mx, S.mice[(size_t)l * n + k]);
-            }
-            mx = block_max_d<NT>(mx, smd);
-            if (tid == 0) X.dec_maxerr[t] = mx;
-        }
         // ============================================================ terms after the merge
-        const int nfe = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, nf_tot, np_tot, smi);
+        if (tid == 0) {
+            for (int l = 0; l < L; ++l) {               // r's cluster is gone (its MICE was read by the merge)
+                S.mice[(size_t)l * n + hw.r] = 0.0;
+                S.mice32[(size_t)l * n + hw.r] = 0.0f;
+            }
+            const u128 sfx = ld128(s_sfx) + ld128(s_dsum);
+            st128(s_sfx, sfx);
+            X.dec_score[t] = fx_to_d(sfx);
+        }
+        const int nfe = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, nf_tot, np_tot, sscan);
         __syncthreads();
         stamp(4);
-        terms += eval_entries<NT>(T, S, X, I, n, L, margin, 0, np_tot + nfe, false, hw.r, list_old, list_new,
-                                  I.acc, I.viol, &E, smi);
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot + nfe, kNew, list_old,
+                                       list_new, hw.r, nullptr, E, sscan);
         stamp(5);
         t += 1;
+        maxerr_done = false;
         if (verify) {
-            // every candidate again from scratch; the carried scores must match bit for bit
+            // every candidate again from scratch; the carried values must match bit for bit
             int cnt = 0;
             for (int w0 = 0; w0 < n; w0 += NT) {
                 const int w = w0 + tid;
                 int c2 = 0;
                 if (w < n) c2 = (X.slot[2 * w].s >= 0) + (X.slot[2 * w + 1].s >= 0);
                 int tot = 0;
-                int o = block_excl_scan<NT>(c2, &tot, smi) + cnt;
+                int o = block_excl_scan<NT>(c2, &tot, sscan) + cnt;
                 if (w < n)
                     for (int d = 0; d < 2; ++d) {
                         const Cand &c = X.slot[2 * w + d];
@@ -751,32 +1085,41 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 cnt += tot;
             }
             __syncthreads();
-            eval_entries<NT>(T, S, X, I, n, L, margin, 0, cnt, false, -1, list_new, list_new, I.vacc, I.vviol, &E,
-                             smi);
+            run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, cnt, kFresh, list_new, list_new, -1,
+                                  nullptr, E, sscan);
             int bad = 0;
             for (int c = tid; c < 2 * n; c += NT) {
                 if (X.slot[c].s < 0) continue;
                 if (I.viol[c] != I.vviol[c] || ld128(I.acc + 2 * (size_t)c) != ld128(I.vacc + 2 * (size_t)c)) ++bad;
             }
-            bad = block_sum_int<NT>(bad, smi);
-            if (tid == 0 && bad) C->inc_mismatch += bad;
+            Red rv;
+            rv.a = rv.b = rv.c = kNone;
+            rv.i = bad;
+            rv = block_red<NT>(rv, sred);
+            if (tid == 0 && rv.i) C->inc_mismatch += rv.i;
         }
+    }
+    if (!maxerr_done && t > 0) {
+        const double m = max_mice<NT>(S, n, L, sred);
+        if (tid == 0) X.dec_maxerr[t - 1] = m;
     }
     if (tid == 0) {
         C->t = t;
         C->n_super = ns;
         C->s_cur = fx_to_d(ld128(s_sfx));
+        C->rechecks = rechecks;
+        C->recheck_cands = recheck_cands;
         if (prof) C->sweep_flops = (double)terms;     // terms evaluated (profile mode)
     }
 }
 
-template <int NT>
+template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify) {
-    inc_run<NT>(T, S, X, I, C, verify != 0);
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0);
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
-template <int NT>
+template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf) {
     __shared__ Topo sT;
     __shared__ State sS;
@@ -794,7 +1137,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT>(sT, sS, sX, sI, C, false);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -803,17 +1146,19 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     }
 }
 
-constexpr int kIncThreads = 1024;           // one feeder on one SM
+constexpr int kIncThreads = 512;            // one feeder on one SM
 constexpr int kIncBatchThreads = 512;       // batches: several feeders per SM
 
-cudaError_t launch_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
-    k_search_inc<kIncThreads><<<1, kIncThreads, 0, st>>>(T, S, X, I, C, verify);
+cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
+    if (precision == 1) k_search_inc<kIncThreads, 1><<<1, kIncThreads, 0, st>>>(T, S, X, I, C, verify);
+    else k_search_inc<kIncThreads, 0><<<1, kIncThreads, 0, st>>>(T, S, X, I, C, verify);
     return cudaGetLastError();
 }
 
-cudaError_t launch_search_inc_batch(const BatchFeeder *fd, const int *order, int nf, cudaStream_t st) {
+cudaError_t launch_search_inc_batch(int precision, const BatchFeeder *fd, const int *order, int nf, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
-    k_search_inc_batch<kIncBatchThreads><<<nf, kIncBatchThreads, 0, st>>>(fd, order, nf);
+    if (precision == 1) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, 0, st>>>(fd, order, nf);
+    else k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, 0, st>>>(fd, order, nf);
     return cudaGetLastError();
 }
 

@@ -147,14 +147,18 @@ struct IncWork {
 
 // Per-feeder buffers of the incremental search.
 struct Inc {
-    unsigned long long *acc;    // [2n][2] D(c) of each candidate slot, fixed point (low, high word)
-    int *viol;                  // [2n] (cluster, scenario) terms above the margin; kIncDead: no candidate
+    unsigned long long *acc;    // [2n][2] carried D(c) of each candidate slot, fixed point (low, high word)
+    unsigned long long *bnd;    // [2n][2] precision 1: carried bound on |D32 - D64|, fixed point
+    int *viol;                  // [2n] precision 0: terms above the margin; precision 1: terms surely
+                                //      above it; kIncDead: no candidate in the slot
+    int *vmay;                  // [2n] precision 1: terms not surely within the margin
     int *qpar;                  // [n] super-node holding the parent of the cluster's top (-1: slack's cluster)
     int *fpair;                 // [n] slot pairs whose candidates are rebuilt after the merge
     IncWork *work;              // [2n] work entries of one iteration
     double *cbuf;               // [n * 10 L] the merge's new voltages, magnitudes and MICE
-    unsigned long long *vacc;   // [2n][2] verification: every term re-evaluated (engine 3)
+    unsigned long long *vacc;   // [2n][2] FP64 rescoring (precision-1 recheck, verification)
     int *vviol;                 // [2n]
+    int *rlist;                 // [2n] slots rescored in FP64 in one iteration
 };
 constexpr int kIncDead = 1 << 30;
 

@@ -157,7 +157,10 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(f.C, 1);
     Inc &I = f.I;
     c.take(I.acc, 4 * N);
+    c.take(I.bnd, 4 * N);
     c.take(I.viol, 2 * N);
+    c.take(I.vmay, 2 * N);
+    c.take(I.rlist, 2 * N);
     c.take(I.qpar, N);
     c.take(I.fpair, N);
     c.take(I.work, 2 * N);

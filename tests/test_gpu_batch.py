@@ -50,11 +50,13 @@ def _check_against_single(ctx, feeders, plist, items, parts):
         assert np.array_equal(sup, ctx.assignment())
 
 
+@pytest.mark.parametrize("engine", [1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_matches_single_feeder_runs(ctx, precision):
+def test_batch_matches_single_feeder_runs(ctx, precision, engine):
     batch = _batch(10, 40, 400, seed=precision * 100)
     feeders = [f for f, _ in batch]
-    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=precision) for _, r in batch]
+    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=precision, engine=engine)
+             for _, r in batch]
     items, parts, stats = ctx.reduce_batch(feeders, plist)
     assert stats["fallbacks"] == 0 and stats["ctas"] >= 1
     assert stats["candidates"] == sum(it["candidates"] for it in items)
@@ -114,7 +116,7 @@ def test_batch_rejects_an_invalid_tree(ctx):
 def test_autotune_picks_a_shape_and_keeps_results(ctx):
     batch = _batch(12, 40, 300, seed=31)
     feeders = [f for f, _ in batch]
-    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1) for _, r in batch]
+    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1, engine=1) for _, r in batch]
     ref, ref_parts, _ = ctx.reduce_batch(feeders, plist)
     cfg, ms = ctx.batch_autotune(feeders, plist)
     assert cfg in (0, 1, 2, 3) and all(m > 0 and math.isfinite(m) for m in ms)
@@ -129,7 +131,7 @@ def test_autotune_picks_a_shape_and_keeps_results(ctx):
 def test_every_team_shape_matches_single_runs(ctx, config):
     batch = _batch(6, 40, 500, seed=41 + config)
     feeders = [f for f, _ in batch]
-    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1) for _, r in batch]
+    plist = [params(margin=r["margin"], target_reduction=r["target"], precision=1, engine=1) for _, r in batch]
     ctx.set_batch_config(config)
     items, parts, stats = ctx.reduce_batch(feeders, plist)
     assert stats["config"] == config and stats["ctas"] % (1 << config) == 0

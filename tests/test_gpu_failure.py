@@ -27,11 +27,11 @@ def ctx():
 def test_search_barrier_timeout_is_reported_and_the_context_recovers(ctx):
     import paper_2510_19608_gb300 as K
     f, run = fg.preset("feeder1000", n_bus=300)
-    p_ok = K.default_params(margin=run["margin"], target_reduction=0.5, precision=1)
+    p_ok = K.default_params(margin=run["margin"], target_reduction=0.5, precision=1, engine=1)
     ctx.reduce(f, p_ok)
     ref = ctx.decisions()
     with pytest.raises(K.OkrError) as e:
-        ctx.reduce(f, K.default_params(margin=run["margin"], target_reduction=0.5, precision=1, max_spins=1))
+        ctx.reduce(f, K.default_params(margin=run["margin"], target_reduction=0.5, precision=1, max_spins=1, engine=1))
     assert e.value.status == ETIMEOUT
     ctx.reduce(f, p_ok)
     again = ctx.decisions()
@@ -42,8 +42,8 @@ def test_batch_team_barrier_timeout_is_reported_per_feeder(ctx):
     import paper_2510_19608_gb300 as K
     batch = fg.batch_presets(count=6, first_seed=50, n_lo=100, n_hi=300)
     feeders = [f for f, _ in batch]
-    ok = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=1) for _, r in batch]
-    bad = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=1, max_spins=1)
+    ok = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=1, engine=1) for _, r in batch]
+    bad = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=1, max_spins=1, engine=1)
            for _, r in batch]
     ctx.set_batch_config(1)                               # teams of two CTAs: their barriers wait
     items, _, _ = ctx.reduce_batch(feeders, bad)

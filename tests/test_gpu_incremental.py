@@ -45,11 +45,12 @@ VERIFY = {
 }
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", sorted(VERIFY))
-def test_carried_scores_equal_a_fresh_evaluation(ctx, name):
+def test_carried_scores_equal_a_fresh_evaluation(ctx, name, precision):
     make, margin, target = VERIFY[name]
     f = make()
-    ctx.reduce(f, params(margin=margin, target_reduction=target, engine=3))
+    ctx.reduce(f, params(margin=margin, target_reduction=target, engine=3, precision=precision))
     s = ctx.summary()
     assert s["engine"] == 2
     assert s["n_iter"] > 0
@@ -69,6 +70,8 @@ def test_auto_engine_choice(ctx):
     ctx.reduce(f, params(margin=0.005))
     assert ctx.summary()["engine"] == 2
     ctx.reduce(f, params(margin=0.005, precision=1))
+    assert ctx.summary()["engine"] == 2
+    ctx.reduce(f, params(margin=0.005, precision=1, engine=1))
     assert ctx.summary()["engine"] == 1
     ctx.reduce(f, params(margin=0.005, objective=1))
     assert ctx.summary()["engine"] == 1
@@ -77,7 +80,7 @@ def test_auto_engine_choice(ctx):
 def test_incremental_engine_rejects_what_it_does_not_run(ctx):
     import paper_2510_19608_gb300 as K
     f, _ = fg.preset("feeder40")
-    for bad in (dict(engine=2, precision=1), dict(engine=2, objective=1), dict(engine=3, precision=1),
+    for bad in (dict(engine=2, objective=1), dict(engine=3, objective=1), dict(engine=2, precision=2),
                 dict(engine=4), dict(engine=-1)):
         with pytest.raises(K.OkrError) as e:
             ctx.reduce(f, params(margin=0.005, **bad))
@@ -94,10 +97,11 @@ def test_profile_counts_terms(ctx):
     assert s["phase_ms"][0] > 0.0
 
 
-def test_batch_incremental_equals_single_runs(ctx):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_incremental_equals_single_runs(ctx, precision):
     batch = fg.batch_presets(count=10, first_seed=70, n_lo=100, n_hi=600)
     feeders = [f for f, _ in batch]
-    ps = [params(margin=r["margin"], target_reduction=r["target"]) for _, r in batch]
+    ps = [params(margin=r["margin"], target_reduction=r["target"], precision=precision) for _, r in batch]
     items, parts, stats = ctx.reduce_batch(feeders, ps)
     assert stats["fallbacks"] == 0
     for f, p, it, part in zip(feeders, ps, items, parts):
@@ -117,7 +121,8 @@ def test_batch_mixing_engines(ctx):
     its single run."""
     batch = fg.batch_presets(count=6, first_seed=90, n_lo=100, n_hi=400)
     feeders = [f for f, _ in batch]
-    ps = [params(margin=r["margin"], target_reduction=r["target"], precision=i % 2) for i, (_, r) in enumerate(batch)]
+    ps = [params(margin=r["margin"], target_reduction=r["target"], precision=i % 2, engine=1 + (i // 2) % 2)
+          for i, (_, r) in enumerate(batch)]
     items, parts, _ = ctx.reduce_batch(feeders, ps)
     for f, p, it, part in zip(feeders, ps, items, parts):
         assert it["status"] == 0

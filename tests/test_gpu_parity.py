@@ -44,6 +44,7 @@ ENGINES = {
     "sweep-fp64": dict(engine=1, precision=0),
     "sweep-mixed": dict(engine=1, precision=1),
     "incremental": dict(engine=2, precision=0),
+    "incremental-mixed": dict(engine=2, precision=1),
 }
 
 
