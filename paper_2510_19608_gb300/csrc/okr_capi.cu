@@ -1128,7 +1128,9 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         if (cnt == 0) continue;
         if (g >= 2) {                           // one CTA per feeder
             ctas = std::max(ctas, cnt);
-            CK(launch_search_inc_batch(g - 2, bf_d, order_d + first, cnt, st));
+            int max_n = 2;
+            for (int i = 0; i < cnt; ++i) max_n = std::max(max_n, (int)feeders[ord[g][i]].n_bus);
+            CK(launch_search_inc_batch(g - 2, max_n, bf_d, order_d + first, cnt, st));
             continue;
         }
         const int nteams = std::min(cnt, ctx->num_sms * per_sm[g] / team);

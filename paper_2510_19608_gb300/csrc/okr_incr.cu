@@ -84,6 +84,23 @@ __device__ __forceinline__ u128 to_fx(double d) {
     return (b >> 63) ? (u128)0 - v : v;
 }
 
+// The same truncation for a float, with integer operations only (FP64
+// instructions are scarce on this GPU): equal to to_fx((double)f).
+__device__ __forceinline__ u128 to_fx32(float f) {
+    const unsigned b = __float_as_uint(f);
+    int e = (int)((b >> 23) & 0xff);
+    if (e == 0xff) return 0;
+    unsigned m = b & 0x7fffffu;
+    if (e == 0) e = 1;
+    else m |= 1u << 23;
+    // f = m * 2^(e - 150), so f * 2^100 = m * 2^(e - 50)
+    const int sh = e - 150 + kFxShift;
+    u128 v;
+    if (sh >= 0) v = sh >= 128 ? (u128)0 : ((u128)m << sh);
+    else v = sh <= -32 ? (u128)0 : (u128)(m >> (-sh));
+    return (b >> 31) ? (u128)0 - v : v;
+}
+
 __device__ __forceinline__ double fx_to_d(u128 v) {
     const bool neg = (v & kSignBit) != 0;
     const u128 a = neg ? (u128)0 - v : v;
@@ -156,6 +173,46 @@ __device__ __forceinline__ Red block_red(Red v, Red *sm) {
         x.i = 0;
         if (lane < NT / 32) x = sm[lane];
         for (int o = 16; o > 0; o >>= 1) x = red_op(x, red_shfl(x, o));
+        if (lane == 0) sm[32] = x;
+    }
+    __syncthreads();
+    return sm[32];
+}
+
+// The same with 64-bit minima (precision 1: every key fits 64 bits).
+struct Red64 {
+    unsigned long long a, b, c;
+    int i;
+};
+
+template <int NT>
+__device__ __forceinline__ Red64 block_red64(Red64 v, Red64 *sm) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    auto op = [](Red64 x, Red64 y) {
+        Red64 r;
+        r.a = x.a < y.a ? x.a : y.a;
+        r.b = x.b < y.b ? x.b : y.b;
+        r.c = x.c < y.c ? x.c : y.c;
+        r.i = x.i + y.i;
+        return r;
+    };
+    auto shfl = [](Red64 x, int o) {
+        Red64 r;
+        r.a = __shfl_xor_sync(0xffffffffu, x.a, o);
+        r.b = __shfl_xor_sync(0xffffffffu, x.b, o);
+        r.c = __shfl_xor_sync(0xffffffffu, x.c, o);
+        r.i = __shfl_xor_sync(0xffffffffu, x.i, o);
+        return r;
+    };
+    for (int o = 16; o > 0; o >>= 1) v = op(v, shfl(v, o));
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        Red64 x;
+        x.a = x.b = x.c = ~0ull;
+        x.i = 0;
+        if (lane < NT / 32) x = sm[lane];
+        for (int o = 16; o > 0; o >>= 1) x = op(x, shfl(x, o));
         if (lane == 0) sm[32] = x;
     }
     __syncthreads();
@@ -253,7 +310,7 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, 
                                           bool valid, int gl, double margin, double *out, u128 *d_out, int *nv_out) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
-    const bool on = lv && p < 3 && (T.ph[k] >> p & 1u);
+    const bool on = lv && p < 3 && (__ldg(T.ph + k) >> p & 1u);
     double e = 0.0;
     if (on) {
         const bool fixed = (k == c.s) && c.fixed;
@@ -261,13 +318,14 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, 
         const size_t ik = sidx(l, p, k, n);
         double2 v = S.vcur[ik];
         if (!fixed) {
-            const unsigned phr = T.ph[c.r];
-            const int y = T.lca[(size_t)(sside ? c.s : c.r) * n + k];
+            const unsigned phr = __ldg(T.ph + c.r);
+            const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
             const double2 *zy = T.zc + (size_t)y * 9 + p * 3, *za = T.zc + (size_t)c.a * 9 + p * 3;
             double2 dv = make_double2(0.0, 0.0);
             for (int q = 0; q < 3; ++q) {
                 if (!(phr >> q & 1u)) continue;
-                const double2 g = sside ? csub(zy[q], za[q]) : csub(za[q], zy[q]);
+                const double2 zyq = __ldg(zy + q), zaq = __ldg(za + q);
+                const double2 g = sside ? csub(zyq, zaq) : csub(zaq, zyq);
                 dv = cadd(dv, cmul(g, S.icur[sidx(l, q, c.r, n)]));
             }
             v = cadd(v, dv);
@@ -315,7 +373,7 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
                                           u128 *b_out, int *ns_out, int *nm_out) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
-    const bool on = lv && p < 3 && (T.ph[k] >> p & 1u);
+    const bool on = lv && p < 3 && (__ldg(T.ph + k) >> p & 1u);
     float e = 0.0f, b = 0.0f;
     if (on) {
         const bool fixed = (k == c.s) && c.fixed;
@@ -323,7 +381,7 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
         const size_t ik = sidx(l, p, k, n);
         float hr = S.hr32[ik], lr = S.lr32[ik];
         float bx = 0.0f;
-        if (k == c.s && (T.ph[c.r] >> p & 1u)) {
+        if (k == c.s && (__ldg(T.ph + c.r) >> p & 1u)) {
             const size_t ir = sidx(l, p, c.r, n);
             const float dr = (float)(S.mcur[ir] - S.mcur[ik]);
             const float hrr = S.hr32[ir] + dr, lrr = S.lr32[ir] + dr;
@@ -333,9 +391,9 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
         }
         float delta = 0.0f, bd = 0.0f;
         if (!fixed) {
-            const unsigned phr = T.ph[c.r];
+            const unsigned phr = __ldg(T.ph + c.r);
             const float2 v = S.v32[ik];
-            const int y = T.lca[(size_t)(sside ? c.s : c.r) * n + k];
+            const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
             const float2 *zhy = T.zh + (size_t)y * 9 + p * 3, *zly = T.zlo + (size_t)y * 9 + p * 3;
             const float2 *zha = T.zh + (size_t)c.a * 9 + p * 3, *zla = T.zlo + (size_t)c.a * 9 + p * 3;
             float2 dv = make_float2(0.0f, 0.0f);
@@ -343,8 +401,9 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
             for (int q = 0; q < 3; ++q) {
                 if (!(phr >> q & 1u)) continue;
                 const float2 iq = S.icur32[sidx(l, q, c.r, n)];
-                float gx = (zhy[q].x - zha[q].x) + (zly[q].x - zla[q].x);
-                float gy = (zhy[q].y - zha[q].y) + (zly[q].y - zla[q].y);
+                const float2 hy = __ldg(zhy + q), ha = __ldg(zha + q), ly = __ldg(zly + q), la = __ldg(zla + q);
+                float gx = (hy.x - ha.x) + (ly.x - la.x);
+                float gy = (hy.y - ha.y) + (ly.y - la.y);
                 if (!sside) { gx = -gx; gy = -gy; }
                 dv.x = fmaf(gx, iq.x, fmaf(-gy, iq.y, dv.x));
                 dv.y = fmaf(gx, iq.y, fmaf(gy, iq.x, dv.y));
@@ -374,8 +433,8 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
         // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
         // factor 1.001 covers the rounding of the bound's own arithmetic
         const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(mo) + fabsf(mr) + fabsf(m)));
-        d = to_fx((double)dd);
-        bb = to_fx((double)bl) + 3;      // + the truncations of both terms to fixed point
+        d = to_fx32(dd);
+        bb = to_fx32(bl) + 3;            // + the truncations of both terms to fixed point
         ns = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
         nm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
     }
@@ -490,6 +549,73 @@ struct EvalSmem {
     int off[kTE + 1];
 };
 
+// Per-slot selection records (shared memory when they fit, else global):
+//   r0 (precision 0): okey(D) of a feasible candidate, kNone otherwise;
+//   r1 (precision 1): order-preserving keys of the lower and upper end of the
+//       interval that holds the FP64 score, in units of 2^-56 p.u. (lower end
+//       rounded down, upper end up); the lower key is ~0 when the candidate is
+//       surely infeasible, the upper key when it is not surely feasible (or
+//       the slot holds no candidate).  Integer keys keep the selection off the
+//       FP64 pipe;
+//   tkey: the tie key (caller r, caller s), ~0u for an empty slot;
+//   maxm: per super-node, its largest MICE over the scenarios (0 when absorbed);
+//   span: per slot pair, what the changed-set scan tests first.
+struct Rec {
+    u128 *r0;
+    ulonglong2 *r1;
+    unsigned *tkey;
+    double *maxm;
+    ushort4 *span;      // per slot pair: bus span [x, y) holding both candidates' ranges, s and r;
+                        // z: the quotient parent (0xffff: none); w: empty pair when 0
+};
+
+constexpr int kKeyShift = 44;                       // 2^-100 -> 2^-56 units
+constexpr unsigned long long kKeyNone = ~0ull;
+
+// floor(v / 2^44) of a signed fixed-point value, as an order-preserving key;
+// *ok = false when it does not fit 64 bits.
+__device__ __forceinline__ unsigned long long key_floor(u128 v, bool *ok) {
+    const bool neg = (v & kSignBit) != 0;
+    const u128 q = neg ? ~((~v) >> kKeyShift) : (v >> kKeyShift);      // arithmetic shift
+    const u128 top = q >> 63;                                          // all sign bits above 63
+    *ok = neg ? (top == ((u128)1 << 65) - 1) : (top == 0);
+    return (unsigned long long)q ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ unsigned long long key_ceil(u128 v, bool *ok) {
+    // ceil(v / 2^44) = -floor(-v / 2^44)
+    const unsigned long long k = key_floor((u128)0 - v, ok);
+    return (unsigned long long)(-(long long)(k ^ 0x8000000000000000ull)) ^ 0x8000000000000000ull;
+}
+__device__ __forceinline__ long long key_val(unsigned long long k) { return (long long)(k ^ 0x8000000000000000ull); }
+__device__ __forceinline__ unsigned long long val_key(long long v) {
+    return (unsigned long long)v ^ 0x8000000000000000ull;
+}
+
+template <int PREC>
+__device__ __forceinline__ void set_rec(const Rec &R, int sl, u128 d, u128 b, int viol, int vmay) {
+    if (PREC == 0) {
+        R.r0[sl] = (viol == 0) ? okey(d) : kNone;
+    } else {
+        unsigned long long lo = kKeyNone, hi = kKeyNone;
+        if (viol == 0) {
+            bool ok;
+            lo = key_floor(d - b, &ok);
+            if (!ok) lo = ((d - b) & kSignBit) ? 0ull : kKeyNone - 1;
+            if (vmay == 0) {
+                hi = key_ceil(d + b, &ok);
+                if (!ok) hi = kKeyNone;
+            }
+        }
+        R.r1[sl] = make_ulonglong2(lo, hi);
+    }
+}
+template <int PREC>
+__device__ __forceinline__ void kill_rec(const Rec &R, int sl) {
+    if (PREC == 0) R.r0[sl] = kNone;
+    else R.r1[sl] = make_ulonglong2(kKeyNone, kKeyNone);
+    R.tkey[sl] = ~0u;
+}
+
 // The merge's own evaluation (FP64, state before the merge): new voltage,
 // magnitude and MICE of each of its positions into the scratch.
 struct Commit {
@@ -498,14 +624,16 @@ struct Commit {
     const int *list;        // super-nodes before the merge
 };
 
-template <int NT>
+// Run by warps [warp0, warp0 + nw) only.
 __device__ __forceinline__ void commit_groups(const Topo &T, const State &S, const Inc &I, int n, int L, int G,
-                                              double margin, const Commit &cm) {
-    const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
+                                              double margin, const Commit &cm, int warp0, int nw) {
+    const int lw = ((int)threadIdx.x >> 5) - warp0, gpw = 32 / G, gl = threadIdx.x % G;
+    const int gi = lw * gpw + ((int)threadIdx.x & 31) / G, NG = nw * gpw;
     const Win &h = *cm.h;
     const int n1 = h.q1hi - h.q1lo, n2 = h.q2hi - h.q2lo;
     for (int r0 = 0; r0 < h.npos; r0 += NG) {
-        const int q = r0 + (NG - 1 - gi);               // the last warps first: the entries start at the first
+        if (r0 + lw * gpw >= h.npos) break;             // this warp's groups are all past the end
+        const int q = r0 + gi;
         bool valid = q < h.npos;
         int k = cm.wc.s;
         if (valid) {
@@ -522,15 +650,13 @@ __device__ __forceinline__ void commit_groups(const Topo &T, const State &S, con
 // Evaluates the terms of work entries [e0, e1) (tiles of kTE entries) and applies
 // them per the pass.  Mode-0 entries take positions from list_pre (and skip r*
 // after the merge), mode-1 entries from list_post; kFresh / kF64 use list_pre.
-// With cm != nullptr the merge's own evaluation runs alongside.  Returns the
-// number of terms evaluated.
+// Returns the number of terms evaluated.
 template <int NT, int PREC>
 __device__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
                                  double margin, float mlo, float mhi, int e0, int e1, int pass, const int *list_pre,
-                                 const int *list_post, int rstar, const Commit *cm, EvalSmem &E, int *sscan) {
+                                 const int *list_post, int rstar, EvalSmem &E, int *sscan, const Rec &R) {
     const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
     long long terms = 0;
-    bool commit_done = (cm == nullptr);
     for (int t0 = e0; t0 < e1; t0 += kTE) {
         const int ne = min(kTE, e1 - t0);
         int cnt = 0;
@@ -547,11 +673,8 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
         }
         terms += tot;
         __syncthreads();
-        if (!commit_done) {
-            commit_groups<NT>(T, S, I, n, L, G, margin, *cm);
-            commit_done = true;
-        }
         for (int r0 = 0; r0 < tot; r0 += NG) {
+            if (r0 + (tid >> 5) * (32 / G) >= tot) break;     // this warp's groups are all past the end
             const int q = r0 + gi;
             bool valid = q < tot;
             int ei = 0, k = 0;
@@ -602,29 +725,29 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
             const u128 d = ((u128)E.dhi[tid] << 64) | (u128)E.dlo[tid];
             const u128 b = ((u128)E.bhi[tid] << 64) | (u128)E.blo[tid];
             unsigned long long *a = I.acc + 2 * (size_t)sl, *bp = I.bnd + 2 * (size_t)sl;
-            if (pass == kOld) {
-                st128(a, ld128(a) - d);
-                I.viol[sl] -= E.n1[tid];
-                if (PREC == 1) {
-                    st128(bp, ld128(bp) - b);
-                    I.vmay[sl] -= E.n2[tid];
-                }
-            } else if (pass == kNew) {
-                if (w.mode == 1) {
-                    st128(a, d);
-                    I.viol[sl] = E.n1[tid];
-                    if (PREC == 1) {
-                        st128(bp, b);
-                        I.vmay[sl] = E.n2[tid];
-                    }
+            if (pass == kOld || pass == kNew) {
+                u128 na, nb = 0;
+                int nv, nm = 0;
+                if (pass == kNew && w.mode == 1) {
+                    na = d;
+                    nv = E.n1[tid];
+                    if (PREC == 1) { nb = b; nm = E.n2[tid]; }
+                } else if (pass == kNew) {
+                    na = ld128(a) + d;
+                    nv = I.viol[sl] + E.n1[tid];
+                    if (PREC == 1) { nb = ld128(bp) + b; nm = I.vmay[sl] + E.n2[tid]; }
                 } else {
-                    st128(a, ld128(a) + d);
-                    I.viol[sl] += E.n1[tid];
-                    if (PREC == 1) {
-                        st128(bp, ld128(bp) + b);
-                        I.vmay[sl] += E.n2[tid];
-                    }
+                    na = ld128(a) - d;
+                    nv = I.viol[sl] - E.n1[tid];
+                    if (PREC == 1) { nb = ld128(bp) - b; nm = I.vmay[sl] - E.n2[tid]; }
                 }
+                st128(a, na);
+                I.viol[sl] = nv;
+                if (PREC == 1) {
+                    st128(bp, nb);
+                    I.vmay[sl] = nm;
+                }
+                set_rec<PREC>(R, sl, na, nb, nv, nm);
             } else {
                 st128(I.vacc + 2 * (size_t)sl, d);
                 I.vviol[sl] = E.n1[tid];
@@ -632,80 +755,58 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
         }
         __syncthreads();
     }
-    if (!commit_done) commit_groups<NT>(T, S, I, n, L, G, margin, *cm);
     return terms;
 }
 
-// Slot pairs w handled by this thread: [wb, we), consecutive.
-template <int NT>
-__device__ __forceinline__ void my_pairs(int n, int &wb, int &we) {
-    const int per = (n + NT - 1) / NT;
-    wb = min(n, (int)threadIdx.x * per);
-    we = min(n, wb + per);
-}
-
 // Rebuilds the slot pairs listed in fp[0, nf) from the current clusters and
-// writes a full work entry for each valid candidate at I.work[base...).
-// Returns the number of entries written.
-template <int NT>
-__device__ int rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
-                             int base, int *sscan) {
-    int added = 0;
-    for (int i0 = 0; i0 < nf; i0 += NT) {
-        const int i = i0 + threadIdx.x;
+// appends a full work entry for each valid candidate at I.work[*cnt...]
+// (*cnt: a shared counter; the caller synchronises before reading it).
+template <int NT, int PREC>
+__device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
+                              int *cnt, const Rec &R) {
+    for (int i = threadIdx.x; i < nf; i += NT) {
+        const int w = fp[i];
         Cand c[2];
-        c[0].s = c[1].s = -1;
-        int cnt = 0;
-        if (i < nf) {
-            const int w = fp[i];
-            I.qpar[w] = slot_geometry(T, S, n, w, c[0], c[1]);
-            for (int d = 0; d < 2; ++d) {
-                X.slot[2 * w + d] = c[d];
-                if (c[d].s >= 0) {
-                    ++cnt;
-                } else {
-                    I.viol[2 * w + d] = kIncDead;
-                    st128(I.acc + 4 * (size_t)w + 2 * d, 0);
-                }
-            }
-        }
-        int tot = 0;
-        int off = block_excl_scan<NT>(cnt, &tot, sscan);
-        if (i < nf) {
-            const int w = fp[i];
+        const int x = slot_geometry(T, S, n, w, c[0], c[1]);
+        I.qpar[w] = x;
+        {
+            int lo = n, hi = 0;
             for (int d = 0; d < 2; ++d) {
                 if (c[d].s < 0) continue;
+                lo = min(lo, min(min(c[d].s, c[d].r), c[d].ns > 0 ? c[d].js : n));
+                lo = min(lo, c[d].nr > 0 ? c[d].jr : n);
+                hi = max(hi, max(max(c[d].s, c[d].r) + 1, max(c[d].js + c[d].ns, c[d].jr + c[d].nr)));
+            }
+            const bool any = c[0].s >= 0 || c[1].s >= 0;
+            R.span[w] = make_ushort4((unsigned short)(any ? lo : 0), (unsigned short)(any ? hi : 0),
+                                     (unsigned short)(x >= 0 ? x : 0xffff), (unsigned short)(any ? 1 : 0));
+        }
+        for (int d = 0; d < 2; ++d) {
+            const int sl = 2 * w + d;
+            X.slot[sl] = c[d];
+            if (c[d].s >= 0) {
                 int2 seg[kIncMaxSeg];
                 const int ns = full_segments(c[d], S.sn_rank, seg);
-                write_entry(I.work + base + added + off, 2 * w + d, 1, ns, seg);
-                ++off;
+                write_entry(I.work + atomicAdd(cnt, 1), sl, 1, ns, seg);
+                R.tkey[sl] = (unsigned)c[d].key;
+            } else {
+                I.viol[sl] = kIncDead;
+                st128(I.acc + 2 * (size_t)sl, 0);
+                kill_rec<PREC>(R, sl);
             }
         }
-        added += tot;
     }
-    return added;
 }
 
 }  // namespace
 
 // ---------------------------------------------------------------- the search
-// Largest MICE over the clusters (dead slots hold 0), for the decision record.
-template <int NT>
-__device__ double max_mice(const State &S, int n, int L, Red *sred) {
-    u128 m = kNone;
-    for (int w = threadIdx.x; w < n; w += NT)
-        for (int l = 0; l < L; ++l)
-            m = umin(m, ~(u128)(unsigned long long)__double_as_longlong(S.mice[(size_t)l * n + w]));
-    Red v;
-    v.a = m;
-    v.b = v.c = kNone;
-    v.i = 0;
-    v = block_red<NT>(v, sred);
-    return v.a == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~v.a);
-}
+// Bytes of the selection records of an n-bus feeder.
+__host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)56 * n + 64; }
 
 template <int NT, int PREC>
-__device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify) {
+__device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
+                        unsigned char *recmem) {
     static_assert(NT >= kTE && NT <= 1024, "thread count");
     __shared__ __align__(16) EvalSmem E;
     __shared__ __align__(16) Red sred[33];
@@ -713,6 +814,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     __shared__ Win h;
     __shared__ unsigned long long s_sfx[2];     // SMICE of the committed state, fixed point
     __shared__ unsigned long long s_dsum[2];    // the last merge's change of it
+    __shared__ int s_cnt[4];                    // append counters: rebuilt pairs, changed entries, entries, R
     const int n = T.n, L = T.L, tid = threadIdx.x;
     const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
     const double margin = C->margin;
@@ -721,8 +823,18 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     const bool prof = C->profile != 0;
     const u128 tau_fx = to_fx(C->tau);
     if (C->done || C->t >= max_merges) return;
+    // selection records: r0 or r1 (2n x 16 B), tkey (2n x 4 B), maxm (n x 8 B), span (n x 8 B)
+    Rec R;
+    R.r0 = reinterpret_cast<u128 *>(recmem);
+    R.r1 = reinterpret_cast<ulonglong2 *>(recmem);
+    R.tkey = reinterpret_cast<unsigned *>(recmem + (size_t)32 * n);
+    R.maxm = reinterpret_cast<double *>(recmem + (size_t)40 * n);
+    R.span = reinterpret_cast<ushort4 *>(recmem + (size_t)48 * n);
     int t = 0, ns = n;
-    if (tid == 0) { s_sfx[0] = 0ull; s_sfx[1] = 0ull; }     // every MICE starts at 0
+    if (tid == 0) {
+        s_sfx[0] = s_sfx[1] = 0ull;                 // every MICE starts at 0
+        s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+    }
     unsigned long long tp = 0;
     auto stamp = [&](int i) {
         if (prof && tid == 0) { const unsigned long long now = gtimer_inc(); C->phase_ns[i] += now - tp; tp = now; }
@@ -732,13 +844,17 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     bool maxerr_done = true;                // dec_maxerr of the last merge written
 
     // ---- every slot pair from the initial clusters (all singletons), every term
-    for (int w = tid; w < n; w += NT) I.fpair[w] = w;
+    for (int w = tid; w < n; w += NT) {
+        I.fpair[w] = w;
+        R.maxm[w] = 0.0;
+    }
+    __syncthreads();
+    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R);
     __syncthreads();
     {
-        const int ne = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, n, 0, sscan);
-        __syncthreads();
+        const int ne = s_cnt[2];
         terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kNew, S.sn_list[0], S.sn_list[0],
-                                       -1, nullptr, E, sscan);
+                                       -1, E, sscan, R);
     }
     if (prof && tid == 0) tp = gtimer_inc();
 
@@ -750,30 +866,40 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         const int *list_old = S.sn_list[t & 1];
         int *list_new = S.sn_list[(t + 1) & 1];
         // ============================================================ selection
-        // pass A: precision 0: minimum over feasible; precision 1: smallest lower
-        // end over possibly feasible (m_lo), smallest upper end over surely
-        // feasible (m_hi); the largest MICE of the last merge; candidates.
+        // pass A: precision 0: the minimum over feasible candidates; precision 1:
+        // the smallest lower end (m_lo) and the smallest upper end (m_hi); the
+        // largest MICE after the last merge; the candidates.
         Red ra;
         ra.a = ra.b = ra.c = kNone;
         ra.i = 0;
-        for (int c = tid; c < 2 * n; c += NT) {
-            if ((c & 1) == 0 && t > 0)
-                for (int l = 0; l < L; ++l)
-                    ra.c = umin(ra.c, ~(u128)(unsigned long long)__double_as_longlong(S.mice[(size_t)l * n + (c >> 1)]));
-            const int v = I.viol[c];
-            if (v >= kIncDead) continue;
-            ++ra.i;
-            if (v != 0) continue;
-            const u128 d = ld128(I.acc + 2 * (size_t)c);
-            if (PREC == 0) {
-                ra.a = umin(ra.a, okey(d));
-            } else {
-                const u128 b = ld128(I.bnd + 2 * (size_t)c);
-                ra.a = umin(ra.a, okey(d - b));
-                if (I.vmay[c] == 0) ra.b = umin(ra.b, okey(d + b));
+        if (PREC == 0) {
+            for (int c = tid; c < 2 * n; c += NT) {
+                if ((c & 1) == 0 && t > 0)
+                    ra.c = umin(ra.c, ~(u128)(unsigned long long)__double_as_longlong(R.maxm[c >> 1]));
+                if (R.tkey[c] != ~0u) ++ra.i;
+                ra.a = umin(ra.a, R.r0[c]);
             }
+            ra = block_red<NT>(ra, sred);
+        } else {
+            Red64 r6;
+            r6.a = r6.b = r6.c = ~0ull;
+            r6.i = 0;
+            for (int c = tid; c < 2 * n; c += NT) {
+                if ((c & 1) == 0 && t > 0) {
+                    const unsigned long long mb = ~(unsigned long long)__double_as_longlong(R.maxm[c >> 1]);
+                    r6.c = mb < r6.c ? mb : r6.c;
+                }
+                if (R.tkey[c] != ~0u) ++r6.i;
+                const ulonglong2 q = R.r1[c];
+                r6.a = q.x < r6.a ? q.x : r6.a;
+                r6.b = q.y < r6.b ? q.y : r6.b;
+            }
+            r6 = block_red64<NT>(r6, reinterpret_cast<Red64 *>(sred));
+            ra.a = r6.a == kKeyNone ? kNone : (u128)r6.a;
+            ra.b = r6.b == kKeyNone ? kNone : (u128)r6.b;
+            ra.c = r6.c == ~0ull ? kNone : ~(u128)(~r6.c);
+            ra.i = r6.i;
         }
-        ra = block_red<NT>(ra, sred);
         const int nvalid = ra.i;
         if (tid == 0) {
             C->candidates += nvalid;
@@ -781,6 +907,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             X.dec_ncand[t] = nvalid;
             if (t > 0)
                 X.dec_maxerr[t - 1] = ra.c == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~ra.c);
+            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
         const double s_cur = fx_to_d(ld128(s_sfx));
         if (t < X.rec_iters) {
@@ -818,9 +945,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             rb.a = rb.b = rb.c = kNone;
             rb.i = 0;
             for (int c = tid; c < 2 * n; c += NT) {
-                if (I.viol[c] != 0) continue;
-                const u128 k = okey(ld128(I.acc + 2 * (size_t)c));
-                if (k <= ek) rb.a = umin(rb.a, ((u128)X.slot[c].key << 32) | (u128)(unsigned)c);
+                const u128 k = R.r0[c];
+                if (k <= ek) rb.a = umin(rb.a, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
                 else rb.b = umin(rb.b, k);
             }
             rb = block_red<NT>(rb, sred);
@@ -828,55 +954,61 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             if (rb.b != kNone) gap = fx_to_d((rb.b ^ kSignBit) - edge);
         } else {
             const bool has_hi = ra.b != kNone;
-            const u128 ein = okey((ra.a ^ kSignBit) + tau_fx);
-            const u128 eout = has_hi ? okey((ra.b ^ kSignBit) + tau_fx) : kNone;
-            Red rb;
-            rb.a = rb.b = rb.c = kNone;
-            rb.i = 0;
+            bool ok;
+            const long long tau_dn = key_val(key_floor(tau_fx, &ok)), tau_up = key_val(key_ceil(tau_fx, &ok));
+            const long long m_lo = key_val((unsigned long long)ra.a);
+            const long long m_hi = has_hi ? key_val((unsigned long long)ra.b) : 0;
+            const unsigned long long ein = val_key(m_lo + tau_dn);
+            const unsigned long long eout = has_hi ? val_key(m_hi + tau_up) : kKeyNone;
+            Red64 r6;
+            r6.a = r6.b = r6.c = ~0ull;
+            r6.i = 0;
             for (int c = tid; c < 2 * n; c += NT) {
-                if (I.viol[c] != 0) continue;
-                const u128 d = ld128(I.acc + 2 * (size_t)c), b = ld128(I.bnd + 2 * (size_t)c);
-                const u128 lo = okey(d - b), hi = okey(d + b);
-                const bool in_sure = I.vmay[c] == 0 && hi <= ein;
-                const bool out_sure = has_hi && lo > eout;
-                const u128 key = (u128)X.slot[c].key;
-                if (in_sure) rb.a = umin(rb.a, (key << 32) | (u128)(unsigned)c);
-                else if (!out_sure) rb.b = umin(rb.b, key);
-                if (out_sure) rb.c = umin(rb.c, lo);
+                const ulonglong2 q = R.r1[c];
+                if (q.x == kKeyNone) continue;
+                const bool in_sure = q.y <= ein;
+                const bool out_sure = has_hi && q.x > eout;
+                const unsigned key = R.tkey[c];
+                if (in_sure) {
+                    const unsigned long long kc = ((unsigned long long)key << 32) | (unsigned)c;
+                    r6.a = kc < r6.a ? kc : r6.a;
+                } else if (!out_sure) {
+                    r6.b = key < r6.b ? key : r6.b;
+                }
+                if (out_sure) r6.c = q.x < r6.c ? q.x : r6.c;
             }
-            rb = block_red<NT>(rb, sred);
+            r6 = block_red64<NT>(r6, reinterpret_cast<Red64 *>(sred));
+            Red rb;
+            rb.a = r6.a == ~0ull ? kNone : (u128)r6.a;
+            rb.b = r6.b == ~0ull ? kNone : (u128)r6.b;
+            rb.c = r6.c == ~0ull ? kNone : (u128)r6.c;
+            rb.i = 0;
             const u128 ks = rb.a == kNone ? kNone : (rb.a >> 32);
             if (!(rb.b < ks)) {                          // no uncertain candidate can take the band's smallest key
                 ws = (int)(unsigned)(rb.a & 0xffffffffu);
-                if (rb.c != kNone) gap = fx_to_d((rb.c ^ kSignBit) - (eout ^ kSignBit));
+                if (rb.c != kNone) gap = (double)(key_val((unsigned long long)rb.c) - key_val(eout)) * 0x1p-56;
             } else {
                 // FP64 rescoring of R: the possible minimizers and the uncertain
                 // candidates with a key below the smallest surely-in key
-                int nR = 0;
-                for (int c0 = 0; c0 < 2 * n; c0 += NT) {
-                    const int c = c0 + tid;
-                    int f = 0;
-                    if (c < 2 * n && I.viol[c] == 0) {
-                        const u128 d = ld128(I.acc + 2 * (size_t)c), b = ld128(I.bnd + 2 * (size_t)c);
-                        const u128 lo = okey(d - b), hi = okey(d + b);
-                        const bool in_sure = I.vmay[c] == 0 && hi <= ein;
-                        const bool out_sure = has_hi && lo > eout;
-                        const bool unc = !in_sure && !out_sure && (u128)X.slot[c].key < ks;
-                        if (unc || !has_hi || lo <= okey(ra.b ^ kSignBit)) f = 1;
-                    }
-                    int tot = 0;
-                    const int o = block_excl_scan<NT>(f, &tot, sscan) + nR;
-                    if (f) {
+                const unsigned long long mh = has_hi ? (unsigned long long)ra.b : kKeyNone;
+                for (int c = tid; c < 2 * n; c += NT) {
+                    const ulonglong2 q = R.r1[c];
+                    if (q.x == kKeyNone) continue;
+                    const bool in_sure = q.y <= ein;
+                    const bool out_sure = has_hi && q.x > eout;
+                    const bool unc = !in_sure && !out_sure && (u128)R.tkey[c] < ks;
+                    if (unc || q.x <= mh) {
+                        const int o = atomicAdd(&s_cnt[3], 1);
                         I.rlist[o] = c;
                         int2 seg[kIncMaxSeg];
                         const int k = full_segments(X.slot[c], S.sn_rank, seg);
                         write_entry(I.work + o, c, 1, k, seg);
                     }
-                    nR += tot;
                 }
                 __syncthreads();
+                const int nR = s_cnt[3];
                 terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, nR, kF64, list_old, list_old,
-                                               -1, nullptr, E, sscan);
+                                               -1, E, sscan, R);
                 // exact selection over R, with the surely-in candidate of key ks
                 Red rc;
                 rc.a = rc.b = rc.c = kNone;
@@ -895,7 +1027,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         const int c = I.rlist[i];
                         if (I.vviol[c] != 0) continue;
                         const u128 k = okey(ld128(I.vacc + 2 * (size_t)c));
-                        if (k <= ek) rd.a = umin(rd.a, ((u128)X.slot[c].key << 32) | (u128)(unsigned)c);
+                        if (k <= ek) rd.a = umin(rd.a, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
                         else rd.b = umin(rd.b, k);
                     }
                     rd = block_red<NT>(rd, sred);
@@ -933,88 +1065,106 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         __syncthreads();
         const Win hw = h;
-        // ---- which candidates change: rebuilt pairs (next to s* or r*) and changed terms
-        int wb, we;
-        my_pairs<NT>(n, wb, we);
-        int nf_mine = 0, np_mine = 0;
-        for (int w = wb; w < we; ++w) {
-            if (w == hw.r) continue;
-            const int qp = I.qpar[w];
-            if (w == hw.s || qp == hw.r || qp == hw.s) { ++nf_mine; continue; }
-            for (int d = 0; d < 2; ++d) {
-                const Cand &c = X.slot[2 * w + d];
-                if (c.s >= 0 && touched(c, hw)) ++np_mine;
-            }
-        }
-        int nf_tot = 0, np_tot = 0;
-        int fo = block_excl_scan<NT>(nf_mine, &nf_tot, sscan);
-        int po = block_excl_scan<NT>(np_mine, &np_tot, sscan);
-        for (int w = wb; w < we && (nf_mine | np_mine); ++w) {
-            if (w == hw.r) continue;
-            const int qp = I.qpar[w];
-            if (w == hw.s || qp == hw.r || qp == hw.s) { I.fpair[fo++] = w; continue; }
-            for (int d = 0; d < 2; ++d) {
-                const Cand &c = X.slot[2 * w + d];
-                if (c.s < 0 || !touched(c, hw)) continue;
-                int2 seg[kIncMaxSeg];
-                const int k = changed_segments(c, hw, S.sn_rank, seg);
-                write_entry(I.work + po++, 2 * w + d, 0, k, seg);
+        // ---- which candidates change: rebuilt pairs (next to s* or r*) and
+        // changed terms; entries are appended in any order (the sums are exact).
+        // The last warps evaluate the merge's own FP64 values meanwhile.
+        {
+            constexpr int NW = NT / 32, CW = 4;
+            if ((tid >> 5) >= NW - CW) {
+                Commit cm;
+                cm.h = &h;
+                cm.wc = X.slot[ws];
+                cm.list = list_old;
+                commit_groups(T, S, I, n, L, G, margin, cm, NW - CW, CW);
+            } else {
+                // the changed buses lie in [hl, hh): a candidate whose span misses it is unchanged
+                int hl = min(hw.s, hw.r), hh = max(hw.s, hw.r) + 1;
+                if (hw.w1lo < hw.w1hi) { hl = min(hl, hw.w1lo); hh = max(hh, hw.w1hi); }
+                if (hw.w2lo < hw.w2hi) { hl = min(hl, hw.w2lo); hh = max(hh, hw.w2hi); }
+                for (int w = tid; w < n; w += (NW - CW) * 32) {
+                    const ushort4 sp = R.span[w];
+                    if (sp.w == 0 || w == hw.r) continue;
+                    const int qp = sp.z == 0xffff ? -1 : (int)sp.z;
+                    if (w == hw.s || qp == hw.r || qp == hw.s) {
+                        I.fpair[atomicAdd(&s_cnt[0], 1)] = w;
+                        continue;
+                    }
+                    if ((int)sp.y <= hl || (int)sp.x >= hh) continue;
+                    for (int d = 0; d < 2; ++d) {
+                        const Cand &c = X.slot[2 * w + d];
+                        if (c.s < 0 || !touched(c, hw)) continue;
+                        int2 seg[kIncMaxSeg];
+                        const int k = changed_segments(c, hw, S.sn_rank, seg);
+                        write_entry(I.work + atomicAdd(&s_cnt[1], 1), 2 * w + d, 0, k, seg);
+                    }
+                }
             }
         }
         __syncthreads();
+        const int nf_tot = s_cnt[0], np_tot = s_cnt[1];
+        if (tid == 0) s_cnt[2] = np_tot;                // rebuilt entries follow the changed ones
         stamp(1);
-        // ============================================================ terms before the merge, and the merge's own values
-        {
-            Commit cm;
-            cm.h = &h;
-            cm.wc = X.slot[ws];
-            cm.list = list_old;
-            terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot, kOld, list_old, list_new,
-                                           hw.r, &cm, E, sscan);
-        }
+        // ============================================================ terms before the merge
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot, kOld, list_old, list_new,
+                                       hw.r, E, sscan, R);
         __syncthreads();
         stamp(2);
         // ============================================================ the merge (FP64, then the FP32 copies)
         {
             const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
+            const int gl = tid % G, gi = tid / G, NG = NT / G, l = gl >> 2, p = gl & 3;
             u128 dsum = 0;
-            for (int j = tid; j < hw.npos; j += NT) {
+            // one lane per (position, scenario, phase)
+            for (int r0 = 0; r0 < hw.npos; r0 += NG) {
+                if (r0 + (tid >> 5) * (32 / G) >= hw.npos) break;
+                const int j = r0 + gi;
+                bool valid = j < hw.npos;
+                int k = hw.s;
+                if (valid) {
+                    k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : hw.s);
+                    valid = k != hw.r;
+                }
                 const bool fx = j >= n1 + n2;
-                const int k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : hw.s);
-                if (k == hw.r) continue;
                 const double *cb = I.cbuf + (size_t)j * 10 * L;
-                const unsigned phk = T.ph[k];
-                for (int l = 0; l < L; ++l) {
-                    for (int p = 0; p < 3; ++p) {
-                        if (!(phk >> p & 1u)) continue;
-                        const size_t ik = sidx(l, p, k, n);
-                        double mc = S.mcur[ik];
-                        if (!fx) {
-                            const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
-                            mc = cb[(l * 3 + p) * 3 + 2];
-                            S.vcur[ik] = v;
-                            S.mcur[ik] = mc;
-                            S.v32[ik] = make_float2((float)v.x, (float)v.y);
-                        }
-                        double hh = S.hi[ik], ll = S.lo[ik];
-                        if (k == hw.s) {
-                            const size_t ir = sidx(l, p, hw.r, n);
-                            hh = fmax(hh, S.hi[ir]);
-                            ll = fmin(ll, S.lo[ir]);
-                            S.hi[ik] = hh;
-                            S.lo[ik] = ll;
-                        }
-                        S.hr32[ik] = (float)(hh - mc);
-                        S.lr32[ik] = (float)(ll - mc);
+                if (valid && l < L && p < 3 && (T.ph[k] >> p & 1u)) {
+                    const size_t ik = sidx(l, p, k, n);
+                    double mc;
+                    if (!fx) {
+                        const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
+                        mc = cb[(l * 3 + p) * 3 + 2];
+                        S.vcur[ik] = v;
+                        S.mcur[ik] = mc;
+                        S.v32[ik] = make_float2((float)v.x, (float)v.y);
+                    } else {
+                        mc = S.mcur[ik];
                     }
-                    // the merge's exact score change: its FP64 terms in fixed point
+                    double hh = S.hi[ik], ll = S.lo[ik];
+                    if (k == hw.s) {
+                        const size_t ir = sidx(l, p, hw.r, n);
+                        hh = fmax(hh, S.hi[ir]);
+                        ll = fmin(ll, S.lo[ir]);
+                        S.hi[ik] = hh;
+                        S.lo[ik] = ll;
+                    }
+                    S.hr32[ik] = (float)(hh - mc);
+                    S.lr32[ik] = (float)(ll - mc);
+                }
+                // the merge's exact score change: its FP64 terms in fixed point
+                unsigned long long mb = 0;                  // MICE >= 0: bit patterns order like values
+                if (valid && l < L && p == 0) {
                     const double m = cb[9 * L + l];
                     double dd = m - S.mice[(size_t)l * n + k];
                     if (k == hw.s) dd -= S.mice[(size_t)l * n + hw.r];
                     dsum += to_fx(dd);
                     S.mice[(size_t)l * n + k] = m;
                     S.mice32[(size_t)l * n + k] = (float)m;
+                    mb = (unsigned long long)__double_as_longlong(m);
                 }
+                for (int o = 4; o < G; o <<= 1) {
+                    const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
+                    mb = y > mb ? y : mb;
+                }
+                if (valid && gl == 0) R.maxm[k] = __longlong_as_double((long long)mb);
             }
             if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
             // r's members join s; ranks past r drop by one; the new super-node list
@@ -1022,17 +1172,18 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 if (S.label[b] == hw.r) S.label[b] = hw.s;
             for (int b = hw.r + 1 + tid; b <= n; b += NT) S.sn_rank[b] -= 1;
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
-            if (tid == 0) {
-                const unsigned phr = T.ph[hw.r];
-                for (int l = 0; l < L; ++l) {
-                    for (int q = 0; q < 3; ++q)
-                        if (phr >> q & 1u) {
-                            const size_t is = sidx(l, q, hw.s, n), ir = sidx(l, q, hw.r, n);
-                            const double2 ni = cadd(S.icur[is], S.icur[ir]);
-                            S.icur[is] = ni;
-                            S.icur32[is] = make_float2((float)ni.x, (float)ni.y);
-                        }
+            // s takes r's injection
+            const unsigned phr = T.ph[hw.r];
+            if (tid < 3 * L) {
+                const int l = tid / 3, q = tid % 3;
+                if (phr >> q & 1u) {
+                    const size_t is = sidx(l, q, hw.s, n), ir = sidx(l, q, hw.r, n);
+                    const double2 ni = cadd(S.icur[is], S.icur[ir]);
+                    S.icur[is] = ni;
+                    S.icur32[is] = make_float2((float)ni.x, (float)ni.y);
                 }
+            }
+            if (tid == 0) {
                 if (hw.dir == 1) {
                     S.top[hw.s] = S.top[hw.r];
                     S.ptop[hw.s] = S.ptop[hw.r];
@@ -1042,51 +1193,47 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             if (tid < 2) {
                 X.slot[2 * hw.r + tid].s = -1;
                 I.viol[2 * hw.r + tid] = kIncDead;
+                kill_rec<PREC>(R, 2 * hw.r + tid);
             }
+            if (tid == 0) R.span[hw.r] = make_ushort4(0, 0, 0xffff, 0);
         }
         __syncthreads();
         ns -= 1;
         stamp(3);
         // ============================================================ terms after the merge
+        if (tid < L) {                                   // r's cluster is gone (its MICE was read by the merge)
+            S.mice[(size_t)tid * n + hw.r] = 0.0;
+            S.mice32[(size_t)tid * n + hw.r] = 0.0f;
+        }
         if (tid == 0) {
-            for (int l = 0; l < L; ++l) {               // r's cluster is gone (its MICE was read by the merge)
-                S.mice[(size_t)l * n + hw.r] = 0.0;
-                S.mice32[(size_t)l * n + hw.r] = 0.0f;
-            }
+            R.maxm[hw.r] = 0.0;
             const u128 sfx = ld128(s_sfx) + ld128(s_dsum);
             st128(s_sfx, sfx);
             X.dec_score[t] = fx_to_d(sfx);
         }
-        const int nfe = rebuild_pairs<NT>(T, S, X, I, n, I.fpair, nf_tot, np_tot, sscan);
+        rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], R);
         __syncthreads();
+        const int ne_new = s_cnt[2];
         stamp(4);
-        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot + nfe, kNew, list_old,
-                                       list_new, hw.r, nullptr, E, sscan);
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne_new, kNew, list_old, list_new, hw.r,
+                                       E, sscan, R);
         stamp(5);
         t += 1;
         maxerr_done = false;
         if (verify) {
             // every candidate again from scratch; the carried values must match bit for bit
-            int cnt = 0;
-            for (int w0 = 0; w0 < n; w0 += NT) {
-                const int w = w0 + tid;
-                int c2 = 0;
-                if (w < n) c2 = (X.slot[2 * w].s >= 0) + (X.slot[2 * w + 1].s >= 0);
-                int tot = 0;
-                int o = block_excl_scan<NT>(c2, &tot, sscan) + cnt;
-                if (w < n)
-                    for (int d = 0; d < 2; ++d) {
-                        const Cand &c = X.slot[2 * w + d];
-                        if (c.s < 0) continue;
-                        int2 seg[kIncMaxSeg];
-                        const int k = full_segments(c, S.sn_rank, seg);
-                        write_entry(I.work + o++, 2 * w + d, 1, k, seg);
-                    }
-                cnt += tot;
+            if (tid == 0) s_cnt[3] = 0;
+            __syncthreads();
+            for (int c = tid; c < 2 * n; c += NT) {
+                const Cand &cc = X.slot[c];
+                if (cc.s < 0) continue;
+                int2 seg[kIncMaxSeg];
+                const int k = full_segments(cc, S.sn_rank, seg);
+                write_entry(I.work + atomicAdd(&s_cnt[3], 1), c, 1, k, seg);
             }
             __syncthreads();
-            run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, cnt, kFresh, list_new, list_new, -1,
-                                  nullptr, E, sscan);
+            run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, s_cnt[3], kFresh, list_new, list_new, -1,
+                                  E, sscan, R);
             int bad = 0;
             for (int c = tid; c < 2 * n; c += NT) {
                 if (X.slot[c].s < 0) continue;
@@ -1100,8 +1247,12 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
     }
     if (!maxerr_done && t > 0) {
-        const double m = max_mice<NT>(S, n, L, sred);
-        if (tid == 0) X.dec_maxerr[t - 1] = m;
+        Red rm;
+        rm.a = rm.b = rm.c = kNone;
+        rm.i = 0;
+        for (int w = tid; w < n; w += NT) rm.a = umin(rm.a, ~(u128)(unsigned long long)__double_as_longlong(R.maxm[w]));
+        rm = block_red<NT>(rm, sred);
+        if (tid == 0) X.dec_maxerr[t - 1] = rm.a == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~rm.a);
     }
     if (tid == 0) {
         C->t = t;
@@ -1113,14 +1264,19 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     }
 }
 
+// Selection records in dynamic shared memory when use_smem, else in I.recbuf.
 template <int NT, int PREC>
-__global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify) {
-    inc_run<NT, PREC>(T, S, X, I, C, verify != 0);
+__global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
+                                                      int use_smem) {
+    extern __shared__ __align__(16) unsigned char inc_dyn[];
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, use_smem ? inc_dyn : I.recbuf);
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
 template <int NT, int PREC>
-__global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf) {
+__global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf,
+                                                         int use_smem) {
+    extern __shared__ __align__(16) unsigned char inc_dyn[];
     __shared__ Topo sT;
     __shared__ State sS;
     __shared__ Search sX;
@@ -1137,7 +1293,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, use_smem ? inc_dyn : sI.recbuf);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -1147,19 +1303,44 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
 }
 
 constexpr int kIncThreads = 512;            // one feeder on one SM
-constexpr int kIncBatchThreads = 512;       // batches: several feeders per SM
+constexpr int kIncBatchThreads = 512;       // batches: one feeder per CTA
+constexpr size_t kIncSmemMax = 196 * 1024;  // largest dynamic shared memory for the selection records
 
-cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
-    if (precision == 1) k_search_inc<kIncThreads, 1><<<1, kIncThreads, 0, st>>>(T, S, X, I, C, verify);
-    else k_search_inc<kIncThreads, 0><<<1, kIncThreads, 0, st>>>(T, S, X, I, C, verify);
-    return cudaGetLastError();
+template <typename K>
+cudaError_t set_smem(K kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-cudaError_t launch_search_inc_batch(int precision, const BatchFeeder *fd, const int *order, int nf, cudaStream_t st) {
+cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
+    const size_t want = rec_bytes(T.n);
+    const int use = want <= kIncSmemMax ? 1 : 0;
+    const size_t smem = use ? want : 0;
+    cudaError_t e;
+    if (precision == 1) {
+        e = set_smem(k_search_inc<kIncThreads, 1>, smem);
+        if (e == cudaSuccess) k_search_inc<kIncThreads, 1><<<1, kIncThreads, smem, st>>>(T, S, X, I, C, verify, use);
+    } else {
+        e = set_smem(k_search_inc<kIncThreads, 0>, smem);
+        if (e == cudaSuccess) k_search_inc<kIncThreads, 0><<<1, kIncThreads, smem, st>>>(T, S, X, I, C, verify, use);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
+                                    cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
-    if (precision == 1) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, 0, st>>>(fd, order, nf);
-    else k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, 0, st>>>(fd, order, nf);
-    return cudaGetLastError();
+    const size_t want = rec_bytes(max_n);
+    const int use = want <= kIncSmemMax ? 1 : 0;
+    const size_t smem = use ? want : 0;
+    cudaError_t e;
+    if (precision == 1) {
+        e = set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem);
+        if (e == cudaSuccess) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
+    } else {
+        e = set_smem(k_search_inc_batch<kIncBatchThreads, 0>, smem);
+        if (e == cudaSuccess) k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
+    }
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace okr

@@ -159,6 +159,7 @@ struct Inc {
     unsigned long long *vacc;   // [2n][2] FP64 rescoring (precision-1 recheck, verification)
     int *vviol;                 // [2n]
     int *rlist;                 // [2n] slots rescored in FP64 in one iteration
+    unsigned char *recbuf;      // [56 n + 64] selection records when they do not fit shared memory
 };
 constexpr int kIncDead = 1 << 30;
 

@@ -139,6 +139,7 @@ __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, dou
 // mismatches of the carried scores in C->inc_mismatch).
 cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st);
 // Many feeders: one CTA each, in the order given.
-cudaError_t launch_search_inc_batch(int precision, const BatchFeeder *fd, const int *order, int nf, cudaStream_t st);
+cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
+                                    cudaStream_t st);
 
 }  // namespace okr
