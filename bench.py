@@ -28,12 +28,16 @@ sys.path.insert(0, ROOT)
 METRIC = "candidates evaluated/s & time-to-optimal reduction, 1000-node feeder vs FP64"
 WORKLOAD = "feeder1000"
 # FP32 ALU peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz
-# (the search's counted arithmetic is its FP32 candidate screen)
+# (the search's counted arithmetic is its FP32 candidate terms)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes of one k_search launch on this workload from the ncu capture in
-# profiles/k_search_feeder1000.md, valid only for the kernel source it was taken on
-NCU_TRAFFIC = {"bytes": 1037824 + 114432, "source": "paper_2510_19608_gb300/csrc/okr_persist.cu",
-               "sha256_prefix": "31fd03f65db8da77", "summary": "profiles/k_search_feeder1000.md"}
+# algorithmic FP operations per (candidate, kept phase-node, scenario) item: the
+# 3-term complex product of the voltage change, the magnitude change, the error
+# against the cluster extremes, a max and a sum
+FLOPS_PER_ITEM = 40
+# DRAM bytes of one search launch on this workload from the ncu capture in
+# profiles/, valid only for the kernel source it was taken on (None otherwise)
+NCU_TRAFFIC = {"bytes": 1128448 + 2560, "source": "paper_2510_19608_gb300/csrc/okr_incr.cu",
+               "sha256_prefix": "5ab9d957ccd00acc", "summary": "profiles/k_search_inc_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
@@ -45,6 +49,8 @@ def _ncu_traffic():
         with open(os.path.join(ROOT, NCU_TRAFFIC["source"]), "rb") as fh:
             h = hashlib.sha256(fh.read()).hexdigest()
     except OSError:
+        return None
+    if not NCU_TRAFFIC["sha256_prefix"] or NCU_TRAFFIC["bytes"] is None:
         return None
     return NCU_TRAFFIC["bytes"] if h.startswith(NCU_TRAFFIC["sha256_prefix"]) else None
 
@@ -211,17 +217,21 @@ def run_reference(args, rank, world):
 
 def batch_line(K, ctx, reps=3):
     """Many-feeder workload: 256 seeded feeders, n ~ U[200, 2000], targets in
-    {50, 70, 90} %, margin 0.005, reduced by okr_reduce_batch (one persistent
-    launch), mixed precision and plain FP64.  Inputs (about 1 GB of device
-    buffers) exceed L2, so no flush is needed between repetitions."""
+    {50, 70, 90} %, margin 0.005, reduced by okr_reduce_batch: the incremental
+    engine (one CTA per feeder) and the sweep engine (one persistent launch,
+    autotuned teams), each with FP32 terms (FP64 rescoring and merges) and in
+    plain FP64.  Inputs (about 1 GB of device buffers) exceed L2, so no flush
+    is needed between repetitions."""
     import feedergen as fg
     batch = fg.batch_presets(256)
     feeders = [f for f, _ in batch]
     out = {"workload": "256 feeders, n ~ U[200, 2000] buses (sum %d), targets {50, 70, 90} %%, margin 0.005 p.u., "
                        "2 scenarios" % sum(f.n_bus for f in feeders)}
-    for prec, key in ((1, "mixed"), (0, "fp64")):
-        plist = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=prec) for _, r in batch]
-        if prec == 1:
+    rows = (("incremental_mixed", 2, 1), ("incremental_fp64", 2, 0), ("sweep_mixed", 1, 1), ("sweep_fp64", 1, 0))
+    for key, engine, prec in rows:
+        plist = [K.default_params(margin=r["margin"], target_reduction=r["target"], precision=prec, engine=engine)
+                 for _, r in batch]
+        if key == "sweep_mixed":
             cfg, ms = ctx.batch_autotune(feeders, plist)
             out["autotune"] = {"config": cfg, "search_ms_by_config": [round(x, 3) for x in ms],
                                "configs": ["1 CTA per feeder", "2 CTAs", "4 CTAs", "8 CTAs"]}
@@ -275,8 +285,9 @@ def learned_line(K, ctx, n_train=64, record=64):
     for name in ("feeder3100", "feeder2200", WORKLOAD):
         fx, rx = fg.preset(name)
         rows = {}
-        for k in (0, 64, 16):
-            px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=1, scorer_topk=k)
+        for k, engine in ((0, 2), (0, 1), (64, 1), (16, 1)):
+            px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=1, scorer_topk=k,
+                                  engine=engine)
             ctx.reduce(fx, px)                                        # warm-up
             times = []
             for _ in range(3):
@@ -284,7 +295,7 @@ def learned_line(K, ctx, n_train=64, record=64):
                 ctx.reduce(fx, px)
                 times.append(time.perf_counter() - t0)
             sm = ctx.summary()
-            rows["exhaustive" if k == 0 else f"top{k}"] = {
+            rows[("exhaustive_incremental" if engine == 2 else "exhaustive_sweep") if k == 0 else f"top{k}"] = {
                 "ms": 1e3 * statistics.median(times), "search_ms": sm["search_ms"], "merges": sm["n_iter"],
                 "stop_reason": sm["stop_reason"], "smice": sm["smice"], "max_error": sm["max_error"],
                 "fallbacks": sm["scorer_fallbacks"]}
@@ -339,10 +350,16 @@ def run_ours(args, rank, world, local):
     f, run = fg.preset(WORKLOAD)
     stream = torch.cuda.current_stream()
     ctx = K.Context(local, stream.cuda_stream)
-    # the mixed-precision search (FP32 screen, FP64 recheck and merges) selects the
-    # same candidates as the all-FP64 one; both are timed, the first is the headline
-    p = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1)
-    p64 = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=0)
+    # every engine and precision selects the same candidates.  Headline: the
+    # incremental engine with FP32 terms (carried bounds, FP64 rescoring where
+    # the bound cannot decide, FP64 merges).  "vs FP64": the plain FP64 search
+    # that scores every candidate afresh each iteration (the sweep engine).
+    p = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1, engine=2)
+    p64 = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=0, engine=1)
+    others = {"sweep_mixed": K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1,
+                                              engine=1),
+              "incremental_fp64": K.default_params(margin=run["margin"], target_reduction=run["target"], precision=0,
+                                                   engine=2)}
 
     dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f.parent, f.phases, f.z_line, f.s_load)]
     dfeed = K.device_feeder(f.n_bus, f.n_scen, *[t.data_ptr() for t in dev], f.v_slack)
@@ -376,21 +393,28 @@ def run_ours(args, rank, world, local):
     ms = max_over_ranks(ms, dist, "cuda")
     value = replica_value(cand_per_step, args.steps, world, ms)
 
-    # ---- the all-FP64 search on the same workload (comparison row)
-    for _ in range(3):
-        ctx.reduce_device(dfeed, p64)
-    f64_steps = max(1, min(args.steps, 50))
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(f64_steps)]
-    for a, b in ev:
-        flush.fill_(0.0)
-        a.record(stream)
-        ctx.reduce_device(dfeed, p64)
-        b.record(stream)
-    torch.cuda.synchronize()
-    ms64 = sum(a.elapsed_time(b) for a, b in ev) / f64_steps
-    s64 = ctx.summary()
-    fp64_row = {"ms_per_step": ms64, "value": s64["candidates"] / (ms64 / 1e3), "unit": "candidates/s",
-                "search_kernel_ms": s64["search_ms"]}
+    # ---- the same workload with the other engines / precisions (comparison rows)
+    def timed_row(params):
+        for _ in range(3):
+            ctx.reduce_device(dfeed, params)
+        steps = max(1, min(args.steps, 50))
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.fill_(0.0)
+            a.record(stream)
+            ctx.reduce_device(dfeed, params)
+            b.record(stream)
+        torch.cuda.synchronize()
+        msr = sum(a.elapsed_time(b) for a, b in ev) / steps
+        sr = ctx.summary()
+        return {"ms_per_step": msr, "value": sr["candidates"] / (msr / 1e3), "unit": "candidates/s",
+                "search_kernel_ms": sr["search_ms"], "merges": sr["n_iter"], "smice": sr["smice"]}
+
+    fp64_row = timed_row(p64)
+    fp64_row["engine"] = "sweep: every candidate scored afresh in FP64 each iteration (one persistent launch)"
+    other_rows = {k: timed_row(v) for k, v in others.items()}
+    other_rows["sweep_mixed"]["engine"] = "sweep: FP32 screen with bounds, FP64 recheck, FP64 merges"
+    other_rows["incremental_fp64"]["engine"] = "incremental: FP64 terms carried across merges"
 
     # ---- end to end: pinned host inputs through okr_reduce, result read back
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (f.parent, f.phases, f.z_line, f.s_load)]
@@ -412,10 +436,11 @@ def run_ours(args, rank, world, local):
     e2e = {"value": cand_per_step / e2e_s, "unit": "candidates/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "time_to_optimal_s": e2e_s}
 
-    # ---- roofline of the dominant kernel: the persistent search kernel, timed
-    # with CUDA events around its launch on the library stream; its arithmetic
-    # is counted by the kernel in one profiled step
-    pp = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1, profile=1)
+    # ---- roofline of the dominant kernel: the search kernel (one CTA runs the
+    # whole search), timed with CUDA events around its launch on the library
+    # stream; its (candidate, phase-node, scenario) items are counted by the
+    # kernel in one profiled step
+    pp = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1, engine=2, profile=1)
     ctx.reduce_device(dfeed, pp)
     ps = ctx.summary()
     # output Y_Kron of the chosen network (Sec. II-B), formed once per feeder
@@ -423,21 +448,20 @@ def run_ours(args, rank, world, local):
     kron = {"ms": ctx.summary()["kron_ms"], "k_phi": int(yk.shape[0]),
             "note": "device time of okr_kron on the chosen network (outside the step)"}
     search_ms = summ_last["search_ms"]
-    achieved = ps["flops"] / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
+    items = ps["terms"]
+    achieved = items * FLOPS_PER_ITEM / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _ncu_traffic(), "kernel": "k_search",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _ncu_traffic(), "kernel": "k_search_inc",
                 "peak_source": "derived FP32 ALU rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
                 "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1,
-                "flops_per_launch": ps["flops"], "sweeps_per_launch": ps["sweeps"],
-                "sweep_phase_share": ps["sweep_ms"] / ps["search_ms"] if ps["search_ms"] > 0 else None,
-                "phase_ms": dict(zip(["select", "recheck", "merge", "setup", "barrier1", "chunkmap", "barrier2",
-                                      "sweep+barrier3", "merge_sum", "list_update", "offsets", "compaction"],
-                                     [round(x, 3) for x in ps["phase_ms"][:12]])),
+                "items_per_launch": items, "flops_per_item": FLOPS_PER_ITEM,
+                "flops_per_launch": items * FLOPS_PER_ITEM,
+                "phase_ms": dict(zip(["select", "changed_set", "terms_before", "merge", "rebuild", "terms_after"],
+                                     [round(x, 3) for x in ps["phase_ms"][:6]])),
+                "rechecks": ps["rechecks"], "recheck_candidates": ps["recheck_cands"],
                 "share_of_step": search_ms / (ms / args.steps),
-                "sweep_warps": {"mean_us": 1e3 * ps["phase_ms"][12] / max(1e-9, 1e6 * ps["phase_ms"][13]),
-                                "max_us": 1e3 * ps["phase_ms"][14], "warp_sweeps": int(round(1e6 * ps["phase_ms"][13])),
-                                "chunks": int(round(1e6 * ps["phase_ms"][15]))}}
-
+                "note": "one CTA runs the whole search (a chain of dependent merges); its time is latency, "
+                        "not arithmetic or memory traffic"}
     batch = batch_line(K, ctx) if not args.no_batch else None
     learned = learned_line(K, ctx) if not args.no_learned else None
     studies = sweeps_line(K, ctx) if not args.no_batch else None
@@ -447,8 +471,12 @@ def run_ours(args, rank, world, local):
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": _workload_config(f, run) | {
-                    "precision": "FP32 screen with rigorous bounds, FP64 recheck of unresolved candidates, FP64 merges",
-                    "fp64_search": fp64_row, "rechecks": summ_last["rechecks"],
+                    "engine": "incremental: every candidate's score carried across merges as an exact fixed-point "
+                              "sum of its terms; only the terms whose inputs the last merge changed are evaluated "
+                              "again; one CTA",
+                    "precision": "FP32 terms with carried rigorous bounds, FP64 rescoring of the candidates the bound "
+                                 "cannot separate, FP64 merges",
+                    "fp64_search": fp64_row, "other_engines": other_rows, "rechecks": summ_last["rechecks"],
                     "recheck_candidates": summ_last["recheck_cands"],
                     "l2": "flushed between steps (256 MB write outside the timed events)",
                     "parallelism": f"replicas x{world}", "time_to_optimal_ms": ms / args.steps,

@@ -149,8 +149,9 @@ typedef struct okr_summary {
                                    evaluation, summed over the merges (0 when correct) */
     int32_t engine;             /* engine that ran: OKR_ENGINE_SWEEP or OKR_ENGINE_INCREMENTAL */
     int32_t pad;
-    int64_t terms;              /* incremental engine: (candidate, cluster) terms evaluated over the
-                                   run, the initial evaluation included (profile mode; 0 otherwise) */
+    int64_t terms;              /* incremental engine, profile mode: (candidate, phase-node, scenario)
+                                   items evaluated over the run, the initial evaluation, the merges'
+                                   own evaluations and FP64 rescorings included (0 otherwise) */
 } okr_summary;
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,

@@ -1270,14 +1270,14 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->launches = ctx->launches;
     out->search_ms = ctx->search_ms;
     out->sweeps = ctx->last.iters;
-    out->sweep_ms = ctx->last.profile ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
+    out->sweep_ms = (ctx->last.profile && ctx->last_engine == OKR_ENGINE_SWEEP) ? 1e-6 * (double)ctx->last.sweep_ns : 0.0;
     out->flops = (ctx->last.profile && ctx->last_engine == OKR_ENGINE_SWEEP) ? ctx->last.sweep_flops : 0.0;
     out->kron_ms = ctx->kron_ms;
     out->scorer_fallbacks = c.scorer_fallbacks;
     out->inc_mismatches = c.inc_mismatch;
     out->engine = ctx->last_engine;
     out->pad = 0;
-    out->terms = (ctx->last_engine == OKR_ENGINE_INCREMENTAL && c.profile) ? (int64_t)c.sweep_flops : 0;
+    out->terms = (ctx->last_engine == OKR_ENGINE_INCREMENTAL && c.profile) ? (int64_t)c.sweep_ns : 0;
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
     for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;

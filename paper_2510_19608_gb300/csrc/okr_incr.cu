@@ -625,8 +625,9 @@ struct Commit {
 };
 
 // Run by warps [warp0, warp0 + nw) only.
-__device__ __forceinline__ void commit_groups(const Topo &T, const State &S, const Inc &I, int n, int L, int G,
-                                              double margin, const Commit &cm, int warp0, int nw) {
+__device__ __forceinline__ long long commit_groups(const Topo &T, const State &S, const Inc &I, int n, int L, int G,
+                                                   double margin, const Commit &cm, int warp0, int nw) {
+    long long items = 0;
     const int lw = ((int)threadIdx.x >> 5) - warp0, gpw = 32 / G, gl = threadIdx.x % G;
     const int gi = lw * gpw + ((int)threadIdx.x & 31) / G, NG = nw * gpw;
     const Win &h = *cm.h;
@@ -644,7 +645,9 @@ __device__ __forceinline__ void commit_groups(const Topo &T, const State &S, con
         int nv;
         group_term64(T, S, n, L, G, cm.wc, k, valid, gl, margin, valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d,
                      &nv);
+        if (valid && gl == 0) items += __popc(__ldg(T.ph + k)) * L;
     }
+    return items;
 }
 
 // Evaluates the terms of work entries [e0, e1) (tiles of kTE entries) and applies
@@ -671,7 +674,6 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
             E.dlo[i] = E.dhi[i] = E.blo[i] = E.bhi[i] = 0ull;
             E.n1[i] = E.n2[i] = 0;
         }
-        terms += tot;
         __syncthreads();
         for (int r0 = 0; r0 < tot; r0 += NG) {
             if (r0 + (tid >> 5) * (32 / G) >= tot) break;     // this warp's groups are all past the end
@@ -698,6 +700,7 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
                 c = X.slot[w.slot];
                 if (k == c.r || (pass == kNew && w.mode == 0 && k == rstar)) valid = false;
             }
+            if (valid && gl == 0) terms += __popc(__ldg(T.ph + k)) * L;      // (phase-node, scenario) items
             if (PREC == 0 || pass == kF64) {
                 u128 d;
                 int nv;
@@ -1075,7 +1078,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 cm.h = &h;
                 cm.wc = X.slot[ws];
                 cm.list = list_old;
-                commit_groups(T, S, I, n, L, G, margin, cm, NW - CW, CW);
+                terms += commit_groups(T, S, I, n, L, G, margin, cm, NW - CW, CW);
             } else {
                 // the changed buses lie in [hl, hh): a candidate whose span misses it is unchanged
                 int hl = min(hw.s, hw.r), hh = max(hw.s, hw.r) + 1;
@@ -1254,13 +1257,17 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         rm = block_red<NT>(rm, sred);
         if (tid == 0) X.dec_maxerr[t - 1] = rm.a == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~rm.a);
     }
+    if (prof) {                                     // (phase-node, scenario) items evaluated over the run
+        unsigned long long tt = (unsigned long long)terms;
+        for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
+        if ((tid & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&C->sweep_ns), tt);
+    }
     if (tid == 0) {
         C->t = t;
         C->n_super = ns;
         C->s_cur = fx_to_d(ld128(s_sfx));
         C->rechecks = rechecks;
         C->recheck_cands = recheck_cands;
-        if (prof) C->sweep_flops = (double)terms;     // terms evaluated (profile mode)
     }
 }
 
