@@ -306,36 +306,57 @@ __device__ int slot_geometry(const Topo &T, const State &S, int n, int w, Cand &
 // FP64 term.  d = sum over l of fixed(new MICE - MICE_k [- MICE_r]); nv = scenarios
 // whose new MICE exceeds the margin.  out != nullptr: the new voltage and
 // magnitude per (l, p) and the new MICE per l (the merge).
-__device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, int L, int G, const Cand &c, int k,
-                                          bool valid, int gl, double margin, double *out, u128 *d_out, int *nv_out) {
+__device__ __noinline__ void group_term64(const Topo &T, const State &S, const uint8_t *ph, int n, int L,
+                                          const Cand &c, int k, bool valid, int gl, double margin, double *out,
+                                          unsigned long long *dlo, unsigned long long *dhi, int *n1) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
-    const bool on = lv && p < 3 && (__ldg(T.ph + k) >> p & 1u);
+    const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
+    const bool on = lv && p < 3 && (phk >> p & 1u);
+    const bool is_s = (k == c.s);
+    const bool fixed = is_s && c.fixed;
+    const bool sside = (k >= c.js && k < c.js + c.ns);
+    const bool moves = on && !fixed;
+    const int li = lv ? l : 0, pi = p < 3 ? p : 0;
+    const size_t ik = sidx(li, pi, k, n), ir = sidx(li, pi, c.r, n);
+    // every load that needs only (c, k, l, p), issued together
+    double2 v = make_double2(0.0, 0.0), iq[3], za[3];
+    double h = 0.0, lo = 0.0, hr = -INFINITY, lr = INFINITY, mo = 0.0, mr = 0.0;
+    int y = 0;
+    if (on) {
+        v = S.vcur[ik];
+        h = S.hi[ik];
+        lo = S.lo[ik];
+        if (is_s) { hr = S.hi[ir]; lr = S.lo[ir]; }
+    }
+    if (lv && p == 0) {
+        mo = S.mice[(size_t)l * n + k];
+        if (is_s) mr = S.mice[(size_t)l * n + c.r];
+    }
+    if (moves) {
+        y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        for (int q = 0; q < 3; ++q) {
+            iq[q] = (phr >> q & 1u) ? S.icur[sidx(li, q, c.r, n)] : make_double2(0.0, 0.0);
+            za[q] = __ldg(T.zc + (size_t)c.a * 9 + pi * 3 + q);
+        }
+    }
     double e = 0.0;
     if (on) {
-        const bool fixed = (k == c.s) && c.fixed;
-        const bool sside = (k >= c.js && k < c.js + c.ns);
-        const size_t ik = sidx(l, p, k, n);
-        double2 v = S.vcur[ik];
-        if (!fixed) {
-            const unsigned phr = __ldg(T.ph + c.r);
-            const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
-            const double2 *zy = T.zc + (size_t)y * 9 + p * 3, *za = T.zc + (size_t)c.a * 9 + p * 3;
+        if (moves) {
+            const double2 *zy = T.zc + (size_t)y * 9 + pi * 3;
             double2 dv = make_double2(0.0, 0.0);
             for (int q = 0; q < 3; ++q) {
                 if (!(phr >> q & 1u)) continue;
-                const double2 zyq = __ldg(zy + q), zaq = __ldg(za + q);
-                const double2 g = sside ? csub(zyq, zaq) : csub(zaq, zyq);
-                dv = cadd(dv, cmul(g, S.icur[sidx(l, q, c.r, n)]));
+                const double2 zyq = __ldg(zy + q);
+                const double2 g = sside ? csub(zyq, za[q]) : csub(za[q], zyq);
+                dv = cadd(dv, cmul(g, iq[q]));
             }
             v = cadd(v, dv);
         }
         const double mag = cmag(v);
-        double h = S.hi[ik], lo = S.lo[ik];
-        if (k == c.s) {
-            const size_t ir = sidx(l, p, c.r, n);
-            h = fmax(h, S.hi[ir]);
-            lo = fmin(lo, S.lo[ir]);
+        if (is_s) {
+            h = fmax(h, hr);
+            lo = fmin(lo, lr);
         }
         e = fmax(h - mag, mag - lo);
         if (out) {
@@ -346,21 +367,15 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, 
     }
     double m = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
     m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    u128 d = 0;
-    int nv = 0;
     if (lv && p == 0) {
-        double dd = m - S.mice[(size_t)l * n + k];
-        if (k == c.s) dd -= S.mice[(size_t)l * n + c.r];
-        d = to_fx(dd);
-        nv = (m > margin) ? 1 : 0;
         if (out) out[9 * L + l] = m;
+        if (dlo) {
+            double dd = m - mo;
+            if (is_s) dd -= mr;
+            sadd128(dlo, dhi, to_fx(dd));
+            if (m > margin) atomicAdd(n1, 1);
+        }
     }
-    for (int o = 4; o < G; o <<= 1) {
-        d += shfl_xor_u128(d, o);
-        nv += __shfl_xor_sync(0xffffffffu, nv, o);
-    }
-    *d_out = d;
-    *nv_out = nv;
 }
 
 // FP32 term with a rigorous bound (the screen of okr_persist.cu, per item
@@ -368,46 +383,66 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, int n, 
 // d = sum over l of fixed(D32 term); b = sum over l of a fixed-point bound on
 // |fixed(D32 term) - fixed(D64 term)|; n_sure = scenarios whose new MICE is
 // surely above the margin; n_maybe = scenarios where it may be.
-__device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, int L, int G, const Cand &c, int k,
-                                          bool valid, int gl, float margin_lo, float margin_hi, u128 *d_out,
-                                          u128 *b_out, int *ns_out, int *nm_out) {
+__device__ __noinline__ void group_term32(const Topo &T, const State &S, const uint8_t *ph, int n, int L,
+                                          const Cand &c, int k, bool valid, int gl, float margin_lo, float margin_hi,
+                                          unsigned long long *dlo, unsigned long long *dhi, unsigned long long *blo,
+                                          unsigned long long *bhi, int *n1, int *n2) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
-    const bool on = lv && p < 3 && (__ldg(T.ph + k) >> p & 1u);
+    const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
+    const bool on = lv && p < 3 && (phk >> p & 1u);
+    const bool is_s = (k == c.s);
+    const bool fixed = is_s && c.fixed;
+    const bool sside = (k >= c.js && k < c.js + c.ns);
+    const bool sterm = on && is_s && (phr >> p & 1u);
+    const bool moves = on && !fixed;
+    const int li = lv ? l : 0, pi = p < 3 ? p : 0;
+    const size_t ik = sidx(li, pi, k, n), ir = sidx(li, pi, c.r, n);
+    // every load that needs only (c, k, l, p), issued together
+    float hr = 0.0f, lr = 0.0f, hrr = 0.0f, lrr = 0.0f, mo = 0.0f, mr = 0.0f;
+    double mcr = 0.0, mck = 0.0;
+    float2 v = make_float2(0.0f, 0.0f), iq[3], ha[3], la[3];
+    int y = 0;
+    if (on) { hr = S.hr32[ik]; lr = S.lr32[ik]; }
+    if (sterm) { mcr = S.mcur[ir]; mck = S.mcur[ik]; hrr = S.hr32[ir]; lrr = S.lr32[ir]; }
+    if (lv && p == 0) {
+        mo = S.mice32[(size_t)l * n + k];
+        if (is_s) mr = S.mice32[(size_t)l * n + c.r];
+    }
+    if (moves) {
+        v = S.v32[ik];
+        y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        for (int q = 0; q < 3; ++q) {
+            iq[q] = (phr >> q & 1u) ? S.icur32[sidx(li, q, c.r, n)] : make_float2(0.0f, 0.0f);
+            ha[q] = __ldg(T.zh + (size_t)c.a * 9 + pi * 3 + q);
+            la[q] = __ldg(T.zlo + (size_t)c.a * 9 + pi * 3 + q);
+        }
+    }
     float e = 0.0f, b = 0.0f;
     if (on) {
-        const bool fixed = (k == c.s) && c.fixed;
-        const bool sside = (k >= c.js && k < c.js + c.ns);
-        const size_t ik = sidx(l, p, k, n);
-        float hr = S.hr32[ik], lr = S.lr32[ik];
         float bx = 0.0f;
-        if (k == c.s && (__ldg(T.ph + c.r) >> p & 1u)) {
-            const size_t ir = sidx(l, p, c.r, n);
-            const float dr = (float)(S.mcur[ir] - S.mcur[ik]);
-            const float hrr = S.hr32[ir] + dr, lrr = S.lr32[ir] + dr;
+        if (sterm) {
+            const float dr = (float)(mcr - mck);
+            hrr += dr;
+            lrr += dr;
             hr = fmaxf(hr, hrr);
             lr = fminf(lr, lrr);
             bx = 2.0f * kU32 * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
         }
         float delta = 0.0f, bd = 0.0f;
-        if (!fixed) {
-            const unsigned phr = __ldg(T.ph + c.r);
-            const float2 v = S.v32[ik];
-            const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
-            const float2 *zhy = T.zh + (size_t)y * 9 + p * 3, *zly = T.zlo + (size_t)y * 9 + p * 3;
-            const float2 *zha = T.zh + (size_t)c.a * 9 + p * 3, *zla = T.zlo + (size_t)c.a * 9 + p * 3;
+        if (moves) {
+            const float2 *zhy = T.zh + (size_t)y * 9 + pi * 3, *zly = T.zlo + (size_t)y * 9 + pi * 3;
             float2 dv = make_float2(0.0f, 0.0f);
             float sdv = 0.0f;
             for (int q = 0; q < 3; ++q) {
                 if (!(phr >> q & 1u)) continue;
-                const float2 iq = S.icur32[sidx(l, q, c.r, n)];
-                const float2 hy = __ldg(zhy + q), ha = __ldg(zha + q), ly = __ldg(zly + q), la = __ldg(zla + q);
-                float gx = (hy.x - ha.x) + (ly.x - la.x);
-                float gy = (hy.y - ha.y) + (ly.y - la.y);
+                const float2 hy = __ldg(zhy + q), ly = __ldg(zly + q);
+                float gx = (hy.x - ha[q].x) + (ly.x - la[q].x);
+                float gy = (hy.y - ha[q].y) + (ly.y - la[q].y);
                 if (!sside) { gx = -gx; gy = -gy; }
-                dv.x = fmaf(gx, iq.x, fmaf(-gy, iq.y, dv.x));
-                dv.y = fmaf(gx, iq.y, fmaf(gy, iq.x, dv.y));
-                sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(iq.x) + fabsf(iq.y), sdv);
+                dv.x = fmaf(gx, iq[q].x, fmaf(-gy, iq[q].y, dv.x));
+                dv.y = fmaf(gx, iq[q].y, fmaf(gy, iq[q].x, dv.y));
+                sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(iq[q].x) + fabsf(iq[q].y), sdv);
             }
             const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
             const float wx = v.x + dv.x, wy = v.y + dv.y;
@@ -424,30 +459,17 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, int n, 
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
     float bm = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, 1));
     bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
-    u128 d = 0, bb = 0;
-    int ns = 0, nm = 0;
     if (lv && p == 0) {
-        const float mo = S.mice32[(size_t)l * n + k];
-        const float mr = (k == c.s) ? S.mice32[(size_t)l * n + c.r] : 0.0f;
         const float dd = (m - mo) - mr;
         // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
         // factor 1.001 covers the rounding of the bound's own arithmetic
         const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(mo) + fabsf(mr) + fabsf(m)));
-        d = to_fx32(dd);
-        bb = to_fx32(bl) + 3;            // + the truncations of both terms to fixed point
-        ns = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
-        nm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
+        // each scenario's term goes straight into the entry's exact sums
+        sadd128(dlo, dhi, to_fx32(dd));
+        sadd128(blo, bhi, to_fx32(bl) + 3);       // + the truncations of both terms to fixed point
+        if (__fsub_rd(m, bm) > margin_hi) atomicAdd(n1, 1);
+        if (__fadd_ru(m, bm) > margin_lo) atomicAdd(n2, 1);
     }
-    for (int o = 4; o < G; o <<= 1) {
-        d += shfl_xor_u128(d, o);
-        bb += shfl_xor_u128(bb, o);
-        ns += __shfl_xor_sync(0xffffffffu, ns, o);
-        nm += __shfl_xor_sync(0xffffffffu, nm, o);
-    }
-    *d_out = d;
-    *b_out = bb;
-    *ns_out = ns;
-    *nm_out = nm;
 }
 
 // ---------------------------------------------------------------- the changed set of a merge
@@ -527,13 +549,34 @@ __device__ int full_segments(const Cand &c, const int *sn_rank, int2 *seg) {
     return k;
 }
 
-__device__ __forceinline__ void write_entry(IncWork *w, int slot, int mode, int nseg, const int2 *seg) {
+__device__ __forceinline__ void write_entry(IncWork *w, int slot, int mode, int nseg, const int2 *seg, const Cand &c) {
     w->slot = slot;
     w->mode = mode;
     w->nseg = nseg;
     w->pad = 0;
     for (int i = 0; i < nseg; ++i) w->seg[i] = seg[i];
+    w->s = c.s; w->r = c.r; w->a = c.a;
+    w->js = c.js; w->ns = c.ns; w->jr = c.jr; w->nr = c.nr; w->fixed = c.fixed;
 }
+
+__device__ __forceinline__ Cand entry_cand(const IncWork &w) {
+    Cand c;
+    c.s = w.s; c.r = w.r; c.a = w.a; c.dir = 0;
+    c.js = w.js; c.ns = w.ns; c.jr = w.jr; c.nr = w.nr;
+    c.fixed = w.fixed; c.pad = 0; c.key = 0;
+    return c;
+}
+
+// Where one search keeps its per-merge data: the first kSE work entries, the
+// super-node lists (16-bit, by merge parity) and the phase masks in shared
+// memory; further entries in global memory.
+constexpr int kSE = 256;
+struct Loc {
+    IncWork *wsm, *wgl;
+    unsigned short *lst[2];
+    const uint8_t *ph;
+    __device__ __forceinline__ IncWork *ent(int i) const { return i < kSE ? wsm + i : wgl + (i - kSE); }
+};
 
 // ---------------------------------------------------------------- evaluation of work entries
 enum Pass {
@@ -621,7 +664,8 @@ __device__ __forceinline__ void kill_rec(const Rec &R, int sl) {
 struct Commit {
     const Win *h;
     Cand wc;
-    const int *list;        // super-nodes before the merge
+    const unsigned short *list;     // super-nodes before the merge
+    const uint8_t *ph;
 };
 
 // Run by warps [warp0, warp0 + nw) only.
@@ -641,11 +685,9 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
             k = q < n1 ? cm.list[h.q1lo + q] : (q < n1 + n2 ? cm.list[h.q2lo + q - n1] : cm.wc.s);
             if (k == cm.wc.r) { valid = false; k = cm.wc.s; }
         }
-        u128 d;
-        int nv;
-        group_term64(T, S, n, L, G, cm.wc, k, valid, gl, margin, valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d,
-                     &nv);
-        if (valid && gl == 0) items += __popc(__ldg(T.ph + k)) * L;
+        group_term64(T, S, cm.ph, n, L, cm.wc, k, valid, gl, margin, valid ? I.cbuf + (size_t)q * 10 * L : nullptr,
+                     nullptr, nullptr, nullptr);
+        if (valid && gl == 0) items += __popc(cm.ph[k]) * L;
     }
     return items;
 }
@@ -656,15 +698,21 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
 // Returns the number of terms evaluated.
 template <int NT, int PREC>
 __device__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
-                                 double margin, float mlo, float mhi, int e0, int e1, int pass, const int *list_pre,
-                                 const int *list_post, int rstar, EvalSmem &E, int *sscan, const Rec &R) {
+                                 double margin, float mlo, float mhi, int e0, int e1, int pass,
+                                 const unsigned short *list_pre, const unsigned short *list_post, int rstar,
+                                 EvalSmem &E, int *sscan, const Rec &R, const Loc &Lc,
+                                 unsigned long long *prof = nullptr) {
     const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
     long long terms = 0;
+    unsigned long long tq = (prof && tid == 0) ? gtimer_inc() : 0;
+    auto sub = [&](int i) {             // profile mode: time of the pass's steps (thread 0, after barriers)
+        if (prof && tid == 0) { const unsigned long long now = gtimer_inc(); prof[i] += now - tq; tq = now; }
+    };
     for (int t0 = e0; t0 < e1; t0 += kTE) {
         const int ne = min(kTE, e1 - t0);
         int cnt = 0;
         if (tid < ne) {
-            const IncWork &w = I.work[t0 + tid];
+            const IncWork &w = *Lc.ent(t0 + tid);
             for (int i = 0; i < w.nseg; ++i) cnt += w.seg[i].y - w.seg[i].x;
         }
         int tot = 0;
@@ -675,21 +723,31 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
             E.n1[i] = E.n2[i] = 0;
         }
         __syncthreads();
+        sub(0);
+        unsigned long long cq = (prof && tid == 0) ? clock64() : 0;
         for (int r0 = 0; r0 < tot; r0 += NG) {
             if (r0 + (tid >> 5) * (32 / G) >= tot) break;     // this warp's groups are all past the end
             const int q = r0 + gi;
             bool valid = q < tot;
             int ei = 0, k = 0;
-            Cand c = X.slot[0];
+            Cand c;
+            c.s = c.r = c.a = c.js = c.ns = c.jr = c.nr = c.fixed = 0;
             if (valid) {
-                int lo = 0, hi = ne - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (E.off[mid] <= q) lo = mid;
-                    else hi = mid - 1;
+                // the entry holding item q: the last one whose offset is <= q
+                if (ne <= 32) {
+                    int cq2 = 0;
+                    for (int i = 1; i < ne; ++i) cq2 += (E.off[i] <= q) ? 1 : 0;
+                    ei = cq2;
+                } else {
+                    int lo = 0, hi = ne - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (E.off[mid] <= q) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    ei = lo;
                 }
-                ei = lo;
-                const IncWork &w = I.work[t0 + ei];
+                const IncWork &w = *Lc.ent(t0 + ei);
                 int rem = q - E.off[ei], j = 0;
                 for (int i = 0; i < w.nseg; ++i) {
                     const int len = w.seg[i].y - w.seg[i].x;
@@ -697,33 +755,24 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
                     rem -= len;
                 }
                 k = ((pass == kNew && w.mode == 1) ? list_post : list_pre)[j];
-                c = X.slot[w.slot];
+                c = entry_cand(w);
                 if (k == c.r || (pass == kNew && w.mode == 0 && k == rstar)) valid = false;
             }
-            if (valid && gl == 0) terms += __popc(__ldg(T.ph + k)) * L;      // (phase-node, scenario) items
+            if (valid && gl == 0) terms += __popc(Lc.ph[k]) * L;      // (phase-node, scenario) items
+            const unsigned long long c0 = (prof && tid == 0) ? clock64() : 0;
+            if (prof && tid == 0) prof[3] += c0 - cq;
             if (PREC == 0 || pass == kF64) {
-                u128 d;
-                int nv;
-                group_term64(T, S, n, L, G, c, k, valid, gl, margin, nullptr, &d, &nv);
-                if (valid && gl == 0) {
-                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
-                    if (nv) atomicAdd(&E.n1[ei], nv);
-                }
+                group_term64(T, S, Lc.ph, n, L, c, k, valid, gl, margin, nullptr, &E.dlo[ei], &E.dhi[ei], &E.n1[ei]);
             } else {
-                u128 d, b;
-                int ns, nm;
-                group_term32(T, S, n, L, G, c, k, valid, gl, mlo, mhi, &d, &b, &ns, &nm);
-                if (valid && gl == 0) {
-                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
-                    sadd128(&E.blo[ei], &E.bhi[ei], b);
-                    if (ns) atomicAdd(&E.n1[ei], ns);
-                    if (nm) atomicAdd(&E.n2[ei], nm);
-                }
+                group_term32(T, S, Lc.ph, n, L, c, k, valid, gl, mlo, mhi, &E.dlo[ei], &E.dhi[ei], &E.blo[ei],
+                             &E.bhi[ei], &E.n1[ei], &E.n2[ei]);
             }
+            if (prof && tid == 0) prof[4] += clock64() - c0;
         }
         __syncthreads();
+        sub(1);
         if (tid < ne) {
-            const IncWork &w = I.work[t0 + tid];
+            const IncWork &w = *Lc.ent(t0 + tid);
             const int sl = w.slot;
             const u128 d = ((u128)E.dhi[tid] << 64) | (u128)E.dlo[tid];
             const u128 b = ((u128)E.bhi[tid] << 64) | (u128)E.blo[tid];
@@ -757,6 +806,7 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
             }
         }
         __syncthreads();
+        sub(2);
     }
     return terms;
 }
@@ -766,7 +816,7 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
 // (*cnt: a shared counter; the caller synchronises before reading it).
 template <int NT, int PREC>
 __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
-                              int *cnt, const Rec &R) {
+                              int *cnt, const Rec &R, const Loc &Lc) {
     for (int i = threadIdx.x; i < nf; i += NT) {
         const int w = fp[i];
         Cand c[2];
@@ -790,7 +840,7 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
             if (c[d].s >= 0) {
                 int2 seg[kIncMaxSeg];
                 const int ns = full_segments(c[d], S.sn_rank, seg);
-                write_entry(I.work + atomicAdd(cnt, 1), sl, 1, ns, seg);
+                write_entry(Lc.ent(atomicAdd(cnt, 1)), sl, 1, ns, seg, c[d]);
                 R.tkey[sl] = (unsigned)c[d].key;
             } else {
                 I.viol[sl] = kIncDead;
@@ -805,11 +855,18 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
 
 // ---------------------------------------------------------------- the search
 // Bytes of the selection records of an n-bus feeder.
-__host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)56 * n + 64; }
+__host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)48 * n + 64; }
+
+// Shared memory of one search: [work entries][two super-node lists][phase
+// masks], then the selection records when they fit.
+__host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
+__host__ __device__ constexpr size_t base_bytes(int n) {
+    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n);
+}
 
 template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
-                        unsigned char *recmem) {
+                        unsigned char *dyn, bool rec_in_smem) {
     static_assert(NT >= kTE && NT <= 1024, "thread count");
     __shared__ __align__(16) EvalSmem E;
     __shared__ __align__(16) Red sred[33];
@@ -826,13 +883,22 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     const bool prof = C->profile != 0;
     const u128 tau_fx = to_fx(C->tau);
     if (C->done || C->t >= max_merges) return;
-    // selection records: r0 or r1 (2n x 16 B), tkey (2n x 4 B), maxm (n x 8 B), span (n x 8 B)
+    // shared memory: entries, lists, phases; selection records: r0 or r1
+    // (2n x 16 B), tkey (2n x 4 B), span (n x 8 B)
+    Loc Lc;
+    Lc.wsm = reinterpret_cast<IncWork *>(dyn);
+    Lc.wgl = I.work;
+    Lc.lst[0] = reinterpret_cast<unsigned short *>(dyn + (size_t)kSE * sizeof(IncWork));
+    Lc.lst[1] = Lc.lst[0] + n;
+    uint8_t *phs = dyn + (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n);
+    Lc.ph = phs;
+    unsigned char *recmem = rec_in_smem ? dyn + base_bytes(n) : I.recbuf;
     Rec R;
     R.r0 = reinterpret_cast<u128 *>(recmem);
     R.r1 = reinterpret_cast<ulonglong2 *>(recmem);
     R.tkey = reinterpret_cast<unsigned *>(recmem + (size_t)32 * n);
-    R.maxm = reinterpret_cast<double *>(recmem + (size_t)40 * n);
-    R.span = reinterpret_cast<ushort4 *>(recmem + (size_t)48 * n);
+    R.maxm = I.maxm;
+    R.span = reinterpret_cast<ushort4 *>(recmem + (size_t)40 * n);
     int t = 0, ns = n;
     if (tid == 0) {
         s_sfx[0] = s_sfx[1] = 0ull;                 // every MICE starts at 0
@@ -842,7 +908,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     auto stamp = [&](int i) {
         if (prof && tid == 0) { const unsigned long long now = gtimer_inc(); C->phase_ns[i] += now - tp; tp = now; }
     };
-    long long terms = 0;
+    long long terms = 0, cands_run = 0;
     int rechecks = 0, recheck_cands = 0;
     bool maxerr_done = true;                // dec_maxerr of the last merge written
 
@@ -850,14 +916,16 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     for (int w = tid; w < n; w += NT) {
         I.fpair[w] = w;
         R.maxm[w] = 0.0;
+        Lc.lst[0][w] = (unsigned short)w;
+        phs[w] = __ldg(T.ph + w);
     }
     __syncthreads();
-    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R);
+    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R, Lc);
     __syncthreads();
     {
         const int ne = s_cnt[2];
-        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kNew, S.sn_list[0], S.sn_list[0],
-                                       -1, E, sscan, R);
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kNew, Lc.lst[0], Lc.lst[0],
+                                       -1, E, sscan, R, Lc);
     }
     if (prof && tid == 0) tp = gtimer_inc();
 
@@ -866,8 +934,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             if (tid == 0) { C->done = 1; C->stop_reason = 0; }
             break;
         }
-        const int *list_old = S.sn_list[t & 1];
-        int *list_new = S.sn_list[(t + 1) & 1];
+        const unsigned short *list_old = Lc.lst[t & 1];
+        unsigned short *list_new = Lc.lst[(t + 1) & 1];
         // ============================================================ selection
         // pass A: precision 0: the minimum over feasible candidates; precision 1:
         // the smallest lower end (m_lo) and the smallest upper end (m_hi); the
@@ -905,15 +973,14 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         const int nvalid = ra.i;
         if (tid == 0) {
-            C->candidates += nvalid;
-            C->iters += 1;
+            cands_run += nvalid;
             X.dec_ncand[t] = nvalid;
             if (t > 0)
                 X.dec_maxerr[t - 1] = ra.c == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~ra.c);
             s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
-        const double s_cur = fx_to_d(ld128(s_sfx));
         if (t < X.rec_iters) {
+            const double s_cur = fx_to_d(ld128(s_sfx));
             // every candidate's SMICE (+inf when (surely) infeasible), compacted in slot order
             int base = 0;
             for (int c0 = 0; c0 < 2 * n; c0 += NT) {
@@ -954,7 +1021,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
             rb = block_red<NT>(rb, sred);
             ws = (int)(unsigned)(rb.a & 0xffffffffu);
-            if (rb.b != kNone) gap = fx_to_d((rb.b ^ kSignBit) - edge);
+            if (tid == 0 && rb.b != kNone) gap = fx_to_d((rb.b ^ kSignBit) - edge);
         } else {
             const bool has_hi = ra.b != kNone;
             bool ok;
@@ -989,7 +1056,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             const u128 ks = rb.a == kNone ? kNone : (rb.a >> 32);
             if (!(rb.b < ks)) {                          // no uncertain candidate can take the band's smallest key
                 ws = (int)(unsigned)(rb.a & 0xffffffffu);
-                if (rb.c != kNone) gap = (double)(key_val((unsigned long long)rb.c) - key_val(eout)) * 0x1p-56;
+                if (tid == 0 && rb.c != kNone) gap = (double)(key_val((unsigned long long)rb.c) - key_val(eout)) * 0x1p-56;
             } else {
                 // FP64 rescoring of R: the possible minimizers and the uncertain
                 // candidates with a key below the smallest surely-in key
@@ -1005,13 +1072,13 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         I.rlist[o] = c;
                         int2 seg[kIncMaxSeg];
                         const int k = full_segments(X.slot[c], S.sn_rank, seg);
-                        write_entry(I.work + o, c, 1, k, seg);
+                        write_entry(Lc.ent(o), c, 1, k, seg, X.slot[c]);
                     }
                 }
                 __syncthreads();
                 const int nR = s_cnt[3];
                 terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, nR, kF64, list_old, list_old,
-                                               -1, E, sscan, R);
+                                               -1, E, sscan, R, Lc);
                 // exact selection over R, with the surely-in candidate of key ks
                 Red rc;
                 rc.a = rc.b = rc.c = kNone;
@@ -1034,7 +1101,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         else rd.b = umin(rd.b, k);
                     }
                     rd = block_red<NT>(rd, sred);
-                    if (rd.b != kNone) gap = fx_to_d((rd.b ^ kSignBit) - edge);
+                    if (tid == 0 && rd.b != kNone) gap = fx_to_d((rd.b ^ kSignBit) - edge);
                 }
                 const u128 best = umin(rd.a, rb.a);
                 ws = best == kNone ? -1 : (int)(unsigned)(best & 0xffffffffu);
@@ -1078,6 +1145,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 cm.h = &h;
                 cm.wc = X.slot[ws];
                 cm.list = list_old;
+                cm.ph = Lc.ph;
                 terms += commit_groups(T, S, I, n, L, G, margin, cm, NW - CW, CW);
             } else {
                 // the changed buses lie in [hl, hh): a candidate whose span misses it is unchanged
@@ -1098,7 +1166,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         if (c.s < 0 || !touched(c, hw)) continue;
                         int2 seg[kIncMaxSeg];
                         const int k = changed_segments(c, hw, S.sn_rank, seg);
-                        write_entry(I.work + atomicAdd(&s_cnt[1], 1), 2 * w + d, 0, k, seg);
+                        write_entry(Lc.ent(atomicAdd(&s_cnt[1], 1)), 2 * w + d, 0, k, seg, c);
                     }
                 }
             }
@@ -1109,7 +1177,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         stamp(1);
         // ============================================================ terms before the merge
         terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot, kOld, list_old, list_new,
-                                       hw.r, E, sscan, R);
+                                       hw.r, E, sscan, R, Lc, prof ? C->phase_ns + 6 : nullptr);
         __syncthreads();
         stamp(2);
         // ============================================================ the merge (FP64, then the FP32 copies)
@@ -1129,7 +1197,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 }
                 const bool fx = j >= n1 + n2;
                 const double *cb = I.cbuf + (size_t)j * 10 * L;
-                if (valid && l < L && p < 3 && (T.ph[k] >> p & 1u)) {
+                if (valid && l < L && p < 3 && (Lc.ph[k] >> p & 1u)) {
                     const size_t ik = sidx(l, p, k, n);
                     double mc;
                     if (!fx) {
@@ -1176,7 +1244,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             for (int b = hw.r + 1 + tid; b <= n; b += NT) S.sn_rank[b] -= 1;
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             // s takes r's injection
-            const unsigned phr = T.ph[hw.r];
+            const unsigned phr = Lc.ph[hw.r];
             if (tid < 3 * L) {
                 const int l = tid / 3, q = tid % 3;
                 if (phr >> q & 1u) {
@@ -1214,12 +1282,12 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             st128(s_sfx, sfx);
             X.dec_score[t] = fx_to_d(sfx);
         }
-        rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], R);
+        rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], R, Lc);
         __syncthreads();
         const int ne_new = s_cnt[2];
         stamp(4);
         terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne_new, kNew, list_old, list_new, hw.r,
-                                       E, sscan, R);
+                                       E, sscan, R, Lc, prof ? C->phase_ns + 11 : nullptr);
         stamp(5);
         t += 1;
         maxerr_done = false;
@@ -1232,11 +1300,11 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 if (cc.s < 0) continue;
                 int2 seg[kIncMaxSeg];
                 const int k = full_segments(cc, S.sn_rank, seg);
-                write_entry(I.work + atomicAdd(&s_cnt[3], 1), c, 1, k, seg);
+                write_entry(Lc.ent(atomicAdd(&s_cnt[3], 1)), c, 1, k, seg, cc);
             }
             __syncthreads();
             run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, s_cnt[3], kFresh, list_new, list_new, -1,
-                                  E, sscan, R);
+                                  E, sscan, R, Lc);
             int bad = 0;
             for (int c = tid; c < 2 * n; c += NT) {
                 if (X.slot[c].s < 0) continue;
@@ -1265,24 +1333,27 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     if (tid == 0) {
         C->t = t;
         C->n_super = ns;
+        C->candidates += cands_run;
+        C->iters += t + (C->stop_reason == 1 ? 1 : 0);
         C->s_cur = fx_to_d(ld128(s_sfx));
         C->rechecks = rechecks;
         C->recheck_cands = recheck_cands;
     }
 }
 
-// Selection records in dynamic shared memory when use_smem, else in I.recbuf.
+// Per-merge data in dynamic shared memory; the selection records too when
+// rec_smem, else in I.recbuf.
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
-                                                      int use_smem) {
+                                                      int rec_smem) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
-    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, use_smem ? inc_dyn : I.recbuf);
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_smem != 0);
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf,
-                                                         int use_smem) {
+                                                         int rec_smem) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
     __shared__ Topo sT;
     __shared__ State sS;
@@ -1300,7 +1371,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, use_smem ? inc_dyn : sI.recbuf);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_smem != 0);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -1311,17 +1382,24 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
 
 constexpr int kIncThreads = 512;            // one feeder on one SM
 constexpr int kIncBatchThreads = 512;       // batches: one feeder per CTA
-constexpr size_t kIncSmemMax = 196 * 1024;  // largest dynamic shared memory for the selection records
+constexpr size_t kIncSmemMax = 200 * 1024;  // largest dynamic shared memory of one search
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Dynamic shared memory for an n-bus feeder: the per-merge data always, the
+// selection records when the total stays within kIncSmemMax.
+static size_t inc_smem(int n, int *rec_smem) {
+    const size_t base = base_bytes(n), all = base + rec_bytes(n);
+    *rec_smem = all <= kIncSmemMax ? 1 : 0;
+    return *rec_smem ? all : base;
+}
+
 cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
-    const size_t want = rec_bytes(T.n);
-    const int use = want <= kIncSmemMax ? 1 : 0;
-    const size_t smem = use ? want : 0;
+    int use = 0;
+    const size_t smem = inc_smem(T.n, &use);
     cudaError_t e;
     if (precision == 1) {
         e = set_smem(k_search_inc<kIncThreads, 1>, smem);
@@ -1336,9 +1414,8 @@ cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, C
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
                                     cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
-    const size_t want = rec_bytes(max_n);
-    const int use = want <= kIncSmemMax ? 1 : 0;
-    const size_t smem = use ? want : 0;
+    int use = 0;
+    const size_t smem = inc_smem(max_n, &use);
     cudaError_t e;
     if (precision == 1) {
         e = set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem);

@@ -143,6 +143,7 @@ struct IncWork {
     int nseg;
     int pad;
     int2 seg[kIncMaxSeg];   // rank ranges [x, y)
+    int s, r, a, js, ns, jr, nr, fixed;     // the candidate's geometry (as in Cand)
 };
 
 // Per-feeder buffers of the incremental search.
@@ -159,7 +160,8 @@ struct Inc {
     unsigned long long *vacc;   // [2n][2] FP64 rescoring (precision-1 recheck, verification)
     int *vviol;                 // [2n]
     int *rlist;                 // [2n] slots rescored in FP64 in one iteration
-    unsigned char *recbuf;      // [56 n + 64] selection records when they do not fit shared memory
+    unsigned char *recbuf;      // [48 n + 64] selection records when they do not fit shared memory
+    double *maxm;               // [n] largest MICE of each super-node over the scenarios (0 when absorbed)
 };
 constexpr int kIncDead = 1 << 30;
 

@@ -161,7 +161,8 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(I.viol, 2 * N);
     c.take(I.vmay, 2 * N);
     c.take(I.rlist, 2 * N);
-    c.take(I.recbuf, 56 * N + 64);
+    c.take(I.recbuf, 48 * N + 64);
+    c.take(I.maxm, N);
     c.take(I.qpar, N);
     c.take(I.fpair, N);
     c.take(I.work, 2 * N);
