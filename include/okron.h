@@ -253,6 +253,26 @@ okr_status okr_reduce_batch(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *f
 okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
                               int32_t n_params, int32_t *config, double *search_ms);
 
+/* ---- a batch reduced again and again: one CUDA graph --------------------
+ * okr_batch_plan_create checks and stages a batch (the feeders are copied into
+ * the plan's pinned host block), allocates the plan's own device memory and
+ * captures the whole device sequence of one okr_reduce_batch -- input copy,
+ * setup launches, search launch(es), result copies -- as one CUDA graph on the
+ * context's stream.  okr_batch_plan_run replays it with one graph launch and
+ * returns what okr_reduce_batch returns for the same batch (items, super_of,
+ * stats; each pointer as there).  okr_batch_plan_set_loads replaces feeder f's
+ * s_load (HOST, [n_scen][n_bus][3][2]) for the following runs, e.g. another
+ * loading scenario of the same feeders.  The plan uses the context's stream and
+ * the team shape current at creation; it must be destroyed before its context.
+ * Errors as okr_reduce_batch; OKR_ECUDA when the capture fails. */
+typedef struct okr_batch_plan okr_batch_plan;
+okr_status okr_batch_plan_create(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                                 int32_t n_params, okr_batch_plan **plan);
+okr_status okr_batch_plan_run(okr_batch_plan *plan, okr_batch_item *items, int32_t *super_of,
+                              okr_batch_stats *stats);
+okr_status okr_batch_plan_set_loads(okr_batch_plan *plan, int32_t feeder, const double *s_load);
+void okr_batch_plan_destroy(okr_batch_plan *plan);
+
 /* Sets the team shape of later okr_reduce_batch calls on this context
  * (0/1/2/3 = 1/2/4/8 CTAs per feeder); OKR_EINVAL outside that range. */
 okr_status okr_set_batch_config(okr_ctx *ctx, int32_t config);

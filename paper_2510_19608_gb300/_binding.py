@@ -66,7 +66,8 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
            "okr_set_batch_config", "okr_radialize", "okr_get_recorded_features", "okr_scorer_init",
            "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict",
-           "okr_evaluate")
+           "okr_evaluate", "okr_batch_plan_create", "okr_batch_plan_run", "okr_batch_plan_set_loads",
+           "okr_batch_plan_destroy")
 
 
 def lib_path() -> str:
@@ -100,6 +101,11 @@ def lib():
             L.okr_reduce_batch.argtypes = [P, I32, P, P, I32, P, P, P]
             L.okr_batch_autotune.argtypes = [P, I32, P, P, I32, P, P]
             L.okr_set_batch_config.argtypes = [P, I32]
+            L.okr_batch_plan_create.argtypes = [P, I32, P, P, I32, C.POINTER(P)]
+            L.okr_batch_plan_run.argtypes = [P, P, P, P]
+            L.okr_batch_plan_set_loads.argtypes = [P, I32, P]
+            L.okr_batch_plan_destroy.argtypes = [P]
+            L.okr_batch_plan_destroy.restype = None
             L.okr_radialize.argtypes = [P, P, P, P]
             L.okr_get_recorded_features.argtypes = [P, I32, I32, P, P]
             L.okr_evaluate.argtypes = [P, C.POINTER(Feeder), P, P, P]
@@ -114,7 +120,7 @@ def lib():
             L.okr_get_voltages.argtypes = [P, P, P]
             L.okr_get_recorded.argtypes = [P, I32, I32, P, P, P, P, P]
             for fn in EXPORTS:
-                if fn not in ("okr_default_params", "okr_status_str", "okr_last_error"):
+                if fn not in ("okr_default_params", "okr_status_str", "okr_last_error", "okr_batch_plan_destroy"):
                     getattr(L, fn).restype = C.c_int
             _lib = L
     return _lib
@@ -273,6 +279,11 @@ class Context:
                 o += h.c.n_bus
         return out, parts, {k: getattr(st, k) for k, _ in BatchStats._fields_}
 
+    def batch_plan(self, feeders, params):
+        """okr_batch_plan_create: the batch staged once and captured as one CUDA
+        graph; run() replays it."""
+        return BatchPlan(self, feeders, params)
+
     def set_batch_config(self, config: int):
         """okr_set_batch_config: team shape 0/1/2/3 = 1/2/4/8 CTAs per feeder."""
         self._check(lib().okr_set_batch_config(self._h, int(config)))
@@ -402,3 +413,52 @@ class Context:
         self._check(lib().okr_get_recorded(self._h, int(it), cap, _ptr(s), _ptr(r), _ptr(sc), _ptr(bd), C.byref(cnt)))
         c = min(cnt.value, cap)
         return dict(s=s[:c], r=r[:c], score=sc[:c], bound=bd[:c])
+
+
+class BatchPlan:
+    """A batch of feeders captured as one CUDA graph (okr_batch_plan_*)."""
+
+    def __init__(self, ctx: Context, feeders, params):
+        self._ctx = ctx
+        hfs, arr, parr, npar = ctx._batch_args(feeders, params)
+        self._n = [h.c.n_bus for h in hfs]
+        self._shapes = [(h.c.n_scen, h.c.n_bus) for h in hfs]
+        h = C.c_void_p()
+        ctx._check(lib().okr_batch_plan_create(ctx._h, len(hfs), arr, parr, npar, C.byref(h)))
+        self._h = h
+
+    def run(self, want_assignment=True):
+        """okr_batch_plan_run: (items, assignments or None, stats) as Context.reduce_batch."""
+        nf = len(self._n)
+        items = (BatchItem * nf)()
+        st = BatchStats()
+        sup = np.zeros(sum(self._n), np.int32) if want_assignment else None
+        self._ctx._check(lib().okr_batch_plan_run(self._h, items, _ptr(sup) if sup is not None else None,
+                                                   C.byref(st)))
+        out = [{k: getattr(it, k) for k, _ in BatchItem._fields_} for it in items]
+        parts = None
+        if sup is not None:
+            parts, o = [], 0
+            for n in self._n:
+                parts.append(sup[o:o + n].copy())
+                o += n
+        return out, parts, {k: getattr(st, k) for k, _ in BatchStats._fields_}
+
+    def set_loads(self, feeder: int, s_load):
+        """okr_batch_plan_set_loads: feeder's loads for the following runs."""
+        L, n = self._shapes[feeder]
+        a = np.ascontiguousarray(s_load, dtype=np.float64)
+        if a.shape != (L, n, 3, 2):
+            raise ValueError(f"s_load must have shape {(L, n, 3, 2)}")
+        self._ctx._check(lib().okr_batch_plan_set_loads(self._h, int(feeder), _ptr(a)))
+
+    def close(self):
+        if self._h:
+            lib().okr_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

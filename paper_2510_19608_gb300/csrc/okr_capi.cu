@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <new>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -899,23 +900,58 @@ okr_status batch_status_of_setup(int e) {
 
 }  // namespace
 
-static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *feeders, const okr_params *params,
-                                    int32_t n_params, okr_batch_item *items, int32_t *super_of,
-                                    okr_batch_stats *stats, int config) {
-    if (!ctx) return OKR_EINVAL;
-    if (nf < 1 || !feeders || !params || !items) return fail(ctx, OKR_EINVAL, "batch: bad arguments");
+// One batch of feeders, laid out in one device arena and one pinned host
+// block.  The host block holds the staged inputs (descriptors, controls, the
+// order, queues, feeder arrays), then a result area (controls, setup errors,
+// largest errors, copied back after the run) and the assignments.
+struct BatchRun {
+    int nf = 0, config = 0, team = 1, max_teams = 1, maxL = 1, ctas = 0;
+    long long max_nn = 1, tot_n = 0;
+    int per_sm[2] = {0, 0};
+    std::vector<int> merges, nbus, nscen, ord[4];
+    std::vector<long long> sum_sz;
+    std::vector<size_t> in_off, fb_off, super_pos;
+    std::vector<okr_params> params;                 // one per feeder
+    size_t staged = 0, total = 0, super_off = 0, res_off = 0, res_len = 0, host_bytes = 0;
+    unsigned char *base = nullptr, *hb = nullptr;
+    BatchSetup *bs_d = nullptr;
+    BatchFeeder *bf_d = nullptr;
+    Ctrl *ctrl_d = nullptr;
+    int *order_d = nullptr, *queue_d = nullptr, *err_d = nullptr, *super_all_d = nullptr;
+    double *maxerr_d = nullptr;
+    BatchTeam *teams_d = nullptr;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    ~BatchRun() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+    // host views of the result area and of the assignments
+    const Ctrl *ctrl_res() const { return reinterpret_cast<const Ctrl *>(hb + staged); }
+    const int *err_res() const { return reinterpret_cast<const int *>(hb + staged + ((unsigned char *)err_d - (unsigned char *)ctrl_d)); }
+    const double *maxerr_res() const {
+        return reinterpret_cast<const double *>(hb + staged + ((unsigned char *)maxerr_d - (unsigned char *)ctrl_d));
+    }
+    int *super_res() const { return reinterpret_cast<int *>(hb + staged + res_len); }
+};
+
+// Checks the batch and computes every size and offset (no memory touched).
+static okr_status batch_measure(okr_ctx *ctx, int32_t nf, const okr_feeder *feeders, const okr_params *params,
+                                int32_t n_params, int config, BatchRun &R) {
+    if (nf < 1 || !feeders || !params) return fail(ctx, OKR_EINVAL, "batch: bad arguments");
     if (n_params != 1 && n_params != nf) return fail(ctx, OKR_EINVAL, "batch: n_params must be 1 or n_feeders");
     if (config < 0 || config > 3) return fail(ctx, OKR_EINVAL, "batch: config %d", config);
-    const int team = 1 << config;                       // CTAs per feeder: 1, 2, 4, 8
-    int per_sm[2] = {search_batch_blocks_per_sm(0), search_batch_blocks_per_sm(1)};
-    if (per_sm[0] < 1 || per_sm[1] < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
-    const int max_teams = std::max(1, ctx->num_sms * std::max(per_sm[0], per_sm[1]) / team);
-    ctx->have_result = false;
-    ctx->have_topo = false;
-    std::vector<long long> sum_sz(nf);
-    std::vector<int> merges(nf);
-    int maxL = 1;
-    long long max_nn = 1, tot_n = 0;
+    R.nf = nf;
+    R.config = config;
+    R.team = 1 << config;                               // CTAs per feeder: 1, 2, 4, 8
+    R.per_sm[0] = search_batch_blocks_per_sm(0);
+    R.per_sm[1] = search_batch_blocks_per_sm(1);
+    if (R.per_sm[0] < 1 || R.per_sm[1] < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
+    R.max_teams = std::max(1, ctx->num_sms * std::max(R.per_sm[0], R.per_sm[1]) / R.team);
+    R.sum_sz.assign(nf, 0);
+    R.merges.assign(nf, 0);
+    R.nbus.assign(nf, 0);
+    R.nscen.assign(nf, 0);
+    R.params.assign(nf, okr_params{});
     for (int f = 0; f < nf; ++f) {
         const okr_feeder *F = &feeders[f];
         const okr_params *P = &params[n_params == 1 ? 0 : f];
@@ -933,32 +969,42 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
             if (i > 0) dep[i] = dep[F->parent[i]] + 1;
             ss += dep[i] + 1;
         }
-        sum_sz[f] = ss;
-        merges[f] = merges_for(n, P);
-        maxL = std::max(maxL, (int)F->n_scen);
-        max_nn = std::max(max_nn, (long long)n * n);
-        tot_n += n;
+        R.sum_sz[f] = ss;
+        R.merges[f] = merges_for(n, P);
+        R.nbus[f] = n;
+        R.nscen[f] = F->n_scen;
+        R.params[f] = *P;
+        R.maxL = std::max(R.maxL, (int)F->n_scen);
+        R.max_nn = std::max(R.max_nn, (long long)n * n);
+        R.tot_n += n;
     }
-    // ---- layout: [staged block: descriptors, controls, order, queues, flags, inputs] [per-feeder buffers] [outputs]
-    Carver m;                                   // staged block (mirrors the pinned host buffer)
-    BatchSetup *bs_d = nullptr;
-    BatchFeeder *bf_d = nullptr;
-    Ctrl *ctrl_d = nullptr;
-    int *order_d = nullptr, *queue_d = nullptr, *err_d = nullptr;
-    double *maxerr_d = nullptr;
-    BatchTeam *teams_d = nullptr;
-    m.take(bs_d, nf);
-    m.take(bf_d, nf);
-    m.take(ctrl_d, nf);
-    m.take(order_d, nf);
-    m.take(queue_d, 2);
-    m.take(err_d, nf);
-    m.take(maxerr_d, nf);
-    m.take(teams_d, 2 * (size_t)max_teams);
-    std::vector<size_t> in_off(nf);
+    // largest expected work first; lists: sweep FP64, sweep mixed precision,
+    // incremental FP64, incremental mixed precision
+    for (int g = 0; g < 4; ++g) R.ord[g].clear();
     for (int f = 0; f < nf; ++f) {
-        const size_t n = feeders[f].n_bus, L = feeders[f].n_scen;
-        in_off[f] = m.used;
+        const okr_params &P = R.params[f];
+        R.ord[(resolve_engine(&P) == OKR_ENGINE_INCREMENTAL ? 2 : 0) + P.precision].push_back(f);
+    }
+    for (int g = 0; g < 4; ++g)
+        std::stable_sort(R.ord[g].begin(), R.ord[g].end(), [&](int a, int b) {
+            return (double)R.nbus[a] * R.merges[a] > (double)R.nbus[b] * R.merges[b];
+        });
+    // ---- layout: [staged block: descriptors, controls, order, queues, flags, inputs] [per-feeder buffers] [outputs]
+    Carver m;
+    m.take(R.bs_d, nf);
+    m.take(R.bf_d, nf);
+    R.res_off = m.used;                         // result area: controls .. largest errors
+    m.take(R.ctrl_d, nf);
+    m.take(R.order_d, nf);
+    m.take(R.queue_d, 2);
+    m.take(R.err_d, nf);
+    m.take(R.maxerr_d, nf);
+    R.res_len = m.used - R.res_off;
+    m.take(R.teams_d, 2 * (size_t)R.max_teams);
+    R.in_off.assign(nf, 0);
+    for (int f = 0; f < nf; ++f) {
+        const size_t n = R.nbus[f], L = R.nscen[f];
+        R.in_off[f] = m.used;
         int *a; uint8_t *b; double *c, *d; double2 *e;
         m.take(a, n);
         m.take(b, n);
@@ -966,52 +1012,42 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         m.take(d, 6 * L * n);
         m.take(e, 3);
     }
-    const size_t staged = m.used;
-    std::vector<size_t> fb_off(nf);
+    R.staged = m.used;
+    R.fb_off.assign(nf, 0);
     Carver w;
-    w.used = staged;
-    std::vector<FeederBufs> fbs(nf);
+    w.used = R.staged;
     for (int f = 0; f < nf; ++f) {
-        const int n = feeders[f].n_bus, L = feeders[f].n_scen;
+        const int n = R.nbus[f], L = R.nscen[f];
         const int ppc = positions_per_chunk(L);
-        const long long chunks = 2LL * ((2LL * sum_sz[f] + 2LL * n + ppc - 1) / ppc + 1);
-        fb_off[f] = w.used;
-        layout_feeder(w, n, L, 0, 8, chunks, fbs[f]);          // per-CTA sums for teams of up to 8
+        const long long chunks = 2LL * ((2LL * R.sum_sz[f] + 2LL * n + ppc - 1) / ppc + 1);
+        R.fb_off[f] = w.used;
+        FeederBufs tmp;
+        layout_feeder(w, n, L, 0, 8, chunks, tmp);          // per-CTA sums for teams of up to 8
     }
-    int *super_all_d = nullptr;
-    const size_t super_off = w.used;
-    w.take(super_all_d, (size_t)tot_n);
-    const size_t total = w.used;
-    if (total > ctx->batch_cap) {
-        if (ctx->batch_arena) cudaFree(ctx->batch_arena);
-        ctx->batch_arena = nullptr;
-        ctx->batch_cap = 0;
-        CK(cudaMalloc(&ctx->batch_arena, total));
-        ctx->batch_cap = total;
-    }
-    const size_t host_need = std::max(staged, (size_t)tot_n * sizeof(int));
-    if (host_need > ctx->batch_host_cap) {
-        if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
-        ctx->batch_host = nullptr;
-        ctx->batch_host_cap = 0;
-        CK(cudaMallocHost((void **)&ctx->batch_host, host_need));
-        ctx->batch_host_cap = host_need;
-    }
-    unsigned char *base = static_cast<unsigned char *>(ctx->batch_arena);
-    unsigned char *hb = ctx->batch_host;
-    super_all_d = reinterpret_cast<int *>(base + super_off);      // the measuring pass left it null
-    std::memset(hb, 0, staged);
-    // device pointers of the staged block
+    R.super_off = w.used;
+    int *sup = nullptr;
+    w.take(sup, (size_t)R.tot_n);
+    R.total = w.used;
+    R.host_bytes = R.staged + R.res_len + sizeof(int) * (size_t)R.tot_n;
+    return OKR_OK;
+}
+
+// Device pointers of the arena at R.base and the staged inputs in R.hb.
+static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeders) {
+    const int nf = R.nf;
+    unsigned char *base = R.base, *hb = R.hb;
+    std::memset(hb, 0, R.staged);
     Carver md;
     md.base = base;
-    md.take(bs_d, nf);
-    md.take(bf_d, nf);
-    md.take(ctrl_d, nf);
-    md.take(order_d, nf);
-    md.take(queue_d, 2);
-    md.take(err_d, nf);
-    md.take(maxerr_d, nf);
-    md.take(teams_d, 2 * (size_t)max_teams);
+    md.take(R.bs_d, nf);
+    md.take(R.bf_d, nf);
+    md.take(R.ctrl_d, nf);
+    md.take(R.order_d, nf);
+    md.take(R.queue_d, 2);
+    md.take(R.err_d, nf);
+    md.take(R.maxerr_d, nf);
+    md.take(R.teams_d, 2 * (size_t)R.max_teams);
+    R.super_all_d = reinterpret_cast<int *>(base + R.super_off);
     Carver mh;                                  // the same offsets in the host buffer
     mh.base = hb;
     BatchSetup *bs_h; BatchFeeder *bf_h; Ctrl *ctrl_h; int *order_h, *queue_h, *err_h; double *maxerr_h;
@@ -1023,27 +1059,28 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     mh.take(err_h, nf);
     mh.take(maxerr_h, nf);
     BatchTeam *teams_h;
-    mh.take(teams_h, 2 * (size_t)max_teams);
-    for (int i = 0; i < 2 * max_teams; ++i) {
-        teams_h[i].ctrl.max_spins = params[0].max_spins > 0 ? params[0].max_spins : kDefaultSpins;
+    mh.take(teams_h, 2 * (size_t)R.max_teams);
+    for (int i = 0; i < 2 * R.max_teams; ++i) {
+        teams_h[i].ctrl.max_spins = R.params[0].max_spins > 0 ? R.params[0].max_spins : kDefaultSpins;
         teams_h[i].slot = 0;
     }
-    // per feeder: buffers, inputs, descriptors, controls
     size_t soff = 0;
-    std::vector<size_t> super_pos(nf);
+    R.super_pos.assign(nf, 0);
     for (int f = 0; f < nf; ++f) {
         const okr_feeder *F = &feeders[f];
-        const okr_params *P = &params[n_params == 1 ? 0 : f];
+        const okr_params *P = &R.params[f];
         const int n = F->n_bus, L = F->n_scen;
+        const int ppc = positions_per_chunk(L);
+        const long long chunks = 2LL * ((2LL * R.sum_sz[f] + 2LL * n + ppc - 1) / ppc + 1);
         Carver c;
-        c.base = base + fb_off[f];
-        FeederBufs &B = fbs[f];
-        layout_feeder(c, n, L, 0, 8, B.X.max_chunks, B);
+        c.base = base + R.fb_off[f];
+        FeederBufs B;
+        layout_feeder(c, n, L, 0, 8, chunks, B);
         // inputs live in the staged block
         Carver ci;
-        ci.base = base + in_off[f];
+        ci.base = base + R.in_off[f];
         Carver chh;
-        chh.base = hb + in_off[f];
+        chh.base = hb + R.in_off[f];
         int *pd, *ph_; uint8_t *phd, *phh; double *zd, *zh_, *sd, *sh_; double2 *vd, *vh_;
         ci.take(pd, n); ci.take(phd, n); ci.take(zd, 18 * (size_t)n); ci.take(sd, 6 * (size_t)L * n); ci.take(vd, 3);
         chh.take(ph_, n); chh.take(phh, n); chh.take(zh_, 18 * (size_t)n); chh.take(sh_, 6 * (size_t)L * n); chh.take(vh_, 3);
@@ -1053,10 +1090,10 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         std::memcpy(sh_, F->s_load, sizeof(double) * 6 * L * n);
         for (int p = 0; p < 3; ++p) vh_[p] = make_double2(F->v_slack[p][0], F->v_slack[p][1]);
         B.T.vslack = vd;
-        B.C = ctrl_d + f;
-        B.err_dev = err_d + f;
-        super_pos[f] = soff;
-        B.super_out = super_all_d + soff;
+        B.C = R.ctrl_d + f;
+        B.err_dev = R.err_d + f;
+        R.super_pos[f] = soff;
+        B.super_out = R.super_all_d + soff;
         soff += n;
         BatchSetup &S = bs_h[f];
         S.n = n;
@@ -1087,10 +1124,10 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         D.C = B.C;
         D.setup_err = B.err_dev;
         D.super_out = B.super_out;
-        D.max_err = maxerr_d + f;
+        D.max_err = R.maxerr_d + f;
         Ctrl &cc = ctrl_h[f];
-        cc.max_merges = merges[f];
-        cc.done = (merges[f] == 0);
+        cc.max_merges = R.merges[f];
+        cc.done = (R.merges[f] == 0);
         cc.margin = P->margin;
         cc.tau = P->tie_tol;
         cc.profile = 0;
@@ -1099,89 +1136,104 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         cc.objective = P->objective;
         cc.max_spins = P->max_spins > 0 ? P->max_spins : kDefaultSpins;
     }
-    // largest expected work first; lists: sweep FP64, sweep mixed precision,
-    // incremental FP64, incremental mixed precision
-    std::vector<int> ord[4];
-    for (int f = 0; f < nf; ++f) {
-        const okr_params *P = &params[n_params == 1 ? 0 : f];
-        ord[(resolve_engine(P) == OKR_ENGINE_INCREMENTAL ? 2 : 0) + P->precision].push_back(f);
-    }
-    for (int g = 0; g < 4; ++g)
-        std::stable_sort(ord[g].begin(), ord[g].end(), [&](int a, int b) {
-            return (double)feeders[a].n_bus * merges[a] > (double)feeders[b].n_bus * merges[b];
-        });
     int k = 0;
     for (int g = 0; g < 4; ++g)
-        for (int f : ord[g]) order_h[k++] = f;
-    cudaStream_t st = ctx->stream;
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    CK(cudaEventCreate(&e2));
-    CK(cudaMemcpyAsync(base, hb, staged, cudaMemcpyHostToDevice, st));
-    CK(cudaEventRecord(e0, st));
-    CK(launch_batch_setup(nf, maxL, max_nn, bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
-    CK(cudaEventRecord(e1, st));
-    int ctas = 0;
-    for (int g = 0, first = 0; g < 4; first += (int)ord[g].size(), ++g) {
-        const int cnt = (int)ord[g].size();
+        for (int f : R.ord[g]) order_h[k++] = f;
+    for (cudaEvent_t &e : R.ev)
+        if (!e) CK(cudaEventCreate(&e));
+    // attributes the launches need, set before any stream capture
+    for (int g = 2; g < 4; ++g) {
+        int max_n = 2;
+        for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
+        if (!R.ord[g].empty()) CK(prepare_search_inc_batch(g - 2, max_n));
+    }
+    return OKR_OK;
+}
+
+// The device work of one run on stream st: inputs, setup, searches, results.
+static okr_status batch_enqueue(okr_ctx *ctx, BatchRun &R, cudaStream_t st, bool want_super, bool captured) {
+    const int nf = R.nf;
+    // in a graph, event records are nodes of their own only when external
+    const unsigned evf = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaMemcpyAsync(R.base, R.hb, R.staged, cudaMemcpyHostToDevice, st));
+    CK(cudaEventRecordWithFlags(R.ev[0], st, evf));
+    CK(launch_batch_setup(nf, R.maxL, R.max_nn, R.bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
+    CK(cudaEventRecordWithFlags(R.ev[1], st, evf));
+    R.ctas = 0;
+    for (int g = 0, first = 0; g < 4; first += (int)R.ord[g].size(), ++g) {
+        const int cnt = (int)R.ord[g].size();
         if (cnt == 0) continue;
         if (g >= 2) {                           // one CTA per feeder
-            ctas = std::max(ctas, cnt);
+            R.ctas = std::max(R.ctas, cnt);
             int max_n = 2;
-            for (int i = 0; i < cnt; ++i) max_n = std::max(max_n, (int)feeders[ord[g][i]].n_bus);
-            CK(launch_search_inc_batch(g - 2, max_n, bf_d, order_d + first, cnt, st));
+            for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
+            CK(launch_search_inc_batch(g - 2, max_n, R.bf_d, R.order_d + first, cnt, st));
             continue;
         }
-        const int nteams = std::min(cnt, ctx->num_sms * per_sm[g] / team);
-        if (nteams < 1) return fail(ctx, OKR_EINVAL, "batched search: team of %d CTAs does not fit", team);
-        const int grid = nteams * team;
-        ctas = std::max(ctas, grid);
-        CK(launch_search_batch(g, team, grid, bf_d, order_d + first, cnt, queue_d + g, teams_d + g * max_teams, st));
+        const int nteams = std::min(cnt, ctx->num_sms * R.per_sm[g] / R.team);
+        if (nteams < 1) return fail(ctx, OKR_EINVAL, "batched search: team of %d CTAs does not fit", R.team);
+        const int grid = nteams * R.team;
+        R.ctas = std::max(R.ctas, grid);
+        CK(launch_search_batch(g, R.team, grid, R.bf_d, R.order_d + first, cnt, R.queue_d + g,
+                               R.teams_d + g * R.max_teams, st));
     }
-    CK(cudaEventRecord(e2, st));
+    CK(cudaEventRecordWithFlags(R.ev[2], st, evf));
     // results: controls, setup errors and largest errors (one copy), assignments
-    const size_t res_off = (size_t)((unsigned char *)ctrl_d - base);
-    const size_t res_len = (size_t)((unsigned char *)(maxerr_d + nf) - (unsigned char *)ctrl_d);
-    CK(cudaMemcpyAsync(hb + res_off, base + res_off, res_len, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpyAsync(R.hb + R.staged, R.base + R.res_off, R.res_len, cudaMemcpyDeviceToHost, st));
+    if (want_super)
+        CK(cudaMemcpyAsync(R.super_res(), R.base + R.super_off, sizeof(int) * (size_t)R.tot_n, cudaMemcpyDeviceToHost, st));
+    return OKR_OK;
+}
+
+// After the stream finished: the items, the assignments and the statistics.
+// A feeder whose sweep work buffer overflowed is re-run alone (its feeder is
+// read back from the staged block).
+static okr_status batch_finish(okr_ctx *ctx, BatchRun &R, okr_batch_item *items, int32_t *super_of,
+                               okr_batch_stats *stats) {
+    const int nf = R.nf;
     float ms_setup = 0.f, ms_search = 0.f;
-    cudaEventElapsedTime(&ms_setup, e0, e1);
-    cudaEventElapsedTime(&ms_search, e1, e2);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaEventDestroy(e2);
-    std::vector<Ctrl> ctrl(ctrl_h, ctrl_h + nf);
-    std::vector<int> serr(err_h, err_h + nf);
-    std::vector<double> maxerr(maxerr_h, maxerr_h + nf);
-    if (super_of) {
-        CK(cudaMemcpyAsync(hb, base + super_off, sizeof(int) * (size_t)tot_n, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::memcpy(super_of, hb, sizeof(int) * (size_t)tot_n);
-    }
+    cudaEventElapsedTime(&ms_setup, R.ev[0], R.ev[1]);
+    cudaEventElapsedTime(&ms_search, R.ev[1], R.ev[2]);
+    const Ctrl *ctrl = R.ctrl_res();
+    const int *serr = R.err_res();
+    const double *maxerr = R.maxerr_res();
+    if (super_of) std::memcpy(super_of, R.super_res(), sizeof(int) * (size_t)R.tot_n);
     int64_t cand_total = 0;
     int fallbacks = 0;
     for (int f = 0; f < nf; ++f) {
         okr_batch_item &it = items[f];
         std::memset(&it, 0, sizeof it);
-        const Ctrl &c = ctrl[f];
+        const Ctrl c = ctrl[f];
         if (serr[f]) { it.status = batch_status_of_setup(serr[f]); continue; }
         if (c.err == 7) {                       // work buffers too small: run this feeder alone
             ++fallbacks;
-            const okr_params *P = &params[n_params == 1 ? 0 : f];
-            okr_status s2 = reduce_impl(ctx, &feeders[f], nullptr, nullptr, P, Src::Host);
+            const int n = R.nbus[f], L = R.nscen[f];
+            Carver chh;
+            chh.base = R.hb + R.in_off[f];
+            int *ph_; uint8_t *phh; double *zh_, *sh_; double2 *vh_;
+            chh.take(ph_, n); chh.take(phh, n); chh.take(zh_, 18 * (size_t)n); chh.take(sh_, 6 * (size_t)L * n);
+            chh.take(vh_, 3);
+            okr_feeder F{};
+            F.n_bus = n;
+            F.n_scen = L;
+            F.parent = ph_;
+            F.phases = phh;
+            F.z_line = zh_;
+            F.s_load = sh_;
+            for (int p = 0; p < 3; ++p) { F.v_slack[p][0] = vh_[p].x; F.v_slack[p][1] = vh_[p].y; }
+            okr_status s2 = reduce_impl(ctx, &F, nullptr, nullptr, &R.params[f], Src::Host);
             it.status = s2;
             if (s2 != OKR_OK) continue;
             const Ctrl &l = ctx->last;
             it.n_iter = l.t;
             it.stop_reason = l.stop_reason;
-            it.n_kept = feeders[f].n_bus - l.t;
+            it.n_kept = n - l.t;
             it.candidates = l.candidates;
             it.smice = l.s_cur;
             double me = 0.0;
             if (l.t > 0) CK(cudaMemcpy(&me, ctx->fb.X.dec_maxerr + (l.t - 1), sizeof me, cudaMemcpyDeviceToHost));
             it.max_error = me;
-            if (super_of) CK(cudaMemcpy(super_of + super_pos[f], ctx->fb.super_out, sizeof(int) * feeders[f].n_bus,
+            if (super_of) CK(cudaMemcpy(super_of + R.super_pos[f], ctx->fb.super_out, sizeof(int) * n,
                                         cudaMemcpyDeviceToHost));
             cand_total += l.candidates;
             continue;
@@ -1191,7 +1243,7 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         it.status = OKR_OK;
         it.n_iter = c.t;
         it.stop_reason = c.stop_reason;
-        it.n_kept = feeders[f].n_bus - c.t;
+        it.n_kept = R.nbus[f] - c.t;
         it.candidates = c.candidates;
         it.smice = c.s_cur;
         it.max_error = maxerr[f];
@@ -1201,13 +1253,65 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
         stats->setup_ms = ms_setup;
         stats->search_ms = ms_search;
         stats->candidates = cand_total;
-        stats->config = config;
-        stats->ctas = ctas;
+        stats->config = R.config;
+        stats->ctas = R.ctas;
         stats->fallbacks = fallbacks;
         stats->reserved = 0;
     }
     return OKR_OK;
 }
+
+static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *feeders, const okr_params *params,
+                                    int32_t n_params, okr_batch_item *items, int32_t *super_of,
+                                    okr_batch_stats *stats, int config) {
+    if (!ctx) return OKR_EINVAL;
+    if (!items) return fail(ctx, OKR_EINVAL, "batch: bad arguments");
+    ctx->have_result = false;
+    ctx->have_topo = false;
+    BatchRun R;
+    okr_status s = batch_measure(ctx, nf, feeders, params, n_params, config, R);
+    if (s != OKR_OK) return s;
+    if (R.total > ctx->batch_cap) {
+        if (ctx->batch_arena) cudaFree(ctx->batch_arena);
+        ctx->batch_arena = nullptr;
+        ctx->batch_cap = 0;
+        CK(cudaMalloc(&ctx->batch_arena, R.total));
+        ctx->batch_cap = R.total;
+    }
+    // host block: staged inputs, then the result area and the assignments
+    const size_t host_need = R.host_bytes;
+    if (host_need > ctx->batch_host_cap) {
+        if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+        ctx->batch_host = nullptr;
+        ctx->batch_host_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->batch_host, host_need));
+        ctx->batch_host_cap = host_need;
+    }
+    R.base = static_cast<unsigned char *>(ctx->batch_arena);
+    R.hb = ctx->batch_host;
+    s = batch_fill(ctx, R, feeders);
+    if (s != OKR_OK) return s;
+    s = batch_enqueue(ctx, R, ctx->stream, super_of != nullptr, false);
+    if (s != OKR_OK) return s;
+    CK(cudaStreamSynchronize(ctx->stream));
+    return batch_finish(ctx, R, items, super_of, stats);
+}
+
+// A batch staged once and captured as one CUDA graph (okr_batch_plan_*).
+struct okr_batch_plan {
+    okr_ctx *ctx = nullptr;
+    BatchRun R;
+    void *arena = nullptr;
+    unsigned char *host = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~okr_batch_plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (arena) cudaFree(arena);
+        if (host) cudaFreeHost(host);
+    }
+};
 
 extern "C" {
 
@@ -1246,6 +1350,82 @@ okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder 
     ctx->batch_config = best_c;
     if (config) *config = best_c;
     return OKR_OK;
+}
+
+okr_status okr_batch_plan_create(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                                 int32_t n_params, okr_batch_plan **plan) {
+    if (!ctx || !plan) return OKR_EINVAL;
+    *plan = nullptr;
+    CK(cudaSetDevice(ctx->device));
+    okr_batch_plan *P = new (std::nothrow) okr_batch_plan;
+    if (!P) return fail(ctx, OKR_ENOMEM, "batch plan: out of host memory");
+    P->ctx = ctx;
+    okr_status s = batch_measure(ctx, n_feeders, feeders, params, n_params, ctx->batch_config, P->R);
+    cudaError_t e = cudaSuccess;
+    if (s == OKR_OK) e = cudaMalloc(&P->arena, P->R.total);
+    if (s == OKR_OK && e == cudaSuccess) e = cudaMallocHost((void **)&P->host, P->R.host_bytes);
+    if (s == OKR_OK && e != cudaSuccess) s = fail(ctx, OKR_ENOMEM, "batch plan: %s", cudaGetErrorString(e));
+    if (s == OKR_OK) {
+        P->R.base = static_cast<unsigned char *>(P->arena);
+        P->R.hb = P->host;
+        s = batch_fill(ctx, P->R, feeders);
+    }
+    if (s == OKR_OK) {
+        // the whole device sequence of one run, captured once
+        cudaStream_t st = ctx->stream;
+        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            s = fail(ctx, OKR_ECUDA, "batch plan capture: %s", cudaGetErrorString(e));
+        } else {
+            s = batch_enqueue(ctx, P->R, st, true, true);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(st, &g);
+            P->graph = g;
+            if (s == OKR_OK && e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "batch plan capture: %s", cudaGetErrorString(e));
+        }
+    }
+    if (s == OKR_OK) {
+        e = cudaGraphInstantiate(&P->exec, P->graph, 0);
+        if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "batch plan instantiate: %s", cudaGetErrorString(e));
+    }
+    if (s != OKR_OK) {
+        delete P;
+        return s;
+    }
+    *plan = P;
+    return OKR_OK;
+}
+
+okr_status okr_batch_plan_run(okr_batch_plan *plan, okr_batch_item *items, int32_t *super_of,
+                              okr_batch_stats *stats) {
+    if (!plan || !items) return OKR_EINVAL;
+    okr_ctx *ctx = plan->ctx;
+    CK(cudaSetDevice(ctx->device));
+    ctx->have_result = false;
+    ctx->have_topo = false;
+    CK(cudaGraphLaunch(plan->exec, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return batch_finish(ctx, plan->R, items, super_of, stats);
+}
+
+okr_status okr_batch_plan_set_loads(okr_batch_plan *plan, int32_t feeder, const double *s_load) {
+    if (!plan || !s_load || feeder < 0 || feeder >= plan->R.nf) return OKR_EINVAL;
+    const int n = plan->R.nbus[feeder], L = plan->R.nscen[feeder];
+    Carver chh;
+    chh.base = plan->R.hb + plan->R.in_off[feeder];
+    int *a; uint8_t *b; double *z, *sl;
+    chh.take(a, n);
+    chh.take(b, n);
+    chh.take(z, 18 * (size_t)n);
+    chh.take(sl, 6 * (size_t)L * n);
+    std::memcpy(sl, s_load, sizeof(double) * 6 * (size_t)L * n);
+    return OKR_OK;
+}
+
+void okr_batch_plan_destroy(okr_batch_plan *plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->ctx->device);
+    delete plan;
 }
 
 }  // extern "C"

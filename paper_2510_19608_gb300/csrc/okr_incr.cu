@@ -26,8 +26,8 @@
 // addition is associative, so removing a term's old value and adding its new
 // one gives exactly the sum a fresh evaluation of every term gives, in any
 // order.  The old value is recomputed from the unchanged inputs by the same
-// compiled function (group_term*, not inlined), so it is bit-identical to the
-// value added earlier.  Counts of terms above the margin are carried the same
+// compiled code (run_entries is not inlined; it holds the one copy of the term
+// arithmetic), so it is bit-identical to the value added earlier.  Counts of terms above the margin are carried the same
 // way.  Engine 3 checks the carried values against a fresh evaluation after
 // every merge.
 //
@@ -58,7 +58,7 @@ constexpr int kFxShift = 100;               // fixed point: value * 2^100
 constexpr u128 kSignBit = (u128)1 << 127;
 constexpr u128 kNone = ~(u128)0;
 constexpr float kU32 = 5.9604645e-08f;      // 2^-24
-constexpr int kTE = 512;                    // work entries per tile
+constexpr int kTE = 512;                    // largest tile of work entries (one per thread)
 
 __device__ __forceinline__ unsigned long long gtimer_inc() {
     unsigned long long t;
@@ -300,15 +300,16 @@ __device__ int slot_geometry(const Topo &T, const State &S, int n, int w, Cand &
 // l = gl / 4 and phase p = gl % 4 (p = 3 idles).  Every lane of the warp calls
 // the group function (it shuffles); `valid` is false for lanes whose group has
 // no term.  The results are the group's sums over its scenarios (every lane
-// holds them).  The functions are not inlined, so that every evaluation of a
-// term runs the same instructions and equal inputs give bit-equal results.
+// holds them).  Every carried term is evaluated inside run_entries, which is
+// not inlined: its one compiled copy of these functions runs for every
+// evaluation of a term, so equal inputs give bit-equal results.
 
 // FP64 term.  d = sum over l of fixed(new MICE - MICE_k [- MICE_r]); nv = scenarios
 // whose new MICE exceeds the margin.  out != nullptr: the new voltage and
 // magnitude per (l, p) and the new MICE per l (the merge).
-__device__ __noinline__ void group_term64(const Topo &T, const State &S, const uint8_t *ph, int n, int L,
-                                          const Cand &c, int k, bool valid, int gl, double margin, double *out,
-                                          unsigned long long *dlo, unsigned long long *dhi, int *n1) {
+__device__ __forceinline__ void group_term64(const Topo &T, const State &S, const uint8_t *ph, int n, int L, int G,
+                                             const Cand &c, int k, bool valid, int gl, double margin, double *out,
+                                             u128 *d_out, int *nv_out) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
     const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
@@ -367,15 +368,21 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, const u
     }
     double m = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
     m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    u128 d = 0;
+    int nv = 0;
     if (lv && p == 0) {
         if (out) out[9 * L + l] = m;
-        if (dlo) {
-            double dd = m - mo;
-            if (is_s) dd -= mr;
-            sadd128(dlo, dhi, to_fx(dd));
-            if (m > margin) atomicAdd(n1, 1);
-        }
+        double dd = m - mo;
+        if (is_s) dd -= mr;
+        d = to_fx(dd);
+        nv = (m > margin) ? 1 : 0;
     }
+    for (int o = 4; o < G; o <<= 1) {            // the group's sum over its scenarios
+        d += shfl_xor_u128(d, o);
+        nv += __shfl_xor_sync(0xffffffffu, nv, o);
+    }
+    *d_out = d;
+    *nv_out = nv;
 }
 
 // FP32 term with a rigorous bound (the screen of okr_persist.cu, per item
@@ -383,10 +390,9 @@ __device__ __noinline__ void group_term64(const Topo &T, const State &S, const u
 // d = sum over l of fixed(D32 term); b = sum over l of a fixed-point bound on
 // |fixed(D32 term) - fixed(D64 term)|; n_sure = scenarios whose new MICE is
 // surely above the margin; n_maybe = scenarios where it may be.
-__device__ __noinline__ void group_term32(const Topo &T, const State &S, const uint8_t *ph, int n, int L,
-                                          const Cand &c, int k, bool valid, int gl, float margin_lo, float margin_hi,
-                                          unsigned long long *dlo, unsigned long long *dhi, unsigned long long *blo,
-                                          unsigned long long *bhi, int *n1, int *n2) {
+__device__ __forceinline__ void group_term32(const Topo &T, const State &S, const uint8_t *ph, int n, int L, int G,
+                                             const Cand &c, int k, bool valid, int gl, float margin_lo,
+                                             float margin_hi, u128 *d_out, u128 *b_out, int *ns_out, int *nm_out) {
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
     const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
@@ -459,17 +465,28 @@ __device__ __noinline__ void group_term32(const Topo &T, const State &S, const u
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
     float bm = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, 1));
     bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
+    u128 d = 0, bb = 0;
+    int ns = 0, nm = 0;
     if (lv && p == 0) {
         const float dd = (m - mo) - mr;
         // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
         // factor 1.001 covers the rounding of the bound's own arithmetic
         const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(mo) + fabsf(mr) + fabsf(m)));
-        // each scenario's term goes straight into the entry's exact sums
-        sadd128(dlo, dhi, to_fx32(dd));
-        sadd128(blo, bhi, to_fx32(bl) + 3);       // + the truncations of both terms to fixed point
-        if (__fsub_rd(m, bm) > margin_hi) atomicAdd(n1, 1);
-        if (__fadd_ru(m, bm) > margin_lo) atomicAdd(n2, 1);
+        d = to_fx32(dd);
+        bb = to_fx32(bl) + 3;            // + the truncations of both terms to fixed point
+        ns = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
+        nm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
     }
+    for (int o = 4; o < G; o <<= 1) {            // the group's sums over its scenarios
+        d += shfl_xor_u128(d, o);
+        bb += shfl_xor_u128(bb, o);
+        ns += __shfl_xor_sync(0xffffffffu, ns, o);
+        nm += __shfl_xor_sync(0xffffffffu, nm, o);
+    }
+    *d_out = d;
+    *b_out = bb;
+    *ns_out = ns;
+    *nm_out = nm;
 }
 
 // ---------------------------------------------------------------- the changed set of a merge
@@ -685,19 +702,21 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
             k = q < n1 ? cm.list[h.q1lo + q] : (q < n1 + n2 ? cm.list[h.q2lo + q - n1] : cm.wc.s);
             if (k == cm.wc.r) { valid = false; k = cm.wc.s; }
         }
-        group_term64(T, S, cm.ph, n, L, cm.wc, k, valid, gl, margin, valid ? I.cbuf + (size_t)q * 10 * L : nullptr,
-                     nullptr, nullptr, nullptr);
+        u128 d;
+        int nv;
+        group_term64(T, S, cm.ph, n, L, G, cm.wc, k, valid, gl, margin,
+                     valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d, &nv);
         if (valid && gl == 0) items += __popc(cm.ph[k]) * L;
     }
     return items;
 }
 
-// Evaluates the terms of work entries [e0, e1) (tiles of kTE entries) and applies
+// Evaluates the terms of work entries [e0, e1) (tiles of NT entries) and applies
 // them per the pass.  Mode-0 entries take positions from list_pre (and skip r*
 // after the merge), mode-1 entries from list_post; kFresh / kF64 use list_pre.
 // Returns the number of terms evaluated.
 template <int NT, int PREC>
-__device__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
+__device__ __noinline__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
                                  double margin, float mlo, float mhi, int e0, int e1, int pass,
                                  const unsigned short *list_pre, const unsigned short *list_post, int rstar,
                                  EvalSmem &E, int *sscan, const Rec &R, const Loc &Lc,
@@ -708,8 +727,8 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
     auto sub = [&](int i) {             // profile mode: time of the pass's steps (thread 0, after barriers)
         if (prof && tid == 0) { const unsigned long long now = gtimer_inc(); prof[i] += now - tq; tq = now; }
     };
-    for (int t0 = e0; t0 < e1; t0 += kTE) {
-        const int ne = min(kTE, e1 - t0);
+    for (int t0 = e0; t0 < e1; t0 += NT) {
+        const int ne = min(NT, e1 - t0);
         int cnt = 0;
         if (tid < ne) {
             const IncWork &w = *Lc.ent(t0 + tid);
@@ -717,8 +736,9 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
         }
         int tot = 0;
         const int off = block_excl_scan<NT>(cnt, &tot, sscan);
-        if (tid < kTE) E.off[tid] = off;
-        for (int i = tid; i < kTE; i += NT) {
+        E.off[tid] = off;
+        {
+            const int i = tid;
             E.dlo[i] = E.dhi[i] = E.blo[i] = E.bhi[i] = 0ull;
             E.n1[i] = E.n2[i] = 0;
         }
@@ -762,10 +782,23 @@ __device__ long long run_entries(const Topo &T, const State &S, const Search &X,
             const unsigned long long c0 = (prof && tid == 0) ? clock64() : 0;
             if (prof && tid == 0) prof[3] += c0 - cq;
             if (PREC == 0 || pass == kF64) {
-                group_term64(T, S, Lc.ph, n, L, c, k, valid, gl, margin, nullptr, &E.dlo[ei], &E.dhi[ei], &E.n1[ei]);
+                u128 d;
+                int nv;
+                group_term64(T, S, Lc.ph, n, L, G, c, k, valid, gl, margin, nullptr, &d, &nv);
+                if (valid && gl == 0) {
+                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
+                    if (nv) atomicAdd(&E.n1[ei], nv);
+                }
             } else {
-                group_term32(T, S, Lc.ph, n, L, c, k, valid, gl, mlo, mhi, &E.dlo[ei], &E.dhi[ei], &E.blo[ei],
-                             &E.bhi[ei], &E.n1[ei], &E.n2[ei]);
+                u128 d, b;
+                int ns, nm;
+                group_term32(T, S, Lc.ph, n, L, G, c, k, valid, gl, mlo, mhi, &d, &b, &ns, &nm);
+                if (valid && gl == 0) {
+                    sadd128(&E.dlo[ei], &E.dhi[ei], d);
+                    sadd128(&E.blo[ei], &E.bhi[ei], b);
+                    if (ns) atomicAdd(&E.n1[ei], ns);
+                    if (nm) atomicAdd(&E.n2[ei], nm);
+                }
             }
             if (prof && tid == 0) prof[4] += clock64() - c0;
         }
@@ -867,7 +900,7 @@ __host__ __device__ constexpr size_t base_bytes(int n) {
 template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
                         unsigned char *dyn, bool rec_in_smem) {
-    static_assert(NT >= kTE && NT <= 1024, "thread count");
+    static_assert(NT >= 128 && NT <= kTE, "thread count");
     __shared__ __align__(16) EvalSmem E;
     __shared__ __align__(16) Red sred[33];
     __shared__ int sscan[33];
@@ -1411,20 +1444,21 @@ cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, C
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+cudaError_t prepare_search_inc_batch(int precision, int max_n) {
+    int use = 0;
+    const size_t smem = inc_smem(max_n, &use);
+    return precision == 1 ? set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem)
+                          : set_smem(k_search_inc_batch<kIncBatchThreads, 0>, smem);
+}
+
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
                                     cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
     int use = 0;
     const size_t smem = inc_smem(max_n, &use);
-    cudaError_t e;
-    if (precision == 1) {
-        e = set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem);
-        if (e == cudaSuccess) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
-    } else {
-        e = set_smem(k_search_inc_batch<kIncBatchThreads, 0>, smem);
-        if (e == cudaSuccess) k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
-    }
-    return e != cudaSuccess ? e : cudaGetLastError();
+    if (precision == 1) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
+    else k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
+    return cudaGetLastError();
 }
 
 }  // namespace okr

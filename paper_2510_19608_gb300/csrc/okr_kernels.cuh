@@ -138,7 +138,10 @@ __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, dou
 // feeder (verify = 1: every merge also re-evaluates every candidate and counts
 // mismatches of the carried scores in C->inc_mismatch).
 cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st);
-// Many feeders: one CTA each, in the order given.
+// Many feeders: one CTA each, in the order given (prepare_search_inc_batch with
+// the same precision and at least the same largest feeder first: it sets the
+// kernel's shared-memory attribute, which a stream capture must not see).
+cudaError_t prepare_search_inc_batch(int precision, int max_n);
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
                                     cudaStream_t st);
 
