@@ -250,6 +250,25 @@ def batch_line(K, ctx, reps=3):
                     "e2e_feeders_per_s": len(feeders) / wall, "e2e_ms": 1e3 * wall,
                     "candidates": st["candidates"], "ctas": st["ctas"], "fallbacks": st["fallbacks"],
                     "failed_feeders": bad}
+        if key == "incremental_mixed":
+            # the same batch captured once as a CUDA graph and replayed
+            plan = ctx.batch_plan(feeders, plist)
+            try:
+                plan.run()                                                # warm-up
+                walls, dev_ms = [], []
+                for _ in range(reps):
+                    t0 = time.perf_counter()
+                    items, _, st = plan.run()
+                    walls.append(time.perf_counter() - t0)
+                    dev_ms.append(st["setup_ms"] + st["search_ms"])
+            finally:
+                plan.close()
+            wall = statistics.median(walls)
+            dms = statistics.median(dev_ms)
+            out["incremental_mixed_graph"] = {
+                "feeders_per_s": len(feeders) / (dms / 1e3), "device_ms": dms, "e2e_feeders_per_s": len(feeders) / wall,
+                "e2e_ms": 1e3 * wall, "failed_feeders": sum(1 for it in items if it["status"] != 0),
+                "note": "okr_batch_plan_run: input copy, setup, search and result copies replayed as one CUDA graph"}
     return out
 
 
