@@ -36,8 +36,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_ITEM = 40
 # DRAM bytes of one search launch on this workload from the ncu capture in
 # profiles/, valid only for the kernel source it was taken on (None otherwise)
-NCU_TRAFFIC = {"bytes": 1128448 + 2560, "source": "paper_2510_19608_gb300/csrc/okr_incr.cu",
-               "sha256_prefix": "5ab9d957ccd00acc", "summary": "profiles/k_search_inc_feeder1000.md"}
+NCU_TRAFFIC = {"bytes": 1092096 + 2560, "source": "paper_2510_19608_gb300/csrc/okr_incr.cu",
+               "sha256_prefix": "606dcfa1dda3f772", "summary": "profiles/k_search_inc_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 
@@ -319,6 +319,7 @@ def learned_line(K, ctx, n_train=64, record=64):
                 "stop_reason": sm["stop_reason"], "smice": sm["smice"], "max_error": sm["max_error"],
                 "fallbacks": sm["scorer_fallbacks"]}
         pruned[name] = rows
+    inference = scorer.inference_timing(ctx, 1 << 20)       # replaces the trained network: last
     return {"train_feeders": n_train, "iterations_per_feeder": record, "samples": int(X.shape[0]),
             "epochs": len(loss), "loss_first_last": [float(loss[0]), float(loss[-1])],
             "collect_s": t_collect, "train_s": t_train, "train_samples_per_s": len(loss) * X.shape[0] / t_train,
@@ -326,7 +327,7 @@ def learned_line(K, ctx, n_train=64, record=64):
                      "predict_and_rank_s": t_eval,
                      "top_k": {str(k): v for k, v in q.items() if isinstance(k, int)},
                      "winner_rank_percentile": q["winner_rank_percentile"]},
-            "pruned_search": pruned}
+            "pruned_search": pruned, "inference": inference}
 
 
 def sweeps_line(K, ctx):

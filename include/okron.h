@@ -332,6 +332,12 @@ okr_status okr_scorer_train(okr_ctx *ctx, const float *x, const float *t, int64_
                             float lr, double *epoch_loss);
 /* Predictions y (HOST [n]) for x (HOST [n][n_features]). */
 okr_status okr_scorer_predict(okr_ctx *ctx, const float *x, int64_t n, float *y);
+/* The same network on the tensor cores (tcgen05, 128 samples per product):
+ * the features and the hidden activations enter each product as bfloat16
+ * (both operands of a bfloat16 tensor-core product are bfloat16), products and
+ * sums are FP32.  For ranking many candidates; training keeps FP32 activations
+ * (okr_scorer_predict).  OKR_ETIMEOUT if a wait for the products gave up. */
+okr_status okr_scorer_predict_tc(okr_ctx *ctx, const float *x, int64_t n, float *y);
 
 /* The reduced network of a given assignment, evaluated on the feeder's own
  * scenarios (HOST feeder; its load flows are solved first): super-nodes take

@@ -80,3 +80,18 @@ def bf16_round(a: np.ndarray) -> np.ndarray:
     u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
     r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
     return (r.astype(np.uint32)).view(np.float32)
+
+
+def forward_bf16_operands(theta: np.ndarray, x: np.ndarray, hidden: int = H) -> np.ndarray:
+    """Prediction when every product of a hidden layer takes bfloat16 operands:
+    the weights W1, W2, W3, w4 and each hidden layer's input (the features, h1,
+    h2) are rounded to bfloat16 (nearest, ties to even) before the product; the
+    products, sums, biases and ReLU are exact (FP64).  The output layer takes
+    h3 unrounded.  This is the arithmetic of a bfloat16 tensor-core product with
+    a wide accumulator, written out."""
+    W1, b1, W2, b2, W3, b3, w4, b4 = unpack(np.asarray(theta, np.float64), x.shape[1], hidden)
+    r = lambda a: bf16_round(np.asarray(a, np.float64)).astype(np.float64)
+    h = np.asarray(x, np.float64)
+    for W, b in ((W1, b1), (W2, b2), (W3, b3)):
+        h = np.maximum(r(h) @ r(W) + b, 0.0)
+    return h @ r(w4) + b4[0]

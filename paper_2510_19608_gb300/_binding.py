@@ -66,7 +66,7 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_power_flow_static", "okr_kron", "okr_reduce_batch", "okr_batch_autotune",
            "okr_set_batch_config", "okr_radialize", "okr_get_recorded_features", "okr_scorer_init",
            "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict",
-           "okr_evaluate", "okr_batch_plan_create", "okr_batch_plan_run", "okr_batch_plan_set_loads",
+           "okr_evaluate", "okr_scorer_predict_tc", "okr_batch_plan_create", "okr_batch_plan_run", "okr_batch_plan_set_loads",
            "okr_batch_plan_destroy")
 
 
@@ -114,6 +114,7 @@ def lib():
             L.okr_scorer_gradient.argtypes = [P, P, P, I32, P, P]
             L.okr_scorer_train.argtypes = [P, P, P, C.c_int64, I32, I32, C.c_float, P]
             L.okr_scorer_predict.argtypes = [P, P, C.c_int64, P]
+            L.okr_scorer_predict_tc.argtypes = [P, P, C.c_int64, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
@@ -356,6 +357,14 @@ class Context:
         x = np.ascontiguousarray(x, dtype=np.float32)
         y = np.zeros(x.shape[0], np.float32)
         self._check(lib().okr_scorer_predict(self._h, _ptr(x), int(x.shape[0]), _ptr(y)))
+        return y
+
+    def scorer_predict_tc(self, x) -> np.ndarray:
+        """okr_scorer_predict_tc: the same network on the tensor cores (bfloat16
+        layer inputs, FP32 accumulation)."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.zeros(x.shape[0], np.float32)
+        self._check(lib().okr_scorer_predict_tc(self._h, _ptr(x), int(x.shape[0]), _ptr(y)))
         return y
 
     def kron(self, kept=None):

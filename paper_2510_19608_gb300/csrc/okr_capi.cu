@@ -72,6 +72,7 @@ struct okr_ctx {
     MlpWork mw;
     std::vector<void *> mlp_allocs, mlp_work_allocs, mlp_data_allocs;
     float *mlp_x = nullptr, *mlp_t = nullptr;    // device copies of a data set
+    int *mlp_err = nullptr;                      // error flag of the tensor-core inference
     long long mlp_data_cap = 0;
     int mlp_step = 0;
 
@@ -134,6 +135,8 @@ void free_mlp(okr_ctx *ctx) {
     ctx->mw = MlpWork{};
     ctx->mlp_data_cap = 0;
     ctx->mlp_x = ctx->mlp_t = nullptr;
+    if (ctx->mlp_err) cudaFree(ctx->mlp_err);
+    ctx->mlp_err = nullptr;
 }
 
 void free_all(okr_ctx *ctx) {
@@ -1676,6 +1679,28 @@ okr_status okr_scorer_train(okr_ctx *ctx, const float *x, const float *t, int64_
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return OKR_OK;
+}
+
+okr_status okr_scorer_predict_tc(okr_ctx *ctx, const float *x, int64_t n, float *y) {
+    if (!ctx || !x || !y || n < 1) return OKR_EINVAL;
+    if (!ctx->mb.theta) return fail(ctx, OKR_ENOTREADY, "scorer not initialised");
+    if (n > INT32_MAX) return fail(ctx, OKR_EINVAL, "too many samples");
+    CK(cudaSetDevice(ctx->device));
+    okr_status s = mlp_upload(ctx, x, nullptr, n);
+    if (s != OKR_OK) return s;
+    float *yd = ctx->mlp_t;                     // the targets' buffer holds the predictions
+    if (!ctx->mlp_err) CK(cudaMalloc(&ctx->mlp_err, sizeof(int)));
+    int *err = ctx->mlp_err;
+    okr_status out = OKR_OK;
+    cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);
+    if (e == cudaSuccess) e = mlp_forward_tc(ctx->mb, ctx->mlp_x, (int)n, yd, err, ctx->num_sms, ctx->stream);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(y, yd, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) out = fail(ctx, OKR_ECUDA, "tensor-core inference: %s", cudaGetErrorString(e));
+    else if (herr) out = fail(ctx, OKR_ETIMEOUT, "tensor-core inference: a wait for the products gave up");
+    return out;
 }
 
 okr_status okr_scorer_predict(okr_ctx *ctx, const float *x, int64_t n, float *y) {

@@ -104,6 +104,9 @@ cudaError_t mlp_gradient(const MlpBufs &b, const MlpWork &w, const float *x, con
                          cudaStream_t st);
 cudaError_t mlp_adam(const MlpBufs &b, float lr, int step, cudaStream_t st);
 cudaError_t mlp_sqerr(const float *y, const float *t, int N, float *part, cudaStream_t st);
+// okr_mlp_tc.cu: inference on the tensor cores (bfloat16 operands, FP32
+// accumulators in tensor memory); *err (device) is set to 1 when a wait gave up.
+cudaError_t mlp_forward_tc(const MlpBufs &b, const float *x, int N, float *y, int *err, int num_sms, cudaStream_t st);
 
 // okr_persist.cu
 // One feeder of a batched search launch.

@@ -13,7 +13,9 @@ then puts the likely optimum first.
 """
 from __future__ import annotations
 
+import json
 import math
+import time
 
 import numpy as np
 
@@ -121,3 +123,37 @@ def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256), T=None,
     pct = [float(np.searchsorted(np.sort(pred[a:b]), pred[a + w], side="left")) / (b - a) for a, b, w in rows]
     out["winner_rank_percentile"] = float(np.mean(pct)) if pct else float("nan")
     return out
+
+
+def inference_timing(ctx: "B.Context", n: int, n_features: int = 12, reps: int = 5, seed: int = 0) -> dict:
+    """Wall time of okr_scorer_predict (CUDA cores, FP32 activations) and
+    okr_scorer_predict_tc (tensor cores, bfloat16 layer inputs) on n seeded
+    samples, host copies included, with a freshly initialised network (the
+    context's scorer is replaced)."""
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0.0, 1.0, (n, n_features)).astype(np.float32)
+    ctx.scorer_init(n_features, init_params(n_features, seed))
+    out = {"samples": n, "features": n_features,
+           "flops_per_sample": 2 * 128 * (n_features + 2 * 128 + 1)}
+    ys = {}
+    for name, fn in (("cuda_core", ctx.scorer_predict), ("tensor_core", ctx.scorer_predict_tc)):
+        ys[name] = fn(x)                                  # warm-up
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn(x)
+            times.append(time.perf_counter() - t0)
+        out[name + "_ms"] = 1e3 * float(np.median(times))
+    out["max_abs_difference"] = float(np.abs(ys["cuda_core"] - ys["tensor_core"]).max())
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="time the scorer's inference on seeded samples")
+    ap.add_argument("--samples", type=int, default=1 << 20)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--device", type=int, default=0)
+    a = ap.parse_args()
+    with B.Context(a.device) as c:
+        print(json.dumps(inference_timing(c, a.samples, reps=a.reps)))

@@ -51,6 +51,31 @@ def test_forward_matches_oracle(ctx):
     assert np.abs(y - y_ref).max() <= 1e-4 * max(1.0, np.abs(y_ref).max())
 
 
+@pytest.mark.parametrize("Fx,N", [(12, 1), (12, 127), (12, 129), (3, 1000), (16, 4096), (12, 40000)])
+def test_tensor_core_forward_matches_oracle(ctx, Fx, N):
+    """okr_scorer_predict_tc against the FP64 forward with bfloat16 operands
+    (weights and every layer input rounded).  A layer input within FP32
+    accumulation error of a bfloat16 rounding boundary may round the other way
+    on the GPU; that moves the output by about one bfloat16 step of one
+    activation's share, hence a tolerance above FP32 rounding for the largest
+    deviation and a much tighter one for the median."""
+    from paper_2510_19608_gb300 import scorer
+    rng = np.random.default_rng(100 + N)
+    theta = scorer.init_params(Fx, 7 + Fx)
+    x = rng.normal(0.0, 1.0, (N, Fx)).astype(np.float32)
+    ctx.scorer_init(Fx, theta)
+    y = ctx.scorer_predict_tc(x)
+    y_ref = M.forward_bf16_operands(_bf16_weights(theta, Fx), x.astype(np.float64))
+    scale = max(1.0, np.abs(y_ref).max())
+    d = np.abs(y - y_ref)
+    assert d.max() <= 2e-3 * scale
+    assert np.median(d) <= 1e-5 * scale
+    # the CUDA-core forward (FP32 activations) ranks the same way
+    y_cc = ctx.scorer_predict(x)
+    assert np.abs(y - y_cc).max() <= 2e-2 * scale
+    ctx.scorer_init(F, _problem(1, 1)[0])
+
+
 @pytest.mark.parametrize("N", [1, 33, 4100])
 def test_gradient_matches_oracle(ctx, N):
     theta, x, t = _problem(2 + N, N)

@@ -1,7 +1,8 @@
 """Pins of the scorer network's CPU oracle (oracle/mlp.py): the backward pass
 against central finite differences of the loss, the forward pass on a network
-whose output is worked out by hand, and the bfloat16 rounding on known bit
-patterns."""
+whose output is worked out by hand, the bfloat16 rounding on known bit
+patterns, and the forward pass with bfloat16 operands (the tensor-core
+inference) on a hand-worked network and on values bfloat16 holds exactly."""
 from __future__ import annotations
 
 import numpy as np
@@ -40,3 +41,39 @@ def test_bf16_rounding_on_known_values():
     vals = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -2.5, 3.140625, 1.0 + 2.0 ** -9], np.float32)
     want = np.array([1.0, 1.0, 1.0 + 2.0 ** -6, -2.5, 3.140625, 1.0], np.float32)
     assert np.array_equal(M.bf16_round(vals), want)
+
+
+def test_bf16_operand_forward_rounds_each_layer_input():
+    # x = (1, 2^-9) is exact in bfloat16; W1 sums both inputs into unit 0, so
+    # h1 = (1 + 2^-9, 0).  Layer 2 takes h1 rounded (1 + 2^-9 -> 1), W2 = I;
+    # layer 3 adds b3 = (2^-9, 0), W3 = I: h3 = (1 + 2^-9, 0), which the output
+    # layer takes unrounded (w4 = (1, 1)).  Unrounded activations give 1 + 2^-8.
+    F, Hd = 2, 2
+    e = 2.0 ** -9
+    theta = np.concatenate([np.array([[1.0, 0.0], [1.0, 0.0]]).ravel(), [0.0, 0.0],
+                            np.eye(2).ravel(), [0.0, 0.0], np.eye(2).ravel(), [e, 0.0], [1.0, 1.0], [0.0]])
+    x = np.array([[1.0, e]])
+    assert M.forward_bf16_operands(theta, x, Hd)[0] == 1.0 + e
+    assert M.forward(theta, x, Hd)[0][0] == 1.0 + 2 * e
+    # an input that bfloat16 does not hold is rounded before the first layer
+    x2 = np.array([[1.0 + e, 0.0]])
+    assert M.forward_bf16_operands(theta, x2, Hd)[0] == 1.0 + e
+
+
+def test_bf16_operand_forward_equals_forward_on_exact_values():
+    # weights in {-1, 0, 1}, integer biases and inputs: every activation is an
+    # integer below 256, which bfloat16 holds, so the rounding changes nothing
+    rng = np.random.default_rng(5)
+    F, Hd = 3, 4
+    sz = M.sizes(F, Hd)
+    parts = []
+    for i, shp in enumerate(sz):
+        if i in (1, 3, 5, 7):
+            parts.append(rng.integers(-2, 3, shp).astype(np.float64).ravel())
+        else:
+            parts.append(rng.integers(-1, 2, shp).astype(np.float64).ravel())
+    theta = np.concatenate(parts)
+    x = rng.integers(-3, 4, (50, F)).astype(np.float64)
+    y, acts = M.forward(theta, x, Hd)
+    assert max(np.abs(a).max() for a in acts) < 256
+    assert np.array_equal(M.forward_bf16_operands(theta, x, Hd), y)
