@@ -140,8 +140,9 @@ typedef struct okr_summary {
     double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration.  Sweep engine:
                                    selection, FP64 recheck, merge, candidate setup, barrier, merge
                                    bookkeeping, list update, offsets, compaction, chunk map, barrier,
-                                   sweep.  Incremental engine: selection, changed set, terms before
-                                   the merge, merge, rebuilt candidates, terms after the merge */
+                                   sweep.  Incremental engine: selection (with the write-back of the
+                                   last merge's new values), changed set, merge, rebuilt candidates,
+                                   the terms that change (before and after the merge, one pass) */
     double kron_ms;             /* device time of the last okr_kron since the reduction (0 if none) */
     int32_t scorer_fallbacks;   /* learned pruning: iterations re-evaluated exhaustively because the
                                    scorer's k candidates were all infeasible */

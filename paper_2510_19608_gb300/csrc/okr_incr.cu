@@ -26,10 +26,11 @@
 // addition is associative, so removing a term's old value and adding its new
 // one gives exactly the sum a fresh evaluation of every term gives, in any
 // order.  The old value is recomputed from the unchanged inputs by the same
-// compiled code (run_entries is not inlined; it holds the one copy of the term
-// arithmetic), so it is bit-identical to the value added earlier.  Counts of terms above the margin are carried the same
-// way.  Engine 3 checks the carried values against a fresh evaluation after
-// every merge.
+// compiled code (the per-state arithmetic, term_arith32 / term_arith64, is not
+// inlined: one copy evaluates every term), so it is bit-identical to the value
+// added earlier.  Counts of terms above the margin are carried the same way.
+// Engine 3 checks the carried values against a fresh evaluation after every
+// merge.
 //
 // Precision 0 carries FP64 terms and selects on them exactly: the minimum m
 // over feasible candidates, the tie band D <= m + tau, the smallest (r, s) key
@@ -44,7 +45,13 @@
 // Execution.  One CTA runs one feeder's whole search; its steps are separated
 // by __syncthreads only (no grid barrier, no device-side wait).  A term is
 // evaluated by a group of lanes, one per (scenario, phase).  A batch runs one
-// CTA per feeder.
+// CTA per feeder.  Each merge takes five steps: selection; the changed set
+// (beside it, the merge's own FP64 evaluation into a scratch, and a map of its
+// positions); the merge's score change and topology; the rebuilt candidates;
+// one pass over the changed terms, which evaluates each term before the merge
+// (the state as stored) and after it (the stored state overlaid with the
+// scratch's new values) in the same lane group and adds the difference.  The
+// new values are written back to the state at the end of that pass.
 #include "okr_internal.cuh"
 #include "okr_kernels.cuh"
 
@@ -219,6 +226,38 @@ __device__ __forceinline__ Red64 block_red64(Red64 v, Red64 *sm) {
     return sm[32];
 }
 
+// Selection reductions of precision 1 in one barrier: each warp reduces with
+// redux.sync (a 64-bit minimum as the minimum of the high words, then of the
+// low words among the lanes that hold it), lane 0 folds the warp's result
+// into the shared accumulator with atomics, one barrier, every thread reads
+// it.  The accumulator must hold the identity (reset_sel) before the first
+// atomic; the caller resets it only after a later barrier.
+__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+    const unsigned hi = (unsigned)(v >> 32);
+    const unsigned mh = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned ml = __reduce_min_sync(0xffffffffu, hi == mh ? (unsigned)v : 0xffffffffu);
+    return ((unsigned long long)mh << 32) | ml;
+}
+__device__ __forceinline__ void reset_sel(Red64 *acc) {
+    acc->a = acc->b = acc->c = ~0ull;
+    acc->i = 0;
+}
+__device__ __forceinline__ Red64 block_sel64(Red64 v, Red64 *acc) {
+    Red64 w;
+    w.a = warp_min64(v.a);
+    w.b = warp_min64(v.b);
+    w.c = warp_min64(v.c);
+    w.i = (int)__reduce_add_sync(0xffffffffu, (unsigned)v.i);
+    if ((threadIdx.x & 31) == 0) {
+        if (w.a != ~0ull) atomicMin(&acc->a, w.a);
+        if (w.b != ~0ull) atomicMin(&acc->b, w.b);
+        if (w.c != ~0ull) atomicMin(&acc->c, w.c);
+        if (w.i) atomicAdd(&acc->i, w.i);
+    }
+    __syncthreads();
+    return *acc;
+}
+
 // Exclusive prefix sum of one int per thread; *total = the block's sum.
 template <int NT>
 __device__ __forceinline__ int block_excl_scan(int v, int *total, int *sm) {
@@ -298,18 +337,144 @@ __device__ int slot_geometry(const Topo &T, const State &S, int n, int w, Cand &
 // A term (candidate c, position k) is evaluated by a group of G = 4 Lp lanes
 // (Lp = scenarios rounded up to a power of two): lane gl takes scenario
 // l = gl / 4 and phase p = gl % 4 (p = 3 idles).  Every lane of the warp calls
-// the group function (it shuffles); `valid` is false for lanes whose group has
-// no term.  The results are the group's sums over its scenarios (every lane
-// holds them).  Every carried term is evaluated inside run_entries, which is
-// not inlined: its one compiled copy of these functions runs for every
-// evaluation of a term, so equal inputs give bit-equal results.
+// the group function (it shuffles); the results are the group's sums over its
+// scenarios (every lane holds them).
+//
+// A group evaluates its term on one or two states, e in [e_lo, e_hi) (the
+// same range for every group of a warp): e = 0, the state as stored; e = 1,
+// the state after the merge in progress, whose new values (voltage,
+// magnitude, extremes, MICE of the merge's positions) are not yet written
+// back and are read through the overlay.  With both, the result is the term
+// on state 1 minus the term on state 0.  v_old / v_new say whether the group
+// has a term on state 0 / 1.  The geometry (the voltage change the candidate
+// causes) is the same on both states and is computed once.  The arithmetic of
+// a term on one state's inputs is a function that is not inlined
+// (term_arith32, term_arith64): every carried term is evaluated by its one
+// compiled copy, so equal inputs give bit-equal results.
+
+// The merge in progress, as the terms after it see it: map[x] = 1 + the index
+// of super-node x among the merge's positions (0: unchanged), whose new values
+// the merge's own evaluation left in cbuf (per position: per (l, p) the new
+// voltage x, y and magnitude; per l the new MICE).  Positions from nfree on
+// are the fixed s (its voltage does not move).  s* takes r*'s extremes.
+struct Ovl {
+    const unsigned short *map;
+    const double *cbuf;
+    int s, r, nfree;
+};
+
+// FP64 state of super-node x, phase p, scenario l on state e (0 stored, 1 overlay).
+__device__ __forceinline__ void at64(const State &S, const Ovl &O, int e, int x, int l, int p, int n, int L,
+                                     bool need_v, double2 *v, double *hh, double *ll) {
+    const size_t ix = sidx(l, p, x, n);
+    const int j = e ? (int)O.map[x] - 1 : -1;
+    double h = S.hi[ix], lo = S.lo[ix];
+    if (j >= 0 && x == O.s) {
+        const size_t irs = sidx(l, p, O.r, n);
+        h = fmax(h, S.hi[irs]);
+        lo = fmin(lo, S.lo[irs]);
+    }
+    *hh = h;
+    *ll = lo;
+    if (need_v) {
+        if (j >= 0 && j < O.nfree) {
+            const double *cb = O.cbuf + (size_t)j * 10 * L + (l * 3 + p) * 3;
+            *v = make_double2(cb[0], cb[1]);
+        } else {
+            *v = S.vcur[ix];
+        }
+    }
+}
+__device__ __forceinline__ double mice64(const State &S, const Ovl &O, int e, int x, int l, int n, int L) {
+    const int j = e ? (int)O.map[x] - 1 : -1;
+    return j >= 0 ? O.cbuf[(size_t)j * 10 * L + 9 * L + l] : S.mice[(size_t)l * n + x];
+}
+
+// FP32 copies (voltage, extremes relative to the magnitude) and the FP64
+// magnitude of super-node x on state e: the values the write-back stores.
+__device__ __forceinline__ void at32(const State &S, const Ovl &O, int e, int x, int l, int p, int n, int L,
+                                     bool need_v, bool need_mc, float2 *v, float *hr, float *lr, double *mc) {
+    const size_t ix = sidx(l, p, x, n);
+    const int j = e ? (int)O.map[x] - 1 : -1;
+    if (j < 0) {
+        *hr = S.hr32[ix];
+        *lr = S.lr32[ix];
+        if (need_v) *v = S.v32[ix];
+        if (need_mc) *mc = S.mcur[ix];
+        return;
+    }
+    const double *cb = O.cbuf + (size_t)j * 10 * L + (l * 3 + p) * 3;
+    const bool fx = j >= O.nfree;
+    const double m = fx ? S.mcur[ix] : cb[2];
+    double h = S.hi[ix], lo = S.lo[ix];
+    if (x == O.s) {
+        const size_t irs = sidx(l, p, O.r, n);
+        h = fmax(h, S.hi[irs]);
+        lo = fmin(lo, S.lo[irs]);
+    }
+    *hr = (float)(h - m);
+    *lr = (float)(lo - m);
+    if (need_v) *v = fx ? S.v32[ix] : make_float2((float)cb[0], (float)cb[1]);
+    *mc = m;
+}
+__device__ __forceinline__ float mice32(const State &S, const Ovl &O, int e, int x, int l, int n, int L) {
+    const int j = e ? (int)O.map[x] - 1 : -1;
+    return j >= 0 ? (float)O.cbuf[(size_t)j * 10 * L + 9 * L + l] : S.mice32[(size_t)l * n + x];
+}
+
+// The arithmetic of one FP64 term on one state's inputs (every lane of the
+// warp calls it: it shuffles).  Not inlined: this one compiled copy evaluates
+// every FP64 term, so equal inputs give bit-equal results wherever it is called.
+struct In64 {
+    double2 v;
+    double h, lo, hr, lr, mo, mr;
+};
+struct Out64 {
+    u128 t;
+    int tv;
+};
+__device__ __noinline__ Out64 term_arith64(In64 x, double2 dv, bool one, bool moves, bool is_s, bool lvp0,
+                                          double margin, double *out, int l, int p, int L) {
+    double em = 0.0;
+    if (one) {
+        double2 v = x.v;
+        if (moves) v = cadd(v, dv);
+        const double mag = cmag(v);
+        double h = x.h, lo = x.lo;
+        if (is_s) {
+            h = fmax(h, x.hr);
+            lo = fmin(lo, x.lr);
+        }
+        em = fmax(h - mag, mag - lo);
+        if (out) {
+            out[(l * 3 + p) * 3 + 0] = v.x;
+            out[(l * 3 + p) * 3 + 1] = v.y;
+            out[(l * 3 + p) * 3 + 2] = mag;
+        }
+    }
+    double m = fmax(em, __shfl_xor_sync(0xffffffffu, em, 1));
+    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    Out64 r;
+    r.t = 0;
+    r.tv = 0;
+    if (lvp0) {
+        if (out) out[9 * L + l] = m;
+        double dd = m - x.mo;
+        if (is_s) dd -= x.mr;
+        r.t = to_fx(dd);
+        r.tv = (m > margin) ? 1 : 0;
+    }
+    return r;
+}
 
 // FP64 term.  d = sum over l of fixed(new MICE - MICE_k [- MICE_r]); nv = scenarios
-// whose new MICE exceeds the margin.  out != nullptr: the new voltage and
-// magnitude per (l, p) and the new MICE per l (the merge).
+// whose new MICE exceeds the margin.  out != nullptr (state 0 only): the new
+// voltage and magnitude per (l, p) and the new MICE per l (the merge).
 __device__ __forceinline__ void group_term64(const Topo &T, const State &S, const uint8_t *ph, int n, int L, int G,
-                                             const Cand &c, int k, bool valid, int gl, double margin, double *out,
-                                             u128 *d_out, int *nv_out) {
+                                             const Cand &c, int k, int e_lo, int e_hi, bool v_old, bool v_new,
+                                             const Ovl &O, int gl, double margin, double *out, u128 *d_out,
+                                             int *nv_out) {
+    const bool valid = v_old || v_new;
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
     const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
@@ -319,63 +484,54 @@ __device__ __forceinline__ void group_term64(const Topo &T, const State &S, cons
     const bool sside = (k >= c.js && k < c.js + c.ns);
     const bool moves = on && !fixed;
     const int li = lv ? l : 0, pi = p < 3 ? p : 0;
-    const size_t ik = sidx(li, pi, k, n), ir = sidx(li, pi, c.r, n);
-    // every load that needs only (c, k, l, p), issued together
-    double2 v = make_double2(0.0, 0.0), iq[3], za[3];
-    double h = 0.0, lo = 0.0, hr = -INFINITY, lr = INFINITY, mo = 0.0, mr = 0.0;
-    int y = 0;
-    if (on) {
-        v = S.vcur[ik];
-        h = S.hi[ik];
-        lo = S.lo[ik];
-        if (is_s) { hr = S.hi[ir]; lr = S.lo[ir]; }
-    }
-    if (lv && p == 0) {
-        mo = S.mice[(size_t)l * n + k];
-        if (is_s) mr = S.mice[(size_t)l * n + c.r];
-    }
+    // the inputs of state e, loaded ahead of the arithmetic that uses them
+    typedef In64 St;
+    auto fetch = [&](int e, St &x) {
+        const bool ve = e == 0 ? v_old : v_new;
+        x.v = make_double2(0.0, 0.0);
+        x.h = x.lo = x.mo = x.mr = 0.0;
+        x.hr = -INFINITY;
+        x.lr = INFINITY;
+        if (on && ve) {
+            at64(S, O, e, k, li, pi, n, L, true, &x.v, &x.h, &x.lo);
+            if (is_s) at64(S, O, e, c.r, li, pi, n, L, false, nullptr, &x.hr, &x.lr);
+        }
+        if (lv && ve && p == 0) {
+            x.mo = mice64(S, O, e, k, l, n, L);
+            if (is_s) x.mr = mice64(S, O, e, c.r, l, n, L);
+        }
+    };
+    St cur;
+    fetch(e_lo, cur);
+    // the voltage change at k (the same on both states)
+    double2 dv = make_double2(0.0, 0.0);
     if (moves) {
-        y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        double2 iq[3], za[3];
         for (int q = 0; q < 3; ++q) {
             iq[q] = (phr >> q & 1u) ? S.icur[sidx(li, q, c.r, n)] : make_double2(0.0, 0.0);
             za[q] = __ldg(T.zc + (size_t)c.a * 9 + pi * 3 + q);
         }
-    }
-    double e = 0.0;
-    if (on) {
-        if (moves) {
-            const double2 *zy = T.zc + (size_t)y * 9 + pi * 3;
-            double2 dv = make_double2(0.0, 0.0);
-            for (int q = 0; q < 3; ++q) {
-                if (!(phr >> q & 1u)) continue;
-                const double2 zyq = __ldg(zy + q);
-                const double2 g = sside ? csub(zyq, za[q]) : csub(za[q], zyq);
-                dv = cadd(dv, cmul(g, iq[q]));
-            }
-            v = cadd(v, dv);
-        }
-        const double mag = cmag(v);
-        if (is_s) {
-            h = fmax(h, hr);
-            lo = fmin(lo, lr);
-        }
-        e = fmax(h - mag, mag - lo);
-        if (out) {
-            out[(l * 3 + p) * 3 + 0] = v.x;
-            out[(l * 3 + p) * 3 + 1] = v.y;
-            out[(l * 3 + p) * 3 + 2] = mag;
+        const double2 *zy = T.zc + (size_t)y * 9 + pi * 3;
+        for (int q = 0; q < 3; ++q) {
+            if (!(phr >> q & 1u)) continue;
+            const double2 zyq = __ldg(zy + q);
+            const double2 g = sside ? csub(zyq, za[q]) : csub(za[q], zyq);
+            dv = cadd(dv, cmul(g, iq[q]));
         }
     }
-    double m = fmax(e, __shfl_xor_sync(0xffffffffu, e, 1));
-    m = fmax(m, __shfl_xor_sync(0xffffffffu, m, 2));
     u128 d = 0;
     int nv = 0;
-    if (lv && p == 0) {
-        if (out) out[9 * L + l] = m;
-        double dd = m - mo;
-        if (is_s) dd -= mr;
-        d = to_fx(dd);
-        nv = (m > margin) ? 1 : 0;
+#pragma unroll 1
+    for (int e = e_lo; e < e_hi; ++e) {
+        const bool ve = e == 0 ? v_old : v_new;
+        const bool one = on && ve;
+        St nxt = cur;
+        if (e + 1 < e_hi) fetch(e + 1, nxt);
+        const Out64 r = term_arith64(cur, dv, one, moves, is_s, lv && ve && p == 0, margin, out, l, p, L);
+        cur = nxt;
+        if (e == 1 || e_hi - e_lo == 1) { d += r.t; nv += r.tv; }
+        else { d -= r.t; nv -= r.tv; }
     }
     for (int o = 4; o < G; o <<= 1) {            // the group's sum over its scenarios
         d += shfl_xor_u128(d, o);
@@ -385,14 +541,78 @@ __device__ __forceinline__ void group_term64(const Topo &T, const State &S, cons
     *nv_out = nv;
 }
 
+// The arithmetic of one FP32 term with its bound on one state's inputs (every
+// lane of the warp calls it: it shuffles).  Not inlined: this one compiled
+// copy evaluates every carried FP32 term, so equal inputs give bit-equal
+// results wherever it is called.
+struct In32 {
+    float hr, lr, hrr, lrr, mo, mr;
+    float2 v;
+    double mck, mcr;
+};
+struct Out32 {
+    u128 td, tb;
+    int ts, tm;
+};
+__device__ __noinline__ Out32 term_arith32(In32 x, float2 dv, float sdv, bool one, bool moves, bool sterm, bool lvp0,
+                                          float margin_lo, float margin_hi) {
+    float em = 0.0f, b = 0.0f;
+    if (one) {
+        float hr = x.hr, lr = x.lr, hrr = x.hrr, lrr = x.lrr;
+        float bx = 0.0f;
+        if (sterm) {
+            const float dr = (float)(x.mcr - x.mck);
+            hrr += dr;
+            lrr += dr;
+            hr = fmaxf(hr, hrr);
+            lr = fminf(lr, lrr);
+            bx = 2.0f * kU32 * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
+        }
+        float delta = 0.0f, bd = 0.0f;
+        if (moves) {
+            const float2 v = x.v;
+            const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
+            const float wx = v.x + dv.x, wy = v.y + dv.y;
+            const float mv = sqrtf(v.x * v.x + v.y * v.y);
+            const float den = sqrtf(wx * wx + wy * wy) + mv;
+            delta = num / den;
+            const float v1 = fabsf(v.x) + fabsf(v.y);
+            bd = kU32 * (40.0f * (v1 + sdv) * sdv / den + 8.0f * fabsf(delta));
+        }
+        em = fmaxf(hr - delta, delta - lr);
+        b = 1.5f * (kU32 * (fabsf(hr) + fabsf(lr) + fabsf(em)) + bd) + bx + 4e-15f;
+    }
+    float m = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, 1));
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    float bm = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, 1));
+    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
+    Out32 r;
+    r.td = r.tb = 0;
+    r.ts = r.tm = 0;
+    if (lvp0) {
+        const float dd = (m - x.mo) - x.mr;
+        // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
+        // factor 1.001 covers the rounding of the bound's own arithmetic
+        const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(x.mo) + fabsf(x.mr) + fabsf(m)));
+        r.td = to_fx32(dd);
+        r.tb = to_fx32(bl) + 3;             // + the truncations of both terms to fixed point
+        r.ts = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
+        r.tm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
+    }
+    return r;
+}
+
 // FP32 term with a rigorous bound (the screen of okr_persist.cu, per item
 // e = max(hr - delta, delta - lr) relative to the cluster's present magnitude).
 // d = sum over l of fixed(D32 term); b = sum over l of a fixed-point bound on
 // |fixed(D32 term) - fixed(D64 term)|; n_sure = scenarios whose new MICE is
-// surely above the margin; n_maybe = scenarios where it may be.
+// surely above the margin; n_maybe = scenarios where it may be.  With two
+// states each is state 1's minus state 0's.
 __device__ __forceinline__ void group_term32(const Topo &T, const State &S, const uint8_t *ph, int n, int L, int G,
-                                             const Cand &c, int k, bool valid, int gl, float margin_lo,
-                                             float margin_hi, u128 *d_out, u128 *b_out, int *ns_out, int *nm_out) {
+                                             const Cand &c, int k, int e_lo, int e_hi, bool v_old, bool v_new,
+                                             const Ovl &O, int gl, float margin_lo, float margin_hi, u128 *d_out,
+                                             u128 *b_out, int *ns_out, int *nm_out) {
+    const bool valid = v_old || v_new;
     const int l = gl >> 2, p = gl & 3;
     const bool lv = valid && l < L;
     const unsigned phk = valid ? ph[k] : 0u, phr = valid ? ph[c.r] : 0u;
@@ -403,79 +623,60 @@ __device__ __forceinline__ void group_term32(const Topo &T, const State &S, cons
     const bool sterm = on && is_s && (phr >> p & 1u);
     const bool moves = on && !fixed;
     const int li = lv ? l : 0, pi = p < 3 ? p : 0;
-    const size_t ik = sidx(li, pi, k, n), ir = sidx(li, pi, c.r, n);
-    // every load that needs only (c, k, l, p), issued together
-    float hr = 0.0f, lr = 0.0f, hrr = 0.0f, lrr = 0.0f, mo = 0.0f, mr = 0.0f;
-    double mcr = 0.0, mck = 0.0;
-    float2 v = make_float2(0.0f, 0.0f), iq[3], ha[3], la[3];
-    int y = 0;
-    if (on) { hr = S.hr32[ik]; lr = S.lr32[ik]; }
-    if (sterm) { mcr = S.mcur[ir]; mck = S.mcur[ik]; hrr = S.hr32[ir]; lrr = S.lr32[ir]; }
-    if (lv && p == 0) {
-        mo = S.mice32[(size_t)l * n + k];
-        if (is_s) mr = S.mice32[(size_t)l * n + c.r];
-    }
+    // the inputs of state e, loaded ahead of the arithmetic that uses them
+    typedef In32 St;
+    auto fetch = [&](int e, St &x) {
+        const bool ve = e == 0 ? v_old : v_new;
+        x.hr = x.lr = x.hrr = x.lrr = x.mo = x.mr = 0.0f;
+        x.v = make_float2(0.0f, 0.0f);
+        x.mck = x.mcr = 0.0;
+        if (on && ve) at32(S, O, e, k, li, pi, n, L, moves, sterm, &x.v, &x.hr, &x.lr, &x.mck);
+        if (on && ve && sterm) {
+            float2 vr;
+            at32(S, O, e, c.r, li, pi, n, L, false, true, &vr, &x.hrr, &x.lrr, &x.mcr);
+        }
+        if (lv && ve && p == 0) {
+            x.mo = mice32(S, O, e, k, l, n, L);
+            if (is_s) x.mr = mice32(S, O, e, c.r, l, n, L);
+        }
+    };
+    St cur;
+    fetch(e_lo, cur);
+    // the voltage change at k (the same on both states)
+    float2 dv = make_float2(0.0f, 0.0f);
+    float sdv = 0.0f;
     if (moves) {
-        v = S.v32[ik];
-        y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        const int y = __ldg(T.lca + (size_t)(sside ? c.s : c.r) * n + k);
+        float2 iq[3], ha[3], la[3];
         for (int q = 0; q < 3; ++q) {
             iq[q] = (phr >> q & 1u) ? S.icur32[sidx(li, q, c.r, n)] : make_float2(0.0f, 0.0f);
             ha[q] = __ldg(T.zh + (size_t)c.a * 9 + pi * 3 + q);
             la[q] = __ldg(T.zlo + (size_t)c.a * 9 + pi * 3 + q);
         }
-    }
-    float e = 0.0f, b = 0.0f;
-    if (on) {
-        float bx = 0.0f;
-        if (sterm) {
-            const float dr = (float)(mcr - mck);
-            hrr += dr;
-            lrr += dr;
-            hr = fmaxf(hr, hrr);
-            lr = fminf(lr, lrr);
-            bx = 2.0f * kU32 * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
+        const float2 *zhy = T.zh + (size_t)y * 9 + pi * 3, *zly = T.zlo + (size_t)y * 9 + pi * 3;
+        for (int q = 0; q < 3; ++q) {
+            if (!(phr >> q & 1u)) continue;
+            const float2 hy = __ldg(zhy + q), ly = __ldg(zly + q);
+            float gx = (hy.x - ha[q].x) + (ly.x - la[q].x);
+            float gy = (hy.y - ha[q].y) + (ly.y - la[q].y);
+            if (!sside) { gx = -gx; gy = -gy; }
+            dv.x = fmaf(gx, iq[q].x, fmaf(-gy, iq[q].y, dv.x));
+            dv.y = fmaf(gx, iq[q].y, fmaf(gy, iq[q].x, dv.y));
+            sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(iq[q].x) + fabsf(iq[q].y), sdv);
         }
-        float delta = 0.0f, bd = 0.0f;
-        if (moves) {
-            const float2 *zhy = T.zh + (size_t)y * 9 + pi * 3, *zly = T.zlo + (size_t)y * 9 + pi * 3;
-            float2 dv = make_float2(0.0f, 0.0f);
-            float sdv = 0.0f;
-            for (int q = 0; q < 3; ++q) {
-                if (!(phr >> q & 1u)) continue;
-                const float2 hy = __ldg(zhy + q), ly = __ldg(zly + q);
-                float gx = (hy.x - ha[q].x) + (ly.x - la[q].x);
-                float gy = (hy.y - ha[q].y) + (ly.y - la[q].y);
-                if (!sside) { gx = -gx; gy = -gy; }
-                dv.x = fmaf(gx, iq[q].x, fmaf(-gy, iq[q].y, dv.x));
-                dv.y = fmaf(gx, iq[q].y, fmaf(gy, iq[q].x, dv.y));
-                sdv = fmaf(fabsf(gx) + fabsf(gy), fabsf(iq[q].x) + fabsf(iq[q].y), sdv);
-            }
-            const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
-            const float wx = v.x + dv.x, wy = v.y + dv.y;
-            const float mv = sqrtf(v.x * v.x + v.y * v.y);
-            const float den = sqrtf(wx * wx + wy * wy) + mv;
-            delta = num / den;
-            const float v1 = fabsf(v.x) + fabsf(v.y);
-            bd = kU32 * (40.0f * (v1 + sdv) * sdv / den + 8.0f * fabsf(delta));
-        }
-        e = fmaxf(hr - delta, delta - lr);
-        b = 1.5f * (kU32 * (fabsf(hr) + fabsf(lr) + fabsf(e)) + bd) + bx + 4e-15f;
     }
-    float m = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, 1));
-    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-    float bm = fmaxf(b, __shfl_xor_sync(0xffffffffu, b, 1));
-    bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, 2));
     u128 d = 0, bb = 0;
     int ns = 0, nm = 0;
-    if (lv && p == 0) {
-        const float dd = (m - mo) - mr;
-        // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
-        // factor 1.001 covers the rounding of the bound's own arithmetic
-        const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(mo) + fabsf(mr) + fabsf(m)));
-        d = to_fx32(dd);
-        bb = to_fx32(bl) + 3;            // + the truncations of both terms to fixed point
-        ns = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
-        nm = (__fadd_ru(m, bm) > margin_lo) ? 1 : 0;
+#pragma unroll 1
+    for (int e = e_lo; e < e_hi; ++e) {
+        const bool ve = e == 0 ? v_old : v_new;
+        const bool one = on && ve;
+        St nxt = cur;
+        if (e + 1 < e_hi) fetch(e + 1, nxt);
+        const Out32 r = term_arith32(cur, dv, sdv, one, moves, sterm, lv && ve && p == 0, margin_lo, margin_hi);
+        cur = nxt;
+        if (e == 1 || e_hi - e_lo == 1) { d += r.td; bb += r.tb; ns += r.ts; nm += r.tm; }
+        else { d -= r.td; bb -= r.tb; ns -= r.ts; nm -= r.tm; }
     }
     for (int o = 4; o < G; o <<= 1) {            // the group's sums over its scenarios
         d += shfl_xor_u128(d, o);
@@ -597,10 +798,10 @@ struct Loc {
 
 // ---------------------------------------------------------------- evaluation of work entries
 enum Pass {
-    kOld = 0,       // carried terms on the state before the merge: subtracted
-    kNew = 1,       // carried terms on the state after it: added (mode 0) or set (mode 1)
-    kFresh = 2,     // carried precision, every term of the entries, into vacc / vviol
-    kF64 = 3        // FP64, every term of the entries, into vacc / vviol
+    kMerge = 0,     // after a merge: mode 0 adds (term after - term before), mode 1 sets every term after
+    kInit = 1,      // the stored state, every term of the entries, set
+    kFresh = 2,     // carried precision, every term after the merge in progress, into vacc / vviol
+    kF64 = 3        // FP64, every term on the stored state, into vacc / vviol
 };
 
 struct EvalSmem {
@@ -683,6 +884,8 @@ struct Commit {
     Cand wc;
     const unsigned short *list;     // super-nodes before the merge
     const uint8_t *ph;
+    Ovl O;                          // (not read: state 0)
+    unsigned short *map;            // the overlay map, filled here
 };
 
 // Run by warps [warp0, warp0 + nw) only.
@@ -704,23 +907,31 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
         }
         u128 d;
         int nv;
-        group_term64(T, S, cm.ph, n, L, G, cm.wc, k, valid, gl, margin,
+        group_term64(T, S, cm.ph, n, L, G, cm.wc, k, 0, 1, valid, false, cm.O, gl, margin,
                      valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d, &nv);
-        if (valid && gl == 0) items += __popc(cm.ph[k]) * L;
+        if (valid && gl == 0) {
+            items += __popc(cm.ph[k]) * L;
+            cm.map[k] = (unsigned short)(q + 1);     // the terms after the merge read k's new values here
+        }
     }
     return items;
 }
 
 // Evaluates the terms of work entries [e0, e1) (tiles of NT entries) and applies
-// them per the pass.  Mode-0 entries take positions from list_pre (and skip r*
-// after the merge), mode-1 entries from list_post; kFresh / kF64 use list_pre.
-// Returns the number of terms evaluated.
+// them per the pass (without the barrier after the last tile's updates when
+// !last_barrier).  kMerge: mode-0 entries take positions from list_pre and
+// add, per term, its value after the merge (r* has none) minus its value before;
+// mode-1 entries take positions from list_post and set every term after the
+// merge.  kInit / kFresh / kF64: every term of the entries, positions from
+// list_pre.  Returns the number of terms evaluated.
 template <int NT, int PREC>
 __device__ __noinline__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
                                  double margin, float mlo, float mhi, int e0, int e1, int pass,
                                  const unsigned short *list_pre, const unsigned short *list_post, int rstar,
-                                 EvalSmem &E, int *sscan, const Rec &R, const Loc &Lc,
-                                 unsigned long long *prof = nullptr) {
+                                 const Ovl O, EvalSmem &E, int *sscan, const Rec &R, const Loc &Lc,
+                                 unsigned long long *prof = nullptr, bool last_barrier = true) {
+    // the states every group evaluates (the same for the whole pass)
+    const int st_lo = (pass == kFresh) ? 1 : 0, st_hi = (pass == kMerge || pass == kFresh) ? 2 : 1;
     const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G;
     long long terms = 0;
     unsigned long long tq = (prof && tid == 0) ? gtimer_inc() : 0;
@@ -748,7 +959,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
         for (int r0 = 0; r0 < tot; r0 += NG) {
             if (r0 + (tid >> 5) * (32 / G) >= tot) break;     // this warp's groups are all past the end
             const int q = r0 + gi;
-            bool valid = q < tot;
+            bool valid = q < tot, v_old = false, v_new = false;
             int ei = 0, k = 0;
             Cand c;
             c.s = c.r = c.a = c.js = c.ns = c.jr = c.nr = c.fixed = 0;
@@ -774,17 +985,27 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
                     if (rem < len) { j = w.seg[i].x + rem; break; }
                     rem -= len;
                 }
-                k = ((pass == kNew && w.mode == 1) ? list_post : list_pre)[j];
+                k = ((pass == kMerge && w.mode == 1) ? list_post : list_pre)[j];
                 c = entry_cand(w);
-                if (k == c.r || (pass == kNew && w.mode == 0 && k == rstar)) valid = false;
+                if (k == c.r) valid = false;
+                if (pass == kMerge) {
+                    v_old = valid && w.mode == 0;
+                    v_new = valid && !(w.mode == 0 && k == rstar);
+                } else {
+                    v_old = v_new = valid;
+                }
+                valid = v_old || v_new;
             }
-            if (valid && gl == 0) terms += __popc(Lc.ph[k]) * L;      // (phase-node, scenario) items
+            if (gl == 0) {                                            // (phase-node, scenario) items
+                const int it = (st_lo == 0 && v_old ? 1 : 0) + (st_hi == 2 && v_new ? 1 : 0);
+                if (it) terms += it * __popc(Lc.ph[k]) * L;
+            }
             const unsigned long long c0 = (prof && tid == 0) ? clock64() : 0;
             if (prof && tid == 0) prof[3] += c0 - cq;
             if (PREC == 0 || pass == kF64) {
                 u128 d;
                 int nv;
-                group_term64(T, S, Lc.ph, n, L, G, c, k, valid, gl, margin, nullptr, &d, &nv);
+                group_term64(T, S, Lc.ph, n, L, G, c, k, st_lo, st_hi, v_old, v_new, O, gl, margin, nullptr, &d, &nv);
                 if (valid && gl == 0) {
                     sadd128(&E.dlo[ei], &E.dhi[ei], d);
                     if (nv) atomicAdd(&E.n1[ei], nv);
@@ -792,7 +1013,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
             } else {
                 u128 d, b;
                 int ns, nm;
-                group_term32(T, S, Lc.ph, n, L, G, c, k, valid, gl, mlo, mhi, &d, &b, &ns, &nm);
+                group_term32(T, S, Lc.ph, n, L, G, c, k, st_lo, st_hi, v_old, v_new, O, gl, mlo, mhi, &d, &b, &ns, &nm);
                 if (valid && gl == 0) {
                     sadd128(&E.dlo[ei], &E.dhi[ei], d);
                     sadd128(&E.blo[ei], &E.bhi[ei], b);
@@ -810,21 +1031,17 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
             const u128 d = ((u128)E.dhi[tid] << 64) | (u128)E.dlo[tid];
             const u128 b = ((u128)E.bhi[tid] << 64) | (u128)E.blo[tid];
             unsigned long long *a = I.acc + 2 * (size_t)sl, *bp = I.bnd + 2 * (size_t)sl;
-            if (pass == kOld || pass == kNew) {
+            if (pass == kMerge || pass == kInit) {
                 u128 na, nb = 0;
                 int nv, nm = 0;
-                if (pass == kNew && w.mode == 1) {
+                if (w.mode == 1) {
                     na = d;
                     nv = E.n1[tid];
                     if (PREC == 1) { nb = b; nm = E.n2[tid]; }
-                } else if (pass == kNew) {
+                } else {
                     na = ld128(a) + d;
                     nv = I.viol[sl] + E.n1[tid];
                     if (PREC == 1) { nb = ld128(bp) + b; nm = I.vmay[sl] + E.n2[tid]; }
-                } else {
-                    na = ld128(a) - d;
-                    nv = I.viol[sl] - E.n1[tid];
-                    if (PREC == 1) { nb = ld128(bp) - b; nm = I.vmay[sl] - E.n2[tid]; }
                 }
                 st128(a, na);
                 I.viol[sl] = nv;
@@ -838,7 +1055,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
                 I.vviol[sl] = E.n1[tid];
             }
         }
-        __syncthreads();
+        if (last_barrier || t0 + NT < e1) __syncthreads();    // else the caller synchronises
         sub(2);
     }
     return terms;
@@ -886,23 +1103,76 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
 
 }  // namespace
 
+// Writes the merge hw's new values from its scratch into the state (the
+// values the overlay gave the terms after it: FP64 voltage, magnitude, MICE,
+// s*'s merged extremes, and their FP32 copies), clears its overlay map, and
+// zeroes r*'s MICE.  `list`: the super-nodes before that merge.
+template <int NT>
+__device__ void write_back(const State &S, const Inc &I, const Win &hw, const unsigned short *list, const uint8_t *ph,
+                           unsigned short *map, int n, int L, int G) {
+    const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G, l = gl >> 2, p = gl & 3;
+    const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
+    for (int j = gi; j < hw.npos; j += NG) {
+        const int k = j < n1 ? list[hw.q1lo + j] : (j < n1 + n2 ? list[hw.q2lo + j - n1] : hw.s);
+        if (k == hw.r) continue;
+        const bool fx = j >= n1 + n2;
+        const double *cb = I.cbuf + (size_t)j * 10 * L;
+        if (l < L && p < 3 && (ph[k] >> p & 1u)) {
+            const size_t ik = sidx(l, p, k, n);
+            double mc;
+            if (!fx) {
+                const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
+                mc = cb[(l * 3 + p) * 3 + 2];
+                S.vcur[ik] = v;
+                S.mcur[ik] = mc;
+                S.v32[ik] = make_float2((float)v.x, (float)v.y);
+            } else {
+                mc = S.mcur[ik];
+            }
+            double hh = S.hi[ik], ll = S.lo[ik];
+            if (k == hw.s) {
+                const size_t ir = sidx(l, p, hw.r, n);
+                hh = fmax(hh, S.hi[ir]);
+                ll = fmin(ll, S.lo[ir]);
+                S.hi[ik] = hh;
+                S.lo[ik] = ll;
+            }
+            S.hr32[ik] = (float)(hh - mc);
+            S.lr32[ik] = (float)(ll - mc);
+        }
+        if (l < L && p == 0) {
+            const double m = cb[9 * L + l];
+            S.mice[(size_t)l * n + k] = m;
+            S.mice32[(size_t)l * n + k] = (float)m;
+        }
+        if (gl == 0) map[k] = 0;
+    }
+    if (tid < L) {                          // r's cluster is gone
+        S.mice[(size_t)tid * n + hw.r] = 0.0;
+        S.mice32[(size_t)tid * n + hw.r] = 0.0f;
+    }
+}
+
 // ---------------------------------------------------------------- the search
 // Bytes of the selection records of an n-bus feeder.
 __host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)48 * n + 64; }
+// ... and with the per-super-node largest MICE after them (shared memory only).
+__host__ __device__ constexpr size_t rec_maxm_bytes(int n) { return rec_bytes(n) + (size_t)8 * n; }
 
 // Shared memory of one search: [work entries][two super-node lists][phase
 // masks], then the selection records when they fit.
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t base_bytes(int n) {
-    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n);
+    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n);
 }
 
 template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
-                        unsigned char *dyn, bool rec_in_smem) {
+                        unsigned char *dyn, int rec_mode) {
     static_assert(NT >= 128 && NT <= kTE, "thread count");
     __shared__ __align__(16) EvalSmem E;
     __shared__ __align__(16) Red sred[33];
+    __shared__ __align__(16) Red64 s_sel[2];   // precision-1 selection accumulators: pass A, pass B
     __shared__ int sscan[33];
     __shared__ Win h;
     __shared__ unsigned long long s_sfx[2];     // SMICE of the committed state, fixed point
@@ -925,17 +1195,25 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     Lc.lst[1] = Lc.lst[0] + n;
     uint8_t *phs = dyn + (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n);
     Lc.ph = phs;
-    unsigned char *recmem = rec_in_smem ? dyn + base_bytes(n) : I.recbuf;
+    unsigned short *ovl_map = reinterpret_cast<unsigned short *>(phs + align16((size_t)n));
+    Ovl O;
+    O.map = ovl_map;
+    O.cbuf = I.cbuf;
+    O.s = O.r = -1;
+    O.nfree = 0;
+    unsigned char *recmem = rec_mode ? dyn + base_bytes(n) : I.recbuf;
     Rec R;
     R.r0 = reinterpret_cast<u128 *>(recmem);
     R.r1 = reinterpret_cast<ulonglong2 *>(recmem);
     R.tkey = reinterpret_cast<unsigned *>(recmem + (size_t)32 * n);
-    R.maxm = I.maxm;
+    R.maxm = rec_mode == 2 ? reinterpret_cast<double *>(recmem + rec_bytes(n)) : I.maxm;
     R.span = reinterpret_cast<ushort4 *>(recmem + (size_t)40 * n);
     int t = 0, ns = n;
     if (tid == 0) {
         s_sfx[0] = s_sfx[1] = 0ull;                 // every MICE starts at 0
         s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+        reset_sel(&s_sel[0]);
+        reset_sel(&s_sel[1]);
     }
     unsigned long long tp = 0;
     auto stamp = [&](int i) {
@@ -951,14 +1229,15 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         R.maxm[w] = 0.0;
         Lc.lst[0][w] = (unsigned short)w;
         phs[w] = __ldg(T.ph + w);
+        ovl_map[w] = 0;
     }
     __syncthreads();
     rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R, Lc);
     __syncthreads();
     {
         const int ne = s_cnt[2];
-        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kNew, Lc.lst[0], Lc.lst[0],
-                                       -1, E, sscan, R, Lc);
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kInit, Lc.lst[0], Lc.lst[0],
+                                       -1, O, E, sscan, R, Lc);
     }
     if (prof && tid == 0) tp = gtimer_inc();
 
@@ -998,7 +1277,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 r6.a = q.x < r6.a ? q.x : r6.a;
                 r6.b = q.y < r6.b ? q.y : r6.b;
             }
-            r6 = block_red64<NT>(r6, reinterpret_cast<Red64 *>(sred));
+            r6 = block_sel64(r6, &s_sel[0]);
             ra.a = r6.a == kKeyNone ? kNone : (u128)r6.a;
             ra.b = r6.b == kKeyNone ? kNone : (u128)r6.b;
             ra.c = r6.c == ~0ull ? kNone : ~(u128)(~r6.c);
@@ -1080,7 +1359,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 }
                 if (out_sure) r6.c = q.x < r6.c ? q.x : r6.c;
             }
-            r6 = block_red64<NT>(r6, reinterpret_cast<Red64 *>(sred));
+            r6 = block_sel64(r6, &s_sel[1]);
             Red rb;
             rb.a = r6.a == ~0ull ? kNone : (u128)r6.a;
             rb.b = r6.b == ~0ull ? kNone : (u128)r6.b;
@@ -1111,7 +1390,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 __syncthreads();
                 const int nR = s_cnt[3];
                 terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, nR, kF64, list_old, list_old,
-                                               -1, E, sscan, R, Lc);
+                                               -1, O, E, sscan, R, Lc);
                 // exact selection over R, with the surely-in candidate of key ks
                 Red rc;
                 rc.a = rc.b = rc.c = kNone;
@@ -1168,9 +1447,17 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         __syncthreads();
         const Win hw = h;
+        if (PREC == 1 && tid == 0) {                 // every thread has read both selection results
+            reset_sel(&s_sel[0]);
+            reset_sel(&s_sel[1]);
+        }
+        O.s = hw.s;
+        O.r = hw.r;
+        O.nfree = (hw.q1hi - hw.q1lo) + (hw.q2hi - hw.q2lo);
         // ---- which candidates change: rebuilt pairs (next to s* or r*) and
         // changed terms; entries are appended in any order (the sums are exact).
-        // The last warps evaluate the merge's own FP64 values meanwhile.
+        // The last warps evaluate the merge's own FP64 values meanwhile and
+        // map its positions for the overlay.
         {
             constexpr int NW = NT / 32, CW = 4;
             if ((tid >> 5) >= NW - CW) {
@@ -1179,6 +1466,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 cm.wc = X.slot[ws];
                 cm.list = list_old;
                 cm.ph = Lc.ph;
+                cm.O = O;
+                cm.map = ovl_map;
                 terms += commit_groups(T, S, I, n, L, G, margin, cm, NW - CW, CW);
             } else {
                 // the changed buses lie in [hl, hh): a candidate whose span misses it is unchanged
@@ -1208,17 +1497,14 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         const int nf_tot = s_cnt[0], np_tot = s_cnt[1];
         if (tid == 0) s_cnt[2] = np_tot;                // rebuilt entries follow the changed ones
         stamp(1);
-        // ============================================================ terms before the merge
-        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, np_tot, kOld, list_old, list_new,
-                                       hw.r, E, sscan, R, Lc, prof ? C->phase_ns + 6 : nullptr);
-        __syncthreads();
-        stamp(2);
-        // ============================================================ the merge (FP64, then the FP32 copies)
+        // ============================================================ the merge: score change and topology
+        // (the new voltages, extremes and MICE stay in the scratch, read through
+        // the overlay, until the terms before the merge have been evaluated)
         {
             const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
             const int gl = tid % G, gi = tid / G, NG = NT / G, l = gl >> 2, p = gl & 3;
             u128 dsum = 0;
-            // one lane per (position, scenario, phase)
+            // one lane per (position, scenario)
             for (int r0 = 0; r0 < hw.npos; r0 += NG) {
                 if (r0 + (tid >> 5) * (32 / G) >= hw.npos) break;
                 const int j = r0 + gi;
@@ -1228,40 +1514,13 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : hw.s);
                     valid = k != hw.r;
                 }
-                const bool fx = j >= n1 + n2;
-                const double *cb = I.cbuf + (size_t)j * 10 * L;
-                if (valid && l < L && p < 3 && (Lc.ph[k] >> p & 1u)) {
-                    const size_t ik = sidx(l, p, k, n);
-                    double mc;
-                    if (!fx) {
-                        const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
-                        mc = cb[(l * 3 + p) * 3 + 2];
-                        S.vcur[ik] = v;
-                        S.mcur[ik] = mc;
-                        S.v32[ik] = make_float2((float)v.x, (float)v.y);
-                    } else {
-                        mc = S.mcur[ik];
-                    }
-                    double hh = S.hi[ik], ll = S.lo[ik];
-                    if (k == hw.s) {
-                        const size_t ir = sidx(l, p, hw.r, n);
-                        hh = fmax(hh, S.hi[ir]);
-                        ll = fmin(ll, S.lo[ir]);
-                        S.hi[ik] = hh;
-                        S.lo[ik] = ll;
-                    }
-                    S.hr32[ik] = (float)(hh - mc);
-                    S.lr32[ik] = (float)(ll - mc);
-                }
                 // the merge's exact score change: its FP64 terms in fixed point
                 unsigned long long mb = 0;                  // MICE >= 0: bit patterns order like values
                 if (valid && l < L && p == 0) {
-                    const double m = cb[9 * L + l];
+                    const double m = I.cbuf[(size_t)j * 10 * L + 9 * L + l];
                     double dd = m - S.mice[(size_t)l * n + k];
                     if (k == hw.s) dd -= S.mice[(size_t)l * n + hw.r];
                     dsum += to_fx(dd);
-                    S.mice[(size_t)l * n + k] = m;
-                    S.mice32[(size_t)l * n + k] = (float)m;
                     mb = (unsigned long long)__double_as_longlong(m);
                 }
                 for (int o = 4; o < G; o <<= 1) {
@@ -1276,7 +1535,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 if (S.label[b] == hw.r) S.label[b] = hw.s;
             for (int b = hw.r + 1 + tid; b <= n; b += NT) S.sn_rank[b] -= 1;
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
-            // s takes r's injection
+            // s takes r's injection (no term before the merge reads s's injection:
+            // every candidate with r = s* is rebuilt)
             const unsigned phr = Lc.ph[hw.r];
             if (tid < 3 * L) {
                 const int l = tid / 3, q = tid % 3;
@@ -1293,6 +1553,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     S.ptop[hw.s] = S.ptop[hw.r];
                 }
                 I.qpar[hw.r] = -1;
+                R.maxm[hw.r] = 0.0;
             }
             if (tid < 2) {
                 X.slot[2 * hw.r + tid].s = -1;
@@ -1303,14 +1564,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         __syncthreads();
         ns -= 1;
-        stamp(3);
-        // ============================================================ terms after the merge
-        if (tid < L) {                                   // r's cluster is gone (its MICE was read by the merge)
-            S.mice[(size_t)tid * n + hw.r] = 0.0;
-            S.mice32[(size_t)tid * n + hw.r] = 0.0f;
-        }
+        stamp(2);
+        // ============================================================ rebuilt candidates
         if (tid == 0) {
-            R.maxm[hw.r] = 0.0;
             const u128 sfx = ld128(s_sfx) + ld128(s_dsum);
             st128(s_sfx, sfx);
             X.dec_score[t] = fx_to_d(sfx);
@@ -1318,14 +1574,20 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], R, Lc);
         __syncthreads();
         const int ne_new = s_cnt[2];
+        stamp(3);
+        // ============================================================ the terms that change
+        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne_new, kMerge, list_old, list_new, hw.r,
+                                       O, E, sscan, R, Lc, prof ? C->phase_ns + 6 : nullptr, false);
+        // the new values into the state (no term reads the state before the
+        // merge any more; this overlaps the last tile's updates of the sums)
+        write_back<NT>(S, I, hw, list_old, Lc.ph, ovl_map, n, L, G);
+        __syncthreads();
         stamp(4);
-        terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne_new, kNew, list_old, list_new, hw.r,
-                                       E, sscan, R, Lc, prof ? C->phase_ns + 11 : nullptr);
-        stamp(5);
         t += 1;
         maxerr_done = false;
         if (verify) {
-            // every candidate again from scratch; the carried values must match bit for bit
+            // every candidate again from scratch (after the merge, through the
+            // overlay); the carried values must match bit for bit
             if (tid == 0) s_cnt[3] = 0;
             __syncthreads();
             for (int c = tid; c < 2 * n; c += NT) {
@@ -1337,7 +1599,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
             __syncthreads();
             run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, s_cnt[3], kFresh, list_new, list_new, -1,
-                                  E, sscan, R, Lc);
+                                  O, E, sscan, R, Lc);
             int bad = 0;
             for (int c = tid; c < 2 * n; c += NT) {
                 if (X.slot[c].s < 0) continue;
@@ -1374,19 +1636,20 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     }
 }
 
-// Per-merge data in dynamic shared memory; the selection records too when
-// rec_smem, else in I.recbuf.
+// Per-merge data in dynamic shared memory; rec_mode 0: the selection records
+// in I.recbuf; 1: in shared memory; 2: in shared memory, with the largest MICE
+// per super-node.
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
-                                                      int rec_smem) {
+                                                      int rec_mode) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
-    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_smem != 0);
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode);
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf,
-                                                         int rec_smem) {
+                                                         int rec_mode) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
     __shared__ Topo sT;
     __shared__ State sS;
@@ -1404,7 +1667,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_smem != 0);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -1423,16 +1686,21 @@ cudaError_t set_smem(K kern, size_t bytes) {
 }
 
 // Dynamic shared memory for an n-bus feeder: the per-merge data always, the
-// selection records when the total stays within kIncSmemMax.
-static size_t inc_smem(int n, int *rec_smem) {
-    const size_t base = base_bytes(n), all = base + rec_bytes(n);
-    *rec_smem = all <= kIncSmemMax ? 1 : 0;
-    return *rec_smem ? all : base;
+// selection records (and, when `maxm`, the largest MICE per super-node) when
+// the total stays within kIncSmemMax.  *rec_mode as k_search_inc takes it.
+static size_t inc_smem(int n, bool maxm, int *rec_mode) {
+    const size_t base = base_bytes(n);
+    if (maxm && base + rec_maxm_bytes(n) <= kIncSmemMax) {
+        *rec_mode = 2;
+        return base + rec_maxm_bytes(n);
+    }
+    *rec_mode = base + rec_bytes(n) <= kIncSmemMax ? 1 : 0;
+    return *rec_mode ? base + rec_bytes(n) : base;
 }
 
 cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
     int use = 0;
-    const size_t smem = inc_smem(T.n, &use);
+    const size_t smem = inc_smem(T.n, true, &use);
     cudaError_t e;
     if (precision == 1) {
         e = set_smem(k_search_inc<kIncThreads, 1>, smem);
@@ -1446,7 +1714,7 @@ cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, C
 
 cudaError_t prepare_search_inc_batch(int precision, int max_n) {
     int use = 0;
-    const size_t smem = inc_smem(max_n, &use);
+    const size_t smem = inc_smem(max_n, false, &use);
     return precision == 1 ? set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem)
                           : set_smem(k_search_inc_batch<kIncBatchThreads, 0>, smem);
 }
@@ -1455,7 +1723,7 @@ cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder 
                                     cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
     int use = 0;
-    const size_t smem = inc_smem(max_n, &use);
+    const size_t smem = inc_smem(max_n, false, &use);
     if (precision == 1) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
     else k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
     return cudaGetLastError();
