@@ -793,6 +793,7 @@ struct Loc {
     IncWork *wsm, *wgl;
     unsigned short *lst[2];
     const uint8_t *ph;
+    int *rank;                  // [n + 1] rank of each bus's super-node among the super-nodes
     __device__ __forceinline__ IncWork *ent(int i) const { return i < kSE ? wsm + i : wgl + (i - kSE); }
 };
 
@@ -1089,7 +1090,7 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
             X.slot[sl] = c[d];
             if (c[d].s >= 0) {
                 int2 seg[kIncMaxSeg];
-                const int ns = full_segments(c[d], S.sn_rank, seg);
+                const int ns = full_segments(c[d], Lc.rank, seg);
                 write_entry(Lc.ent(atomicAdd(cnt, 1)), sl, 1, ns, seg, c[d]);
                 R.tkey[sl] = (unsigned)c[d].key;
             } else {
@@ -1160,10 +1161,12 @@ __host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)48 * n + 
 __host__ __device__ constexpr size_t rec_maxm_bytes(int n) { return rec_bytes(n) + (size_t)8 * n; }
 
 // Shared memory of one search: [work entries][two super-node lists][phase
-// masks], then the selection records when they fit.
+// masks][overlay map][super-node ranks], then the selection records when they
+// fit.
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
 __host__ __device__ constexpr size_t base_bytes(int n) {
-    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n);
+    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n) +
+           align16((size_t)4 * (n + 1));
 }
 
 template <int NT, int PREC>
@@ -1196,6 +1199,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     uint8_t *phs = dyn + (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n);
     Lc.ph = phs;
     unsigned short *ovl_map = reinterpret_cast<unsigned short *>(phs + align16((size_t)n));
+    // the super-node ranks live in shared memory during the search (copied back at the end)
+    int *rank = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(ovl_map) + align16((size_t)2 * n));
+    Lc.rank = rank;
     Ovl O;
     O.map = ovl_map;
     O.cbuf = I.cbuf;
@@ -1230,7 +1236,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         Lc.lst[0][w] = (unsigned short)w;
         phs[w] = __ldg(T.ph + w);
         ovl_map[w] = 0;
+        rank[w] = S.sn_rank[w];
     }
+    if (tid == 0) rank[n] = S.sn_rank[n];
     __syncthreads();
     rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R, Lc);
     __syncthreads();
@@ -1383,7 +1391,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         const int o = atomicAdd(&s_cnt[3], 1);
                         I.rlist[o] = c;
                         int2 seg[kIncMaxSeg];
-                        const int k = full_segments(X.slot[c], S.sn_rank, seg);
+                        const int k = full_segments(X.slot[c], rank, seg);
                         write_entry(Lc.ent(o), c, 1, k, seg, X.slot[c]);
                     }
                 }
@@ -1433,11 +1441,11 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             h.w1lo = w.js; h.w1hi = w.js + w.ns; h.w2lo = w.jr; h.w2hi = w.jr + w.nr;
             h.rtop = S.top[w.r];
             h.rtop_end = h.rtop + T.sz[h.rtop];
-            h.jr = S.sn_rank[w.r];
-            h.q1lo = w.ns > 0 ? S.sn_rank[w.js] : 0;
-            h.q1hi = w.ns > 0 ? S.sn_rank[w.js + w.ns] : 0;
-            h.q2lo = w.nr > 0 ? S.sn_rank[w.jr] : 0;
-            h.q2hi = w.nr > 0 ? S.sn_rank[w.jr + w.nr] : 0;
+            h.jr = rank[w.r];
+            h.q1lo = w.ns > 0 ? rank[w.js] : 0;
+            h.q1hi = w.ns > 0 ? rank[w.js + w.ns] : 0;
+            h.q2lo = w.nr > 0 ? rank[w.jr] : 0;
+            h.q2hi = w.nr > 0 ? rank[w.jr + w.nr] : 0;
             h.npos = (h.q1hi - h.q1lo) + (h.q2hi - h.q2lo) + w.fixed;
             X.dec_s[t] = T.orig[w.s];
             X.dec_r[t] = T.orig[w.r];
@@ -1487,7 +1495,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                         const Cand &c = X.slot[2 * w + d];
                         if (c.s < 0 || !touched(c, hw)) continue;
                         int2 seg[kIncMaxSeg];
-                        const int k = changed_segments(c, hw, S.sn_rank, seg);
+                        const int k = changed_segments(c, hw, rank, seg);
                         write_entry(Lc.ent(atomicAdd(&s_cnt[1], 1)), 2 * w + d, 0, k, seg, c);
                     }
                 }
@@ -1533,7 +1541,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             // r's members join s; ranks past r drop by one; the new super-node list
             for (int b = hw.rtop + tid; b < hw.rtop_end; b += NT)
                 if (S.label[b] == hw.r) S.label[b] = hw.s;
-            for (int b = hw.r + 1 + tid; b <= n; b += NT) S.sn_rank[b] -= 1;
+            for (int b = hw.r + 1 + tid; b <= n; b += NT) rank[b] -= 1;
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             // s takes r's injection (no term before the merge reads s's injection:
             // every candidate with r = s* is rebuilt)
@@ -1594,7 +1602,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 const Cand &cc = X.slot[c];
                 if (cc.s < 0) continue;
                 int2 seg[kIncMaxSeg];
-                const int k = full_segments(cc, S.sn_rank, seg);
+                const int k = full_segments(cc, rank, seg);
                 write_entry(Lc.ent(atomicAdd(&s_cnt[3], 1)), c, 1, k, seg, cc);
             }
             __syncthreads();
@@ -1625,6 +1633,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
         if ((tid & 31) == 0) atomicAdd(reinterpret_cast<unsigned long long *>(&C->sweep_ns), tt);
     }
+    for (int b = tid; b <= n; b += NT) S.sn_rank[b] = rank[b];
     if (tid == 0) {
         C->t = t;
         C->n_super = ns;
