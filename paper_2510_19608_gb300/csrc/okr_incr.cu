@@ -363,6 +363,15 @@ struct Ovl {
     int s, r, nfree;
 };
 
+// A position's FP32 copies in its scratch (after the 10 L FP64 values): per
+// (l, p) the voltage, and the extremes relative to the magnitude; per l the MICE.
+__device__ __forceinline__ float4 *cb_f4(const double *cb_pos, int L, int l, int p) {
+    return reinterpret_cast<float4 *>(const_cast<double *>(cb_pos) + 10 * L) + (l * 3 + p);
+}
+__device__ __forceinline__ float *cb_mice32(const double *cb_pos, int L, int l) {
+    return reinterpret_cast<float *>(const_cast<double *>(cb_pos) + 10 * L) + 12 * L + l;
+}
+
 // FP64 state of super-node x, phase p, scenario l on state e (0 stored, 1 overlay).
 __device__ __forceinline__ void at64(const State &S, const Ovl &O, int e, int x, int l, int p, int n, int L,
                                      bool need_v, double2 *v, double *hh, double *ll) {
@@ -378,7 +387,7 @@ __device__ __forceinline__ void at64(const State &S, const Ovl &O, int e, int x,
     *ll = lo;
     if (need_v) {
         if (j >= 0 && j < O.nfree) {
-            const double *cb = O.cbuf + (size_t)j * 10 * L + (l * 3 + p) * 3;
+            const double *cb = O.cbuf + (size_t)j * kIncCbStride * L + (l * 3 + p) * 3;
             *v = make_double2(cb[0], cb[1]);
         } else {
             *v = S.vcur[ix];
@@ -387,7 +396,7 @@ __device__ __forceinline__ void at64(const State &S, const Ovl &O, int e, int x,
 }
 __device__ __forceinline__ double mice64(const State &S, const Ovl &O, int e, int x, int l, int n, int L) {
     const int j = e ? (int)O.map[x] - 1 : -1;
-    return j >= 0 ? O.cbuf[(size_t)j * 10 * L + 9 * L + l] : S.mice[(size_t)l * n + x];
+    return j >= 0 ? O.cbuf[(size_t)j * kIncCbStride * L + 9 * L + l] : S.mice[(size_t)l * n + x];
 }
 
 // FP32 copies (voltage, extremes relative to the magnitude) and the FP64
@@ -403,23 +412,17 @@ __device__ __forceinline__ void at32(const State &S, const Ovl &O, int e, int x,
         if (need_mc) *mc = S.mcur[ix];
         return;
     }
-    const double *cb = O.cbuf + (size_t)j * 10 * L + (l * 3 + p) * 3;
-    const bool fx = j >= O.nfree;
-    const double m = fx ? S.mcur[ix] : cb[2];
-    double h = S.hi[ix], lo = S.lo[ix];
-    if (x == O.s) {
-        const size_t irs = sidx(l, p, O.r, n);
-        h = fmax(h, S.hi[irs]);
-        lo = fmin(lo, S.lo[irs]);
-    }
-    *hr = (float)(h - m);
-    *lr = (float)(lo - m);
-    if (need_v) *v = fx ? S.v32[ix] : make_float2((float)cb[0], (float)cb[1]);
-    *mc = m;
+    // the FP32 copies the merge's evaluation derived (the write-back stores the same)
+    const double *cbp = O.cbuf + (size_t)j * kIncCbStride * L;
+    const float4 f = *cb_f4(cbp, L, l, p);
+    *hr = f.z;
+    *lr = f.w;
+    if (need_v) *v = make_float2(f.x, f.y);
+    if (need_mc) *mc = j >= O.nfree ? S.mcur[ix] : cbp[(l * 3 + p) * 3 + 2];
 }
 __device__ __forceinline__ float mice32(const State &S, const Ovl &O, int e, int x, int l, int n, int L) {
     const int j = e ? (int)O.map[x] - 1 : -1;
-    return j >= 0 ? (float)O.cbuf[(size_t)j * 10 * L + 9 * L + l] : S.mice32[(size_t)l * n + x];
+    return j >= 0 ? *cb_mice32(O.cbuf + (size_t)j * kIncCbStride * L, L, l) : S.mice32[(size_t)l * n + x];
 }
 
 // The arithmetic of one FP64 term on one state's inputs (every lane of the
@@ -909,10 +912,31 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
         u128 d;
         int nv;
         group_term64(T, S, cm.ph, n, L, G, cm.wc, k, 0, 1, valid, false, cm.O, gl, margin,
-                     valid ? I.cbuf + (size_t)q * 10 * L : nullptr, &d, &nv);
-        if (valid && gl == 0) {
-            items += __popc(cm.ph[k]) * L;
-            cm.map[k] = (unsigned short)(q + 1);     // the terms after the merge read k's new values here
+                     valid ? I.cbuf + (size_t)q * kIncCbStride * L : nullptr, &d, &nv);
+        if (valid) {
+            // the FP32 copies of the new values (what the write-back will store),
+            // from the FP64 values this lane has just written
+            const int l = gl >> 2, p = gl & 3;
+            const double *cb = I.cbuf + (size_t)q * kIncCbStride * L;
+            const bool fx = q >= n1 + n2;
+            if (l < L && p < 3 && (cm.ph[k] >> p & 1u)) {
+                const size_t ik = sidx(l, p, k, n);
+                const double mc = fx ? S.mcur[ik] : cb[(l * 3 + p) * 3 + 2];
+                double hh = S.hi[ik], ll = S.lo[ik];
+                if (k == h.s) {
+                    const size_t ir = sidx(l, p, h.r, n);
+                    hh = fmax(hh, S.hi[ir]);
+                    ll = fmin(ll, S.lo[ir]);
+                }
+                const float2 v32 =
+                    fx ? S.v32[ik] : make_float2((float)cb[(l * 3 + p) * 3], (float)cb[(l * 3 + p) * 3 + 1]);
+                *cb_f4(cb, L, l, p) = make_float4(v32.x, v32.y, (float)(hh - mc), (float)(ll - mc));
+            }
+            if (l < L && p == 0) *cb_mice32(cb, L, l) = (float)cb[9 * L + l];
+            if (gl == 0) {
+                items += __popc(cm.ph[k]) * L;
+                cm.map[k] = (unsigned short)(q + 1);     // the terms after the merge read k's new values here
+            }
         }
     }
     return items;
@@ -1117,34 +1141,26 @@ __device__ void write_back(const State &S, const Inc &I, const Win &hw, const un
         const int k = j < n1 ? list[hw.q1lo + j] : (j < n1 + n2 ? list[hw.q2lo + j - n1] : hw.s);
         if (k == hw.r) continue;
         const bool fx = j >= n1 + n2;
-        const double *cb = I.cbuf + (size_t)j * 10 * L;
+        const double *cb = I.cbuf + (size_t)j * kIncCbStride * L;
         if (l < L && p < 3 && (ph[k] >> p & 1u)) {
             const size_t ik = sidx(l, p, k, n);
-            double mc;
+            const float4 f = *cb_f4(cb, L, l, p);
             if (!fx) {
-                const double2 v = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
-                mc = cb[(l * 3 + p) * 3 + 2];
-                S.vcur[ik] = v;
-                S.mcur[ik] = mc;
-                S.v32[ik] = make_float2((float)v.x, (float)v.y);
-            } else {
-                mc = S.mcur[ik];
+                S.vcur[ik] = make_double2(cb[(l * 3 + p) * 3 + 0], cb[(l * 3 + p) * 3 + 1]);
+                S.mcur[ik] = cb[(l * 3 + p) * 3 + 2];
+                S.v32[ik] = make_float2(f.x, f.y);
             }
-            double hh = S.hi[ik], ll = S.lo[ik];
             if (k == hw.s) {
                 const size_t ir = sidx(l, p, hw.r, n);
-                hh = fmax(hh, S.hi[ir]);
-                ll = fmin(ll, S.lo[ir]);
-                S.hi[ik] = hh;
-                S.lo[ik] = ll;
+                S.hi[ik] = fmax(S.hi[ik], S.hi[ir]);
+                S.lo[ik] = fmin(S.lo[ik], S.lo[ir]);
             }
-            S.hr32[ik] = (float)(hh - mc);
-            S.lr32[ik] = (float)(ll - mc);
+            S.hr32[ik] = f.z;
+            S.lr32[ik] = f.w;
         }
         if (l < L && p == 0) {
-            const double m = cb[9 * L + l];
-            S.mice[(size_t)l * n + k] = m;
-            S.mice32[(size_t)l * n + k] = (float)m;
+            S.mice[(size_t)l * n + k] = cb[9 * L + l];
+            S.mice32[(size_t)l * n + k] = *cb_mice32(cb, L, l);
         }
         if (gl == 0) map[k] = 0;
     }
@@ -1506,8 +1522,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         if (tid == 0) s_cnt[2] = np_tot;                // rebuilt entries follow the changed ones
         stamp(1);
         // ============================================================ the merge: score change and topology
-        // (the new voltages, extremes and MICE stay in the scratch, read through
-        // the overlay, until the terms before the merge have been evaluated)
+        // (the new voltages, extremes and MICE stay in the scratch, with the
+        // FP32 copies the merge's evaluation derived, read through the overlay,
+        // until the terms before the merge have been evaluated)
         {
             const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
             const int gl = tid % G, gi = tid / G, NG = NT / G, l = gl >> 2, p = gl & 3;
@@ -1522,10 +1539,11 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     k = j < n1 ? list_old[hw.q1lo + j] : (j < n1 + n2 ? list_old[hw.q2lo + j - n1] : hw.s);
                     valid = k != hw.r;
                 }
+                const double *cb = I.cbuf + (size_t)j * kIncCbStride * L;
                 // the merge's exact score change: its FP64 terms in fixed point
                 unsigned long long mb = 0;                  // MICE >= 0: bit patterns order like values
                 if (valid && l < L && p == 0) {
-                    const double m = I.cbuf[(size_t)j * 10 * L + 9 * L + l];
+                    const double m = cb[9 * L + l];
                     double dd = m - S.mice[(size_t)l * n + k];
                     if (k == hw.s) dd -= S.mice[(size_t)l * n + hw.r];
                     dsum += to_fx(dd);

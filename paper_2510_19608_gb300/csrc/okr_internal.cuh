@@ -137,6 +137,10 @@ struct GridBar {
 // terms of one candidate slot that an iteration evaluates, as ranges of
 // super-node ranks.
 constexpr int kIncMaxSeg = 7;
+// Doubles per scenario of one position's scratch in Inc::cbuf: 10 FP64 values
+// (voltage x, y and magnitude per phase, the MICE), then 8 doubles' room for
+// their FP32 copies (a 16-byte (v.x, v.y, hr, lr) per phase, the MICE).
+constexpr int kIncCbStride = 18;
 struct IncWork {
     int slot;           // candidate slot 2 w + d (w = the lower super-node of the quotient edge)
     int mode;           // 0: terms of changed clusters, ranks before the merge; 1: every term, ranks after
@@ -156,7 +160,7 @@ struct Inc {
     int *qpar;                  // [n] super-node holding the parent of the cluster's top (-1: slack's cluster)
     int *fpair;                 // [n] slot pairs whose candidates are rebuilt after the merge
     IncWork *work;              // [2n] work entries of one iteration
-    double *cbuf;               // [n * 10 L] the merge's new voltages, magnitudes and MICE
+    double *cbuf;               // [n * kIncCbStride L] the merge's new values per position (okr_incr.cu)
     unsigned long long *vacc;   // [2n][2] FP64 rescoring (precision-1 recheck, verification)
     int *vviol;                 // [2n]
     int *rlist;                 // [2n] slots rescored in FP64 in one iteration
