@@ -476,8 +476,8 @@ def run_ours(args, rank, world, local):
                 "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1,
                 "items_per_launch": items, "flops_per_item": FLOPS_PER_ITEM,
                 "flops_per_launch": items * FLOPS_PER_ITEM,
-                "phase_ms": dict(zip(["select", "changed_set", "merge", "rebuild", "terms"],
-                                     [round(x, 3) for x in ps["phase_ms"][:5]])),
+                "phase_ms": dict(zip(["select", "changed_set", "merge_and_rebuild", "terms"],
+                                     [round(x, 3) for x in ps["phase_ms"][:4]])),
                 "rechecks": ps["rechecks"], "recheck_candidates": ps["recheck_cands"],
                 "share_of_step": search_ms / (ms / args.steps),
                 "note": "one CTA runs the whole search (a chain of dependent merges); its time is latency, "

@@ -140,9 +140,9 @@ typedef struct okr_summary {
     double phase_ms[16];        /* profile mode: time of CTA 0 per step of an iteration.  Sweep engine:
                                    selection, FP64 recheck, merge, candidate setup, barrier, merge
                                    bookkeeping, list update, offsets, compaction, chunk map, barrier,
-                                   sweep.  Incremental engine: selection (with the write-back of the
-                                   last merge's new values), changed set, merge, rebuilt candidates,
-                                   the terms that change (before and after the merge, one pass) */
+                                   sweep.  Incremental engine: selection, changed set, merge with the
+                                   rebuilt candidates beside it, the terms that change (before and
+                                   after the merge, one pass, with the write-back) */
     double kron_ms;             /* device time of the last okr_kron since the reduction (0 if none) */
     int32_t scorer_fallbacks;   /* learned pruning: iterations re-evaluated exhaustively because the
                                    scorer's k candidates were all infeasible */

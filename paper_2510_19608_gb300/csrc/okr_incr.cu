@@ -45,13 +45,14 @@
 // Execution.  One CTA runs one feeder's whole search; its steps are separated
 // by __syncthreads only (no grid barrier, no device-side wait).  A term is
 // evaluated by a group of lanes, one per (scenario, phase).  A batch runs one
-// CTA per feeder.  Each merge takes five steps: selection; the changed set
+// CTA per feeder.  Each merge takes four steps: selection; the changed set
 // (beside it, the merge's own FP64 evaluation into a scratch, and a map of its
-// positions); the merge's score change and topology; the rebuilt candidates;
-// one pass over the changed terms, which evaluates each term before the merge
-// (the state as stored) and after it (the stored state overlaid with the
-// scratch's new values) in the same lane group and adds the difference.  The
-// new values are written back to the state at the end of that pass.
+// positions); the merge's score change and topology, and beside it the
+// rebuilt candidates (which read the clusters through the merge's view); one
+// pass over the changed terms, which evaluates each term before the merge (the
+// state as stored) and after it (the stored state overlaid with the scratch's
+// new values) in the same lane group and adds the difference.  The new values
+// and ranks are written back to the state at the end of that pass.
 #include "okr_internal.cuh"
 #include "okr_kernels.cuh"
 
@@ -297,6 +298,31 @@ __device__ __forceinline__ int child_toward_inc(const Topo &T, int a, int v) {
     return T.child[lo];
 }
 
+// The clusters as a merge (s*, r*) leaves them, read while that merge is being
+// written: r*'s members belong to s*; with dir = 1 s* takes r*'s top; ranks
+// past r* drop by one.  Either value of an entry the merge is rewriting reads
+// the same through the view, and the ranks are rewritten only after the
+// rebuild.  With no merge (s = -1) the state as stored.
+struct View {
+    int s, r, dir;
+    __device__ __forceinline__ int label(const State &S, int b) const {
+        const int l = S.label[b];
+        return l == r ? s : l;
+    }
+    __device__ __forceinline__ int top(const State &S, int w) const {
+        return (w == s && dir == 1) ? S.top[r] : S.top[w];
+    }
+    __device__ __forceinline__ int ptop(const State &S, int w) const {
+        return (w == s && dir == 1) ? S.ptop[r] : S.ptop[w];
+    }
+};
+__device__ __forceinline__ View no_view() {
+    View v;
+    v.s = v.r = -1;
+    v.dir = 0;
+    return v;
+}
+
 // The two candidates of the quotient edge above super-node w, from the current
 // clusters: x = super-node holding the parent of w's top, a = lca(x, w), cw and
 // cx the children of a toward w and x.  Slot 2w: w's cluster joins x (s = x,
@@ -304,13 +330,13 @@ __device__ __forceinline__ int child_toward_inc(const Topo &T, int a, int v) {
 // cluster).  js/ns and jr/nr hold the s-side and r-side subtrees as BUS
 // ranges [j, j + size) (preorder ids); fixed = 1 when s is the common ancestor.
 // Returns x (-1 for the slack's cluster, which has no edge above it).
-__device__ int slot_geometry(const Topo &T, const State &S, int n, int w, Cand &c0, Cand &c1) {
+__device__ int slot_geometry(const Topo &T, const State &S, const View &V, int n, int w, Cand &c0, Cand &c1) {
     c0.s = -1;
     c1.s = -1;
-    const int pb = S.ptop[w];
-    if (pb < 0 || S.label[w] != w) return -1;
-    const int tw = S.top[w];
-    const int x = S.label[pb];
+    const int pb = V.ptop(S, w);
+    if (pb < 0 || V.label(S, w) != w) return -1;
+    const int tw = V.top(S, w);
+    const int x = V.label(S, pb);
     const bool direct = (x == pb);
     const int a = direct ? x : (int)T.lca[(size_t)x * n + w];
     const int cw = direct ? tw : child_toward_inc(T, a, w);
@@ -756,17 +782,19 @@ __device__ int changed_segments(const Cand &c, const Win &h, const int *sn_rank,
 }
 
 // Every term of candidate c: its two ranges and the fixed s, as ranks.
-__device__ int full_segments(const Cand &c, const int *sn_rank, int2 *seg) {
+__device__ int full_segments(const Cand &c, const int *sn_rank, int2 *seg, int rdead = -1) {
+    // rdead >= 0: ranks past bus rdead drop by one (the merge of r* = rdead)
+    auto rk = [&](int b) { return sn_rank[b] - (rdead >= 0 && b > rdead ? 1 : 0); };
     int k = 0;
     if (c.ns > 0) {
-        const int a = sn_rank[c.js], b = sn_rank[c.js + c.ns];
+        const int a = rk(c.js), b = rk(c.js + c.ns);
         if (a < b) seg[k++] = make_int2(a, b);
     }
     if (c.nr > 0) {
-        const int a = sn_rank[c.jr], b = sn_rank[c.jr + c.nr];
+        const int a = rk(c.jr), b = rk(c.jr + c.nr);
         if (a < b) seg[k++] = make_int2(a, b);
     }
-    if (c.fixed) { const int a = sn_rank[c.s]; seg[k++] = make_int2(a, a + 1); }
+    if (c.fixed) { const int a = rk(c.s); seg[k++] = make_int2(a, a + 1); }
     return k;
 }
 
@@ -1086,16 +1114,18 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
     return terms;
 }
 
-// Rebuilds the slot pairs listed in fp[0, nf) from the current clusters and
-// appends a full work entry for each valid candidate at I.work[*cnt...]
-// (*cnt: a shared counter; the caller synchronises before reading it).
+// Rebuilds the slot pairs listed in fp[0, nf) from the clusters as the view
+// shows them and appends a full work entry for each valid candidate at entry
+// base + *cnt (*cnt: a shared counter; the caller synchronises before reading
+// it).
 template <int NT, int PREC>
 __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
-                              int *cnt, const Rec &R, const Loc &Lc) {
-    for (int i = threadIdx.x; i < nf; i += NT) {
+                              int *cnt, int base, const Rec &R, const Loc &Lc, const View &V) {
+    // from the last thread down: beside a merge, the first threads write the merge
+    for (int i = NT - 1 - (int)threadIdx.x; i < nf; i += NT) {
         const int w = fp[i];
         Cand c[2];
-        const int x = slot_geometry(T, S, n, w, c[0], c[1]);
+        const int x = slot_geometry(T, S, V, n, w, c[0], c[1]);
         I.qpar[w] = x;
         {
             int lo = n, hi = 0;
@@ -1114,8 +1144,8 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
             X.slot[sl] = c[d];
             if (c[d].s >= 0) {
                 int2 seg[kIncMaxSeg];
-                const int ns = full_segments(c[d], Lc.rank, seg);
-                write_entry(Lc.ent(atomicAdd(cnt, 1)), sl, 1, ns, seg, c[d]);
+                const int ns = full_segments(c[d], Lc.rank, seg, V.r);
+                write_entry(Lc.ent(base + atomicAdd(cnt, 1)), sl, 1, ns, seg, c[d]);
                 R.tkey[sl] = (unsigned)c[d].key;
             } else {
                 I.viol[sl] = kIncDead;
@@ -1256,7 +1286,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     }
     if (tid == 0) rank[n] = S.sn_rank[n];
     __syncthreads();
-    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], R, Lc);
+    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], 0, R, Lc, no_view());
     __syncthreads();
     {
         const int ne = s_cnt[2];
@@ -1518,10 +1548,10 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
         }
         __syncthreads();
-        const int nf_tot = s_cnt[0], np_tot = s_cnt[1];
-        if (tid == 0) s_cnt[2] = np_tot;                // rebuilt entries follow the changed ones
+        const int nf_tot = s_cnt[0], np_tot = s_cnt[1];   // (s_cnt[2] is 0: rebuilt entries follow these)
         stamp(1);
-        // ============================================================ the merge: score change and topology
+        // ============================================================ the merge (score change, topology) and,
+        // beside it, the rebuilt candidates
         // (the new voltages, extremes and MICE stay in the scratch, with the
         // FP32 copies the merge's evaluation derived, read through the overlay,
         // until the terms before the merge have been evaluated)
@@ -1556,10 +1586,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 if (valid && gl == 0) R.maxm[k] = __longlong_as_double((long long)mb);
             }
             if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
-            // r's members join s; ranks past r drop by one; the new super-node list
+            // r's members join s; the new super-node list
             for (int b = hw.rtop + tid; b < hw.rtop_end; b += NT)
                 if (S.label[b] == hw.r) S.label[b] = hw.s;
-            for (int b = hw.r + 1 + tid; b <= n; b += NT) rank[b] -= 1;
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             // s takes r's injection (no term before the merge reads s's injection:
             // every candidate with r = s* is rebuilt)
@@ -1588,27 +1617,34 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
             if (tid == 0) R.span[hw.r] = make_ushort4(0, 0, 0xffff, 0);
         }
+        // rebuilt pairs from the last thread down, reading the clusters through the
+        // merge's view (the ranks change only after the terms below)
+        {
+            View V;
+            V.s = hw.s;
+            V.r = hw.r;
+            V.dir = hw.dir;
+            rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], np_tot, R, Lc, V);
+        }
         __syncthreads();
         ns -= 1;
+        const int ne_new = np_tot + s_cnt[2];
         stamp(2);
-        // ============================================================ rebuilt candidates
         if (tid == 0) {
             const u128 sfx = ld128(s_sfx) + ld128(s_dsum);
             st128(s_sfx, sfx);
             X.dec_score[t] = fx_to_d(sfx);
         }
-        rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, nf_tot, &s_cnt[2], R, Lc);
-        __syncthreads();
-        const int ne_new = s_cnt[2];
-        stamp(3);
         // ============================================================ the terms that change
         terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne_new, kMerge, list_old, list_new, hw.r,
                                        O, E, sscan, R, Lc, prof ? C->phase_ns + 6 : nullptr, false);
         // the new values into the state (no term reads the state before the
-        // merge any more; this overlaps the last tile's updates of the sums)
+        // merge any more; this overlaps the last tile's updates of the sums);
+        // ranks past r* drop by one
         write_back<NT>(S, I, hw, list_old, Lc.ph, ovl_map, n, L, G);
+        for (int b = hw.r + 1 + tid; b <= n; b += NT) rank[b] -= 1;
         __syncthreads();
-        stamp(4);
+        stamp(3);
         t += 1;
         maxerr_done = false;
         if (verify) {
