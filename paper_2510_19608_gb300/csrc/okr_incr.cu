@@ -723,7 +723,6 @@ __device__ __forceinline__ void group_term32(const Topo &T, const State &S, cons
 struct Win {
     int slot, s, r, a, dir, fixed;
     int w1lo, w1hi, w2lo, w2hi;     // bus ranges whose voltages move
-    int rtop, rtop_end;             // r's cluster lies inside [rtop, rtop_end)
     int jr;                         // rank of r before the merge
     int npos;                       // positions of the merge (ranks of the two ranges, r excluded, + fixed s)
     int q1lo, q1hi, q2lo, q2hi;     // their rank ranges before the merge
@@ -1483,18 +1482,16 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         // ============================================================ the merge's changed set
         if (tid == 0) {
             const Cand w = X.slot[ws];
+            // (only what the next steps need at once: r*'s subtree and the
+            // decision's bus ids are looked up in the merge step)
             h.slot = ws; h.s = w.s; h.r = w.r; h.a = w.a; h.dir = w.dir; h.fixed = w.fixed;
             h.w1lo = w.js; h.w1hi = w.js + w.ns; h.w2lo = w.jr; h.w2hi = w.jr + w.nr;
-            h.rtop = S.top[w.r];
-            h.rtop_end = h.rtop + T.sz[h.rtop];
             h.jr = rank[w.r];
             h.q1lo = w.ns > 0 ? rank[w.js] : 0;
             h.q1hi = w.ns > 0 ? rank[w.js + w.ns] : 0;
             h.q2lo = w.nr > 0 ? rank[w.jr] : 0;
             h.q2hi = w.nr > 0 ? rank[w.jr + w.nr] : 0;
             h.npos = (h.q1hi - h.q1lo) + (h.q2hi - h.q2lo) + w.fixed;
-            X.dec_s[t] = T.orig[w.s];
-            X.dec_r[t] = T.orig[w.r];
             X.dec_gap[t] = gap;
             s_dsum[0] = 0ull;
             s_dsum[1] = 0ull;
@@ -1586,9 +1583,13 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 if (valid && gl == 0) R.maxm[k] = __longlong_as_double((long long)mb);
             }
             if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
-            // r's members join s; the new super-node list
-            for (int b = hw.rtop + tid; b < hw.rtop_end; b += NT)
-                if (S.label[b] == hw.r) S.label[b] = hw.s;
+            // r's members join s (they lie in the subtree of r's top); the new
+            // super-node list
+            {
+                const int rtop = S.top[hw.r], rtop_end = rtop + T.sz[rtop];
+                for (int b = rtop + tid; b < rtop_end; b += NT)
+                    if (S.label[b] == hw.r) S.label[b] = hw.s;
+            }
             for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             // s takes r's injection (no term before the merge reads s's injection:
             // every candidate with r = s* is rebuilt)
@@ -1609,6 +1610,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 }
                 I.qpar[hw.r] = -1;
                 R.maxm[hw.r] = 0.0;
+                X.dec_s[t] = T.orig[hw.s];
+                X.dec_r[t] = T.orig[hw.r];
             }
             if (tid < 2) {
                 X.slot[2 * hw.r + tid].s = -1;
