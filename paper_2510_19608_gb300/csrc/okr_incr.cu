@@ -730,6 +730,25 @@ struct Win {
 
 __device__ __forceinline__ bool in_range(int b, int lo, int hi) { return b >= lo && b < hi; }
 
+// The winner's record from its candidate (slot ws) and the super-node ranks.
+__device__ __forceinline__ Win make_win(const Cand &w, int ws, const int *rank) {
+    Win h;
+    h.slot = ws; h.s = w.s; h.r = w.r; h.a = w.a; h.dir = w.dir; h.fixed = w.fixed;
+    h.w1lo = w.js; h.w1hi = w.js + w.ns; h.w2lo = w.jr; h.w2hi = w.jr + w.nr;
+    h.jr = rank[w.r];
+    h.q1lo = w.ns > 0 ? rank[w.js] : 0;
+    h.q1hi = w.ns > 0 ? rank[w.js + w.ns] : 0;
+    h.q2lo = w.nr > 0 ? rank[w.jr] : 0;
+    h.q2hi = w.nr > 0 ? rank[w.jr + w.nr] : 0;
+    h.npos = (h.q1hi - h.q1lo) + (h.q2hi - h.q2lo) + w.fixed;
+    return h;
+}
+
+// Barrier of the first `count` threads of the block (named barrier 1).
+__device__ __forceinline__ void first_threads_sync(int count) {
+    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+
 // Whether candidate c (not next to s* or r*) has a term that reads an input
 // the merge h changes: a position in the moved ranges or at s*, r*; its fixed
 // s when that cluster changed; its s term when r's MICE changed.
@@ -1480,27 +1499,24 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         stamp(0);
         // ============================================================ the merge's changed set
-        if (tid == 0) {
-            const Cand w = X.slot[ws];
-            // (only what the next steps need at once: r*'s subtree and the
-            // decision's bus ids are looked up in the merge step)
-            h.slot = ws; h.s = w.s; h.r = w.r; h.a = w.a; h.dir = w.dir; h.fixed = w.fixed;
-            h.w1lo = w.js; h.w1hi = w.js + w.ns; h.w2lo = w.jr; h.w2hi = w.jr + w.nr;
-            h.jr = rank[w.r];
-            h.q1lo = w.ns > 0 ? rank[w.js] : 0;
-            h.q1hi = w.ns > 0 ? rank[w.js + w.ns] : 0;
-            h.q2lo = w.nr > 0 ? rank[w.jr] : 0;
-            h.q2hi = w.nr > 0 ? rank[w.jr + w.nr] : 0;
-            h.npos = (h.q1hi - h.q1lo) + (h.q2hi - h.q2lo) + w.fixed;
-            X.dec_gap[t] = gap;
-            s_dsum[0] = 0ull;
-            s_dsum[1] = 0ull;
-        }
-        __syncthreads();
-        const Win hw = h;
-        if (PREC == 1 && tid == 0) {                 // every thread has read both selection results
-            reset_sel(&s_sel[0]);
-            reset_sel(&s_sel[1]);
+        // The winner's record: the scan warps share thread 0's copy (r*'s
+        // subtree and the decision's bus ids are looked up in the merge step);
+        // the warps that evaluate the merge build their own at once, without
+        // waiting (every thread knows ws).
+        constexpr int NW = NT / 32, CW = 4;
+        const bool commit_warp = (tid >> 5) >= NW - CW;
+        Win hw;
+        if (commit_warp) {
+            hw = make_win(X.slot[ws], ws, rank);
+        } else {
+            if (tid == 0) {
+                h = make_win(X.slot[ws], ws, rank);
+                X.dec_gap[t] = gap;
+                s_dsum[0] = 0ull;
+                s_dsum[1] = 0ull;
+            }
+            first_threads_sync((NW - CW) * 32);
+            hw = h;
         }
         O.s = hw.s;
         O.r = hw.r;
@@ -1510,10 +1526,9 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         // The last warps evaluate the merge's own FP64 values meanwhile and
         // map its positions for the overlay.
         {
-            constexpr int NW = NT / 32, CW = 4;
-            if ((tid >> 5) >= NW - CW) {
+            if (commit_warp) {
                 Commit cm;
-                cm.h = &h;
+                cm.h = &hw;
                 cm.wc = X.slot[ws];
                 cm.list = list_old;
                 cm.ph = Lc.ph;
@@ -1546,6 +1561,10 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         __syncthreads();
         const int nf_tot = s_cnt[0], np_tot = s_cnt[1];   // (s_cnt[2] is 0: rebuilt entries follow these)
+        if (PREC == 1 && tid == 0) {                 // every thread has read both selection results
+            reset_sel(&s_sel[0]);
+            reset_sel(&s_sel[1]);
+        }
         stamp(1);
         // ============================================================ the merge (score change, topology) and,
         // beside it, the rebuilt candidates
