@@ -1183,7 +1183,9 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
 template <int NT>
 __device__ void write_back(const State &S, const Inc &I, const Win &hw, const unsigned short *list, const uint8_t *ph,
                            unsigned short *map, int n, int L, int G) {
-    const int tid = threadIdx.x, gl = tid % G, gi = tid / G, NG = NT / G, l = gl >> 2, p = gl & 3;
+    // lanes from the last thread down (no shuffles here), beside the first
+    // threads' updates of the entries' sums
+    const int tid = threadIdx.x, rt = NT - 1 - tid, gl = rt % G, gi = rt / G, NG = NT / G, l = gl >> 2, p = gl & 3;
     const int n1 = hw.q1hi - hw.q1lo, n2 = hw.q2hi - hw.q2lo;
     for (int j = gi; j < hw.npos; j += NG) {
         const int k = j < n1 ? list[hw.q1lo + j] : (j < n1 + n2 ? list[hw.q2lo + j - n1] : hw.s);
@@ -1212,9 +1214,9 @@ __device__ void write_back(const State &S, const Inc &I, const Win &hw, const un
         }
         if (gl == 0) map[k] = 0;
     }
-    if (tid < L) {                          // r's cluster is gone
-        S.mice[(size_t)tid * n + hw.r] = 0.0;
-        S.mice32[(size_t)tid * n + hw.r] = 0.0f;
+    if (rt < L) {                           // r's cluster is gone
+        S.mice[(size_t)rt * n + hw.r] = 0.0;
+        S.mice32[(size_t)rt * n + hw.r] = 0.0f;
     }
 }
 
