@@ -40,6 +40,41 @@ NCU_TRAFFIC = {"bytes": 1200896 + 3072, "source": "paper_2510_19608_gb300/csrc/o
                "sha256_prefix": "c7662960b3fabf33", "summary": "profiles/k_search_inc_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
+# Latency floor of one merge of the incremental search.  One merge is a chain
+# of phases, each of which needs the previous one's result: selection, the
+# merge's own FP64 evaluation (beside the changed-set scan), the rebuilt
+# candidates, the terms that change.  The floor takes, per phase, its longest
+# chain of dependent steps at the latencies measured on a GB300 (one-off
+# clock64 probes, one CTA of 512 threads), with unlimited parallelism inside a
+# phase.  Cycles:
+PRIM_CYCLES = {"l2": 290,        # dependent L2 load (ld.global.cg, 8 MB footprint)
+               "l1": 47,         # dependent load through L1 / shared memory, data the CTA wrote
+               "bar": 48,        # __syncthreads of 512 threads arriving together
+               "dfma": 64,       # dependent DFMA
+               "dsqrt_add": 675,  # dependent FP64 square root + add
+               "ffma": 4}        # dependent FFMA (nominal)
+MERGE_CHAIN = {
+    # two block reductions over the selection records, then the winner's candidate
+    "select": lambda c: 2 * (c["l1"] + c["bar"]) + c["l2"],
+    # position -> lca -> path impedance -> 3-term complex product (6 dependent
+    # DFMAs) -> magnitude -> barrier
+    "merge_eval": lambda c: c["l1"] + 2 * c["l2"] + 6 * c["dfma"] + c["dsqrt_add"] + c["bar"],
+    # a rebuilt pair: label -> parent's cluster -> lca -> child offsets -> child
+    # search -> subtree size (six dependent L2 loads), then a barrier
+    "rebuild": lambda c: 6 * c["l2"] + c["bar"],
+    # offsets scan (two barriers), entry lookup (four shared loads), state, lca
+    # and path-impedance loads, one FP32 term (about 40 dependent operations),
+    # the sums' shared update, a barrier, the carried sum's load, a barrier
+    "terms": lambda c: 2 * c["bar"] + 4 * c["l1"] + 3 * c["l2"] + 40 * c["ffma"] + c["bar"] + c["l2"] + c["bar"],
+}
+SM_CLOCK_HZ = 2.07e9
+
+
+def merge_floor_us(clock_hz: float = SM_CLOCK_HZ) -> tuple[float, dict]:
+    """Latency floor of one merge (µs) and its per-phase cycles."""
+    cyc = {k: f(PRIM_CYCLES) for k, f in MERGE_CHAIN.items()}
+    return sum(cyc.values()) / clock_hz * 1e6, cyc
+
 
 def _ncu_traffic():
     """Per-launch DRAM bytes from the committed ncu capture, or None when the
@@ -58,11 +93,13 @@ def _ncu_traffic():
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batch", action="store_true", help="skip the 256-feeder batch measurement")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-scorer training and evaluation")
+    ap.add_argument("--no-large", action="store_true", help="skip the 2,200- and 3,100-bus rows and their CPU baseline")
+    ap.add_argument("--cpu-repeats", type=int, default=3, help="oracle runs per CPU baseline (median)")
     return ap.parse_args()
 
 
@@ -149,15 +186,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(f, run, max_seconds=30.0):
+def cpu_baseline(f, run, repeats=3):
     """The CPU oracle (delta mode, FP64, OpenMP over candidates) on the same
-    feeder: the full reduction when it fits the time budget."""
+    feeder: the full reduction, median of `repeats` runs."""
     from oracle import oracle as O
     vhat, ihat = O.operating_points(f)
     merges = O.max_merges_for(f.n_bus, run["target"])
-    t0 = time.perf_counter()
-    res = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
-    dt = time.perf_counter() - t0
+    times = []
+    for _ in range(max(1, repeats)):
+        t0 = time.perf_counter()
+        res = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
     cores = O.num_threads()
     # the same oracle on one thread (first 50 merges), and its literal mode
     # (a full network solve per candidate) on the 40-bus case
@@ -176,7 +216,7 @@ def cpu_baseline(f, run, max_seconds=30.0):
         O.set_threads(cores)
     return {"value": res["candidates"] / dt, "unit": "candidates/s", "cores": cores, "kind": "oracle",
             "sample": f"full {WORKLOAD} reduction ({res['n_iter']} merges, {res['candidates']} candidates) "
-                      f"in {dt:.2f} s, delta mode", "seconds": dt, "merges": int(res["n_iter"]),
+                      f"in {dt:.2f} s, delta mode, median of {len(times)}", "seconds": dt, "merges": int(res["n_iter"]),
             "one_thread": {"value": r1["candidates"] / d1, "unit": "candidates/s", "cores": 1,
                            "sample": f"first {r1['n_iter']} merges of {WORKLOAD}, delta mode", "seconds": d1},
             "literal_feeder40": {"value": r40["candidates"] / d2, "unit": "candidates/s", "cores": 1,
@@ -185,6 +225,9 @@ def cpu_baseline(f, run, max_seconds=30.0):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle (the paper ships no code; the oracle is
+    the plain FP64 statement of Algorithm 1) timed on the host cores on the
+    same workload as our arm, one full reduction per step."""
     import feedergen as fg
     from oracle import oracle as O
     if rank != 0:
@@ -192,15 +235,12 @@ def run_reference(args, rank, world):
     f, run = fg.preset(WORKLOAD)
     vhat, ihat = O.operating_points(f)
     merges = O.max_merges_for(f.n_bus, run["target"])
-    # one step = the first `sample` merges of the reduction (the costliest part:
-    # the candidate count falls as the feeder shrinks), sized to finish in seconds
-    sample = min(merges, 100)
     for _ in range(args.warmup):
-        O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=sample)
+        O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
     times, cands = [], 0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        r = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=sample)
+        r = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
         times.append(time.perf_counter() - t0)
         cands += r["candidates"]
     total = sum(times)
@@ -208,9 +248,10 @@ def run_reference(args, rank, world):
     line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": _workload_config(f, run) | {"step": f"first {sample} merges by the CPU oracle"},
+            "config": _workload_config(f, run),
+            "step": f"one full reduction ({r['n_iter']} merges) by the CPU oracle, delta mode",
             "cpu_baseline": {"value": value, "unit": "candidates/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"first {sample} merges of {WORKLOAD} per step, delta mode"},
+                             "sample": f"full {WORKLOAD} reduction per step ({r['n_iter']} merges), delta mode"},
             "e2e": {"value": value, "unit": "candidates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -353,6 +394,101 @@ def sweeps_line(K, ctx):
                            "max_error_by_hour": [round(e, 6) for e in rob["max_error_by_hour"]]}}
 
 
+def search_roofline(K, ctx, dfeed, run, search_ms: float, merges: int) -> dict:
+    """Roofline block of the incremental search kernel (one CTA runs a
+    feeder's whole search, a chain of dependent merges): its per-merge time
+    against the latency floor of a merge, and, beside it, its counted FP32
+    arithmetic against the FP32 ALU peak.  search_ms: the kernel's CUDA-event
+    time per launch; items are counted by the kernel in one profiled run."""
+    pp = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1, engine=2, profile=1)
+    ctx.reduce_device(dfeed, pp)
+    ps = ctx.summary()
+    items = ps["terms"]
+    floor_us, cyc = merge_floor_us()
+    per_merge_us = 1e3 * search_ms / max(merges, 1)
+    achieved_flops = items * FLOPS_PER_ITEM / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
+    return {"bound": "latency", "achieved": 1e6 / per_merge_us, "peak": 1e6 / floor_us, "unit": "merges/s",
+            "frac": floor_us / per_merge_us, "kernel": "k_search_inc",
+            "measured_us_per_merge": per_merge_us, "floor_us_per_merge": floor_us,
+            "floor_cycles_per_phase": cyc, "floor_clock_hz": SM_CLOCK_HZ,
+            "peak_source": "latency floor of one merge: per phase, the longest chain of dependent steps at latencies "
+                           "measured on a GB300 (L2 290, L1 47, barrier 48, DFMA 64, DP sqrt+add 675 cycles; FFMA 4 "
+                           "nominal), unlimited parallelism inside a phase",
+            "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1, "merges": merges,
+            "items_per_launch": items, "flops_per_item": FLOPS_PER_ITEM, "flops_per_launch": items * FLOPS_PER_ITEM,
+            "alu": {"bound": "alu", "achieved": achieved_flops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved_flops / FP32_PEAK_TFLOPS,
+                    "peak_source": "derived FP32 ALU rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"},
+            "phase_us_per_merge": dict(zip(["select", "changed_set", "merge_and_rebuild", "terms"],
+                                           [round(1e3 * x / max(merges, 1), 3) for x in ps["phase_ms"][:4]])),
+            "rechecks": ps["rechecks"], "recheck_candidates": ps["recheck_cands"],
+            "shape": {k: ps[k] for k in ("inc_threads", "inc_eval_warps", "inc_shared_entries", "inc_records")}}
+
+
+def large_feeder_rows(K, ctx, stream, steps: int, flush) -> dict:
+    """The 2,200- and 3,100-bus stand-ins of the paper's 5,991- and 8,381-node
+    feeders (Table 2) at their targets (90 %, 80 %): time to optimal reduction
+    with inputs resident in HBM (CUDA events around okr_reduce_device on the
+    library's stream, L2 flushed between steps), candidates/s, the (candidate,
+    phase-node, scenario) items evaluated per second, the FP64 sweep beside
+    it, and the search kernel's roofline block."""
+    import numpy as np
+    import torch
+    import feedergen as fg
+    out = {}
+    for name in ("feeder2200", "feeder3100"):
+        f, run = fg.preset(name)
+        dev = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (f.parent, f.phases, f.z_line, f.s_load)]
+        dfeed = K.device_feeder(f.n_bus, f.n_scen, *[t.data_ptr() for t in dev], f.v_slack)
+        row = {"workload": f"{name}: {f.n_bus} buses ({f.n_phase_nodes} phase nodes), 12.47 kV, {f.n_scen} "
+                           f"scenarios, 45/15/40 % phase mix, lognormal loads, target {int(run['target'] * 100)}%, "
+                           f"margin {run['margin']} p.u."}
+        for key, prec, engine in (("incremental_mixed", 1, 2), ("sweep_fp64", 0, 1)):
+            p = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=prec, engine=engine)
+            for _ in range(3):
+                ctx.reduce_device(dfeed, p)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            kern = []
+            for a, b in ev:
+                flush.fill_(1.0)
+                a.record(stream)
+                ctx.reduce_device(dfeed, p)
+                b.record(stream)
+                kern.append(ctx.summary()["search_ms"])
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+            sm = ctx.summary()
+            row[key] = {"time_to_optimal_ms": ms, "candidates_per_s": sm["candidates"] / (ms / 1e3),
+                        "candidates": sm["candidates"], "merges": sm["n_iter"], "stop_reason": sm["stop_reason"],
+                        "search_kernel_ms": statistics.median(kern), "smice": sm["smice"]}
+            if key == "incremental_mixed":
+                rl = search_roofline(K, ctx, dfeed, run, statistics.median(kern), sm["n_iter"])
+                row[key]["items_per_s"] = rl["items_per_launch"] / (ms / 1e3)
+                row[key]["roofline"] = rl
+        row["fp64_over_incremental"] = row["sweep_fp64"]["time_to_optimal_ms"] / row["incremental_mixed"]["time_to_optimal_ms"]
+        out[name] = row
+    return out
+
+
+def cpu_baseline_large(name: str = "feeder2200", repeats: int = 3) -> dict:
+    """The oracle's full reduction of a large stand-in on every host core
+    (median of `repeats`)."""
+    import feedergen as fg
+    from oracle import oracle as O
+    f, run = fg.preset(name)
+    vhat, ihat = O.operating_points(f)
+    merges = O.max_merges_for(f.n_bus, run["target"])
+    times, res = [], None
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        res = O.reduce(f, vhat, ihat, margin=run["margin"], max_merges=merges)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
+    return {"value": res["candidates"] / dt, "unit": "candidates/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"full {name} reduction ({res['n_iter']} merges, {res['candidates']} candidates), delta mode, "
+                      f"median of {repeats}", "seconds": dt, "seconds_all": times}
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -464,42 +600,41 @@ def run_ours(args, rank, world, local):
     # whole search), timed with CUDA events around its launch on the library
     # stream; its (candidate, phase-node, scenario) items are counted by the
     # kernel in one profiled step
-    pp = K.default_params(margin=run["margin"], target_reduction=run["target"], precision=1, engine=2, profile=1)
-    ctx.reduce_device(dfeed, pp)
-    ps = ctx.summary()
+    search_ms = summ_last["search_ms"]
+    roofline = search_roofline(K, ctx, dfeed, run, search_ms, summ["n_iter"])
+    roofline["traffic"] = _ncu_traffic()
+    roofline["share_of_step"] = search_ms / (ms / args.steps)
+    roofline["note"] = ("one CTA runs the whole search, a chain of dependent merges: its time is latency, not "
+                        "arithmetic or memory traffic; frac = latency floor / measured time per merge")
     # output Y_Kron of the chosen network (Sec. II-B), formed once per feeder
     yk, _ = ctx.kron()
     kron = {"ms": ctx.summary()["kron_ms"], "k_phi": int(yk.shape[0]),
             "note": "device time of okr_kron on the chosen network (outside the step)"}
-    search_ms = summ_last["search_ms"]
-    items = ps["terms"]
-    achieved = items * FLOPS_PER_ITEM / (search_ms / 1e3) / 1e12 if search_ms > 0 else 0.0
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": _ncu_traffic(), "kernel": "k_search_inc",
-                "peak_source": "derived FP32 ALU rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz",
-                "avg_launch_us": 1e3 * search_ms, "launches_per_step": 1,
-                "items_per_launch": items, "flops_per_item": FLOPS_PER_ITEM,
-                "flops_per_launch": items * FLOPS_PER_ITEM,
-                "phase_ms": dict(zip(["select", "changed_set", "merge_and_rebuild", "terms"],
-                                     [round(x, 3) for x in ps["phase_ms"][:4]])),
-                "rechecks": ps["rechecks"], "recheck_candidates": ps["recheck_cands"],
-                "share_of_step": search_ms / (ms / args.steps),
-                "note": "one CTA runs the whole search (a chain of dependent merges); its time is latency, "
-                        "not arithmetic or memory traffic"}
+    large = large_feeder_rows(K, ctx, stream, max(1, min(args.steps, 10)), flush) if not args.no_large else None
     batch = batch_line(K, ctx) if not args.no_batch else None
     learned = learned_line(K, ctx) if not args.no_learned else None
     studies = sweeps_line(K, ctx) if not args.no_batch else None
     if rank == 0:
-        cb = cpu_baseline(f, run) if world == 1 else None
+        cb = cpu_baseline(f, run, repeats=args.cpu_repeats) if world == 1 else None
+        if cb is not None and not args.no_large:
+            cb["feeder2200"] = cpu_baseline_large("feeder2200", repeats=args.cpu_repeats)
         line = {"metric": METRIC, "value": value, "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "fp64_search": {"ms_per_step": fp64_row["ms_per_step"], "value": fp64_row["value"],
+                                "unit": "candidates/s", "headline_speedup": fp64_row["ms_per_step"] / (ms / args.steps),
+                                "engine": "sweep, plain FP64: every candidate scored afresh each iteration"},
+                "large_feeders": large,
                 "config": _workload_config(f, run) | {
                     "engine": "incremental: every candidate's score carried across merges as an exact fixed-point "
                               "sum of its terms; only the terms whose inputs the last merge changed are evaluated "
                               "again; one CTA",
                     "precision": "FP32 terms with carried rigorous bounds, FP64 rescoring of the candidates the bound "
                                  "cannot separate, FP64 merges",
+                    "value_counts": "every candidate of every iteration gets its exact score and feasibility; the "
+                                    "incremental engine carries most scores from the last merge and recomputes only "
+                                    "the terms whose inputs changed (roofline.items_per_launch); fp64_search scores "
+                                    "every candidate afresh",
                     "fp64_search": fp64_row, "other_engines": other_rows, "rechecks": summ_last["rechecks"],
                     "recheck_candidates": summ_last["recheck_cands"],
                     "l2": "flushed between steps (256 MB write outside the timed events)",

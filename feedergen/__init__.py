@@ -45,7 +45,8 @@ import math
 
 import numpy as np
 
-__all__ = ["Feeder", "make_feeder", "preset", "batch_presets", "PRESETS", "daily_profiles", "with_loads"]
+__all__ = ["Feeder", "make_feeder", "preset", "batch_presets", "PRESETS", "daily_profiles", "with_loads",
+           "fingerprint"]
 
 
 @dataclasses.dataclass
@@ -322,3 +323,15 @@ def with_loads(feeder: Feeder, s_load: np.ndarray) -> Feeder:
     """The same network with other per-scenario loads ([L, n, 3, 2])."""
     return Feeder(parent=feeder.parent, phases=feeder.phases, z_line=feeder.z_line,
                   s_load=np.ascontiguousarray(s_load, dtype=np.float64), v_slack=feeder.v_slack, meta=dict(feeder.meta))
+
+
+def fingerprint(feeder: Feeder) -> str:
+    """SHA-256 of a feeder's arrays (their bytes, in a fixed order): two
+    machines that draw the same feeder bit for bit give the same string, so a
+    stored expected value can be checked against the inputs it was made from."""
+    import hashlib
+    h = hashlib.sha256()
+    for a, dt in ((feeder.parent, np.int32), (feeder.phases, np.uint8), (feeder.z_line, np.float64),
+                  (feeder.s_load, np.float64), (feeder.v_slack, np.float64)):
+        h.update(np.ascontiguousarray(a, dtype=dt).tobytes())
+    return h.hexdigest()

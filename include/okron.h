@@ -39,6 +39,7 @@
 #ifndef OKRON_H
 #define OKRON_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -111,7 +112,9 @@ typedef struct okr_params {
                                    OKR_ENGINE_VERIFY (3): as 2, and after every merge every candidate
                                      is also evaluated afresh and compared bit for bit with its
                                      carried score (okr_summary.inc_mismatches; for tests). */
-    int64_t max_spins;          /* limit for device-side waits (0 = default; the sweep engine) */
+    int64_t max_spins;          /* polls before a device-side wait gives up with OKR_ETIMEOUT: the grid
+                                   barriers of the load flow and of the sweep engine (0 = default,
+                                   4,000,000: well under a second) */
 } okr_params;
 
 #define OKR_ENGINE_AUTO 0
@@ -153,7 +156,33 @@ typedef struct okr_summary {
     int64_t terms;              /* incremental engine, profile mode: (candidate, phase-node, scenario)
                                    items evaluated over the run, the initial evaluation, the merges'
                                    own evaluations and FP64 rescorings included (0 otherwise) */
+    /* incremental engine: the launch shape that ran (okr_inc_shape's meaning; 0 for the sweep) */
+    int32_t inc_threads, inc_eval_warps, inc_shared_entries, inc_records;
 } okr_summary;
+
+/* Launch shape of the incremental engine (one CTA runs one feeder's search).
+ * Every shape gives the same results; only the time differs.  Set per
+ * context (okr_set_inc_shape), used by the later okr_reduce* and
+ * okr_reduce_batch calls on it.  A field of 0 takes its default. */
+typedef struct okr_inc_shape {
+    int32_t threads;            /* threads of the CTA: 256 or 512 (0 = 512) */
+    int32_t eval_warps;         /* warps that evaluate the merge's own new values while the others
+                                   find the changed candidates: 1 .. threads/32 - 1 (0 = 4, or 2
+                                   with 256 threads) */
+    int32_t shared_entries;     /* work entries of one merge kept in shared memory, 1 .. 256
+                                   (0 = 256); the rest live in device memory */
+    int32_t records;            /* where the per-candidate selection records live: 0 automatic
+                                   (shared memory when it fits), 1 device memory, 2 shared memory,
+                                   3 shared memory with the largest MICE per super-node (single-
+                                   feeder searches only).  A forced placement that does not fit
+                                   makes the reduction fail with OKR_EINVAL. */
+} okr_inc_shape;
+
+/* Sets the context's incremental-engine shape (NULL = every field default).
+ * OKR_EINVAL for a value outside the ranges above. */
+okr_status okr_set_inc_shape(okr_ctx *ctx, const okr_inc_shape *shape);
+/* The context's shape with the defaults filled in (records 0 stays automatic). */
+okr_status okr_get_inc_shape(const okr_ctx *ctx, okr_inc_shape *shape);
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
  * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, scorer_topk 0,
@@ -168,6 +197,23 @@ okr_status okr_create(okr_ctx **ctx, int device, void *stream);
 okr_status okr_destroy(okr_ctx *ctx);
 const char *okr_status_str(okr_status s);
 const char *okr_last_error(const okr_ctx *ctx);
+
+/* Device memory from the caller's allocator (e.g. a framework's caching
+ * allocator, so that the library's workspace is accounted for and reused
+ * there).  Every device allocation of the context -- its workspace, batch
+ * arenas, batch plans, Y_Kron and scorer buffers -- then calls
+ * alloc(user, bytes, device, stream) and later free(user, ptr, device,
+ * stream), with the context's device and stream; pinned host staging is
+ * unaffected.  alloc returns NULL on failure (the call then returns
+ * OKR_ENOMEM) and must return memory usable by work on `stream` at once.
+ * The library frees a block only after the work on its stream that used it
+ * has finished.  Without a registered allocator the context uses
+ * cudaMalloc / cudaFree.  Must be called before the context's first device
+ * allocation (right after okr_create), else OKR_EINVAL; alloc = free = NULL
+ * restores cudaMalloc / cudaFree under the same condition. */
+typedef void *(*okr_alloc_fn)(void *user, size_t bytes, int device, void *stream);
+typedef void (*okr_free_fn)(void *user, void *ptr, int device, void *stream);
+okr_status okr_set_allocator(okr_ctx *ctx, okr_alloc_fn alloc, okr_free_fn free_fn, void *user);
 
 /* Full path (Sec. III operating points, then Algorithm 1): load flow of every
  * scenario by backward/forward sweep, Ihat = Y Vhat, then the search.  Feeder
@@ -311,7 +357,9 @@ okr_status okr_radialize(okr_ctx *ctx, const uint8_t *kept, uint8_t *critical, i
 #define OKR_SCORER_FEATURES 14
 
 /* Features of every candidate of recorded iteration `iter` of the last
- * reduction (same order as okr_get_recorded).  features: HOST [cap][12]. */
+ * reduction (same order as okr_get_recorded).  features: HOST
+ * [cap][OKR_SCORER_FEATURES] floats, caller-owned, written for the first
+ * min(cap, count) candidates; NULL with cap = 0 queries *count alone. */
 okr_status okr_get_recorded_features(const okr_ctx *ctx, int32_t iter, int32_t cap, float *features,
                                      int32_t *count);
 
@@ -385,6 +433,42 @@ okr_status okr_evaluate(okr_ctx *ctx, const okr_feeder *f, const int32_t *super_
  * by the caller. */
 okr_status okr_power_flow_static(const okr_feeder *f, double *vhat_out, double *ihat_out,
                                  int32_t *sweeps, void *stream);
+
+/* ---- results as library-owned objects ----------------------------------
+ * The problem statement's outputs (Sec. III-IV: the kept set and clusters,
+ * the reduced network's voltages and errors; Sec. II-B: Y_Kron) of one
+ * reduction, copied out of the context so that later calls on the context
+ * do not touch them.  The object holds host memory only and is owned by the
+ * library until okr_result_free; its getters copy into caller buffers and
+ * never fail on a valid object.  Any output pointer may be NULL; a call with
+ * every array pointer NULL returns the sizes alone. */
+typedef struct okr_result okr_result;
+
+/* Takes the results of the context's last okr_reduce / okr_reduce_device /
+ * okr_reduce_ops: the summary, the decision sequence, the assignment, the
+ * voltages of the full and of the reduced network and, with with_ykron = 1,
+ * Y_Kron of the chosen network (computed on the device as by okr_kron).
+ * Errors: OKR_ENOTREADY without a reduction; OKR_ENOMEM; okr_kron's errors
+ * with with_ykron. */
+okr_status okr_result_take(okr_ctx *ctx, int32_t with_ykron, okr_result **out);
+void okr_result_free(okr_result *res);
+okr_status okr_result_summary(const okr_result *res, okr_summary *out);
+/* super_of: [n_bus] caller ids of each bus's super-node; *n_bus, *n_kept. */
+okr_status okr_result_assignment(const okr_result *res, int32_t *super_of, int32_t *n_bus, int32_t *n_kept);
+/* The decision sequence as okr_get_decisions; *count = merges (the first
+ * min(cap, count) entries are written). */
+okr_status okr_result_decisions(const okr_result *res, int32_t cap, int32_t *s, int32_t *r, double *smice,
+                                double *max_error, double *gap, int32_t *ncand, int32_t *count);
+/* Largest per-phase error and SMICE of the chosen network; vhat, vred:
+ * [n_scen][n_bus][3][2] voltages of the full and the reduced network. */
+okr_status okr_result_errors(const okr_result *res, double *max_error, double *smice, double *vhat, double *vred,
+                             int32_t *n_scen, int32_t *n_bus);
+/* Y_Kron of the chosen network as okr_kron writes it (y: [k_phi][k_phi][2],
+ * phase_node: [k_phi]; cap >= k_phi when either is given, else OKR_EINVAL);
+ * OKR_ENOTREADY when the result was taken without it. */
+okr_status okr_result_ykron(const okr_result *res, int32_t cap, double *y, int32_t *phase_node, int32_t *k_phi);
+/* Candidates evaluated, merges committed, seconds of the search kernel. */
+okr_status okr_result_stats(const okr_result *res, int64_t *candidates, int32_t *iterations, double *seconds);
 
 /* ---- results of the last reduction (host buffers, caller-owned) ---- */
 okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out);

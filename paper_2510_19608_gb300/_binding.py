@@ -19,6 +19,8 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, EPF, ETIMEOUT, ENOTREADY, ESINGULAR, EINTERNAL = range(9)
+SCORER_FEATURES = 14     # OKR_SCORER_FEATURES: floats per candidate row of okr_get_recorded_features
+STATIC_MAX_BUS = 4096    # OKR_STATIC_MAX_BUS: largest feeder of okr_power_flow_static
 
 
 class OkrError(RuntimeError):
@@ -47,7 +49,14 @@ class Summary(C.Structure):
                 ("search_ms", C.c_double), ("sweeps", C.c_int64), ("sweep_ms", C.c_double), ("flops", C.c_double),
                 ("rechecks", C.c_int32), ("recheck_cands", C.c_int32), ("phase_ms", C.c_double * 16),
                 ("kron_ms", C.c_double), ("scorer_fallbacks", C.c_int32), ("inc_mismatches", C.c_int32),
-                ("engine", C.c_int32), ("pad", C.c_int32), ("terms", C.c_int64)]
+                ("engine", C.c_int32), ("pad", C.c_int32), ("terms", C.c_int64),
+                ("inc_threads", C.c_int32), ("inc_eval_warps", C.c_int32), ("inc_shared_entries", C.c_int32),
+                ("inc_records", C.c_int32)]
+
+
+class IncShape(C.Structure):
+    _fields_ = [("threads", C.c_int32), ("eval_warps", C.c_int32), ("shared_entries", C.c_int32),
+                ("records", C.c_int32)]
 
 
 class BatchItem(C.Structure):
@@ -60,6 +69,10 @@ class BatchStats(C.Structure):
                 ("config", C.c_int32), ("ctas", C.c_int32), ("fallbacks", C.c_int32), ("reserved", C.c_int32)]
 
 
+# okr_alloc_fn / okr_free_fn
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_void_p, C.c_size_t, C.c_int, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p)
+
 EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", "okr_last_error",
            "okr_reduce", "okr_reduce_device", "okr_reduce_ops", "okr_power_flow", "okr_get_summary",
            "okr_get_decisions", "okr_get_assignment", "okr_get_voltages", "okr_get_recorded",
@@ -67,7 +80,10 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_set_batch_config", "okr_radialize", "okr_get_recorded_features", "okr_scorer_init",
            "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict",
            "okr_evaluate", "okr_scorer_predict_tc", "okr_batch_plan_create", "okr_batch_plan_run", "okr_batch_plan_set_loads",
-           "okr_batch_plan_destroy")
+           "okr_batch_plan_destroy", "okr_set_inc_shape", "okr_get_inc_shape",
+           "okr_set_allocator", "okr_result_take", "okr_result_free", "okr_result_summary",
+           "okr_result_assignment", "okr_result_decisions", "okr_result_errors", "okr_result_ykron",
+           "okr_result_stats")
 
 
 def lib_path() -> str:
@@ -116,12 +132,25 @@ def lib():
             L.okr_scorer_predict.argtypes = [P, P, C.c_int64, P]
             L.okr_scorer_predict_tc.argtypes = [P, P, C.c_int64, P]
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
+            L.okr_set_inc_shape.argtypes = [P, P]
+            L.okr_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
+            L.okr_result_take.argtypes = [P, I32, C.POINTER(P)]
+            L.okr_result_free.argtypes = [P]
+            L.okr_result_free.restype = None
+            L.okr_result_summary.argtypes = [P, C.POINTER(Summary)]
+            L.okr_result_assignment.argtypes = [P, P, P, P]
+            L.okr_result_decisions.argtypes = [P, I32, P, P, P, P, P, P, P]
+            L.okr_result_errors.argtypes = [P, P, P, P, P, P, P]
+            L.okr_result_ykron.argtypes = [P, I32, P, P, P]
+            L.okr_result_stats.argtypes = [P, P, P, P]
+            L.okr_get_inc_shape.argtypes = [P, C.POINTER(IncShape)]
             L.okr_get_decisions.argtypes = [P, I32, P, P, P, P, P, P]
             L.okr_get_assignment.argtypes = [P, P]
             L.okr_get_voltages.argtypes = [P, P, P]
             L.okr_get_recorded.argtypes = [P, I32, I32, P, P, P, P, P]
             for fn in EXPORTS:
-                if fn not in ("okr_default_params", "okr_status_str", "okr_last_error", "okr_batch_plan_destroy"):
+                if fn not in ("okr_default_params", "okr_status_str", "okr_last_error", "okr_batch_plan_destroy",
+                              "okr_result_free"):
                     getattr(L, fn).restype = C.c_int
             _lib = L
     return _lib
@@ -285,6 +314,60 @@ class Context:
         graph; run() replays it."""
         return BatchPlan(self, feeders, params)
 
+    def set_allocator(self, alloc=None, free=None):
+        """okr_set_allocator: alloc(bytes, device, stream) -> int device address
+        (0 on failure) and free(ptr, device, stream), called for every device
+        block of this context; None, None restores cudaMalloc / cudaFree.  Call
+        right after creating the context."""
+        if alloc is None and free is None:
+            self._alloc_cbs = None
+            self._check(lib().okr_set_allocator(self._h, ALLOC_FN(), FREE_FN(), None))
+            return
+
+        def _a(user, nbytes, device, stream):
+            try:
+                return int(alloc(int(nbytes), int(device), int(stream or 0))) or None
+            except Exception:
+                return None
+
+        def _f(user, ptr, device, stream):
+            try:
+                free(int(ptr), int(device), int(stream or 0))
+            except Exception:
+                pass
+
+        cbs = (ALLOC_FN(_a), FREE_FN(_f))
+        self._check(lib().okr_set_allocator(self._h, cbs[0], cbs[1], None))
+        self._alloc_cbs = cbs             # the library calls them until the context is closed
+
+    def use_torch_allocator(self):
+        """Device memory from torch's caching allocator (torch.cuda.caching_allocator_alloc
+        on the context's device and stream)."""
+        import torch
+
+        def alloc(nbytes, device, stream):
+            return torch.cuda.caching_allocator_alloc(nbytes, device, stream)
+
+        def free(ptr, device, stream):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self.set_allocator(alloc, free)
+
+    def set_inc_shape(self, threads: int = 0, eval_warps: int = 0, shared_entries: int = 0, records: int = 0):
+        """okr_set_inc_shape: launch shape of the incremental engine (0 = default)."""
+        sh = IncShape(int(threads), int(eval_warps), int(shared_entries), int(records))
+        self._check(lib().okr_set_inc_shape(self._h, C.byref(sh)))
+
+    def reset_inc_shape(self):
+        """okr_set_inc_shape(NULL): every field back to its default."""
+        self._check(lib().okr_set_inc_shape(self._h, None))
+
+    def inc_shape(self) -> dict:
+        """okr_get_inc_shape: the context's shape, defaults filled in."""
+        sh = IncShape()
+        self._check(lib().okr_get_inc_shape(self._h, C.byref(sh)))
+        return {k: getattr(sh, k) for k, _ in IncShape._fields_}
+
     def set_batch_config(self, config: int):
         """okr_set_batch_config: team shape 0/1/2/3 = 1/2/4/8 CTAs per feeder."""
         self._check(lib().okr_set_batch_config(self._h, int(config)))
@@ -322,7 +405,7 @@ class Context:
     def recorded_features(self, it: int) -> np.ndarray:
         cnt = C.c_int32()
         self._check(lib().okr_get_recorded_features(self._h, it, 0, None, C.byref(cnt)))
-        out = np.zeros((int(cnt.value), 14), np.float32)
+        out = np.zeros((int(cnt.value), SCORER_FEATURES), np.float32)
         self._check(lib().okr_get_recorded_features(self._h, it, out.shape[0], _ptr(out), C.byref(cnt)))
         return out
 
@@ -380,6 +463,12 @@ class Context:
         pn = np.zeros(K, np.int32)
         self._check(lib().okr_kron(self._h, _ptr(kp) if kp is not None else None, K, _ptr(y), _ptr(pn), C.byref(k)))
         return y[..., 0] + 1j * y[..., 1], pn
+
+    def take_result(self, with_ykron: bool = False) -> "Result":
+        """okr_result_take: the last reduction's results as a library-owned object."""
+        h = C.c_void_p()
+        self._check(lib().okr_result_take(self._h, 1 if with_ykron else 0, C.byref(h)))
+        return Result(h)
 
     # ---- results
     def summary(self) -> dict:
@@ -471,3 +560,81 @@ class BatchPlan:
             self.close()
         except Exception:
             pass
+
+
+def _checked(status: int):
+    if status != OK:
+        raise OkrError(status, lib().okr_status_str(status).decode())
+
+
+class Result:
+    """An okr_result: one reduction's results, owned by the library until close()."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def close(self):
+        if self._h:
+            lib().okr_result_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def summary(self) -> dict:
+        s = Summary()
+        _checked(lib().okr_result_summary(self._h, C.byref(s)))
+        out = {k: getattr(s, k) for k, _ in Summary._fields_}
+        out["phase_ms"] = list(s.phase_ms)
+        return out
+
+    def assignment(self) -> np.ndarray:
+        n, k = C.c_int32(), C.c_int32()
+        _checked(lib().okr_result_assignment(self._h, None, C.byref(n), C.byref(k)))
+        out = np.zeros(int(n.value), np.int32)
+        _checked(lib().okr_result_assignment(self._h, _ptr(out), C.byref(n), C.byref(k)))
+        return out
+
+    def decisions(self) -> dict:
+        cnt = C.c_int32()
+        _checked(lib().okr_result_decisions(self._h, 0, None, None, None, None, None, None, C.byref(cnt)))
+        t = int(cnt.value)
+        cap = max(t, 1)
+        s, r, nc = (np.zeros(cap, np.int32) for _ in range(3))
+        sm, me, gap = (np.zeros(cap) for _ in range(3))
+        _checked(lib().okr_result_decisions(self._h, cap, _ptr(s), _ptr(r), _ptr(sm), _ptr(me), _ptr(gap), _ptr(nc),
+                                            C.byref(cnt)))
+        return dict(s=s[:t], r=r[:t], score=sm[:t], maxerr=me[:t], gap=gap[:t], ncand=nc[:t])
+
+    def errors(self) -> dict:
+        me, sm = C.c_double(), C.c_double()
+        L, n = C.c_int32(), C.c_int32()
+        _checked(lib().okr_result_errors(self._h, C.byref(me), C.byref(sm), None, None, C.byref(L), C.byref(n)))
+        vh = np.zeros((L.value, n.value, 3, 2))
+        vr = np.zeros((L.value, n.value, 3, 2))
+        _checked(lib().okr_result_errors(self._h, None, None, _ptr(vh), _ptr(vr), None, None))
+        return dict(max_error=me.value, smice=sm.value, vhat=vh[..., 0] + 1j * vh[..., 1],
+                    vred=vr[..., 0] + 1j * vr[..., 1])
+
+    def ykron(self):
+        k = C.c_int32()
+        _checked(lib().okr_result_ykron(self._h, 0, None, None, C.byref(k)))
+        K = int(k.value)
+        y = np.zeros((K, K, 2))
+        pn = np.zeros(K, np.int32)
+        _checked(lib().okr_result_ykron(self._h, K, _ptr(y), _ptr(pn), C.byref(k)))
+        return y[..., 0] + 1j * y[..., 1], pn
+
+    def stats(self) -> dict:
+        c, it, sec = C.c_int64(), C.c_int32(), C.c_double()
+        _checked(lib().okr_result_stats(self._h, C.byref(c), C.byref(it), C.byref(sec)))
+        return dict(candidates=c.value, iterations=it.value, seconds=sec.value)

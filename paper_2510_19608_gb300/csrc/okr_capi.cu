@@ -66,6 +66,9 @@ struct okr_ctx {
     unsigned char *batch_host = nullptr;    // pinned staging
     size_t batch_host_cap = 0;
     int batch_config = 1;                   // team shape of the batched search: 2 CTAs per feeder (autotuned)
+    IncShape inc_shape{0, 0, 0, -1};        // launch shape of the incremental search (resolved at launch)
+    IncShape last_shape{0, 0, 0, -1};       // shape of the last incremental search, resolved
+    int last_rec = -1;                      // its record placement (-1: the sweep engine ran)
 
     // learned scorer
     MlpBufs mb;
@@ -76,12 +79,47 @@ struct okr_ctx {
     long long mlp_data_cap = 0;
     int mlp_step = 0;
 
+    // device allocator (cudaMalloc / cudaFree unless the caller registered one)
+    okr_alloc_fn alloc_fn = nullptr;
+    okr_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    long long live_allocs = 0;  // device blocks currently held
+
     // last result
     bool have_topo = false;     // T describes the feeder of the last call
     bool have_result = false;
     int n = 0, L = 0, rec_iters = 0, pf_sweeps = 0;
     Ctrl last{};
 };
+
+namespace {
+
+// Every device allocation of a context: the registered allocator, else
+// cudaMalloc.  Returns cudaErrorMemoryAllocation when it fails.
+cudaError_t dev_alloc(okr_ctx *ctx, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (ctx->alloc_fn) {
+        *p = ctx->alloc_fn(ctx->alloc_user, bytes, ctx->device, (void *)ctx->stream);
+        if (!*p) return cudaErrorMemoryAllocation;
+    } else {
+        const cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) { *p = nullptr; return e; }
+    }
+    ctx->live_allocs += 1;
+    return cudaSuccess;
+}
+
+// Frees a block of dev_alloc (NULL is ignored).  The work that used it on
+// the context's stream has finished: every entry point returns after its work.
+void dev_free(okr_ctx *ctx, void *p) {
+    if (!p) return;
+    if (ctx->free_fn) ctx->free_fn(ctx->alloc_user, p, ctx->device, (void *)ctx->stream);
+    else cudaFree(p);
+    ctx->live_allocs -= 1;
+}
+
+}  // namespace
 
 namespace {
 
@@ -104,17 +142,17 @@ okr_status fail(okr_ctx *c, okr_status s, const char *fmt, ...) {
     } while (0)
 
 void free_kron(okr_ctx *ctx) {
-    for (void *p : ctx->kron_allocs) cudaFree(p);
+    for (void *p : ctx->kron_allocs) dev_free(ctx, p);
     ctx->kron_allocs.clear();
     ctx->cap_kron_n = 0;
-    if (ctx->ykr) cudaFree(ctx->ykr);
-    if (ctx->kbig) cudaFree(ctx->kbig);
+    dev_free(ctx, ctx->ykr);
+    dev_free(ctx, ctx->kbig);
     ctx->ykr = ctx->kbig = nullptr;
     ctx->cap_ykr = ctx->cap_kbig = 0;
 }
 
 void free_batch(okr_ctx *ctx) {
-    if (ctx->batch_arena) cudaFree(ctx->batch_arena);
+    dev_free(ctx, ctx->batch_arena);
     ctx->batch_arena = nullptr;
     ctx->batch_cap = 0;
     if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
@@ -122,28 +160,28 @@ void free_batch(okr_ctx *ctx) {
     ctx->batch_host_cap = 0;
 }
 
-void free_list(std::vector<void *> &v) {
-    for (void *p : v) cudaFree(p);
+void free_list(okr_ctx *ctx, std::vector<void *> &v) {
+    for (void *p : v) dev_free(ctx, p);
     v.clear();
 }
 
 void free_mlp(okr_ctx *ctx) {
-    free_list(ctx->mlp_allocs);
-    free_list(ctx->mlp_work_allocs);
-    free_list(ctx->mlp_data_allocs);
+    free_list(ctx, ctx->mlp_allocs);
+    free_list(ctx, ctx->mlp_work_allocs);
+    free_list(ctx, ctx->mlp_data_allocs);
     ctx->mb = MlpBufs{};
     ctx->mw = MlpWork{};
     ctx->mlp_data_cap = 0;
     ctx->mlp_x = ctx->mlp_t = nullptr;
-    if (ctx->mlp_err) cudaFree(ctx->mlp_err);
+    dev_free(ctx, ctx->mlp_err);
     ctx->mlp_err = nullptr;
 }
 
 void free_all(okr_ctx *ctx) {
     free_kron(ctx);
-    if (ctx->arena) cudaFree(ctx->arena);
+    dev_free(ctx, ctx->arena);
     ctx->arena = nullptr;
-    for (void *p : ctx->work_allocs) cudaFree(p);
+    for (void *p : ctx->work_allocs) dev_free(ctx, p);
     ctx->work_allocs.clear();
     ctx->cap_chunks = 0;
     ctx->cap_n = ctx->cap_L = ctx->cap_rec = 0;
@@ -164,7 +202,7 @@ okr_status ensure_workspace(okr_ctx *ctx, int n, int L, int rec) {
     FeederBufs f;
     layout_feeder(m, n, L, rec, ctx->num_sms, 0, f);
     void *p = nullptr;
-    CK(cudaMalloc(&p, m.used));
+    CK(dev_alloc(ctx, &p, m.used));
     ctx->arena = p;
     Carver c;
     c.base = static_cast<unsigned char *>(p);
@@ -278,12 +316,13 @@ okr_status read_setup_errors(okr_ctx *ctx) {
     return OKR_OK;
 }
 
-okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
+// max_spins: polls per grid barrier of the load flow (params.max_spins; 0 = default).
+okr_status run_power_flow(okr_ctx *ctx, int n, int L, long long max_spins = 0) {
     cudaStream_t st = ctx->stream;
     Topo &T = ctx->fb.T;
     // the load flow's work buffers alias T.ihat and T.amag, which the next two kernels fill
     CK(launch_power_flow(n, L, T, ctx->fb.s_in, kPfTol, kPfMaxIter, ctx->fb.J, T.ihat, T.amag, ctx->fb.pf_iters,
-                         ctx->fb.err_dev, ctx->num_sms, st));
+                         ctx->fb.err_dev, ctx->num_sms, st, max_spins > 0 ? max_spins : kDefaultSpins));
     k_line_currents<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->fb.J);
     k_injections<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, T, ctx->fb.J);
     ctx->launches += 3;
@@ -295,14 +334,14 @@ okr_status run_power_flow(okr_ctx *ctx, int n, int L) {
 okr_status ensure_work(okr_ctx *ctx, long long chunks) {
     if (chunks <= ctx->cap_chunks) return OKR_OK;
     if (chunks > (long long)INT32_MAX / 2) return fail(ctx, OKR_EINVAL, "feeder too large for the search buffers");
-    for (void *p : ctx->work_allocs) cudaFree(p);
+    for (void *p : ctx->work_allocs) dev_free(ctx, p);
     ctx->work_allocs.clear();
     ctx->cap_chunks = 0;
     void *a = nullptr, *b = nullptr;
-    cudaError_t e = cudaMalloc(&a, sizeof(int) * (size_t)chunks);
-    if (e == cudaSuccess) e = cudaMalloc(&b, sizeof(double2) * ((size_t)chunks + 2 * (size_t)ctx->cap_n));
+    cudaError_t e = dev_alloc(ctx, &a, sizeof(int) * (size_t)chunks);
+    if (e == cudaSuccess) e = dev_alloc(ctx, &b, sizeof(double2) * ((size_t)chunks + 2 * (size_t)ctx->cap_n));
     if (e != cudaSuccess) {
-        if (a) cudaFree(a);
+        dev_free(ctx, a);
         return fail(ctx, OKR_ENOMEM, "search buffers: %s", cudaGetErrorString(e));
     }
     ctx->work_allocs.push_back(a);
@@ -323,6 +362,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p);
 
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     ctx->last_engine = resolve_engine(p);
+    ctx->last_rec = -1;
     if (ctx->last_engine == OKR_ENGINE_INCREMENTAL) return run_search_inc(ctx, p);
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
@@ -442,9 +482,19 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    const IncShape sh = inc_shape_resolve(ctx->inc_shape);
+    int rec_used = -1;
+    {
+        size_t bytes = 0;
+        if (!inc_smem(n, true, sh, &rec_used, &bytes))
+            return fail(ctx, OKR_EINVAL, "incremental search: the forced record placement does not fit shared memory "
+                                         "for %d buses", n);
+    }
+    ctx->last_shape = sh;
+    ctx->last_rec = rec_used;
     cudaEventRecord(e0, st);
     cudaError_t e = launch_search_inc(p->precision, ctx->fb.T, ctx->fb.S, X, ctx->fb.I, ctx->fb.C,
-                                      p->engine == OKR_ENGINE_VERIFY ? 1 : 0, st);
+                                      p->engine == OKR_ENGINE_VERIFY ? 1 : 0, sh, &rec_used, st);
     cudaEventRecord(e1, st);
     ctx->launches += 1;
     okr_status s = OKR_OK;
@@ -513,7 +563,7 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
         CK(cudaGetLastError());
         ctx->pf_sweeps = 0;
     } else {
-        s = run_power_flow(ctx, n, L);
+        s = run_power_flow(ctx, n, L, p->max_spins);
         if (s != OKR_OK) return s;
     }
     s = read_setup_errors(ctx);
@@ -540,13 +590,13 @@ namespace {
 
 okr_status ensure_kron_work(okr_ctx *ctx, int n) {
     if (ctx->cap_kron_n < n) {
-        for (void *q : ctx->kron_allocs) cudaFree(q);
+        for (void *q : ctx->kron_allocs) dev_free(ctx, q);
         ctx->kron_allocs.clear();
         ctx->cap_kron_n = 0;
         KronWork &W = ctx->kw;
         auto take = [&](auto **ptr, size_t count) -> cudaError_t {
             void *q = nullptr;
-            cudaError_t e = cudaMalloc(&q, sizeof(**ptr) * (count ? count : 1));
+            cudaError_t e = dev_alloc(ctx, &q, sizeof(**ptr) * (count ? count : 1));
             if (e == cudaSuccess) { ctx->kron_allocs.push_back(q); *ptr = static_cast<std::remove_reference_t<decltype(*ptr)>>(q); }
             return e;
         };
@@ -649,6 +699,19 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
         return OKR_ENOMEM;
     }
     *out = ctx;
+    return OKR_OK;
+}
+
+okr_status okr_set_allocator(okr_ctx *ctx, okr_alloc_fn alloc, okr_free_fn free_fn, void *user) {
+    if (!ctx) return OKR_EINVAL;
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(ctx, OKR_EINVAL, "allocator: give both alloc and free, or neither");
+    if (ctx->live_allocs != 0)
+        return fail(ctx, OKR_EINVAL, "allocator: the context already holds %lld device blocks (set it right after "
+                                     "okr_create)", ctx->live_allocs);
+    ctx->alloc_fn = alloc;
+    ctx->free_fn = free_fn;
+    ctx->alloc_user = user;
     return OKR_OK;
 }
 
@@ -842,17 +905,17 @@ okr_status okr_kron(okr_ctx *ctx, const uint8_t *kept, int32_t cap, double *y_ou
     }
     const size_t K = h.k_phi, need_y = K * K, need_big = (size_t)h.big_total;
     if (need_y > ctx->cap_ykr) {
-        if (ctx->ykr) cudaFree(ctx->ykr);
+        dev_free(ctx, ctx->ykr);
         ctx->ykr = nullptr;
         ctx->cap_ykr = 0;
-        CK(cudaMalloc(&ctx->ykr, sizeof(double2) * need_y));
+        CK(dev_alloc(ctx, (void **)&ctx->ykr, sizeof(double2) * need_y));
         ctx->cap_ykr = need_y;
     }
     if (need_big > ctx->cap_kbig) {
-        if (ctx->kbig) cudaFree(ctx->kbig);
+        dev_free(ctx, ctx->kbig);
         ctx->kbig = nullptr;
         ctx->cap_kbig = 0;
-        CK(cudaMalloc(&ctx->kbig, sizeof(double2) * need_big));
+        CK(dev_alloc(ctx, (void **)&ctx->kbig, sizeof(double2) * need_big));
         ctx->cap_kbig = need_big;
     }
     CK(cudaMemsetAsync(ctx->ykr, 0, sizeof(double2) * need_y, st));
@@ -909,6 +972,7 @@ okr_status batch_status_of_setup(int e) {
 // largest errors, copied back after the run) and the assignments.
 struct BatchRun {
     int nf = 0, config = 0, team = 1, max_teams = 1, maxL = 1, ctas = 0;
+    IncShape shape{0, 0, 0, -1};                    // incremental engine: launch shape (resolved)
     long long max_nn = 1, tot_n = 0;
     int per_sm[2] = {0, 0};
     std::vector<int> merges, nbus, nscen, ord[4];
@@ -946,6 +1010,7 @@ static okr_status batch_measure(okr_ctx *ctx, int32_t nf, const okr_feeder *feed
     R.nf = nf;
     R.config = config;
     R.team = 1 << config;                               // CTAs per feeder: 1, 2, 4, 8
+    R.shape = inc_shape_resolve(ctx->inc_shape);
     R.per_sm[0] = search_batch_blocks_per_sm(0);
     R.per_sm[1] = search_batch_blocks_per_sm(1);
     if (R.per_sm[0] < 1 || R.per_sm[1] < 1) return fail(ctx, OKR_ECUDA, "batched search: no CTA fits an SM");
@@ -992,6 +1057,17 @@ static okr_status batch_measure(okr_ctx *ctx, int32_t nf, const okr_feeder *feed
         std::stable_sort(R.ord[g].begin(), R.ord[g].end(), [&](int a, int b) {
             return (double)R.nbus[a] * R.merges[a] > (double)R.nbus[b] * R.merges[b];
         });
+    // the incremental launches need their shape's record placement to fit
+    for (int g = 2; g < 4; ++g) {
+        if (R.ord[g].empty()) continue;
+        int max_n = 2;
+        for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
+        int rec = 0;
+        size_t bytes = 0;
+        if (!inc_smem(max_n, false, R.shape, &rec, &bytes))
+            return fail(ctx, OKR_EINVAL, "batch: the incremental shape's record placement does not fit (%d buses; "
+                                         "the largest MICE per super-node is single-feeder only)", max_n);
+    }
     // ---- layout: [staged block: descriptors, controls, order, queues, flags, inputs] [per-feeder buffers] [outputs]
     Carver m;
     m.take(R.bs_d, nf);
@@ -1148,7 +1224,7 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
     for (int g = 2; g < 4; ++g) {
         int max_n = 2;
         for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
-        if (!R.ord[g].empty()) CK(prepare_search_inc_batch(g - 2, max_n));
+        if (!R.ord[g].empty()) CK(prepare_search_inc_batch(g - 2, max_n, R.shape));
     }
     return OKR_OK;
 }
@@ -1170,7 +1246,7 @@ static okr_status batch_enqueue(okr_ctx *ctx, BatchRun &R, cudaStream_t st, bool
             R.ctas = std::max(R.ctas, cnt);
             int max_n = 2;
             for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
-            CK(launch_search_inc_batch(g - 2, max_n, R.bf_d, R.order_d + first, cnt, st));
+            CK(launch_search_inc_batch(g - 2, max_n, R.bf_d, R.order_d + first, cnt, R.shape, st));
             continue;
         }
         const int nteams = std::min(cnt, ctx->num_sms * R.per_sm[g] / R.team);
@@ -1275,10 +1351,10 @@ static okr_status reduce_batch_impl(okr_ctx *ctx, int32_t nf, const okr_feeder *
     okr_status s = batch_measure(ctx, nf, feeders, params, n_params, config, R);
     if (s != OKR_OK) return s;
     if (R.total > ctx->batch_cap) {
-        if (ctx->batch_arena) cudaFree(ctx->batch_arena);
+        dev_free(ctx, ctx->batch_arena);
         ctx->batch_arena = nullptr;
         ctx->batch_cap = 0;
-        CK(cudaMalloc(&ctx->batch_arena, R.total));
+        CK(dev_alloc(ctx, &ctx->batch_arena, R.total));
         ctx->batch_cap = R.total;
     }
     // host block: staged inputs, then the result area and the assignments
@@ -1311,7 +1387,7 @@ struct okr_batch_plan {
     ~okr_batch_plan() {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
-        if (arena) cudaFree(arena);
+        if (arena) dev_free(ctx, arena);
         if (host) cudaFreeHost(host);
     }
 };
@@ -1365,7 +1441,7 @@ okr_status okr_batch_plan_create(okr_ctx *ctx, int32_t n_feeders, const okr_feed
     P->ctx = ctx;
     okr_status s = batch_measure(ctx, n_feeders, feeders, params, n_params, ctx->batch_config, P->R);
     cudaError_t e = cudaSuccess;
-    if (s == OKR_OK) e = cudaMalloc(&P->arena, P->R.total);
+    if (s == OKR_OK) e = dev_alloc(ctx, &P->arena, P->R.total);
     if (s == OKR_OK && e == cudaSuccess) e = cudaMallocHost((void **)&P->host, P->R.host_bytes);
     if (s == OKR_OK && e != cudaSuccess) s = fail(ctx, OKR_ENOMEM, "batch plan: %s", cudaGetErrorString(e));
     if (s == OKR_OK) {
@@ -1464,6 +1540,37 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->rechecks = ctx->last.rechecks;
     out->recheck_cands = ctx->last.recheck_cands;
     for (int i = 0; i < 16; ++i) out->phase_ms[i] = ctx->last.profile ? 1e-6 * (double)ctx->last.phase_ns[i] : 0.0;
+    const bool inc = ctx->last_engine == OKR_ENGINE_INCREMENTAL && ctx->last_rec >= 0;
+    out->inc_threads = inc ? ctx->last_shape.threads : 0;
+    out->inc_eval_warps = inc ? ctx->last_shape.cw : 0;
+    out->inc_shared_entries = inc ? ctx->last_shape.se : 0;
+    out->inc_records = inc ? ctx->last_rec + 1 : 0;
+    return OKR_OK;
+}
+
+okr_status okr_set_inc_shape(okr_ctx *ctx, const okr_inc_shape *shape) {
+    if (!ctx) return OKR_EINVAL;
+    if (!shape) {
+        ctx->inc_shape = IncShape{0, 0, 0, -1};
+        return OKR_OK;
+    }
+    const int t = shape->threads, w = shape->eval_warps, e = shape->shared_entries, r = shape->records;
+    if (t != 0 && t != 256 && t != 512) return fail(ctx, OKR_EINVAL, "inc shape: threads %d (0, 256 or 512)", t);
+    const int nw = (t == 0 ? kIncDefaultThreads : t) / 32;
+    if (w < 0 || w > nw - 1) return fail(ctx, OKR_EINVAL, "inc shape: eval_warps %d outside [0, %d]", w, nw - 1);
+    if (e < 0 || e > 256) return fail(ctx, OKR_EINVAL, "inc shape: shared_entries %d outside [0, 256]", e);
+    if (r < 0 || r > 3) return fail(ctx, OKR_EINVAL, "inc shape: records %d outside [0, 3]", r);
+    ctx->inc_shape = IncShape{t, w, e, r - 1};
+    return OKR_OK;
+}
+
+okr_status okr_get_inc_shape(const okr_ctx *ctx, okr_inc_shape *shape) {
+    if (!ctx || !shape) return OKR_EINVAL;
+    const IncShape sh = inc_shape_resolve(ctx->inc_shape);
+    shape->threads = sh.threads;
+    shape->eval_warps = sh.cw;
+    shape->shared_entries = sh.se;
+    shape->records = sh.rec + 1;
     return OKR_OK;
 }
 
@@ -1498,6 +1605,132 @@ okr_status okr_get_voltages(const okr_ctx *ctx, double *vhat, double *vred) {
     const size_t bytes = sizeof(double) * 6 * ctx->L * ctx->n;
     if (vhat && cudaMemcpy(vhat, ctx->fb.vhat_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
     if (vred && cudaMemcpy(vred, ctx->fb.vred_out, bytes, cudaMemcpyDeviceToHost) != cudaSuccess) return OKR_ECUDA;
+    return OKR_OK;
+}
+
+}  // extern "C"
+
+// A reduction's results copied out of its context (host memory, owned by the
+// object): later calls on the context leave them alone.
+struct okr_result {
+    int n = 0, L = 0, t = 0, k_phi = -1;   // k_phi < 0: Y_Kron not taken
+    okr_summary summary{};
+    std::vector<int32_t> super_of, dec_s, dec_r, dec_ncand, phase_node;
+    std::vector<double> dec_score, dec_maxerr, dec_gap, vhat, vred, ykron;
+};
+
+extern "C" {
+
+okr_status okr_result_take(okr_ctx *ctx, int32_t with_ykron, okr_result **out) {
+    if (!ctx || !out) return OKR_EINVAL;
+    *out = nullptr;
+    if (!ctx->have_result) return fail(ctx, OKR_ENOTREADY, "no reduction to take results from");
+    okr_result *R = new (std::nothrow) okr_result;
+    if (!R) return fail(ctx, OKR_ENOMEM, "result: out of host memory");
+    okr_status s = OKR_OK;
+    try {
+        s = okr_get_summary(ctx, &R->summary);
+        R->n = ctx->n;
+        R->L = ctx->L;
+        R->t = ctx->last.t;
+        const size_t t = R->t > 0 ? (size_t)R->t : 1, nv = (size_t)6 * R->L * R->n;
+        R->super_of.assign(R->n, 0);
+        R->dec_s.assign(t, 0);
+        R->dec_r.assign(t, 0);
+        R->dec_ncand.assign(t, 0);
+        R->dec_score.assign(t, 0.0);
+        R->dec_maxerr.assign(t, 0.0);
+        R->dec_gap.assign(t, 0.0);
+        R->vhat.assign(nv, 0.0);
+        R->vred.assign(nv, 0.0);
+        if (s == OKR_OK) s = okr_get_assignment(ctx, R->super_of.data());
+        if (s == OKR_OK)
+            s = okr_get_decisions(ctx, R->t, R->dec_s.data(), R->dec_r.data(), R->dec_score.data(),
+                                  R->dec_maxerr.data(), R->dec_gap.data(), R->dec_ncand.data());
+        if (s == OKR_OK) s = okr_get_voltages(ctx, R->vhat.data(), R->vred.data());
+        if (s == OKR_OK && with_ykron) {
+            int32_t k = 0;
+            s = okr_kron(ctx, nullptr, 0, nullptr, nullptr, &k);
+            if (s == OKR_OK) {
+                R->ykron.assign((size_t)2 * k * k, 0.0);
+                R->phase_node.assign(k > 0 ? k : 1, 0);
+                s = okr_kron(ctx, nullptr, k, R->ykron.data(), R->phase_node.data(), &k);
+                R->k_phi = k;
+                R->summary.kron_ms = ctx->kron_ms;
+            }
+        }
+    } catch (const std::bad_alloc &) {
+        s = fail(ctx, OKR_ENOMEM, "result: out of host memory");
+    }
+    if (s != OKR_OK) {
+        delete R;
+        return s;
+    }
+    *out = R;
+    return OKR_OK;
+}
+
+void okr_result_free(okr_result *res) { delete res; }
+
+okr_status okr_result_summary(const okr_result *res, okr_summary *out) {
+    if (!res || !out) return OKR_EINVAL;
+    *out = res->summary;
+    return OKR_OK;
+}
+
+okr_status okr_result_assignment(const okr_result *res, int32_t *super_of, int32_t *n_bus, int32_t *n_kept) {
+    if (!res) return OKR_EINVAL;
+    if (n_bus) *n_bus = res->n;
+    if (n_kept) *n_kept = res->n - res->t;
+    if (super_of) std::memcpy(super_of, res->super_of.data(), sizeof(int32_t) * res->n);
+    return OKR_OK;
+}
+
+okr_status okr_result_decisions(const okr_result *res, int32_t cap, int32_t *s, int32_t *r, double *smice,
+                                double *max_error, double *gap, int32_t *ncand, int32_t *count) {
+    if (!res || cap < 0) return OKR_EINVAL;
+    if (count) *count = res->t;
+    const size_t k = (size_t)(res->t < cap ? res->t : cap);
+    if (k == 0) return OKR_OK;
+    if (s) std::memcpy(s, res->dec_s.data(), sizeof(int32_t) * k);
+    if (r) std::memcpy(r, res->dec_r.data(), sizeof(int32_t) * k);
+    if (smice) std::memcpy(smice, res->dec_score.data(), sizeof(double) * k);
+    if (max_error) std::memcpy(max_error, res->dec_maxerr.data(), sizeof(double) * k);
+    if (gap) std::memcpy(gap, res->dec_gap.data(), sizeof(double) * k);
+    if (ncand) std::memcpy(ncand, res->dec_ncand.data(), sizeof(int32_t) * k);
+    return OKR_OK;
+}
+
+okr_status okr_result_errors(const okr_result *res, double *max_error, double *smice, double *vhat, double *vred,
+                             int32_t *n_scen, int32_t *n_bus) {
+    if (!res) return OKR_EINVAL;
+    if (max_error) *max_error = res->summary.max_error;
+    if (smice) *smice = res->summary.smice;
+    if (n_scen) *n_scen = res->L;
+    if (n_bus) *n_bus = res->n;
+    const size_t nv = (size_t)6 * res->L * res->n;
+    if (vhat) std::memcpy(vhat, res->vhat.data(), sizeof(double) * nv);
+    if (vred) std::memcpy(vred, res->vred.data(), sizeof(double) * nv);
+    return OKR_OK;
+}
+
+okr_status okr_result_ykron(const okr_result *res, int32_t cap, double *y, int32_t *phase_node, int32_t *k_phi) {
+    if (!res || !k_phi) return OKR_EINVAL;
+    if (res->k_phi < 0) return OKR_ENOTREADY;
+    *k_phi = res->k_phi;
+    if (!y && !phase_node) return OKR_OK;
+    if (cap < res->k_phi) return OKR_EINVAL;
+    const size_t K = res->k_phi;
+    if (y && K) std::memcpy(y, res->ykron.data(), sizeof(double) * 2 * K * K);
+    if (phase_node && K) std::memcpy(phase_node, res->phase_node.data(), sizeof(int32_t) * K);
+    return OKR_OK;
+}
+
+okr_status okr_result_stats(const okr_result *res, int64_t *candidates, int32_t *iterations, double *seconds) {
+    if (!res) return OKR_EINVAL;
+    if (candidates) *candidates = res->summary.candidates;
+    if (iterations) *iterations = res->summary.n_iter;
+    if (seconds) *seconds = 1e-3 * res->summary.search_ms;
     return OKR_OK;
 }
 
@@ -1542,28 +1775,28 @@ okr_status okr_get_recorded(const okr_ctx *ctx, int32_t iter, int32_t cap, int32
 namespace {
 
 template <typename T>
-cudaError_t grab(std::vector<void *> &list, T **p, size_t count) {
+cudaError_t grab(okr_ctx *ctx, std::vector<void *> &list, T **p, size_t count) {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, sizeof(T) * (count ? count : 1));
+    cudaError_t e = dev_alloc(ctx, &q, sizeof(T) * (count ? count : 1));
     if (e == cudaSuccess) { list.push_back(q); *p = static_cast<T *>(q); }
     return e;
 }
 
 okr_status mlp_ensure_work(okr_ctx *ctx, int N) {
     if (N <= ctx->mw.cap) return OKR_OK;
-    free_list(ctx->mlp_work_allocs);
+    free_list(ctx, ctx->mlp_work_allocs);
     ctx->mw = MlpWork{};
     MlpWork &w = ctx->mw;
     const size_t NH = (size_t)N * kMlpHidden;
-    CK(grab(ctx->mlp_work_allocs, &w.h1, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.h2, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.h3, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.d1, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.d2, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.d3, NH));
-    CK(grab(ctx->mlp_work_allocs, &w.y, (size_t)N));
-    CK(grab(ctx->mlp_work_allocs, &w.dy, (size_t)N));
-    CK(grab(ctx->mlp_work_allocs, &w.part, (size_t)mlp_segments(N) * (kMlpHidden + 1) * kMlpHidden));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.h1, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.h2, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.h3, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.d1, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.d2, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.d3, NH));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.y, (size_t)N));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.dy, (size_t)N));
+    CK(grab(ctx, ctx->mlp_work_allocs, &w.part, (size_t)mlp_segments(N) * (kMlpHidden + 1) * kMlpHidden));
     w.cap = N;
     return OKR_OK;
 }
@@ -1571,10 +1804,10 @@ okr_status mlp_ensure_work(okr_ctx *ctx, int N) {
 okr_status mlp_upload(okr_ctx *ctx, const float *x, const float *t, long long N) {
     const int F = ctx->mb.F;
     if (N > ctx->mlp_data_cap) {
-        free_list(ctx->mlp_data_allocs);
+        free_list(ctx, ctx->mlp_data_allocs);
         ctx->mlp_data_cap = 0;
-        CK(grab(ctx->mlp_data_allocs, &ctx->mlp_x, (size_t)N * F));
-        CK(grab(ctx->mlp_data_allocs, &ctx->mlp_t, (size_t)N));
+        CK(grab(ctx, ctx->mlp_data_allocs, &ctx->mlp_x, (size_t)N * F));
+        CK(grab(ctx, ctx->mlp_data_allocs, &ctx->mlp_t, (size_t)N));
         ctx->mlp_data_cap = N;
     }
     CK(cudaMemcpyAsync(ctx->mlp_x, x, sizeof(float) * (size_t)N * F, cudaMemcpyHostToDevice, ctx->stream));
@@ -1606,14 +1839,14 @@ okr_status okr_scorer_init(okr_ctx *ctx, int32_t n_features, const float *theta)
     MlpBufs &b = ctx->mb;
     b.F = n_features;
     const int P = mlp_param_count(n_features);
-    CK(grab(ctx->mlp_allocs, &b.theta, (size_t)P));
-    CK(grab(ctx->mlp_allocs, &b.grad, (size_t)P));
-    CK(grab(ctx->mlp_allocs, &b.m, (size_t)P));
-    CK(grab(ctx->mlp_allocs, &b.v, (size_t)P));
-    CK(grab(ctx->mlp_allocs, &b.w1, (size_t)kMlpMaxF * kMlpHidden));
-    CK(grab(ctx->mlp_allocs, &b.w2, (size_t)kMlpHidden * kMlpHidden));
-    CK(grab(ctx->mlp_allocs, &b.w3, (size_t)kMlpHidden * kMlpHidden));
-    CK(grab(ctx->mlp_allocs, &b.w4, (size_t)kMlpHidden));
+    CK(grab(ctx, ctx->mlp_allocs, &b.theta, (size_t)P));
+    CK(grab(ctx, ctx->mlp_allocs, &b.grad, (size_t)P));
+    CK(grab(ctx, ctx->mlp_allocs, &b.m, (size_t)P));
+    CK(grab(ctx, ctx->mlp_allocs, &b.v, (size_t)P));
+    CK(grab(ctx, ctx->mlp_allocs, &b.w1, (size_t)kMlpMaxF * kMlpHidden));
+    CK(grab(ctx, ctx->mlp_allocs, &b.w2, (size_t)kMlpHidden * kMlpHidden));
+    CK(grab(ctx, ctx->mlp_allocs, &b.w3, (size_t)kMlpHidden * kMlpHidden));
+    CK(grab(ctx, ctx->mlp_allocs, &b.w4, (size_t)kMlpHidden));
     cudaStream_t st = ctx->stream;
     if (theta) CK(cudaMemcpyAsync(b.theta, theta, sizeof(float) * P, cudaMemcpyHostToDevice, st));
     else CK(cudaMemsetAsync(b.theta, 0, sizeof(float) * P, st));
@@ -1689,7 +1922,7 @@ okr_status okr_scorer_predict_tc(okr_ctx *ctx, const float *x, int64_t n, float 
     okr_status s = mlp_upload(ctx, x, nullptr, n);
     if (s != OKR_OK) return s;
     float *yd = ctx->mlp_t;                     // the targets' buffer holds the predictions
-    if (!ctx->mlp_err) CK(cudaMalloc(&ctx->mlp_err, sizeof(int)));
+    if (!ctx->mlp_err) CK(dev_alloc(ctx, (void **)&ctx->mlp_err, sizeof(int)));
     int *err = ctx->mlp_err;
     okr_status out = OKR_OK;
     cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), ctx->stream);

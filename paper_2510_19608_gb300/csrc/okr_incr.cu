@@ -66,7 +66,6 @@ constexpr int kFxShift = 100;               // fixed point: value * 2^100
 constexpr u128 kSignBit = (u128)1 << 127;
 constexpr u128 kNone = ~(u128)0;
 constexpr float kU32 = 5.9604645e-08f;      // 2^-24
-constexpr int kTE = 512;                    // largest tile of work entries (one per thread)
 
 __device__ __forceinline__ unsigned long long gtimer_inc() {
     unsigned long long t;
@@ -834,16 +833,17 @@ __device__ __forceinline__ Cand entry_cand(const IncWork &w) {
     return c;
 }
 
-// Where one search keeps its per-merge data: the first kSE work entries, the
-// super-node lists (16-bit, by merge parity) and the phase masks in shared
-// memory; further entries in global memory.
-constexpr int kSE = 256;
+// Where one search keeps its per-merge data: the first `se` work entries
+// (at most kSEMax), the super-node lists (16-bit, by merge parity) and the
+// phase masks in shared memory; further entries in global memory.
+constexpr int kSEMax = 256;
 struct Loc {
     IncWork *wsm, *wgl;
+    int se;                     // work entries in shared memory
     unsigned short *lst[2];
     const uint8_t *ph;
     int *rank;                  // [n + 1] rank of each bus's super-node among the super-nodes
-    __device__ __forceinline__ IncWork *ent(int i) const { return i < kSE ? wsm + i : wgl + (i - kSE); }
+    __device__ __forceinline__ IncWork *ent(int i) const { return i < se ? wsm + i : wgl + (i - se); }
 };
 
 // ---------------------------------------------------------------- evaluation of work entries
@@ -854,10 +854,12 @@ enum Pass {
     kF64 = 3        // FP64, every term on the stored state, into vacc / vviol
 };
 
+// One tile of NT work entries (one per thread): their sums and offsets.
+template <int NT>
 struct EvalSmem {
-    unsigned long long dlo[kTE], dhi[kTE], blo[kTE], bhi[kTE];
-    int n1[kTE], n2[kTE];
-    int off[kTE + 1];
+    unsigned long long dlo[NT], dhi[NT], blo[NT], bhi[NT];
+    int n1[NT], n2[NT];
+    int off[NT + 1];
 };
 
 // Per-slot selection records (shared memory when they fit, else global):
@@ -999,7 +1001,7 @@ template <int NT, int PREC>
 __device__ __noinline__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
                                  double margin, float mlo, float mhi, int e0, int e1, int pass,
                                  const unsigned short *list_pre, const unsigned short *list_post, int rstar,
-                                 const Ovl O, EvalSmem &E, int *sscan, const Rec &R, const Loc &Lc,
+                                 const Ovl O, EvalSmem<NT> &E, int *sscan, const Rec &R, const Loc &Lc,
                                  unsigned long long *prof = nullptr, bool last_barrier = true) {
     // the states every group evaluates (the same for the whole pass)
     const int st_lo = (pass == kFresh) ? 1 : 0, st_hi = (pass == kMerge || pass == kFresh) ? 2 : 1;
@@ -1230,16 +1232,18 @@ __host__ __device__ constexpr size_t rec_maxm_bytes(int n) { return rec_bytes(n)
 // masks][overlay map][super-node ranks], then the selection records when they
 // fit.
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
-__host__ __device__ constexpr size_t base_bytes(int n) {
-    return (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n) +
+// The entries' region is rounded up to 16 bytes: the selection records after
+// the base are 16-byte keys.
+__host__ __device__ constexpr size_t base_bytes(int n, int se) {
+    return align16((size_t)se * sizeof(IncWork)) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n) +
            align16((size_t)4 * (n + 1));
 }
 
 template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
-                        unsigned char *dyn, int rec_mode) {
-    static_assert(NT >= 128 && NT <= kTE, "thread count");
-    __shared__ __align__(16) EvalSmem E;
+                        unsigned char *dyn, int rec_mode, int se, int cw) {
+    static_assert(NT >= 128 && NT <= 1024 && NT % 32 == 0, "thread count");
+    __shared__ __align__(16) EvalSmem<NT> E;
     __shared__ __align__(16) Red sred[33];
     __shared__ __align__(16) Red64 s_sel[2];   // precision-1 selection accumulators: pass A, pass B
     __shared__ int sscan[33];
@@ -1260,9 +1264,10 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     Loc Lc;
     Lc.wsm = reinterpret_cast<IncWork *>(dyn);
     Lc.wgl = I.work;
-    Lc.lst[0] = reinterpret_cast<unsigned short *>(dyn + (size_t)kSE * sizeof(IncWork));
+    Lc.se = se;
+    Lc.lst[0] = reinterpret_cast<unsigned short *>(dyn + align16((size_t)se * sizeof(IncWork)));
     Lc.lst[1] = Lc.lst[0] + n;
-    uint8_t *phs = dyn + (size_t)kSE * sizeof(IncWork) + align16((size_t)4 * n);
+    uint8_t *phs = dyn + align16((size_t)se * sizeof(IncWork)) + align16((size_t)4 * n);
     Lc.ph = phs;
     unsigned short *ovl_map = reinterpret_cast<unsigned short *>(phs + align16((size_t)n));
     // the super-node ranks live in shared memory during the search (copied back at the end)
@@ -1273,7 +1278,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     O.cbuf = I.cbuf;
     O.s = O.r = -1;
     O.nfree = 0;
-    unsigned char *recmem = rec_mode ? dyn + base_bytes(n) : I.recbuf;
+    unsigned char *recmem = rec_mode ? dyn + base_bytes(n, se) : I.recbuf;
     Rec R;
     R.r0 = reinterpret_cast<u128 *>(recmem);
     R.r1 = reinterpret_cast<ulonglong2 *>(recmem);
@@ -1358,6 +1363,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             ra.i = r6.i;
         }
         const int nvalid = ra.i;
+        stamp(11);                                      // profile: pass A
         if (tid == 0) {
             cands_run += nvalid;
             X.dec_ncand[t] = nvalid;
@@ -1505,7 +1511,8 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         // subtree and the decision's bus ids are looked up in the merge step);
         // the warps that evaluate the merge build their own at once, without
         // waiting (every thread knows ws).
-        constexpr int NW = NT / 32, CW = 4;
+        constexpr int NW = NT / 32;
+        const int CW = cw;                  // warps that evaluate the merge (1 .. NW - 1)
         const bool commit_warp = (tid >> 5) >= NW - CW;
         Win hw;
         if (commit_warp) {
@@ -1519,6 +1526,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
             first_threads_sync((NW - CW) * 32);
             hw = h;
+            stamp(12);                                  // profile: the scan warps' wait for the winner's record
         }
         O.s = hw.s;
         O.r = hw.r;
@@ -1723,20 +1731,23 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     }
 }
 
+namespace {
+
 // Per-merge data in dynamic shared memory; rec_mode 0: the selection records
 // in I.recbuf; 1: in shared memory; 2: in shared memory, with the largest MICE
-// per super-node.
+// per super-node.  se: work entries in shared memory; cw: warps that evaluate
+// the merge beside the changed-set scan.
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
-                                                      int rec_mode) {
+                                                      int rec_mode, int se, int cw) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
-    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode);
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode, se, cw);
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf,
-                                                         int rec_mode) {
+                                                         int rec_mode, int se, int cw) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
     __shared__ Topo sT;
     __shared__ State sS;
@@ -1754,7 +1765,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode, se, cw);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -1763,8 +1774,6 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     }
 }
 
-constexpr int kIncThreads = 512;            // one feeder on one SM
-constexpr int kIncBatchThreads = 512;       // batches: one feeder per CTA
 constexpr size_t kIncSmemMax = 200 * 1024;  // largest dynamic shared memory of one search
 
 template <typename K>
@@ -1772,47 +1781,89 @@ cudaError_t set_smem(K kern, size_t bytes) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-// Dynamic shared memory for an n-bus feeder: the per-merge data always, the
-// selection records (and, when `maxm`, the largest MICE per super-node) when
-// the total stays within kIncSmemMax.  *rec_mode as k_search_inc takes it.
-static size_t inc_smem(int n, bool maxm, int *rec_mode) {
-    const size_t base = base_bytes(n);
-    if (maxm && base + rec_maxm_bytes(n) <= kIncSmemMax) {
-        *rec_mode = 2;
-        return base + rec_maxm_bytes(n);
-    }
-    *rec_mode = base + rec_bytes(n) <= kIncSmemMax ? 1 : 0;
-    return *rec_mode ? base + rec_bytes(n) : base;
+}  // namespace
+
+IncShape inc_shape_resolve(IncShape sh) {
+    if (sh.threads != 256 && sh.threads != 512) sh.threads = kIncDefaultThreads;
+    const int nw = sh.threads / 32;
+    if (sh.cw < 1 || sh.cw > nw - 1) sh.cw = sh.threads == 256 ? 2 : 4;
+    if (sh.se < 1 || sh.se > kSEMax) sh.se = kSEMax;
+    if (sh.rec < -1 || sh.rec > 2) sh.rec = -1;
+    return sh;
 }
 
-cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st) {
-    int use = 0;
-    const size_t smem = inc_smem(T.n, true, &use);
-    cudaError_t e;
-    if (precision == 1) {
-        e = set_smem(k_search_inc<kIncThreads, 1>, smem);
-        if (e == cudaSuccess) k_search_inc<kIncThreads, 1><<<1, kIncThreads, smem, st>>>(T, S, X, I, C, verify, use);
-    } else {
-        e = set_smem(k_search_inc<kIncThreads, 0>, smem);
-        if (e == cudaSuccess) k_search_inc<kIncThreads, 0><<<1, kIncThreads, smem, st>>>(T, S, X, I, C, verify, use);
-    }
+// Dynamic shared memory for an n-bus feeder: the per-merge data always, the
+// selection records (and, when `maxm`, the largest MICE per super-node) when
+// the total stays within kIncSmemMax, or where sh.rec places them.  Returns
+// false when a forced placement does not fit (or asks for the per-super-node
+// maximum where `maxm` is false).
+bool inc_smem(int n, bool maxm, const IncShape &sh, int *rec_mode, size_t *bytes) {
+    const size_t base = base_bytes(n, sh.se);
+    const bool fit2 = maxm && base + rec_maxm_bytes(n) <= kIncSmemMax;
+    const bool fit1 = base + rec_bytes(n) <= kIncSmemMax;
+    int m = sh.rec;
+    if (m < 0) m = fit2 ? 2 : (fit1 ? 1 : 0);
+    if ((m == 2 && !fit2) || (m == 1 && !fit1) || base > kIncSmemMax) return false;
+    *rec_mode = m;
+    *bytes = m == 2 ? base + rec_maxm_bytes(n) : (m == 1 ? base + rec_bytes(n) : base);
+    return true;
+}
+
+namespace {
+
+template <int NT, int PREC>
+cudaError_t launch_one(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, int use, size_t smem, const IncShape &sh,
+                       cudaStream_t st) {
+    cudaError_t e = set_smem(k_search_inc<NT, PREC>, smem);
+    if (e == cudaSuccess) k_search_inc<NT, PREC><<<1, NT, smem, st>>>(T, S, X, I, C, verify, use, sh.se, sh.cw);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-cudaError_t prepare_search_inc_batch(int precision, int max_n) {
+template <int NT>
+cudaError_t set_batch_smem(int precision, size_t smem) {
+    return precision == 1 ? set_smem(k_search_inc_batch<NT, 1>, smem) : set_smem(k_search_inc_batch<NT, 0>, smem);
+}
+
+template <int NT>
+void launch_batch(int precision, const BatchFeeder *fd, const int *order, int nf, int use, size_t smem,
+                  const IncShape &sh, cudaStream_t st) {
+    if (precision == 1) k_search_inc_batch<NT, 1><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw);
+    else k_search_inc_batch<NT, 0><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw);
+}
+
+}  // namespace
+
+cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, IncShape sh,
+                              int *rec_used, cudaStream_t st) {
+    sh = inc_shape_resolve(sh);
     int use = 0;
-    const size_t smem = inc_smem(max_n, false, &use);
-    return precision == 1 ? set_smem(k_search_inc_batch<kIncBatchThreads, 1>, smem)
-                          : set_smem(k_search_inc_batch<kIncBatchThreads, 0>, smem);
+    size_t smem = 0;
+    if (!inc_smem(T.n, true, sh, &use, &smem)) return cudaErrorInvalidValue;
+    if (rec_used) *rec_used = use;
+    if (sh.threads == 256)
+        return precision == 1 ? launch_one<256, 1>(T, S, X, I, C, verify, use, smem, sh, st)
+                              : launch_one<256, 0>(T, S, X, I, C, verify, use, smem, sh, st);
+    return precision == 1 ? launch_one<512, 1>(T, S, X, I, C, verify, use, smem, sh, st)
+                          : launch_one<512, 0>(T, S, X, I, C, verify, use, smem, sh, st);
+}
+
+cudaError_t prepare_search_inc_batch(int precision, int max_n, IncShape sh) {
+    sh = inc_shape_resolve(sh);
+    int use = 0;
+    size_t smem = 0;
+    if (!inc_smem(max_n, false, sh, &use, &smem)) return cudaErrorInvalidValue;
+    return sh.threads == 256 ? set_batch_smem<256>(precision, smem) : set_batch_smem<512>(precision, smem);
 }
 
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
-                                    cudaStream_t st) {
+                                    IncShape sh, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
+    sh = inc_shape_resolve(sh);
     int use = 0;
-    const size_t smem = inc_smem(max_n, false, &use);
-    if (precision == 1) k_search_inc_batch<kIncBatchThreads, 1><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
-    else k_search_inc_batch<kIncBatchThreads, 0><<<nf, kIncBatchThreads, smem, st>>>(fd, order, nf, use);
+    size_t smem = 0;
+    if (!inc_smem(max_n, false, sh, &use, &smem)) return cudaErrorInvalidValue;
+    if (sh.threads == 256) launch_batch<256>(precision, fd, order, nf, use, smem, sh, st);
+    else launch_batch<512>(precision, fd, order, nf, use, smem, sh, st);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,10 @@ cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sm
 // load flow of every scenario (cooperative launch).  J: [L*3n] line currents,
 // W: [L*3n] work (its contents are overwritten), red: [3L+1] doubles of
 // reduction slots and barrier counter (cleared by the launch), iters: [L].
+// Each grid barrier polls at most max_spins times (> 0), then sets err = 6.
 cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double tol, int max_iter, double2 *J,
-                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st);
+                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st,
+                              long long max_spins);
 __global__ void k_line_currents(int n, int L, Topo T, double2 *J);
 __global__ void k_injections(int n, int L, Topo T, const double2 *__restrict__ J);
 __global__ void k_import_ops(int n, int L, Topo T, const double *__restrict__ vh, const double *__restrict__ ih);
@@ -140,12 +142,33 @@ __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, dou
 // okr_incr.cu -- the search with scores carried across iterations: one CTA per
 // feeder (verify = 1: every merge also re-evaluates every candidate and counts
 // mismatches of the carried scores in C->inc_mismatch).
-cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, cudaStream_t st);
+//
+// Launch shape of that CTA: threads (256 or 512), warps that evaluate the
+// merge beside the changed-set scan (cw, 1 .. threads/32 - 1), work entries in
+// shared memory (se, 1 .. 256; the rest in device memory) and where the
+// selection records live (rec: -1 automatic, 0 device memory, 1 shared memory,
+// 2 shared memory with the largest MICE per super-node; batches take 0 or 1).
+// Every shape gives the same results.
+struct IncShape {
+    int threads, cw, se, rec;
+};
+constexpr int kIncDefaultThreads = 512;
+// Out-of-range fields replaced by the defaults (512 threads, 4 evaluation
+// warps (2 with 256 threads), 256 shared entries, automatic records).
+IncShape inc_shape_resolve(IncShape sh);
+// Dynamic shared memory and record placement of one search; false when a
+// forced placement does not fit.
+bool inc_smem(int n, bool maxm, const IncShape &sh, int *rec_mode, size_t *bytes);
+// cudaErrorInvalidValue when the shape's forced record placement does not fit;
+// *rec_used (may be NULL): the placement that ran.
+cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, Ctrl *C, int verify, IncShape sh,
+                              int *rec_used, cudaStream_t st);
 // Many feeders: one CTA each, in the order given (prepare_search_inc_batch with
-// the same precision and at least the same largest feeder first: it sets the
-// kernel's shared-memory attribute, which a stream capture must not see).
-cudaError_t prepare_search_inc_batch(int precision, int max_n);
+// the same precision, shape and at least the same largest feeder first: it
+// sets the kernel's shared-memory attribute, which a stream capture must not
+// see).
+cudaError_t prepare_search_inc_batch(int precision, int max_n, IncShape sh);
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
-                                    cudaStream_t st);
+                                    IncShape sh, cudaStream_t st);
 
 }  // namespace okr

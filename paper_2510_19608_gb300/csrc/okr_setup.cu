@@ -377,7 +377,6 @@ cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sm
 // The arithmetic is the same, operation for operation, as a one-thread-per-bus
 // sweep.
 constexpr int kPfShared = 2048;     // buses whose (l, p) slice is staged in shared memory
-constexpr long long kPfSpins = 4000000;
 
 __device__ __forceinline__ unsigned pf_ld_acquire(const unsigned *p) {
     unsigned v;
@@ -385,9 +384,9 @@ __device__ __forceinline__ unsigned pf_ld_acquire(const unsigned *p) {
     return v;
 }
 
-// Grid barrier on a monotonic counter; bounded: returns false (and sets
-// err = 6) when the wait gives up or another CTA already gave up.
-__device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsigned &epoch) {
+// Grid barrier on a monotonic counter; bounded by max_spins polls: returns
+// false (and sets err = 6) when the wait gives up or another CTA already gave up.
+__device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsigned &epoch, long long max_spins) {
     __shared__ int s_ok;
     __syncthreads();
     epoch += 1;
@@ -398,7 +397,7 @@ __device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsign
         int ok = 1;
         long long spins = 0;
         while (pf_ld_acquire(count) < target) {
-            if (++spins > kPfSpins || *(volatile int *)err == 6) { ok = 0; break; }
+            if (++spins > max_spins || *(volatile int *)err == 6) { ok = 0; break; }
             __nanosleep(20);
         }
         if (!ok) atomicExch(err, 6);
@@ -411,7 +410,7 @@ __device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsign
 
 __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const double *__restrict__ s_in, double tol,
                                                     int max_iter, double2 *J, double2 *W, double *red, unsigned *bar,
-                                                    int *iters, int *err) {
+                                                    int *iters, int *err, long long max_spins) {
     extern __shared__ double2 pf_sm[];
     __shared__ int s_live[kMaxScen];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -432,7 +431,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     bool conv_all = false;
     int it;
     for (it = 1; it <= max_iter; ++it) {
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         if (gt == 0) for (int l = 0; l < L; ++l) red[((it + 1) % 3) * L + l] = 0.0;
         // S1: load currents
         for (size_t e = gt; e < tot; e += gs) {
@@ -446,7 +445,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
             }
             W[e] = j;
         }
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         // S2: line currents, deepest level first
         if (line_cta && s_live[ll]) {
             const size_t off = ((size_t)ll * 3 + lp) * n;
@@ -469,7 +468,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
             if (loc)
                 for (int v = tid; v < n; v += nt) J[off + v] = loc[v];
         }
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         // S3: drops z J on the phases of each line (root excluded)
         for (size_t e = gt; e < tot; e += gs) {
             const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
@@ -482,7 +481,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
                         drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], J[(size_t)l * N3 + (size_t)q * n + v]));
             W[e] = drop;
         }
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         // S4: new voltages, top down (Vn overwrites D)
         if (line_cta && s_live[ll]) {
             const size_t off = ((size_t)ll * 3 + lp) * n;
@@ -502,7 +501,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
             if (loc)
                 for (int v = tid; v < n; v += nt) W[off + v] = loc[v];
         }
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         // S5: change of the voltages, per-scenario maximum
         double mx[kMaxScen] = {0.0, 0.0, 0.0, 0.0};
         for (size_t e = gt; e < tot; e += gs) {
@@ -524,7 +523,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
             if ((tid & 31) == 0 && m > 0.0)
                 atomicMax((unsigned long long *)&red[(it % 3) * L + l], (unsigned long long)__double_as_longlong(m));
         }
-        if (!pf_grid_sync(bar, err, G, epoch)) return;
+        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         conv_all = true;
         __syncthreads();
         if (tid < L && s_live[tid]) {
@@ -547,7 +546,8 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
 // Blocks of the cooperative load flow: enough for the grid-wide stages, at
 // least one per (scenario, phase), at most one per SM.
 cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double tol, int max_iter, double2 *J,
-                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st) {
+                              double2 *W, double *red, int *iters, int *err, int num_sms, cudaStream_t st,
+                              long long max_spins) {
     int G = (int)(((size_t)3 * L * n + 127) / 128);
     if (G < 3 * L) G = 3 * L;
     if (G > num_sms) G = num_sms;
@@ -555,7 +555,7 @@ cudaError_t launch_power_flow(int n, int L, Topo T, const double *s_in, double t
     unsigned *bar = reinterpret_cast<unsigned *>(red + 3 * L);
     cudaError_t e = cudaMemsetAsync(red, 0, sizeof(double) * (3 * L + 1), st);
     if (e != cudaSuccess) return e;
-    void *args[] = {&n, &L, &T, &s_in, &tol, &max_iter, &J, &W, &red, &bar, &iters, &err};
+    void *args[] = {&n, &L, &T, &s_in, &tol, &max_iter, &J, &W, &red, &bar, &iters, &err, &max_spins};
     return cudaLaunchCooperativeKernel((const void *)k_power_flow, dim3(G), dim3(256), args, smem, st);
 }
 

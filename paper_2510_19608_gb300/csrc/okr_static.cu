@@ -186,6 +186,7 @@ okr_status read_err(const int *err_dev, cudaStream_t st) {
 
 constexpr double kPfTol = 1e-13;
 constexpr int kPfMaxIter = 200;
+constexpr long long kPfSpins = 4000000;     // polls per grid barrier of the load flow: well under a second
 
 }  // namespace
 
@@ -222,9 +223,14 @@ extern "C" okr_status okr_power_flow_static(const okr_feeder *f, double *vhat_ou
     if (s != OKR_OK) return s;
     k_child_offsets<<<1, 1024, 0, st>>>(n, T, w.coff_c, w.child_c);
     if (launch_lines(n, T, f->z_line, w.err, slot.num_sms, st) != cudaSuccess) return OKR_ECUDA;
+    // a singular line block (err = 2) stops here, as okr_power_flow does: the
+    // load flow would run on undefined admittances and its own outcome would
+    // overwrite the flag
+    s = read_err(w.err, st);
+    if (s != OKR_OK) return s;
     // the load flow's work buffers alias T.ihat and T.amag, which the next two kernels fill
     if (launch_power_flow(n, L, T, f->s_load, kPfTol, kPfMaxIter, w.J, T.ihat, T.amag, w.sweeps, w.err,
-                          slot.num_sms, st) != cudaSuccess)
+                          slot.num_sms, st, kPfSpins) != cudaSuccess)
         return OKR_ECUDA;
     k_line_currents<<<grid_for((size_t)L * n, slot.num_sms), 256, 0, st>>>(n, L, T, w.J);
     k_injections<<<grid_for((size_t)L * n, slot.num_sms), 256, 0, st>>>(n, L, T, w.J);

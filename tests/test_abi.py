@@ -56,6 +56,8 @@ def test_struct_layouts_match_c(built, tmp_path):
         ' printf("%zu %zu %zu\\n", sizeof(okr_feeder), offsetof(okr_feeder, s_load), offsetof(okr_feeder, v_slack));\n'
         ' printf("%zu %zu %zu\\n", sizeof(okr_params), offsetof(okr_params, objective), offsetof(okr_params, max_spins));\n'
         ' printf("%zu %zu %zu\\n", sizeof(okr_summary), offsetof(okr_summary, candidates), offsetof(okr_summary, max_error));\n'
+        ' printf("%zu %zu %zu\\n", sizeof(okr_summary), offsetof(okr_summary, terms), offsetof(okr_summary, inc_records));\n'
+        ' printf("%zu %zu %zu\\n", sizeof(okr_inc_shape), offsetof(okr_inc_shape, eval_warps), offsetof(okr_inc_shape, records));\n'
         " return 0; }\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
@@ -64,6 +66,8 @@ def test_struct_layouts_match_c(built, tmp_path):
     assert got[0] == [C.sizeof(B.Feeder), B.Feeder.s_load.offset, B.Feeder.v_slack.offset]
     assert got[1] == [C.sizeof(B.Params), B.Params.objective.offset, B.Params.max_spins.offset]
     assert got[2] == [C.sizeof(B.Summary), B.Summary.candidates.offset, B.Summary.max_error.offset]
+    assert got[3] == [C.sizeof(B.Summary), B.Summary.terms.offset, B.Summary.inc_records.offset]
+    assert got[4] == [C.sizeof(B.IncShape), B.IncShape.eval_warps.offset, B.IncShape.records.offset]
 
 
 def test_default_params_from_the_library(built):
@@ -73,3 +77,44 @@ def test_default_params_from_the_library(built):
     assert p.objective == 0 and p.precision == 0 and p.max_merges == -1 and p.profile == 0
     q = default_params(margin=0.01, record_iters=3)
     assert q.margin == 0.01 and q.record_iters == 3
+
+
+def header_define(name: str) -> int:
+    m = re.search(rf"#define\s+{name}\s+(\d+)", open(HEADER).read())
+    assert m, name
+    return int(m.group(1))
+
+
+def test_binding_constants_match_header():
+    from paper_2510_19608_gb300 import _binding as B
+    assert B.SCORER_FEATURES == header_define("OKR_SCORER_FEATURES")
+    assert B.STATIC_MAX_BUS == header_define("OKR_STATIC_MAX_BUS")
+
+
+@pytest.mark.gpu
+def test_recorded_features_rows_have_the_declared_width(built):
+    """okr_get_recorded_features writes rows of OKR_SCORER_FEATURES floats, as
+    the header declares: a C caller that sizes its buffer by the header's
+    constant gets every row filled and nothing written past cap rows."""
+    import numpy as np
+    import feedergen as fg
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import _binding as B
+    width = header_define("OKR_SCORER_FEATURES")
+    f, run = fg.preset("feeder40")
+    with K.Context(0) as ctx:
+        ctx.reduce(f, K.default_params(margin=run["margin"], record_iters=2, precision=0, engine=1))
+        lib = B.lib()
+        cnt = C.c_int32()
+        assert lib.okr_get_recorded_features(ctx._h, 0, 0, None, C.byref(cnt)) == B.OK
+        count = int(cnt.value)
+        assert count > 4
+        cap = count - 3                                   # fewer rows than candidates: the copy must stop at cap
+        guard = 4 * width
+        sentinel = np.float32(-1234.5)
+        buf = np.full(cap * width + guard, sentinel, np.float32)
+        assert lib.okr_get_recorded_features(ctx._h, 0, cap, buf.ctypes.data_as(C.c_void_p), C.byref(cnt)) == B.OK
+        assert int(cnt.value) == count
+        assert np.all(buf[cap * width:] == sentinel)      # nothing past cap rows of the declared width
+        assert np.all(np.isfinite(buf[:cap * width]))
+        assert not np.all(buf[(cap - 1) * width:cap * width] == sentinel)   # the last row was written

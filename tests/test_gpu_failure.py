@@ -53,3 +53,25 @@ def test_batch_team_barrier_timeout_is_reported_per_feeder(ctx):
     assert all(it["status"] == 0 for it in items2)
     ctx.reduce(feeders[0], ok[0])
     assert np.array_equal(parts2[0], ctx.assignment())
+
+
+def test_load_flow_barrier_timeout_is_reported_and_the_context_recovers(ctx):
+    """The cooperative load flow's grid barriers honour params.max_spins too:
+    with one poll a CTA that waits for a slower one gives up, every CTA
+    leaves at its next barrier, and the call reports OKR_ETIMEOUT.  The
+    incremental engine has no device-side wait, so the timeout can only come
+    from the load flow here.  The same context then runs normally."""
+    import paper_2510_19608_gb300 as K
+    f, run = fg.preset("feeder1000")
+    p_ok = K.default_params(margin=run["margin"], target_reduction=0.5, precision=1, engine=2)
+    ctx.reduce(f, p_ok)
+    ref = ctx.decisions()
+    with pytest.raises(K.OkrError) as e:
+        ctx.reduce(f, K.default_params(margin=run["margin"], target_reduction=0.5, precision=1, engine=2,
+                                       max_spins=1))
+    assert e.value.status == ETIMEOUT
+    assert "load flow" in str(e.value)
+    ctx.reduce(f, p_ok)
+    again = ctx.decisions()
+    assert np.array_equal(again["s"], ref["s"]) and np.array_equal(again["r"], ref["r"])
+    assert np.array_equal(again["score"], ref["score"])

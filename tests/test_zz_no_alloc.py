@@ -59,6 +59,43 @@ def test_static_load_flow_matches_context_entry_two_calls(ctx):
         assert sw == sw_ref
 
 
+def test_static_load_flow_at_the_size_limits(ctx):
+    """The largest feeder the static scratch holds (OKR_STATIC_MAX_BUS buses,
+    4 scenarios: the carve fills the array exactly) and a 3,000-bus feeder
+    (above the 2,048 buses whose load-flow slices fit shared memory, so the
+    global-memory path of the sweep runs), each against okr_power_flow."""
+    from paper_2510_19608_gb300 import _binding as B
+    for n, L, seed in ((B.STATIC_MAX_BUS, 4, 4096), (3000, 2, 3000)):
+        f = fg.make_feeder(n, seed, phase_mode=(0.45, 0.15, 0.4), load=("lognormal", 15.0, 1.0), n_scen=L)
+        v_ref, i_ref, sw_ref = ctx.power_flow(f)
+        v, i, sw = _static_run(f)
+        assert np.isfinite(v).all() and np.isfinite(i).all()
+        assert np.abs(v - v_ref).max() <= V_TOL
+        assert np.abs(i - i_ref).max() <= I_TOL
+        assert sw == sw_ref
+
+
+def test_static_load_flow_reports_a_singular_line_as_the_context_entry_does(ctx):
+    """A line whose impedance block is singular: both entry points return
+    OKR_ESINGULAR (the static one stops after the line inverses, before its
+    load flow could overwrite the flag), and the next call works."""
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import _binding as B
+    f, _ = fg.preset("feeder40")
+    bad = fg.Feeder(parent=f.parent.copy(), phases=f.phases.copy(), z_line=f.z_line.copy(),
+                    s_load=f.s_load.copy(), v_slack=f.v_slack, meta={})
+    bad.z_line[3] = 0.0
+    with pytest.raises(K.OkrError) as e:
+        ctx.power_flow(bad)
+    assert e.value.status == B.ESINGULAR
+    with pytest.raises(K.OkrError) as e:
+        _static_run(bad)
+    assert e.value.status == B.ESINGULAR
+    v_ref, _, _ = ctx.power_flow(f)
+    v, _, _ = _static_run(f)
+    assert np.abs(v - v_ref).max() <= V_TOL
+
+
 def test_static_load_flow_rejects_oversized_feeder():
     import torch
     import paper_2510_19608_gb300 as K
@@ -68,6 +105,18 @@ def test_static_load_flow_rejects_oversized_feeder():
     ibuf = torch.zeros(8, dtype=torch.int32, device="cuda")
     df = K.device_feeder(n, 2, ibuf.data_ptr(), ibuf.data_ptr(), buf.data_ptr(), buf.data_ptr(),
                          np.zeros((3, 2)))
+    with pytest.raises(K.OkrError) as e:
+        K.power_flow_static(df, buf.data_ptr())
+    assert e.value.status == B.EINVAL
+
+
+def test_static_load_flow_rejects_five_scenarios():
+    import torch
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import _binding as B
+    buf = torch.zeros(8, dtype=torch.float64, device="cuda")
+    ibuf = torch.zeros(8, dtype=torch.int32, device="cuda")
+    df = K.device_feeder(100, 5, ibuf.data_ptr(), ibuf.data_ptr(), buf.data_ptr(), buf.data_ptr(), np.zeros((3, 2)))
     with pytest.raises(K.OkrError) as e:
         K.power_flow_static(df, buf.data_ptr())
     assert e.value.status == B.EINVAL
