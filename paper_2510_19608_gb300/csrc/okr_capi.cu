@@ -258,6 +258,18 @@ int resolve_engine(const okr_params *p) {
     return (p->objective == 0 && p->scorer_topk == 0) ? OKR_ENGINE_INCREMENTAL : OKR_ENGINE_SWEEP;
 }
 
+// False when the automatic engine would pick the incremental one for an
+// n-bus feeder whose per-merge data does not fit one SM's shared memory
+// (about 13,900 buses): that feeder runs on the sweep instead.
+bool inc_fits(const okr_ctx *ctx, int n, const okr_params *p) {
+    if (p->engine != OKR_ENGINE_AUTO || resolve_engine(p) != OKR_ENGINE_INCREMENTAL) return true;
+    IncShape sh = inc_shape_resolve(ctx->inc_shape);
+    sh.rec = -1;
+    int rec = 0;
+    size_t bytes = 0;
+    return inc_smem(n, true, sh, &rec, &bytes);
+}
+
 int merges_for(int n, const okr_params *p) {
     long m;
     if (p->max_merges >= 0) m = p->max_merges;
@@ -363,6 +375,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p);
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     ctx->last_engine = resolve_engine(p);
     ctx->last_rec = -1;
+    if (!inc_fits(ctx, ctx->fb.T.n, p)) ctx->last_engine = OKR_ENGINE_SWEEP;
     if (ctx->last_engine == OKR_ENGINE_INCREMENTAL) return run_search_inc(ctx, p);
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
@@ -1051,7 +1064,8 @@ static okr_status batch_measure(okr_ctx *ctx, int32_t nf, const okr_feeder *feed
     for (int g = 0; g < 4; ++g) R.ord[g].clear();
     for (int f = 0; f < nf; ++f) {
         const okr_params &P = R.params[f];
-        R.ord[(resolve_engine(&P) == OKR_ENGINE_INCREMENTAL ? 2 : 0) + P.precision].push_back(f);
+        const bool inc = resolve_engine(&P) == OKR_ENGINE_INCREMENTAL && inc_fits(ctx, R.nbus[f], &P);
+        R.ord[(inc ? 2 : 0) + P.precision].push_back(f);
     }
     for (int g = 0; g < 4; ++g)
         std::stable_sort(R.ord[g].begin(), R.ord[g].end(), [&](int a, int b) {

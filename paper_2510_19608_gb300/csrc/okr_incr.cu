@@ -26,9 +26,10 @@
 // addition is associative, so removing a term's old value and adding its new
 // one gives exactly the sum a fresh evaluation of every term gives, in any
 // order.  The old value is recomputed from the unchanged inputs by the same
-// compiled code (the per-state arithmetic, term_arith32 / term_arith64, is not
-// inlined: one copy evaluates every term), so it is bit-identical to the value
-// added earlier.  Counts of terms above the margin are carried the same way.
+// arithmetic, every operation of which is explicitly rounded (no contraction
+// into fused multiply-adds, whose use could differ between inlined copies), so
+// it is bit-identical to the value added earlier.  Counts of terms above the
+// margin are carried the same way.
 // Engine 3 checks the carried values against a fresh evaluation after every
 // merge.
 //
@@ -373,9 +374,9 @@ __device__ int slot_geometry(const Topo &T, const State &S, const View &V, int n
 // on state 1 minus the term on state 0.  v_old / v_new say whether the group
 // has a term on state 0 / 1.  The geometry (the voltage change the candidate
 // causes) is the same on both states and is computed once.  The arithmetic of
-// a term on one state's inputs is a function that is not inlined
-// (term_arith32, term_arith64): every carried term is evaluated by its one
-// compiled copy, so equal inputs give bit-equal results.
+// a term on one state's inputs (term_arith32, term_arith64) rounds every
+// operation explicitly, so equal inputs give bit-equal results in every
+// inlined copy.
 
 // The merge in progress, as the terms after it see it: map[x] = 1 + the index
 // of super-node x among the merge's positions (0: unchanged), whose new values
@@ -451,8 +452,8 @@ __device__ __forceinline__ float mice32(const State &S, const Ovl &O, int e, int
 }
 
 // The arithmetic of one FP64 term on one state's inputs (every lane of the
-// warp calls it: it shuffles).  Not inlined: this one compiled copy evaluates
-// every FP64 term, so equal inputs give bit-equal results wherever it is called.
+// warp calls it: it shuffles).  Explicitly rounded operations: equal inputs
+// give bit-equal results wherever it is inlined.
 struct In64 {
     double2 v;
     double h, lo, hr, lr, mo, mr;
@@ -461,19 +462,21 @@ struct Out64 {
     u128 t;
     int tv;
 };
-__device__ __noinline__ Out64 term_arith64(In64 x, double2 dv, bool one, bool moves, bool is_s, bool lvp0,
-                                          double margin, double *out, int l, int p, int L) {
+__device__ __forceinline__ Out64 term_arith64(In64 x, double2 dv, bool one, bool moves, bool is_s, bool lvp0,
+                                              double margin, double *out, int l, int p, int L) {
+    // every operation explicitly rounded (no contraction): each inlined copy
+    // gives the same bits for the same inputs
     double em = 0.0;
     if (one) {
         double2 v = x.v;
-        if (moves) v = cadd(v, dv);
+        if (moves) v = make_double2(__dadd_rn(v.x, dv.x), __dadd_rn(v.y, dv.y));
         const double mag = cmag(v);
         double h = x.h, lo = x.lo;
         if (is_s) {
             h = fmax(h, x.hr);
             lo = fmin(lo, x.lr);
         }
-        em = fmax(h - mag, mag - lo);
+        em = fmax(__dsub_rn(h, mag), __dsub_rn(mag, lo));
         if (out) {
             out[(l * 3 + p) * 3 + 0] = v.x;
             out[(l * 3 + p) * 3 + 1] = v.y;
@@ -487,8 +490,8 @@ __device__ __noinline__ Out64 term_arith64(In64 x, double2 dv, bool one, bool mo
     r.tv = 0;
     if (lvp0) {
         if (out) out[9 * L + l] = m;
-        double dd = m - x.mo;
-        if (is_s) dd -= x.mr;
+        double dd = __dsub_rn(m, x.mo);
+        if (is_s) dd = __dsub_rn(dd, x.mr);
         r.t = to_fx(dd);
         r.tv = (m > margin) ? 1 : 0;
     }
@@ -570,9 +573,8 @@ __device__ __forceinline__ void group_term64(const Topo &T, const State &S, cons
 }
 
 // The arithmetic of one FP32 term with its bound on one state's inputs (every
-// lane of the warp calls it: it shuffles).  Not inlined: this one compiled
-// copy evaluates every carried FP32 term, so equal inputs give bit-equal
-// results wherever it is called.
+// lane of the warp calls it: it shuffles).  Explicitly rounded operations:
+// equal inputs give bit-equal results wherever it is inlined.
 struct In32 {
     float hr, lr, hrr, lrr, mo, mr;
     float2 v;
@@ -582,33 +584,39 @@ struct Out32 {
     u128 td, tb;
     int ts, tm;
 };
-__device__ __noinline__ Out32 term_arith32(In32 x, float2 dv, float sdv, bool one, bool moves, bool sterm, bool lvp0,
-                                          float margin_lo, float margin_hi) {
+__device__ __forceinline__ Out32 term_arith32(In32 x, float2 dv, float sdv, bool one, bool moves, bool sterm,
+                                              bool lvp0, float margin_lo, float margin_hi) {
+    // every operation explicitly rounded (no contraction): each inlined copy
+    // gives the same bits for the same inputs
     float em = 0.0f, b = 0.0f;
     if (one) {
         float hr = x.hr, lr = x.lr, hrr = x.hrr, lrr = x.lrr;
         float bx = 0.0f;
         if (sterm) {
-            const float dr = (float)(x.mcr - x.mck);
-            hrr += dr;
-            lrr += dr;
+            const float dr = (float)__dsub_rn(x.mcr, x.mck);
+            hrr = __fadd_rn(hrr, dr);
+            lrr = __fadd_rn(lrr, dr);
             hr = fmaxf(hr, hrr);
             lr = fminf(lr, lrr);
-            bx = 2.0f * kU32 * (fabsf(hrr) + fabsf(lrr) + 2.0f * fabsf(dr));
+            bx = __fmul_rn(2.0f * kU32, __fadd_rn(__fadd_rn(fabsf(hrr), fabsf(lrr)), __fmul_rn(2.0f, fabsf(dr))));
         }
         float delta = 0.0f, bd = 0.0f;
         if (moves) {
             const float2 v = x.v;
-            const float num = 2.0f * (v.x * dv.x + v.y * dv.y) + (dv.x * dv.x + dv.y * dv.y);
-            const float wx = v.x + dv.x, wy = v.y + dv.y;
-            const float mv = sqrtf(v.x * v.x + v.y * v.y);
-            const float den = sqrtf(wx * wx + wy * wy) + mv;
-            delta = num / den;
-            const float v1 = fabsf(v.x) + fabsf(v.y);
-            bd = kU32 * (40.0f * (v1 + sdv) * sdv / den + 8.0f * fabsf(delta));
+            const float s1 = __fadd_rn(__fmul_rn(v.x, dv.x), __fmul_rn(v.y, dv.y));
+            const float s2 = __fadd_rn(__fmul_rn(dv.x, dv.x), __fmul_rn(dv.y, dv.y));
+            const float num = __fadd_rn(__fmul_rn(2.0f, s1), s2);
+            const float wx = __fadd_rn(v.x, dv.x), wy = __fadd_rn(v.y, dv.y);
+            const float mv = __fsqrt_rn(__fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)));
+            const float den = __fadd_rn(__fsqrt_rn(__fadd_rn(__fmul_rn(wx, wx), __fmul_rn(wy, wy))), mv);
+            delta = __fdiv_rn(num, den);
+            const float v1 = __fadd_rn(fabsf(v.x), fabsf(v.y));
+            bd = __fmul_rn(kU32, __fadd_rn(__fdiv_rn(__fmul_rn(__fmul_rn(40.0f, __fadd_rn(v1, sdv)), sdv), den),
+                                           __fmul_rn(8.0f, fabsf(delta))));
         }
-        em = fmaxf(hr - delta, delta - lr);
-        b = 1.5f * (kU32 * (fabsf(hr) + fabsf(lr) + fabsf(em)) + bd) + bx + 4e-15f;
+        em = fmaxf(__fsub_rn(hr, delta), __fsub_rn(delta, lr));
+        const float ab = __fadd_rn(__fadd_rn(fabsf(hr), fabsf(lr)), fabsf(em));
+        b = __fadd_rn(__fadd_rn(__fmul_rn(1.5f, __fadd_rn(__fmul_rn(kU32, ab), bd)), bx), 4e-15f);
     }
     float m = fmaxf(em, __shfl_xor_sync(0xffffffffu, em, 1));
     m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
@@ -618,10 +626,11 @@ __device__ __noinline__ Out32 term_arith32(In32 x, float2 dv, float sdv, bool on
     r.td = r.tb = 0;
     r.ts = r.tm = 0;
     if (lvp0) {
-        const float dd = (m - x.mo) - x.mr;
+        const float dd = __fsub_rn(__fsub_rn(m, x.mo), x.mr);
         // rounding of MICE_k, MICE_r to FP32 and of the two subtractions; the
         // factor 1.001 covers the rounding of the bound's own arithmetic
-        const float bl = 1.001f * (bm + 3.0f * kU32 * (fabsf(x.mo) + fabsf(x.mr) + fabsf(m)));
+        const float am = __fadd_rn(__fadd_rn(fabsf(x.mo), fabsf(x.mr)), fabsf(m));
+        const float bl = __fmul_rn(1.001f, __fadd_rn(bm, __fmul_rn(3.0f * kU32, am)));
         r.td = to_fx32(dd);
         r.tb = to_fx32(bl) + 3;             // + the truncations of both terms to fixed point
         r.ts = (__fsub_rd(m, bm) > margin_hi) ? 1 : 0;
@@ -880,6 +889,20 @@ struct Rec {
     double *maxm;
     ushort4 *span;      // per slot pair: bus span [x, y) holding both candidates' ranges, s and r;
                         // z: the quotient parent (0xffff: none); w: empty pair when 0
+    // Summaries of blocks of 32 slots (shared memory), so that a selection
+    // reads the blocks, not every record: the smallest r0 (precision 0) or the
+    // smallest lower and upper keys (precision 1), the slots holding a
+    // candidate, and the largest maxm over the block's 16 super-nodes (bit
+    // patterns: MICE >= 0 orders like its bits).  A block whose records
+    // changed since the last selection is marked dirty and summarised again
+    // before the next one.
+    void *bsum;         // [nb] u128 (precision 0) or ulonglong2 (precision 1)
+    int *bcnt;          // [nb]
+    unsigned long long *bmx;    // [nb]
+    unsigned char *dirty;       // [nb]
+    int nb;
+    __device__ __forceinline__ void touch(int sl) const { dirty[sl >> 5] = 1; }
+    __device__ __forceinline__ void touch_sn(int k) const { dirty[k >> 4] = 1; }   // maxm of super-node k (slot 2k)
 };
 
 constexpr int kKeyShift = 44;                       // 2^-100 -> 2^-56 units
@@ -904,8 +927,48 @@ __device__ __forceinline__ unsigned long long val_key(long long v) {
     return (unsigned long long)v ^ 0x8000000000000000ull;
 }
 
+__device__ __forceinline__ unsigned long long warp_max64(unsigned long long v) { return ~warp_min64(~v); }
+__device__ __forceinline__ u128 warp_min128(u128 v) {
+    for (int o = 16; o > 0; o >>= 1) v = umin(v, shfl_xor_u128(v, o));
+    return v;
+}
+
+// Blocks whose records pass B reads one warp per block (or all warps each,
+// when there are at most this many).
+constexpr int kFewBlocks = 8;
+
+// The summaries of the dirty blocks, one warp per block, then a barrier.
+template <int NT, int PREC>
+__device__ __forceinline__ void refresh_blocks(const Rec &R, int n) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int j = wid; j < R.nb; j += NT / 32) {
+        if (!R.dirty[j]) continue;                      // (the same for the whole warp)
+        const int c = 32 * j + lane;
+        const bool in = c < 2 * n;
+        const unsigned long long mb =
+            (in && (c & 1) == 0) ? (unsigned long long)__double_as_longlong(R.maxm[c >> 1]) : 0ull;
+        const unsigned cnt = __popc(__ballot_sync(0xffffffffu, in && R.tkey[c] != ~0u));
+        const unsigned long long mx = warp_max64(mb);
+        if (PREC == 0) {
+            const u128 k = warp_min128(in ? R.r0[c] : kNone);
+            if (lane == 0) reinterpret_cast<u128 *>(R.bsum)[j] = k;
+        } else {
+            const ulonglong2 q = in ? R.r1[c] : make_ulonglong2(kKeyNone, kKeyNone);
+            const unsigned long long lo = warp_min64(q.x), hi = warp_min64(q.y);
+            if (lane == 0) reinterpret_cast<ulonglong2 *>(R.bsum)[j] = make_ulonglong2(lo, hi);
+        }
+        if (lane == 0) {
+            R.bcnt[j] = (int)cnt;
+            R.bmx[j] = mx;
+            R.dirty[j] = 0;
+        }
+    }
+    __syncthreads();
+}
+
 template <int PREC>
 __device__ __forceinline__ void set_rec(const Rec &R, int sl, u128 d, u128 b, int viol, int vmay) {
+    R.touch(sl);
     if (PREC == 0) {
         R.r0[sl] = (viol == 0) ? okey(d) : kNone;
     } else {
@@ -924,6 +987,7 @@ __device__ __forceinline__ void set_rec(const Rec &R, int sl, u128 d, u128 b, in
 }
 template <int PREC>
 __device__ __forceinline__ void kill_rec(const Rec &R, int sl) {
+    R.touch(sl);
     if (PREC == 0) R.r0[sl] = kNone;
     else R.r1[sl] = make_ulonglong2(kKeyNone, kKeyNone);
     R.tkey[sl] = ~0u;
@@ -1038,11 +1102,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
             c.s = c.r = c.a = c.js = c.ns = c.jr = c.nr = c.fixed = 0;
             if (valid) {
                 // the entry holding item q: the last one whose offset is <= q
-                if (ne <= 32) {
-                    int cq2 = 0;
-                    for (int i = 1; i < ne; ++i) cq2 += (E.off[i] <= q) ? 1 : 0;
-                    ei = cq2;
-                } else {
+                {
                     int lo = 0, hi = ne - 1;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
@@ -1167,6 +1227,7 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
                 const int ns = full_segments(c[d], Lc.rank, seg, V.r);
                 write_entry(Lc.ent(base + atomicAdd(cnt, 1)), sl, 1, ns, seg, c[d]);
                 R.tkey[sl] = (unsigned)c[d].key;
+                R.touch(sl);
             } else {
                 I.viol[sl] = kIncDead;
                 st128(I.acc + 2 * (size_t)sl, 0);
@@ -1229,14 +1290,20 @@ __host__ __device__ constexpr size_t rec_bytes(int n) { return (size_t)48 * n + 
 __host__ __device__ constexpr size_t rec_maxm_bytes(int n) { return rec_bytes(n) + (size_t)8 * n; }
 
 // Shared memory of one search: [work entries][two super-node lists][phase
-// masks][overlay map][super-node ranks], then the selection records when they
-// fit.
+// masks][overlay map][super-node ranks][block summaries of the selection
+// records], then the selection records when they fit.
 __host__ __device__ constexpr size_t align16(size_t b) { return (b + 15) / 16 * 16; }
-// The entries' region is rounded up to 16 bytes: the selection records after
-// the base are 16-byte keys.
+// Blocks of 32 selection slots, and the bytes of their summaries.
+__host__ __device__ constexpr int sel_blocks(int n) { return (2 * n + 31) / 32; }
+__host__ __device__ constexpr size_t sel_bytes(int n) {
+    return align16((size_t)16 * sel_blocks(n)) + align16((size_t)4 * sel_blocks(n)) +
+           align16((size_t)8 * sel_blocks(n)) + align16((size_t)sel_blocks(n));
+}
+// Every region is rounded up to 16 bytes: the block summaries and the
+// selection records are 16-byte keys.
 __host__ __device__ constexpr size_t base_bytes(int n, int se) {
     return align16((size_t)se * sizeof(IncWork)) + align16((size_t)4 * n) + align16((size_t)n) + align16((size_t)2 * n) +
-           align16((size_t)4 * (n + 1));
+           align16((size_t)4 * (n + 1)) + sel_bytes(n);
 }
 
 template <int NT, int PREC>
@@ -1285,6 +1352,17 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     R.tkey = reinterpret_cast<unsigned *>(recmem + (size_t)32 * n);
     R.maxm = rec_mode == 2 ? reinterpret_cast<double *>(recmem + rec_bytes(n)) : I.maxm;
     R.span = reinterpret_cast<ushort4 *>(recmem + (size_t)40 * n);
+    {
+        unsigned char *sm = reinterpret_cast<unsigned char *>(rank) + align16((size_t)4 * (n + 1));
+        R.nb = sel_blocks(n);
+        R.bsum = sm;
+        sm += align16((size_t)16 * R.nb);
+        R.bcnt = reinterpret_cast<int *>(sm);
+        sm += align16((size_t)4 * R.nb);
+        R.bmx = reinterpret_cast<unsigned long long *>(sm);
+        sm += align16((size_t)8 * R.nb);
+        R.dirty = sm;
+    }
     int t = 0, ns = n;
     if (tid == 0) {
         s_sfx[0] = s_sfx[1] = 0ull;                 // every MICE starts at 0
@@ -1310,6 +1388,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         rank[w] = S.sn_rank[w];
     }
     if (tid == 0) rank[n] = S.sn_rank[n];
+    for (int j = tid; j < R.nb; j += NT) R.dirty[j] = 1;
     __syncthreads();
     rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], 0, R, Lc, no_view());
     __syncthreads();
@@ -1328,48 +1407,55 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         const unsigned short *list_old = Lc.lst[t & 1];
         unsigned short *list_new = Lc.lst[(t + 1) & 1];
         // ============================================================ selection
-        // pass A: precision 0: the minimum over feasible candidates; precision 1:
-        // the smallest lower end (m_lo) and the smallest upper end (m_hi); the
-        // largest MICE after the last merge; the candidates.
+        // The blocks whose records changed are summarised again (one warp per
+        // block; the append counters are cleared before that barrier).
+        if (tid == 0) s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+        refresh_blocks<NT, PREC>(R, n);
+        // pass A, by every warp on its own from the block summaries (no
+        // barrier): precision 0: the minimum over feasible candidates;
+        // precision 1: the smallest lower end (m_lo) and the smallest upper end
+        // (m_hi); the largest MICE after the last merge; the candidates.
+        const int lane = tid & 31, wid = tid >> 5;
         Red ra;
         ra.a = ra.b = ra.c = kNone;
         ra.i = 0;
-        if (PREC == 0) {
-            for (int c = tid; c < 2 * n; c += NT) {
-                if ((c & 1) == 0 && t > 0)
-                    ra.c = umin(ra.c, ~(u128)(unsigned long long)__double_as_longlong(R.maxm[c >> 1]));
-                if (R.tkey[c] != ~0u) ++ra.i;
-                ra.a = umin(ra.a, R.r0[c]);
-            }
-            ra = block_red<NT>(ra, sred);
-        } else {
-            Red64 r6;
-            r6.a = r6.b = r6.c = ~0ull;
-            r6.i = 0;
-            for (int c = tid; c < 2 * n; c += NT) {
-                if ((c & 1) == 0 && t > 0) {
-                    const unsigned long long mb = ~(unsigned long long)__double_as_longlong(R.maxm[c >> 1]);
-                    r6.c = mb < r6.c ? mb : r6.c;
+        {
+            unsigned long long mx = 0;
+            unsigned cnt = 0;
+            if (PREC == 0) {
+                const u128 *bs = reinterpret_cast<const u128 *>(R.bsum);
+                u128 mn = kNone;
+                for (int j = lane; j < R.nb; j += 32) {
+                    mn = umin(mn, bs[j]);
+                    cnt += (unsigned)R.bcnt[j];
+                    mx = R.bmx[j] > mx ? R.bmx[j] : mx;
                 }
-                if (R.tkey[c] != ~0u) ++r6.i;
-                const ulonglong2 q = R.r1[c];
-                r6.a = q.x < r6.a ? q.x : r6.a;
-                r6.b = q.y < r6.b ? q.y : r6.b;
+                ra.a = warp_min128(mn);
+            } else {
+                const ulonglong2 *bs = reinterpret_cast<const ulonglong2 *>(R.bsum);
+                unsigned long long lo = ~0ull, hi = ~0ull;
+                for (int j = lane; j < R.nb; j += 32) {
+                    const ulonglong2 b = bs[j];
+                    lo = b.x < lo ? b.x : lo;
+                    hi = b.y < hi ? b.y : hi;
+                    cnt += (unsigned)R.bcnt[j];
+                    mx = R.bmx[j] > mx ? R.bmx[j] : mx;
+                }
+                lo = warp_min64(lo);
+                hi = warp_min64(hi);
+                ra.a = lo == kKeyNone ? kNone : (u128)lo;
+                ra.b = hi == kKeyNone ? kNone : (u128)hi;
             }
-            r6 = block_sel64(r6, &s_sel[0]);
-            ra.a = r6.a == kKeyNone ? kNone : (u128)r6.a;
-            ra.b = r6.b == kKeyNone ? kNone : (u128)r6.b;
-            ra.c = r6.c == ~0ull ? kNone : ~(u128)(~r6.c);
-            ra.i = r6.i;
+            ra.i = (int)__reduce_add_sync(0xffffffffu, cnt);
+            ra.c = ~(u128)warp_max64(mx);               // kNone when every maxm is 0
         }
         const int nvalid = ra.i;
-        stamp(11);                                      // profile: pass A
+        stamp(11);                                      // profile: block summaries and pass A
         if (tid == 0) {
             cands_run += nvalid;
             X.dec_ncand[t] = nvalid;
             if (t > 0)
                 X.dec_maxerr[t - 1] = ra.c == kNone ? 0.0 : __longlong_as_double((long long)(unsigned long long)~ra.c);
-            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
         if (t < X.rec_iters) {
             const double s_cur = fx_to_d(ld128(s_sfx));
@@ -1398,22 +1484,61 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             maxerr_done = true;
             break;
         }
-        // pass B
+        // pass B: only the blocks that may hold a candidate of the tie band
+        // (or one that the screen cannot place) are read record by record; a
+        // block whose smallest key lies above the band counts whole.  With few
+        // such blocks every warp reads them all and needs no barrier; with
+        // more they are spread over the warps and reduced block-wide.
         int ws = -1;
         double gap = INFINITY;
         if (PREC == 0) {
             const u128 edge = (ra.a ^ kSignBit) + tau_fx, ek = okey(edge);
-            Red rb;
-            rb.a = rb.b = rb.c = kNone;
-            rb.i = 0;
-            for (int c = tid; c < 2 * n; c += NT) {
-                const u128 k = R.r0[c];
-                if (k <= ek) rb.a = umin(rb.a, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
-                else rb.b = umin(rb.b, k);
+            const u128 *bs = reinterpret_cast<const u128 *>(R.bsum);
+            u128 pa = kNone, pb = kNone;        // smallest (key, slot) in the band; smallest score above it
+            auto relevant = [&](int j) {
+                const u128 bk = j < R.nb ? bs[j] : kNone;
+                return bk != kNone && bk <= ek;
+            };
+            int nrel = 0;
+            for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                const int j = j0 + lane;
+                const bool rel = relevant(j);
+                if (!rel && j < R.nb) pb = umin(pb, bs[j]);          // the whole block above the band
+                nrel += __popc(__ballot_sync(0xffffffffu, rel));
             }
-            rb = block_red<NT>(rb, sred);
-            ws = (int)(unsigned)(rb.a & 0xffffffffu);
-            if (tid == 0 && rb.b != kNone) gap = fx_to_d((rb.b ^ kSignBit) - edge);
+            const bool few = nrel <= kFewBlocks;
+            int kq = 0;
+            for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    if (few || kq % (NT / 32) == wid) {
+                        const int c = 32 * (j0 + b) + lane;
+                        if (c < 2 * n) {
+                            const u128 k = R.r0[c];
+                            if (k <= ek) pa = umin(pa, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
+                            else pb = umin(pb, k);
+                        }
+                    }
+                    ++kq;
+                }
+            }
+            if (few) {
+                pa = warp_min128(pa);
+                pb = warp_min128(pb);
+            } else {
+                Red rb;
+                rb.a = pa;
+                rb.b = pb;
+                rb.c = kNone;
+                rb.i = 0;
+                rb = block_red<NT>(rb, sred);
+                pa = rb.a;
+                pb = rb.b;
+            }
+            ws = (int)(unsigned)(pa & 0xffffffffu);
+            if (tid == 0 && pb != kNone) gap = fx_to_d((pb ^ kSignBit) - edge);
         } else {
             const bool has_hi = ra.b != kNone;
             bool ok;
@@ -1422,28 +1547,69 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             const long long m_hi = has_hi ? key_val((unsigned long long)ra.b) : 0;
             const unsigned long long ein = val_key(m_lo + tau_dn);
             const unsigned long long eout = has_hi ? val_key(m_hi + tau_up) : kKeyNone;
-            Red64 r6;
-            r6.a = r6.b = r6.c = ~0ull;
-            r6.i = 0;
-            for (int c = tid; c < 2 * n; c += NT) {
-                const ulonglong2 q = R.r1[c];
-                if (q.x == kKeyNone) continue;
-                const bool in_sure = q.y <= ein;
-                const bool out_sure = has_hi && q.x > eout;
-                const unsigned key = R.tkey[c];
-                if (in_sure) {
-                    const unsigned long long kc = ((unsigned long long)key << 32) | (unsigned)c;
-                    r6.a = kc < r6.a ? kc : r6.a;
-                } else if (!out_sure) {
-                    r6.b = key < r6.b ? key : r6.b;
-                }
-                if (out_sure) r6.c = q.x < r6.c ? q.x : r6.c;
+            const ulonglong2 *bs = reinterpret_cast<const ulonglong2 *>(R.bsum);
+            // a block is read record by record unless every candidate in it is
+            // surely out of the band (its smallest lower end above eout)
+            auto relevant = [&](int j) {
+                const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
+                return bl != kKeyNone && !(has_hi && bl > eout);
+            };
+            unsigned long long pa = ~0ull, pb = ~0ull, pc = ~0ull;
+            int nrel = 0;
+            for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                const int j = j0 + lane;
+                const bool rel = relevant(j);
+                const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
+                if (bl != kKeyNone && !rel) pc = bl < pc ? bl : pc;        // the whole block surely out
+                nrel += __popc(__ballot_sync(0xffffffffu, rel));
             }
-            r6 = block_sel64(r6, &s_sel[1]);
+            const bool few = nrel <= kFewBlocks;
+            int kq = 0;
+            for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
+                while (mask) {
+                    const int b = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    if (few || kq % (NT / 32) == wid) {
+                        const int c = 32 * (j0 + b) + lane;
+                        if (c < 2 * n) {
+                            const ulonglong2 q = R.r1[c];
+                            if (q.x != kKeyNone) {
+                                const bool in_sure = q.y <= ein;
+                                const bool out_sure = has_hi && q.x > eout;
+                                const unsigned key = R.tkey[c];
+                                if (in_sure) {
+                                    const unsigned long long kc = ((unsigned long long)key << 32) | (unsigned)c;
+                                    pa = kc < pa ? kc : pa;
+                                } else if (!out_sure) {
+                                    pb = key < pb ? key : pb;
+                                }
+                                if (out_sure) pc = q.x < pc ? q.x : pc;
+                            }
+                        }
+                    }
+                    ++kq;
+                }
+            }
+            if (few) {
+                pa = warp_min64(pa);
+                pb = warp_min64(pb);
+                pc = warp_min64(pc);
+            } else {
+                Red64 r6;
+                r6.a = pa;
+                r6.b = pb;
+                r6.c = pc;
+                r6.i = 0;
+                r6 = block_sel64(r6, &s_sel[1]);
+                pa = r6.a;
+                pb = r6.b;
+                pc = r6.c;
+            }
             Red rb;
-            rb.a = r6.a == ~0ull ? kNone : (u128)r6.a;
-            rb.b = r6.b == ~0ull ? kNone : (u128)r6.b;
-            rb.c = r6.c == ~0ull ? kNone : (u128)r6.c;
+            rb.a = pa == ~0ull ? kNone : (u128)pa;
+            rb.b = pb == ~0ull ? kNone : (u128)pb;
+            rb.c = pc == ~0ull ? kNone : (u128)pc;
             rb.i = 0;
             const u128 ks = rb.a == kNone ? kNone : (rb.a >> 32);
             if (!(rb.b < ks)) {                          // no uncertain candidate can take the band's smallest key
@@ -1609,7 +1775,10 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                     const unsigned long long y = __shfl_xor_sync(0xffffffffu, mb, o);
                     mb = y > mb ? y : mb;
                 }
-                if (valid && gl == 0) R.maxm[k] = __longlong_as_double((long long)mb);
+                if (valid && gl == 0) {
+                    R.maxm[k] = __longlong_as_double((long long)mb);
+                    R.touch_sn(k);
+                }
             }
             if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
             // r's members join s (they lie in the subtree of r's top); the new
@@ -1639,6 +1808,7 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
                 }
                 I.qpar[hw.r] = -1;
                 R.maxm[hw.r] = 0.0;
+                R.touch_sn(hw.r);
                 X.dec_s[t] = T.orig[hw.s];
                 X.dec_r[t] = T.orig[hw.r];
             }
