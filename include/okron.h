@@ -165,10 +165,10 @@ typedef struct okr_summary {
  * context (okr_set_inc_shape), used by the later okr_reduce* and
  * okr_reduce_batch calls on it.  A field of 0 takes its default. */
 typedef struct okr_inc_shape {
-    int32_t threads;            /* threads of the CTA: 256 or 512 (0 = 512) */
+    int32_t threads;            /* threads of the CTA: 256, 384 or 512 (0 = 384) */
     int32_t eval_warps;         /* warps that evaluate the merge's own new values while the others
-                                   find the changed candidates: 1 .. threads/32 - 1 (0 = 4, or 2
-                                   with 256 threads) */
+                                   find the changed candidates: 1 .. threads/32 - 1 (0 = 2, or 4
+                                   with 512 threads) */
     int32_t shared_entries;     /* work entries of one merge kept in shared memory, 1 .. 256
                                    (0 = 256); the rest live in device memory */
     int32_t records;            /* where the per-candidate selection records live: 0 automatic
@@ -183,6 +183,23 @@ typedef struct okr_inc_shape {
 okr_status okr_set_inc_shape(okr_ctx *ctx, const okr_inc_shape *shape);
 /* The context's shape with the defaults filled in (records 0 stays automatic). */
 okr_status okr_get_inc_shape(const okr_ctx *ctx, okr_inc_shape *shape);
+
+/* Autotuner of the incremental engine's shape: times the search kernel under
+ * each of a fixed list of shapes (CTA sizes 256/384/512, evaluation-warp
+ * splits, a smaller shared tile, records in device memory) on the caller's
+ * workload -- one feeder through okr_reduce when n_feeders = 1, else the
+ * batch through okr_reduce_batch -- two runs each, the faster counted, and
+ * keeps the fastest shape on the context for later calls.  feeders: HOST,
+ * as okr_reduce / okr_reduce_batch; params: [n_params], n_params = 1 or
+ * n_feeders, selecting the incremental engine (else OKR_EINVAL).
+ * best (may be NULL): the shape kept.  shapes, search_ms (may be NULL): the
+ * first `cap` shapes tried and their search times in ms (infinity for a
+ * shape whose record placement does not fit the workload); *n_tried (may be
+ * NULL): how many shapes the list holds.  The results of the runs are those
+ * of the last run (every shape gives the same results). */
+okr_status okr_inc_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                            int32_t n_params, okr_inc_shape *best, okr_inc_shape *shapes, double *search_ms,
+                            int32_t cap, int32_t *n_tried);
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
  * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, scorer_topk 0,

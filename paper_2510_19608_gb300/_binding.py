@@ -81,7 +81,7 @@ EXPORTS = ("okr_default_params", "okr_create", "okr_destroy", "okr_status_str", 
            "okr_scorer_params", "okr_scorer_gradient", "okr_scorer_train", "okr_scorer_predict",
            "okr_evaluate", "okr_scorer_predict_tc", "okr_batch_plan_create", "okr_batch_plan_run", "okr_batch_plan_set_loads",
            "okr_batch_plan_destroy", "okr_set_inc_shape", "okr_get_inc_shape",
-           "okr_set_allocator", "okr_result_take", "okr_result_free", "okr_result_summary",
+           "okr_set_allocator", "okr_inc_autotune", "okr_result_take", "okr_result_free", "okr_result_summary",
            "okr_result_assignment", "okr_result_decisions", "okr_result_errors", "okr_result_ykron",
            "okr_result_stats")
 
@@ -134,6 +134,7 @@ def lib():
             L.okr_get_summary.argtypes = [P, C.POINTER(Summary)]
             L.okr_set_inc_shape.argtypes = [P, P]
             L.okr_set_allocator.argtypes = [P, ALLOC_FN, FREE_FN, P]
+            L.okr_inc_autotune.argtypes = [P, I32, P, P, I32, C.POINTER(IncShape), P, P, I32, P]
             L.okr_result_take.argtypes = [P, I32, C.POINTER(P)]
             L.okr_result_free.argtypes = [P]
             L.okr_result_free.restype = None
@@ -367,6 +368,22 @@ class Context:
         sh = IncShape()
         self._check(lib().okr_get_inc_shape(self._h, C.byref(sh)))
         return {k: getattr(sh, k) for k, _ in IncShape._fields_}
+
+    def inc_autotune(self, feeders, params):
+        """okr_inc_autotune: times the incremental engine's shapes on one feeder
+        (a list of one) or a batch; keeps the fastest.  Returns (best shape,
+        [(shape, search ms), ...])."""
+        hfs, arr, parr, npar = self._batch_args(feeders, params)
+        cap = 32
+        best = IncShape()
+        shapes = (IncShape * cap)()
+        ms = (C.c_double * cap)()
+        cnt = C.c_int32()
+        self._check(lib().okr_inc_autotune(self._h, len(hfs), arr, parr, npar, C.byref(best), shapes, ms, cap,
+                                           C.byref(cnt)))
+        self.n_bus, self.n_scen = hfs[0].c.n_bus, hfs[0].c.n_scen
+        as_dict = lambda sh: {k: getattr(sh, k) for k, _ in IncShape._fields_}   # noqa: E731
+        return as_dict(best), [(as_dict(shapes[i]), ms[i]) for i in range(min(cnt.value, cap))]
 
     def set_batch_config(self, config: int):
         """okr_set_batch_config: team shape 0/1/2/3 = 1/2/4/8 CTAs per feeder."""

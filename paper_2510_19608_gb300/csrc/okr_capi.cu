@@ -1445,6 +1445,68 @@ okr_status okr_batch_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder 
     return OKR_OK;
 }
 
+// Shapes the incremental-engine autotuner times, in this order.
+static const okr_inc_shape kIncTuneShapes[] = {
+    {384, 2, 0, 0}, {384, 3, 0, 0}, {512, 2, 0, 0}, {512, 4, 0, 0}, {256, 2, 0, 0}, {256, 1, 0, 0},
+    {384, 2, 128, 0}, {384, 2, 0, 1},
+};
+static const int kIncTuneCount = (int)(sizeof kIncTuneShapes / sizeof kIncTuneShapes[0]);
+
+okr_status okr_inc_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
+                            int32_t n_params, okr_inc_shape *best, okr_inc_shape *shapes, double *search_ms,
+                            int32_t cap, int32_t *n_tried) {
+    if (!ctx) return OKR_EINVAL;
+    if (n_feeders < 1 || !feeders || !params || cap < 0) return fail(ctx, OKR_EINVAL, "inc autotune: bad arguments");
+    if (n_params != 1 && n_params != n_feeders) return fail(ctx, OKR_EINVAL, "inc autotune: n_params must be 1 or n_feeders");
+    for (int f = 0; f < n_params; ++f) {
+        okr_status st = check_params(ctx, &params[f]);
+        if (st != OKR_OK) return st;
+        if (resolve_engine(&params[f]) != OKR_ENGINE_INCREMENTAL)
+            return fail(ctx, OKR_EINVAL, "inc autotune: the parameters select the sweep engine");
+    }
+    CK(cudaSetDevice(ctx->device));
+    const IncShape saved = ctx->inc_shape;
+    std::vector<okr_batch_item> items(n_feeders);
+    double best_t = 1e300;
+    int best_i = -1;
+    for (int i = 0; i < kIncTuneCount; ++i) {
+        okr_status s = okr_set_inc_shape(ctx, &kIncTuneShapes[i]);
+        double t = 1e300;
+        for (int rep = 0; rep < 2 && s == OKR_OK; ++rep) {     // the first run warms the buffers
+            double ms = 0.0;
+            if (n_feeders == 1) {
+                s = reduce_impl(ctx, &feeders[0], nullptr, nullptr, &params[0], Src::Host);
+                ms = ctx->search_ms;
+            } else {
+                okr_batch_stats st{};
+                s = reduce_batch_impl(ctx, n_feeders, feeders, params, n_params, items.data(), nullptr, &st,
+                                      ctx->batch_config);
+                ms = st.search_ms;
+            }
+            if (s == OKR_OK) t = std::min(t, ms);
+        }
+        if (s == OKR_EINVAL) {
+            t = INFINITY;                       // this shape's record placement does not fit the workload
+        } else if (s != OKR_OK) {
+            ctx->inc_shape = saved;
+            return s;
+        }
+        if (i < cap) {
+            if (shapes) shapes[i] = kIncTuneShapes[i];
+            if (search_ms) search_ms[i] = t;
+        }
+        if (t < best_t) { best_t = t; best_i = i; }
+    }
+    if (n_tried) *n_tried = kIncTuneCount;
+    if (best_i < 0) {
+        ctx->inc_shape = saved;
+        return fail(ctx, OKR_EINVAL, "inc autotune: no shape ran");
+    }
+    okr_set_inc_shape(ctx, &kIncTuneShapes[best_i]);
+    if (best) okr_get_inc_shape(ctx, best);
+    return OKR_OK;
+}
+
 okr_status okr_batch_plan_create(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *feeders, const okr_params *params,
                                  int32_t n_params, okr_batch_plan **plan) {
     if (!ctx || !plan) return OKR_EINVAL;
@@ -1569,7 +1631,8 @@ okr_status okr_set_inc_shape(okr_ctx *ctx, const okr_inc_shape *shape) {
         return OKR_OK;
     }
     const int t = shape->threads, w = shape->eval_warps, e = shape->shared_entries, r = shape->records;
-    if (t != 0 && t != 256 && t != 512) return fail(ctx, OKR_EINVAL, "inc shape: threads %d (0, 256 or 512)", t);
+    if (t != 0 && t != 256 && t != 384 && t != 512)
+        return fail(ctx, OKR_EINVAL, "inc shape: threads %d (0, 256, 384 or 512)", t);
     const int nw = (t == 0 ? kIncDefaultThreads : t) / 32;
     if (w < 0 || w > nw - 1) return fail(ctx, OKR_EINVAL, "inc shape: eval_warps %d outside [0, %d]", w, nw - 1);
     if (e < 0 || e > 256) return fail(ctx, OKR_EINVAL, "inc shape: shared_entries %d outside [0, 256]", e);

@@ -1134,7 +1134,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
                 if (it) terms += it * __popc(Lc.ph[k]) * L;
             }
             const unsigned long long c0 = (prof && tid == 0) ? clock64() : 0;
-            if (prof && tid == 0) prof[3] += c0 - cq;
+            if (prof && tid == 0) { prof[3] += c0 - cq; prof[7] += 1; }     // lookup cycles, rounds
             if (PREC == 0 || pass == kF64) {
                 u128 d;
                 int nv;
@@ -1154,7 +1154,7 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
                     if (nm) atomicAdd(&E.n2[ei], nm);
                 }
             }
-            if (prof && tid == 0) prof[4] += clock64() - c0;
+            if (prof && tid == 0) { cq = clock64(); prof[4] += cq - c0; }   // term cycles
         }
         __syncthreads();
         sub(1);
@@ -1954,9 +1954,9 @@ cudaError_t set_smem(K kern, size_t bytes) {
 }  // namespace
 
 IncShape inc_shape_resolve(IncShape sh) {
-    if (sh.threads != 256 && sh.threads != 512) sh.threads = kIncDefaultThreads;
+    if (sh.threads != 256 && sh.threads != 384 && sh.threads != 512) sh.threads = kIncDefaultThreads;
     const int nw = sh.threads / 32;
-    if (sh.cw < 1 || sh.cw > nw - 1) sh.cw = sh.threads == 256 ? 2 : 4;
+    if (sh.cw < 1 || sh.cw > nw - 1) sh.cw = sh.threads == 512 ? 4 : 2;
     if (sh.se < 1 || sh.se > kSEMax) sh.se = kSEMax;
     if (sh.rec < -1 || sh.rec > 2) sh.rec = -1;
     return sh;
@@ -2013,6 +2013,9 @@ cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, C
     if (sh.threads == 256)
         return precision == 1 ? launch_one<256, 1>(T, S, X, I, C, verify, use, smem, sh, st)
                               : launch_one<256, 0>(T, S, X, I, C, verify, use, smem, sh, st);
+    if (sh.threads == 384)
+        return precision == 1 ? launch_one<384, 1>(T, S, X, I, C, verify, use, smem, sh, st)
+                              : launch_one<384, 0>(T, S, X, I, C, verify, use, smem, sh, st);
     return precision == 1 ? launch_one<512, 1>(T, S, X, I, C, verify, use, smem, sh, st)
                           : launch_one<512, 0>(T, S, X, I, C, verify, use, smem, sh, st);
 }
@@ -2022,6 +2025,7 @@ cudaError_t prepare_search_inc_batch(int precision, int max_n, IncShape sh) {
     int use = 0;
     size_t smem = 0;
     if (!inc_smem(max_n, false, sh, &use, &smem)) return cudaErrorInvalidValue;
+    if (sh.threads == 384) return set_batch_smem<384>(precision, smem);
     return sh.threads == 256 ? set_batch_smem<256>(precision, smem) : set_batch_smem<512>(precision, smem);
 }
 
@@ -2033,6 +2037,7 @@ cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder 
     size_t smem = 0;
     if (!inc_smem(max_n, false, sh, &use, &smem)) return cudaErrorInvalidValue;
     if (sh.threads == 256) launch_batch<256>(precision, fd, order, nf, use, smem, sh, st);
+    else if (sh.threads == 384) launch_batch<384>(precision, fd, order, nf, use, smem, sh, st);
     else launch_batch<512>(precision, fd, order, nf, use, smem, sh, st);
     return cudaGetLastError();
 }

@@ -143,7 +143,7 @@ __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, dou
 // feeder (verify = 1: every merge also re-evaluates every candidate and counts
 // mismatches of the carried scores in C->inc_mismatch).
 //
-// Launch shape of that CTA: threads (256 or 512), warps that evaluate the
+// Launch shape of that CTA: threads (256, 384 or 512), warps that evaluate the
 // merge beside the changed-set scan (cw, 1 .. threads/32 - 1), work entries in
 // shared memory (se, 1 .. 256; the rest in device memory) and where the
 // selection records live (rec: -1 automatic, 0 device memory, 1 shared memory,
@@ -152,9 +152,9 @@ __global__ void k_export(Topo T, State S, double *super_vred, int *super_of, dou
 struct IncShape {
     int threads, cw, se, rec;
 };
-constexpr int kIncDefaultThreads = 512;
-// Out-of-range fields replaced by the defaults (512 threads, 4 evaluation
-// warps (2 with 256 threads), 256 shared entries, automatic records).
+constexpr int kIncDefaultThreads = 384;
+// Out-of-range fields replaced by the defaults (384 threads, 2 evaluation
+// warps (4 with 512 threads), 256 shared entries, automatic records).
 IncShape inc_shape_resolve(IncShape sh);
 // Dynamic shared memory and record placement of one search; false when a
 // forced placement does not fit.

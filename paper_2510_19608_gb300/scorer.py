@@ -125,7 +125,8 @@ def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256), T=None,
     return out
 
 
-def inference_timing(ctx: "B.Context", n: int, n_features: int = 12, reps: int = 5, seed: int = 0) -> dict:
+def inference_timing(ctx: "B.Context", n: int, n_features: int = B.SCORER_FEATURES, reps: int = 5,
+                     seed: int = 0) -> dict:
     """Wall time of okr_scorer_predict (CUDA cores, FP32 activations) and
     okr_scorer_predict_tc (tensor cores, bfloat16 layer inputs) on n seeded
     samples, host copies included, with a freshly initialised network (the
@@ -154,6 +155,8 @@ if __name__ == "__main__":
     ap.add_argument("--samples", type=int, default=1 << 20)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--device", type=int, default=0)
+    ap.add_argument("--features", type=int, default=B.SCORER_FEATURES,
+                    help="inputs of the network (the search's scorer has OKR_SCORER_FEATURES)")
     a = ap.parse_args()
     with B.Context(a.device) as c:
-        print(json.dumps(inference_timing(c, a.samples, reps=a.reps)))
+        print(json.dumps(inference_timing(c, a.samples, n_features=a.features, reps=a.reps)))

@@ -194,6 +194,8 @@ SHAPES = {
     "256-threads-default": dict(threads=256),
     "512-threads-12-eval-warps": dict(threads=512, eval_warps=12, shared_entries=32),
     "512-threads-1-eval-warp": dict(threads=512, eval_warps=1, records=2),
+    "384-threads-11-eval-warps-dev-records": dict(threads=384, eval_warps=11, records=1, shared_entries=24),
+    "512-threads-default": dict(threads=512),
 }
 
 SMALL = [
@@ -225,7 +227,7 @@ def test_forced_shapes_verify_and_match_oracle(ctx, shape, precision):
             ctx.reduce(f, params(margin=margin, target_reduction=target, engine=3, precision=precision))
             s = ctx.summary()
             sh = SHAPES[shape]
-            assert s["inc_threads"] == (sh.get("threads") or 512)
+            assert s["inc_threads"] == (sh.get("threads") or 384)
             if sh.get("eval_warps", 0):
                 assert s["inc_eval_warps"] == sh["eval_warps"]
             if sh.get("records", 0):
@@ -244,13 +246,14 @@ def test_forced_shapes_verify_and_match_oracle(ctx, shape, precision):
 def test_shape_setter_rejects_out_of_range(ctx):
     import paper_2510_19608_gb300 as K
     from paper_2510_19608_gb300._binding import EINVAL
-    for bad in (dict(threads=128), dict(threads=1024), dict(eval_warps=16), dict(threads=256, eval_warps=8),
+    for bad in (dict(threads=128), dict(threads=1024), dict(threads=320), dict(eval_warps=12),
+                dict(threads=256, eval_warps=8),
                 dict(shared_entries=257), dict(shared_entries=-1), dict(records=4), dict(records=-1)):
         with pytest.raises(K.OkrError) as e:
             ctx.set_inc_shape(**bad)
         assert e.value.status == EINVAL
     ctx.reset_inc_shape()
-    assert ctx.inc_shape() == dict(threads=512, eval_warps=4, shared_entries=256, records=0)
+    assert ctx.inc_shape() == dict(threads=384, eval_warps=2, shared_entries=256, records=0)
     # a forced placement that does not fit shared memory is refused at the reduction
     f, run = fg.preset("feeder3100")
     try:
@@ -346,6 +349,43 @@ def test_batch_rejects_the_per_super_node_maximum(ctx, batch256):
         ctx.set_inc_shape(records=3)
         with pytest.raises(K.OkrError) as e:
             ctx.reduce_batch(feeders, ps)
+        assert e.value.status == EINVAL
+    finally:
+        ctx.reset_inc_shape()
+
+
+def test_inc_autotune_single_and_batch(ctx, batch256):
+    """okr_inc_autotune times every shape of its list, keeps the fastest on the
+    context, and the results under the kept shape are the default shape's."""
+    import math
+    f, run = fg.preset("feeder1000", n_bus=600)
+    p = params(margin=run["margin"], target_reduction=0.5, precision=1, engine=2)
+    ctx.reset_inc_shape()
+    ctx.reduce(f, p)
+    ref = ctx.decisions()
+    try:
+        best, table = ctx.inc_autotune([f], [p])
+        assert len(table) >= 6
+        times = [t for _, t in table]
+        assert all(t > 0 for t in times)
+        i = int(np.argmin(times))
+        for k in ("threads", "eval_warps"):
+            assert best[k] == table[i][0][k]
+        assert ctx.inc_shape() == best
+        ctx.reduce(f, p)
+        d = ctx.decisions()
+        assert np.array_equal(d["s"], ref["s"]) and np.array_equal(d["score"], ref["score"])
+        sel = list(range(0, 256, 32))
+        feeders = [batch256[k][0] for k in sel]
+        ps = [params(margin=batch256[k][1]["margin"], target_reduction=batch256[k][1]["target"], precision=1,
+                     engine=2) for k in sel]
+        bbest, btable = ctx.inc_autotune(feeders, ps)
+        assert all(t > 0 and not math.isnan(t) for _, t in btable)
+        assert ctx.inc_shape() == bbest
+        from paper_2510_19608_gb300._binding import EINVAL
+        import paper_2510_19608_gb300 as K
+        with pytest.raises(K.OkrError) as e:
+            ctx.inc_autotune([f], [params(margin=run["margin"], engine=1)])
         assert e.value.status == EINVAL
     finally:
         ctx.reset_inc_shape()
