@@ -345,9 +345,13 @@ def learned_line(K, ctx, n_train=64, record=64):
     for name in ("feeder3100", "feeder2200", WORKLOAD):
         fx, rx = fg.preset(name)
         rows = {}
-        for k, engine in ((0, 2), (0, 1), (64, 1), (16, 1)):
-            px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=1, scorer_topk=k,
-                                  engine=engine)
+        # (name, top-k, engine, precision, certified pruning)
+        for key, k, engine, prec, exact in (("exhaustive_incremental", 0, 2, 1, 0), ("exhaustive_sweep", 0, 1, 1, 0),
+                                            ("top64", 64, 1, 1, 0), ("top16", 16, 1, 1, 0),
+                                            ("exhaustive_sweep_fp64", 0, 1, 0, 0),
+                                            ("certified_top64_fp64", 64, 1, 0, 1)):
+            px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=prec, scorer_topk=k,
+                                  engine=engine, prune_exact=exact)
             ctx.reduce(fx, px)                                        # warm-up
             times = []
             for _ in range(3):
@@ -355,10 +359,15 @@ def learned_line(K, ctx, n_train=64, record=64):
                 ctx.reduce(fx, px)
                 times.append(time.perf_counter() - t0)
             sm = ctx.summary()
-            rows[("exhaustive_incremental" if engine == 2 else "exhaustive_sweep") if k == 0 else f"top{k}"] = {
+            rows[key] = {
                 "ms": 1e3 * statistics.median(times), "search_ms": sm["search_ms"], "merges": sm["n_iter"],
                 "stop_reason": sm["stop_reason"], "smice": sm["smice"], "max_error": sm["max_error"],
                 "fallbacks": sm["scorer_fallbacks"]}
+            if exact:
+                rows[key]["pruned_fraction"] = sm["pruned"] / max(1, sm["candidates"])
+                rows[key]["same_decisions_as_exhaustive_fp64"] = (
+                    sm["smice"] == rows["exhaustive_sweep_fp64"]["smice"]
+                    and sm["n_iter"] == rows["exhaustive_sweep_fp64"]["merges"])
         pruned[name] = rows
     inference = scorer.inference_timing(ctx, 1 << 20)       # replaces the trained network: last
     return {"train_feeders": n_train, "iterations_per_feeder": record, "samples": int(X.shape[0]),

@@ -115,6 +115,17 @@ typedef struct okr_params {
     int64_t max_spins;          /* polls before a device-side wait gives up with OKR_ETIMEOUT: the grid
                                    barriers of the load flow and of the sweep engine (0 = default,
                                    4,000,000: well under a second) */
+    int32_t prune_exact;        /* 1 = certified pruning with the learned ordering (scorer_topk > 0,
+                                   objective 0, precision 0, the sweep engine; else OKR_EINVAL): each
+                                   iteration scores the scorer's top-k candidates exactly, then every
+                                   other candidate whose certified lower bound on its score does not
+                                   exclude it from the tie band; the decisions are the exhaustive
+                                   search's.  The bound: a cluster evaluated at one voltage magnitude
+                                   has MICE >= half the spread of its members' |Vhat|, so a merged
+                                   cluster adds at least that half spread less the two MICE it
+                                   replaces, and every other cluster at least its own half spread less
+                                   its MICE.  okr_summary.pruned counts the candidates it excluded. */
+    int32_t reserved;           /* 0 */
 } okr_params;
 
 #define OKR_ENGINE_AUTO 0
@@ -158,6 +169,7 @@ typedef struct okr_summary {
                                    own evaluations and FP64 rescorings included (0 otherwise) */
     /* incremental engine: the launch shape that ran (okr_inc_shape's meaning; 0 for the sweep) */
     int32_t inc_threads, inc_eval_warps, inc_shared_entries, inc_records;
+    int64_t pruned;             /* prune_exact: candidates excluded by the certified bound over the run */
 } okr_summary;
 
 /* Launch shape of the incremental engine (one CTA runs one feeder's search).
@@ -203,7 +215,7 @@ okr_status okr_inc_autotune(okr_ctx *ctx, int32_t n_feeders, const okr_feeder *f
 
 /* Fills *p with the defaults: margin 0.005, target 1.0, tie_tol 1e-9,
  * objective 0, precision 0, record_iters 0, max_merges -1, profile 0, scorer_topk 0,
- * engine OKR_ENGINE_AUTO, max_spins 0. */
+ * engine OKR_ENGINE_AUTO, max_spins 0, prune_exact 0. */
 void okr_default_params(okr_params *p);
 
 /* Creates a context on CUDA device `device`.  stream: a cudaStream_t to run

@@ -39,7 +39,8 @@ class Params(C.Structure):
     _fields_ = [("margin", C.c_double), ("target_reduction", C.c_double), ("tie_tol", C.c_double),
                 ("objective", C.c_int32), ("precision", C.c_int32), ("record_iters", C.c_int32),
                 ("max_merges", C.c_int32), ("profile", C.c_int32), ("scorer_topk", C.c_int32),
-                ("engine", C.c_int32), ("max_spins", C.c_int64)]
+                ("engine", C.c_int32), ("max_spins", C.c_int64), ("prune_exact", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class Summary(C.Structure):
@@ -51,7 +52,7 @@ class Summary(C.Structure):
                 ("kron_ms", C.c_double), ("scorer_fallbacks", C.c_int32), ("inc_mismatches", C.c_int32),
                 ("engine", C.c_int32), ("pad", C.c_int32), ("terms", C.c_int64),
                 ("inc_threads", C.c_int32), ("inc_eval_warps", C.c_int32), ("inc_shared_entries", C.c_int32),
-                ("inc_records", C.c_int32)]
+                ("inc_records", C.c_int32), ("pruned", C.c_int64)]
 
 
 class IncShape(C.Structure):

@@ -248,6 +248,10 @@ okr_status check_params(okr_ctx *ctx, const okr_params *p) {
         return fail(ctx, OKR_EINVAL, "engine %d not supported", p->engine);
     if (p->engine >= OKR_ENGINE_INCREMENTAL && (p->objective != 0 || p->scorer_topk != 0))
         return fail(ctx, OKR_EINVAL, "the incremental engine needs objective 0 and scorer_topk 0");
+    if (p->prune_exact != 0 && p->prune_exact != 1) return fail(ctx, OKR_EINVAL, "prune_exact must be 0 or 1");
+    if (p->prune_exact && (p->scorer_topk <= 0 || p->objective != 0 || p->precision != 0 ||
+                           p->engine >= OKR_ENGINE_INCREMENTAL))
+        return fail(ctx, OKR_EINVAL, "prune_exact needs scorer_topk > 0, objective 0, precision 0 and the sweep engine");
     return OKR_OK;
 }
 
@@ -382,6 +386,7 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     Search &X = ctx->fb.X;
     X.rec_iters = p->record_iters;
     X.topk = p->scorer_topk;
+    X.prune_exact = p->prune_exact;
     if (X.topk > 0) {
         X.mlp_theta = ctx->mb.theta;
         X.mlp_w1 = reinterpret_cast<const uint16_t *>(ctx->mb.w1);
@@ -470,6 +475,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     Search &X = ctx->fb.X;
     X.rec_iters = p->record_iters;
     X.topk = 0;
+    X.prune_exact = 0;
     k_state_init<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.S);
     ctx->launches += 1;
     CK(cudaGetLastError());
@@ -657,6 +663,8 @@ void okr_default_params(okr_params *p) {
     p->scorer_topk = 0;
     p->engine = OKR_ENGINE_AUTO;
     p->max_spins = 0;
+    p->prune_exact = 0;
+    p->reserved = 0;
 }
 
 const char *okr_status_str(okr_status s) {
@@ -1621,6 +1629,7 @@ okr_status okr_get_summary(const okr_ctx *ctx, okr_summary *out) {
     out->inc_eval_warps = inc ? ctx->last_shape.cw : 0;
     out->inc_shared_entries = inc ? ctx->last_shape.se : 0;
     out->inc_records = inc ? ctx->last_rec + 1 : 0;
+    out->pruned = ctx->last_engine == OKR_ENGINE_SWEEP ? c.pruned : 0;
     return OKR_OK;
 }
 

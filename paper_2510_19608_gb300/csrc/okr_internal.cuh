@@ -121,6 +121,8 @@ struct Ctrl {
     long long candidates;   // candidates evaluated over the run
     int inc_mismatch;       // incremental search, verification mode: slots whose carried score differs
     int pad2;
+    long long gtot_fx[2];   // certified pruning: sum over super-nodes of floor(g_k 2^56), by merge parity
+    long long pruned;       // certified pruning: candidates the bound excluded over the run
     long long max_spins;    // limit of a device-side wait
     double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
     unsigned long long sweep_ns;   // time in the sweep phase (profile mode, device timer)
@@ -200,6 +202,10 @@ struct Search {
     const float *mlp_theta;
     const uint16_t *mlp_w1, *mlp_w2, *mlp_w3, *mlp_w4;
     float *pred;            // [2n]
+    // certified pruning (prune_exact = 1, with topk > 0): per compact candidate the
+    // part of its lower bound that depends on it (lbp; +inf: surely infeasible)
+    int prune_exact;
+    double *lbp;            // [2n]
     int *rec_count;
 };
 

@@ -151,7 +151,9 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(X.rec_count, R);
     c.take(X.rec_feat, R * 2 * N * kScorerFeatures);
     c.take(X.pred, 2 * N);
+    c.take(X.lbp, 2 * N);
     X.topk = 0;
+    X.prune_exact = 0;
     X.mlp_theta = nullptr;
     X.mlp_w1 = X.mlp_w2 = X.mlp_w3 = X.mlp_w4 = nullptr;
     c.take(f.C, 1);

@@ -467,6 +467,71 @@ __device__ __forceinline__ bool slot_selected(const Search &X, const Cand &c, un
     return theta == ~0u || fkey(__ldcg(X.pred + c.pad)) <= theta;
 }
 
+// ---------------------------------------------------------------- certified pruning
+// A cluster evaluated at one voltage magnitude m has, per scenario, MICE =
+// max over members and phases of | |Vhat| - m | >= max over phases of
+// (hi - lo) / 2, half the spread of its members' |Vhat|.  So with
+// g_k = sum_l (max_p (hi - lo) / 2 - MICE_{k,l}) <= 0, a candidate (s, r)
+// changes SMICE by at least
+//   sum_l (max_p (max(hi_s, hi_r) - min(lo_s, lo_r)) / 2 - MICE_s - MICE_r)
+//   + sum of g_k over every other cluster
+// (the merged cluster, and every other cluster: affected ones by at least
+// g_k, unaffected ones by 0 >= g_k).  The sum over the other clusters is
+// bounded below by G - g_s - g_r, G = the sum of g_k over all clusters.
+// Directed rounding keeps every piece a bound: G sums floor(g_k 2^56) exactly
+// in integers (g_k rounded down), the candidate's part rounds down and
+// subtracts g_s, g_r rounded up.
+__device__ __forceinline__ double half_spread(double hi, double lo, bool up) {
+    return up ? __dmul_ru(__dsub_ru(hi, lo), 0.5) : __dmul_rd(__dsub_rd(hi, lo), 0.5);
+}
+// g_k rounded down (up = false) or up.
+__device__ double cluster_g(const Topo &T, const State &S, int n, int L, int k, bool up) {
+    const unsigned ph = T.ph[k];
+    double g = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double hs = 0.0;
+        for (int p = 0; p < 3; ++p)
+            if (ph >> p & 1u)
+                hs = fmax(hs, half_spread(ldd(S.hi + sidx(l, p, k, n)), ldd(S.lo + sidx(l, p, k, n)), up));
+        const double mc = ldd(S.mice + (size_t)l * n + k);
+        g = up ? __dadd_ru(g, __dsub_ru(hs, mc)) : __dadd_rd(g, __dsub_rd(hs, mc));
+    }
+    return g;
+}
+// floor(g_k 2^56) (g_k in [-1, 1]: no overflow).
+__device__ __forceinline__ long long cluster_g_fx(const Topo &T, const State &S, int n, int L, int k) {
+    return __double2ll_rd(cluster_g(T, S, n, L, k, false) * 72057594037927936.0);
+}
+// The candidate's own part of its bound (rounded down); +inf when the merged
+// cluster's half spread exceeds the margin in some scenario (surely infeasible).
+__device__ double cand_lb_part(const Topo &T, const State &S, int n, int L, const Cand &c, double margin) {
+    const unsigned phs = T.ph[c.s], phr = T.ph[c.r];
+    double part = 0.0;
+    for (int l = 0; l < L; ++l) {
+        double hs = 0.0;
+        for (int p = 0; p < 3; ++p) {
+            if (!(phs >> p & 1u)) continue;
+            double hi = ldd(S.hi + sidx(l, p, c.s, n)), lo = ldd(S.lo + sidx(l, p, c.s, n));
+            if (phr >> p & 1u) {
+                hi = fmax(hi, ldd(S.hi + sidx(l, p, c.r, n)));
+                lo = fmin(lo, ldd(S.lo + sidx(l, p, c.r, n)));
+            }
+            hs = fmax(hs, half_spread(hi, lo, false));
+        }
+        if (hs > margin) return INFINITY;
+        const double ms = ldd(S.mice + (size_t)l * n + c.s), mr = ldd(S.mice + (size_t)l * n + c.r);
+        part = __dadd_rd(part, __dsub_rd(__dsub_rd(hs, ms), mr));
+    }
+    const double gs = cluster_g(T, S, n, L, c.s, true), gr = cluster_g(T, S, n, L, c.r, true);
+    return __dsub_rd(__dsub_rd(part, gs), gr);
+}
+// Whether the bound excludes candidate ci from the tie band: its lower bound
+// on the score change exceeds thr (or it is surely infeasible).
+__device__ __forceinline__ bool lb_excludes(const Search &X, int ci, double G, double thr) {
+    const double part = ldd(X.lbp + ci);
+    return isinf(part) || __dadd_rd(part, G) > thr;
+}
+
 // Objective 1: the largest MICE among the clusters a candidate leaves unchanged,
 // i.e. over the super-node ranks outside [js, js+ns), [jr, jr+nr) and, when s is
 // the common ancestor, s's own rank.  Whole blocks of 32 ranks come from bmax,
@@ -496,10 +561,15 @@ __device__ __forceinline__ double unaffected_max(const Search &X, int nsn, int j
 __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, int n, int L, int SP, int g,
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
                               double margin, double *out_score, int *out_feas, bool prof, double &flops,
-                              bool obj1 = false, int nsn = 0, unsigned theta = ~0u) {
+                              bool obj1 = false, int nsn = 0, unsigned theta = ~0u, int pmode = 0,
+                              double pG = 0.0, double pthr = 0.0) {
     // one lane per phase (SP == 4), the scenarios in turn inside the lane
     const int lane = threadIdx.x & 31, p = lane & 3;
-    const bool chosen = !active || slot_selected(X, cd, theta);    // learned pruning
+    // pmode 0: the candidates the learned pruning keeps (all with theta = ~0u);
+    // pmode 1: the certified pruning's second pass, the candidates the first
+    // pass left out and the bound does not exclude (the others keep their scores)
+    const bool chosen = !active || (pmode == 0 ? slot_selected(X, cd, theta)
+                                               : (!slot_selected(X, cd, theta) && !lb_excludes(X, ci, pG, pthr)));
     int k = cd.r;
     bool sside = false;
     if (active && chosen) k = position_bus(list, cd, q, sside);
@@ -539,8 +609,10 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
     bool fin = false, direct = false;
     if (active && last) {
         if (!chosen) {                      // pruned: never the winner (the same value from every chunk)
-            out_score[ci] = INFINITY;
-            out_feas[ci] = 0;
+            if (pmode == 0) {
+                out_score[ci] = INFINITY;
+                out_feas[ci] = 0;
+            }
         } else if (np == 1) {               // the whole candidate lies in this chunk
             if (obj1) {
                 direct = true;
@@ -752,6 +824,7 @@ __device__ __forceinline__ double dval(unsigned long long k) {
 }
 struct MinF { __device__ float operator()(float a, float b) const { return fminf(a, b); } };
 struct MaxU { __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; } };
+struct SumLL { __device__ long long operator()(long long a, long long b) const { return a + b; } };
 
 // Exact selection over m entries with FP64 scores (entry i is candidate
 // map ? map[i] : i): minimum over feasible entries, tie band [min, min + tau],
@@ -1062,6 +1135,9 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         };
         const int told = t;
         const int *list_old = S.sn_list[told & 1];
+        // certified pruning: the slot of G that this pass's phase 2 accumulates
+        // (read last two passes ago; phase 1's closing barrier precedes the adds)
+        if (X.prune_exact && lead) C->gtot_fx[(t + 1) & 1] = 0;
         bool committed = false, finishing = false;
         int r0 = -1, s0 = -1, dir0 = 0, jr0 = 0;
         if (have) {
@@ -1166,7 +1242,47 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
                 stamp(PREC == 0 ? 0 : 1);
             }
-            if (theta != ~0u && sel.w < 0) {
+            if (theta != ~0u && X.prune_exact) {
+                // certified pruning, second pass: every candidate the learned
+                // ordering left out is scored too, unless its lower bound on the
+                // score change exceeds the first pass's best feasible score plus
+                // the tie band (1e-12 covers the rounding of the FP64 scores)
+                const long long gfx = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(&C->gtot_fx[t & 1]));
+                const double gbound = __ll2double_rd(gfx) * 1.3877787807814457e-17;     // 2^-56
+                const double thr = sel.w >= 0 ? __dadd_ru(__dadd_ru(ldd(X.score + sel.w), tau), 1e-12) : INFINITY;
+                long long excl = 0;
+                if (rank == 0) {
+                    for (int c = tid; c < nc; c += nt) {
+                        const Cand cd = ldcand(X.cand + c);
+                        if (!slot_selected(X, cd, theta) && lb_excludes(X, c, gbound, thr)) ++excl;
+                    }
+                    excl = block_reduce(excl, SumLL(), reinterpret_cast<long long *>(smu));
+                    if (tid == 0) C->pruned += excl;
+                }
+                const int *list = S.sn_list[t & 1];
+                for (int g = warp; g < nchunks; g += nwarps) {
+                    const int c0 = ldi(X.chunk_first + g);
+                    const int q = g * PPW + lane / SP;
+                    const int cb = (c0 + lane <= nc) ? ldi(X.base + c0 + lane) : 0x7fffffff;    // base[nc] = P
+                    const int off = chunk_offset(cb, g * PPW, PPW, lane / SP);
+                    const int cbase = __shfl_sync(0xffffffffu, cb, off);
+                    const int c = c0 + off;
+                    const bool active = q < P;
+                    Cand cd;
+                    cd.r = -1;
+                    int first = 0, np = 1;
+                    if (active) {
+                        cd = ldcand(X.cand + c);
+                        first = cbase / PPW;
+                        np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
+                    }
+                    score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin, X.score,
+                                  X.feas, false, flops, obj1, ns, theta, 1, gbound, thr);
+                }
+                if (!team_barrier(gb, C, G, epoch)) return;
+                sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
+            }
+            if (theta != ~0u && sel.w < 0 && !X.prune_exact) {
                 // learned pruning left no feasible candidate: evaluate them all in FP64
                 const int *list = S.sn_list[t & 1];
                 for (int g = warp; g < nchunks; g += nwarps) {
@@ -1370,6 +1486,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             const int rwarp = nwarps - 1 - warp;
             // CTAs whose (reversed) warps hold no list entry skip the loop and its reduction
             const bool has_list = (nwarps - (rank + 1) * (nt / 32)) * 32 < ns;
+            long long gsum = 0;                // certified pruning: sum of floor(g_k 2^56) over this thread's clusters
             for (int j0 = rwarp * 32; has_list && j0 < ns; j0 += gs) {    // warp-uniform trip count
                 const int j = j0 + lane;
                 double mr = 0.0;
@@ -1379,6 +1496,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                     for (int l = 0; l < L; ++l) mr = fmax(mr, ldd(S.mice + (size_t)l * n + k));
                     m = max(m, (unsigned long long)__double_as_longlong(mr));
                     if (obj1) X.mrank[j] = mr;
+                    if (X.prune_exact) gsum += cluster_g_fx(T, S, n, L, k);
                 }
                 if (obj1) {                                   // 32 consecutive ranks per warp
                     for (int o2 = 16; o2 > 0; o2 >>= 1) mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o2));
@@ -1389,6 +1507,11 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             if (has_list) {
                 m = block_reduce(m, MaxU(), smu);
                 if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
+            }
+            if (X.prune_exact) {               // G of the state after this merge (slot zeroed in phase 1)
+                for (int o2 = 16; o2 > 0; o2 >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o2);
+                if (lane == 0 && gsum != 0)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&C->gtot_fx[t & 1]), (unsigned long long)gsum);
             }
             stamp(9);
         }
@@ -1439,6 +1562,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         Cand c = X.slot[2 * gt + d];
                         if (c.s < 0) continue;
                         c.pad = 2 * gt + d;                 // the candidate's slot (its prediction)
+                        if (X.prune_exact) X.lbp[ci] = cand_lb_part(T, S, n, L, c, margin);
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;
@@ -1456,6 +1580,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         Cand c = X.slot[2 * j + d];
                         if (c.s < 0) continue;
                         c.pad = 2 * j + d;
+                        if (X.prune_exact) X.lbp[ci] = cand_lb_part(T, S, n, L, c, margin);
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;

@@ -185,3 +185,48 @@ def test_pruning_needs_a_scorer_of_the_right_width(ctx):
     with pytest.raises(K.OkrError) as e:
         ctx.reduce(f, K.default_params(scorer_topk=8))
     assert e.value.status == 1
+
+
+CERTIFIED = {
+    "feeder1000_300": lambda: fg.preset("feeder1000", n_bus=300),
+    "feeder2200_600": lambda: fg.preset("feeder2200", n_bus=600),
+    "feeder40": lambda: fg.preset("feeder40"),
+}
+
+
+@pytest.mark.parametrize("topk", [1, 16, 64])
+@pytest.mark.parametrize("name", sorted(CERTIFIED))
+def test_certified_pruning_reproduces_the_exhaustive_search(ctx, name, topk):
+    """prune_exact: the scorer's top-k candidates are scored first, then every
+    other candidate unless the certified lower bound (half spreads of the
+    clusters against their MICE) excludes it from the tie band.  Any weights
+    order the candidates; the decisions and scores must be the exhaustive FP64
+    sweep's, bit for bit, and the bound must exclude some candidates."""
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import scorer
+    f, run = CERTIFIED[name]()
+    ctx.scorer_init(14, scorer.init_params(14, 5))
+    p = dict(margin=run["margin"], target_reduction=min(run["target"], 0.9), precision=0, engine=1)
+    ctx.reduce(f, K.default_params(**p))
+    ref = ctx.decisions()
+    ref_s = ctx.summary()
+    ctx.reduce(f, K.default_params(scorer_topk=topk, prune_exact=1, **p))
+    got = ctx.decisions()
+    s = ctx.summary()
+    assert s["n_iter"] == ref_s["n_iter"] and s["stop_reason"] == ref_s["stop_reason"]
+    for k in ("s", "r", "score", "maxerr", "ncand"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert s["scorer_fallbacks"] == 0
+    assert 0 < s["pruned"] < s["candidates"]
+
+
+def test_certified_pruning_rejects_what_it_does_not_run(ctx):
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300._binding import EINVAL
+    f, run = fg.preset("feeder40")
+    for bad in (dict(prune_exact=1), dict(prune_exact=1, scorer_topk=8, precision=1),
+                dict(prune_exact=1, scorer_topk=8, objective=1), dict(prune_exact=2, scorer_topk=8),
+                dict(prune_exact=1, scorer_topk=8, engine=2)):
+        with pytest.raises(K.OkrError) as e:
+            ctx.reduce(f, K.default_params(margin=run["margin"], **bad))
+        assert e.value.status == EINVAL
