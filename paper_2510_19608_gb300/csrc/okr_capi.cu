@@ -515,7 +515,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     cudaError_t e = launch_search_inc(p->precision, ctx->fb.T, ctx->fb.S, X, ctx->fb.I, ctx->fb.C,
                                       p->engine == OKR_ENGINE_VERIFY ? 1 : 0, sh, &rec_used, st);
     cudaEventRecord(e1, st);
-    ctx->launches += 1;
+    ctx->launches += 2;                     // the first evaluation on many CTAs, the search on one
     okr_status s = OKR_OK;
     if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e));
     if (s == OKR_OK) {

@@ -901,8 +901,9 @@ struct Rec {
     unsigned long long *bmx;    // [nb]
     unsigned char *dirty;       // [nb]
     int nb;
-    __device__ __forceinline__ void touch(int sl) const { dirty[sl >> 5] = 1; }
-    __device__ __forceinline__ void touch_sn(int k) const { dirty[k >> 4] = 1; }   // maxm of super-node k (slot 2k)
+    // (dirty is null in the first evaluation on many CTAs: the search marks every block)
+    __device__ __forceinline__ void touch(int sl) const { if (dirty) dirty[sl >> 5] = 1; }
+    __device__ __forceinline__ void touch_sn(int k) const { if (dirty) dirty[k >> 4] = 1; }   // maxm of super-node k (slot 2k)
 };
 
 constexpr int kKeyShift = 44;                       // 2^-100 -> 2^-56 units
@@ -1308,7 +1309,7 @@ __host__ __device__ constexpr size_t base_bytes(int n, int se) {
 
 template <int NT, int PREC>
 __device__ void inc_run(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, bool verify,
-                        unsigned char *dyn, int rec_mode, int se, int cw) {
+                        unsigned char *dyn, int rec_mode, int se, int cw, bool pre_init) {
     static_assert(NT >= 128 && NT <= 1024 && NT % 32 == 0, "thread count");
     __shared__ __align__(16) EvalSmem<NT> E;
     __shared__ __align__(16) Red sred[33];
@@ -1389,10 +1390,19 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     }
     if (tid == 0) rank[n] = S.sn_rank[n];
     for (int j = tid; j < R.nb; j += NT) R.dirty[j] = 1;
-    __syncthreads();
-    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], 0, R, Lc, no_view());
-    __syncthreads();
-    {
+    if (pre_init) {
+        // the first evaluation ran on many CTAs (k_inc_init): its records are in
+        // device memory in the same layout; bring them into shared memory
+        if (rec_mode) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(I.recbuf);
+            uint4 *dst = reinterpret_cast<uint4 *>(recmem);
+            for (int i = tid; i < 3 * n; i += NT) dst[i] = src[i];       // 48 n bytes
+        }
+        __syncthreads();
+    } else {
+        __syncthreads();
+        rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair, n, &s_cnt[2], 0, R, Lc, no_view());
+        __syncthreads();
         const int ne = s_cnt[2];
         terms += run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, ne, kInit, Lc.lst[0], Lc.lst[0],
                                        -1, O, E, sscan, R, Lc);
@@ -1909,9 +1919,70 @@ namespace {
 // the merge beside the changed-set scan.
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
-                                                      int rec_mode, int se, int cw) {
+                                                      int rec_mode, int se, int cw, int pre_init) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
-    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode, se, cw);
+    inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode, se, cw, pre_init != 0);
+}
+
+// The first evaluation of every candidate (every slot pair from the initial
+// clusters, all singletons, every term), which needs no merge before it: the
+// pairs are spread over many CTAs (kInitPairs per CTA) instead of the one CTA
+// of the search.  Each CTA writes its pairs' candidates, carried sums and
+// selection records to device memory, in the layout the search reads
+// (k_search_inc with pre_init copies the records into shared memory).  The
+// terms are evaluated by the same code as in the search, so the carried sums
+// are the ones the search's own first evaluation gives.
+constexpr int kInitPairs = 8;
+template <int NT, int PREC>
+__global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
+    extern __shared__ __align__(16) unsigned char init_dyn[];
+    __shared__ __align__(16) EvalSmem<NT> E;
+    __shared__ int sscan[33];
+    __shared__ int s_cnt;
+    const int n = T.n, L = T.L, tid = threadIdx.x;
+    const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
+    const double margin = C->margin;
+    const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
+    const int w0 = blockIdx.x * kInitPairs, w1 = min(n, w0 + kInitPairs);
+    if (w0 >= n) return;
+    // every bus is its own super-node: the list and the ranks are the identity
+    unsigned short *list = reinterpret_cast<unsigned short *>(init_dyn);
+    for (int w = tid; w < n; w += NT) list[w] = (unsigned short)w;
+    for (int w = w0 + tid; w < w1; w += NT) I.fpair[w] = w;
+    if (tid == 0) s_cnt = 0;
+    Loc Lc;
+    Lc.wsm = nullptr;
+    Lc.wgl = I.work + 2 * (size_t)w0;           // at most two entries per pair
+    Lc.se = 0;
+    Lc.lst[0] = Lc.lst[1] = list;
+    Lc.ph = T.ph;
+    Lc.rank = S.sn_rank;
+    Rec R;
+    R.r0 = reinterpret_cast<u128 *>(I.recbuf);
+    R.r1 = reinterpret_cast<ulonglong2 *>(I.recbuf);
+    R.tkey = reinterpret_cast<unsigned *>(I.recbuf + (size_t)32 * n);
+    R.maxm = I.maxm;
+    R.span = reinterpret_cast<ushort4 *>(I.recbuf + (size_t)40 * n);
+    R.bsum = nullptr;
+    R.bcnt = nullptr;
+    R.bmx = nullptr;
+    R.dirty = nullptr;
+    R.nb = 0;
+    Ovl O;
+    O.map = nullptr;                            // (the first evaluation reads the stored state only)
+    O.cbuf = I.cbuf;
+    O.s = O.r = -1;
+    O.nfree = 0;
+    __syncthreads();
+    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair + w0, w1 - w0, &s_cnt, 0, R, Lc, no_view());
+    __syncthreads();
+    const long long terms = run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, s_cnt, kInit, list, list,
+                                                  -1, O, E, sscan, R, Lc);
+    if (C->profile) {                           // (phase-node, scenario) items
+        unsigned long long tt = (unsigned long long)terms;
+        for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
+        if ((tid & 31) == 0 && tt) atomicAdd(reinterpret_cast<unsigned long long *>(&C->sweep_ns), tt);
+    }
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
@@ -1935,7 +2006,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode, se, cw);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode, se, cw, false);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -1984,8 +2055,16 @@ namespace {
 template <int NT, int PREC>
 cudaError_t launch_one(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, int use, size_t smem, const IncShape &sh,
                        cudaStream_t st) {
-    cudaError_t e = set_smem(k_search_inc<NT, PREC>, smem);
-    if (e == cudaSuccess) k_search_inc<NT, PREC><<<1, NT, smem, st>>>(T, S, X, I, C, verify, use, sh.se, sh.cw);
+    // the first evaluation on many CTAs, then the search on one
+    constexpr int kInitThreads = 384;
+    const int ginit = (T.n + kInitPairs - 1) / kInitPairs;
+    const size_t ismem = align16((size_t)2 * T.n);
+    cudaError_t e = cudaSuccess;
+    if (ismem > 48 * 1024) e = set_smem(k_inc_init<kInitThreads, PREC>, ismem);
+    if (e == cudaSuccess) k_inc_init<kInitThreads, PREC><<<ginit, kInitThreads, ismem, st>>>(T, S, X, I, C);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e == cudaSuccess) e = set_smem(k_search_inc<NT, PREC>, smem);
+    if (e == cudaSuccess) k_search_inc<NT, PREC><<<1, NT, smem, st>>>(T, S, X, I, C, verify, use, sh.se, sh.cw, 1);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
