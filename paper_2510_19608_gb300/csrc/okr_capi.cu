@@ -1008,6 +1008,8 @@ struct BatchRun {
     int *order_d = nullptr, *queue_d = nullptr, *err_d = nullptr, *super_all_d = nullptr;
     double *maxerr_d = nullptr;
     BatchTeam *teams_d = nullptr;
+    int *ictas_d = nullptr;                         // incremental groups: first CTA of each feeder's first evaluation
+    int init_ctas[2] = {0, 0};                      // CTAs of that evaluation, per precision
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     ~BatchRun() {
         for (cudaEvent_t e : ev)
@@ -1102,6 +1104,7 @@ static okr_status batch_measure(okr_ctx *ctx, int32_t nf, const okr_feeder *feed
     m.take(R.maxerr_d, nf);
     R.res_len = m.used - R.res_off;
     m.take(R.teams_d, 2 * (size_t)R.max_teams);
+    m.take(R.ictas_d, (size_t)nf + 1);
     R.in_off.assign(nf, 0);
     for (int f = 0; f < nf; ++f) {
         const size_t n = R.nbus[f], L = R.nscen[f];
@@ -1148,6 +1151,7 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
     md.take(R.err_d, nf);
     md.take(R.maxerr_d, nf);
     md.take(R.teams_d, 2 * (size_t)R.max_teams);
+    md.take(R.ictas_d, (size_t)nf + 1);
     R.super_all_d = reinterpret_cast<int *>(base + R.super_off);
     Carver mh;                                  // the same offsets in the host buffer
     mh.base = hb;
@@ -1161,6 +1165,8 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
     mh.take(maxerr_h, nf);
     BatchTeam *teams_h;
     mh.take(teams_h, 2 * (size_t)R.max_teams);
+    int *ictas_h;
+    mh.take(ictas_h, (size_t)nf + 1);
     for (int i = 0; i < 2 * R.max_teams; ++i) {
         teams_h[i].ctrl.max_spins = R.params[0].max_spins > 0 ? R.params[0].max_spins : kDefaultSpins;
         teams_h[i].slot = 0;
@@ -1238,15 +1244,27 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
         cc.max_spins = P->max_spins > 0 ? P->max_spins : kDefaultSpins;
     }
     int k = 0;
-    for (int g = 0; g < 4; ++g)
-        for (int f : R.ord[g]) order_h[k++] = f;
+    for (int g = 0; g < 4; ++g) {
+        int ctas = 0;
+        for (int f : R.ord[g]) {
+            if (g >= 2) {                           // the incremental groups' first evaluation on many CTAs
+                ictas_h[k] = ctas;
+                ctas += (R.nbus[f] + kIncInitPairs - 1) / kIncInitPairs;
+            }
+            order_h[k++] = f;
+        }
+        if (g >= 2) R.init_ctas[g - 2] = ctas;
+    }
     for (cudaEvent_t &e : R.ev)
         if (!e) CK(cudaEventCreate(&e));
     // attributes the launches need, set before any stream capture
     for (int g = 2; g < 4; ++g) {
         int max_n = 2;
         for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
-        if (!R.ord[g].empty()) CK(prepare_search_inc_batch(g - 2, max_n, R.shape));
+        if (!R.ord[g].empty()) {
+            CK(prepare_search_inc_batch(g - 2, max_n, R.shape));
+            CK(prepare_inc_init_batch(g - 2, max_n));
+        }
     }
     return OKR_OK;
 }
@@ -1268,6 +1286,8 @@ static okr_status batch_enqueue(okr_ctx *ctx, BatchRun &R, cudaStream_t st, bool
             R.ctas = std::max(R.ctas, cnt);
             int max_n = 2;
             for (int f : R.ord[g]) max_n = std::max(max_n, R.nbus[f]);
+            CK(launch_inc_init_batch(g - 2, max_n, R.bf_d, R.order_d + first, R.ictas_d + first, cnt,
+                                     R.init_ctas[g - 2], st));
             CK(launch_search_inc_batch(g - 2, max_n, R.bf_d, R.order_d + first, cnt, R.shape, st));
             continue;
         }

@@ -1195,16 +1195,13 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
     return terms;
 }
 
-// Rebuilds the slot pairs listed in fp[0, nf) from the clusters as the view
-// shows them and appends a full work entry for each valid candidate at entry
-// base + *cnt (*cnt: a shared counter; the caller synchronises before reading
-// it).
+// Rebuilds slot pair w from the clusters as the view shows them and appends
+// a full work entry for each valid candidate at entry base + *cnt (*cnt: a
+// shared counter; the caller synchronises before reading it).
 template <int NT, int PREC>
-__device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
-                              int *cnt, int base, const Rec &R, const Loc &Lc, const View &V) {
-    // from the last thread down: beside a merge, the first threads write the merge
-    for (int i = NT - 1 - (int)threadIdx.x; i < nf; i += NT) {
-        const int w = fp[i];
+__device__ void rebuild_pair(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int w, int *cnt,
+                             int base, const Rec &R, const Loc &Lc, const View &V) {
+    {
         Cand c[2];
         const int x = slot_geometry(T, S, V, n, w, c[0], c[1]);
         I.qpar[w] = x;
@@ -1236,6 +1233,14 @@ __device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, co
             }
         }
     }
+}
+
+// The slot pairs listed in fp[0, nf), from the last thread down.
+template <int NT, int PREC>
+__device__ void rebuild_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, int n, const int *fp, int nf,
+                              int *cnt, int base, const Rec &R, const Loc &Lc, const View &V) {
+    for (int i = NT - 1 - (int)threadIdx.x; i < nf; i += NT)
+        rebuild_pair<NT, PREC>(T, S, X, I, n, fp[i], cnt, base, R, Lc, V);
 }
 
 }  // namespace
@@ -1932,24 +1937,21 @@ __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X,
 // (k_search_inc with pre_init copies the records into shared memory).  The
 // terms are evaluated by the same code as in the search, so the carried sums
 // are the ones the search's own first evaluation gives.
-constexpr int kInitPairs = 8;
+constexpr int kInitPairs = kIncInitPairs;
+// The pairs [w0, w0 + kInitPairs) of one feeder (list: shared scratch of n
+// 16-bit entries).
 template <int NT, int PREC>
-__global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
-    extern __shared__ __align__(16) unsigned char init_dyn[];
-    __shared__ __align__(16) EvalSmem<NT> E;
-    __shared__ int sscan[33];
-    __shared__ int s_cnt;
+__device__ void inc_init_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, int w0,
+                               unsigned short *list, EvalSmem<NT> &E, int *sscan, int *s_cnt) {
     const int n = T.n, L = T.L, tid = threadIdx.x;
     const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
     const double margin = C->margin;
     const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
-    const int w0 = blockIdx.x * kInitPairs, w1 = min(n, w0 + kInitPairs);
-    if (w0 >= n) return;
+    const int w1 = min(n, w0 + kInitPairs);
     // every bus is its own super-node: the list and the ranks are the identity
-    unsigned short *list = reinterpret_cast<unsigned short *>(init_dyn);
     for (int w = tid; w < n; w += NT) list[w] = (unsigned short)w;
     for (int w = w0 + tid; w < w1; w += NT) I.fpair[w] = w;
-    if (tid == 0) s_cnt = 0;
+    if (tid == 0) *s_cnt = 0;
     Loc Lc;
     Lc.wsm = nullptr;
     Lc.wgl = I.work + 2 * (size_t)w0;           // at most two entries per pair
@@ -1974,9 +1976,9 @@ __global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc 
     O.s = O.r = -1;
     O.nfree = 0;
     __syncthreads();
-    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair + w0, w1 - w0, &s_cnt, 0, R, Lc, no_view());
+    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair + w0, w1 - w0, s_cnt, 0, R, Lc, no_view());
     __syncthreads();
-    const long long terms = run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, s_cnt, kInit, list, list,
+    const long long terms = run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, *s_cnt, kInit, list, list,
                                                   -1, O, E, sscan, R, Lc);
     if (C->profile) {                           // (phase-node, scenario) items
         unsigned long long tt = (unsigned long long)terms;
@@ -1985,10 +1987,59 @@ __global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc 
     }
 }
 
+template <int NT, int PREC>
+__global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
+    extern __shared__ __align__(16) unsigned char init_dyn[];
+    __shared__ __align__(16) EvalSmem<NT> E;
+    __shared__ int sscan[33];
+    __shared__ int s_cnt;
+    const int w0 = blockIdx.x * kInitPairs;
+    if (w0 >= T.n) return;
+    inc_init_pairs<NT, PREC>(T, S, X, I, C, w0, reinterpret_cast<unsigned short *>(init_dyn), E, sscan, &s_cnt);
+}
+
+// The same for many feeders: cta_off[i] = the first CTA of the i-th feeder of
+// the order (ceil(n / kInitPairs) CTAs each); feeders whose setup failed are
+// skipped.
+template <int NT, int PREC>
+__global__ void __launch_bounds__(NT) k_inc_init_batch(const BatchFeeder *fd, const int *order, const int *cta_off,
+                                                       int nf) {
+    extern __shared__ __align__(16) unsigned char init_dyn[];
+    __shared__ __align__(16) EvalSmem<NT> E;
+    __shared__ int sscan[33];
+    __shared__ int s_cnt;
+    __shared__ Topo sT;
+    __shared__ State sS;
+    __shared__ Search sX;
+    __shared__ Inc sI;
+    __shared__ int s_f, s_w0;
+    const int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = nf - 1;                 // the last feeder whose first CTA is <= b
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta_off[mid] <= b) lo = mid;
+            else hi = mid - 1;
+        }
+        const int f = order[lo];
+        s_f = f;
+        s_w0 = (b - cta_off[lo]) * kInitPairs;
+        sT = fd[f].T;
+        sS = fd[f].S;
+        sX = fd[f].X;
+        sI = fd[f].I;
+    }
+    __syncthreads();
+    const int f = s_f;
+    if (*fd[f].setup_err != 0 || s_w0 >= sT.n) return;
+    inc_init_pairs<NT, PREC>(sT, sS, sX, sI, fd[f].C, s_w0, reinterpret_cast<unsigned short *>(init_dyn), E, sscan,
+                             &s_cnt);
+}
+
 // One CTA per feeder, feeders in the order given (largest first).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, const int *order, int nf,
-                                                         int rec_mode, int se, int cw) {
+                                                         int rec_mode, int se, int cw, int pre_init) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
     __shared__ Topo sT;
     __shared__ State sS;
@@ -2006,7 +2057,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
     __syncthreads();
     Ctrl *C = fd[f].C;
     const bool ok = *fd[f].setup_err == 0;
-    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode, se, cw, false);
+    if (ok) inc_run<NT, PREC>(sT, sS, sX, sI, C, false, inc_dyn, rec_mode, se, cw, pre_init != 0);
     __syncthreads();
     for (int i = threadIdx.x; i < sT.n; i += NT) fd[f].super_out[i] = ok ? sT.orig[sS.label[sT.pre[i]]] : -1;
     if (threadIdx.x == 0) {
@@ -2016,6 +2067,7 @@ __global__ void __launch_bounds__(NT) k_search_inc_batch(const BatchFeeder *fd, 
 }
 
 constexpr size_t kIncSmemMax = 200 * 1024;  // largest dynamic shared memory of one search
+constexpr int kInitThreads = 384;           // CTAs of the first evaluation
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
@@ -2056,7 +2108,6 @@ template <int NT, int PREC>
 cudaError_t launch_one(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, int use, size_t smem, const IncShape &sh,
                        cudaStream_t st) {
     // the first evaluation on many CTAs, then the search on one
-    constexpr int kInitThreads = 384;
     const int ginit = (T.n + kInitPairs - 1) / kInitPairs;
     const size_t ismem = align16((size_t)2 * T.n);
     cudaError_t e = cudaSuccess;
@@ -2076,8 +2127,8 @@ cudaError_t set_batch_smem(int precision, size_t smem) {
 template <int NT>
 void launch_batch(int precision, const BatchFeeder *fd, const int *order, int nf, int use, size_t smem,
                   const IncShape &sh, cudaStream_t st) {
-    if (precision == 1) k_search_inc_batch<NT, 1><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw);
-    else k_search_inc_batch<NT, 0><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw);
+    if (precision == 1) k_search_inc_batch<NT, 1><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw, 1);
+    else k_search_inc_batch<NT, 0><<<nf, NT, smem, st>>>(fd, order, nf, use, sh.se, sh.cw, 1);
 }
 
 }  // namespace
@@ -2118,6 +2169,22 @@ cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder 
     if (sh.threads == 256) launch_batch<256>(precision, fd, order, nf, use, smem, sh, st);
     else if (sh.threads == 384) launch_batch<384>(precision, fd, order, nf, use, smem, sh, st);
     else launch_batch<512>(precision, fd, order, nf, use, smem, sh, st);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_inc_init_batch(int precision, int max_n) {
+    const size_t ismem = align16((size_t)2 * max_n);
+    if (ismem <= 48 * 1024) return cudaSuccess;
+    return precision == 1 ? set_smem(k_inc_init_batch<kInitThreads, 1>, ismem)
+                          : set_smem(k_inc_init_batch<kInitThreads, 0>, ismem);
+}
+
+cudaError_t launch_inc_init_batch(int precision, int max_n, const BatchFeeder *fd, const int *order,
+                                  const int *cta_off, int nf, int ctas, cudaStream_t st) {
+    if (nf <= 0 || ctas <= 0) return cudaSuccess;
+    const size_t ismem = align16((size_t)2 * max_n);
+    if (precision == 1) k_inc_init_batch<kInitThreads, 1><<<ctas, kInitThreads, ismem, st>>>(fd, order, cta_off, nf);
+    else k_inc_init_batch<kInitThreads, 0><<<ctas, kInitThreads, ismem, st>>>(fd, order, cta_off, nf);
     return cudaGetLastError();
 }
 

@@ -153,6 +153,7 @@ struct IncShape {
     int threads, cw, se, rec;
 };
 constexpr int kIncDefaultThreads = 384;
+constexpr int kIncInitPairs = 8;        // slot pairs per CTA of the first evaluation
 // Out-of-range fields replaced by the defaults (384 threads, 2 evaluation
 // warps (4 with 512 threads), 256 shared entries, automatic records).
 IncShape inc_shape_resolve(IncShape sh);
@@ -170,5 +171,12 @@ cudaError_t launch_search_inc(int precision, Topo T, State S, Search X, Inc I, C
 cudaError_t prepare_search_inc_batch(int precision, int max_n, IncShape sh);
 cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder *fd, const int *order, int nf,
                                     IncShape sh, cudaStream_t st);
+// The batch's first evaluation on many CTAs, before launch_search_inc_batch
+// (which then takes it as done): cta_off[i] = the first CTA of order[i]
+// (ceil(n / kIncInitPairs) each), ctas = their total.  prepare_inc_init_batch sets the
+// kernel's shared-memory attribute (before any stream capture).
+cudaError_t prepare_inc_init_batch(int precision, int max_n);
+cudaError_t launch_inc_init_batch(int precision, int max_n, const BatchFeeder *fd, const int *order,
+                                  const int *cta_off, int nf, int ctas, cudaStream_t st);
 
 }  // namespace okr
