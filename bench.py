@@ -334,6 +334,7 @@ def learned_line(K, ctx, n_train=64, record=64):
     t0 = time.perf_counter()
     loss = scorer.train(ctx, X, T, epochs=8, batch=8192, lr=1e-3, seed=0)
     t_train = time.perf_counter() - t0
+    trained = ctx.scorer_params().copy()
     f3, run3 = fg.preset("feeder3100")
     Xt, Tt, groups = scorer.collect(ctx, [(f3, K.default_params(margin=run3["margin"], target_reduction=run3["target"],
                                                                 max_merges=record))], record)
@@ -345,11 +346,14 @@ def learned_line(K, ctx, n_train=64, record=64):
     for name in ("feeder3100", "feeder2200", WORKLOAD):
         fx, rx = fg.preset(name)
         rows = {}
-        # (name, top-k, engine, precision, certified pruning)
-        for key, k, engine, prec, exact in (("exhaustive_incremental", 0, 2, 1, 0), ("exhaustive_sweep", 0, 1, 1, 0),
-                                            ("top64", 64, 1, 1, 0), ("top16", 16, 1, 1, 0),
-                                            ("exhaustive_sweep_fp64", 0, 1, 0, 0),
-                                            ("certified_top64_fp64", 64, 1, 0, 1)):
+        # (name, top-k, engine, precision, certified pruning, trained weights)
+        for key, k, engine, prec, exact, tw in (("exhaustive_incremental", 0, 2, 1, 0, 1),
+                                                ("exhaustive_sweep", 0, 1, 1, 0, 1),
+                                                ("top64", 64, 1, 1, 0, 1), ("top16", 16, 1, 1, 0, 1),
+                                                ("exhaustive_sweep_fp64", 0, 1, 0, 0, 1),
+                                                ("certified_top64_fp64", 64, 1, 0, 1, 1),
+                                                ("certified_top64_fp64_untrained", 64, 1, 0, 1, 0)):
+            ctx.scorer_init(X.shape[1], trained if tw else scorer.init_params(X.shape[1], 5))
             px = K.default_params(margin=rx["margin"], target_reduction=rx["target"], precision=prec, scorer_topk=k,
                                   engine=engine, prune_exact=exact)
             ctx.reduce(fx, px)                                        # warm-up
@@ -365,6 +369,7 @@ def learned_line(K, ctx, n_train=64, record=64):
                 "fallbacks": sm["scorer_fallbacks"]}
             if exact:
                 rows[key]["pruned_fraction"] = sm["pruned"] / max(1, sm["candidates"])
+                rows[key]["candidates_scored"] = sm["candidates"] - sm["pruned"]
                 rows[key]["same_decisions_as_exhaustive_fp64"] = (
                     sm["smice"] == rows["exhaustive_sweep_fp64"]["smice"]
                     and sm["n_iter"] == rows["exhaustive_sweep_fp64"]["merges"])

@@ -413,6 +413,10 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     CK(cudaMemsetAsync(X.arrive, 0, sizeof(int) * 2 * n, st));
     CK(cudaMemsetAsync(X.mrank, 0, sizeof(double) * n, st));           // every MICE starts at 0
     CK(cudaMemsetAsync(X.bmax, 0, sizeof(double) * (n / 32 + 2), st));
+    if (p->prune_exact) {                       // every g_k starts at 0 (singletons: no spread, MICE 0)
+        CK(cudaMemsetAsync(X.gpre, 0, sizeof(long long) * n, st));
+        CK(cudaMemsetAsync(X.gbp, 0, sizeof(long long) * (n / 32 + 2), st));
+    }
     CK(cudaMemsetAsync(ctx->fb.gb, 0, sizeof(GridBar), st));
     if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));
     ctx->rec_iters = p->record_iters;
@@ -701,9 +705,9 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
         delete ctx;
         return OKR_ECUDA;
     }
-    int coop = 0, per_sm = 0;
+    int coop = 0;
     if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop ||
-        (per_sm = search_blocks_per_sm()) < 1) {
+        search_blocks_per_sm() < 1) {
         delete ctx;
         return OKR_ECUDA;
     }

@@ -121,7 +121,7 @@ struct Ctrl {
     long long candidates;   // candidates evaluated over the run
     int inc_mismatch;       // incremental search, verification mode: slots whose carried score differs
     int pad2;
-    long long gtot_fx[2];   // certified pruning: sum over super-nodes of floor(g_k 2^56), by merge parity
+    long long pad3[2];
     long long pruned;       // certified pruning: candidates the bound excluded over the run
     long long max_spins;    // limit of a device-side wait
     double sweep_flops;     // algorithmic flops of the sweeps (profile mode)
@@ -203,9 +203,15 @@ struct Search {
     const uint16_t *mlp_w1, *mlp_w2, *mlp_w3, *mlp_w4;
     float *pred;            // [2n]
     // certified pruning (prune_exact = 1, with topk > 0): per compact candidate the
-    // part of its lower bound that depends on it (lbp; +inf: surely infeasible)
+    // part of its lower bound that depends on it (lbp; +inf: surely infeasible);
+    // per super-node rank floor(g_k 2^56) summed within its block of 32 ranks
+    // (gpre, inclusive), per block the total (gblk) and the sum of the blocks
+    // before it (gbp, one past the last block included)
     int prune_exact;
     double *lbp;            // [2n]
+    long long *gpre;        // [n]
+    long long *gblk;        // [n / 32 + 2]
+    long long *gbp;         // [n / 32 + 2]
     int *rec_count;
 };
 

@@ -470,37 +470,30 @@ __device__ __forceinline__ bool slot_selected(const Search &X, const Cand &c, un
 // ---------------------------------------------------------------- certified pruning
 // A cluster evaluated at one voltage magnitude m has, per scenario, MICE =
 // max over members and phases of | |Vhat| - m | >= max over phases of
-// (hi - lo) / 2, half the spread of its members' |Vhat|.  So with
-// g_k = sum_l (max_p (hi - lo) / 2 - MICE_{k,l}) <= 0, a candidate (s, r)
-// changes SMICE by at least
+// (hi - lo) / 2, half the spread of its members' |Vhat|.  A candidate (s, r)
+// changes SMICE by (new MICE of s u r) - MICE_s - MICE_r plus, over its other
+// positions k, (new MICE_k) - MICE_k: the clusters outside its positions keep
+// their voltages.  With g_k = sum_l (max_p (hi - lo) / 2 - MICE_{k,l}) <= 0
+// the change is therefore at least
 //   sum_l (max_p (max(hi_s, hi_r) - min(lo_s, lo_r)) / 2 - MICE_s - MICE_r)
-//   + sum of g_k over every other cluster
-// (the merged cluster, and every other cluster: affected ones by at least
-// g_k, unaffected ones by 0 >= g_k).  The sum over the other clusters is
-// bounded below by G - g_s - g_r, G = the sum of g_k over all clusters.
-// Directed rounding keeps every piece a bound: G sums floor(g_k 2^56) exactly
-// in integers (g_k rounded down), the candidate's part rounds down and
-// subtracts g_s, g_r rounded up.
-__device__ __forceinline__ double half_spread(double hi, double lo, bool up) {
-    return up ? __dmul_ru(__dsub_ru(hi, lo), 0.5) : __dmul_rd(__dsub_rd(hi, lo), 0.5);
-}
-// g_k rounded down (up = false) or up.
-__device__ double cluster_g(const Topo &T, const State &S, int n, int L, int k, bool up) {
+//   + the sum of g_k over the positions other than s and r.
+// The positions are the super-nodes whose ranks lie in the candidate's two
+// ranges (and s).  Their sum comes from prefix sums over ranks of
+// floor(g_k 2^56), exact in 64-bit integers (g_k rounded down), less the
+// values of s and r where their ranks lie in the ranges; the candidate's own
+// part is rounded down.
+__device__ __forceinline__ double half_spread_rd(double hi, double lo) { return __dmul_rd(__dsub_rd(hi, lo), 0.5); }
+// floor(g_k 2^56) (|g_k| <= L: no overflow).
+__device__ long long cluster_g_fx(const Topo &T, const State &S, int n, int L, int k) {
     const unsigned ph = T.ph[k];
     double g = 0.0;
     for (int l = 0; l < L; ++l) {
         double hs = 0.0;
         for (int p = 0; p < 3; ++p)
-            if (ph >> p & 1u)
-                hs = fmax(hs, half_spread(ldd(S.hi + sidx(l, p, k, n)), ldd(S.lo + sidx(l, p, k, n)), up));
-        const double mc = ldd(S.mice + (size_t)l * n + k);
-        g = up ? __dadd_ru(g, __dsub_ru(hs, mc)) : __dadd_rd(g, __dsub_rd(hs, mc));
+            if (ph >> p & 1u) hs = fmax(hs, half_spread_rd(ldd(S.hi + sidx(l, p, k, n)), ldd(S.lo + sidx(l, p, k, n))));
+        g = __dadd_rd(g, __dsub_rd(hs, ldd(S.mice + (size_t)l * n + k)));
     }
-    return g;
-}
-// floor(g_k 2^56) (g_k in [-1, 1]: no overflow).
-__device__ __forceinline__ long long cluster_g_fx(const Topo &T, const State &S, int n, int L, int k) {
-    return __double2ll_rd(cluster_g(T, S, n, L, k, false) * 72057594037927936.0);
+    return __double2ll_rd(g * 72057594037927936.0);
 }
 // The candidate's own part of its bound (rounded down); +inf when the merged
 // cluster's half spread exceeds the margin in some scenario (surely infeasible).
@@ -516,20 +509,36 @@ __device__ double cand_lb_part(const Topo &T, const State &S, int n, int L, cons
                 hi = fmax(hi, ldd(S.hi + sidx(l, p, c.r, n)));
                 lo = fmin(lo, ldd(S.lo + sidx(l, p, c.r, n)));
             }
-            hs = fmax(hs, half_spread(hi, lo, false));
+            hs = fmax(hs, half_spread_rd(hi, lo));
         }
         if (hs > margin) return INFINITY;
         const double ms = ldd(S.mice + (size_t)l * n + c.s), mr = ldd(S.mice + (size_t)l * n + c.r);
         part = __dadd_rd(part, __dsub_rd(__dsub_rd(hs, ms), mr));
     }
-    const double gs = cluster_g(T, S, n, L, c.s, true), gr = cluster_g(T, S, n, L, c.r, true);
-    return __dsub_rd(__dsub_rd(part, gs), gr);
+    return part;
+}
+// The sum of floor(g_k 2^56) over the ranks below j: the blocks of 32 ranks
+// before j's (gbp) and the ranks of j's block below j (gpre, inclusive per block).
+__device__ __forceinline__ long long g_prefix(const Search &X, int j) {
+    long long v = __ldcg(X.gbp + (j >> 5));
+    if (j & 31) v += __ldcg(X.gpre + j - 1);
+    return v;
 }
 // Whether the bound excludes candidate ci from the tie band: its lower bound
 // on the score change exceeds thr (or it is surely infeasible).
-__device__ __forceinline__ bool lb_excludes(const Search &X, int ci, double G, double thr) {
+__device__ __forceinline__ bool lb_excludes(const Search &X, const State &S, int ci, const Cand &cd, double thr) {
     const double part = ldd(X.lbp + ci);
-    return isinf(part) || __dadd_rd(part, G) > thr;
+    if (isinf(part)) return true;
+    long long g = 0;
+    if (cd.ns > 0) g += g_prefix(X, cd.js + cd.ns) - g_prefix(X, cd.js);
+    if (cd.nr > 0) g += g_prefix(X, cd.jr + cd.nr) - g_prefix(X, cd.jr);
+    auto in_ranges = [&](int j) {
+        return (j >= cd.js && j < cd.js + cd.ns) || (j >= cd.jr && j < cd.jr + cd.nr);
+    };
+    const int rs = ldi(S.sn_rank + cd.s), rr = ldi(S.sn_rank + cd.r);
+    if (in_ranges(rs)) g -= g_prefix(X, rs + 1) - g_prefix(X, rs);
+    if (in_ranges(rr)) g -= g_prefix(X, rr + 1) - g_prefix(X, rr);
+    return __dadd_rd(part, __ll2double_rd(g) * 1.3877787807814457e-17) > thr;      // 2^-56
 }
 
 // Objective 1: the largest MICE among the clusters a candidate leaves unchanged,
@@ -562,14 +571,18 @@ __device__ void score64_chunk(const Topo &T, const State &S, const Search &X, in
                               bool active, int ci, const Cand &cd, int q, int first, int np, const int *list,
                               double margin, double *out_score, int *out_feas, bool prof, double &flops,
                               bool obj1 = false, int nsn = 0, unsigned theta = ~0u, int pmode = 0,
-                              double pG = 0.0, double pthr = 0.0) {
+                              double pthr = 0.0, int *n_excl = nullptr) {
     // one lane per phase (SP == 4), the scenarios in turn inside the lane
     const int lane = threadIdx.x & 31, p = lane & 3;
     // pmode 0: the candidates the learned pruning keeps (all with theta = ~0u);
     // pmode 1: the certified pruning's second pass, the candidates the first
     // pass left out and the bound does not exclude (the others keep their scores)
-    const bool chosen = !active || (pmode == 0 ? slot_selected(X, cd, theta)
-                                               : (!slot_selected(X, cd, theta) && !lb_excludes(X, ci, pG, pthr)));
+    bool chosen = !active || slot_selected(X, cd, theta);
+    if (pmode == 1 && active) {
+        const bool excl = !chosen && lb_excludes(X, S, ci, cd, pthr);
+        if (excl && q == 0 && p == 0) ++*n_excl;        // counted once per candidate
+        chosen = !chosen && !excl;
+    }
     int k = cd.r;
     bool sside = false;
     if (active && chosen) k = position_bus(list, cd, q, sside);
@@ -1135,9 +1148,6 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         };
         const int told = t;
         const int *list_old = S.sn_list[told & 1];
-        // certified pruning: the slot of G that this pass's phase 2 accumulates
-        // (read last two passes ago; phase 1's closing barrier precedes the adds)
-        if (X.prune_exact && lead) C->gtot_fx[(t + 1) & 1] = 0;
         bool committed = false, finishing = false;
         int r0 = -1, s0 = -1, dir0 = 0, jr0 = 0;
         if (have) {
@@ -1247,18 +1257,8 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 // ordering left out is scored too, unless its lower bound on the
                 // score change exceeds the first pass's best feasible score plus
                 // the tie band (1e-12 covers the rounding of the FP64 scores)
-                const long long gfx = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(&C->gtot_fx[t & 1]));
-                const double gbound = __ll2double_rd(gfx) * 1.3877787807814457e-17;     // 2^-56
                 const double thr = sel.w >= 0 ? __dadd_ru(__dadd_ru(ldd(X.score + sel.w), tau), 1e-12) : INFINITY;
-                long long excl = 0;
-                if (rank == 0) {
-                    for (int c = tid; c < nc; c += nt) {
-                        const Cand cd = ldcand(X.cand + c);
-                        if (!slot_selected(X, cd, theta) && lb_excludes(X, c, gbound, thr)) ++excl;
-                    }
-                    excl = block_reduce(excl, SumLL(), reinterpret_cast<long long *>(smu));
-                    if (tid == 0) C->pruned += excl;
-                }
+                int excl = 0;
                 const int *list = S.sn_list[t & 1];
                 for (int g = warp; g < nchunks; g += nwarps) {
                     const int c0 = ldi(X.chunk_first + g);
@@ -1277,8 +1277,10 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         np = (cbase + cand_positions(cd) - 1) / PPW - first + 1;
                     }
                     score64_chunk(T, S, X, n, L, SP, g, active, c, cd, q - cbase, first, np, list, margin, X.score,
-                                  X.feas, false, flops, obj1, ns, theta, 1, gbound, thr);
+                                  X.feas, false, flops, obj1, ns, theta, 1, thr, &excl);
                 }
+                for (int o2 = 16; o2 > 0; o2 >>= 1) excl += __shfl_xor_sync(0xffffffffu, excl, o2);
+                if (lane == 0 && excl) atomicAdd(reinterpret_cast<unsigned long long *>(&C->pruned), (unsigned long long)excl);
                 if (!team_barrier(gb, C, G, epoch)) return;
                 sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
             }
@@ -1486,17 +1488,25 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             const int rwarp = nwarps - 1 - warp;
             // CTAs whose (reversed) warps hold no list entry skip the loop and its reduction
             const bool has_list = (nwarps - (rank + 1) * (nt / 32)) * 32 < ns;
-            long long gsum = 0;                // certified pruning: sum of floor(g_k 2^56) over this thread's clusters
             for (int j0 = rwarp * 32; has_list && j0 < ns; j0 += gs) {    // warp-uniform trip count
                 const int j = j0 + lane;
                 double mr = 0.0;
+                long long gk = 0;              // certified pruning: floor(g_k 2^56) of rank j
                 if (j < ns) {
                     const int k = ldi(list_old + j + (j >= jr0 ? 1 : 0));
                     list_new[j] = k;
                     for (int l = 0; l < L; ++l) mr = fmax(mr, ldd(S.mice + (size_t)l * n + k));
                     m = max(m, (unsigned long long)__double_as_longlong(mr));
                     if (obj1) X.mrank[j] = mr;
-                    if (X.prune_exact) gsum += cluster_g_fx(T, S, n, L, k);
+                    if (X.prune_exact) gk = cluster_g_fx(T, S, n, L, k);
+                }
+                if (X.prune_exact) {                          // prefix within the block of 32 ranks
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const long long y = __shfl_up_sync(0xffffffffu, gk, o2);
+                        if (lane >= o2) gk += y;
+                    }
+                    if (j < ns) X.gpre[j] = gk;
+                    if (lane == 31) X.gblk[j0 >> 5] = gk;
                 }
                 if (obj1) {                                   // 32 consecutive ranks per warp
                     for (int o2 = 16; o2 > 0; o2 >>= 1) mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o2));
@@ -1507,11 +1517,6 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             if (has_list) {
                 m = block_reduce(m, MaxU(), smu);
                 if (tid == 0 && m > 0) atomicMax((unsigned long long *)&X.dec_maxerr[told], m);
-            }
-            if (X.prune_exact) {               // G of the state after this merge (slot zeroed in phase 1)
-                for (int o2 = 16; o2 > 0; o2 >>= 1) gsum += __shfl_xor_sync(0xffffffffu, gsum, o2);
-                if (lane == 0 && gsum != 0)
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&C->gtot_fx[t & 1]), (unsigned long long)gsum);
             }
             stamp(9);
         }
@@ -1645,6 +1650,23 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         stamp(6);
 
         // ============================================================ phase 3
+        if (X.prune_exact && warp == nwarps - 1) {
+            // certified pruning: the blocks' sums of floor(g_k 2^56) into exclusive
+            // prefix sums (read by the next phase 1, after this phase's barrier)
+            const int nb = (ns + 31) >> 5;
+            long long carry = 0;
+            for (int b0 = 0; b0 <= nb; b0 += 32) {
+                const int b = b0 + lane;
+                const long long v = b < nb ? __ldcg(X.gblk + b) : 0;
+                long long x = v;
+                for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                    const long long y = __shfl_up_sync(0xffffffffu, x, o2);
+                    if (lane >= o2) x += y;
+                }
+                if (b <= nb) X.gbp[b] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
         theta = MW ? topk_threshold(X, 2 * ns, X.topk, nc) : ~0u;
         {
             const int *list_new = S.sn_list[t & 1];

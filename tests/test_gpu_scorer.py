@@ -199,7 +199,7 @@ CERTIFIED = {
 def test_certified_pruning_reproduces_the_exhaustive_search(ctx, name, topk):
     """prune_exact: the scorer's top-k candidates are scored first, then every
     other candidate unless the certified lower bound (half spreads of the
-    clusters against their MICE) excludes it from the tie band.  Any weights
+    clusters at its positions against their MICE) excludes it from the tie band.  Any weights
     order the candidates; the decisions and scores must be the exhaustive FP64
     sweep's, bit for bit, and the bound must exclude some candidates."""
     import paper_2510_19608_gb300 as K
@@ -218,6 +218,35 @@ def test_certified_pruning_reproduces_the_exhaustive_search(ctx, name, topk):
         assert np.array_equal(got[k], ref[k]), k
     assert s["scorer_fallbacks"] == 0
     assert 0 < s["pruned"] < s["candidates"]
+
+
+def test_trained_network_lets_the_bound_exclude_more(ctx):
+    """What the trained network gains over the search without it: with the
+    same top-k and the same exact decisions, the candidates the trained
+    network ranks first give a tighter threshold, so the certified bound
+    excludes more of the other candidates than with untrained weights."""
+    import paper_2510_19608_gb300 as K
+    from paper_2510_19608_gb300 import scorer
+    runs = [(fg.make_feeder(n, 10000 + k, phase_mode=(0.45, 0.15, 0.4), load=("lognormal", 15.0, 1.0)),
+             K.default_params(margin=0.005, target_reduction=0.8, max_merges=48))
+            for k, n in enumerate((400, 500, 600, 700))]
+    X, T, _ = scorer.collect(ctx, runs, record_iters=48)
+    scorer.train(ctx, X, T, epochs=8, batch=2048, lr=1e-3, seed=0)
+    trained = ctx.scorer_params().copy()
+    f, run = fg.preset("feeder2200", n_bus=600)
+    p = dict(margin=run["margin"], target_reduction=0.8, precision=0, engine=1)
+    ctx.reduce(f, K.default_params(**p))
+    ref = ctx.decisions()
+    frac = {}
+    for name, theta in (("trained", trained), ("untrained", scorer.init_params(14, 5))):
+        ctx.scorer_init(14, theta)
+        ctx.reduce(f, K.default_params(scorer_topk=16, prune_exact=1, **p))
+        got = ctx.decisions()
+        for k in ("s", "r", "score"):
+            assert np.array_equal(got[k], ref[k]), (name, k)
+        s = ctx.summary()
+        frac[name] = s["pruned"] / s["candidates"]
+    assert frac["trained"] > frac["untrained"] + 0.1, frac
 
 
 def test_certified_pruning_rejects_what_it_does_not_run(ctx):
