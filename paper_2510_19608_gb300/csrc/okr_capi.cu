@@ -274,6 +274,11 @@ bool inc_fits(const okr_ctx *ctx, int n, const okr_params *p) {
     return inc_smem(n, true, sh, &rec, &bytes);
 }
 
+// The engine a reduction of an n-bus feeder runs.
+int run_engine(const okr_ctx *ctx, int n, const okr_params *p) {
+    return inc_fits(ctx, n, p) ? resolve_engine(p) : OKR_ENGINE_SWEEP;
+}
+
 int merges_for(int n, const okr_params *p) {
     long m;
     if (p->max_merges >= 0) m = p->max_merges;
@@ -285,8 +290,18 @@ int merges_for(int n, const okr_params *p) {
 
 okr_status read_setup_errors(okr_ctx *ctx);
 
+// Pinned host staging: the search's Ctrl, then the setup's error flag and the
+// load flow's sweep count per scenario (read together after the last launch).
+constexpr size_t kHostStageBytes = sizeof(Ctrl) + 16 + sizeof(int) * (1 + kMaxScen);
+int *host_err(okr_ctx *ctx) { return reinterpret_cast<int *>(reinterpret_cast<char *>(ctx->C_host) + sizeof(Ctrl) + 16); }
+int *host_pf_iters(okr_ctx *ctx) { return host_err(ctx) + 1; }
+
 // Per-feeder setup on the device: topology, LCA table, lines, path impedances.
-okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
+// The host waits for the topology's check of the tree (the later kernels index
+// through its renumbering); with check_lines it also waits for the lines and
+// reads the tree's statistics, else a singular line is reported with the
+// caller's last read of the error flag (the load flow skips its work then).
+okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack, bool check_lines = true) {
     cudaStream_t st = ctx->stream;
     Topo &T = ctx->fb.T;
     T.n = n;
@@ -309,6 +324,10 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     CK(launch_lines(n, T, ctx->fb.z_in, ctx->fb.err_dev, ctx->num_sms, st));
     ctx->launches += 5;
     CK(cudaGetLastError());
+    if (!check_lines) {
+        ctx->have_topo = true;
+        return OKR_OK;
+    }
     s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
     int stats[2] = {0, 0};
@@ -319,11 +338,16 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack) {
     return OKR_OK;
 }
 
+okr_status setup_status(okr_ctx *ctx, int e);
+
 okr_status read_setup_errors(okr_ctx *ctx) {
-    int e = 0;
-    CK(cudaMemcpyAsync(ctx->C_host, ctx->fb.err_dev, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(host_err(ctx), ctx->fb.err_dev, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
-    std::memcpy(&e, ctx->C_host, sizeof e);
+    return setup_status(ctx, *host_err(ctx));
+}
+
+// The status of a setup error code (0: none).
+okr_status setup_status(okr_ctx *ctx, int e) {
     if (e == 1) return fail(ctx, OKR_EINVAL, "invalid feeder: parent[0] must be -1, parent[i] < i, phases non-empty and within the parent's");
     if (e == 2) return fail(ctx, OKR_ESINGULAR, "singular line impedance block");
     if (e == 3) return fail(ctx, OKR_EPF, "load flow did not converge in %d sweeps", kPfMaxIter);
@@ -377,9 +401,8 @@ int positions_per_chunk(int L) { return 32 / (4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4)
 okr_status run_search_inc(okr_ctx *ctx, const okr_params *p);
 
 okr_status run_search(okr_ctx *ctx, const okr_params *p) {
-    ctx->last_engine = resolve_engine(p);
+    ctx->last_engine = run_engine(ctx, ctx->fb.T.n, p);
     ctx->last_rec = -1;
-    if (!inc_fits(ctx, ctx->fb.T.n, p)) ctx->last_engine = OKR_ENGINE_SWEEP;
     if (ctx->last_engine == OKR_ENGINE_INCREMENTAL) return run_search_inc(ctx, p);
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
@@ -477,6 +500,7 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     cudaStream_t st = ctx->stream;
     const int n = ctx->fb.T.n, L = ctx->fb.T.L;
     Search &X = ctx->fb.X;
+    X.setup_err = ctx->fb.err_dev;          // a failed setup step leaves the search idle
     X.rec_iters = p->record_iters;
     X.topk = 0;
     X.prune_exact = 0;
@@ -523,7 +547,17 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     okr_status s = OKR_OK;
     if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "search launch: %s", cudaGetErrorString(e));
     if (s == OKR_OK) {
-        e = cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        // the export needs no check first (a failed search leaves valid indices);
+        // then one wait for everything: the search's control block, the setup's
+        // error flag and the load flow's sweep counts
+        k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, ctx->fb.vred_out,
+                                                                                    ctx->fb.super_out, ctx->fb.vhat_out);
+        ctx->launches += 1;
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_err(ctx), ctx->fb.err_dev, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(host_pf_iters(ctx), ctx->fb.pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = fail(ctx, OKR_ECUDA, "search: %s", cudaGetErrorString(e));
     }
@@ -535,16 +569,21 @@ okr_status run_search_inc(okr_ctx *ctx, const okr_params *p) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    X.setup_err = nullptr;
     if (s != OKR_OK) return s;
+    s = setup_status(ctx, *host_err(ctx));
+    if (s != OKR_OK) {
+        ctx->have_topo = false;
+        return s;
+    }
+    if (ctx->pf_sweeps < 0) {               // the load flow ran in this call: its sweeps, read with the rest
+        int w = 0;
+        for (int l = 0; l < L; ++l) w = host_pf_iters(ctx)[l] > w ? host_pf_iters(ctx)[l] : w;
+        ctx->pf_sweeps = w;
+    }
     if (c.err) return fail(ctx, OKR_EINTERNAL, "search device error %d", c.err);
     if (!c.done) return fail(ctx, OKR_EINTERNAL, "search stopped without a result");
-    k_export<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(ctx->fb.T, ctx->fb.S, ctx->fb.vred_out,
-                                                                                ctx->fb.super_out, ctx->fb.vhat_out);
-    ctx->launches += 1;
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->C_host, ctx->fb.C, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    ctx->last = *ctx->C_host;
+    ctx->last = c;
     return OKR_OK;
 }
 
@@ -578,7 +617,10 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
     } else {
         CK(cudaMemcpyAsync(ctx->fb.s_in, f->s_load, sizeof(double) * 6 * L * n, kind, st));
     }
-    s = build_topology(ctx, n, L, &f->v_slack[0][0]);
+    // the incremental engine's path waits once, after the last launch (the
+    // sweep engine sizes its work buffers from the tree's statistics first)
+    const bool one_wait = run_engine(ctx, n, p) == OKR_ENGINE_INCREMENTAL;
+    s = build_topology(ctx, n, L, &f->v_slack[0][0], !one_wait);
     if (s != OKR_OK) return s;
     if (src == Src::Ops) {
         k_import_ops<<<blocks_for((size_t)L * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, L, ctx->fb.T, ctx->fb.vh_in, ctx->fb.ih_in);
@@ -589,14 +631,18 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
         s = run_power_flow(ctx, n, L, p->max_spins);
         if (s != OKR_OK) return s;
     }
-    s = read_setup_errors(ctx);
-    if (s != OKR_OK) return s;
-    if (src != Src::Ops) {
-        int it[kMaxScen];
-        CK(cudaMemcpy(it, ctx->fb.pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
-        int w = 0;
-        for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
-        ctx->pf_sweeps = w;
+    if (one_wait) {
+        if (src != Src::Ops) ctx->pf_sweeps = -1;   // read after the search
+    } else {
+        s = read_setup_errors(ctx);
+        if (s != OKR_OK) return s;
+        if (src != Src::Ops) {
+            int it[kMaxScen];
+            CK(cudaMemcpy(it, ctx->fb.pf_iters, sizeof(int) * L, cudaMemcpyDeviceToHost));
+            int w = 0;
+            for (int l = 0; l < L; ++l) w = it[l] > w ? it[l] : w;
+            ctx->pf_sweeps = w;
+        }
     }
     s = run_search(ctx, p);
     if (s != OKR_OK) return s;
@@ -718,7 +764,7 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
         if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { delete ctx; return OKR_ECUDA; }
         ctx->own_stream = true;
     }
-    if (cudaMallocHost((void **)&ctx->C_host, sizeof(Ctrl)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&ctx->C_host, kHostStageBytes) != cudaSuccess) {
         if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
         delete ctx;
         return OKR_ENOMEM;

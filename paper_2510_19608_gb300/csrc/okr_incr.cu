@@ -1926,6 +1926,7 @@ template <int NT, int PREC>
 __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X, Inc I, Ctrl *C, int verify,
                                                       int rec_mode, int se, int cw, int pre_init) {
     extern __shared__ __align__(16) unsigned char inc_dyn[];
+    if (X.setup_err && *X.setup_err != 0) return;           // the setup failed: no result (C->done stays 0)
     inc_run<NT, PREC>(T, S, X, I, C, verify != 0, inc_dyn, rec_mode, se, cw, pre_init != 0);
 }
 
@@ -1994,7 +1995,7 @@ __global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc 
     __shared__ int sscan[33];
     __shared__ int s_cnt;
     const int w0 = blockIdx.x * kInitPairs;
-    if (w0 >= T.n) return;
+    if (w0 >= T.n || (X.setup_err && *X.setup_err != 0)) return;
     inc_init_pairs<NT, PREC>(T, S, X, I, C, w0, reinterpret_cast<unsigned short *>(init_dyn), E, sscan, &s_cnt);
 }
 

@@ -172,6 +172,7 @@ struct Inc {
 constexpr int kIncDead = 1 << 30;
 
 struct Search {
+    const int *setup_err;   // the setup's error flag: the incremental search does nothing when it is set (null: none)
     Cand *cand;             // [2n] compact candidate list
     unsigned long long *ckey;   // [2n] tie key of each compact candidate
     Cand *slot;             // [2n] candidates by super-node slot (s < 0: none)

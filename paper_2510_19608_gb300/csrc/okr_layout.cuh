@@ -155,6 +155,7 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(X.gpre, N);
     c.take(X.gblk, N / 32 + 2);
     c.take(X.gbp, N / 32 + 2);
+    X.setup_err = nullptr;
     X.topk = 0;
     X.prune_exact = 0;
     X.mlp_theta = nullptr;

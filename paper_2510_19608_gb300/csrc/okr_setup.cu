@@ -67,7 +67,7 @@ __device__ void dev_topology(int n, const int *__restrict__ parent_in, const uin
         if (!ok) atomicExch(&s_bad, 1);
     }
     block_barrier();
-    if (s_bad) { if (tid == 0) atomicExch(err, 1); return; }
+    if (s_bad) { if (tid == 0) atomicCAS(err, 0, 1); return; }
     // 2. depth by pointer jumping (caller numbering)
     for (int i = tid; i < n; i += nt) { anc[i] = (i == 0) ? 0 : parent_in[i]; dep[i] = (i == 0) ? 0 : 1; }
     block_barrier();
@@ -311,7 +311,7 @@ __device__ void dev_line_inverses(int n, Topo T, const double *__restrict__ z_in
         if (v == 0) {
             for (int q = 0; q < 9; ++q) y[q] = make_double2(0.0, 0.0);
         } else if (!inv3_sub(z, T.ph[v], y)) {
-            atomicExch(err, 2);
+            atomicCAS(err, 0, 2);
             for (int q = 0; q < 9; ++q) y[q] = make_double2(0.0, 0.0);
         }
         for (int q = 0; q < 9; ++q) T.yl[(size_t)v * 9 + q] = y[q];
@@ -400,7 +400,7 @@ __device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsign
             if (++spins > max_spins || *(volatile int *)err == 6) { ok = 0; break; }
             __nanosleep(20);
         }
-        if (!ok) atomicExch(err, 6);
+        if (!ok) atomicCAS(err, 0, 6);
         __threadfence();
         s_ok = ok;
     }
@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     const int gt = blockIdx.x * nt + tid, gs = (int)G * nt;
     const size_t N3 = (size_t)3 * n;
     const size_t tot = (size_t)L * N3;
+    // an earlier setup step failed (every CTA reads the same flag: no writer runs)
+    if (*reinterpret_cast<volatile const int *>(err) != 0) return;
     const int maxd = T.maxd[0];
     unsigned epoch = 0;
     for (size_t e = gt; e < tot; e += gs) {
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     }
     if (blockIdx.x == 0 && tid < L && s_live[tid]) {
         iters[tid] = -1;
-        atomicExch(err, 3);
+        atomicCAS(err, 0, 3);
     }
 }
 
@@ -722,7 +724,7 @@ __device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__
     }
     if (tid == 0) {
         iters[l] = conv ? it : -1;
-        if (!conv) atomicExch(err, 3);
+        if (!conv) atomicCAS(err, 0, 3);
     }
 }
 
