@@ -860,7 +860,9 @@ enum Pass {
     kMerge = 0,     // after a merge: mode 0 adds (term after - term before), mode 1 sets every term after
     kInit = 1,      // the stored state, every term of the entries, set
     kFresh = 2,     // carried precision, every term after the merge in progress, into vacc / vviol
-    kF64 = 3        // FP64, every term on the stored state, into vacc / vviol
+    kF64 = 3,       // FP64, every term on the stored state, into vacc / vviol
+    kInitPart = 4   // the stored state, every term of the entries (parts of candidates): added to the carried
+                    // sums with atomics, the records left to the search
 };
 
 // One tile of NT work entries (one per thread): their sums and offsets.
@@ -1165,7 +1167,14 @@ __device__ __noinline__ long long run_entries(const Topo &T, const State &S, con
             const u128 d = ((u128)E.dhi[tid] << 64) | (u128)E.dlo[tid];
             const u128 b = ((u128)E.bhi[tid] << 64) | (u128)E.blo[tid];
             unsigned long long *a = I.acc + 2 * (size_t)sl, *bp = I.bnd + 2 * (size_t)sl;
-            if (pass == kMerge || pass == kInit) {
+            if (pass == kInitPart) {
+                sadd128(a, a + 1, d);
+                if (E.n1[tid]) atomicAdd(I.viol + sl, E.n1[tid]);
+                if (PREC == 1) {
+                    sadd128(bp, bp + 1, b);
+                    if (E.n2[tid]) atomicAdd(I.vmay + sl, E.n2[tid]);
+                }
+            } else if (pass == kMerge || pass == kInit) {
                 u128 na, nb = 0;
                 int nv, nm = 0;
                 if (w.mode == 1) {
@@ -1402,6 +1411,15 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             const uint4 *src = reinterpret_cast<const uint4 *>(I.recbuf);
             uint4 *dst = reinterpret_cast<uint4 *>(recmem);
             for (int i = tid; i < 3 * n; i += NT) dst[i] = src[i];       // 48 n bytes
+        }
+        __syncthreads();
+        // the live candidates' keys from their carried sums (the first evaluation
+        // may have summed a candidate's terms on several CTAs)
+        for (int sl = tid; sl < 2 * n; sl += NT) {
+            const int v = I.viol[sl];
+            if (v == kIncDead) continue;
+            set_rec<PREC>(R, sl, ld128(I.acc + 2 * (size_t)sl), PREC == 1 ? ld128(I.bnd + 2 * (size_t)sl) : (u128)0, v,
+                          PREC == 1 ? I.vmay[sl] : 0);
         }
         __syncthreads();
     } else {
@@ -1939,6 +1957,7 @@ __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X,
 // terms are evaluated by the same code as in the search, so the carried sums
 // are the ones the search's own first evaluation gives.
 constexpr int kInitPairs = kIncInitPairs;
+constexpr int kInitCtasMax = kIncInitCtasMax;
 // The pairs [w0, w0 + kInitPairs) of one feeder (list: shared scratch of n
 // 16-bit entries).
 template <int NT, int PREC>
@@ -1988,15 +2007,150 @@ __device__ void inc_init_pairs(const Topo &T, const State &S, const Search &X, c
     }
 }
 
+// The first evaluation of one feeder with its work spread evenly over the
+// grid.  A pair's candidates can hold up to n positions each (the pairs next
+// to the root), so splitting by pairs leaves one CTA with most of the work.
+// Instead every CTA derives the position count of every initial candidate
+// (the geometry of a pair of singletons is a few loads), lays the candidates'
+// positions end to end in slot order, and takes an equal share of them; a
+// candidate cut by a share's ends is summed in parts, added to the carried
+// sums with 128-bit atomics (integer sums: exact in any order; the sums start
+// at zero).  Each pair's own outputs (the slots, its span, the tie keys and
+// the dead slots' records) are written by one CTA, and the search derives
+// the live candidates' selection keys from the finished sums.
+// Dynamic shared memory: the identity super-node list (2n bytes) and the
+// position count of every slot (8n bytes).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
     extern __shared__ __align__(16) unsigned char init_dyn[];
     __shared__ __align__(16) EvalSmem<NT> E;
     __shared__ int sscan[33];
-    __shared__ int s_cnt;
-    const int w0 = blockIdx.x * kInitPairs;
-    if (w0 >= T.n || (X.setup_err && *X.setup_err != 0)) return;
-    inc_init_pairs<NT, PREC>(T, S, X, I, C, w0, reinterpret_cast<unsigned short *>(init_dyn), E, sscan, &s_cnt);
+    __shared__ int s_first, s_ne;
+    if (X.setup_err && *X.setup_err != 0) return;
+    const int n = T.n, L = T.L, tid = threadIdx.x, b = blockIdx.x, B = gridDim.x;
+    const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
+    const double margin = C->margin;
+    const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
+    unsigned short *list = reinterpret_cast<unsigned short *>(init_dyn);
+    int *pcnt = reinterpret_cast<int *>(init_dyn + align16((size_t)2 * n));
+    for (int w = tid; w < n; w += NT) list[w] = (unsigned short)w;
+    Loc Lc;
+    Lc.wsm = nullptr;
+    Lc.wgl = I.work;
+    Lc.se = 0;
+    Lc.lst[0] = Lc.lst[1] = list;
+    Lc.ph = T.ph;
+    Lc.rank = S.sn_rank;
+    Rec R;
+    R.r0 = reinterpret_cast<u128 *>(I.recbuf);
+    R.r1 = reinterpret_cast<ulonglong2 *>(I.recbuf);
+    R.tkey = reinterpret_cast<unsigned *>(I.recbuf + (size_t)32 * n);
+    R.maxm = I.maxm;
+    R.span = reinterpret_cast<ushort4 *>(I.recbuf + (size_t)40 * n);
+    R.bsum = nullptr;
+    R.bcnt = nullptr;
+    R.bmx = nullptr;
+    R.dirty = nullptr;
+    R.nb = 0;
+    Ovl O;
+    O.map = nullptr;                            // (the first evaluation reads the stored state only)
+    O.cbuf = I.cbuf;
+    O.s = O.r = -1;
+    O.nfree = 0;
+    const View V = no_view();
+    // this CTA's pairs: the slots, the span, the tie keys, the dead slots
+    for (int w = b + B * tid; w < n; w += B * NT) {
+        Cand c[2];
+        const int x = slot_geometry(T, S, V, n, w, c[0], c[1]);
+        I.qpar[w] = x;
+        int lo = n, hi = 0;
+        for (int d = 0; d < 2; ++d) {
+            if (c[d].s < 0) continue;
+            lo = min(lo, min(min(c[d].s, c[d].r), c[d].ns > 0 ? c[d].js : n));
+            lo = min(lo, c[d].nr > 0 ? c[d].jr : n);
+            hi = max(hi, max(max(c[d].s, c[d].r) + 1, max(c[d].js + c[d].ns, c[d].jr + c[d].nr)));
+        }
+        const bool any = c[0].s >= 0 || c[1].s >= 0;
+        R.span[w] = make_ushort4((unsigned short)(any ? lo : 0), (unsigned short)(any ? hi : 0),
+                                 (unsigned short)(x >= 0 ? x : 0xffff), (unsigned short)(any ? 1 : 0));
+        for (int d = 0; d < 2; ++d) {
+            const int sl = 2 * w + d;
+            X.slot[sl] = c[d];
+            if (c[d].s >= 0) {
+                R.tkey[sl] = (unsigned)c[d].key;
+            } else {
+                I.viol[sl] = kIncDead;
+                kill_rec<PREC>(R, sl);
+            }
+        }
+    }
+    // every slot's position count; thread tid takes the pairs [p0, p1)
+    const int per = (n + NT - 1) / NT, p0 = min(n, tid * per), p1 = min(n, p0 + per);
+    int mine = 0;
+    for (int w = p0; w < p1; ++w) {
+        Cand c[2];
+        slot_geometry(T, S, V, n, w, c[0], c[1]);
+        for (int d = 0; d < 2; ++d) {
+            int k = 0;
+            if (c[d].s >= 0) {
+                int2 seg[kIncMaxSeg];
+                const int ns = full_segments(c[d], Lc.rank, seg);
+                for (int i = 0; i < ns; ++i) k += seg[i].y - seg[i].x;
+            }
+            pcnt[2 * w + d] = k;
+            mine += k;
+        }
+    }
+    if (tid == 0) { s_first = 2 * n; s_ne = 0; }
+    int tot = 0;
+    const int base = block_excl_scan<NT>(mine, &tot, sscan);
+    // this CTA's share of the positions: [q0, q1)
+    const int share = max(1, (tot + B - 1) / B);
+    const int q0 = min(tot, b * share), q1 = min(tot, q0 + share);
+    {
+        int off = base;
+        for (int sl = 2 * p0; sl < 2 * p1; ++sl) {
+            const int k = pcnt[sl];
+            if (k > 0 && off < q1 && off + k > q0) atomicMin(&s_first, sl);
+            off += k;
+        }
+    }
+    __syncthreads();
+    // the entries: one per candidate that meets the share, its segments cut to
+    // the share, at [first slot + b, ...) (the CTAs' ranges do not overlap)
+    {
+        const int e0 = s_first + b;
+        int off = base;
+        for (int sl = 2 * p0; sl < 2 * p1; ++sl) {
+            const int k = pcnt[sl];
+            if (k > 0 && off < q1 && off + k > q0) {
+                Cand c[2];
+                slot_geometry(T, S, V, n, sl >> 1, c[0], c[1]);
+                const Cand &cc = c[sl & 1];
+                int2 seg[kIncMaxSeg], cut[kIncMaxSeg];
+                const int ns = full_segments(cc, Lc.rank, seg);
+                const int lo = max(q0 - off, 0), hi = min(q1 - off, k);    // the share, in the candidate's positions
+                int nc = 0, at = 0;
+                for (int i = 0; i < ns; ++i) {
+                    const int len = seg[i].y - seg[i].x;
+                    const int a = max(lo, at), z = min(hi, at + len);
+                    if (a < z) cut[nc++] = make_int2(seg[i].x + (a - at), seg[i].x + (z - at));
+                    at += len;
+                }
+                write_entry(Lc.ent(e0 + atomicAdd(&s_ne, 1)), sl, 1, nc, cut, cc);
+            }
+            off += k;
+        }
+    }
+    __syncthreads();
+    if (s_ne == 0) return;
+    const long long terms = run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, s_first + b, s_first + b + s_ne,
+                                                  kInitPart, list, list, -1, O, E, sscan, R, Lc);
+    if (C->profile) {                           // (phase-node, scenario) items
+        unsigned long long tt = (unsigned long long)terms;
+        for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
+        if ((tid & 31) == 0 && tt) atomicAdd(reinterpret_cast<unsigned long long *>(&C->sweep_ns), tt);
+    }
 }
 
 // The same for many feeders: cta_off[i] = the first CTA of the i-th feeder of
@@ -2108,11 +2262,20 @@ namespace {
 template <int NT, int PREC>
 cudaError_t launch_one(Topo T, State S, Search X, Inc I, Ctrl *C, int verify, int use, size_t smem, const IncShape &sh,
                        cudaStream_t st) {
-    // the first evaluation on many CTAs, then the search on one
-    const int ginit = (T.n + kInitPairs - 1) / kInitPairs;
-    const size_t ismem = align16((size_t)2 * T.n);
-    cudaError_t e = cudaSuccess;
-    if (ismem > 48 * 1024) e = set_smem(k_inc_init<kInitThreads, PREC>, ismem);
+    // the first evaluation spread over the SMs (its sums start at zero), then
+    // the search on one CTA
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || sms < 1)
+            sms = 1;
+    }
+    const int ginit = std::min(std::min(sms, kInitCtasMax), std::max(1, (T.n + kInitPairs - 1) / kInitPairs));
+    const size_t ismem = align16((size_t)2 * T.n) + align16((size_t)8 * T.n);
+    cudaError_t e = cudaMemsetAsync(I.acc, 0, reinterpret_cast<const char *>(I.vmay + 2 * (size_t)T.n) -
+                                                  reinterpret_cast<const char *>(I.acc), st);
+    if (e == cudaSuccess && ismem > 48 * 1024) e = set_smem(k_inc_init<kInitThreads, PREC>, ismem);
     if (e == cudaSuccess) k_inc_init<kInitThreads, PREC><<<ginit, kInitThreads, ismem, st>>>(T, S, X, I, C);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = set_smem(k_search_inc<NT, PREC>, smem);

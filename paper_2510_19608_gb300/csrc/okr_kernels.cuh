@@ -153,7 +153,8 @@ struct IncShape {
     int threads, cw, se, rec;
 };
 constexpr int kIncDefaultThreads = 384;
-constexpr int kIncInitPairs = 8;        // slot pairs per CTA of the first evaluation
+constexpr int kIncInitPairs = 8;        // slot pairs per CTA of the first evaluation (batches)
+constexpr int kIncInitCtasMax = 256;    // CTAs of one feeder's first evaluation, at most
 // Out-of-range fields replaced by the defaults (384 threads, 2 evaluation
 // warps (4 with 512 threads), 256 shared entries, automatic records).
 IncShape inc_shape_resolve(IncShape sh);

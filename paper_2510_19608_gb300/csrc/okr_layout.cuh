@@ -171,7 +171,7 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(I.maxm, N);
     c.take(I.qpar, N);
     c.take(I.fpair, N);
-    c.take(I.work, 2 * N);
+    c.take(I.work, 2 * N + kIncInitCtasMax);      // (+ the first evaluation's candidates cut between CTAs)
     c.take(I.cbuf, N * (size_t)kIncCbStride * L);
     c.take(I.vacc, 4 * N);
     c.take(I.vviol, 2 * N);

@@ -350,9 +350,12 @@ __global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
 }
 
 cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
-    int blocks = (n + 255) / 256;
+    // one warp per CTA: each line's inverse is a chain of FP64 operations, and
+    // an SM's FP64 unit serves few warps at speed, so the lines go to as many
+    // SMs as possible
+    int blocks = (n + 31) / 32;
     if (blocks > num_sms * 8) blocks = num_sms * 8;
-    k_line_inverses<<<blocks, 256, 0, st>>>(n, T, z_in, err);
+    k_line_inverses<<<blocks, 32, 0, st>>>(n, T, z_in, err);
     k_path_impedance<<<1, 1024, 0, st>>>(n, T);
     return cudaGetLastError();
 }
