@@ -114,7 +114,7 @@ typedef struct okr_params {
                                      carried score (okr_summary.inc_mismatches; for tests). */
     int64_t max_spins;          /* polls before a device-side wait gives up with OKR_ETIMEOUT: the grid
                                    barriers of the load flow and of the sweep engine (0 = default,
-                                   4,000,000: well under a second) */
+                                   1,000,000: one L2 round trip each, under a second) */
     int32_t prune_exact;        /* 1 = certified pruning with the learned ordering (scorer_topk > 0,
                                    objective 0, precision 0, the sweep engine; else OKR_EINVAL): each
                                    iteration scores the scorer's top-k candidates exactly, then every

@@ -21,7 +21,7 @@ using namespace okr;
 
 namespace {
 
-constexpr long long kDefaultSpins = 4000000;   // bounded device waits: well under a second
+constexpr long long kDefaultSpins = 1000000;   // bounded device waits: one L2 round trip per poll, under a second
 constexpr double kPfTol = 1e-13;
 constexpr int kPfMaxIter = 200;
 
@@ -44,6 +44,11 @@ struct okr_ctx {
     int cap_chunks = 0;
     int sum_sz = 0, max_depth = 0;      // of the current feeder
     Ctrl *C_host = nullptr;             // pinned
+    // the setup steps the load flow does not need (LCA table, path impedances)
+    // run on a second stream beside it; ev_side marks their end
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_topo = nullptr, ev_lines = nullptr, ev_side = nullptr;
+    bool side_pending = false;          // the stream has not waited for ev_side yet
 
     // counters of the last call
     int64_t launches = 0;
@@ -290,6 +295,13 @@ int merges_for(int n, const okr_params *p) {
 
 okr_status read_setup_errors(okr_ctx *ctx);
 
+// The stream waits for the setup steps on the side stream (a no-op when it already has).
+cudaError_t join_side(okr_ctx *ctx) {
+    if (!ctx->side_pending) return cudaSuccess;
+    ctx->side_pending = false;
+    return cudaStreamWaitEvent(ctx->stream, ctx->ev_side, 0);
+}
+
 // Pinned host staging: the search's Ctrl, then the setup's error flag and the
 // load flow's sweep count per scenario (read together after the last launch).
 constexpr size_t kHostStageBytes = sizeof(Ctrl) + 16 + sizeof(int) * (1 + kMaxScen);
@@ -303,6 +315,7 @@ int *host_pf_iters(okr_ctx *ctx) { return host_err(ctx) + 1; }
 // caller's last read of the error flag (the load flow skips its work then).
 okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack, bool check_lines = true) {
     cudaStream_t st = ctx->stream;
+    CK(join_side(ctx));                     // (a failed call may have left side work unjoined)
     Topo &T = ctx->fb.T;
     T.n = n;
     T.L = L;
@@ -317,17 +330,29 @@ okr_status build_topology(okr_ctx *ctx, int n, int L, const double *vslack, bool
     // the later setup kernels index with the renumbering: stop here on an invalid tree
     okr_status s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
+    // the LCA table and the path impedances (on the side stream) are not read
+    // by the load flow: they run beside it, and the stream waits for them
+    // before the search (join_side)
+    cudaStream_t sd = ctx->side;
+    CK(cudaEventRecord(ctx->ev_topo, st));
+    CK(cudaStreamWaitEvent(sd, ctx->ev_topo, 0));
     k_child_offsets<<<1, 1024, 0, st>>>(n, T, ctx->fb.coff_c, ctx->fb.child_c);
     const int LOG = log2_ceil(n) + 1;
-    k_rmq_all<<<1, 1024, 0, st>>>(n, LOG, T.depth, ctx->fb.rmq);
-    k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, st>>>(n, T.parent, T.sz, T.depth, ctx->fb.rmq, T.lca);
-    CK(launch_lines(n, T, ctx->fb.z_in, ctx->fb.err_dev, ctx->num_sms, st));
+    k_rmq_all<<<1, 1024, 0, sd>>>(n, LOG, T.depth, ctx->fb.rmq);
+    k_lca_fill<<<blocks_for((size_t)n * n, 256, ctx->num_sms * 8), 256, 0, sd>>>(n, T.parent, T.sz, T.depth, ctx->fb.rmq, T.lca);
+    CK(launch_line_inverses(n, T, ctx->fb.z_in, ctx->fb.err_dev, ctx->num_sms, st));
+    CK(cudaEventRecord(ctx->ev_lines, st));
+    CK(cudaStreamWaitEvent(sd, ctx->ev_lines, 0));
+    CK(launch_path_impedance(n, T, sd));
+    CK(cudaEventRecord(ctx->ev_side, sd));
+    ctx->side_pending = true;
     ctx->launches += 5;
     CK(cudaGetLastError());
     if (!check_lines) {
         ctx->have_topo = true;
         return OKR_OK;
     }
+    CK(join_side(ctx));
     s = read_setup_errors(ctx);
     if (s != OKR_OK) return s;
     int stats[2] = {0, 0};
@@ -644,6 +669,7 @@ okr_status reduce_impl(okr_ctx *ctx, const okr_feeder *f, const double *vhat, co
             ctx->pf_sweeps = w;
         }
     }
+    CK(join_side(ctx));
     s = run_search(ctx, p);
     if (s != OKR_OK) return s;
     ctx->n = n;
@@ -769,6 +795,13 @@ okr_status okr_create(okr_ctx **out, int device, void *stream) {
         delete ctx;
         return OKR_ENOMEM;
     }
+    if (cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_topo, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_lines, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        okr_destroy(ctx);
+        return OKR_ECUDA;
+    }
     *out = ctx;
     return OKR_OK;
 }
@@ -794,6 +827,12 @@ okr_status okr_destroy(okr_ctx *ctx) {
     free_batch(ctx);
     free_mlp(ctx);
     if (ctx->C_host) cudaFreeHost(ctx->C_host);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    for (cudaEvent_t ev : {ctx->ev_topo, ctx->ev_lines, ctx->ev_side})
+        if (ev) cudaEventDestroy(ev);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return OKR_OK;

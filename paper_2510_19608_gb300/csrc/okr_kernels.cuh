@@ -18,6 +18,8 @@ __global__ void k_lca_fill(int n, const int *__restrict__ parent, const int *__r
                            const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca);
 // line inverses (grid) and path impedances (one CTA)
 cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st);
+cudaError_t launch_line_inverses(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st);
+cudaError_t launch_path_impedance(int n, Topo T, cudaStream_t st);
 // load flow of every scenario (cooperative launch).  J: [L*3n] line currents,
 // W: [L*3n] work (its contents are overwritten), red: [3L+1] doubles of
 // reduction slots and barrier counter (cleared by the launch), iters: [L].

@@ -100,9 +100,9 @@ __device__ bool grid_barrier(GridBar *gb, Ctrl *C, unsigned nblocks, unsigned &e
         int ok = 1;
         long long spins = 0;
         const long long lim = C->max_spins;
+        // one L2 round trip per poll; another CTA's give-up is looked for every 64 polls
         while (ld_acquire(&gb->count) < target) {
-            if (++spins > lim || *(volatile int *)&C->err) { ok = 0; break; }
-            __nanosleep(20);
+            if (++spins > lim || ((spins & 63) == 0 && *(volatile int *)&C->err)) { ok = 0; break; }
         }
         if (!ok) atomicCAS(&C->err, 0, 6);
         __threadfence();

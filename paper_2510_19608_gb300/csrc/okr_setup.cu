@@ -349,15 +349,24 @@ __global__ void __launch_bounds__(1024) k_path_impedance(int n, Topo T) {
     dev_path_impedance(n, T);
 }
 
-cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
+cudaError_t launch_line_inverses(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
     // one warp per CTA: each line's inverse is a chain of FP64 operations, and
     // an SM's FP64 unit serves few warps at speed, so the lines go to as many
     // SMs as possible
     int blocks = (n + 31) / 32;
     if (blocks > num_sms * 8) blocks = num_sms * 8;
     k_line_inverses<<<blocks, 32, 0, st>>>(n, T, z_in, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_path_impedance(int n, Topo T, cudaStream_t st) {
     k_path_impedance<<<1, 1024, 0, st>>>(n, T);
     return cudaGetLastError();
+}
+
+cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sms, cudaStream_t st) {
+    const cudaError_t e = launch_line_inverses(n, T, z_in, err, num_sms, st);
+    return e != cudaSuccess ? e : launch_path_impedance(n, T, st);
 }
 
 // ---------------------------------------------------------------- load flow
@@ -370,14 +379,17 @@ cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sm
 // FP64 division, the 3x3 products and the magnitudes dominate the arithmetic,
 // and GB300's FP64 rate per SM is low, so these run over the whole cooperative
 // grid; only the level-by-level sums (additions) run one CTA per (scenario,
-// phase), staged in shared memory.  Five grid barriers per sweep:
+// phase), staged in shared memory.  Four grid barriers per sweep:
 //   S1 load currents I1 = conj(S / V)          (grid)
 //   S2 line currents J = I1 + sum children J  (CTA per (l, p), deepest level first)
 //   S3 drops D = z J                            (grid)
 //   S4 new voltages Vn = Vn_parent - D          (CTA per (l, p), top down)
 //   S5 |Vn - V|, V = Vn, per-scenario maximum   (grid)
-// I1, D and Vn share one buffer W (D overwrites I1, Vn overwrites D in place).
-// The arithmetic is the same, operation for operation, as a one-thread-per-bus
+// S5 and the next sweep's S1 touch the same element on the same thread, so
+// they run as one pass (the load currents of a scenario that has just
+// converged are computed and never read).  I1, D and Vn share one buffer W
+// (D overwrites I1, Vn overwrites D in place, I1 overwrites Vn).  The
+// arithmetic is the same, operation for operation, as a one-thread-per-bus
 // sweep.
 constexpr int kPfShared = 2048;     // buses whose (l, p) slice is staged in shared memory
 
@@ -399,9 +411,9 @@ __device__ bool pf_grid_sync(unsigned *count, int *err, unsigned nblocks, unsign
         atomicAdd(count, 1u);
         int ok = 1;
         long long spins = 0;
+        // one L2 round trip per poll; another CTA's give-up is looked for every 64 polls
         while (pf_ld_acquire(count) < target) {
-            if (++spins > max_spins || *(volatile int *)err == 6) { ok = 0; break; }
-            __nanosleep(20);
+            if (++spins > max_spins || ((spins & 63) == 0 && *(volatile int *)err == 6)) { ok = 0; break; }
         }
         if (!ok) atomicCAS(err, 0, 6);
         __threadfence();
@@ -434,23 +446,26 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     const int ll = blockIdx.x / 3, lp = blockIdx.x % 3;      // (scenario, phase) of a level CTA
     double2 *const loc = n <= kPfShared ? pf_sm : nullptr;
     bool conv_all = false;
+    // the load current of element e on voltage vv (S1)
+    auto load_current = [&](size_t e, int l, int p, int v, double2 vv) {
+        double2 j = make_double2(0.0, 0.0);
+        if (T.ph[v] >> p & 1u) {
+            const size_t o = (((size_t)l * n + T.orig[v]) * 3 + p) * 2;
+            const double2 sv = make_double2(__ldg(s_in + o), __ldg(s_in + o + 1));
+            j = cconj(cdiv(sv, vv));
+        }
+        W[e] = j;
+    };
+    __syncthreads();                                         // (s_live)
+    // S1 of the first sweep (each element on the thread that set its voltage)
+    for (size_t e = gt; e < tot; e += gs) {
+        const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
+        load_current(e, l, p, v, T.vhat[e]);
+    }
+    if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
     int it;
     for (it = 1; it <= max_iter; ++it) {
-        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         if (gt == 0) for (int l = 0; l < L; ++l) red[((it + 1) % 3) * L + l] = 0.0;
-        // S1: load currents
-        for (size_t e = gt; e < tot; e += gs) {
-            const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
-            if (!s_live[l]) continue;
-            double2 j = make_double2(0.0, 0.0);
-            if (T.ph[v] >> p & 1u) {
-                const size_t o = (((size_t)l * n + T.orig[v]) * 3 + p) * 2;
-                const double2 sv = make_double2(__ldg(s_in + o), __ldg(s_in + o + 1));
-                j = cconj(cdiv(sv, T.vhat[e]));
-            }
-            W[e] = j;
-        }
-        if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
         // S2: line currents, deepest level first
         if (line_cta && s_live[ll]) {
             const size_t off = ((size_t)ll * 3 + lp) * n;
@@ -507,17 +522,22 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
                 for (int v = tid; v < n; v += nt) W[off + v] = loc[v];
         }
         if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
-        // S5: change of the voltages, per-scenario maximum
+        // S5: change of the voltages, per-scenario maximum; then S1 of the next sweep
         double mx[kMaxScen] = {0.0, 0.0, 0.0, 0.0};
         for (size_t e = gt; e < tot; e += gs) {
             const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
-            if (!s_live[l] || v == 0 || !(T.ph[v] >> p & 1u)) continue;
-            const double2 vn = W[e];
-            double dd = cmag(csub(vn, T.vhat[e]));
-            if (!isfinite(dd)) dd = INFINITY;               // a diverging sweep never converges
-            T.vhat[e] = vn;
-            for (int l2 = 0; l2 < kMaxScen; ++l2)
-                if (l2 == l) mx[l2] = fmax(mx[l2], dd);
+            if (!s_live[l]) continue;
+            double2 vv = T.vhat[e];
+            if (v != 0 && (T.ph[v] >> p & 1u)) {
+                const double2 vn = W[e];
+                double dd = cmag(csub(vn, vv));
+                if (!isfinite(dd)) dd = INFINITY;           // a diverging sweep never converges
+                T.vhat[e] = vn;
+                vv = vn;
+                for (int l2 = 0; l2 < kMaxScen; ++l2)
+                    if (l2 == l) mx[l2] = fmax(mx[l2], dd);
+            }
+            load_current(e, l, p, v, vv);
         }
         for (int l = 0; l < L; ++l) {
             double m = mx[0];

@@ -186,7 +186,7 @@ okr_status read_err(const int *err_dev, cudaStream_t st) {
 
 constexpr double kPfTol = 1e-13;
 constexpr int kPfMaxIter = 200;
-constexpr long long kPfSpins = 4000000;     // polls per grid barrier of the load flow: well under a second
+constexpr long long kPfSpins = 1000000;     // polls per grid barrier of the load flow: under a second
 
 }  // namespace
 
