@@ -47,6 +47,43 @@ __device__ bool inv3_sub(const double2 *a, unsigned m, double2 *out) {
 
 __device__ __forceinline__ void block_barrier() { __syncthreads(); }
 
+// out[i] = in[0] + ... + in[i - 1] for i <= n (one CTA, blockDim.x a multiple
+// of 32, at most 1024; tiles of blockDim.x with a carried total).
+__device__ void block_exclusive_scan(const int *in, int *out, int n) {
+    __shared__ int s_w[32];
+    __shared__ int s_carry;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + tid;
+        const int c = i < n ? in[i] : 0;
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? s_w[lane] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < nw) s_w[lane] = w;
+        }
+        __syncthreads();
+        const int carry = s_carry;
+        if (i < n) out[i] = carry + (warp > 0 ? s_w[warp - 1] : 0) + x - c;
+        __syncthreads();
+        if (tid == 0) s_carry = carry + s_w[nw - 1];
+        __syncthreads();
+    }
+    if (tid == 0) out[n] = s_carry;
+    __syncthreads();
+}
+
 // ---------------------------------------------------------------- topology (one CTA)
 // Input in caller numbering.  Scratch arrays (caller numbering): dep, anc/anc2,
 // d2, size, ccount.  Writes the Topo arrays in preorder numbering.
@@ -105,12 +142,7 @@ __device__ void dev_topology(int n, const int *__restrict__ parent_in, const uin
         block_barrier();
     }
     // 5. children CSR in caller numbering, each list sorted by caller id
-    if (tid == 0) {
-        int acc = 0;
-        for (int i = 0; i < n; ++i) { coff_c[i] = acc; acc += ccount[i]; }
-        coff_c[n] = acc;
-    }
-    block_barrier();
+    block_exclusive_scan(ccount, coff_c, n);
     for (int i = tid; i < n; i += nt) ccount[i] = 0;
     block_barrier();
     for (int i = tid + 1; i < n; i += nt) {
