@@ -461,9 +461,14 @@ okr_status run_search(okr_ctx *ctx, const okr_params *p) {
     CK(cudaMemsetAsync(X.arrive, 0, sizeof(int) * 2 * n, st));
     CK(cudaMemsetAsync(X.mrank, 0, sizeof(double) * n, st));           // every MICE starts at 0
     CK(cudaMemsetAsync(X.bmax, 0, sizeof(double) * (n / 32 + 2), st));
+    if (p->scorer_topk > 0) {                   // no kept prediction; no super-node changed yet
+        CK(cudaMemsetAsync(X.pkey, 0xff, sizeof(unsigned long long) * 2 * n, st));
+        CK(cudaMemsetAsync(X.moved, 0xff, sizeof(int) * n, st));
+    }
     if (p->prune_exact) {                       // every g_k starts at 0 (singletons: no spread, MICE 0)
         CK(cudaMemsetAsync(X.gpre, 0, sizeof(long long) * n, st));
         CK(cudaMemsetAsync(X.gbp, 0, sizeof(long long) * (n / 32 + 2), st));
+        CK(cudaMemsetAsync(X.lbkey, 0xff, sizeof(unsigned long long) * 2 * n, st));
     }
     CK(cudaMemsetAsync(ctx->fb.gb, 0, sizeof(GridBar), st));
     if (p->record_iters > 0) CK(cudaMemsetAsync(X.rec_count, 0, sizeof(int) * p->record_iters, st));

@@ -202,7 +202,13 @@ struct Search {
     int topk;
     const float *mlp_theta;
     const uint16_t *mlp_w1, *mlp_w2, *mlp_w3, *mlp_w4;
-    float *pred;            // [2n]
+    float *pred;            // [2n] by slot
+    // kept predictions, by candidate (2 * the slot pair's super-node + direction):
+    // the prediction, the key of the candidate it was made for (~0: none), and per
+    // super-node the merge count after which its state last changed (-1: never)
+    float *pcache;          // [2n]
+    unsigned long long *pkey;   // [2n]
+    int *moved;             // [n]
     // certified pruning (prune_exact = 1, with topk > 0): per compact candidate the
     // part of its lower bound that depends on it (lbp; +inf: surely infeasible);
     // per super-node rank floor(g_k 2^56) summed within its block of 32 ranks
@@ -213,6 +219,8 @@ struct Search {
     long long *gpre;        // [n]
     long long *gblk;        // [n / 32 + 2]
     long long *gbp;         // [n / 32 + 2]
+    double *lbc;            // [2n] lbp kept by candidate (as pcache), with its key
+    unsigned long long *lbkey;  // [2n]
     int *rec_count;
 };
 

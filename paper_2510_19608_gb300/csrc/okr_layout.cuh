@@ -151,10 +151,15 @@ inline void layout_feeder(Carver &c, int n, int L, int rec, int grid, long long 
     c.take(X.rec_count, R);
     c.take(X.rec_feat, R * 2 * N * kScorerFeatures);
     c.take(X.pred, 2 * N);
+    c.take(X.pcache, 2 * N);
+    c.take(X.pkey, 2 * N);
+    c.take(X.moved, N);
     c.take(X.lbp, 2 * N);
     c.take(X.gpre, N);
     c.take(X.gblk, N / 32 + 2);
     c.take(X.gbp, N / 32 + 2);
+    c.take(X.lbc, 2 * N);
+    c.take(X.lbkey, 2 * N);
     X.setup_err = nullptr;
     X.topk = 0;
     X.prune_exact = 0;

@@ -393,22 +393,32 @@ __device__ void mlp_load_smem(const Search &X, MlpSmem *W) {
 __device__ float mlp_predict_warp(const MlpSmem *W, const float *f) {
     const int lane = threadIdx.x & 31;
     float h[4], g[4];
+    // (unrolled, so that the shuffles and weight loads of later k issue ahead
+    // of the multiply-adds they feed: one prediction is a latency chain)
+#pragma unroll
     for (int m = 0; m < 4; ++m) {
         const int j = lane + 32 * m;
         float z = W->b1[j];
+#pragma unroll
         for (int k = 0; k < kScorerFeatures; ++k) z = fmaf(f[k], bf16f(W->w1[k * kMlpH + j]), z);
         h[m] = fmaxf(z, 0.0f);
     }
+#pragma unroll 1
     for (int layer = 0; layer < 2; ++layer) {
         const uint16_t *w = layer == 0 ? W->w2 : W->w3;
         const float *bias = layer == 0 ? W->b2 : W->b3;
+#pragma unroll
         for (int m = 0; m < 4; ++m) g[m] = bias[lane + 32 * m];
+#pragma unroll
         for (int ms = 0; ms < 4; ++ms)
+#pragma unroll 8
             for (int sl = 0; sl < 32; ++sl) {
                 const float hk = __shfl_sync(0xffffffffu, h[ms], sl);
                 const int k = ms * 32 + sl;
+#pragma unroll
                 for (int m = 0; m < 4; ++m) g[m] = fmaf(hk, bf16f(w[k * kMlpH + lane + 32 * m]), g[m]);
             }
+#pragma unroll
         for (int m = 0; m < 4; ++m) h[m] = fmaxf(g[m], 0.0f);
     }
     float acc = h[0] * bf16f(W->w4[lane]) + h[1] * bf16f(W->w4[lane + 32]) + h[2] * bf16f(W->w4[lane + 64]) +
@@ -463,6 +473,16 @@ __device__ unsigned topk_threshold(const Search &X, int nslots, int k, int nc) {
     return s_prefix;
 }
 
+// What a candidate's features depend on besides its clusters' state: s, r,
+// the common ancestor, the direction and the count of affected clusters,
+// packed (~0: not packable, n above 2^16; the prediction is then made again).
+__device__ __forceinline__ unsigned long long pred_key(const Cand &c, int n) {
+    const unsigned cnt = (unsigned)(c.ns + c.nr);
+    if (n >= 65536 || cnt >= (1u << 15)) return ~0ull;
+    return (unsigned long long)c.s | ((unsigned long long)c.r << 16) | ((unsigned long long)c.a << 32) |
+           ((unsigned long long)(c.dir & 1) << 48) | ((unsigned long long)cnt << 49);
+}
+
 __device__ __forceinline__ bool slot_selected(const Search &X, const Cand &c, unsigned theta) {
     return theta == ~0u || fkey(__ldcg(X.pred + c.pad)) <= theta;
 }
@@ -515,6 +535,20 @@ __device__ double cand_lb_part(const Topo &T, const State &S, int n, int L, cons
         const double ms = ldd(S.mice + (size_t)l * n + c.s), mr = ldd(S.mice + (size_t)l * n + c.r);
         part = __dadd_rd(part, __dsub_rd(__dsub_rd(hs, ms), mr));
     }
+    return part;
+}
+// The candidate's own part, kept per candidate like the scorer's predictions
+// (it reads only s's and r's state): computed again when the candidate changed
+// or s or r took part in the merge that made state number t.
+__device__ double cand_lb_part_kept(const Topo &T, const State &S, const Search &X, int n, int L, const Cand &c,
+                                    double margin, int t) {
+    const int cs = 2 * (c.dir == 0 ? c.r : c.s) + c.dir;
+    const unsigned long long key = pred_key(c, n);
+    if (key != ~0ull && __ldcg(X.lbkey + cs) == key && ldi(X.moved + c.s) != t && ldi(X.moved + c.r) != t)
+        return ldd(X.lbc + cs);
+    const double part = cand_lb_part(T, S, n, L, c, margin);
+    X.lbc[cs] = part;
+    X.lbkey[cs] = key;
     return part;
 }
 // The sum of floor(g_k 2^56) over the ranks below j: the blocks of 32 ranks
@@ -1039,62 +1073,77 @@ __device__ Screen screen_select(const Search &X, int nc, double margin, double t
 // scorer: how far r's injection moves (path impedance between r and the
 // common ancestor, and between s and it), how much is moved (injections of r
 // and s), phase counts, the current MICE and voltage spread of both clusters
-// relative to the margin, the direction and the number of affected clusters.
-__device__ void cand_features(const Topo &T, const State &S, int n, int L, const Cand &c, double margin, float *f) {
-    auto zdist = [&](int u) {
-        double acc = 0.0;
-        for (int q = 0; q < 9; ++q) {
-            const double2 d = csub(ldz(T.zc + (size_t)u * 9 + q), ldz(T.zc + (size_t)c.a * 9 + q));
-            acc += fabs(d.x) + fabs(d.y);
+// relative to the margin, the direction, the number of affected clusters and
+// the merged cluster's error at s's present voltage magnitude.  The whole
+// warp computes them (every lane must call this): the loads are spread over
+// the lanes, reduced by shuffles, and lane i < kScorerFeatures writes f[i].
+__device__ void cand_features_warp(const Topo &T, const State &S, int n, int L, const Cand &c, double margin,
+                                   float *f) {
+    const int lane = threadIdx.x & 31;
+    auto wsum = [](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    auto wmax = [](double v) {                 // (every value is >= 0)
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    };
+    const unsigned phs = T.ph[c.s], phr = T.ph[c.r];
+    // path impedances to the common ancestor: r on lanes 0-8, s on lanes 9-17
+    double zr = 0.0, zs = 0.0;
+    if (lane < 18) {
+        const int u = lane < 9 ? c.r : c.s, q = lane < 9 ? lane : lane - 9;
+        const double2 d = csub(ldz(T.zc + (size_t)u * 9 + q), ldz(T.zc + (size_t)c.a * 9 + q));
+        (lane < 9 ? zr : zs) = fabs(d.x) + fabs(d.y);
+    }
+    // per (scenario, phase) on lanes 0 .. 3L-1: injections, spreads, the merged error
+    double ir = 0.0, is = 0.0, spr = 0.0, sps = 0.0, em = 0.0;
+    if (lane < 3 * L) {
+        const int l = lane / 3, p = lane % 3;
+        const double2 a = ldz(S.icur + sidx(l, p, c.r, n)), b = ldz(S.icur + sidx(l, p, c.s, n));
+        ir = fabs(a.x) + fabs(a.y);
+        is = fabs(b.x) + fabs(b.y);
+        const size_t kr = sidx(l, p, c.r, n), ks = sidx(l, p, c.s, n);
+        if (phr >> p & 1u) spr = ldd(S.hi + kr) - ldd(S.lo + kr);
+        if (phs >> p & 1u) {
+            const double hs = ldd(S.hi + ks), lo = ldd(S.lo + ks), ms = ldd(S.mcur + ks);
+            sps = hs - lo;
+            em = fmax(hs - ms, ms - lo);
+            if (phr >> p & 1u) em = fmax(em, fmax(ldd(S.hi + kr) - ms, ms - ldd(S.lo + kr)));
         }
-        return acc;
-    };
-    auto inj = [&](int u) {
-        double acc = 0.0;
-        for (int l = 0; l < L; ++l)
-            for (int p = 0; p < 3; ++p) {
-                const double2 i = ldz(S.icur + sidx(l, p, u, n));
-                acc += fabs(i.x) + fabs(i.y);
-            }
-        return acc;
-    };
-    auto mice = [&](int u) {
-        double m = 0.0;
-        for (int l = 0; l < L; ++l) m = fmax(m, ldd(S.mice + (size_t)l * n + u));
-        return m;
-    };
-    auto spread = [&](int u) {
-        double m = 0.0;
-        for (int l = 0; l < L; ++l)
-            for (int p = 0; p < 3; ++p)
-                if (T.ph[u] >> p & 1u) m = fmax(m, ldd(S.hi + sidx(l, p, u, n)) - ldd(S.lo + sidx(l, p, u, n)));
-        return m;
-    };
-    f[0] = (float)log10(1e-9 + zdist(c.r));
-    f[1] = (float)log10(1e-9 + zdist(c.s));
-    f[2] = (float)log10(1e-9 + inj(c.r));
-    f[3] = (float)log10(1e-9 + inj(c.s));
-    f[4] = (float)__popc(T.ph[c.r]) / 3.0f;
-    f[5] = (float)__popc(T.ph[c.s]) / 3.0f;
-    f[6] = (float)(mice(c.r) / margin);
-    f[7] = (float)(mice(c.s) / margin);
-    f[8] = (float)c.dir;
-    f[9] = (float)log10(1.0 + c.ns + c.nr);
-    f[10] = (float)(spread(c.r) / margin);
-    f[11] = (float)(spread(c.s) / margin);
-    // the merged cluster's error before any voltage moves: r's members (and
-    // s's) measured against s's present voltage magnitude
-    double em = 0.0;
-    for (int l = 0; l < L; ++l)
-        for (int p = 0; p < 3; ++p) {
-            if (!(T.ph[c.s] >> p & 1u)) continue;
-            const double ms = ldd(S.mcur + sidx(l, p, c.s, n));
-            em = fmax(em, fmax(ldd(S.hi + sidx(l, p, c.s, n)) - ms, ms - ldd(S.lo + sidx(l, p, c.s, n))));
-            if (T.ph[c.r] >> p & 1u)
-                em = fmax(em, fmax(ldd(S.hi + sidx(l, p, c.r, n)) - ms, ms - ldd(S.lo + sidx(l, p, c.r, n))));
-        }
-    f[12] = (float)(em / margin);
-    f[13] = (float)((em - mice(c.r) - mice(c.s)) / margin);
+    }
+    // MICE per scenario: r on lanes 0 .. L-1, s on lanes 8 .. 8+L-1
+    double mr = 0.0, msx = 0.0;
+    if (lane < L) mr = ldd(S.mice + (size_t)lane * n + c.r);
+    if (lane >= 8 && lane < 8 + L) msx = ldd(S.mice + (size_t)(lane - 8) * n + c.s);
+    zr = wsum(zr);
+    zs = wsum(zs);
+    ir = wsum(ir);
+    is = wsum(is);
+    spr = wmax(spr);
+    sps = wmax(sps);
+    em = wmax(em);
+    mr = wmax(mr);
+    msx = wmax(msx);
+    if (lane >= kScorerFeatures) return;
+    float v = 0.0f;
+    switch (lane) {
+        case 0: v = (float)log10(1e-9 + zr); break;
+        case 1: v = (float)log10(1e-9 + zs); break;
+        case 2: v = (float)log10(1e-9 + ir); break;
+        case 3: v = (float)log10(1e-9 + is); break;
+        case 4: v = (float)__popc(phr) / 3.0f; break;
+        case 5: v = (float)__popc(phs) / 3.0f; break;
+        case 6: v = (float)(mr / margin); break;
+        case 7: v = (float)(msx / margin); break;
+        case 8: v = (float)c.dir; break;
+        case 9: v = (float)log10(1.0 + c.ns + c.nr); break;
+        case 10: v = (float)(spr / margin); break;
+        case 11: v = (float)(sps / margin); break;
+        case 12: v = (float)(em / margin); break;
+        default: v = (float)((em - mr - msx) / margin); break;
+    }
+    f[lane] = v;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -1158,15 +1207,17 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 const int nR = sc.nR;
                 stamp(0);
                 if (rank == 0 && t < X.rec_iters) {
-                    for (int c = tid; c < nc; c += nt) {
+                    for (int c = tid >> 5; c < nc; c += nt >> 5) {        // one warp per candidate
                         const Cand cc = ldcand(X.cand + c);
-                        const float4 q = __ldcg(X.scr + c);
-                        const bool out = __fsub_rd(q.z, q.w) > __double2float_ru(margin);
-                        X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
-                        X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
-                        X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : (obj1 ? 0.0 : s_cur) + (double)q.x;
-                        X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
-                        cand_features(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
+                        if (lane == 0) {
+                            const float4 q = __ldcg(X.scr + c);
+                            const bool out = __fsub_rd(q.z, q.w) > __double2float_ru(margin);
+                            X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
+                            X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
+                            X.rec_score[(size_t)t * 2 * n + c] = out ? INFINITY : (obj1 ? 0.0 : s_cur) + (double)q.x;
+                            X.rec_bound[(size_t)t * 2 * n + c] = out ? 0.0 : (double)q.y;
+                        }
+                        cand_features_warp(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
                     }
                 }
                 if (!sc.any) {
@@ -1239,14 +1290,16 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
             }
             if (full64) {
                 if (PREC == 0 && rank == 0 && t < X.rec_iters) {
-                    for (int c = tid; c < nc; c += nt) {
+                    for (int c = tid >> 5; c < nc; c += nt >> 5) {        // one warp per candidate
                         const Cand cc = ldcand(X.cand + c);
-                        X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
-                        X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
-                        X.rec_score[(size_t)t * 2 * n + c] =
-                            ldi(X.feas + c) ? (obj1 ? 0.0 : s_cur) + ldd(X.score + c) : INFINITY;
-                        X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
-                        cand_features(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
+                        if (lane == 0) {
+                            X.rec_s[(size_t)t * 2 * n + c] = T.orig[cc.s];
+                            X.rec_r[(size_t)t * 2 * n + c] = T.orig[cc.r];
+                            X.rec_score[(size_t)t * 2 * n + c] =
+                                ldi(X.feas + c) ? (obj1 ? 0.0 : s_cur) + ldd(X.score + c) : INFINITY;
+                            X.rec_bound[(size_t)t * 2 * n + c] = 0.0;
+                        }
+                        cand_features_warp(T, S, n, L, cc, margin, X.rec_feat + ((size_t)t * 2 * n + c) * kScorerFeatures);
                     }
                 }
                 sel = select_exact(X, nc, nullptr, X.score, X.feas, tau, smd, smu, smi, ~0ull, nc);
@@ -1363,6 +1416,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                     S.hr32[ik] = (float)(h - o.m);
                     S.lr32[ik] = (float)(lo - o.m);
                 }
+                if (live && p == 0 && l == 0 && X.moved) X.moved[kk] = t + 1;   // its inputs change with this merge
                 if (live && p == 0) {
                     const double mold = ldd(S.mice + (size_t)l * n + kk);
                     double d = m - mold;
@@ -1387,6 +1441,10 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                 if (cd.dir == 1) {
                     S.top[cd.s] = ldi(S.top + cd.r);
                     S.ptop[cd.s] = ldi(S.ptop + cd.r);
+                }
+                if (X.moved) {
+                    X.moved[cd.s] = t + 1;
+                    X.moved[cd.r] = t + 1;
                 }
                 X.dec_s[t] = T.orig[cd.s];
                 X.dec_r[t] = T.orig[cd.r];
@@ -1567,7 +1625,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         Cand c = X.slot[2 * gt + d];
                         if (c.s < 0) continue;
                         c.pad = 2 * gt + d;                 // the candidate's slot (its prediction)
-                        if (X.prune_exact) X.lbp[ci] = cand_lb_part(T, S, n, L, c, margin);
+                        if (X.prune_exact) X.lbp[ci] = cand_lb_part_kept(T, S, X, n, L, c, margin, t);
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;
@@ -1585,7 +1643,7 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
                         Cand c = X.slot[2 * j + d];
                         if (c.s < 0) continue;
                         c.pad = 2 * j + d;
-                        if (X.prune_exact) X.lbp[ci] = cand_lb_part(T, S, n, L, c, margin);
+                        if (X.prune_exact) X.lbp[ci] = cand_lb_part_kept(T, S, X, n, L, c, margin, t);
                         X.cand[ci] = c;
                         X.ckey[ci] = c.key;
                         X.base[ci] = pos;
@@ -1623,17 +1681,32 @@ __device__ __forceinline__ void search_run(const Topo &T, const State &S, const 
         }
         if (MW) {
             // the scorer's prediction for every candidate slot (slots are readable
-            // since barrier 1), warps of the CTAs that compact taking the last slots
+            // since barrier 1), warps of the CTAs that compact taking the last slots.
+            // Predictions are kept per candidate (by its slot pair's super-node,
+            // which, unlike the slot index, does not shift with the ranks) and
+            // made again only when the candidate changed (s, r, the common
+            // ancestor, the direction or the count of affected clusters) or s or
+            // r took part in the last merge: every feature reads only those.
             const int nsl = 2 * ns, wl = tid >> 5;
             const int mw = (warp + nwarps - min(32, nwarps)) % nwarps;
             for (int sl = mw; sl < nsl; sl += nwarps) {
                 const Cand c = ldcand(X.slot + sl);
                 float y = INFINITY;
                 if (c.s >= 0) {
-                    if (lane == 0) cand_features(T, S, n, L, c, margin, MW->feat[wl]);
-                    __syncwarp();
-                    y = mlp_predict_warp(MW, MW->feat[wl]);
-                    __syncwarp();
+                    const int cs = 2 * (c.dir == 0 ? c.r : c.s) + c.dir;     // the slot pair's super-node
+                    const unsigned long long key = pred_key(c, n);
+                    if (key != ~0ull && __ldcg(X.pkey + cs) == key && ldi(X.moved + c.s) != t && ldi(X.moved + c.r) != t) {
+                        y = __ldcg(X.pcache + cs);                       // (the same for the whole warp)
+                    } else {
+                        cand_features_warp(T, S, n, L, c, margin, MW->feat[wl]);
+                        __syncwarp();
+                        y = mlp_predict_warp(MW, MW->feat[wl]);
+                        __syncwarp();
+                        if (lane == 0) {
+                            X.pcache[cs] = y;
+                            X.pkey[cs] = key;
+                        }
+                    }
                 }
                 if (lane == 0) X.pred[sl] = y;
             }
