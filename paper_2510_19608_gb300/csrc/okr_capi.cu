@@ -1343,7 +1343,7 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
         for (int f : R.ord[g]) {
             if (g >= 2) {                           // the incremental groups' first evaluation on many CTAs
                 ictas_h[k] = ctas;
-                ctas += (R.nbus[f] + kIncInitPairs - 1) / kIncInitPairs;
+                ctas += inc_init_batch_ctas(R.nbus[f]);
             }
             order_h[k++] = f;
         }

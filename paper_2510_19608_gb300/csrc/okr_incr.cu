@@ -1949,64 +1949,15 @@ __global__ void __launch_bounds__(NT, 1) k_search_inc(Topo T, State S, Search X,
 }
 
 // The first evaluation of every candidate (every slot pair from the initial
-// clusters, all singletons, every term), which needs no merge before it: the
-// pairs are spread over many CTAs (kInitPairs per CTA) instead of the one CTA
-// of the search.  Each CTA writes its pairs' candidates, carried sums and
-// selection records to device memory, in the layout the search reads
-// (k_search_inc with pre_init copies the records into shared memory).  The
+// clusters, all singletons, every term), which needs no merge before it: its
+// work is spread over many CTAs instead of the one CTA of the search.  The
+// CTAs write the candidates, carried sums and tie keys to device memory, in
+// the layout the search reads (k_search_inc with pre_init copies the records
+// into shared memory and derives the selection keys from the sums).  The
 // terms are evaluated by the same code as in the search, so the carried sums
 // are the ones the search's own first evaluation gives.
 constexpr int kInitPairs = kIncInitPairs;
 constexpr int kInitCtasMax = kIncInitCtasMax;
-// The pairs [w0, w0 + kInitPairs) of one feeder (list: shared scratch of n
-// 16-bit entries).
-template <int NT, int PREC>
-__device__ void inc_init_pairs(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, int w0,
-                               unsigned short *list, EvalSmem<NT> &E, int *sscan, int *s_cnt) {
-    const int n = T.n, L = T.L, tid = threadIdx.x;
-    const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
-    const double margin = C->margin;
-    const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
-    const int w1 = min(n, w0 + kInitPairs);
-    // every bus is its own super-node: the list and the ranks are the identity
-    for (int w = tid; w < n; w += NT) list[w] = (unsigned short)w;
-    for (int w = w0 + tid; w < w1; w += NT) I.fpair[w] = w;
-    if (tid == 0) *s_cnt = 0;
-    Loc Lc;
-    Lc.wsm = nullptr;
-    Lc.wgl = I.work + 2 * (size_t)w0;           // at most two entries per pair
-    Lc.se = 0;
-    Lc.lst[0] = Lc.lst[1] = list;
-    Lc.ph = T.ph;
-    Lc.rank = S.sn_rank;
-    Rec R;
-    R.r0 = reinterpret_cast<u128 *>(I.recbuf);
-    R.r1 = reinterpret_cast<ulonglong2 *>(I.recbuf);
-    R.tkey = reinterpret_cast<unsigned *>(I.recbuf + (size_t)32 * n);
-    R.maxm = I.maxm;
-    R.span = reinterpret_cast<ushort4 *>(I.recbuf + (size_t)40 * n);
-    R.bsum = nullptr;
-    R.bcnt = nullptr;
-    R.bmx = nullptr;
-    R.dirty = nullptr;
-    R.nb = 0;
-    Ovl O;
-    O.map = nullptr;                            // (the first evaluation reads the stored state only)
-    O.cbuf = I.cbuf;
-    O.s = O.r = -1;
-    O.nfree = 0;
-    __syncthreads();
-    rebuild_pairs<NT, PREC>(T, S, X, I, n, I.fpair + w0, w1 - w0, s_cnt, 0, R, Lc, no_view());
-    __syncthreads();
-    const long long terms = run_entries<NT, PREC>(T, S, X, I, n, L, G, margin, mlo, mhi, 0, *s_cnt, kInit, list, list,
-                                                  -1, O, E, sscan, R, Lc);
-    if (C->profile) {                           // (phase-node, scenario) items
-        unsigned long long tt = (unsigned long long)terms;
-        for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
-        if ((tid & 31) == 0 && tt) atomicAdd(reinterpret_cast<unsigned long long *>(&C->sweep_ns), tt);
-    }
-}
-
 // The first evaluation of one feeder with its work spread evenly over the
 // grid.  A pair's candidates can hold up to n positions each (the pairs next
 // to the root), so splitting by pairs leaves one CTA with most of the work.
@@ -2020,19 +1971,17 @@ __device__ void inc_init_pairs(const Topo &T, const State &S, const Search &X, c
 // the live candidates' selection keys from the finished sums.
 // Dynamic shared memory: the identity super-node list (2n bytes) and the
 // position count of every slot (8n bytes).
+// CTA b of the B CTAs that evaluate one feeder (dyn: dynamic shared memory of
+// 2n + 8n bytes, 16-byte aligned parts).
 template <int NT, int PREC>
-__global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
-    extern __shared__ __align__(16) unsigned char init_dyn[];
-    __shared__ __align__(16) EvalSmem<NT> E;
-    __shared__ int sscan[33];
-    __shared__ int s_first, s_ne;
-    if (X.setup_err && *X.setup_err != 0) return;
-    const int n = T.n, L = T.L, tid = threadIdx.x, b = blockIdx.x, B = gridDim.x;
+__device__ void inc_init_share(const Topo &T, const State &S, const Search &X, const Inc &I, Ctrl *C, int b, int B,
+                               unsigned char *dyn, EvalSmem<NT> &E, int *sscan, int &s_first, int &s_ne) {
+    const int n = T.n, L = T.L, tid = threadIdx.x;
     const int G = 4 * (L <= 1 ? 1 : (L <= 2 ? 2 : 4));
     const double margin = C->margin;
     const float mlo = __double2float_rd(margin), mhi = __double2float_ru(margin);
-    unsigned short *list = reinterpret_cast<unsigned short *>(init_dyn);
-    int *pcnt = reinterpret_cast<int *>(init_dyn + align16((size_t)2 * n));
+    unsigned short *list = reinterpret_cast<unsigned short *>(dyn);
+    int *pcnt = reinterpret_cast<int *>(dyn + align16((size_t)2 * n));
     for (int w = tid; w < n; w += NT) list[w] = (unsigned short)w;
     Loc Lc;
     Lc.wsm = nullptr;
@@ -2153,21 +2102,33 @@ __global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc 
     }
 }
 
+template <int NT, int PREC>
+__global__ void __launch_bounds__(NT) k_inc_init(Topo T, State S, Search X, Inc I, Ctrl *C) {
+    extern __shared__ __align__(16) unsigned char init_dyn[];
+    __shared__ __align__(16) EvalSmem<NT> E;
+    __shared__ int sscan[33];
+    __shared__ int s_first, s_ne;
+    if (X.setup_err && *X.setup_err != 0) return;
+    inc_init_share<NT, PREC>(T, S, X, I, C, blockIdx.x, gridDim.x, init_dyn, E, sscan, s_first, s_ne);
+}
+
 // The same for many feeders: cta_off[i] = the first CTA of the i-th feeder of
-// the order (ceil(n / kInitPairs) CTAs each); feeders whose setup failed are
-// skipped.
+// the order (the feeder's CTAs end where the next feeder's begin, the last
+// feeder's at the end of the grid); each feeder's CTAs split its positions
+// as above.  Feeders whose setup failed are skipped.  The carried sums of
+// every feeder start at zero (k_inc_zero_batch).
 template <int NT, int PREC>
 __global__ void __launch_bounds__(NT) k_inc_init_batch(const BatchFeeder *fd, const int *order, const int *cta_off,
                                                        int nf) {
     extern __shared__ __align__(16) unsigned char init_dyn[];
     __shared__ __align__(16) EvalSmem<NT> E;
     __shared__ int sscan[33];
-    __shared__ int s_cnt;
+    __shared__ int s_first, s_ne;
     __shared__ Topo sT;
     __shared__ State sS;
     __shared__ Search sX;
     __shared__ Inc sI;
-    __shared__ int s_f, s_w0;
+    __shared__ int s_f, s_b, s_B;
     const int b = blockIdx.x;
     if (threadIdx.x == 0) {
         int lo = 0, hi = nf - 1;                 // the last feeder whose first CTA is <= b
@@ -2178,7 +2139,8 @@ __global__ void __launch_bounds__(NT) k_inc_init_batch(const BatchFeeder *fd, co
         }
         const int f = order[lo];
         s_f = f;
-        s_w0 = (b - cta_off[lo]) * kInitPairs;
+        s_b = b - cta_off[lo];
+        s_B = (lo + 1 < nf ? cta_off[lo + 1] : (int)gridDim.x) - cta_off[lo];
         sT = fd[f].T;
         sS = fd[f].S;
         sX = fd[f].X;
@@ -2186,9 +2148,21 @@ __global__ void __launch_bounds__(NT) k_inc_init_batch(const BatchFeeder *fd, co
     }
     __syncthreads();
     const int f = s_f;
-    if (*fd[f].setup_err != 0 || s_w0 >= sT.n) return;
-    inc_init_pairs<NT, PREC>(sT, sS, sX, sI, fd[f].C, s_w0, reinterpret_cast<unsigned short *>(init_dyn), E, sscan,
-                             &s_cnt);
+    if (*fd[f].setup_err != 0 || s_b >= s_B) return;
+    inc_init_share<NT, PREC>(sT, sS, sX, sI, fd[f].C, s_b, s_B, init_dyn, E, sscan, s_first, s_ne);
+}
+
+// The carried sums, violation counts and their bounds of every feeder of the
+// order set to zero before its first evaluation adds to them (one CTA per
+// feeder).
+__global__ void k_inc_zero_batch(const BatchFeeder *fd, const int *order, int nf) {
+    const int q = blockIdx.x;
+    if (q >= nf) return;
+    const Inc &I = fd[order[q]].I;
+    const int n = fd[order[q]].T.n;
+    unsigned char *p0 = reinterpret_cast<unsigned char *>(I.acc);
+    const size_t bytes = reinterpret_cast<const unsigned char *>(I.vmay + 2 * (size_t)n) - p0;
+    for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) reinterpret_cast<unsigned *>(p0)[i] = 0u;
 }
 
 // One CTA per feeder, feeders in the order given (largest first).
@@ -2337,7 +2311,7 @@ cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder 
 }
 
 cudaError_t prepare_inc_init_batch(int precision, int max_n) {
-    const size_t ismem = align16((size_t)2 * max_n);
+    const size_t ismem = align16((size_t)2 * max_n) + align16((size_t)8 * max_n);
     if (ismem <= 48 * 1024) return cudaSuccess;
     return precision == 1 ? set_smem(k_inc_init_batch<kInitThreads, 1>, ismem)
                           : set_smem(k_inc_init_batch<kInitThreads, 0>, ismem);
@@ -2346,7 +2320,8 @@ cudaError_t prepare_inc_init_batch(int precision, int max_n) {
 cudaError_t launch_inc_init_batch(int precision, int max_n, const BatchFeeder *fd, const int *order,
                                   const int *cta_off, int nf, int ctas, cudaStream_t st) {
     if (nf <= 0 || ctas <= 0) return cudaSuccess;
-    const size_t ismem = align16((size_t)2 * max_n);
+    const size_t ismem = align16((size_t)2 * max_n) + align16((size_t)8 * max_n);
+    k_inc_zero_batch<<<nf, 256, 0, st>>>(fd, order, nf);
     if (precision == 1) k_inc_init_batch<kInitThreads, 1><<<ctas, kInitThreads, ismem, st>>>(fd, order, cta_off, nf);
     else k_inc_init_batch<kInitThreads, 0><<<ctas, kInitThreads, ismem, st>>>(fd, order, cta_off, nf);
     return cudaGetLastError();

@@ -35,6 +35,18 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
     double d = b.x * b.x + b.y * b.y;
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
+// Load current of a constant-power load s at voltage v, conj(s / v), as
+// conj(s) v / |v|^2 with one reciprocal.  Every operation is explicitly
+// rounded, so the single-feeder and the batched load flows, which both call
+// it, give the same bits.
+__device__ __forceinline__ double2 load_current(double2 s, double2 v) {
+    const double inv = __drcp_rn(__fma_rn(v.x, v.x, __dmul_rn(v.y, v.y)));
+    return make_double2(__dmul_rn(__fma_rn(s.x, v.x, __dmul_rn(s.y, v.y)), inv),
+                        __dmul_rn(__fma_rn(s.x, v.y, -__dmul_rn(s.y, v.x)), inv));
+}
+// |a|^2, explicitly rounded (the load flows' convergence test compares the
+// largest squared voltage change with tol^2: no square root per element).
+__device__ __forceinline__ double cmag2(double2 a) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)); }
 
 __host__ __device__ __forceinline__ size_t sidx(int l, int p, int k, int n) { return ((size_t)l * 3 + p) * n + k; }
 

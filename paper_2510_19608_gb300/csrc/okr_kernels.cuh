@@ -155,8 +155,15 @@ struct IncShape {
     int threads, cw, se, rec;
 };
 constexpr int kIncDefaultThreads = 384;
-constexpr int kIncInitPairs = 8;        // slot pairs per CTA of the first evaluation (batches)
+constexpr int kIncInitPairs = 8;        // slot pairs per CTA of one feeder's first evaluation (at most all SMs)
 constexpr int kIncInitCtasMax = 256;    // CTAs of one feeder's first evaluation, at most
+constexpr int kIncInitBatchBuses = 64;  // buses per CTA of a batch's first evaluation
+// CTAs of one feeder's first evaluation in a batch (its positions split
+// evenly over them; the work buffer holds 2n + kIncInitCtasMax entries).
+inline int inc_init_batch_ctas(int n) {
+    const int c = (n + kIncInitBatchBuses - 1) / kIncInitBatchBuses;
+    return c < 1 ? 1 : (c > kIncInitCtasMax ? kIncInitCtasMax : c);
+}
 // Out-of-range fields replaced by the defaults (384 threads, 2 evaluation
 // warps (4 with 512 threads), 256 shared entries, automatic records).
 IncShape inc_shape_resolve(IncShape sh);
@@ -176,8 +183,9 @@ cudaError_t launch_search_inc_batch(int precision, int max_n, const BatchFeeder 
                                     IncShape sh, cudaStream_t st);
 // The batch's first evaluation on many CTAs, before launch_search_inc_batch
 // (which then takes it as done): cta_off[i] = the first CTA of order[i]
-// (ceil(n / kIncInitPairs) each), ctas = their total.  prepare_inc_init_batch sets the
-// kernel's shared-memory attribute (before any stream capture).
+// (inc_init_batch_ctas(n) each), ctas = their total; it first zeroes the
+// feeders' carried sums.  prepare_inc_init_batch sets the kernel's
+// shared-memory attribute (before any stream capture).
 cudaError_t prepare_inc_init_batch(int precision, int max_n);
 cudaError_t launch_inc_init_batch(int precision, int max_n, const BatchFeeder *fd, const int *order,
                                   const int *cta_off, int nf, int ctas, cudaStream_t st);

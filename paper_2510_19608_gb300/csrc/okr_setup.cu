@@ -303,9 +303,13 @@ __global__ void __launch_bounds__(1024) k_rmq_all(int n, int nlev, const int *__
 __device__ void dev_lca_fill(int n, const int *__restrict__ parent, const int *__restrict__ sz,
                              const int *__restrict__ depth, const uint16_t *__restrict__ st, uint16_t *lca,
                              size_t first, size_t stride) {
-    size_t tot = (size_t)n * n;
+    // (u, v) of element e advanced by the stride without a division per
+    // element (n * n < 2^31 for the 16-bit table)
+    const size_t tot = (size_t)n * n;
+    if (first >= tot) return;
+    const int du = (int)(stride / n), dv = (int)(stride % n);
+    int u = (int)(first / n), v = (int)(first % n);
     for (size_t e = first; e < tot; e += stride) {
-        int u = (int)(e / n), v = (int)(e % n);
         int lo = u < v ? u : v, hi = u < v ? v : u;
         int res;
         if (lo == hi || hi < lo + sz[lo]) {
@@ -319,6 +323,9 @@ __device__ void dev_lca_fill(int n, const int *__restrict__ parent, const int *_
             res = parent[m];
         }
         lca[e] = (uint16_t)res;
+        u += du;
+        v += dv;
+        if (v >= n) { v -= n; ++u; }
     }
 }
 
@@ -405,10 +412,10 @@ cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sm
 // Backward/forward sweep for every scenario.  Constant-power wye loads: the
 // current drawn at (k,p) is conj(S/V).  Backward: J_k = load(k) + the sum of the
 // children's J (children in preorder order).  Forward: V_k = V_parent - z_k J_k.
-// A scenario stops when max |dV| < tol; one that has not stopped after max_iter
-// sweeps is a failure.
+// A scenario stops when max |dV| < tol (tested as max |dV|^2 < tol^2); one that
+// has not stopped after max_iter sweeps is a failure.
 //
-// FP64 division, the 3x3 products and the magnitudes dominate the arithmetic,
+// FP64 reciprocals, the 3x3 products and the squared changes dominate the arithmetic,
 // and GB300's FP64 rate per SM is low, so these run over the whole cooperative
 // grid; only the level-by-level sums (additions) run one CTA per (scenario,
 // phase), staged in shared memory.  Four grid barriers per sweep:
@@ -416,7 +423,7 @@ cudaError_t launch_lines(int n, Topo T, const double *z_in, int *err, int num_sm
 //   S2 line currents J = I1 + sum children J  (CTA per (l, p), deepest level first)
 //   S3 drops D = z J                            (grid)
 //   S4 new voltages Vn = Vn_parent - D          (CTA per (l, p), top down)
-//   S5 |Vn - V|, V = Vn, per-scenario maximum   (grid)
+//   S5 |Vn - V|^2, V = Vn, per-scenario maximum (grid)
 // S5 and the next sweep's S1 touch the same element on the same thread, so
 // they run as one pass (the load currents of a scenario that has just
 // converged are computed and never read).  I1, D and Vn share one buffer W
@@ -468,6 +475,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     // an earlier setup step failed (every CTA reads the same flag: no writer runs)
     if (*reinterpret_cast<volatile const int *>(err) != 0) return;
     const int maxd = T.maxd[0];
+    const double tol2 = tol * tol;                  // the test is max |dV|^2 < tol^2
     unsigned epoch = 0;
     for (size_t e = gt; e < tot; e += gs) {
         const int v = (int)(e % n), p = (int)((e / n) % 3);
@@ -479,12 +487,12 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     double2 *const loc = n <= kPfShared ? pf_sm : nullptr;
     bool conv_all = false;
     // the load current of element e on voltage vv (S1)
-    auto load_current = [&](size_t e, int l, int p, int v, double2 vv) {
+    auto set_load_current = [&](size_t e, int l, int p, int v, double2 vv) {
         double2 j = make_double2(0.0, 0.0);
         if (T.ph[v] >> p & 1u) {
             const size_t o = (((size_t)l * n + T.orig[v]) * 3 + p) * 2;
             const double2 sv = make_double2(__ldg(s_in + o), __ldg(s_in + o + 1));
-            j = cconj(cdiv(sv, vv));
+            j = load_current(sv, vv);
         }
         W[e] = j;
     };
@@ -492,7 +500,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
     // S1 of the first sweep (each element on the thread that set its voltage)
     for (size_t e = gt; e < tot; e += gs) {
         const int l = (int)(e / N3), p = (int)((e / n) % 3), v = (int)(e % n);
-        load_current(e, l, p, v, T.vhat[e]);
+        set_load_current(e, l, p, v, T.vhat[e]);
     }
     if (!pf_grid_sync(bar, err, G, epoch, max_spins)) return;
     int it;
@@ -562,14 +570,14 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
             double2 vv = T.vhat[e];
             if (v != 0 && (T.ph[v] >> p & 1u)) {
                 const double2 vn = W[e];
-                double dd = cmag(csub(vn, vv));
+                double dd = cmag2(csub(vn, vv));             // squared change (compared with tol^2)
                 if (!isfinite(dd)) dd = INFINITY;           // a diverging sweep never converges
                 T.vhat[e] = vn;
                 vv = vn;
                 for (int l2 = 0; l2 < kMaxScen; ++l2)
                     if (l2 == l) mx[l2] = fmax(mx[l2], dd);
             }
-            load_current(e, l, p, v, vv);
+            set_load_current(e, l, p, v, vv);
         }
         for (int l = 0; l < L; ++l) {
             double m = mx[0];
@@ -585,7 +593,7 @@ __global__ void __launch_bounds__(256) k_power_flow(int n, int L, Topo T, const 
         __syncthreads();
         if (tid < L && s_live[tid]) {
             const double m = __longlong_as_double((long long)__ldcg((const unsigned long long *)&red[(it % 3) * L + tid]));
-            if (m < tol) {
+            if (m < tol2) {
                 s_live[tid] = 0;
                 if (blockIdx.x == 0) iters[tid] = it;
             }
@@ -730,6 +738,7 @@ __device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__
             V[sidx(l, p, v, n)] = (T.ph[v] >> p & 1u) ? T.vslack[p] : make_double2(0.0, 0.0);
     __syncthreads();
     const int maxd = T.maxd[0];
+    const double tol2 = tol * tol;                  // the test is max |dV|^2 < tol^2
     int it;
     bool conv = false;
     for (it = 1; it <= max_iter; ++it) {
@@ -740,7 +749,7 @@ __device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__
                     double2 j = make_double2(0.0, 0.0);
                     if (T.ph[v] >> p & 1u) {
                         const size_t o = (((size_t)l * n + i) * 3 + p) * 2;
-                        j = cconj(cdiv(make_double2(s_in[o], s_in[o + 1]), V[sidx(l, p, v, n)]));
+                        j = load_current(make_double2(s_in[o], s_in[o + 1]), V[sidx(l, p, v, n)]);
                     }
                     for (int c = T.child_off[v]; c < T.child_off[v + 1]; ++c) j = cadd(j, Jl[(size_t)p * n + T.child[c]]);
                     Jl[(size_t)p * n + v] = j;
@@ -758,7 +767,7 @@ __device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__
                     for (int q = 0; q < 3; ++q)
                         if (T.ph[v] >> q & 1u) drop = cadd(drop, cmul(T.zl[(size_t)v * 9 + p * 3 + q], Jl[(size_t)q * n + v]));
                     const double2 vn = csub(V[sidx(l, p, par, n)], drop);
-                    double dd = cmag(csub(vn, V[sidx(l, p, v, n)]));
+                    double dd = cmag2(csub(vn, V[sidx(l, p, v, n)]));   // squared change
                     if (!isfinite(dd)) dd = INFINITY;
                     dmax = fmax(dmax, dd);
                     V[sidx(l, p, v, n)] = vn;
@@ -772,7 +781,7 @@ __device__ void dev_power_flow_cta(int n, int l, const Topo &T, const double *__
         if (tid == 0) {
             double m = 0.0;
             for (int w = 0; w < (nt + 31) / 32; ++w) m = fmax(m, s_red[w]);
-            s_conv = (m < tol);
+            s_conv = (m < tol2);
         }
         __syncthreads();
         if (s_conv) { conv = true; break; }
