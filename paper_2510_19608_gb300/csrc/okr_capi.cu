@@ -1105,9 +1105,12 @@ struct BatchRun {
     int *ictas_d = nullptr;                         // incremental groups: first CTA of each feeder's first evaluation
     int init_ctas[2] = {0, 0};                      // CTAs of that evaluation, per precision
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;    // the setup's side-stream fork and join
     ~BatchRun() {
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
     }
     // host views of the result area and of the assignments
     const Ctrl *ctrl_res() const { return reinterpret_cast<const Ctrl *>(hb + staged); }
@@ -1351,6 +1354,8 @@ static okr_status batch_fill(okr_ctx *ctx, BatchRun &R, const okr_feeder *feeder
     }
     for (cudaEvent_t &e : R.ev)
         if (!e) CK(cudaEventCreate(&e));
+    if (!R.ev_fork) CK(cudaEventCreateWithFlags(&R.ev_fork, cudaEventDisableTiming));
+    if (!R.ev_join) CK(cudaEventCreateWithFlags(&R.ev_join, cudaEventDisableTiming));
     // attributes the launches need, set before any stream capture
     for (int g = 2; g < 4; ++g) {
         int max_n = 2;
@@ -1368,9 +1373,11 @@ static okr_status batch_enqueue(okr_ctx *ctx, BatchRun &R, cudaStream_t st, bool
     const int nf = R.nf;
     // in a graph, event records are nodes of their own only when external
     const unsigned evf = captured ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (!captured) CK(join_side(ctx));          // (the setup forks onto the side stream)
     CK(cudaMemcpyAsync(R.base, R.hb, R.staged, cudaMemcpyHostToDevice, st));
     CK(cudaEventRecordWithFlags(R.ev[0], st, evf));
-    CK(launch_batch_setup(nf, R.maxL, R.max_nn, R.bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st));
+    CK(launch_batch_setup(nf, R.maxL, R.max_nn, R.bs_d, kPfTol, kPfMaxIter, ctx->num_sms, st, ctx->side, R.ev_fork,
+                          R.ev_join));
     CK(cudaEventRecordWithFlags(R.ev[1], st, evf));
     R.ctas = 0;
     for (int g = 0, first = 0; g < 4; first += (int)R.ord[g].size(), ++g) {
@@ -1648,9 +1655,12 @@ okr_status okr_batch_plan_create(okr_ctx *ctx, int32_t n_feeders, const okr_feed
         s = batch_fill(ctx, P->R, feeders);
     }
     if (s == OKR_OK) {
-        // the whole device sequence of one run, captured once
+        // the whole device sequence of one run, captured once (the side stream,
+        // which the setup forks onto, has no earlier work left to join)
         cudaStream_t st = ctx->stream;
-        e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        e = join_side(ctx);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->side);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             s = fail(ctx, OKR_ECUDA, "batch plan capture: %s", cudaGetErrorString(e));
         } else {

@@ -1065,7 +1065,7 @@ __device__ __forceinline__ long long commit_groups(const Topo &T, const State &S
 // merge.  kInit / kFresh / kF64: every term of the entries, positions from
 // list_pre.  Returns the number of terms evaluated.
 template <int NT, int PREC>
-__device__ __noinline__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
+__device__ __forceinline__ long long run_entries(const Topo &T, const State &S, const Search &X, const Inc &I, int n, int L, int G,
                                  double margin, float mlo, float mhi, int e0, int e1, int pass,
                                  const unsigned short *list_pre, const unsigned short *list_post, int rstar,
                                  const Ovl O, EvalSmem<NT> &E, int *sscan, const Rec &R, const Loc &Lc,

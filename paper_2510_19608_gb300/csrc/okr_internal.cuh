@@ -48,7 +48,8 @@ __device__ __forceinline__ double2 load_current(double2 s, double2 v) {
 // largest squared voltage change with tol^2: no square root per element).
 __device__ __forceinline__ double cmag2(double2 a) { return __fma_rn(a.x, a.x, __dmul_rn(a.y, a.y)); }
 
-__host__ __device__ __forceinline__ size_t sidx(int l, int p, int k, int n) { return ((size_t)l * 3 + p) * n + k; }
+// (32-bit arithmetic: L * 3 * n < 2^31 for every feeder the library accepts)
+__host__ __device__ __forceinline__ size_t sidx(int l, int p, int k, int n) { return (size_t)(unsigned)((l * 3 + p) * n + k); }
 
 // ---------------------------------------------------------------- device structures
 // Static description of one feeder (preorder numbering), built once per call.

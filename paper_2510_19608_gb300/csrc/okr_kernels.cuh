@@ -48,9 +48,13 @@ struct BatchSetup {
     double *dec_maxerr, *mrank, *bmax;
     int *arrive;
 };
-// Setup of many feeders in four launches (CTA per feeder, per feeder x scenario).
+// Setup of many feeders in four launches (CTA per feeder, per feeder x scenario):
+// the LCA tables run on `side` (forked from st after the per-feeder prep by
+// ev_fork, joined back into st by ev_join before the call returns), the load
+// flows on st.
 cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchSetup *bs, double tol, int max_iter,
-                               int num_sms, cudaStream_t st);
+                               int num_sms, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
+                               cudaEvent_t ev_join);
 
 // The reduced network of a caller assignment (one CTA per scenario).
 __global__ void __launch_bounds__(1024) k_eval_reduced(Topo T, const int *__restrict__ sup, const int *__restrict__ moff,

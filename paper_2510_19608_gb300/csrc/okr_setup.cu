@@ -850,16 +850,25 @@ __global__ void __launch_bounds__(1024) k_batch_finish(const BatchSetup *bs) {
 }
 
 cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchSetup *bs, double tol, int max_iter,
-                               int num_sms, cudaStream_t st) {
+                               int num_sms, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_fork,
+                               cudaEvent_t ev_join) {
     if (nf <= 0) return cudaSuccess;
     k_batch_prep<<<nf, 1024, 0, st>>>(bs);
+    // the LCA tables (integer work, read only by the searches) on the side
+    // stream beside the load flows (FP64 work)
+    cudaError_t e = cudaEventRecord(ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side, ev_fork, 0);
+    if (e != cudaSuccess) return e;
     long long bx = (max_nn + 255) / 256;
     if (bx > num_sms * 2) bx = num_sms * 2;
     if (bx < 1) bx = 1;
-    k_batch_lca<<<dim3((unsigned)bx, nf), 256, 0, st>>>(bs);
+    k_batch_lca<<<dim3((unsigned)bx, nf), 256, 0, side>>>(bs);
+    e = cudaEventRecord(ev_join, side);
+    if (e != cudaSuccess) return e;
     k_batch_pf<<<dim3(max_L, nf), 1024, 0, st>>>(bs, tol, max_iter);
     k_batch_finish<<<nf, 1024, 0, st>>>(bs);
-    return cudaGetLastError();
+    e = cudaStreamWaitEvent(st, ev_join, 0);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace okr
