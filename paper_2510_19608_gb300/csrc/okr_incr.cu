@@ -936,8 +936,12 @@ __device__ __forceinline__ u128 warp_min128(u128 v) {
     return v;
 }
 
-// Blocks whose records pass B reads one warp per block (or all warps each,
-// when there are at most this many).
+// Pass B of the selection reads every record when they are in shared memory
+// and the feeder has at most this many buses (at most 8 records a thread of
+// a 384-thread CTA; measured faster up to 1,000 buses, slower from 2,200);
+// otherwise it reads the blocks that may hold a candidate of the tie band, one
+// warp per block (or all warps each, when there are at most kFewBlocks).
+constexpr int kFlatSelectMax = 1536;
 constexpr int kFewBlocks = 8;
 
 // The summaries of the dirty blocks, one warp per block, then a barrier.
@@ -1517,58 +1521,83 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             maxerr_done = true;
             break;
         }
-        // pass B: only the blocks that may hold a candidate of the tie band
-        // (or one that the screen cannot place) are read record by record; a
-        // block whose smallest key lies above the band counts whole.  With few
-        // such blocks every warp reads them all and needs no barrier; with
-        // more they are spread over the warps and reduced block-wide.
+        // pass B: the smallest (tie key, slot) in the tie band and the smallest
+        // key above it (precision 0); in precision 1, the smallest (tie key,
+        // slot) surely in the band, the smallest tie key of a candidate the
+        // screen cannot place, and the smallest lower end surely out of it.
+        // Records in shared memory, at most kFlatSelectMax buses: every record
+        // once, each thread a strided share of the slots, then one block
+        // reduction.  Otherwise only the blocks that may hold a candidate of the band are
+        // read record by record (a block whose smallest key lies above the
+        // band counts whole); with few such blocks every warp reads them all
+        // and needs no barrier, with more they are spread over the warps.
         int ws = -1;
         double gap = INFINITY;
+        const bool flat_b = rec_mode != 0 && n <= kFlatSelectMax;
         if (PREC == 0) {
             const u128 edge = (ra.a ^ kSignBit) + tau_fx, ek = okey(edge);
-            const u128 *bs = reinterpret_cast<const u128 *>(R.bsum);
             u128 pa = kNone, pb = kNone;        // smallest (key, slot) in the band; smallest score above it
-            auto relevant = [&](int j) {
-                const u128 bk = j < R.nb ? bs[j] : kNone;
-                return bk != kNone && bk <= ek;
-            };
-            int nrel = 0;
-            for (int j0 = 0; j0 < R.nb; j0 += 32) {
-                const int j = j0 + lane;
-                const bool rel = relevant(j);
-                if (!rel && j < R.nb) pb = umin(pb, bs[j]);          // the whole block above the band
-                nrel += __popc(__ballot_sync(0xffffffffu, rel));
-            }
-            const bool few = nrel <= kFewBlocks;
-            int kq = 0;
-            for (int j0 = 0; j0 < R.nb; j0 += 32) {
-                unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
-                while (mask) {
-                    const int b = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    if (few || kq % (NT / 32) == wid) {
-                        const int c = 32 * (j0 + b) + lane;
-                        if (c < 2 * n) {
-                            const u128 k = R.r0[c];
-                            if (k <= ek) pa = umin(pa, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
-                            else pb = umin(pb, k);
-                        }
-                    }
-                    ++kq;
+            if (flat_b) {
+                for (int c = tid; c < 2 * n; c += NT) {
+                    const u128 k = R.r0[c];
+                    if (k == kNone) continue;
+                    if (k <= ek) pa = umin(pa, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
+                    else pb = umin(pb, k);
                 }
-            }
-            if (few) {
-                pa = warp_min128(pa);
-                pb = warp_min128(pb);
+                {
+                    Red rb;
+                    rb.a = pa;
+                    rb.b = pb;
+                    rb.c = kNone;
+                    rb.i = 0;
+                    rb = block_red<NT>(rb, sred);
+                    pa = rb.a;
+                    pb = rb.b;
+                }
             } else {
-                Red rb;
-                rb.a = pa;
-                rb.b = pb;
-                rb.c = kNone;
-                rb.i = 0;
-                rb = block_red<NT>(rb, sred);
-                pa = rb.a;
-                pb = rb.b;
+                const u128 *bs = reinterpret_cast<const u128 *>(R.bsum);
+                auto relevant = [&](int j) {
+                    const u128 bk = j < R.nb ? bs[j] : kNone;
+                    return bk != kNone && bk <= ek;
+                };
+                int nrel = 0;
+                for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool rel = relevant(j);
+                    if (!rel && j < R.nb) pb = umin(pb, bs[j]);          // the whole block above the band
+                    nrel += __popc(__ballot_sync(0xffffffffu, rel));
+                }
+                const bool few = nrel <= kFewBlocks;
+                int kq = 0;
+                for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                    unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
+                    while (mask) {
+                        const int b = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        if (few || kq % (NT / 32) == wid) {
+                            const int c = 32 * (j0 + b) + lane;
+                            if (c < 2 * n) {
+                                const u128 k = R.r0[c];
+                                if (k <= ek) pa = umin(pa, ((u128)R.tkey[c] << 32) | (u128)(unsigned)c);
+                                else pb = umin(pb, k);
+                            }
+                        }
+                        ++kq;
+                    }
+                }
+                if (few) {
+                    pa = warp_min128(pa);
+                    pb = warp_min128(pb);
+                } else {
+                    Red rb;
+                    rb.a = pa;
+                    rb.b = pb;
+                    rb.c = kNone;
+                    rb.i = 0;
+                    rb = block_red<NT>(rb, sred);
+                    pa = rb.a;
+                    pb = rb.b;
+                }
             }
             ws = (int)(unsigned)(pa & 0xffffffffu);
             if (tid == 0 && pb != kNone) gap = fx_to_d((pb ^ kSignBit) - edge);
@@ -1580,64 +1609,93 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             const long long m_hi = has_hi ? key_val((unsigned long long)ra.b) : 0;
             const unsigned long long ein = val_key(m_lo + tau_dn);
             const unsigned long long eout = has_hi ? val_key(m_hi + tau_up) : kKeyNone;
-            const ulonglong2 *bs = reinterpret_cast<const ulonglong2 *>(R.bsum);
-            // a block is read record by record unless every candidate in it is
-            // surely out of the band (its smallest lower end above eout)
-            auto relevant = [&](int j) {
-                const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
-                return bl != kKeyNone && !(has_hi && bl > eout);
-            };
             unsigned long long pa = ~0ull, pb = ~0ull, pc = ~0ull;
-            int nrel = 0;
-            for (int j0 = 0; j0 < R.nb; j0 += 32) {
-                const int j = j0 + lane;
-                const bool rel = relevant(j);
-                const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
-                if (bl != kKeyNone && !rel) pc = bl < pc ? bl : pc;        // the whole block surely out
-                nrel += __popc(__ballot_sync(0xffffffffu, rel));
-            }
-            const bool few = nrel <= kFewBlocks;
-            int kq = 0;
-            for (int j0 = 0; j0 < R.nb; j0 += 32) {
-                unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
-                while (mask) {
-                    const int b = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    if (few || kq % (NT / 32) == wid) {
-                        const int c = 32 * (j0 + b) + lane;
-                        if (c < 2 * n) {
-                            const ulonglong2 q = R.r1[c];
-                            if (q.x != kKeyNone) {
-                                const bool in_sure = q.y <= ein;
-                                const bool out_sure = has_hi && q.x > eout;
-                                const unsigned key = R.tkey[c];
-                                if (in_sure) {
-                                    const unsigned long long kc = ((unsigned long long)key << 32) | (unsigned)c;
-                                    pa = kc < pa ? kc : pa;
-                                } else if (!out_sure) {
-                                    pb = key < pb ? key : pb;
+            if (flat_b) {
+                for (int c = tid; c < 2 * n; c += NT) {
+                    const ulonglong2 q = R.r1[c];
+                    if (q.x == kKeyNone) continue;
+                    const bool in_sure = q.y <= ein;
+                    const bool out_sure = has_hi && q.x > eout;     // (never both: lo <= hi, m_lo <= m_hi)
+                    if (in_sure) {
+                        const unsigned long long kc = ((unsigned long long)R.tkey[c] << 32) | (unsigned)c;
+                        pa = kc < pa ? kc : pa;
+                    } else if (!out_sure) {
+                        const unsigned long long key = R.tkey[c];
+                        pb = key < pb ? key : pb;
+                    } else {
+                        pc = q.x < pc ? q.x : pc;
+                    }
+                }
+                {
+                    Red64 r6;
+                    r6.a = pa;
+                    r6.b = pb;
+                    r6.c = pc;
+                    r6.i = 0;
+                    r6 = block_sel64(r6, &s_sel[1]);
+                    pa = r6.a;
+                    pb = r6.b;
+                    pc = r6.c;
+                }
+            } else {
+                const ulonglong2 *bs = reinterpret_cast<const ulonglong2 *>(R.bsum);
+                // a block is read record by record unless every candidate in it is
+                // surely out of the band (its smallest lower end above eout)
+                auto relevant = [&](int j) {
+                    const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
+                    return bl != kKeyNone && !(has_hi && bl > eout);
+                };
+                int nrel = 0;
+                for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                    const int j = j0 + lane;
+                    const bool rel = relevant(j);
+                    const unsigned long long bl = j < R.nb ? bs[j].x : kKeyNone;
+                    if (bl != kKeyNone && !rel) pc = bl < pc ? bl : pc;        // the whole block surely out
+                    nrel += __popc(__ballot_sync(0xffffffffu, rel));
+                }
+                const bool few = nrel <= kFewBlocks;
+                int kq = 0;
+                for (int j0 = 0; j0 < R.nb; j0 += 32) {
+                    unsigned mask = __ballot_sync(0xffffffffu, relevant(j0 + lane));
+                    while (mask) {
+                        const int b = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        if (few || kq % (NT / 32) == wid) {
+                            const int c = 32 * (j0 + b) + lane;
+                            if (c < 2 * n) {
+                                const ulonglong2 q = R.r1[c];
+                                if (q.x != kKeyNone) {
+                                    const bool in_sure = q.y <= ein;
+                                    const bool out_sure = has_hi && q.x > eout;
+                                    const unsigned key = R.tkey[c];
+                                    if (in_sure) {
+                                        const unsigned long long kc = ((unsigned long long)key << 32) | (unsigned)c;
+                                        pa = kc < pa ? kc : pa;
+                                    } else if (!out_sure) {
+                                        pb = key < pb ? key : pb;
+                                    }
+                                    if (out_sure) pc = q.x < pc ? q.x : pc;
                                 }
-                                if (out_sure) pc = q.x < pc ? q.x : pc;
                             }
                         }
+                        ++kq;
                     }
-                    ++kq;
                 }
-            }
-            if (few) {
-                pa = warp_min64(pa);
-                pb = warp_min64(pb);
-                pc = warp_min64(pc);
-            } else {
-                Red64 r6;
-                r6.a = pa;
-                r6.b = pb;
-                r6.c = pc;
-                r6.i = 0;
-                r6 = block_sel64(r6, &s_sel[1]);
-                pa = r6.a;
-                pb = r6.b;
-                pc = r6.c;
+                if (few) {
+                    pa = warp_min64(pa);
+                    pb = warp_min64(pb);
+                    pc = warp_min64(pc);
+                } else {
+                    Red64 r6;
+                    r6.a = pa;
+                    r6.b = pb;
+                    r6.c = pc;
+                    r6.i = 0;
+                    r6 = block_sel64(r6, &s_sel[1]);
+                    pa = r6.a;
+                    pb = r6.b;
+                    pc = r6.c;
+                }
             }
             Red rb;
             rb.a = pa == ~0ull ? kNone : (u128)pa;
