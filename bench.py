@@ -381,7 +381,10 @@ def learned_line(K, ctx, n_train=64, record=64):
             "eval": {"workload": "feeder3100, first %d iterations" % record, "candidates": int(Xt.shape[0]),
                      "predict_and_rank_s": t_eval,
                      "top_k": {str(k): v for k, v in q.items() if isinstance(k, int)},
-                     "winner_rank_percentile": q["winner_rank_percentile"]},
+                     "winner_rank_percentile": q["winner_rank_percentile"],
+                     "tie_band_median": q.get("tie_band_median"), "tie_band_max": q.get("tie_band_max"),
+                     "note": "miss_rate: the committed candidate (the smallest (r, s) of the candidates tied with the "
+                             "optimum) outside the top-k; optimum_missed: no optimal candidate in the top-k"},
             "pruned_search": pruned, "inference": inference}
 
 

@@ -819,7 +819,7 @@ __global__ void k_batch_lca(const BatchSetup *bs) {
 }
 
 // Load flow: blockIdx.y = feeder, blockIdx.x = scenario.
-__global__ void __launch_bounds__(1024) k_batch_pf(const BatchSetup *bs, double tol, int max_iter) {
+__global__ void __launch_bounds__(256) k_batch_pf(const BatchSetup *bs, double tol, int max_iter) {
     __shared__ BatchSetup b;
     if (threadIdx.x == 0) b = bs[blockIdx.y];
     __syncthreads();
@@ -865,7 +865,10 @@ cudaError_t launch_batch_setup(int nf, int max_L, long long max_nn, const BatchS
     k_batch_lca<<<dim3((unsigned)bx, nf), 256, 0, side>>>(bs);
     e = cudaEventRecord(ev_join, side);
     if (e != cudaSuccess) return e;
-    k_batch_pf<<<dim3(max_L, nf), 1024, 0, st>>>(bs, tol, max_iter);
+    // 256 threads: every (feeder, scenario) CTA resident at once, so that the
+    // SMs interleave many CTAs' level-by-level chains (1,024-thread CTAs ran
+    // in waves: 4.0 -> 3.2 ms for 256 feeders)
+    k_batch_pf<<<dim3(max_L, nf), 256, 0, st>>>(bs, tol, max_iter);
     k_batch_finish<<<nf, 1024, 0, st>>>(bs);
     e = cudaStreamWaitEvent(st, ev_join, 0);
     return e != cudaSuccess ? e : cudaGetLastError();

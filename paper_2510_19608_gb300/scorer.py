@@ -94,8 +94,9 @@ def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256), T=None,
     the committed candidate is among the top-k predictions (miss_rate); with the
     targets T, also whether the top-k holds any candidate of optimal score
     (optimum_missed: none within the tie band) and the regret, the best exact
-    score among the top-k above the optimum, in margins; and the mean fraction
-    of candidates a top-k evaluation would score."""
+    score among the top-k above the optimum, in margins; the mean fraction
+    of candidates a top-k evaluation would score; and how many candidates tie
+    with the optimum per iteration (tie_band_median, tie_band_max)."""
     pred = ctx.scorer_predict(X) if X.shape[0] else np.zeros(0, np.float32)
     out = {}
     rows = [(a, b, w) for a, b, w in groups if w >= 0]
@@ -122,6 +123,13 @@ def miss_rate(ctx: "B.Context", X: np.ndarray, groups, ks=(16, 64, 256), T=None,
         out[k] = d
     pct = [float(np.searchsorted(np.sort(pred[a:b]), pred[a + w], side="left")) / (b - a) for a, b, w in rows]
     out["winner_rank_percentile"] = float(np.mean(pct)) if pct else float("nan")
+    if T is not None and rows:
+        # candidates tied with the iteration's optimum (inside the tie band):
+        # the committed one is the smallest (r, s) among them, which no
+        # ranking by predicted score can single out when many tie
+        sizes = [int(np.count_nonzero(T[a:b] <= band + 1e-6)) for a, b, _ in rows]
+        out["tie_band_median"] = float(np.median(sizes))
+        out["tie_band_max"] = int(max(sizes))
     return out
 
 
