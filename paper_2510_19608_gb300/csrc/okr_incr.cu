@@ -1873,13 +1873,16 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
             }
             if (dsum != 0) sadd128(&s_dsum[0], &s_dsum[1], dsum);
             // r's members join s (they lie in the subtree of r's top); the new
-            // super-node list
-            {
+            // super-node list.  Not on the last warp, which goes straight to the
+            // rebuilt pairs below (their chain of dependent loads is this
+            // step's longest).
+            constexpr int NB = NT - 32;
+            if (tid < NB) {
                 const int rtop = S.top[hw.r], rtop_end = rtop + T.sz[rtop];
-                for (int b = rtop + tid; b < rtop_end; b += NT)
+                for (int b = rtop + tid; b < rtop_end; b += NB)
                     if (S.label[b] == hw.r) S.label[b] = hw.s;
+                for (int j = tid; j < ns - 1; j += NB) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             }
-            for (int j = tid; j < ns - 1; j += NT) list_new[j] = list_old[j + (j >= hw.jr ? 1 : 0)];
             // s takes r's injection (no term before the merge reads s's injection:
             // every candidate with r = s* is rebuilt)
             const unsigned phr = Lc.ph[hw.r];
