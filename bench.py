@@ -437,7 +437,7 @@ def search_roofline(K, ctx, dfeed, run, search_ms: float, merges: int) -> dict:
                     "frac": achieved_flops / FP32_PEAK_TFLOPS,
                     "peak_source": "derived FP32 ALU rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"},
             # incremental engine's phase timer (CTA 0): selection = block summaries and pass A (11) + pass B (0);
-            # changed set = the wait for the winner's record (12) + the scan beside the merge's evaluation (1)
+            # changed set = the winner's record (12) + the scan beside the merge's evaluation (1)
             "phase_us_per_merge": {k: round(1e3 * v / max(merges, 1), 3) for k, v in (
                 ("select", ps["phase_ms"][11] + ps["phase_ms"][0]), ("changed_set", ps["phase_ms"][12] + ps["phase_ms"][1]),
                 ("merge_and_rebuild", ps["phase_ms"][2]), ("terms", ps["phase_ms"][3]))},

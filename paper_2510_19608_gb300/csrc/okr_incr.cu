@@ -752,10 +752,6 @@ __device__ __forceinline__ Win make_win(const Cand &w, int ws, const int *rank) 
     return h;
 }
 
-// Barrier of the first `count` threads of the block (named barrier 1).
-__device__ __forceinline__ void first_threads_sync(int count) {
-    asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
-}
 
 // Whether candidate c (not next to s* or r*) has a term that reads an input
 // the merge h changes: a position in the moved ranges or at s*, r*; its fixed
@@ -1333,7 +1329,6 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
     __shared__ __align__(16) Red sred[33];
     __shared__ __align__(16) Red64 s_sel[2];   // precision-1 selection accumulators: pass A, pass B
     __shared__ int sscan[33];
-    __shared__ Win h;
     __shared__ unsigned long long s_sfx[2];     // SMICE of the committed state, fixed point
     __shared__ unsigned long long s_dsum[2];    // the last merge's change of it
     __shared__ int s_cnt[4];                    // append counters: rebuilt pairs, changed entries, entries, R
@@ -1764,27 +1759,20 @@ __device__ void inc_run(const Topo &T, const State &S, const Search &X, const In
         }
         stamp(0);
         // ============================================================ the merge's changed set
-        // The winner's record: the scan warps share thread 0's copy (r*'s
-        // subtree and the decision's bus ids are looked up in the merge step);
-        // the warps that evaluate the merge build their own at once, without
-        // waiting (every thread knows ws).
+        // The winner's record: every thread builds its own at once (every
+        // thread knows ws; one broadcast load of its candidate), so no warp
+        // waits for another's copy (r*'s subtree and the decision's bus ids
+        // are looked up in the merge step).
         constexpr int NW = NT / 32;
         const int CW = cw;                  // warps that evaluate the merge (1 .. NW - 1)
         const bool commit_warp = (tid >> 5) >= NW - CW;
-        Win hw;
-        if (commit_warp) {
-            hw = make_win(X.slot[ws], ws, rank);
-        } else {
-            if (tid == 0) {
-                h = make_win(X.slot[ws], ws, rank);
-                X.dec_gap[t] = gap;
-                s_dsum[0] = 0ull;
-                s_dsum[1] = 0ull;
-            }
-            first_threads_sync((NW - CW) * 32);
-            hw = h;
-            stamp(12);                                  // profile: the scan warps' wait for the winner's record
+        const Win hw = make_win(X.slot[ws], ws, rank);
+        if (tid == 0) {
+            X.dec_gap[t] = gap;
+            s_dsum[0] = 0ull;
+            s_dsum[1] = 0ull;
         }
+        stamp(12);                                      // profile: the winner's record
         O.s = hw.s;
         O.r = hw.r;
         O.nfree = (hw.q1hi - hw.q1lo) + (hw.q2hi - hw.q2lo);
