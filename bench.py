@@ -36,8 +36,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FLOPS_PER_ITEM = 40
 # DRAM bytes of one search launch on this workload from the ncu capture in
 # profiles/, valid only for the kernel source it was taken on (None otherwise)
-NCU_TRAFFIC = {"bytes": 1185792 + 3328, "source": "paper_2510_19608_gb300/csrc/okr_incr.cu",
-               "sha256_prefix": "421b0d4b1715c190", "summary": "profiles/k_search_inc_feeder1000.md"}
+NCU_TRAFFIC = {"bytes": 1166336 + 768, "source": "paper_2510_19608_gb300/csrc/okr_incr.cu",
+               "sha256_prefix": "56d4cc024db929ed", "summary": "profiles/k_search_inc_feeder1000.md"}
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 
 # Latency floor of one merge of the incremental search.  One merge is a chain
