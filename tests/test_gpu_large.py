@@ -389,3 +389,34 @@ def test_inc_autotune_single_and_batch(ctx, batch256):
         assert e.value.status == EINVAL
     finally:
         ctx.reset_inc_shape()
+
+
+def test_flat_and_block_walk_selection_agree_at_the_flat_limit(ctx):
+    """Pass B of the selection reads every record when the feeder has at most
+    1,536 buses and its records are in shared memory, and walks the block
+    summaries otherwise.  On a feeder of exactly 1,536 buses both ways (the
+    records in shared memory, then forced into device memory) give the same
+    run in both precisions: every decision, score, largest error, gap and
+    candidate count bit for bit, and the same assignment; verify mode with
+    the flat pass finds every carried score equal to a fresh evaluation."""
+    f = fg.make_feeder(1536, 1536, phase_mode=(0.45, 0.15, 0.4), load=("lognormal", 15.0, 1.0))
+    for precision in (0, 1):
+        runs = []
+        for shape in ({}, dict(records=1)):
+            try:
+                if shape:
+                    ctx.set_inc_shape(**shape)
+                ctx.reduce(f, params(margin=0.005, target_reduction=0.5, engine=2, precision=precision))
+                s = ctx.summary()
+                assert (s["inc_records"] == 1) if shape else (s["inc_records"] in (2, 3))
+                runs.append((ctx.decisions(), s, ctx.assignment()))
+            finally:
+                ctx.reset_inc_shape()
+        (d0, s0, a0), (d1, s1, a1) = runs
+        assert s0["n_iter"] == s1["n_iter"] > 0 and s0["stop_reason"] == s1["stop_reason"]
+        for key in ("s", "r", "score", "maxerr", "gap", "ncand"):
+            assert np.array_equal(d0[key], d1[key]), key
+        assert np.array_equal(a0, a1)
+        ctx.reduce(f, params(margin=0.005, max_merges=150, engine=3, precision=precision))
+        s = ctx.summary()
+        assert s["inc_records"] in (2, 3) and s["n_iter"] == 150 and s["inc_mismatches"] == 0
